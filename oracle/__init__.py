@@ -1,0 +1,193 @@
+"""FP64 CPU oracle of the GiFt filter path -- TEST INFRASTRUCTURE ONLY.
+
+Only ``tests/``, the smoke check and the CPU-baseline leg of ``bench.py`` may
+import this package.  The product path (the CUDA library and its binding)
+never calls it.  The arithmetic lives in ``gift_oracle.c`` (plain C, FP64,
+single thread); this module compiles it with gcc and marshals numpy arrays.
+
+Every function states the paper passage it follows:
+
+* :func:`build_graph`   -- clique net model, weight 2/M (Sec. 2.2 after Eq. 4,
+  Sec. 3.2.3); duplicates summed in net order (Sec. 2.1, single w_ij).
+* :func:`round_values`  -- storage rounding of the edge weights (round to
+  nearest even into binary32 / bfloat16 / binary16), an implementation choice
+  the paper does not make (its precision is unstated).
+* :func:`degrees`       -- d_i = sum_j w_ij (Sec. 2.1).
+* :func:`apply`         -- one product with A~_sigma (Eq. 16) or its random-walk form.
+* :func:`gift`          -- Eq. 15 with the Sec. 4.1 coefficients; fixed cells
+  reimposed (Sec. 3.2.2, Algorithm 1).
+* :func:`hpwl`          -- half-perimeter wirelength (Sec. 4.1 reports it).
+
+Parity pins live in ``tests/test_oracle_*.py``.
+"""
+from __future__ import annotations
+
+import ctypes as C
+import os
+import subprocess
+from dataclasses import dataclass
+
+import numpy as np
+
+_HERE = os.path.dirname(os.path.abspath(__file__))
+_SRC = os.path.join(_HERE, "gift_oracle.c")
+_LIBDIR = os.path.join(_HERE, "lib")
+_LIB = os.path.join(_LIBDIR, "libgift_oracle.so")
+
+DEFAULT_TERMS = ((2.0, 2, 0.1), (4.0, 2, 0.7), (4.0, 4, 0.2))  # Eq. 15 + Sec. 4.1
+FMT = {"f64": 0, "f32": 1, "bf16": 2, "f16": 3}
+
+
+def build() -> str:
+    """Compile the oracle library (gcc, -O2, no fast-math)."""
+    os.makedirs(_LIBDIR, exist_ok=True)
+    if (not os.path.exists(_LIB)) or os.path.getmtime(_LIB) < os.path.getmtime(_SRC):
+        tmp = _LIB + f".tmp{os.getpid()}"
+        subprocess.check_call(["gcc", "-O2", "-std=c11", "-fPIC", "-shared", "-fno-fast-math",
+                               "-ffp-contract=off", "-o", tmp, _SRC, "-lm"])
+        os.replace(tmp, _LIB)
+    return _LIB
+
+
+_lib = None
+
+
+def lib():
+    global _lib
+    if _lib is None:
+        L = C.CDLL(build())
+        P = C.c_void_p
+        L.oracle_build.restype = P
+        L.oracle_build.argtypes = [C.c_int32, C.c_int32, P, P]
+        L.oracle_graph_nnz.restype = C.c_int64
+        L.oracle_graph_nnz.argtypes = [P]
+        L.oracle_graph_copy.argtypes = [P, P, P, P]
+        L.oracle_graph_free.argtypes = [P]
+        L.oracle_round.argtypes = [C.c_int64, P, P, C.c_int32]
+        L.oracle_degrees.argtypes = [C.c_int32, P, P, P]
+        L.oracle_apply.argtypes = [C.c_int32, C.c_int32, P, P, P, P, C.c_double, C.c_int32, P, P]
+        L.oracle_filter.restype = C.c_int
+        L.oracle_filter.argtypes = [C.c_int32, C.c_int32, P, P, P, P, C.c_int32, P, P, P,
+                                    C.c_int32, C.c_int32, P, P, P]
+        L.oracle_hpwl.argtypes = [C.c_int32, P, P, C.c_int32, P, P]
+        _lib = L
+    return _lib
+
+
+def _p(a: np.ndarray):
+    return a.ctypes.data_as(C.c_void_p)
+
+
+@dataclass
+class Graph:
+    n: int
+    row_ptr: np.ndarray  # int64 [n+1]
+    col: np.ndarray      # int32 [nnz]
+    val: np.ndarray      # float64 [nnz]
+
+    @property
+    def nnz(self) -> int:
+        return int(self.row_ptr[-1])
+
+
+def build_graph(num_cells: int, net_ptr: np.ndarray, pin_cell: np.ndarray) -> Graph:
+    """Clique expansion (weight 2/M, duplicates summed in net order) to CSR."""
+    net_ptr = np.ascontiguousarray(net_ptr, dtype=np.int64)
+    pin_cell = np.ascontiguousarray(pin_cell, dtype=np.int32)
+    if pin_cell.size == 0:
+        pin_cell = np.zeros(1, dtype=np.int32)
+    h = lib().oracle_build(int(num_cells), int(net_ptr.size - 1), _p(net_ptr), _p(pin_cell))
+    if not h:
+        raise ValueError("oracle_build rejected the netlist")
+    try:
+        nnz = lib().oracle_graph_nnz(h)
+        rp = np.zeros(num_cells + 1, dtype=np.int64)
+        col = np.zeros(max(nnz, 1), dtype=np.int32)
+        val = np.zeros(max(nnz, 1), dtype=np.float64)
+        lib().oracle_graph_copy(h, _p(rp), _p(col), _p(val))
+    finally:
+        lib().oracle_graph_free(h)
+    return Graph(num_cells, rp, col[:nnz], val[:nnz])
+
+
+def round_values(v: np.ndarray, fmt: str) -> np.ndarray:
+    v = np.ascontiguousarray(v, dtype=np.float64)
+    out = np.empty_like(v)
+    if v.size:
+        lib().oracle_round(v.size, _p(v), _p(out), FMT[fmt])
+    return out
+
+
+def stored(g: Graph, fmt: str) -> Graph:
+    """The graph with its weights rounded to the storage format."""
+    return Graph(g.n, g.row_ptr, g.col, round_values(g.val, fmt))
+
+
+def degrees(g: Graph) -> np.ndarray:
+    d = np.zeros(g.n, dtype=np.float64)
+    val = g.val if g.val.size else np.zeros(1)
+    lib().oracle_degrees(g.n, _p(g.row_ptr), _p(val), _p(d))
+    return d
+
+
+def _csr_args(g: Graph):
+    col = g.col if g.col.size else np.zeros(1, dtype=np.int32)
+    val = g.val if g.val.size else np.zeros(1, dtype=np.float64)
+    return g.row_ptr, np.ascontiguousarray(col), np.ascontiguousarray(val)
+
+
+def apply(g: Graph, d: np.ndarray, sigma: float, x: np.ndarray, norm: str = "sym") -> np.ndarray:
+    """One product y = A~_sigma x (Eq. 16; ``norm='rw'``: (D+sigma I)^-1 (A+sigma I) x)."""
+    x = np.ascontiguousarray(x, dtype=np.float64)
+    K = 1 if x.ndim == 1 else int(np.prod(x.shape[1:]))
+    y = np.zeros_like(x)
+    rp, col, val = _csr_args(g)
+    lib().oracle_apply(g.n, K, _p(rp), _p(col), _p(val), _p(np.ascontiguousarray(d, dtype=np.float64)),
+                       float(sigma), 0 if norm == "sym" else 1, _p(x), _p(y))
+    return y
+
+
+def gift(g: Graph, d: np.ndarray, sig: np.ndarray, is_fixed: np.ndarray | None,
+         terms=DEFAULT_TERMS, norm: str = "sym", reimpose: bool = True) -> np.ndarray:
+    """GiFt (Eq. 15): sum_t alpha_t A~_{sigma_t}^{k_t} g, fixed rows reimposed."""
+    x = np.ascontiguousarray(sig, dtype=np.float64)
+    K = 1 if x.ndim == 1 else int(np.prod(x.shape[1:]))
+    out = np.zeros_like(x)
+    sg = np.array([t[0] for t in terms], dtype=np.float64)
+    pw = np.array([t[1] for t in terms], dtype=np.int32)
+    al = np.array([t[2] for t in terms], dtype=np.float64)
+    fx = np.ascontiguousarray(is_fixed if is_fixed is not None else np.zeros(g.n), dtype=np.uint8)
+    rp, col, val = _csr_args(g)
+    rc = lib().oracle_filter(g.n, K, _p(rp), _p(col), _p(val), _p(np.ascontiguousarray(d, dtype=np.float64)),
+                             len(terms), _p(sg), _p(pw), _p(al), 0 if norm == "sym" else 1,
+                             1 if reimpose else 0, _p(fx), _p(x), _p(out))
+    if rc != 0:
+        raise MemoryError("oracle_filter: out of memory")
+    return out
+
+
+def hpwl(net_ptr: np.ndarray, pin_cell: np.ndarray, xy: np.ndarray) -> np.ndarray:
+    """HPWL per signal of locations xy [N, S, 2]."""
+    xy = np.ascontiguousarray(xy, dtype=np.float64)
+    S = xy.shape[1]
+    out = np.zeros(S, dtype=np.float64)
+    net_ptr = np.ascontiguousarray(net_ptr, dtype=np.int64)
+    pc = np.ascontiguousarray(pin_cell, dtype=np.int32)
+    if pc.size == 0:
+        pc = np.zeros(1, dtype=np.int32)
+    lib().oracle_hpwl(int(net_ptr.size - 1), _p(net_ptr), _p(pc), S, _p(xy), _p(out))
+    return out
+
+
+def run(nl, sig: np.ndarray, fmt: str = "f64", terms=DEFAULT_TERMS, norm: str = "sym",
+        reimpose: bool = True):
+    """Whole path for a netlist: (graph, degrees, filtered signal).
+
+    ``fmt`` rounds the weights as the storage format would before the degrees
+    are taken (degrees always over the stored weights)."""
+    g = build_graph(nl.num_cells, nl.net_ptr, nl.pin_cell)
+    if fmt != "f64":
+        g = stored(g, fmt)
+    d = degrees(g)
+    out = gift(g, d, sig, nl.is_fixed, terms, norm, reimpose)
+    return g, d, out
