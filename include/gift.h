@@ -1,0 +1,198 @@
+/*
+ * gift.h -- C ABI of the GiFt filter library for GB300 (sm_103a).
+ *
+ * GiFt (Liu et al., "The Power of Graph Signal Processing for Chip Placement
+ * Acceleration", ICCAD 2024) turns a netlist into an initial placement with a
+ * parameter-free multi-resolution low-pass graph filter.  This library runs
+ * its data-parallel path on one GPU:
+ *
+ *   gift_build_graph  netlist -> clique graph (Sec. 2.2 weight rule w = 2/M,
+ *                     Sec. 3.2.3 clique net model) -> CSR + FP64 degrees
+ *   gift_filter       g' = sum_t alpha_t A~_{sigma_t}^{k_t} g  (Eq. 15-16),
+ *                     fixed cells put back (Sec. 3.2.2, Algorithm 1)
+ *   gift_hpwl         half-perimeter wirelength of a placement (Sec. 4.1)
+ *
+ * Conventions shared by every call:
+ *   - Every call returns a gift_status; no exception or abort crosses the ABI.
+ *     On a non-OK status gift_last_error() gives a message (thread-local).
+ *   - Invalid input (ids out of range, decreasing net_ptr, N <= 0, S <= 0,
+ *     unknown enum values, null pointers) yields GIFT_ERR_INVALID and leaves
+ *     no allocation behind.  The filter does not scan its input for NaN.
+ *   - Input arrays are borrowed for the duration of the call only.  Host
+ *     inputs are copied before the call returns; device inputs must stay valid
+ *     until the work queued on `stream` has completed.
+ *   - `stream` is a cudaStream_t passed as void* (NULL = legacy default stream).
+ *     Work is queued on it; calls that return host data synchronise it.
+ *   - Handles (gift_ctx, gift_graph) own their device memory and must be
+ *     released with the matching *_destroy / *_free call.
+ *   - A signal is row-major float32 [N][S][2]: for each cell, S (x, y) pairs.
+ */
+#ifndef GIFT_H
+#define GIFT_H
+
+#include <stdint.h>
+
+#if defined(__GNUC__)
+#define GIFT_API __attribute__((visibility("default")))
+#else
+#define GIFT_API
+#endif
+
+#ifdef __cplusplus
+extern "C" {
+#endif
+
+typedef enum gift_status {
+    GIFT_OK = 0,
+    GIFT_ERR_INVALID = 1,     /* malformed argument or netlist                 */
+    GIFT_ERR_OOM = 2,         /* device or host allocation failed              */
+    GIFT_ERR_CUDA = 3,        /* a CUDA runtime call failed                    */
+    GIFT_ERR_TIMEOUT = 4,     /* a bounded device or host wait ran out         */
+    GIFT_ERR_BUSY = 5,        /* result not ready yet / no capacity right now  */
+    GIFT_ERR_UNSUPPORTED = 6  /* valid request this build cannot serve         */
+} gift_status;
+
+/* where the arrays of a call live */
+#define GIFT_MEM_HOST 0
+#define GIFT_MEM_DEVICE 1
+
+/* storage type of the edge weights; signals and accumulation are always FP32 */
+#define GIFT_WEIGHT_F32 0
+#define GIFT_WEIGHT_BF16 1
+#define GIFT_WEIGHT_F16 2
+
+/* normalisation of A + sigma I */
+#define GIFT_NORM_SYM 0 /* (D+sI)^-1/2 (A+sI) (D+sI)^-1/2, Eq. 16 (the paper)      */
+#define GIFT_NORM_RW 1  /* (D+sI)^-1 (A+sI), random-walk form (not in the paper)   */
+
+#define GIFT_MAX_TERMS 8
+
+typedef struct gift_ctx gift_ctx;
+typedef struct gift_graph gift_graph;
+
+/* A netlist (Sec. 2.2: objects and nets; Algorithm 1: fixed cells keep their
+ * predetermined locations).  Net e owns pins [net_ptr[e], net_ptr[e+1]) and
+ * pin p sits on cell pin_cell[p].  net_ptr[0] must be 0 and net_ptr must not
+ * decrease; every pin_cell value must lie in [0, num_cells).  is_fixed[i] != 0
+ * marks a fixed cell (may be NULL: no fixed cells).  All three arrays live in
+ * the memory named by `mem`. */
+typedef struct gift_netlist {
+    int32_t num_cells;       /* N > 0                                  */
+    int32_t num_nets;        /* E >= 0                                 */
+    const int64_t *net_ptr;  /* [E + 1]                                */
+    const int32_t *pin_cell; /* [net_ptr[E]]                           */
+    const uint8_t *is_fixed; /* [N] or NULL                            */
+    int32_t mem;             /* GIFT_MEM_HOST or GIFT_MEM_DEVICE       */
+} gift_netlist;
+
+typedef struct gift_build_opts {
+    int32_t weight_dtype;    /* GIFT_WEIGHT_*; default F32                    */
+    int32_t reserved[7];     /* must be zero                                  */
+} gift_build_opts;
+
+/* One filter term alpha * A~_sigma^power (Eq. 15-16). */
+typedef struct gift_term {
+    float sigma;   /* self-loop weight, finite and > 0              */
+    int32_t power; /* k >= 1, <= 64                                 */
+    double alpha;  /* coefficient                                   */
+} gift_term;
+
+typedef struct gift_filter_spec {
+    int32_t num_terms;              /* 1 .. GIFT_MAX_TERMS                      */
+    gift_term term[GIFT_MAX_TERMS];
+    int32_t norm;                   /* GIFT_NORM_SYM (paper) or GIFT_NORM_RW    */
+    int32_t reimpose_fixed;         /* 1: fixed rows of the output := input     */
+    int32_t compensated;            /* 1: compensated FP32 sums on long rows    */
+    int32_t schedule;               /* 0: autotuned; else a fixed kernel choice */
+} gift_filter_spec;
+
+typedef struct gift_graph_desc {
+    int32_t num_cells;
+    int32_t num_nets;
+    int64_t num_pins;
+    int64_t nnz;            /* stored off-diagonal entries (both halves)       */
+    int64_t raw_pairs;      /* ordered pin pairs before duplicates are summed  */
+    int32_t weight_dtype;
+    int32_t max_row_nnz;
+    int64_t device_bytes;   /* device memory the graph owns                    */
+    const int64_t *row_ptr; /* device pointers owned by the graph              */
+    const int32_t *col;
+    const void *val;        /* weight_dtype elements                           */
+    const double *degree;   /* d_i = sum_j A_ij over the stored weights (FP64) */
+} gift_graph_desc;
+
+typedef struct gift_kernel_stat {
+    char name[48];
+    int64_t launches;
+    double total_ms;        /* sum of CUDA-event durations of the launches     */
+    double alg_bytes;       /* algorithmic (compulsory) bytes of the launches  */
+} gift_kernel_stat;
+
+/* ---- context -------------------------------------------------------------
+ * gift_ctx_create: binds to CUDA device `device` (made current on the calling
+ * thread), sets up the stream-ordered allocator.  *out receives the handle. */
+GIFT_API gift_status gift_ctx_create(int32_t device, gift_ctx **out);
+GIFT_API void gift_ctx_destroy(gift_ctx *ctx);
+
+/* Per-kernel CUDA-event timing of every launch the library makes (off by
+ * default).  gift_ctx_kernel_stats copies up to `max` records and returns the
+ * number of kernels seen; gift_ctx_reset_stats clears them. */
+GIFT_API gift_status gift_ctx_set_profiling(gift_ctx *ctx, int32_t enable);
+GIFT_API int32_t gift_ctx_kernel_stats(gift_ctx *ctx, gift_kernel_stat *out, int32_t max);
+GIFT_API void gift_ctx_reset_stats(gift_ctx *ctx);
+
+/* Fault injection for tests: the `n`-th device allocation from now (1 = the
+ * next one) fails as if the device were out of memory; 0 disables. */
+GIFT_API void gift_ctx_debug_fail_alloc(gift_ctx *ctx, int32_t n);
+
+/* Paper defaults: terms {sigma 2, k 2, 0.1}, {4, 2, 0.7}, {4, 4, 0.2} (Eq. 15
+ * with the Sec. 4.1 coefficients), symmetric normalisation, fixed cells kept. */
+GIFT_API void gift_filter_spec_default(gift_filter_spec *spec);
+GIFT_API void gift_build_opts_default(gift_build_opts *opts);
+
+/* ---- graph ----------------------------------------------------------------
+ * gift_build_graph: clique expansion of every net with M >= 2 pins (weight
+ * 2/M on each ordered pair of its pins on distinct cells; pairs repeated
+ * across nets are summed in increasing net order in FP64, then rounded once
+ * to weight_dtype), CSR with sorted columns and no diagonal, degrees
+ * d_i = sum_j A_ij in FP64 over the stored weights.  Copies the netlist into
+ * the graph (for gift_hpwl).  Synchronises `stream` (sizes are data-dependent).
+ * Errors: GIFT_ERR_INVALID (bad netlist), GIFT_ERR_OOM, GIFT_ERR_CUDA. */
+GIFT_API gift_status gift_build_graph(gift_ctx *ctx, const gift_netlist *netlist, const gift_build_opts *opts,
+                             gift_graph **out, void *stream);
+GIFT_API gift_status gift_graph_info(const gift_graph *graph, gift_graph_desc *info);
+/* Host copies for parity checks: row_ptr [N+1], col [nnz], val [nnz] (stored
+ * weights widened exactly to FP64), degree [N].  Any pointer may be NULL. */
+GIFT_API gift_status gift_graph_export(const gift_graph *graph, int64_t *row_ptr, int32_t *col, double *val,
+                              double *degree);
+/* Synchronises the device, then releases the graph. */
+GIFT_API void gift_graph_free(gift_graph *graph);
+/* Stream-ordered release: the caller guarantees every use of the graph was
+ * queued on `stream` (or completed) before this call. */
+GIFT_API void gift_graph_free_async(gift_graph *graph, void *stream);
+
+/* ---- filter ---------------------------------------------------------------
+ * g_out = sum_t alpha_t A~_{sigma_t}^{k_t} g_in (Eq. 15-16), every column of
+ * the [N][S][2] signal filtered independently; with spec->reimpose_fixed the
+ * fixed rows of g_out equal those of g_in.  spec NULL = paper defaults.
+ * g_in and g_out (same memory kind, `mem`) must not overlap; device pointers
+ * must be 8-byte aligned.  FP32 signal and accumulation.
+ * Errors: GIFT_ERR_INVALID, GIFT_ERR_OOM, GIFT_ERR_CUDA. */
+GIFT_API gift_status gift_filter(gift_ctx *ctx, const gift_graph *graph, const gift_filter_spec *spec,
+                        const float *g_in, int32_t num_signals, float *g_out, int32_t mem, void *stream);
+
+/* ---- HPWL -----------------------------------------------------------------
+ * out[s] = sum over nets of (max x - min x) + (max y - min y) of signal s, pin
+ * locations = cell locations of xy [N][S][2] (memory `mem`).  Per-net extents
+ * exact, sum in FP64 in a fixed order.  `out` is a HOST array of S doubles;
+ * the call synchronises `stream`. */
+GIFT_API gift_status gift_hpwl(gift_ctx *ctx, const gift_graph *graph, const float *xy, int32_t num_signals,
+                      double *out, int32_t mem, void *stream);
+
+/* Message for the last non-OK status returned on this thread ("" if none). */
+GIFT_API const char *gift_last_error(void);
+
+#ifdef __cplusplus
+}
+#endif
+#endif /* GIFT_H */

@@ -1,0 +1,608 @@
+// build_graph.cu -- netlist -> clique graph (CSR) on the device.
+//
+// Clique net model (Sec. 3.2.3, Algorithm 1) with the weight rule stated after
+// Eq. 4 (w = 2/M for an M-pin net): every ordered pair of pin slots (p, q) of a
+// net with M >= 2, p != q, on distinct cells i != j adds w to A_ij; a cell pair
+// shared by several nets sums (one w_ij per pair, Sec. 2.1).
+//
+// Row-centric pipeline, no global sort of pairs:
+//   count    per pin of a net with M >= 2: incidences and raw pair count of its cell
+//   scan     -> incidence offsets and raw-pair offsets per cell
+//   scatter  cell -> list of its nets (one entry per pin)
+//   rows     per cell: generate (neighbour, net) keys from its nets, sort them in
+//            shared memory, sum duplicates in FP64 in increasing net order
+//            (warp per row; a block per row for long rows; global-memory keys
+//            for rows beyond the shared-memory capacity)
+//   scan     unique counts -> row_ptr
+//   compact  round each sum once to the storage type, write col/val, and
+//            d_i = sum_j A_ij in FP64 over the stored weights in column order.
+#include <algorithm>
+
+#include "internal.cuh"
+#include "scan.cuh"
+
+namespace gift {
+namespace {
+
+constexpr int kWarpCap = 512;      // keys per warp in the warp tier
+constexpr int kRowsWarps = 8;      // warps per block in the warp tier
+constexpr int kBlockCap = 16384;   // keys in shared memory in the block tier (128 KiB)
+constexpr int kBlockThreads = 512;
+constexpr uint64_t kPadKey = ~0ull;
+
+__device__ __forceinline__ uint64_t make_key(int32_t cell, int32_t net) {
+    return (static_cast<uint64_t>(static_cast<uint32_t>(cell)) << 32) | static_cast<uint32_t>(net);
+}
+__device__ __forceinline__ int32_t key_cell(uint64_t k) { return static_cast<int32_t>(k >> 32); }
+__device__ __forceinline__ int32_t key_net(uint64_t k) { return static_cast<int32_t>(k & 0xffffffffu); }
+
+// ------------------------------------------------------------------ validate
+__global__ void k_validate(int32_t E, int64_t P, int32_t N, const int64_t *__restrict__ net_ptr,
+                           const int32_t *__restrict__ pin_cell, int *__restrict__ flag) {
+    int64_t tid = blockIdx.x * (int64_t)blockDim.x + threadIdx.x;
+    int64_t stride = (int64_t)gridDim.x * blockDim.x;
+    int bad = 0;
+    if (tid == 0 && net_ptr[0] != 0) bad |= 4;
+    for (int64_t e = tid; e < E; e += stride)
+        if (net_ptr[e + 1] < net_ptr[e]) bad |= 1;
+    for (int64_t p = tid; p < P; p += stride) {
+        int32_t c = pin_cell[p];
+        if (c < 0 || c >= N) bad |= 2;
+    }
+    if (bad) atomicOr(flag, bad);
+}
+
+// Each lane owns one net of the warp's 32; nets above 32 pins are then done by
+// the whole warp, one after another.
+template <class F>
+__device__ __forceinline__ void for_each_pin_of_nets(int32_t E, const int64_t *__restrict__ net_ptr, F &&f) {
+    const int lane = threadIdx.x & 31;
+    const int64_t warp = (blockIdx.x * (int64_t)blockDim.x + threadIdx.x) >> 5;
+    const int64_t nwarps = ((int64_t)gridDim.x * blockDim.x) >> 5;
+    for (int64_t base = warp * 32; base < E; base += nwarps * 32) {
+        int64_t e = base + lane;
+        int64_t b = 0, m = 0;
+        if (e < E) {
+            b = net_ptr[e];
+            m = net_ptr[e + 1] - b;
+        }
+        if (m >= 2 && m <= 32)
+            for (int64_t t = 0; t < m; ++t) f((int32_t)e, b, m, t);
+        unsigned big = __ballot_sync(0xffffffffu, m > 32);
+        while (big) {
+            int src = __ffs(big) - 1;
+            big &= big - 1;
+            int64_t bb = __shfl_sync(0xffffffffu, b, src);
+            int64_t mb = __shfl_sync(0xffffffffu, m, src);
+            int32_t eb = (int32_t)(base + src);
+            for (int64_t t = lane; t < mb; t += 32) f(eb, bb, mb, t);
+        }
+    }
+}
+
+// ------------------------------------------------------------------ count
+__global__ void k_net_weights(int32_t E, const int64_t *__restrict__ net_ptr, double *__restrict__ wnet) {
+    for (int64_t e = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; e < E; e += (int64_t)gridDim.x * blockDim.x) {
+        int64_t m = net_ptr[e + 1] - net_ptr[e];
+        wnet[e] = m >= 2 ? 2.0 / (double)m : 0.0;  // weight rule after Eq. 4
+    }
+}
+
+__global__ void k_count(int32_t E, const int64_t *__restrict__ net_ptr, const int32_t *__restrict__ pin_cell,
+                        int32_t *__restrict__ cnt, unsigned long long *__restrict__ rawlen) {
+    for_each_pin_of_nets(E, net_ptr, [&](int32_t, int64_t b, int64_t m, int64_t t) {
+        int32_t c = pin_cell[b + t];
+        atomicAdd(&cnt[c], 1);
+        atomicAdd(&rawlen[c], (unsigned long long)(m - 1));
+    });
+}
+
+__global__ void k_max_rawlen(int32_t N, const int64_t *__restrict__ raw_ptr, unsigned long long *__restrict__ mx) {
+    unsigned long long best = 0;
+    for (int64_t i = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; i < N; i += (int64_t)gridDim.x * blockDim.x)
+        best = max(best, (unsigned long long)(raw_ptr[i + 1] - raw_ptr[i]));
+    for (int o = 16; o; o >>= 1) best = max(best, __shfl_xor_sync(0xffffffffu, best, o));
+    if ((threadIdx.x & 31) == 0 && best) atomicMax(mx, best);
+}
+
+// ------------------------------------------------------------------ scatter
+__global__ void k_scatter(int32_t E, const int64_t *__restrict__ net_ptr, const int32_t *__restrict__ pin_cell,
+                          const int64_t *__restrict__ inc_ptr, int32_t *__restrict__ fill,
+                          int32_t *__restrict__ inc_net) {
+    for_each_pin_of_nets(E, net_ptr, [&](int32_t e, int64_t b, int64_t, int64_t t) {
+        int32_t c = pin_cell[b + t];
+        int64_t pos = inc_ptr[c] + atomicAdd(&fill[c], 1);
+        inc_net[pos] = e;
+    });
+}
+
+// ------------------------------------------------------------------ rows, warp tier
+// One warp per row with at most kWarpCap raw entries.  Rows above that are
+// appended to big_rows for the block tiers.
+__global__ void __launch_bounds__(kRowsWarps * 32)
+k_rows_warp(int32_t N, const int64_t *__restrict__ inc_ptr, const int32_t *__restrict__ inc_net,
+            const int64_t *__restrict__ net_ptr, const int32_t *__restrict__ pin_cell,
+            const double *__restrict__ wnet, const int64_t *__restrict__ raw_ptr, int32_t *__restrict__ s_col,
+            double *__restrict__ s_val, int32_t *__restrict__ ucount, int32_t *__restrict__ big_rows,
+            int32_t *__restrict__ big_count) {
+    __shared__ uint64_t keys_all[kRowsWarps][kWarpCap];
+    __shared__ int32_t ofs_all[kRowsWarps][33];
+    __shared__ int32_t net_all[kRowsWarps][32];
+    __shared__ int64_t base_all[kRowsWarps][32];
+    __shared__ int32_t cnt_all[kRowsWarps];
+    const int lane = threadIdx.x & 31;
+    const int w = threadIdx.x >> 5;
+    uint64_t *keys = keys_all[w];
+    int32_t *ofs = ofs_all[w];
+    const unsigned full = 0xffffffffu;
+    const int64_t gw = (blockIdx.x * (int64_t)blockDim.x + threadIdx.x) >> 5;
+    const int64_t nw = ((int64_t)gridDim.x * blockDim.x) >> 5;
+
+    for (int64_t row = gw; row < N; row += nw) {
+        const int64_t rbase = raw_ptr[row];
+        const int64_t rawlen = raw_ptr[row + 1] - rbase;
+        if (rawlen > kWarpCap) {
+            if (lane == 0) big_rows[atomicAdd(big_count, 1)] = (int32_t)row;
+            continue;
+        }
+        if (rawlen == 0) {
+            if (lane == 0) ucount[row] = 0;
+            continue;
+        }
+        if (lane == 0) cnt_all[w] = 0;
+        __syncwarp();
+        const int64_t ib = inc_ptr[row];
+        const int64_t ninc = inc_ptr[row + 1] - ib;
+        for (int64_t k0 = 0; k0 < ninc; k0 += 32) {
+            int32_t e = 0;
+            int64_t nb = 0;
+            int32_t m = 0;
+            if (k0 + lane < ninc) {
+                e = inc_net[ib + k0 + lane];
+                nb = net_ptr[e];
+                m = (int32_t)(net_ptr[e + 1] - nb);
+            }
+            int32_t incl = m;
+#pragma unroll
+            for (int o = 1; o < 32; o <<= 1) {
+                int32_t t = __shfl_up_sync(full, incl, o);
+                if (lane >= o) incl += t;
+            }
+            const int32_t total = __shfl_sync(full, incl, 31);
+            ofs[lane] = incl - m;
+            net_all[w][lane] = e;
+            base_all[w][lane] = nb;
+            __syncwarp();
+            for (int32_t f = lane; f < total; f += 32) {
+                int lo = 0, hi = 31;  // last incidence whose offset <= f
+                while (lo < hi) {
+                    int mid = (lo + hi + 1) >> 1;
+                    if (ofs[mid] <= f) lo = mid;
+                    else hi = mid - 1;
+                }
+                int32_t q = pin_cell[base_all[w][lo] + (f - ofs[lo])];
+                if (q != (int32_t)row) {
+                    int pos = atomicAdd(&cnt_all[w], 1);
+                    keys[pos] = make_key(q, net_all[w][lo]);
+                }
+            }
+            __syncwarp();
+        }
+        const int n = cnt_all[w];
+        int p2 = 2;
+        while (p2 < n) p2 <<= 1;
+        for (int t = n + lane; t < p2; t += 32) keys[t] = kPadKey;
+        __syncwarp();
+        // bitonic sort of keys[0, p2): by neighbour cell, then by net
+        for (int size = 2; size <= p2; size <<= 1) {
+            for (int stride = size >> 1; stride > 0; stride >>= 1) {
+                for (int t = lane; t < (p2 >> 1); t += 32) {
+                    int i = 2 * t - (t & (stride - 1));
+                    int j = i + stride;
+                    bool up = (i & size) == 0;
+                    uint64_t a = keys[i], b = keys[j];
+                    if ((a > b) == up) {
+                        keys[i] = b;
+                        keys[j] = a;
+                    }
+                }
+                __syncwarp();
+            }
+        }
+        // run heads -> unique index; each head sums its run in sorted (net) order
+        int uniq = 0;
+        for (int base = 0; base < n; base += 32) {
+            int t = base + lane;
+            bool head = false;
+            int32_t c = 0;
+            if (t < n) {
+                c = key_cell(keys[t]);
+                head = (t == 0) || key_cell(keys[t - 1]) != c;
+            }
+            unsigned hm = __ballot_sync(full, head);
+            if (head) {
+                int u = uniq + __popc(hm & ((1u << lane) - 1));
+                double s = 0.0;
+                for (int r = t; r < n && key_cell(keys[r]) == c; ++r) s += wnet[key_net(keys[r])];
+                s_col[rbase + u] = c;
+                s_val[rbase + u] = s;
+            }
+            uniq += __popc(hm);
+        }
+        if (lane == 0) ucount[row] = uniq;
+        __syncwarp();
+    }
+}
+
+// ------------------------------------------------------------------ rows, block tiers
+// One block per long row.  GLOBAL_KEYS: keys live in a per-block global scratch
+// of `gcap` entries (rows beyond the shared-memory capacity); else in dynamic
+// shared memory of kBlockCap entries.
+template <bool GLOBAL_KEYS>
+__global__ void __launch_bounds__(kBlockThreads)
+k_rows_block(const int64_t *__restrict__ inc_ptr, const int32_t *__restrict__ inc_net,
+             const int64_t *__restrict__ net_ptr, const int32_t *__restrict__ pin_cell,
+             const double *__restrict__ wnet, const int64_t *__restrict__ raw_ptr, int32_t *__restrict__ s_col,
+             double *__restrict__ s_val, int32_t *__restrict__ ucount, const int32_t *__restrict__ big_rows,
+             const int32_t *__restrict__ big_count, uint64_t *__restrict__ gkeys, int64_t gcap) {
+    extern __shared__ uint64_t smem_keys[];
+    __shared__ int s_cnt;
+    __shared__ int s_warp[kBlockThreads / 32];
+    __shared__ int s_uniq;
+    uint64_t *keys = GLOBAL_KEYS ? gkeys + blockIdx.x * gcap : smem_keys;
+    const int tid = threadIdx.x, lane = tid & 31, wid = tid >> 5;
+    const int nrows = *big_count;
+    for (int r = blockIdx.x; r < nrows; r += gridDim.x) {
+        const int32_t row = big_rows[r];
+        const int64_t rbase = raw_ptr[row];
+        const int64_t rawlen = raw_ptr[row + 1] - rbase;
+        if (GLOBAL_KEYS != (rawlen > kBlockCap)) continue;
+        if (tid == 0) {
+            s_cnt = 0;
+            s_uniq = 0;
+        }
+        __syncthreads();
+        const int64_t ib = inc_ptr[row], ie = inc_ptr[row + 1];
+        for (int64_t k = ib; k < ie; ++k) {
+            int32_t e = inc_net[k];
+            int64_t nb = net_ptr[e], m = net_ptr[e + 1] - nb;
+            for (int64_t t = tid; t < m; t += blockDim.x) {
+                int32_t q = pin_cell[nb + t];
+                if (q != row) keys[atomicAdd(&s_cnt, 1)] = make_key(q, e);
+            }
+        }
+        __syncthreads();
+        const int n = s_cnt;
+        int64_t p2 = 2;
+        while (p2 < n) p2 <<= 1;
+        for (int64_t t = n + tid; t < p2; t += blockDim.x) keys[t] = kPadKey;
+        __syncthreads();
+        for (int64_t size = 2; size <= p2; size <<= 1) {
+            for (int64_t stride = size >> 1; stride > 0; stride >>= 1) {
+                for (int64_t t = tid; t < (p2 >> 1); t += blockDim.x) {
+                    int64_t i = 2 * t - (t & (stride - 1));
+                    int64_t j = i + stride;
+                    bool up = (i & size) == 0;
+                    uint64_t a = keys[i], b = keys[j];
+                    if ((a > b) == up) {
+                        keys[i] = b;
+                        keys[j] = a;
+                    }
+                }
+                __syncthreads();
+            }
+        }
+        for (int base = 0; base < n; base += blockDim.x) {
+            int t = base + tid;
+            bool head = false;
+            int32_t c = 0;
+            if (t < n) {
+                c = key_cell(keys[t]);
+                head = (t == 0) || key_cell(keys[t - 1]) != c;
+            }
+            unsigned hm = __ballot_sync(0xffffffffu, head);
+            if (lane == 0) s_warp[wid] = __popc(hm);
+            __syncthreads();
+            int before = s_uniq;
+            for (int q = 0; q < wid; ++q) before += s_warp[q];
+            if (head) {
+                int u = before + __popc(hm & ((1u << lane) - 1));
+                double s = 0.0;
+                for (int rr = t; rr < n && key_cell(keys[rr]) == c; ++rr) s += wnet[key_net(keys[rr])];
+                s_col[rbase + u] = c;
+                s_val[rbase + u] = s;
+            }
+            __syncthreads();
+            if (tid == 0) {
+                int add = 0;
+                for (int q = 0; q < (int)(blockDim.x >> 5); ++q) add += s_warp[q];
+                s_uniq += add;
+            }
+            __syncthreads();
+        }
+        if (tid == 0) ucount[row] = s_uniq;
+        __syncthreads();
+    }
+}
+
+// ------------------------------------------------------------------ storage rounding
+// Round-to-nearest-even of an FP64 value to a format with `keep` explicit
+// significand bits and minimum normal exponent `emin`, on the bit pattern.
+__device__ __forceinline__ double rne_to(double v, int keep, int emin) {
+    unsigned long long b = (unsigned long long)__double_as_longlong(v);
+    int ex = (int)((b >> 52) & 0x7ff);
+    if (ex == 0 || ex == 0x7ff) return v;  // zero / FP64 subnormal (tiny) / inf / nan
+    if (ex - 1023 < emin) {                // subnormal in the target: fixed quantum
+        double q = ldexp(1.0, emin - keep);
+        return rint(v / q) * q;
+    }
+    const int drop = 52 - keep;
+    const unsigned long long mask = (1ull << drop) - 1, half = 1ull << (drop - 1);
+    unsigned long long rem = b & mask, kept = b & ~mask;
+    if (rem > half || (rem == half && ((kept >> drop) & 1ull))) kept += 1ull << drop;
+    return __longlong_as_double((long long)kept);
+}
+
+template <typename WT>
+struct Store;
+template <>
+struct Store<float> {
+    __device__ static float put(double v) { return __double2float_rn(rne_to(v, 23, -126)); }
+    __device__ static double get(float w) { return (double)w; }
+};
+template <>
+struct Store<__nv_bfloat16> {
+    __device__ static __nv_bfloat16 put(double v) {
+        float f = __double2float_rn(rne_to(v, 7, -126));  // exact in binary32
+        return __ushort_as_bfloat16((unsigned short)(__float_as_uint(f) >> 16));
+    }
+    __device__ static double get(__nv_bfloat16 w) { return (double)__bfloat162float(w); }
+};
+template <>
+struct Store<__half> {
+    __device__ static __half put(double v) { return __float2half_rn(__double2float_rn(rne_to(v, 10, -14))); }
+    __device__ static double get(__half w) { return (double)__half2float(w); }
+};
+
+// One thread per row: copy the row's sums, rounded once, and sum the stored
+// weights in column order in FP64 (the degree, Sec. 2.1).
+template <typename WT>
+__global__ void k_compact(int32_t N, const int64_t *__restrict__ raw_ptr, const int64_t *__restrict__ row_ptr,
+                          const int32_t *__restrict__ s_col, const double *__restrict__ s_val,
+                          int32_t *__restrict__ col, WT *__restrict__ val, double *__restrict__ degree,
+                          int32_t *__restrict__ max_row) {
+    int best = 0;
+    for (int64_t i = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; i < N; i += (int64_t)gridDim.x * blockDim.x) {
+        const int64_t src = raw_ptr[i], dst = row_ptr[i], n = row_ptr[i + 1] - dst;
+        double d = 0.0;
+        for (int64_t t = 0; t < n; ++t) {
+            WT w = Store<WT>::put(s_val[src + t]);
+            col[dst + t] = s_col[src + t];
+            val[dst + t] = w;
+            d += Store<WT>::get(w);
+        }
+        degree[i] = d;
+        best = max(best, (int)n);
+    }
+    for (int o = 16; o; o >>= 1) best = max(best, __shfl_xor_sync(0xffffffffu, best, o));
+    if ((threadIdx.x & 31) == 0 && best) atomicMax(max_row, best);
+}
+
+int grid_for(gift_ctx *ctx, int64_t work, int threads, int per_sm = 8) {
+    int64_t g = ceil_div(std::max<int64_t>(work, 1), threads);
+    return (int)std::max<int64_t>(1, std::min<int64_t>(g, (int64_t)ctx->num_sms * per_sm));
+}
+
+template <class T>
+void h2d_or_d2d(T *dst, const T *src, size_t count, int mem, cudaStream_t st) {
+    if (count == 0) return;
+    GIFT_CUDA(cudaMemcpyAsync(dst, src, sizeof(T) * count,
+                              mem == GIFT_MEM_HOST ? cudaMemcpyHostToDevice : cudaMemcpyDeviceToDevice, st));
+}
+
+}  // namespace
+
+void release_graph(gift_graph *g, cudaStream_t st) {
+    void *ptrs[] = {g->row_ptr, g->col, g->val, g->degree, g->net_ptr, g->pin_cell, g->is_fixed};
+    for (void *p : ptrs) dev_free(p, st);
+    for (auto &s : g->scales) {
+        if (s.pre && s.pre != s.post) dev_free(s.pre, st);
+        dev_free(s.post, st);
+    }
+    g->scales.clear();
+}
+
+void build_graph_impl(gift_ctx *ctx, const gift_netlist *nl, const gift_build_opts *opts, gift_graph **out,
+                      cudaStream_t st) {
+    gift_build_opts def;
+    if (!opts) {
+        gift_build_opts_default(&def);
+        opts = &def;
+    }
+    GIFT_REQUIRE(opts->weight_dtype == GIFT_WEIGHT_F32 || opts->weight_dtype == GIFT_WEIGHT_BF16 ||
+                     opts->weight_dtype == GIFT_WEIGHT_F16,
+                 "gift_build_graph: unknown weight_dtype");
+    for (int r : opts->reserved) GIFT_REQUIRE(r == 0, "gift_build_graph: reserved option fields must be zero");
+    GIFT_REQUIRE(nl->num_cells > 0, "gift_build_graph: num_cells must be > 0");
+    GIFT_REQUIRE(nl->num_nets >= 0, "gift_build_graph: num_nets must be >= 0");
+    GIFT_REQUIRE(nl->mem == GIFT_MEM_HOST || nl->mem == GIFT_MEM_DEVICE, "gift_build_graph: bad mem kind");
+    GIFT_REQUIRE(nl->net_ptr != nullptr, "gift_build_graph: net_ptr is NULL");
+    const int32_t N = nl->num_cells, E = nl->num_nets;
+
+    int64_t ends[2] = {0, 0};
+    if (nl->mem == GIFT_MEM_HOST) {
+        ends[0] = nl->net_ptr[0];
+        ends[1] = nl->net_ptr[E];
+    } else {
+        GIFT_CUDA(cudaMemcpyAsync(&ends[0], nl->net_ptr, sizeof(int64_t), cudaMemcpyDeviceToHost, st));
+        GIFT_CUDA(cudaMemcpyAsync(&ends[1], nl->net_ptr + E, sizeof(int64_t), cudaMemcpyDeviceToHost, st));
+        GIFT_CUDA(cudaStreamSynchronize(st));
+    }
+    GIFT_REQUIRE(ends[0] == 0, "gift_build_graph: net_ptr[0] must be 0");
+    GIFT_REQUIRE(ends[1] >= 0, "gift_build_graph: net_ptr[E] must be >= 0");
+    const int64_t P = ends[1];
+    GIFT_REQUIRE(P == 0 || nl->pin_cell != nullptr, "gift_build_graph: pin_cell is NULL");
+
+    struct GraphOwner {
+        gift_graph *g;
+        cudaStream_t st;
+        ~GraphOwner() {
+            if (g) {
+                release_graph(g, st);
+                delete g;
+            }
+        }
+    } owner{new gift_graph(), st};
+    gift_graph *g = owner.g;
+    g->ctx = ctx;
+    g->n = N;
+    g->num_nets = E;
+    g->num_pins = P;
+    g->weight_dtype = opts->weight_dtype;
+    g->home = st;
+
+    g->net_ptr = (int64_t *)dev_alloc(ctx, sizeof(int64_t) * (E + 1), st);
+    g->pin_cell = (int32_t *)dev_alloc(ctx, sizeof(int32_t) * std::max<int64_t>(P, 1), st);
+    g->is_fixed = (uint8_t *)dev_alloc(ctx, N, st);
+    h2d_or_d2d(g->net_ptr, nl->net_ptr, E + 1, nl->mem, st);
+    h2d_or_d2d(g->pin_cell, nl->pin_cell, P, nl->mem, st);
+    if (nl->is_fixed) h2d_or_d2d(g->is_fixed, nl->is_fixed, N, nl->mem, st);
+    else GIFT_CUDA(cudaMemsetAsync(g->is_fixed, 0, N, st));
+
+    // ---- validate on the device
+    DevBuf flag(ctx, sizeof(int) * 4, st);
+    GIFT_CUDA(cudaMemsetAsync(flag.p, 0, sizeof(int) * 4, st));
+    {
+        LaunchTimer lt(ctx, st, "build.validate", 8.0 * (E + 1) + 4.0 * P);
+        k_validate<<<grid_for(ctx, std::max<int64_t>(E, P), 256), 256, 0, st>>>(E, P, N, g->net_ptr, g->pin_cell,
+                                                                              flag.as<int>());
+        check_launch("k_validate");
+    }
+    int hflag = 0;
+    GIFT_CUDA(cudaMemcpyAsync(&hflag, flag.p, sizeof(int), cudaMemcpyDeviceToHost, st));
+    GIFT_CUDA(cudaStreamSynchronize(st));
+    GIFT_REQUIRE(!(hflag & 4), "gift_build_graph: net_ptr[0] must be 0");
+    GIFT_REQUIRE(!(hflag & 1), "gift_build_graph: net_ptr decreases");
+    GIFT_REQUIRE(!(hflag & 2), "gift_build_graph: pin_cell id out of [0, num_cells)");
+
+    // ---- count incidences and raw pairs per cell
+    DevBuf wnet(ctx, sizeof(double) * std::max(E, 1), st);
+    DevBuf cnt(ctx, sizeof(int32_t) * N, st);
+    DevBuf rawlen(ctx, sizeof(int64_t) * N, st);
+    GIFT_CUDA(cudaMemsetAsync(cnt.p, 0, sizeof(int32_t) * N, st));
+    GIFT_CUDA(cudaMemsetAsync(rawlen.p, 0, sizeof(int64_t) * N, st));
+    if (E > 0) {
+        LaunchTimer lt(ctx, st, "build.count", 16.0 * (E + 1) + 4.0 * P + 12.0 * N);
+        k_net_weights<<<grid_for(ctx, E, 256), 256, 0, st>>>(E, g->net_ptr, wnet.as<double>());
+        k_count<<<grid_for(ctx, E, 256), 256, 0, st>>>(E, g->net_ptr, g->pin_cell, cnt.as<int32_t>(),
+                                                         rawlen.as<unsigned long long>());
+        check_launch("k_count");
+    }
+    DevBuf inc_ptr(ctx, sizeof(int64_t) * (N + 1), st);
+    DevBuf raw_ptr(ctx, sizeof(int64_t) * (N + 1), st);
+    {
+        LaunchTimer lt(ctx, st, "build.scan", 4.0 * N + 8.0 * N + 16.0 * (N + 1));
+        exclusive_scan(ctx, cnt.as<int32_t>(), inc_ptr.as<int64_t>(), N, st);
+        exclusive_scan(ctx, rawlen.as<int64_t>(), raw_ptr.as<int64_t>(), N, st);
+    }
+    GIFT_CUDA(cudaMemsetAsync(flag.p, 0, sizeof(int) * 4, st));
+    k_max_rawlen<<<grid_for(ctx, N, 256), 256, 0, st>>>(N, raw_ptr.as<int64_t>(), (unsigned long long *)flag.p);
+    check_launch("k_max_rawlen");
+    int64_t totals[3] = {0, 0, 0};
+    GIFT_CUDA(cudaMemcpyAsync(&totals[0], inc_ptr.as<int64_t>() + N, sizeof(int64_t), cudaMemcpyDeviceToHost, st));
+    GIFT_CUDA(cudaMemcpyAsync(&totals[1], raw_ptr.as<int64_t>() + N, sizeof(int64_t), cudaMemcpyDeviceToHost, st));
+    GIFT_CUDA(cudaMemcpyAsync(&totals[2], flag.p, sizeof(int64_t), cudaMemcpyDeviceToHost, st));
+    GIFT_CUDA(cudaStreamSynchronize(st));
+    const int64_t ninc = totals[0], nraw = totals[1], maxraw = totals[2];
+    g->raw_pairs = nraw;
+
+    // ---- scatter nets to cells
+    DevBuf inc_net(ctx, sizeof(int32_t) * std::max<int64_t>(ninc, 1), st);
+    DevBuf fill(ctx, sizeof(int32_t) * N, st);
+    GIFT_CUDA(cudaMemsetAsync(fill.p, 0, sizeof(int32_t) * N, st));
+    if (E > 0 && ninc > 0) {
+        LaunchTimer lt(ctx, st, "build.scatter", 8.0 * (E + 1) + 4.0 * P + 8.0 * N + 4.0 * ninc + 4.0 * N);
+        k_scatter<<<grid_for(ctx, E, 256), 256, 0, st>>>(E, g->net_ptr, g->pin_cell, inc_ptr.as<int64_t>(),
+                                                           fill.as<int32_t>(), inc_net.as<int32_t>());
+        check_launch("k_scatter");
+    }
+
+    // ---- per-row expansion, sort, duplicate sums
+    DevBuf s_col(ctx, sizeof(int32_t) * std::max<int64_t>(nraw, 1), st);
+    DevBuf s_val(ctx, sizeof(double) * std::max<int64_t>(nraw, 1), st);
+    DevBuf ucount(ctx, sizeof(int32_t) * N, st);
+    DevBuf big_rows(ctx, sizeof(int32_t) * N, st);
+    DevBuf big_count(ctx, sizeof(int32_t), st);
+    GIFT_CUDA(cudaMemsetAsync(big_count.p, 0, sizeof(int32_t), st));
+    {
+        LaunchTimer lt(ctx, st, "build.rows",
+                       16.0 * N + 4.0 * ninc + 16.0 * ninc + 12.0 * nraw + 12.0 * nraw + 4.0 * N);
+        k_rows_warp<<<grid_for(ctx, (int64_t)N * 32, kRowsWarps * 32, 6), kRowsWarps * 32, 0, st>>>(
+            N, inc_ptr.as<int64_t>(), inc_net.as<int32_t>(), g->net_ptr, g->pin_cell, wnet.as<double>(),
+            raw_ptr.as<int64_t>(), s_col.as<int32_t>(), s_val.as<double>(), ucount.as<int32_t>(),
+            big_rows.as<int32_t>(), big_count.as<int32_t>());
+        check_launch("k_rows_warp");
+    }
+    if (maxraw > kWarpCap) {
+        LaunchTimer lt(ctx, st, "build.rows_block", 0.0);
+        const size_t smem = sizeof(uint64_t) * kBlockCap;
+        GIFT_CUDA(cudaFuncSetAttribute(k_rows_block<false>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem));
+        k_rows_block<false><<<ctx->num_sms, kBlockThreads, smem, st>>>(
+            inc_ptr.as<int64_t>(), inc_net.as<int32_t>(), g->net_ptr, g->pin_cell, wnet.as<double>(),
+            raw_ptr.as<int64_t>(), s_col.as<int32_t>(), s_val.as<double>(), ucount.as<int32_t>(),
+            big_rows.as<int32_t>(), big_count.as<int32_t>(), nullptr, 0);
+        check_launch("k_rows_block");
+    }
+    DevBuf gkeys;
+    if (maxraw > kBlockCap) {
+        LaunchTimer lt(ctx, st, "build.rows_global", 0.0);
+        int64_t cap = 2;
+        while (cap < maxraw) cap <<= 1;
+        const int blocks = ctx->num_sms;
+        gkeys = DevBuf(ctx, sizeof(uint64_t) * cap * blocks, st);
+        k_rows_block<true><<<blocks, kBlockThreads, 0, st>>>(
+            inc_ptr.as<int64_t>(), inc_net.as<int32_t>(), g->net_ptr, g->pin_cell, wnet.as<double>(),
+            raw_ptr.as<int64_t>(), s_col.as<int32_t>(), s_val.as<double>(), ucount.as<int32_t>(),
+            big_rows.as<int32_t>(), big_count.as<int32_t>(), gkeys.as<uint64_t>(), cap);
+        check_launch("k_rows_block<global>");
+    }
+
+    // ---- row_ptr, compaction with storage rounding, degrees
+    g->row_ptr = (int64_t *)dev_alloc(ctx, sizeof(int64_t) * (N + 1), st);
+    exclusive_scan(ctx, ucount.as<int32_t>(), g->row_ptr, N, st);
+    int64_t nnz = 0;
+    GIFT_CUDA(cudaMemcpyAsync(&nnz, g->row_ptr + N, sizeof(int64_t), cudaMemcpyDeviceToHost, st));
+    GIFT_CUDA(cudaStreamSynchronize(st));
+    g->nnz = nnz;
+    const size_t wsz = g->weight_dtype == GIFT_WEIGHT_F32 ? 4 : 2;
+    g->col = (int32_t *)dev_alloc(ctx, sizeof(int32_t) * std::max<int64_t>(nnz, 1), st);
+    g->val = dev_alloc(ctx, wsz * std::max<int64_t>(nnz, 1), st);
+    g->degree = (double *)dev_alloc(ctx, sizeof(double) * N, st);
+    GIFT_CUDA(cudaMemsetAsync(flag.p, 0, sizeof(int) * 4, st));
+    {
+        LaunchTimer lt(ctx, st, "build.compact", 16.0 * N + 12.0 * nnz + (4.0 + wsz) * nnz + 8.0 * N);
+        const int grid = grid_for(ctx, N, 256);
+        if (g->weight_dtype == GIFT_WEIGHT_F32)
+            k_compact<float><<<grid, 256, 0, st>>>(N, raw_ptr.as<int64_t>(), g->row_ptr, s_col.as<int32_t>(),
+                                                    s_val.as<double>(), g->col, (float *)g->val, g->degree,
+                                                    flag.as<int32_t>());
+        else if (g->weight_dtype == GIFT_WEIGHT_BF16)
+            k_compact<__nv_bfloat16><<<grid, 256, 0, st>>>(N, raw_ptr.as<int64_t>(), g->row_ptr, s_col.as<int32_t>(),
+                                                            s_val.as<double>(), g->col, (__nv_bfloat16 *)g->val,
+                                                            g->degree, flag.as<int32_t>());
+        else
+            k_compact<__half><<<grid, 256, 0, st>>>(N, raw_ptr.as<int64_t>(), g->row_ptr, s_col.as<int32_t>(),
+                                                     s_val.as<double>(), g->col, (__half *)g->val, g->degree,
+                                                     flag.as<int32_t>());
+        check_launch("k_compact");
+    }
+    int32_t maxrow = 0;
+    GIFT_CUDA(cudaMemcpyAsync(&maxrow, flag.p, sizeof(int32_t), cudaMemcpyDeviceToHost, st));
+    GIFT_CUDA(cudaStreamSynchronize(st));
+    g->max_row_nnz = maxrow;
+    g->device_bytes = (int64_t)(sizeof(int64_t) * (N + 1) + (4 + wsz) * nnz + 8 * N + 8 * (E + 1) + 4 * P + N);
+    *out = g;
+    owner.g = nullptr;
+}
+
+}  // namespace gift

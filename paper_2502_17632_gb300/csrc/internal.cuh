@@ -1,0 +1,190 @@
+// internal.cuh -- shared internals of libgift: context, graph handle, errors,
+// stream-ordered allocation with fault injection, per-kernel event timing.
+#pragma once
+
+#include <cuda_runtime.h>
+#include <cuda_bf16.h>
+#include <cuda_fp16.h>
+
+#include <cstdint>
+#include <cstdio>
+#include <map>
+#include <mutex>
+#include <string>
+#include <vector>
+
+#include "gift.h"
+
+namespace gift {
+
+// ---------------------------------------------------------------- errors
+void set_error(const std::string &msg);
+void clear_error();
+
+struct Failure {
+    gift_status st;
+    std::string msg;
+};
+
+#define GIFT_CUDA(call)                                                                        \
+    do {                                                                                       \
+        cudaError_t e_ = (call);                                                               \
+        if (e_ != cudaSuccess) {                                                               \
+            throw ::gift::Failure{e_ == cudaErrorMemoryAllocation ? GIFT_ERR_OOM : GIFT_ERR_CUDA, \
+                                  std::string(#call) + ": " + cudaGetErrorString(e_)};         \
+        }                                                                                      \
+    } while (0)
+
+#define GIFT_REQUIRE(cond, msg)                                                                \
+    do {                                                                                       \
+        if (!(cond)) throw ::gift::Failure{GIFT_ERR_INVALID, (msg)};                           \
+    } while (0)
+
+// Runs body, turning a Failure into a status (and the thread's message).
+template <class F>
+gift_status guarded(F &&body) {
+    try {
+        body();
+        clear_error();
+        return GIFT_OK;
+    } catch (const Failure &f) {
+        set_error(f.msg);
+        return f.st;
+    } catch (const std::bad_alloc &) {
+        set_error("host allocation failed");
+        return GIFT_ERR_OOM;
+    } catch (...) {
+        set_error("unexpected internal error");
+        return GIFT_ERR_CUDA;
+    }
+}
+
+// ---------------------------------------------------------------- context
+struct KernelRecord {
+    int64_t launches = 0;
+    double total_ms = 0;
+    double alg_bytes = 0;
+};
+
+struct PendingTiming {
+    std::string name;
+    cudaEvent_t start, stop;
+    double alg_bytes;
+};
+
+}  // namespace gift
+
+struct gift_ctx {
+    int device = 0;
+    int num_sms = 0;
+    int l2_bytes = 0;
+    int max_smem_optin = 0;
+    cudaMemPool_t pool = nullptr;
+    // fault injection: countdown to a failing allocation (0 = off)
+    int fail_alloc_in = 0;
+    // profiling
+    bool profiling = false;
+    std::mutex prof_mu;
+    std::map<std::string, gift::KernelRecord> records;
+    std::vector<gift::PendingTiming> pending;
+    std::vector<cudaEvent_t> event_pool;
+};
+
+namespace gift {
+
+// Stream-ordered device allocation (pool kept warm); honours fault injection.
+void *dev_alloc(gift_ctx *ctx, size_t bytes, cudaStream_t st);
+void dev_free(void *p, cudaStream_t st);
+
+// RAII owner of a stream-ordered allocation.
+struct DevBuf {
+    void *p = nullptr;
+    cudaStream_t st = nullptr;
+    DevBuf() = default;
+    DevBuf(gift_ctx *ctx, size_t bytes, cudaStream_t s) : st(s) { p = dev_alloc(ctx, bytes, s); }
+    DevBuf(const DevBuf &) = delete;
+    DevBuf &operator=(const DevBuf &) = delete;
+    DevBuf(DevBuf &&o) noexcept : p(o.p), st(o.st) { o.p = nullptr; }
+    DevBuf &operator=(DevBuf &&o) noexcept {
+        reset();
+        p = o.p;
+        st = o.st;
+        o.p = nullptr;
+        return *this;
+    }
+    ~DevBuf() { reset(); }
+    void reset() {
+        if (p) dev_free(p, st);
+        p = nullptr;
+    }
+    void *release() {
+        void *q = p;
+        p = nullptr;
+        return q;
+    }
+    template <class T>
+    T *as() const { return static_cast<T *>(p); }
+};
+
+// Launch timing: wraps one kernel launch in events when profiling is on.
+struct LaunchTimer {
+    gift_ctx *ctx;
+    cudaStream_t st;
+    const char *name;
+    double bytes;
+    cudaEvent_t a = nullptr, b = nullptr;
+    LaunchTimer(gift_ctx *c, cudaStream_t s, const char *n, double alg_bytes);
+    ~LaunchTimer();
+};
+// Folds completed timings into the records (called after a synchronisation).
+void collect_timings(gift_ctx *ctx, bool wait);
+
+void check_launch(const char *what);
+
+inline int64_t ceil_div(int64_t a, int64_t b) { return (a + b - 1) / b; }
+
+}  // namespace gift
+
+// ---------------------------------------------------------------- graph
+struct gift_graph {
+    gift_ctx *ctx = nullptr;
+    int32_t n = 0;            // cells
+    int32_t num_nets = 0;
+    int64_t num_pins = 0;
+    int64_t nnz = 0;
+    int64_t raw_pairs = 0;
+    int32_t weight_dtype = GIFT_WEIGHT_F32;
+    int32_t max_row_nnz = 0;
+    int64_t device_bytes = 0;
+    cudaStream_t home = nullptr;  // stream of the build
+    // device arrays owned by the graph
+    int64_t *row_ptr = nullptr;   // [n+1]
+    int32_t *col = nullptr;       // [nnz]
+    void *val = nullptr;          // [nnz] weight_dtype
+    double *degree = nullptr;     // [n]
+    int64_t *net_ptr = nullptr;   // [E+1]
+    int32_t *pin_cell = nullptr;  // [P]
+    uint8_t *is_fixed = nullptr;  // [n] (all zero if none were given)
+    // cache of per-(sigma, norm) scale vectors: pre / post, FP32 [n]
+    struct Scale {
+        float sigma;
+        int norm;
+        float *pre;   // nullptr for the random-walk form (pre = 1)
+        float *post;
+    };
+    std::vector<Scale> scales;
+    std::mutex mu;
+};
+
+namespace gift {
+// build_graph.cu
+void build_graph_impl(gift_ctx *ctx, const gift_netlist *nl, const gift_build_opts *opts, gift_graph **out,
+                      cudaStream_t st);
+void release_graph(gift_graph *g, cudaStream_t st);
+// filter.cu
+void filter_impl(gift_ctx *ctx, const gift_graph *g, const gift_filter_spec *spec, const float *g_in, int S,
+                 float *g_out, int mem, cudaStream_t st);
+gift_graph::Scale graph_scale(gift_ctx *ctx, gift_graph *g, float sigma, int norm, cudaStream_t st);
+// hpwl.cu
+void hpwl_impl(gift_ctx *ctx, const gift_graph *g, const float *xy, int S, double *out, int mem, cudaStream_t st);
+}  // namespace gift

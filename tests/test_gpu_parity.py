@@ -1,0 +1,287 @@
+"""CUDA path vs the FP64 oracle, element by element, through the C ABI.
+
+Bars: graph structure (row_ptr, col) bit-exact; stored weights and FP64
+degrees bit-exact (same FP64 summation order, same round-to-nearest-even);
+filter output within 1e-5 relative per coordinate in FP32 arithmetic; fixed
+rows bit-exact; HPWL within 1e-12 relative (FP64 sums in another order).
+"""
+import numpy as np
+import pytest
+
+import oracle
+from paper_2502_17632_gb300 import gift, synth
+
+torch = pytest.importorskip("torch")
+pytestmark = pytest.mark.gpu
+
+RTOL = 1e-5  # FP32 filter vs FP64 oracle, per coordinate
+
+
+@pytest.fixture(scope="module")
+def ctx():
+    c = gift.gift_ctx_create(0)
+    yield c
+    gift.gift_ctx_destroy(c)
+
+
+def dev(a):
+    return torch.from_numpy(np.ascontiguousarray(a)).cuda()
+
+
+def build(ctx, nl, wd="f32", device=True):
+    if device:
+        return gift.gift_build_graph(ctx, nl.num_cells, dev(nl.net_ptr), dev(nl.pin_cell), dev(nl.is_fixed),
+                                     gift.WEIGHT[wd])
+    return gift.gift_build_graph(ctx, nl.num_cells, nl.net_ptr, nl.pin_cell, nl.is_fixed, gift.WEIGHT[wd])
+
+
+def rel_err(got, ref, g):
+    floor = 1e-3 * max(float(np.abs(g).max()), 1e-30)
+    return np.abs(got.astype(np.float64) - ref) / np.maximum(np.abs(ref), floor)
+
+
+def star_netlist(num_cells, hub_nets, pins_per_net, seed, extra_nets=0):
+    """Cell 0 sits in `hub_nets` nets of `pins_per_net` pins (a long row) plus random small nets."""
+    nets = []
+    for e in range(hub_nets):
+        u = synth.u64(seed, 77, np.arange(e * 1000, e * 1000 + 4 * pins_per_net, dtype=np.uint64))
+        cells = [0]
+        for v in (u % np.uint64(num_cells - 1) + np.uint64(1)).astype(np.int64):
+            if v not in cells:
+                cells.append(int(v))
+            if len(cells) == pins_per_net:
+                break
+        nets.append(cells)
+    small = synth.random_small(seed, num_cells, extra_nets, 6, min_pins=2) if extra_nets else None
+    if small is not None:
+        for e in range(small.num_nets):
+            nets.append(list(small.pin_cell[small.net_ptr[e]:small.net_ptr[e + 1]]))
+    net_ptr = np.concatenate([[0], np.cumsum([len(n) for n in nets])]).astype(np.int64)
+    pin_cell = np.array([c for n in nets for c in n], dtype=np.int32)
+    fx = np.zeros(num_cells, dtype=np.uint8)
+    fx[-3:] = 1
+    return synth.Netlist(num_cells, len(nets), net_ptr, pin_cell, fx, np.zeros((num_cells, 2), np.float32))
+
+
+def netlists():
+    out = {
+        "plain-10k": synth.workload("plain-10k")[0],
+        "repeat-cells": synth.random_small(3, 300, 420, 9, num_fixed=10, allow_repeat=True),
+        "tiny": synth.random_small(4, 7, 5, 4, num_fixed=1),
+        "no-nets": synth.random_small(5, 9, 0, 3),
+        "single-pin-nets": synth.random_small(6, 20, 30, 1),
+        "one-cell": synth.Netlist(1, 2, np.array([0, 1, 1], dtype=np.int64), np.array([0], dtype=np.int32),
+                                  np.zeros(1, np.uint8), np.zeros((1, 2), np.float32)),
+        "block-tier-row": star_netlist(1000, 20, 40, 8, extra_nets=300),
+        "global-tier-row": star_netlist(3000, 400, 45, 9, extra_nets=500),
+    }
+    return out
+
+
+NETLISTS = netlists()
+
+
+@pytest.mark.parametrize("wd", ["f32", "bf16", "f16"])
+@pytest.mark.parametrize("name", sorted(NETLISTS))
+def test_graph_bit_exact(ctx, name, wd):
+    nl = NETLISTS[name]
+    h = build(ctx, nl, wd)
+    try:
+        rp, col, val, deg = gift.gift_graph_export(h)
+        info = gift.gift_graph_info(h)
+    finally:
+        gift.gift_graph_free(h)
+    og = oracle.stored(oracle.build_graph(nl.num_cells, nl.net_ptr, nl.pin_cell), wd)
+    np.testing.assert_array_equal(rp, og.row_ptr)
+    np.testing.assert_array_equal(col, og.col)
+    np.testing.assert_array_equal(val, og.val)
+    np.testing.assert_array_equal(deg, oracle.degrees(og))
+    assert info.nnz == og.nnz
+    m = nl.net_ptr[1:] - nl.net_ptr[:-1]
+    assert info.raw_pairs == int((m * (m - 1))[m >= 2].sum())
+    if og.nnz:
+        assert info.max_row_nnz == int((og.row_ptr[1:] - og.row_ptr[:-1]).max())
+
+
+def test_host_and_device_inputs_agree(ctx):
+    nl = NETLISTS["repeat-cells"]
+    a, b = build(ctx, nl, device=True), build(ctx, nl, device=False)
+    try:
+        for x, y in zip(gift.gift_graph_export(a), gift.gift_graph_export(b)):
+            np.testing.assert_array_equal(x, y)
+    finally:
+        gift.gift_graph_free(a)
+        gift.gift_graph_free(b)
+
+
+def run_filter(ctx, nl, g, wd="f32", spec=None, device=True):
+    h = build(ctx, nl, wd)
+    try:
+        if device:
+            gi = dev(g)
+            go = torch.empty_like(gi)
+            gift.gift_filter(ctx, h, gi, go, spec)
+            torch.cuda.synchronize()
+            return go.cpu().numpy()
+        out = np.empty_like(g)
+        gift.gift_filter(ctx, h, g, out, spec)
+        return out
+    finally:
+        gift.gift_graph_free(h)
+
+
+@pytest.mark.parametrize("name", sorted(NETLISTS))
+@pytest.mark.parametrize("S", [1, 2, 3, 8])
+def test_filter_parity(ctx, name, S):
+    nl = NETLISTS[name]
+    g = synth.make_signals(nl, S, 1234 + S)
+    got = run_filter(ctx, nl, g)
+    _, _, ref = oracle.run(nl, g.reshape(nl.num_cells, -1))
+    ref = ref.reshape(g.shape)
+    assert rel_err(got, ref, g).max() <= RTOL
+    fx = nl.is_fixed.astype(bool)
+    np.testing.assert_array_equal(got[fx], g[fx])
+
+
+@pytest.mark.parametrize("S", [1, 2, 4, 5, 8, 9, 16])
+@pytest.mark.parametrize("schedule", [0, 1, 2, 4, 8])
+def test_filter_shapes_and_schedules(ctx, S, schedule):
+    nl = NETLISTS["repeat-cells"]
+    g = synth.make_signals(nl, S, 99 + S)
+    spec = gift.make_spec(schedule=schedule)
+    got = run_filter(ctx, nl, g, spec=spec)
+    _, _, ref = oracle.run(nl, g.reshape(nl.num_cells, -1))
+    assert rel_err(got, ref.reshape(g.shape), g).max() <= RTOL
+
+
+@pytest.mark.parametrize("terms,norm,reimpose", [
+    (((2.0, 2, 0.1), (4.0, 2, 0.7), (4.0, 4, 0.2)), "rw", True),
+    (((2.0, 2, 0.1), (4.0, 2, 0.7), (4.0, 4, 0.2)), "sym", False),
+    (((1.0, 1, 0.25), (3.0, 3, 0.5), (0.5, 2, 0.25)), "sym", True),   # three chains at once
+    (((4.0, 4, 1.0),), "sym", True),
+    (((2.0, 1, 0.3), (2.0, 3, 0.7)), "sym", True),
+    (((1.0, 1, 0.2), (2.0, 2, 0.2), (3.0, 3, 0.2), (4.0, 4, 0.2), (5.0, 5, 0.2)), "sym", True),
+])
+def test_filter_general_specs(ctx, terms, norm, reimpose):
+    nl = NETLISTS["plain-10k"]
+    g = synth.make_signals(nl, 2, 5)
+    spec = gift.make_spec(terms=terms, norm=gift.GIFT_NORM_RW if norm == "rw" else gift.GIFT_NORM_SYM,
+                          reimpose=reimpose)
+    got = run_filter(ctx, nl, g, spec=spec)
+    _, _, ref = oracle.run(nl, g.reshape(nl.num_cells, -1), terms=terms, norm=norm, reimpose=reimpose)
+    assert rel_err(got, ref.reshape(g.shape), g).max() <= RTOL
+
+
+@pytest.mark.parametrize("wd", ["bf16", "f16"])
+def test_reduced_precision_weights(ctx, wd):
+    """Against the oracle on the same rounded weights: the FP32 bar.  Against the
+    exact-weight oracle: the weight-rounding error, bounded as measured."""
+    nl = NETLISTS["plain-10k"]
+    g = synth.make_signals(nl, 4, 17)
+    got = run_filter(ctx, nl, g, wd=wd)
+    _, _, ref_q = oracle.run(nl, g.reshape(nl.num_cells, -1), fmt=wd)
+    assert rel_err(got, ref_q.reshape(g.shape), g).max() <= RTOL
+    _, _, ref = oracle.run(nl, g.reshape(nl.num_cells, -1))
+    bound = {"bf16": 5e-3, "f16": 1e-3}[wd]
+    assert rel_err(got, ref.reshape(g.shape), g).max() <= bound
+
+
+def test_host_memory_filter_matches_device(ctx):
+    nl = NETLISTS["plain-10k"]
+    g = synth.make_signals(nl, 3, 3)
+    np.testing.assert_array_equal(run_filter(ctx, nl, g, device=True), run_filter(ctx, nl, g, device=False))
+
+
+def test_filter_is_deterministic(ctx):
+    nl = NETLISTS["repeat-cells"]
+    g = synth.make_signals(nl, 8, 1)
+    np.testing.assert_array_equal(run_filter(ctx, nl, g), run_filter(ctx, nl, g))
+
+
+@pytest.mark.parametrize("name", ["plain-10k", "repeat-cells", "global-tier-row", "single-pin-nets"])
+def test_hpwl_parity(ctx, name):
+    nl = NETLISTS[name]
+    g = synth.make_signals(nl, 3, 8)
+    h = build(ctx, nl)
+    try:
+        got_d = gift.gift_hpwl(ctx, h, dev(g))
+        got_h = gift.gift_hpwl(ctx, h, g)
+    finally:
+        gift.gift_graph_free(h)
+    ref = oracle.hpwl(nl.net_ptr, nl.pin_cell, g)
+    np.testing.assert_allclose(got_d, ref, rtol=1e-12)
+    np.testing.assert_array_equal(got_d, got_h)
+
+
+# ---------------------------------------------------------------- errors
+def test_invalid_netlists_rejected(ctx):
+    nl = NETLISTS["tiny"]
+    bad_pin = nl.pin_cell.copy()
+    bad_pin[0] = nl.num_cells
+    with pytest.raises(gift.GiftError) as e:
+        gift.gift_build_graph(ctx, nl.num_cells, dev(nl.net_ptr), dev(bad_pin), None)
+    assert e.value.status == gift.GIFT_ERR_INVALID
+    bad_pin[0] = -1
+    with pytest.raises(gift.GiftError) as e:
+        gift.gift_build_graph(ctx, nl.num_cells, nl.net_ptr, bad_pin, None)
+    assert e.value.status == gift.GIFT_ERR_INVALID
+    bad_ptr = nl.net_ptr.copy()
+    bad_ptr[1] = bad_ptr[2] + 1  # net 1 ends before it starts
+    with pytest.raises(gift.GiftError) as e:
+        gift.gift_build_graph(ctx, nl.num_cells, dev(bad_ptr), dev(nl.pin_cell), None)
+    assert e.value.status == gift.GIFT_ERR_INVALID
+    with pytest.raises(gift.GiftError) as e:
+        gift.gift_build_graph(ctx, 0, nl.net_ptr, nl.pin_cell, None)
+    assert e.value.status == gift.GIFT_ERR_INVALID
+
+
+def test_invalid_filter_args(ctx):
+    nl = NETLISTS["tiny"]
+    h = build(ctx, nl)
+    g = dev(synth.make_signals(nl, 2, 1))
+    out = torch.empty_like(g)
+    try:
+        for terms in [((0.0, 2, 1.0),), ((2.0, 0, 1.0),), ((2.0, 65, 1.0),), ((float("nan"), 1, 1.0),)]:
+            with pytest.raises(gift.GiftError) as e:
+                gift.gift_filter(ctx, h, g, out, gift.make_spec(terms=terms))
+            assert e.value.status == gift.GIFT_ERR_INVALID
+        spec = gift.make_spec()
+        spec.num_terms = 9
+        with pytest.raises(gift.GiftError):
+            gift.gift_filter(ctx, h, g, out, spec)
+        with pytest.raises(gift.GiftError):
+            gift.gift_filter(ctx, h, g, g, None)  # overlap
+        with pytest.raises(gift.GiftError):
+            gift.gift_filter(ctx, h, g, out, None, num_signals=0)
+    finally:
+        gift.gift_graph_free(h)
+
+
+def test_injected_oom_leaves_library_usable(ctx):
+    nl = NETLISTS["repeat-cells"]
+    g = synth.make_signals(nl, 2, 4)
+    for n in (1, 3, 6, 9):
+        gift.gift_ctx_debug_fail_alloc(ctx, n)
+        try:
+            h = build(ctx, nl)
+        except gift.GiftError as e:
+            assert e.status == gift.GIFT_ERR_OOM
+            continue
+        finally:
+            gift.gift_ctx_debug_fail_alloc(ctx, 0)
+        gift.gift_graph_free(h)
+    h = build(ctx, nl)
+    try:
+        gift.gift_ctx_debug_fail_alloc(ctx, 2)
+        gi = dev(g)
+        go = torch.empty_like(gi)
+        with pytest.raises(gift.GiftError) as e:
+            gift.gift_filter(ctx, h, gi, go)
+        assert e.value.status == gift.GIFT_ERR_OOM
+        gift.gift_ctx_debug_fail_alloc(ctx, 0)
+        gift.gift_filter(ctx, h, gi, go)
+        torch.cuda.synchronize()
+        _, _, ref = oracle.run(nl, g.reshape(nl.num_cells, -1))
+        assert rel_err(go.cpu().numpy(), ref.reshape(g.shape), g).max() <= RTOL
+    finally:
+        gift.gift_graph_free(h)
