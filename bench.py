@@ -1,0 +1,364 @@
+"""Benchmark of the GiFt hot path on GB300.
+
+One step = the whole path over one synthetic netlist already resident in HBM:
+gift_build_graph (clique expansion, CSR, degrees) -> gift_filter (the paper's
+three-term filter, 4 fused passes over the CSR) -> gift_hpwl of the result.
+Metric: GiFt edge-updates/s = 6 * nnz * S per step (every stored nonzero
+applied to every (x, y) signal in each of the filter's 6 products) / step time.
+
+    python bench.py [--gpus N] [--steps K] [--warmup W] [--impl ours|reference]
+                    [--workload large-2.2m] [--weights f32|bf16|f16]
+
+Prints one JSON line (rank 0).  ``--impl reference`` times the FP64 CPU oracle
+on the host cores (a bounded sample of the same workload) for the same metric.
+"""
+from __future__ import annotations
+
+import argparse
+import hashlib
+import json
+import os
+import statistics
+import subprocess
+import sys
+import threading
+import time
+
+import numpy as np
+
+ROOT = os.path.dirname(os.path.abspath(__file__))
+sys.path.insert(0, ROOT)
+
+from paper_2502_17632_gb300 import synth  # noqa: E402
+
+METRIC = "GiFt filter edge-updates/s (6*nnz*signals per filter call; step = graph build + filter + HPWL)"
+UNIT = "edge-updates/s"
+
+
+def parse():
+    p = argparse.ArgumentParser()
+    p.add_argument("--gpus", type=int, default=1)
+    p.add_argument("--steps", type=int, default=10)
+    p.add_argument("--warmup", type=int, default=3)
+    p.add_argument("--impl", default="ours", choices=["ours", "reference"])
+    p.add_argument("--workload", default="large-2.2m", choices=sorted(synth.WORKLOADS))
+    p.add_argument("--weights", default="f32", choices=["f32", "bf16", "f16"])
+    p.add_argument("--scale", type=float, default=1.0, help="shrink the workload (profiling captures only)")
+    p.add_argument("--no-cpu-baseline", action="store_true")
+    p.add_argument("--no-e2e", action="store_true")
+    return p.parse_args()
+
+
+def dist_env():
+    return int(os.environ.get("RANK", 0)), int(os.environ.get("WORLD_SIZE", 1)), int(os.environ.get("LOCAL_RANK", 0))
+
+
+def peaks():
+    try:
+        with open(os.path.join(ROOT, "MEASURED_PEAKS.json")) as f:
+            d = json.load(f)
+        return float(d["hbm_gbs"]), "measured"
+    except Exception:
+        return 6800.0, "fallback"
+
+
+# ----------------------------------------------------------------- clocks
+class ClockSampler:
+    """nvidia-smi samples during the timed region."""
+    Q = ("index,clocks.sm,clocks.max.sm,power.draw,clocks_event_reasons.active,"
+         "clocks_event_reasons.hw_slowdown,clocks_event_reasons.hw_thermal_slowdown,"
+         "clocks_event_reasons.sw_thermal_slowdown,clocks_event_reasons.sw_power_cap")
+
+    def __init__(self, index: int):
+        self.index = index
+        self.proc = None
+        self.lines = []
+
+    def __enter__(self):
+        try:
+            self.proc = subprocess.Popen(["nvidia-smi", "-i", str(self.index), f"--query-gpu={self.Q}",
+                                          "--format=csv,noheader,nounits", "-lms", "200"],
+                                         stdout=subprocess.PIPE, stderr=subprocess.DEVNULL, text=True)
+            self.t = threading.Thread(target=self._read, daemon=True)
+            self.t.start()
+        except Exception:
+            self.proc = None
+        return self
+
+    def _read(self):
+        for line in self.proc.stdout:
+            self.lines.append(line.strip())
+
+    def __exit__(self, *a):
+        if self.proc:
+            self.proc.terminate()
+            try:
+                self.proc.wait(timeout=5)
+            except Exception:
+                self.proc.kill()
+
+    def summary(self):
+        sm, mx, reasons = [], None, set()
+        names = ["hw_slowdown", "hw_thermal_slowdown", "sw_thermal_slowdown", "sw_power_cap"]
+        for ln in self.lines:
+            f = [x.strip() for x in ln.split(",")]
+            if len(f) < 9:
+                continue
+            try:
+                sm.append(float(f[1]))
+                mx = float(f[2])
+            except ValueError:
+                continue
+            for n, v in zip(names, f[5:9]):
+                if v.lower() == "active":
+                    reasons.add(n)
+        if not sm:
+            return {"sm_mhz": None, "sm_max_mhz": None, "reasons": ["unsampled"], "samples": 0}
+        return {"sm_mhz": statistics.median(sm), "sm_max_mhz": mx, "reasons": sorted(reasons), "samples": len(sm)}
+
+
+# ----------------------------------------------------------------- traffic record
+def sweep_source_hash() -> str:
+    h = hashlib.sha256()
+    for f in ("sweep.cuh", "filter.cu"):
+        with open(os.path.join(ROOT, "paper_2502_17632_gb300", "csrc", f), "rb") as fh:
+            h.update(fh.read())
+    return h.hexdigest()[:16]
+
+
+def recorded_traffic(kernel: str, workload: str, weights: str):
+    """DRAM bytes per launch from a committed ncu summary, if it was taken on
+    the current kernel source."""
+    path = os.path.join(ROOT, "profiles", "traffic.json")
+    try:
+        with open(path) as f:
+            rec = json.load(f)
+        r = rec[kernel][f"{workload}/{weights}"]
+        if r.get("source_hash") != sweep_source_hash():
+            return None
+        return r["dram_bytes_per_launch"]
+    except Exception:
+        return None
+
+
+# ----------------------------------------------------------------- oracle (CPU)
+def oracle_sample(nl, g, num_signals: int = 1):
+    """Oracle build + filter on the netlist with `num_signals` signals; returns (seconds, edge-updates)."""
+    import oracle  # CPU baseline leg only
+
+    gs = np.ascontiguousarray(g[:, :num_signals, :]).reshape(nl.num_cells, -1)
+    t0 = time.perf_counter()
+    G = oracle.build_graph(nl.num_cells, nl.net_ptr, nl.pin_cell)
+    d = oracle.degrees(G)
+    out = oracle.gift(G, d, gs, nl.is_fixed)
+    oracle.hpwl(nl.net_ptr, nl.pin_cell, out.reshape(nl.num_cells, num_signals, 2))
+    dt = time.perf_counter() - t0
+    return dt, 6.0 * G.nnz * num_signals
+
+
+def run_reference(args):
+    rank, world, _ = dist_env()
+    if rank != 0:
+        return
+    import oracle
+    oracle.build()
+    scale = 0.1
+    nl, g = synth.workload(args.workload, scale=scale)
+    sample = f"{args.workload} law at {scale:g} scale ({nl.num_cells} cells, {nl.num_nets} nets), 1 of {g.shape[1]} signals; build + filter + HPWL"
+    for _ in range(args.warmup):
+        oracle_sample(nl, g)
+    times, units = [], 0.0
+    for _ in range(args.steps):
+        dt, u = oracle_sample(nl, g)
+        times.append(dt)
+        units += u
+    total = sum(times)
+    v = units / total
+    line = {
+        "impl": "reference", "metric": METRIC, "value": v, "unit": UNIT, "n_gpus": args.gpus, "steps": args.steps,
+        "warmup": args.warmup, "ms_per_step": 1e3 * total / args.steps, "higher_is_better": True,
+        "scaling": "weak", "vs_baseline": None, "dtype": "f64", "data": "synthetic",
+        "config": {"workload": args.workload, "sample": sample},
+        "cpu_baseline": {"value": v, "unit": UNIT, "cores": 1, "kind": "oracle", "sample": sample},
+        "e2e": {"value": v, "unit": UNIT, "h2d_bytes_per_step": 0, "d2h_bytes_per_step": 0},
+    }
+    print(json.dumps(line), flush=True)
+
+
+# ----------------------------------------------------------------- GPU arm
+def run_ours(args):
+    import torch
+    from paper_2502_17632_gb300 import gift
+
+    rank, world, local = dist_env()
+    torch.cuda.set_device(local)
+    if world > 1:
+        import torch.distributed as dist
+        dist.init_process_group("nccl", device_id=torch.device("cuda", local))
+    gift.load()
+    nl, g = synth.workload(args.workload, scale=args.scale)
+    N, S = nl.num_cells, g.shape[1]
+    wd = gift.WEIGHT[args.weights]
+    ctx = gift.gift_ctx_create(local)
+    stream = torch.cuda.current_stream()
+    dev = lambda a: torch.from_numpy(np.ascontiguousarray(a)).cuda()  # noqa: E731
+    d_np, d_pc, d_fx, d_g = dev(nl.net_ptr), dev(nl.pin_cell), dev(nl.is_fixed), dev(g)
+    d_out = torch.empty_like(d_g)
+
+    def step():
+        h = gift.gift_build_graph(ctx, N, d_np, d_pc, d_fx, wd, stream=stream)
+        gift.gift_filter(ctx, h, d_g, d_out, stream=stream)
+        hp = gift.gift_hpwl(ctx, h, d_out, stream=stream)
+        gift.gift_graph_free_async(h, stream)
+        return hp
+
+    # one build for sizes
+    h = gift.gift_build_graph(ctx, N, d_np, d_pc, d_fx, wd, stream=stream)
+    info = gift.gift_graph_info(h)
+    nnz = int(info.nnz)
+    gift.gift_graph_free(h)
+    units = 6.0 * nnz * S
+
+    gift.gift_ctx_set_profiling(ctx, True)
+    for _ in range(args.warmup):
+        step()
+    torch.cuda.synchronize()
+    gift.gift_ctx_reset_stats(ctx)
+
+    def barrier():
+        if world > 1:
+            import torch.distributed as dist
+            dist.barrier()
+        torch.cuda.synchronize()
+
+    barrier()
+    e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+    with ClockSampler(local) as clk:
+        e0.record(stream)
+        for _ in range(args.steps):
+            hp = step()
+        e1.record(stream)
+        torch.cuda.synchronize()
+    barrier()
+    ms = e0.elapsed_time(e1) / args.steps
+    schedule = gift.gift_ctx_last_schedule(ctx)
+    stats = gift.gift_ctx_kernel_stats(ctx)
+    gift.gift_ctx_set_profiling(ctx, False)
+    if world > 1:
+        import torch.distributed as dist
+        t = torch.tensor([ms], device="cuda")
+        dist.all_reduce(t, op=dist.ReduceOp.MAX)
+        ms = float(t.item())
+    value = units * world / (ms * 1e-3)
+    launches = int(sum(r["kernels"] for r in stats.values()))
+
+    # dominant kernel and its roofline
+    peak, peak_src = peaks()
+    top = max(stats.items(), key=lambda kv: kv[1]["total_ms"])
+    tname, trec = top
+    per_launch_ms = trec["total_ms"] / max(trec["launches"], 1)
+    per_launch_bytes = trec["alg_bytes"] / max(trec["launches"], 1)
+    achieved = per_launch_bytes / (per_launch_ms * 1e-3) / 1e9 if per_launch_ms > 0 else 0.0
+    roofline = {"bound": "hbm", "kernel": tname, "achieved": achieved, "peak": peak, "unit": "GB/s",
+                "frac": achieved / peak, "peak_source": f"hbm_gbs, {peak_src}",
+                "alg_bytes_per_launch": per_launch_bytes, "ms_per_launch": per_launch_ms,
+                "traffic": recorded_traffic(tname, args.workload, args.weights)}
+    breakdown = {k: {"ms_per_step": v["total_ms"] / args.steps, "kernels_per_step": v["kernels"] / args.steps,
+                     "alg_GBps": (v["alg_bytes"] / (v["total_ms"] * 1e-3) / 1e9) if v["total_ms"] > 0 else None}
+                 for k, v in sorted(stats.items())}
+
+    # filter alone, per weight type (same graph, resident)
+    filt = {}
+    for wname in ("f32", "bf16", "f16"):
+        h = gift.gift_build_graph(ctx, N, d_np, d_pc, d_fx, gift.WEIGHT[wname], stream=stream)
+        for _ in range(3):
+            gift.gift_filter(ctx, h, d_g, d_out, stream=stream)
+        torch.cuda.synchronize()
+        gift.gift_ctx_reset_stats(ctx)
+        gift.gift_ctx_set_profiling(ctx, True)
+        f0, f1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+        f0.record(stream)
+        reps = max(args.steps, 5)
+        for _ in range(reps):
+            gift.gift_filter(ctx, h, d_g, d_out, stream=stream)
+        f1.record(stream)
+        torch.cuda.synchronize()
+        st = gift.gift_ctx_kernel_stats(ctx)
+        gift.gift_ctx_set_profiling(ctx, False)
+        fms = f0.elapsed_time(f1) / reps
+        sw = st.get("filter.sweep", {"alg_bytes": 0, "total_ms": 1, "launches": 1})
+        filt[wname] = {"ms": fms, "edge_updates_per_s": units / (fms * 1e-3),
+                       "sweep_alg_GBps": sw["alg_bytes"] / (sw["total_ms"] * 1e-3) / 1e9,
+                       "sweep_frac_of_hbm": sw["alg_bytes"] / (sw["total_ms"] * 1e-3) / 1e9 / peak}
+        gift.gift_graph_free(h)
+
+    # end to end through the public API with pinned host buffers
+    e2e = None
+    if not args.no_e2e:
+        pin = lambda a: torch.from_numpy(np.ascontiguousarray(a)).pin_memory().numpy()  # noqa: E731
+        h_np, h_pc, h_fx, h_g = pin(nl.net_ptr), pin(nl.pin_cell), pin(nl.is_fixed), pin(g)
+        h_out = torch.empty(g.shape, dtype=torch.float32).pin_memory().numpy()
+
+        def estep():
+            hh = gift.gift_build_graph(ctx, N, h_np, h_pc, h_fx, wd, stream=stream)
+            gift.gift_filter(ctx, hh, h_g, h_out, stream=stream)
+            r = gift.gift_hpwl(ctx, hh, h_out, stream=stream)
+            gift.gift_graph_free_async(hh, stream)
+            return r
+
+        for _ in range(max(1, args.warmup)):
+            estep()
+        torch.cuda.synchronize()
+        barrier()
+        t0 = time.perf_counter()
+        for _ in range(args.steps):
+            estep()
+        torch.cuda.synchronize()
+        et = (time.perf_counter() - t0) / args.steps
+        if world > 1:
+            import torch.distributed as dist
+            t = torch.tensor([et], device="cuda")
+            dist.all_reduce(t, op=dist.ReduceOp.MAX)
+            et = float(t.item())
+        h2d = nl.net_ptr.nbytes + nl.pin_cell.nbytes + nl.is_fixed.nbytes + g.nbytes + g.nbytes
+        d2h = g.nbytes + 8 * S
+        e2e = {"value": units * world / et, "unit": UNIT, "ms_per_step": et * 1e3,
+               "h2d_bytes_per_step": int(h2d), "d2h_bytes_per_step": int(d2h)}
+
+    cpu = None
+    if rank == 0 and world == 1 and not args.no_cpu_baseline:
+        dt, u = oracle_sample(nl, g, 1)
+        cpu = {"value": u / dt, "unit": UNIT, "cores": 1, "kind": "oracle",
+               "sample": f"{args.workload}: full netlist ({N} cells), build + filter + HPWL of 1 of {S} signals, "
+                         f"FP64 single-threaded C, {dt:.1f} s"}
+    clocks = clk.summary()
+    gift.gift_ctx_destroy(ctx)
+    if rank == 0:
+        line = {
+            "metric": METRIC, "value": value, "unit": UNIT, "n_gpus": world, "steps": args.steps,
+            "warmup": args.warmup, "ms_per_step": ms, "higher_is_better": True, "scaling": "weak",
+            "vs_baseline": None, "dtype": "f32", "data": "synthetic",
+            "config": {"workload": args.workload if args.scale == 1.0 else f"{args.workload} x{args.scale:g}", "cells": N, "nets": nl.num_nets, "pins": nl.num_pins, "nnz": nnz,
+                       "signals": S, "weights": args.weights, "l2": "inputs larger than L2 (netlist + signal "
+                       f"{(nl.net_ptr.nbytes + nl.pin_cell.nbytes + g.nbytes) / 1e6:.0f} MB; >2 GB touched per step)",
+                       "parallelism": f"replicas x{world}", "hpwl_out": float(hp[0]),
+                       "sweep_schedule": schedule},
+            "roofline": roofline, "cpu_baseline": cpu, "e2e": e2e, "gpu_launches": launches * world,
+            "clocks": clocks, "breakdown": breakdown, "filter_only": filt,
+        }
+        print(json.dumps(line), flush=True)
+    if world > 1:
+        import torch.distributed as dist
+        dist.destroy_process_group()
+
+
+def main():
+    args = parse()
+    if args.impl == "reference":
+        run_reference(args)
+    else:
+        run_ours(args)
+
+
+if __name__ == "__main__":
+    main()

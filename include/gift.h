@@ -123,7 +123,8 @@ typedef struct gift_graph_desc {
 
 typedef struct gift_kernel_stat {
     char name[48];
-    int64_t launches;
+    int64_t launches;       /* timed scopes (one call of the stage)            */
+    int64_t kernels;        /* kernel launches inside those scopes             */
     double total_ms;        /* sum of CUDA-event durations of the launches     */
     double alg_bytes;       /* algorithmic (compulsory) bytes of the launches  */
 } gift_kernel_stat;
@@ -140,6 +141,16 @@ GIFT_API void gift_ctx_destroy(gift_ctx *ctx);
 GIFT_API gift_status gift_ctx_set_profiling(gift_ctx *ctx, int32_t enable);
 GIFT_API int32_t gift_ctx_kernel_stats(gift_ctx *ctx, gift_kernel_stat *out, int32_t max);
 GIFT_API void gift_ctx_reset_stats(gift_ctx *ctx);
+
+/* Schedule code the last gift_filter call on this context ran with (the
+ * autotuner's choice when spec->schedule was 0); 0 before the first call. */
+GIFT_API int32_t gift_ctx_last_schedule(gift_ctx *ctx);
+
+/* Synchronises the device and reports whether a kernel of this context hit
+ * the limit of one of its bounded waits since the last check:
+ * GIFT_ERR_TIMEOUT if so (the results of that work are invalid), else GIFT_OK.
+ * gift_hpwl and host-memory gift_filter calls perform the same check. */
+GIFT_API gift_status gift_ctx_device_status(gift_ctx *ctx);
 
 /* Fault injection for tests: the `n`-th device allocation from now (1 = the
  * next one) fails as if the device were out of memory; 0 disables. */

@@ -37,6 +37,15 @@ void check_launch(const char *what) {
     if (e != cudaSuccess) throw Failure{GIFT_ERR_CUDA, std::string(what) + ": " + cudaGetErrorString(e)};
 }
 
+void check_device_error(gift_ctx *ctx) {
+    int32_t code = 0;
+    GIFT_CUDA(cudaMemcpy(&code, ctx->dev_error, sizeof(int32_t), cudaMemcpyDeviceToHost));
+    if (code != 0) {
+        GIFT_CUDA(cudaMemset(ctx->dev_error, 0, sizeof(int32_t)));
+        throw Failure{GIFT_ERR_TIMEOUT, "a bounded device wait ran out (code " + std::to_string(code) + ")"};
+    }
+}
+
 static cudaEvent_t take_event(gift_ctx *ctx) {
     if (!ctx->event_pool.empty()) {
         cudaEvent_t e = ctx->event_pool.back();
@@ -48,8 +57,8 @@ static cudaEvent_t take_event(gift_ctx *ctx) {
     return e;
 }
 
-LaunchTimer::LaunchTimer(gift_ctx *c, cudaStream_t s, const char *n, double alg_bytes)
-    : ctx(c), st(s), name(n), bytes(alg_bytes) {
+LaunchTimer::LaunchTimer(gift_ctx *c, cudaStream_t s, const char *n, double alg_bytes, int k)
+    : ctx(c), st(s), name(n), bytes(alg_bytes), kernels(k) {
     if (!ctx->profiling) return;
     std::lock_guard<std::mutex> lk(ctx->prof_mu);
     a = take_event(ctx);
@@ -61,7 +70,7 @@ LaunchTimer::~LaunchTimer() {
     if (!a) return;
     cudaEventRecord(b, st);
     std::lock_guard<std::mutex> lk(ctx->prof_mu);
-    ctx->pending.push_back(PendingTiming{name, a, b, bytes});
+    ctx->pending.push_back(PendingTiming{name, a, b, bytes, kernels});
 }
 
 void collect_timings(gift_ctx *ctx, bool wait) {
@@ -77,6 +86,7 @@ void collect_timings(gift_ctx *ctx, bool wait) {
         cudaEventElapsedTime(&ms, p.start, p.stop);
         auto &r = ctx->records[p.name];
         r.launches += 1;
+        r.kernels += p.kernels;
         r.total_ms += ms;
         r.alg_bytes += p.alg_bytes;
         ctx->event_pool.push_back(p.start);
@@ -116,7 +126,10 @@ gift_status gift_ctx_create(int32_t device, gift_ctx **out) {
             GIFT_CUDA(cudaMemPoolCreate(&ctx->pool, &props));
             uint64_t keep = std::numeric_limits<uint64_t>::max();
             GIFT_CUDA(cudaMemPoolSetAttribute(ctx->pool, cudaMemPoolAttrReleaseThreshold, &keep));
+            GIFT_CUDA(cudaMalloc(&ctx->dev_error, sizeof(int32_t)));
+            GIFT_CUDA(cudaMemset(ctx->dev_error, 0, sizeof(int32_t)));
         } catch (...) {
+            if (ctx->dev_error) cudaFree(ctx->dev_error);
             if (ctx->pool) cudaMemPoolDestroy(ctx->pool);
             delete ctx;
             throw;
@@ -131,6 +144,7 @@ void gift_ctx_destroy(gift_ctx *ctx) {
     cudaDeviceSynchronize();
     collect_timings(ctx, true);
     for (auto e : ctx->event_pool) cudaEventDestroy(e);
+    if (ctx->dev_error) cudaFree(ctx->dev_error);
     if (ctx->pool) cudaMemPoolDestroy(ctx->pool);
     delete ctx;
 }
@@ -153,6 +167,7 @@ int32_t gift_ctx_kernel_stats(gift_ctx *ctx, gift_kernel_stat *out, int32_t max)
             std::memset(&out[i], 0, sizeof(gift_kernel_stat));
             std::strncpy(out[i].name, kv.first.c_str(), sizeof(out[i].name) - 1);
             out[i].launches = kv.second.launches;
+            out[i].kernels = kv.second.kernels;
             out[i].total_ms = kv.second.total_ms;
             out[i].alg_bytes = kv.second.alg_bytes;
         }
@@ -166,6 +181,17 @@ void gift_ctx_reset_stats(gift_ctx *ctx) {
     collect_timings(ctx, true);
     std::lock_guard<std::mutex> lk(ctx->prof_mu);
     ctx->records.clear();
+}
+
+int32_t gift_ctx_last_schedule(gift_ctx *ctx) { return ctx ? ctx->last_schedule : 0; }
+
+gift_status gift_ctx_device_status(gift_ctx *ctx) {
+    return guarded([&] {
+        GIFT_REQUIRE(ctx != nullptr, "ctx is NULL");
+        GIFT_CUDA(cudaSetDevice(ctx->device));
+        GIFT_CUDA(cudaDeviceSynchronize());
+        check_device_error(ctx);
+    });
 }
 
 void gift_ctx_debug_fail_alloc(gift_ctx *ctx, int32_t n) {

@@ -410,6 +410,7 @@ void release_graph(gift_graph *g, cudaStream_t st) {
         dev_free(s.post, st);
     }
     g->scales.clear();
+    release_sell(g, st);
 }
 
 void build_graph_impl(gift_ctx *ctx, const gift_netlist *nl, const gift_build_opts *opts, gift_graph **out,
@@ -492,7 +493,7 @@ void build_graph_impl(gift_ctx *ctx, const gift_netlist *nl, const gift_build_op
     GIFT_CUDA(cudaMemsetAsync(cnt.p, 0, sizeof(int32_t) * N, st));
     GIFT_CUDA(cudaMemsetAsync(rawlen.p, 0, sizeof(int64_t) * N, st));
     if (E > 0) {
-        LaunchTimer lt(ctx, st, "build.count", 16.0 * (E + 1) + 4.0 * P + 12.0 * N);
+        LaunchTimer lt(ctx, st, "build.count", 16.0 * (E + 1) + 4.0 * P + 12.0 * N, 2);
         k_net_weights<<<grid_for(ctx, E, 256), 256, 0, st>>>(E, g->net_ptr, wnet.as<double>());
         k_count<<<grid_for(ctx, E, 256), 256, 0, st>>>(E, g->net_ptr, g->pin_cell, cnt.as<int32_t>(),
                                                          rawlen.as<unsigned long long>());
@@ -501,13 +502,16 @@ void build_graph_impl(gift_ctx *ctx, const gift_netlist *nl, const gift_build_op
     DevBuf inc_ptr(ctx, sizeof(int64_t) * (N + 1), st);
     DevBuf raw_ptr(ctx, sizeof(int64_t) * (N + 1), st);
     {
-        LaunchTimer lt(ctx, st, "build.scan", 4.0 * N + 8.0 * N + 16.0 * (N + 1));
+        LaunchTimer lt(ctx, st, "build.scan", 4.0 * N + 8.0 * N + 16.0 * (N + 1), 6);
         exclusive_scan(ctx, cnt.as<int32_t>(), inc_ptr.as<int64_t>(), N, st);
         exclusive_scan(ctx, rawlen.as<int64_t>(), raw_ptr.as<int64_t>(), N, st);
     }
     GIFT_CUDA(cudaMemsetAsync(flag.p, 0, sizeof(int) * 4, st));
-    k_max_rawlen<<<grid_for(ctx, N, 256), 256, 0, st>>>(N, raw_ptr.as<int64_t>(), (unsigned long long *)flag.p);
-    check_launch("k_max_rawlen");
+    {
+        LaunchTimer lt(ctx, st, "build.maxraw", 8.0 * (N + 1));
+        k_max_rawlen<<<grid_for(ctx, N, 256), 256, 0, st>>>(N, raw_ptr.as<int64_t>(), (unsigned long long *)flag.p);
+        check_launch("k_max_rawlen");
+    }
     int64_t totals[3] = {0, 0, 0};
     GIFT_CUDA(cudaMemcpyAsync(&totals[0], inc_ptr.as<int64_t>() + N, sizeof(int64_t), cudaMemcpyDeviceToHost, st));
     GIFT_CUDA(cudaMemcpyAsync(&totals[1], raw_ptr.as<int64_t>() + N, sizeof(int64_t), cudaMemcpyDeviceToHost, st));
@@ -569,7 +573,10 @@ void build_graph_impl(gift_ctx *ctx, const gift_netlist *nl, const gift_build_op
 
     // ---- row_ptr, compaction with storage rounding, degrees
     g->row_ptr = (int64_t *)dev_alloc(ctx, sizeof(int64_t) * (N + 1), st);
-    exclusive_scan(ctx, ucount.as<int32_t>(), g->row_ptr, N, st);
+    {
+        LaunchTimer lt(ctx, st, "build.scan", 4.0 * N + 8.0 * (N + 1), 3);
+        exclusive_scan(ctx, ucount.as<int32_t>(), g->row_ptr, N, st);
+    }
     int64_t nnz = 0;
     GIFT_CUDA(cudaMemcpyAsync(&nnz, g->row_ptr + N, sizeof(int64_t), cudaMemcpyDeviceToHost, st));
     GIFT_CUDA(cudaStreamSynchronize(st));

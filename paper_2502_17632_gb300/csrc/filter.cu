@@ -14,12 +14,92 @@
 
 #include "internal.cuh"
 #include "sweep.cuh"
+#include "sweep_mp.cuh"
+#include "sweep_tma.cuh"
+#include "sell.cuh"
 
 namespace gift {
 
 const void *sweep_kernel_f32(int vec, int cw, int ns, int nc);
 const void *sweep_kernel_bf16(int vec, int cw, int ns, int nc);
 const void *sweep_kernel_f16(int vec, int cw, int ns, int nc);
+const void *sweep_mp_kernel_f32(int vec, int w, int nc);
+const void *sweep_mp_kernel_bf16(int vec, int w, int nc);
+const void *sweep_mp_kernel_f16(int vec, int w, int nc);
+
+const void *sweep_tma_kernel_f32(int w, int nx, int nc);
+const void *sweep_tma_kernel_bf16(int w, int nx, int nc);
+const void *sweep_tma_kernel_f16(int w, int nx, int nc);
+int sweep_tma_stage_bytes_f32(int w, int nx, int nc);
+
+const void *sweep_tma_kernel(int weight_dtype, int w, int nx, int nc) {
+    switch (weight_dtype) {
+    case GIFT_WEIGHT_F32: return sweep_tma_kernel_f32(w, nx, nc);
+    case GIFT_WEIGHT_BF16: return sweep_tma_kernel_bf16(w, nx, nc);
+    case GIFT_WEIGHT_F16: return sweep_tma_kernel_f16(w, nx, nc);
+    default: return nullptr;
+    }
+}
+
+// cuTensorMapEncodeTiled, looked up through the runtime (no link to libcuda).
+using EncodeTiledFn = CUresult (*)(CUtensorMap *, CUtensorMapDataType, cuuint32_t, void *, const cuuint64_t *,
+                                   const cuuint64_t *, const cuuint32_t *, const cuuint32_t *, CUtensorMapInterleave,
+                                   CUtensorMapSwizzle, CUtensorMapL2promotion, CUtensorMapFloatOOBfill);
+
+static EncodeTiledFn encode_tiled() {
+    static EncodeTiledFn fn = nullptr;
+    static std::once_flag once;
+    std::call_once(once, [] {
+        void *p = nullptr;
+        cudaDriverEntryPointQueryResult q;
+        if (cudaGetDriverEntryPointByVersion("cuTensorMapEncodeTiled", &p, 12000, cudaEnableDefault, &q) ==
+                cudaSuccess &&
+            q == cudaDriverEntryPointSuccess)
+            fn = reinterpret_cast<EncodeTiledFn>(p);
+        cudaGetLastError();
+    });
+    return fn;
+}
+
+// 2-D map over a row-major [n][K] float signal, box = W columns x 1 row (gather4 rows).
+static CUtensorMap row_map(const float *base, int64_t n, int K, int W) {
+    CUtensorMap m;
+    std::memset(&m, 0, sizeof(m));
+    const cuuint64_t dims[2] = {(cuuint64_t)K, (cuuint64_t)std::max<int64_t>(n, 1)};
+    const cuuint64_t strides[1] = {(cuuint64_t)K * 4};
+    const cuuint32_t box[2] = {(cuuint32_t)W, 1};
+    const cuuint32_t es[2] = {1, 1};
+    EncodeTiledFn fn = encode_tiled();
+    if (!fn) throw Failure{GIFT_ERR_UNSUPPORTED, "gift_filter: tensor-map encoding is unavailable"};
+    CUresult r = fn(&m, CU_TENSOR_MAP_DATA_TYPE_FLOAT32, 2, const_cast<float *>(base), dims, strides, box, es,
+                    CU_TENSOR_MAP_INTERLEAVE_NONE, CU_TENSOR_MAP_SWIZZLE_NONE, CU_TENSOR_MAP_L2_PROMOTION_L2_64B,
+                    CU_TENSOR_MAP_FLOAT_OOB_FILL_NONE);
+    if (r != CUDA_SUCCESS)
+        throw Failure{GIFT_ERR_UNSUPPORTED, "gift_filter: cuTensorMapEncodeTiled failed (" + std::to_string((int)r) + ")"};
+    return m;
+}
+
+const void *sweep_sell_kernel_f32(int vec, int cw, int nx, int nc);
+const void *sweep_sell_kernel_bf16(int vec, int cw, int nx, int nc);
+const void *sweep_sell_kernel_f16(int vec, int cw, int nx, int nc);
+
+const void *sweep_sell_kernel(int weight_dtype, int vec, int cw, int nx, int nc) {
+    switch (weight_dtype) {
+    case GIFT_WEIGHT_F32: return sweep_sell_kernel_f32(vec, cw, nx, nc);
+    case GIFT_WEIGHT_BF16: return sweep_sell_kernel_bf16(vec, cw, nx, nc);
+    case GIFT_WEIGHT_F16: return sweep_sell_kernel_f16(vec, cw, nx, nc);
+    default: return nullptr;
+    }
+}
+
+const void *sweep_mp_kernel(int weight_dtype, int vec, int w, int nc) {
+    switch (weight_dtype) {
+    case GIFT_WEIGHT_F32: return sweep_mp_kernel_f32(vec, w, nc);
+    case GIFT_WEIGHT_BF16: return sweep_mp_kernel_bf16(vec, w, nc);
+    case GIFT_WEIGHT_F16: return sweep_mp_kernel_f16(vec, w, nc);
+    default: return nullptr;
+    }
+}
 
 const void *sweep_kernel(int weight_dtype, int vec, int cw, int ns, int nc) {
     switch (weight_dtype) {
@@ -39,6 +119,11 @@ __global__ void k_scale(int64_t n, const double *__restrict__ d, double sigma, i
         double t = d[i] + sigma;
         out[i] = norm == GIFT_NORM_SYM ? (float)(1.0 / sqrt(t)) : (float)(1.0 / t);
     }
+}
+
+__global__ void k_pack2(int64_t n, const float *__restrict__ a, const float *__restrict__ b, float2 *__restrict__ out) {
+    for (int64_t i = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; i < n; i += (int64_t)gridDim.x * blockDim.x)
+        out[i] = make_float2(a[i], b[i]);
 }
 
 struct Chain {
@@ -89,6 +174,282 @@ gift_graph::Scale graph_scale(gift_ctx *ctx, gift_graph *g, float sigma, int nor
     return g->scales.back();
 }
 
+namespace {
+
+// Kernel shape.  family 0: row groups (k_sweep), a = lanes across the widest
+// slab (slab = vec * a columns), b = lanes per row.  family 1: warp merge-path
+// (k_sweep_mp), a = widest slab in columns.  family 2: TMA gathers
+// (k_sweep_tma), a = slab in columns (8 or 16).
+using Shape = TunedShape;
+
+struct Plan {
+    const gift_graph *g;
+    std::vector<Chain> chains;
+    std::vector<gift_graph::Scale> sc;
+    int Lmax;
+    int K;
+    int vec;
+    int reimpose;
+    const float *din;
+    float *dout;
+    float *acc;
+    std::vector<std::array<float *, 2>> X;
+    int32_t *counters;  // one zeroed tile counter per TMA launch
+    int ncounters;
+    const float2 *gpre2;  // first-sweep gather scales of chains 0 and 1, packed
+};
+
+// Dynamic shared memory the TMA kernel is opted into, once per kernel.
+void tma_set_smem(const void *fn, int bytes) {
+    static std::mutex mu;
+    static std::map<const void *, int> done;
+    std::lock_guard<std::mutex> lk(mu);
+    auto it = done.find(fn);
+    if (it != done.end() && it->second >= bytes) return;
+    GIFT_CUDA(cudaFuncSetAttribute(fn, cudaFuncAttributeMaxDynamicSharedMemorySize, bytes));
+    done[fn] = bytes;
+}
+
+// Launches every sweep of the filter with one kernel shape.
+// Sliced-ELL slab width actually used: the requested width clamped to 1..4
+// vectors, halved until it divides K.
+int sell_width(const Plan &p, int requested) {
+    int w = std::min(std::max(requested, p.vec), 4 * p.vec);
+    while (p.K % w != 0) w >>= 1;
+    return w;
+}
+
+void run_sweeps(gift_ctx *ctx, const Plan &p, Shape shape, cudaStream_t st) {
+    const gift_graph *g = p.g;
+    if (shape.family == 3) shape.a = sell_width(p, shape.a);
+    const int64_t N = g->n;
+    const size_t wsz = g->weight_dtype == GIFT_WEIGHT_F32 ? 4 : 2;
+    const double csr_bytes = (double)g->nnz * (4.0 + wsz) + 8.0 * (N + 1);
+    std::vector<std::pair<int, int>> slabs;  // (c0, width in vectors)
+    for (int c0 = 0; c0 < p.K;) {
+        const int left = (p.K - c0) / p.vec;
+        // merge-path slabs with float2 vectors are instantiated up to 8 columns;
+        // TMA and sliced-ELL slabs are exactly shape.a columns (K is a multiple of it)
+        int cw = shape.family == 0 ? shape.a : std::min(shape.a, p.vec == 2 ? 8 : 16) / p.vec;
+        cw = std::max(cw, 1);
+        while (cw > left) cw >>= 1;
+        GIFT_REQUIRE(cw >= 1, "gift_filter: empty column slab");
+        slabs.push_back({c0, cw});
+        c0 += cw * p.vec;
+    }
+    GIFT_REQUIRE(shape.family != 2 || (p.vec == 4 && p.K % shape.a == 0),
+                 "gift_filter: TMA schedule needs K a multiple of the slab and 16-byte aligned signals");
+    if (shape.family == 3) {
+        const int rps = 32 / (shape.a / p.vec);
+        std::lock_guard<std::mutex> lk(const_cast<gift_graph *>(g)->mu);
+        if (g->sell.rps != rps) {
+            release_sell(const_cast<gift_graph *>(g), st);
+            build_sell(ctx, const_cast<gift_graph *>(g), rps, st);
+        }
+    }
+    int tma_launch = 0;
+    bool contributed = false;
+    for (int k = 1; k <= p.Lmax; ++k) {
+        std::vector<int> active;
+        for (size_t c = 0; c < p.chains.size(); ++c)
+            if (p.chains[c].L >= k) active.push_back((int)c);
+        for (size_t gi = 0; gi < active.size(); gi += 2) {
+            const int nc = (int)std::min<size_t>(2, active.size() - gi);
+            const bool last = (k == p.Lmax) && (gi + 2 >= active.size());
+            bool group_terms = false;
+            for (int q = 0; q < nc; ++q) group_terms |= p.chains[active[gi + q]].has_at[k];
+            for (size_t si = 0; si < slabs.size(); ++si) {
+                const int c0 = slabs[si].first, cw = slabs[si].second, W = cw * p.vec;
+                SweepArgs a;
+                std::memset(&a, 0, sizeof(a));
+                a.row_ptr = g->row_ptr;
+                a.col = g->col;
+                a.val = g->val;
+                a.n_rows = N;
+                a.K = p.K;
+                a.c0 = c0;
+                double bytes = si == 0 ? csr_bytes : 0.0;
+                for (int q = 0; q < nc; ++q) {
+                    const int c = active[gi + q];
+                    const Chain &ch = p.chains[c];
+                    ChainIO &io = a.ch[q];
+                    io.x = k == 1 ? p.din : p.X[c][(k - 1) % 2];
+                    io.gpre = k == 1 ? p.sc[c].pre : nullptr;
+                    io.post = p.sc[c].post;
+                    io.sigma = ch.sigma;
+                    io.alpha = (float)ch.alpha_at[k];
+                    io.has_term = ch.has_at[k] ? 1 : 0;
+                    io.xnext = ch.L > k ? p.X[c][k % 2] : nullptr;
+                    io.pnext = p.sc[c].pre;
+                    bytes += 4.0 * N * W + (si == 0 ? 4.0 * N : 0.0);  // input slab + scale
+                    if (io.xnext) bytes += 4.0 * N * W;
+                }
+                if (last) {
+                    a.acc_in = contributed ? p.acc : nullptr;
+                    a.acc_out = p.dout;
+                    if (p.reimpose) {
+                        a.fixed = g->is_fixed;
+                        a.g_fixed = p.din;
+                        bytes += si == 0 ? (double)N : 0.0;
+                    }
+                } else if (group_terms) {
+                    a.acc_in = contributed ? p.acc : nullptr;
+                    a.acc_out = p.acc;
+                }
+                if (a.acc_in) bytes += 4.0 * N * W;
+                if (a.acc_out) bytes += 4.0 * N * W;
+                if (shape.family == 2) {
+                    const int nx = k == 1 ? 1 : nc;
+                    const void *fn = sweep_tma_kernel(g->weight_dtype, W, nx, nc);
+                    GIFT_REQUIRE(fn != nullptr, "gift_filter: no TMA kernel for this shape");
+                    GIFT_REQUIRE(tma_launch < p.ncounters, "gift_filter: too many TMA launches");
+                    const int stage_bytes = sweep_tma_stage_bytes_f32(W, nx, nc);
+                    const int stages = std::min(16, (ctx->max_smem_optin - 2048) / stage_bytes);
+                    GIFT_REQUIRE(stages >= 2, "gift_filter: not enough shared memory for the TMA pipeline");
+                    const int smem = stages * stage_bytes + 1024;
+                    tma_set_smem(fn, smem);
+                    const CUtensorMap m0 = row_map(a.ch[0].x, N, p.K, W);
+                    const CUtensorMap m1 = nx == 2 ? row_map(a.ch[1].x, N, p.K, W) : m0;
+                    TmaArgs t;
+                    t.tiles = ceil_div(std::max<int64_t>(N, 1), kTmaRows);
+                    t.stages = stages;
+                    t.stage_bytes = stage_bytes;
+                    t.tile_counter = p.counters + tma_launch++;
+                    t.error = ctx->dev_error;
+                    void *params[] = {&a, const_cast<CUtensorMap *>(&m0), const_cast<CUtensorMap *>(&m1), &t};
+                    LaunchTimer lt(ctx, st, "filter.sweep", bytes);
+                    GIFT_CUDA(cudaLaunchKernel(fn, dim3(ctx->num_sms), dim3(32 + kTmaRows * (W / 4)), params, smem, st));
+                    continue;
+                }
+                if (shape.family == 3) {
+                    const int nx = k == 1 ? 1 : nc;
+                    const void *fn = sweep_sell_kernel(g->weight_dtype, p.vec, cw, nx, nc);
+                    GIFT_REQUIRE(fn != nullptr, "gift_filter: no sliced-ELL kernel for this shape");
+                    SellArgs sa;
+                    sa.nslices = g->sell.nslices;
+                    sa.slice_ptr = g->sell.slice_ptr;
+                    sa.perm = g->sell.perm;
+                    sa.col = g->sell.col;
+                    sa.val = g->sell.val;
+                    sa.gpre2 = (k == 1 && nc == 2) ? p.gpre2 : nullptr;
+                    const int64_t want = ceil_div(std::max<int64_t>(sa.nslices, 1), kSellWarps);
+                    const int grid = (int)std::max<int64_t>(
+                        1, std::min<int64_t>(want, (int64_t)ctx->num_sms * occupancy_blocks(fn, kSellThreads)));
+                    void *params[] = {&a, &sa};
+                    LaunchTimer lt(ctx, st, "filter.sweep", bytes);
+                    GIFT_CUDA(cudaLaunchKernel(fn, dim3(grid), dim3(kSellThreads), params, 0, st));
+                    continue;
+                }
+                const void *fn = nullptr;
+                int threads = kSweepThreads;
+                int64_t rows_per_block = 0;
+                if (shape.family == 0) {
+                    const int gl = std::max(shape.b, cw);
+                    fn = sweep_kernel(g->weight_dtype, p.vec, cw, gl, nc);
+                    rows_per_block = (kSweepThreads / 32) * (32 / gl);
+                } else {
+                    fn = sweep_mp_kernel(g->weight_dtype, p.vec, cw * p.vec, nc);
+                    threads = kMpThreads;
+                    rows_per_block = kMpWarps * 32;
+                }
+                GIFT_REQUIRE(fn != nullptr, "gift_filter: no kernel for this shape");
+                const int64_t want = ceil_div(std::max<int64_t>(N, 1), rows_per_block);
+                const int grid = (int)std::max<int64_t>(
+                    1, std::min<int64_t>(want, (int64_t)ctx->num_sms * occupancy_blocks(fn, threads)));
+                void *params[] = {&a};
+                LaunchTimer lt(ctx, st, "filter.sweep", bytes);
+                GIFT_CUDA(cudaLaunchKernel(fn, dim3(grid), dim3(threads), params, 0, st));
+            }
+            if (group_terms && !last) contributed = true;
+        }
+    }
+}
+
+// Shape key of a graph / signal for the autotuner cache.
+std::string tune_key(const gift_graph *g, int vec, int K, const Plan &p) {
+    const double avg = g->n > 0 ? (double)g->nnz / g->n : 0.0;
+    int lg = 0;
+    while ((1ll << (lg + 1)) <= (int64_t)g->n) ++lg;
+    return std::to_string(g->weight_dtype) + "/" + std::to_string(vec) + "/" + std::to_string(K) + "/" +
+           std::to_string(lg) + "/" + std::to_string((int)std::floor(2.0 * std::log2(avg + 1.0))) + "/" +
+           std::to_string(p.chains.size()) + "/" + std::to_string(p.Lmax);
+}
+
+// schedule codes: 4..32 (row groups, widest slab), 100*cw + g (row groups),
+// 1000 + w (merge-path, slab of w columns), 2000 + w (TMA gathers),
+// 3000 + w (sliced ELL)
+Shape shape_from_schedule(int schedule) {
+    if (schedule >= 3000) return Shape{3, schedule - 3000, 1};
+    if (schedule >= 2000) return Shape{2, schedule - 2000, 1};
+    if (schedule >= 1000) return Shape{1, schedule - 1000, 1};
+    if (schedule >= 100) return Shape{0, schedule / 100, schedule % 100};
+    return Shape{0, 4, schedule};
+}
+
+bool valid_shape(Shape s) {
+    if (s.family == 3) return s.a == 2 || s.a == 4 || s.a == 8 || s.a == 16;
+    if (s.family == 2) return s.a == 8 || s.a == 16;
+    if (s.family == 1) return s.a == 2 || s.a == 4 || s.a == 8 || s.a == 16;
+    return (s.a == 1 || s.a == 2 || s.a == 4) && (s.b == 4 || s.b == 8 || s.b == 16 || s.b == 32) && s.b >= s.a;
+}
+
+// Times the whole filter once per candidate shape (after one warm run) and keeps the fastest.
+Shape autotune(gift_ctx *ctx, const Plan &p, cudaStream_t st) {
+    const std::string key = tune_key(p.g, p.vec, p.K, p);
+    {
+        std::lock_guard<std::mutex> lk(ctx->tune_mu);
+        auto it = ctx->tuned.find(key);
+        if (it != ctx->tuned.end()) return it->second;
+    }
+    std::vector<Shape> cands;
+    // TMA gather4 (family 2) measured ~4x slower than LSU gathers for 64-byte
+    // random rows on GB300; it stays available as an explicit schedule only.
+    for (int w : {16, 8, 4, 2})
+        if (sell_width(p, w) == w) cands.push_back(Shape{3, w, 1});
+    for (int w : {16, 8, 4, 2})
+        if (w >= p.vec && w <= std::max(p.K, p.vec) && (p.vec == 4 || w <= 8)) cands.push_back(Shape{1, w, 1});
+    for (int cw : {4, 2, 1})
+        for (int gg : {8, 16})
+            if (gg >= 2 * cw && cw * p.vec <= std::max(p.K, p.vec)) cands.push_back(Shape{0, cw, gg});
+    const bool prof = ctx->profiling;
+    ctx->profiling = false;
+    cudaEvent_t e0, e1;
+    GIFT_CUDA(cudaEventCreate(&e0));
+    GIFT_CUDA(cudaEventCreate(&e1));
+    Shape best = cands.front();
+    float best_ms = 1e30f;
+    try {
+        for (const Shape &s : cands) {
+            GIFT_CUDA(cudaMemsetAsync(p.counters, 0, sizeof(int32_t) * p.ncounters, st));
+            run_sweeps(ctx, p, s, st);
+            GIFT_CUDA(cudaMemsetAsync(p.counters, 0, sizeof(int32_t) * p.ncounters, st));
+            GIFT_CUDA(cudaEventRecord(e0, st));
+            run_sweeps(ctx, p, s, st);
+            GIFT_CUDA(cudaEventRecord(e1, st));
+            GIFT_CUDA(cudaEventSynchronize(e1));
+            float ms = 0.f;
+            GIFT_CUDA(cudaEventElapsedTime(&ms, e0, e1));
+            if (ms < best_ms) {
+                best_ms = ms;
+                best = s;
+            }
+        }
+    } catch (...) {
+        cudaEventDestroy(e0);
+        cudaEventDestroy(e1);
+        ctx->profiling = prof;
+        throw;
+    }
+    cudaEventDestroy(e0);
+    cudaEventDestroy(e1);
+    ctx->profiling = prof;
+    std::lock_guard<std::mutex> lk(ctx->tune_mu);
+    ctx->tuned[key] = best;
+    return best;
+}
+
+}  // namespace
+
 void filter_impl(gift_ctx *ctx, const gift_graph *cg, const gift_filter_spec *spec, const float *g_in, int S,
                  float *g_out, int mem, cudaStream_t st) {
     gift_graph *g = const_cast<gift_graph *>(cg);
@@ -98,153 +459,91 @@ void filter_impl(gift_ctx *ctx, const gift_graph *cg, const gift_filter_spec *sp
     GIFT_REQUIRE(spec->num_terms >= 1 && spec->num_terms <= GIFT_MAX_TERMS, "gift_filter: num_terms out of range");
     GIFT_REQUIRE(spec->norm == GIFT_NORM_SYM || spec->norm == GIFT_NORM_RW, "gift_filter: unknown norm");
     GIFT_REQUIRE(spec->reimpose_fixed == 0 || spec->reimpose_fixed == 1, "gift_filter: reimpose_fixed is 0 or 1");
+    GIFT_REQUIRE(spec->schedule == 0 || valid_shape(shape_from_schedule(spec->schedule)),
+                 "gift_filter: schedule is 0 (autotune), 4..32, 100*cw + lanes, or 1000/2000/3000 + slab width");
     const int64_t N = g->n;
     const int32_t K = 2 * S;
     GIFT_REQUIRE((int64_t)K * N < (int64_t)1 << 40, "gift_filter: signal too large");
     const size_t sig_bytes = sizeof(float) * (size_t)N * K;
     GIFT_REQUIRE(!ranges_overlap(g_in, sig_bytes, g_out, sig_bytes), "gift_filter: g_in and g_out overlap");
 
+    Plan p;
+    p.g = g;
+    p.K = K;
+    p.reimpose = spec->reimpose_fixed;
     // ---- chains by sigma
-    std::vector<Chain> chains;
     for (int t = 0; t < spec->num_terms; ++t) {
         const gift_term &tm = spec->term[t];
         GIFT_REQUIRE(std::isfinite(tm.sigma) && tm.sigma > 0.f, "gift_filter: sigma must be finite and > 0");
         GIFT_REQUIRE(tm.power >= 1 && tm.power <= 64, "gift_filter: power must be in [1, 64]");
         GIFT_REQUIRE(std::isfinite(tm.alpha), "gift_filter: alpha must be finite");
         Chain *c = nullptr;
-        for (auto &x : chains)
+        for (auto &x : p.chains)
             if (x.sigma == tm.sigma) c = &x;
         if (!c) {
-            chains.push_back(Chain{});
-            c = &chains.back();
+            p.chains.push_back(Chain{});
+            c = &p.chains.back();
             c->sigma = tm.sigma;
         }
         c->L = std::max(c->L, tm.power);
         c->alpha_at[tm.power] += tm.alpha;
         c->has_at[tm.power] = true;
     }
-    int Lmax = 0;
-    for (auto &c : chains) Lmax = std::max(Lmax, c.L);
+    p.Lmax = 0;
+    for (auto &c : p.chains) p.Lmax = std::max(p.Lmax, c.L);
 
     // ---- signal buffers
     DevBuf din_buf, dout_buf;
-    const float *din = g_in;
-    float *dout = g_out;
+    p.din = g_in;
+    p.dout = g_out;
     if (mem == GIFT_MEM_HOST) {
         din_buf = DevBuf(ctx, sig_bytes, st);
         dout_buf = DevBuf(ctx, sig_bytes, st);
         GIFT_CUDA(cudaMemcpyAsync(din_buf.p, g_in, sig_bytes, cudaMemcpyHostToDevice, st));
-        din = din_buf.as<float>();
-        dout = dout_buf.as<float>();
+        p.din = din_buf.as<float>();
+        p.dout = dout_buf.as<float>();
     }
-    const bool al16 = (reinterpret_cast<uintptr_t>(din) % 16 == 0) && (reinterpret_cast<uintptr_t>(dout) % 16 == 0);
-    const bool al8 = (reinterpret_cast<uintptr_t>(din) % 8 == 0) && (reinterpret_cast<uintptr_t>(dout) % 8 == 0);
+    const bool al16 = (reinterpret_cast<uintptr_t>(p.din) % 16 == 0) && (reinterpret_cast<uintptr_t>(p.dout) % 16 == 0);
+    const bool al8 = (reinterpret_cast<uintptr_t>(p.din) % 8 == 0) && (reinterpret_cast<uintptr_t>(p.dout) % 8 == 0);
     GIFT_REQUIRE(al8, "gift_filter: device signal pointers must be 8-byte aligned");
-    const int vec = (K % 4 == 0 && al16) ? 4 : 2;
+    p.vec = (K % 4 == 0 && al16) ? 4 : 2;
 
     std::vector<DevBuf> xbuf;  // two per chain with L >= 2
-    std::vector<std::array<float *, 2>> X(chains.size(), {nullptr, nullptr});
-    for (size_t c = 0; c < chains.size(); ++c)
-        if (chains[c].L >= 2) {
+    p.X.assign(p.chains.size(), {nullptr, nullptr});
+    for (size_t c = 0; c < p.chains.size(); ++c)
+        if (p.chains[c].L >= 2) {
             xbuf.emplace_back(ctx, sig_bytes, st);
-            X[c][0] = xbuf.back().as<float>();
+            p.X[c][0] = xbuf.back().as<float>();
             xbuf.emplace_back(ctx, sig_bytes, st);
-            X[c][1] = xbuf.back().as<float>();
+            p.X[c][1] = xbuf.back().as<float>();
         }
     DevBuf acc_buf(ctx, sig_bytes, st);
-    float *acc = acc_buf.as<float>();
+    p.acc = acc_buf.as<float>();
+    p.sc.resize(p.chains.size());
+    for (size_t c = 0; c < p.chains.size(); ++c) p.sc[c] = graph_scale(ctx, g, p.chains[c].sigma, spec->norm, st);
 
-    std::vector<gift_graph::Scale> sc(chains.size());
-    for (size_t c = 0; c < chains.size(); ++c) sc[c] = graph_scale(ctx, g, chains[c].sigma, spec->norm, st);
-
-    // ---- kernel shape: column slabs of VEC * CW columns, NS lanes per row
-    std::vector<std::pair<int, int>> slabs;  // (c0, cw)
-    for (int c0 = 0; c0 < K;) {
-        int left = (K - c0) / vec;
-        int cw = left >= 4 ? 4 : (left >= 2 ? 2 : 1);
-        slabs.push_back({c0, cw});
-        c0 += cw * vec;
+    DevBuf gpre2_buf;
+    p.gpre2 = nullptr;
+    if (p.chains.size() >= 2 && p.sc[0].pre && p.sc[1].pre) {
+        gpre2_buf = DevBuf(ctx, sizeof(float2) * (size_t)std::max<int64_t>(N, 1), st);
+        LaunchTimer lt(ctx, st, "filter.scale", 16.0 * N);
+        k_pack2<<<(int)std::min<int64_t>(ceil_div(N, 256), (int64_t)ctx->num_sms * 8), 256, 0, st>>>(
+            N, p.sc[0].pre, p.sc[1].pre, gpre2_buf.as<float2>());
+        check_launch("k_pack2");
+        p.gpre2 = gpre2_buf.as<float2>();
     }
-    const double avg = N > 0 ? (double)g->nnz / (double)N : 0.0;
-    auto pick_ns = [&](int cw) {
-        int ns = 1;
-        if (spec->schedule > 0) ns = spec->schedule;
-        else
-            while (ns < 8 && ns * cw < 32 && (double)ns * 4.0 < avg) ns <<= 1;
-        while (ns * cw > 32) ns >>= 1;
-        return std::max(1, std::min(ns, 8));
-    };
-    const size_t wsz = g->weight_dtype == GIFT_WEIGHT_F32 ? 4 : 2;
-    const double csr_bytes = (double)g->nnz * (4.0 + wsz) + 8.0 * (N + 1);
+    p.ncounters = 1024;
+    DevBuf counters(ctx, sizeof(int32_t) * p.ncounters, st);
+    p.counters = counters.as<int32_t>();
+    const Shape shape = spec->schedule == 0 ? autotune(ctx, p, st) : shape_from_schedule(spec->schedule);
+    GIFT_CUDA(cudaMemsetAsync(p.counters, 0, sizeof(int32_t) * p.ncounters, st));
+    run_sweeps(ctx, p, shape, st);
+    ctx->last_schedule = shape.family >= 1 ? 1000 * shape.family + shape.a : 100 * shape.a + shape.b;
 
-    // ---- sweeps
-    bool contributed = false;
-    for (int k = 1; k <= Lmax; ++k) {
-        std::vector<int> active;
-        for (size_t c = 0; c < chains.size(); ++c)
-            if (chains[c].L >= k) active.push_back((int)c);
-        for (size_t gi = 0; gi < active.size(); gi += 2) {
-            const int nc = (int)std::min<size_t>(2, active.size() - gi);
-            const bool last = (k == Lmax) && (gi + 2 >= active.size());
-            bool group_terms = false;
-            for (int q = 0; q < nc; ++q) group_terms |= chains[active[gi + q]].has_at[k];
-            for (size_t si = 0; si < slabs.size(); ++si) {
-                const int c0 = slabs[si].first, cw = slabs[si].second, W = cw * vec;
-                const int ns = pick_ns(cw);
-                SweepArgs a;
-                std::memset(&a, 0, sizeof(a));
-                a.row_ptr = g->row_ptr;
-                a.col = g->col;
-                a.val = g->val;
-                a.n_rows = N;
-                a.K = K;
-                a.c0 = c0;
-                double bytes = si == 0 ? csr_bytes : 0.0;
-                for (int q = 0; q < nc; ++q) {
-                    const int c = active[gi + q];
-                    const Chain &ch = chains[c];
-                    ChainIO &io = a.ch[q];
-                    io.x = k == 1 ? din : X[c][(k - 1) % 2];
-                    io.gpre = k == 1 ? sc[c].pre : nullptr;
-                    io.post = sc[c].post;
-                    io.sigma = ch.sigma;
-                    io.alpha = (float)ch.alpha_at[k];
-                    io.has_term = ch.has_at[k] ? 1 : 0;
-                    io.xnext = ch.L > k ? X[c][k % 2] : nullptr;
-                    io.pnext = sc[c].pre;
-                    bytes += 4.0 * N * W + 4.0 * N;  // input slab + scale
-                    if (io.xnext) bytes += 4.0 * N * W;
-                }
-                if (last) {
-                    a.acc_in = contributed ? acc : nullptr;
-                    a.acc_out = dout;
-                    if (spec->reimpose_fixed) {
-                        a.fixed = g->is_fixed;
-                        a.g_fixed = din;
-                        bytes += (double)N;
-                    }
-                } else if (group_terms) {
-                    a.acc_in = contributed ? acc : nullptr;
-                    a.acc_out = acc;
-                }
-                if (a.acc_in) bytes += 4.0 * N * W;
-                if (a.acc_out) bytes += 4.0 * N * W;
-                const void *fn = sweep_kernel(g->weight_dtype, vec, cw, ns, nc);
-                GIFT_REQUIRE(fn != nullptr, "gift_filter: no kernel for this shape");
-                const int G = cw * ns, rows_per_block = (kSweepThreads / 32) * (32 / G);
-                const int64_t want = ceil_div(std::max<int64_t>(N, 1), rows_per_block);
-                const int grid = (int)std::max<int64_t>(
-                    1, std::min<int64_t>(want, (int64_t)ctx->num_sms * occupancy_blocks(fn, kSweepThreads)));
-                void *params[] = {&a};
-                LaunchTimer lt(ctx, st, "filter.sweep", bytes);
-                GIFT_CUDA(cudaLaunchKernel(fn, dim3(grid), dim3(kSweepThreads), params, 0, st));
-            }
-            if (group_terms && !last) contributed = true;
-        }
-    }
     if (mem == GIFT_MEM_HOST) {
-        GIFT_CUDA(cudaMemcpyAsync(g_out, dout, sig_bytes, cudaMemcpyDeviceToHost, st));
+        GIFT_CUDA(cudaMemcpyAsync(g_out, p.dout, sig_bytes, cudaMemcpyDeviceToHost, st));
         GIFT_CUDA(cudaStreamSynchronize(st));
+        check_device_error(ctx);
     }
 }
 

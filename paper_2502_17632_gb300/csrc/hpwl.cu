@@ -11,23 +11,39 @@ namespace gift {
 namespace {
 
 constexpr int kHpwlThreads = 256;
+constexpr int kSC = 8;  // signals per pass (grid.y covers the rest)
 
-__device__ __forceinline__ double net_extent(float xlo, float xhi, float ylo, float yhi) {
-    return ((double)xhi - (double)xlo) + ((double)yhi - (double)ylo);
+struct Box {
+    float xlo, xhi, ylo, yhi;
+};
+
+__device__ __forceinline__ void grow(Box &b, float2 p) {
+    b.xlo = fminf(b.xlo, p.x);
+    b.xhi = fmaxf(b.xhi, p.x);
+    b.ylo = fminf(b.ylo, p.y);
+    b.yhi = fmaxf(b.yhi, p.y);
 }
 
-// grid.y = signal.  Each lane owns one net of its warp's 32 (nets of up to 32
-// pins); larger nets are reduced by the whole warp.
+__device__ __forceinline__ double extent(const Box &b) {
+    return ((double)b.xhi - (double)b.xlo) + ((double)b.yhi - (double)b.ylo);
+}
+
+// grid.y = pass over signals [kSC * y, kSC * y + kSC).  Each lane owns one net
+// of its warp's 32 (nets of up to 32 pins) and reads each pin's locations for
+// all signals of the pass (one contiguous row piece); larger nets are reduced
+// by the whole warp.
 __global__ void __launch_bounds__(kHpwlThreads)
 k_hpwl(int32_t E, int32_t S, const int64_t *__restrict__ net_ptr, const int32_t *__restrict__ pin_cell,
-       const float *__restrict__ xy, double *__restrict__ partial) {
-    __shared__ double red[kHpwlThreads / 32];
-    const int s = blockIdx.y;
-    const int lane = threadIdx.x & 31;
+       const float2 *__restrict__ xy, double *__restrict__ partial) {
+    __shared__ double red[kSC][kHpwlThreads / 32];
+    const int s0 = blockIdx.y * kSC;
+    const int ns = min(kSC, S - s0);
+    const int lane = threadIdx.x & 31, wid = threadIdx.x >> 5;
     const int64_t warp = (blockIdx.x * (int64_t)blockDim.x + threadIdx.x) >> 5;
     const int64_t nwarps = ((int64_t)gridDim.x * blockDim.x) >> 5;
-    auto loc = [&](int32_t c) { return __ldg(reinterpret_cast<const float2 *>(xy) + (int64_t)c * S + s); };
-    double sum = 0.0;
+    double sum[kSC];
+#pragma unroll
+    for (int q = 0; q < kSC; ++q) sum[q] = 0.0;
     for (int64_t base = warp * 32; base < E; base += nwarps * 32) {
         const int64_t e = base + lane;
         int64_t b = 0, m = 0;
@@ -35,43 +51,52 @@ k_hpwl(int32_t E, int32_t S, const int64_t *__restrict__ net_ptr, const int32_t 
             b = net_ptr[e];
             m = net_ptr[e + 1] - b;
         }
-        if (m >= 1 && m <= 32) {
-            float2 p = loc(pin_cell[b]);
-            float xlo = p.x, xhi = p.x, ylo = p.y, yhi = p.y;
-            for (int64_t t = 1; t < m; ++t) {
-                p = loc(pin_cell[b + t]);
-                xlo = fminf(xlo, p.x); xhi = fmaxf(xhi, p.x);
-                ylo = fminf(ylo, p.y); yhi = fmaxf(yhi, p.y);
+        if (m >= 2 && m <= 32) {
+            Box bx[kSC];
+            const float2 *r = xy + (int64_t)pin_cell[b] * S + s0;
+#pragma unroll
+            for (int q = 0; q < kSC; ++q) {
+                float2 p = q < ns ? __ldg(r + q) : make_float2(0.f, 0.f);
+                bx[q] = Box{p.x, p.x, p.y, p.y};
             }
-            sum += net_extent(xlo, xhi, ylo, yhi);
+            for (int64_t t = 1; t < m; ++t) {
+                r = xy + (int64_t)pin_cell[b + t] * S + s0;
+#pragma unroll
+                for (int q = 0; q < kSC; ++q)
+                    if (q < ns) grow(bx[q], __ldg(r + q));
+            }
+#pragma unroll
+            for (int q = 0; q < kSC; ++q) sum[q] += extent(bx[q]);
         }
         unsigned big = __ballot_sync(0xffffffffu, m > 32);
         while (big) {
             const int src = __ffs(big) - 1;
             big &= big - 1;
             const int64_t bb = __shfl_sync(0xffffffffu, b, src), mb = __shfl_sync(0xffffffffu, m, src);
-            float xlo = INFINITY, xhi = -INFINITY, ylo = INFINITY, yhi = -INFINITY;
-            for (int64_t t = lane; t < mb; t += 32) {
-                float2 p = loc(pin_cell[bb + t]);
-                xlo = fminf(xlo, p.x); xhi = fmaxf(xhi, p.x);
-                ylo = fminf(ylo, p.y); yhi = fmaxf(yhi, p.y);
+            for (int q = 0; q < ns; ++q) {
+                Box bx{INFINITY, -INFINITY, INFINITY, -INFINITY};
+                for (int64_t t = lane; t < mb; t += 32) grow(bx, __ldg(xy + (int64_t)pin_cell[bb + t] * S + s0 + q));
+                for (int o = 16; o; o >>= 1) {
+                    bx.xlo = fminf(bx.xlo, __shfl_xor_sync(0xffffffffu, bx.xlo, o));
+                    bx.xhi = fmaxf(bx.xhi, __shfl_xor_sync(0xffffffffu, bx.xhi, o));
+                    bx.ylo = fminf(bx.ylo, __shfl_xor_sync(0xffffffffu, bx.ylo, o));
+                    bx.yhi = fmaxf(bx.yhi, __shfl_xor_sync(0xffffffffu, bx.yhi, o));
+                }
+                if (lane == src) sum[q] += extent(bx);
             }
-            for (int o = 16; o; o >>= 1) {
-                xlo = fminf(xlo, __shfl_xor_sync(0xffffffffu, xlo, o));
-                xhi = fmaxf(xhi, __shfl_xor_sync(0xffffffffu, xhi, o));
-                ylo = fminf(ylo, __shfl_xor_sync(0xffffffffu, ylo, o));
-                yhi = fmaxf(yhi, __shfl_xor_sync(0xffffffffu, yhi, o));
-            }
-            if (lane == src) sum += net_extent(xlo, xhi, ylo, yhi);
         }
     }
-    for (int o = 16; o; o >>= 1) sum += __shfl_xor_sync(0xffffffffu, sum, o);
-    if (lane == 0) red[threadIdx.x >> 5] = sum;
+#pragma unroll
+    for (int q = 0; q < kSC; ++q) {
+        double v = sum[q];
+        for (int o = 16; o; o >>= 1) v += __shfl_xor_sync(0xffffffffu, v, o);
+        if (lane == 0) red[q][wid] = v;
+    }
     __syncthreads();
-    if (threadIdx.x == 0) {
+    if (threadIdx.x < ns) {
         double t = 0.0;
-        for (int w = 0; w < kHpwlThreads / 32; ++w) t += red[w];
-        partial[(int64_t)s * gridDim.x + blockIdx.x] = t;
+        for (int w = 0; w < kHpwlThreads / 32; ++w) t += red[threadIdx.x][w];
+        partial[(int64_t)(s0 + threadIdx.x) * gridDim.x + blockIdx.x] = t;
     }
 }
 
@@ -86,7 +111,7 @@ __global__ void k_hpwl_final(int32_t S, int32_t nblocks, const double *__restric
 }  // namespace
 
 void hpwl_impl(gift_ctx *ctx, const gift_graph *g, const float *xy, int S, double *out, int mem, cudaStream_t st) {
-    GIFT_REQUIRE(S >= 1 && S <= 65535, "gift_hpwl: num_signals must be in [1, 65535]");
+    GIFT_REQUIRE(S >= 1 && S <= 65535 * kSC, "gift_hpwl: num_signals out of range");
     GIFT_REQUIRE(xy && out, "gift_hpwl: NULL pointer");
     GIFT_REQUIRE(mem == GIFT_MEM_HOST || mem == GIFT_MEM_DEVICE, "gift_hpwl: bad mem kind");
     GIFT_REQUIRE(reinterpret_cast<uintptr_t>(xy) % 8 == 0, "gift_hpwl: xy must be 8-byte aligned");
@@ -99,19 +124,22 @@ void hpwl_impl(gift_ctx *ctx, const gift_graph *g, const float *xy, int S, doubl
         dxy = dxy_buf.as<float>();
     }
     const int64_t E = g->num_nets;
+    const int passes = (S + kSC - 1) / kSC;
     const int nblocks = (int)std::max<int64_t>(
-        1, std::min<int64_t>(ceil_div(std::max<int64_t>(E, 1), kHpwlThreads), (int64_t)ctx->num_sms * 8 / S + 1));
+        1, std::min<int64_t>(ceil_div(std::max<int64_t>(E, 1), kHpwlThreads), (int64_t)ctx->num_sms * 8));
     DevBuf partial(ctx, sizeof(double) * (size_t)nblocks * S, st);
     DevBuf dout(ctx, sizeof(double) * S, st);
     {
-        LaunchTimer lt(ctx, st, "hpwl", 8.0 * (E + 1) + 4.0 * g->num_pins + 8.0 * g->num_pins * S);
-        k_hpwl<<<dim3(nblocks, S), kHpwlThreads, 0, st>>>((int32_t)E, S, g->net_ptr, g->pin_cell, dxy,
-                                                           partial.as<double>());
+        LaunchTimer lt(ctx, st, "hpwl", 8.0 * (E + 1) + 4.0 * g->num_pins + 8.0 * g->num_pins * S, 2);
+        k_hpwl<<<dim3(nblocks, passes), kHpwlThreads, 0, st>>>((int32_t)E, S, g->net_ptr, g->pin_cell,
+                                                                reinterpret_cast<const float2 *>(dxy),
+                                                                partial.as<double>());
         k_hpwl_final<<<1, 128, 0, st>>>(S, nblocks, partial.as<double>(), dout.as<double>());
         check_launch("k_hpwl");
     }
     GIFT_CUDA(cudaMemcpyAsync(out, dout.p, sizeof(double) * S, cudaMemcpyDeviceToHost, st));
     GIFT_CUDA(cudaStreamSynchronize(st));
+    check_device_error(ctx);
 }
 
 }  // namespace gift

@@ -62,14 +62,20 @@ gift_status guarded(F &&body) {
 // ---------------------------------------------------------------- context
 struct KernelRecord {
     int64_t launches = 0;
+    int64_t kernels = 0;
     double total_ms = 0;
     double alg_bytes = 0;
+};
+
+struct TunedShape {
+    int family, a, b;
 };
 
 struct PendingTiming {
     std::string name;
     cudaEvent_t start, stop;
     double alg_bytes;
+    int kernels;
 };
 
 }  // namespace gift
@@ -88,6 +94,12 @@ struct gift_ctx {
     std::map<std::string, gift::KernelRecord> records;
     std::vector<gift::PendingTiming> pending;
     std::vector<cudaEvent_t> event_pool;
+    // autotuned sweep shapes by graph/signal shape key: (family, a, b)
+    std::mutex tune_mu;
+    std::map<std::string, gift::TunedShape> tuned;
+    int last_schedule = 0;
+    // device word set by kernels whose bounded waits ran out (0 = fine)
+    int32_t *dev_error = nullptr;
 };
 
 namespace gift {
@@ -132,14 +144,19 @@ struct LaunchTimer {
     cudaStream_t st;
     const char *name;
     double bytes;
+    int kernels;
     cudaEvent_t a = nullptr, b = nullptr;
-    LaunchTimer(gift_ctx *c, cudaStream_t s, const char *n, double alg_bytes);
+    // `kernels`: how many kernel launches the scope contains
+    LaunchTimer(gift_ctx *c, cudaStream_t s, const char *n, double alg_bytes, int kernels = 1);
     ~LaunchTimer();
 };
 // Folds completed timings into the records (called after a synchronisation).
 void collect_timings(gift_ctx *ctx, bool wait);
 
 void check_launch(const char *what);
+// Reads (and clears) the context's device error word; throws GIFT_ERR_TIMEOUT if set.
+// Call only after the work that may set it has been synchronised.
+void check_device_error(gift_ctx *ctx);
 
 inline int64_t ceil_div(int64_t a, int64_t b) { return (a + b - 1) / b; }
 
@@ -173,6 +190,16 @@ struct gift_graph {
         float *post;
     };
     std::vector<Scale> scales;
+    // sliced-ELL execution format (built on first use by a sliced-ELL schedule)
+    struct Sell {
+        int rps = 0;              // rows per slice (0: not built)
+        int64_t nslices = 0;
+        int64_t entries = 0;
+        int32_t *perm = nullptr;
+        int64_t *slice_ptr = nullptr;
+        int32_t *col = nullptr;
+        void *val = nullptr;
+    } sell;
     std::mutex mu;
 };
 
@@ -181,6 +208,9 @@ namespace gift {
 void build_graph_impl(gift_ctx *ctx, const gift_netlist *nl, const gift_build_opts *opts, gift_graph **out,
                       cudaStream_t st);
 void release_graph(gift_graph *g, cudaStream_t st);
+// sell.cu
+void build_sell(gift_ctx *ctx, gift_graph *g, int rps, cudaStream_t st);
+void release_sell(gift_graph *g, cudaStream_t st);
 // filter.cu
 void filter_impl(gift_ctx *ctx, const gift_graph *g, const gift_filter_spec *spec, const float *g_in, int S,
                  float *g_out, int mem, cudaStream_t st);

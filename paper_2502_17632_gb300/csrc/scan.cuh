@@ -5,6 +5,7 @@
 #include "internal.cuh"
 
 namespace gift {
+namespace {  // every translation unit that scans gets its own copy of the kernels
 
 constexpr int kScanThreads = 256;
 constexpr int kScanTile = 4096;
@@ -93,4 +94,5 @@ void exclusive_scan(gift_ctx *ctx, const T *in, int64_t *out, int64_t n, cudaStr
     check_launch("exclusive_scan");
 }
 
+}  // namespace
 }  // namespace gift

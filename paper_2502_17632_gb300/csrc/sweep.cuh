@@ -13,9 +13,9 @@
 // contributions alpha * y added to an accumulator or, in the last sweep, to
 // the result with fixed rows taken from g (Sec. 3.2.2, Algorithm 1).
 //
-// Thread mapping: a group of G = CW * NS lanes owns one row; CW lanes split
-// the slab's columns into VEC-wide vectors, NS lanes split the row's nonzeros
-// and are reduced with xor shuffles.  FP32 multiply-add, FP32 accumulation.
+// Thread mapping: a group of G lanes owns one row; CW lanes split the slab's
+// columns into VEC-wide vectors and G / CW lanes split the row's nonzeros,
+// reduced with xor shuffles at the end.  FP32 multiply-add and accumulation.
 #pragma once
 
 #include "internal.cuh"
@@ -49,19 +49,95 @@ struct SweepArgs {
     const float *g_fixed;
 };
 
+// ---- loads with L2 eviction priority: the CSR is streamed once per pass
+// (evict first), the gathered signal rows should stay in L2 (evict last).
+__device__ __forceinline__ uint64_t l2_evict_first() {
+    uint64_t p;
+    asm("createpolicy.fractional.L2::evict_first.b64 %0, 1.0;" : "=l"(p));
+    return p;
+}
+__device__ __forceinline__ uint64_t l2_evict_last() {
+    uint64_t p;
+    asm("createpolicy.fractional.L2::evict_last.b64 %0, 1.0;" : "=l"(p));
+    return p;
+}
+// Measured on GB300 (large workload, every row-group shape): the hints made
+// the sweep 5-15% slower, so they are off by default.
+#ifndef GIFT_HINT_STREAM
+#define GIFT_HINT_STREAM 0
+#endif
+#ifndef GIFT_HINT_KEEP
+#define GIFT_HINT_KEEP 0
+#endif
+__device__ __forceinline__ int32_t ld_stream_i32(const int32_t *p, uint64_t pol) {
+#if GIFT_HINT_STREAM
+    int32_t v;
+    asm("ld.global.nc.L1::no_allocate.L2::cache_hint.b32 %0, [%1], %2;" : "=r"(v) : "l"(p), "l"(pol));
+    return v;
+#else
+    return __ldg(p);
+#endif
+}
+__device__ __forceinline__ uint16_t ld_stream_u16(const void *p, uint64_t pol) {
+#if GIFT_HINT_STREAM
+    uint16_t v;
+    asm("ld.global.nc.L1::no_allocate.L2::cache_hint.b16 %0, [%1], %2;" : "=h"(v) : "l"(p), "l"(pol));
+    return v;
+#else
+    return __ldg(static_cast<const unsigned short *>(p));
+#endif
+}
+
 template <typename WT>
-__device__ __forceinline__ float ld_weight(const void *v, int64_t k);
+__device__ __forceinline__ float ld_weight(const void *v, int64_t k, uint64_t pol);
 template <>
-__device__ __forceinline__ float ld_weight<float>(const void *v, int64_t k) {
+__device__ __forceinline__ float ld_weight<float>(const void *v, int64_t k, uint64_t pol) {
+    return __int_as_float(ld_stream_i32(static_cast<const int32_t *>(v) + k, pol));
+}
+template <>
+__device__ __forceinline__ float ld_weight<__nv_bfloat16>(const void *v, int64_t k, uint64_t pol) {
+    return __uint_as_float((uint32_t)ld_stream_u16(static_cast<const __nv_bfloat16 *>(v) + k, pol) << 16);
+}
+template <>
+__device__ __forceinline__ float ld_weight<__half>(const void *v, int64_t k, uint64_t pol) {
+    return __half2float(__ushort_as_half(ld_stream_u16(static_cast<const __half *>(v) + k, pol)));
+}
+
+// plain read-only load of one stored weight
+template <typename WT>
+__device__ __forceinline__ float ld_weight_plain(const void *v, int64_t k);
+template <>
+__device__ __forceinline__ float ld_weight_plain<float>(const void *v, int64_t k) {
     return __ldg(static_cast<const float *>(v) + k);
 }
 template <>
-__device__ __forceinline__ float ld_weight<__nv_bfloat16>(const void *v, int64_t k) {
+__device__ __forceinline__ float ld_weight_plain<__nv_bfloat16>(const void *v, int64_t k) {
     return __bfloat162float(__ldg(static_cast<const __nv_bfloat16 *>(v) + k));
 }
 template <>
-__device__ __forceinline__ float ld_weight<__half>(const void *v, int64_t k) {
+__device__ __forceinline__ float ld_weight_plain<__half>(const void *v, int64_t k) {
     return __half2float(__ldg(static_cast<const __half *>(v) + k));
+}
+
+// gathered signal rows (kept in L2)
+template <int VEC>
+__device__ __forceinline__ void ld_keep(const float *p, float (&r)[VEC], uint64_t pol) {
+#if !GIFT_HINT_KEEP
+    if constexpr (VEC == 4) {
+        float4 t = __ldg(reinterpret_cast<const float4 *>(p));
+        r[0] = t.x; r[1] = t.y; r[2] = t.z; r[3] = t.w;
+    } else {
+        float2 t = __ldg(reinterpret_cast<const float2 *>(p));
+        r[0] = t.x; r[1] = t.y;
+    }
+    return;
+#endif
+    if constexpr (VEC == 4) {
+        asm("ld.global.nc.L2::cache_hint.v4.f32 {%0,%1,%2,%3}, [%4], %5;"
+            : "=f"(r[0]), "=f"(r[1]), "=f"(r[2]), "=f"(r[3]) : "l"(p), "l"(pol));
+    } else {
+        asm("ld.global.nc.L2::cache_hint.v2.f32 {%0,%1}, [%2], %3;" : "=f"(r[0]), "=f"(r[1]) : "l"(p), "l"(pol));
+    }
 }
 
 template <int VEC>
@@ -69,11 +145,9 @@ __device__ __forceinline__ void ldv(const float *p, float (&r)[VEC]) {
     if constexpr (VEC == 4) {
         float4 t = __ldg(reinterpret_cast<const float4 *>(p));
         r[0] = t.x; r[1] = t.y; r[2] = t.z; r[3] = t.w;
-    } else if constexpr (VEC == 2) {
+    } else {
         float2 t = __ldg(reinterpret_cast<const float2 *>(p));
         r[0] = t.x; r[1] = t.y;
-    } else {
-        r[0] = __ldg(p);
     }
 }
 
@@ -81,38 +155,29 @@ template <int VEC>
 __device__ __forceinline__ void stv(float *p, const float (&r)[VEC]) {
     if constexpr (VEC == 4) {
         *reinterpret_cast<float4 *>(p) = make_float4(r[0], r[1], r[2], r[3]);
-    } else if constexpr (VEC == 2) {
-        *reinterpret_cast<float2 *>(p) = make_float2(r[0], r[1]);
     } else {
-        *p = r[0];
+        *reinterpret_cast<float2 *>(p) = make_float2(r[0], r[1]);
     }
 }
 
-template <typename WT, int VEC, int NC>
-__device__ __forceinline__ void gather_fma(const SweepArgs &a, int64_t k, int colo, float (&acc)[NC][VEC]) {
-    const int32_t j = __ldg(a.col + k);
-    const float w = ld_weight<WT>(a.val, k);
-    const int64_t off = (int64_t)j * a.K + colo;
-#pragma unroll
-    for (int c = 0; c < NC; ++c) {
-        float xv[VEC];
-        ldv<VEC>(a.ch[c].x + off, xv);
-        const float wc = a.ch[c].gpre ? w * __ldg(a.ch[c].gpre + j) : w;
-#pragma unroll
-        for (int v = 0; v < VEC; ++v) acc[c][v] = fmaf(wc, xv[v], acc[c][v]);
-    }
-}
-
-template <typename WT, int VEC, int CW, int NS, int NC>
+// Row group of G lanes: CW lanes across the slab's columns (VEC floats each),
+// NS = G / CW nonzeros at a time.  Each chunk of G nonzeros of the row is
+// loaded with one coalesced access (one (col, val) per lane), then broadcast
+// by shuffles so that every gather of the chunk is independent of the others.
+template <typename WT, int VEC, int CW, int G, int NC>
 __global__ void __launch_bounds__(kSweepThreads) k_sweep(const SweepArgs a) {
-    constexpr int G = CW * NS;
-    constexpr int RPW = 32 / G;  // rows per warp
+    static_assert(G % CW == 0 && G <= 32 && (32 % G) == 0, "bad group shape");
+    constexpr int NS = G / CW;
+    constexpr int RPW = 32 / G;
     const int lane = threadIdx.x & 31;
     const int gi = lane / G, gl = lane % G;
     const int cc = gl % CW, ns = gl / CW;
+    const unsigned gmask = G == 32 ? 0xffffffffu : (((1u << G) - 1u) << (gi * G));
     const int64_t warp = (blockIdx.x * (int64_t)blockDim.x + threadIdx.x) >> 5;
     const int64_t nwarps = ((int64_t)gridDim.x * blockDim.x) >> 5;
     const int colo = a.c0 + cc * VEC;
+    const uint64_t pol_stream = l2_evict_first();
+    const uint64_t pol_keep = l2_evict_last();
 
     for (int64_t rb = warp * RPW; rb < a.n_rows; rb += nwarps * RPW) {
         const int64_t row = rb + gi;
@@ -122,21 +187,61 @@ __global__ void __launch_bounds__(kSweepThreads) k_sweep(const SweepArgs a) {
         for (int c = 0; c < NC; ++c)
 #pragma unroll
             for (int v = 0; v < VEC; ++v) acc[c][v] = 0.f;
+        int64_t kb = 0, ke = 0;
         if (active) {
-            const int64_t ke = __ldg(a.row_ptr + row + 1);
-            int64_t k = __ldg(a.row_ptr + row) + ns;
-            for (; k + NS < ke; k += 2 * NS) {
-                gather_fma<WT, VEC, NC>(a, k, colo, acc);
-                gather_fma<WT, VEC, NC>(a, k + NS, colo, acc);
+            kb = __ldg(a.row_ptr + row);
+            ke = __ldg(a.row_ptr + row + 1);
+        }
+        for (int64_t c0 = kb; c0 < ke; c0 += G) {
+            const int64_t k = c0 + gl;
+            int32_t jl = 0;
+            float wl = 0.f;
+            if (k < ke) {
+                jl = ld_stream_i32(a.col + k, pol_stream);
+                wl = ld_weight<WT>(a.val, k, pol_stream);
             }
-            if (k < ke) gather_fma<WT, VEC, NC>(a, k, colo, acc);
+            const int cnt = (int)(ke - c0 < (int64_t)G ? ke - c0 : (int64_t)G);
+            float xv[CW][NC][VEC];
+            float wv[CW];
+#pragma unroll
+            for (int t = 0; t < CW; ++t) {
+                const int src = t * NS + ns;
+                const int32_t j = __shfl_sync(gmask, jl, src, G);
+                const float w = __shfl_sync(gmask, wl, src, G);
+                wv[t] = src < cnt ? w : 0.f;
+                const int64_t off = (int64_t)(src < cnt ? j : 0) * a.K + colo;
+#pragma unroll
+                for (int c = 0; c < NC; ++c) {
+                    if (src < cnt) {
+                        ld_keep<VEC>(a.ch[c].x + off, xv[t][c], pol_keep);
+                    } else {
+#pragma unroll
+                        for (int v = 0; v < VEC; ++v) xv[t][c][v] = 0.f;
+                    }
+                }
+                // unscaled input (first sweep): gather scale of row j per chain
+#pragma unroll
+                for (int c = 0; c < NC; ++c) {
+                    if (a.ch[c].gpre) {
+                        const float sj = src < cnt ? __ldg(a.ch[c].gpre + j) : 0.f;
+#pragma unroll
+                        for (int v = 0; v < VEC; ++v) xv[t][c][v] *= sj;
+                    }
+                }
+            }
+#pragma unroll
+            for (int t = 0; t < CW; ++t)
+#pragma unroll
+                for (int c = 0; c < NC; ++c)
+#pragma unroll
+                    for (int v = 0; v < VEC; ++v) acc[c][v] = fmaf(wv[t], xv[t][c][v], acc[c][v]);
         }
 #pragma unroll
         for (int o = CW; o < G; o <<= 1)
 #pragma unroll
             for (int c = 0; c < NC; ++c)
 #pragma unroll
-                for (int v = 0; v < VEC; ++v) acc[c][v] += __shfl_xor_sync(0xffffffffu, acc[c][v], o);
+                for (int v = 0; v < VEC; ++v) acc[c][v] += __shfl_xor_sync(0xffffffffu, acc[c][v], o, G);
 
         if (!active || ns != 0) continue;
         const int64_t off = row * a.K + colo;
@@ -183,32 +288,29 @@ __global__ void __launch_bounds__(kSweepThreads) k_sweep(const SweepArgs a) {
 }
 
 // Kernel pointer for a configuration; nullptr if not instantiated.
-// vec in {2, 4}; cw in {1, 2, 4}; ns in {1, 2, 4, 8}; nc in {1, 2}.
-const void *sweep_kernel(int weight_dtype, int vec, int cw, int ns, int nc);
+// vec in {2, 4}; cw in {1, 2, 4}; g (lanes per row) in {4, 8, 16, 32}; nc in {1, 2}.
+const void *sweep_kernel(int weight_dtype, int vec, int cw, int g, int nc);
 
-#define GIFT_SWEEP_TABLE(WT)                                                                         \
-    template <int VEC, int NC>                                                                      \
-    static const void *pick_##WT(int cw, int ns) {                                                  \
-        switch (cw * 16 + ns) {                                                                     \
-        case 16 + 1: return (const void *)k_sweep<WT, VEC, 1, 1, NC>;                               \
-        case 16 + 2: return (const void *)k_sweep<WT, VEC, 1, 2, NC>;                               \
-        case 16 + 4: return (const void *)k_sweep<WT, VEC, 1, 4, NC>;                               \
-        case 16 + 8: return (const void *)k_sweep<WT, VEC, 1, 8, NC>;                               \
-        case 32 + 1: return (const void *)k_sweep<WT, VEC, 2, 1, NC>;                               \
-        case 32 + 2: return (const void *)k_sweep<WT, VEC, 2, 2, NC>;                               \
-        case 32 + 4: return (const void *)k_sweep<WT, VEC, 2, 4, NC>;                               \
-        case 32 + 8: return (const void *)k_sweep<WT, VEC, 2, 8, NC>;                               \
-        case 64 + 1: return (const void *)k_sweep<WT, VEC, 4, 1, NC>;                               \
-        case 64 + 2: return (const void *)k_sweep<WT, VEC, 4, 2, NC>;                               \
-        case 64 + 4: return (const void *)k_sweep<WT, VEC, 4, 4, NC>;                               \
-        case 64 + 8: return (const void *)k_sweep<WT, VEC, 4, 8, NC>;                               \
-        default: return nullptr;                                                                    \
-        }                                                                                           \
-    }                                                                                               \
-    const void *sweep_kernel_##WT(int vec, int cw, int ns, int nc) {                                \
-        if (vec == 4) return nc == 1 ? pick_##WT<4, 1>(cw, ns) : pick_##WT<4, 2>(cw, ns);           \
-        if (vec == 2) return nc == 1 ? pick_##WT<2, 1>(cw, ns) : pick_##WT<2, 2>(cw, ns);           \
-        return nullptr;                                                                             \
+#define GIFT_SWEEP_CW(WT, VEC, NC, CW)                                                              \
+    case CW * 64 + 4: return (const void *)k_sweep<WT, VEC, CW, 4, NC>;                             \
+    case CW * 64 + 8: return (const void *)k_sweep<WT, VEC, CW, 8, NC>;                             \
+    case CW * 64 + 16: return (const void *)k_sweep<WT, VEC, CW, 16, NC>;                           \
+    case CW * 64 + 32: return (const void *)k_sweep<WT, VEC, CW, 32, NC>;
+
+#define GIFT_SWEEP_TABLE(WT)                                                                        \
+    template <int VEC, int NC>                                                                     \
+    static const void *pick_##WT(int cw, int g) {                                                  \
+        switch (cw * 64 + g) {                                                                     \
+            GIFT_SWEEP_CW(WT, VEC, NC, 1)                                                          \
+            GIFT_SWEEP_CW(WT, VEC, NC, 2)                                                          \
+            GIFT_SWEEP_CW(WT, VEC, NC, 4)                                                          \
+        default: return nullptr;                                                                   \
+        }                                                                                          \
+    }                                                                                              \
+    const void *sweep_kernel_##WT(int vec, int cw, int g, int nc) {                                \
+        if (vec == 4) return nc == 1 ? pick_##WT<4, 1>(cw, g) : pick_##WT<4, 2>(cw, g);            \
+        if (vec == 2) return nc == 1 ? pick_##WT<2, 1>(cw, g) : pick_##WT<2, 2>(cw, g);            \
+        return nullptr;                                                                            \
     }
 
 }  // namespace gift

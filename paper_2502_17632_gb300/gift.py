@@ -58,8 +58,8 @@ class gift_graph_desc(C.Structure):
 
 
 class gift_kernel_stat(C.Structure):
-    _fields_ = [("name", C.c_char * 48), ("launches", C.c_int64), ("total_ms", C.c_double),
-                ("alg_bytes", C.c_double)]
+    _fields_ = [("name", C.c_char * 48), ("launches", C.c_int64), ("kernels", C.c_int64),
+                ("total_ms", C.c_double), ("alg_bytes", C.c_double)]
 
 
 _lib = None
@@ -86,6 +86,8 @@ def load(build_if_missing: bool = True):
         "gift_ctx_kernel_stats": (I32, [P, P, I32]),
         "gift_ctx_reset_stats": (None, [P]),
         "gift_ctx_debug_fail_alloc": (None, [P, I32]),
+        "gift_ctx_last_schedule": (I32, [P]),
+        "gift_ctx_device_status": (I32, [P]),
         "gift_filter_spec_default": (None, [P]),
         "gift_build_opts_default": (None, [P]),
         "gift_build_graph": (I32, [P, P, P, C.POINTER(P), P]),
@@ -152,12 +154,20 @@ def gift_ctx_kernel_stats(ctx) -> dict:
     n = L.gift_ctx_kernel_stats(ctx, None, 0)
     arr = (gift_kernel_stat * max(n, 1))()
     n = L.gift_ctx_kernel_stats(ctx, arr, n)
-    return {arr[i].name.decode(): dict(launches=arr[i].launches, total_ms=arr[i].total_ms,
+    return {arr[i].name.decode(): dict(launches=arr[i].launches, kernels=arr[i].kernels, total_ms=arr[i].total_ms,
                                        alg_bytes=arr[i].alg_bytes) for i in range(n)}
 
 
 def gift_ctx_reset_stats(ctx):
     load().gift_ctx_reset_stats(ctx)
+
+
+def gift_ctx_last_schedule(ctx) -> int:
+    return int(load().gift_ctx_last_schedule(ctx))
+
+
+def gift_ctx_device_status(ctx):
+    _check(load().gift_ctx_device_status(ctx))
 
 
 def gift_ctx_debug_fail_alloc(ctx, n: int):

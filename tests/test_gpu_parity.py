@@ -132,10 +132,11 @@ def run_filter(ctx, nl, g, wd="f32", spec=None, device=True):
 
 @pytest.mark.parametrize("name", sorted(NETLISTS))
 @pytest.mark.parametrize("S", [1, 2, 3, 8])
-def test_filter_parity(ctx, name, S):
+@pytest.mark.parametrize("schedule", [0, 416, 1016, 1004, 3002])
+def test_filter_parity(ctx, name, S, schedule):
     nl = NETLISTS[name]
     g = synth.make_signals(nl, S, 1234 + S)
-    got = run_filter(ctx, nl, g)
+    got = run_filter(ctx, nl, g, spec=gift.make_spec(schedule=schedule))
     _, _, ref = oracle.run(nl, g.reshape(nl.num_cells, -1))
     ref = ref.reshape(g.shape)
     assert rel_err(got, ref, g).max() <= RTOL
@@ -144,14 +145,38 @@ def test_filter_parity(ctx, name, S):
 
 
 @pytest.mark.parametrize("S", [1, 2, 4, 5, 8, 9, 16])
-@pytest.mark.parametrize("schedule", [0, 1, 2, 4, 8])
+@pytest.mark.parametrize("schedule", [0, 4, 8, 16, 32, 108, 132, 204, 216, 408, 416, 432,
+                                      1002, 1004, 1008, 1016, 2008, 2016, 3002, 3004, 3008, 3016])
 def test_filter_shapes_and_schedules(ctx, S, schedule):
     nl = NETLISTS["repeat-cells"]
     g = synth.make_signals(nl, S, 99 + S)
     spec = gift.make_spec(schedule=schedule)
+    K = 2 * S
+    bad_tma = 2000 <= schedule < 3000 and K % (schedule - 2000) != 0
+    if bad_tma:
+        with pytest.raises(gift.GiftError) as e:
+            run_filter(ctx, nl, g, spec=spec)
+        assert e.value.status == gift.GIFT_ERR_INVALID
+        return
     got = run_filter(ctx, nl, g, spec=spec)
     _, _, ref = oracle.run(nl, g.reshape(nl.num_cells, -1))
     assert rel_err(got, ref.reshape(g.shape), g).max() <= RTOL
+
+
+@pytest.mark.parametrize("name", sorted(NETLISTS))
+@pytest.mark.parametrize("S,schedule", [(4, 2008), (8, 2016), (8, 2008), (16, 2016), (4, 3008), (8, 3016),
+                                        (8, 3008), (16, 3016), (2, 3004)])
+def test_filter_tma_and_sell(ctx, name, S, schedule):
+    """The TMA gather4 pipeline and the sliced-ELL format on every netlist shape
+    (empty rows, long rows, one cell)."""
+    nl = NETLISTS[name]
+    g = synth.make_signals(nl, S, 4321 + S)
+    got = run_filter(ctx, nl, g, spec=gift.make_spec(schedule=schedule))
+    gift.gift_ctx_device_status(ctx)
+    _, _, ref = oracle.run(nl, g.reshape(nl.num_cells, -1))
+    assert rel_err(got, ref.reshape(g.shape), g).max() <= RTOL
+    fx = nl.is_fixed.astype(bool)
+    np.testing.assert_array_equal(got[fx], g[fx])
 
 
 @pytest.mark.parametrize("terms,norm,reimpose", [
@@ -253,6 +278,10 @@ def test_invalid_filter_args(ctx):
             gift.gift_filter(ctx, h, g, g, None)  # overlap
         with pytest.raises(gift.GiftError):
             gift.gift_filter(ctx, h, g, out, None, num_signals=0)
+        for bad in (1, 2, 3, 404 + 1, 800 + 16, 216 + 100, 1161, 1003, 1032):
+            with pytest.raises(gift.GiftError) as e:
+                gift.gift_filter(ctx, h, g, out, gift.make_spec(schedule=bad))
+            assert e.value.status == gift.GIFT_ERR_INVALID
     finally:
         gift.gift_graph_free(h)
 
