@@ -192,6 +192,33 @@ GIFT_API void gift_graph_free_async(gift_graph *graph, void *stream);
 GIFT_API gift_status gift_filter(gift_ctx *ctx, const gift_graph *graph, const gift_filter_spec *spec,
                         const float *g_in, int32_t num_signals, float *g_out, int32_t mem, void *stream);
 
+/* ---- filter without device allocation ------------------------------------
+ * The paper has no counterpart to this entry point; it serves callers that
+ * cannot allocate device memory while they filter (a fixed memory budget set
+ * aside in advance, real-time loops that must not allocate or fail to, or
+ * hosts that own the allocator).
+ *
+ * Same result as gift_filter for DEVICE buffers g_in / g_out ([N][S][2]
+ * float32, 8-byte aligned, not overlapping), but every scratch buffer comes
+ * from one fixed device array of GIFT_NOALLOC_SCRATCH_BYTES, allocated when
+ * the library is loaded and held by every GPU that loads it until the
+ * process exits.  The call allocates nothing: no cudaMalloc, no cudaFree, no
+ * allocating library routine.  A graph/signal that needs more scratch
+ * (about 4 + 2 x (chains with power >= 2) times N x S x 8 bytes) is rejected
+ * with GIFT_ERR_INVALID and a message giving both sizes.
+ *
+ * The first call on a device looks up the array's device address (once per
+ * device); make that first call before any stream capture.  Every call uses
+ * the same array, so calls whose work overlaps on the GPU (other streams,
+ * other threads, other contexts of the process) race and corrupt each other;
+ * serialise them.  Each call rewrites all scratch it reads before reading it,
+ * so nothing needs clearing between calls.  The kernel shape is the
+ * autotuner's cached choice for this graph shape if an earlier gift_filter
+ * call made one, else a fixed default. */
+#define GIFT_NOALLOC_SCRATCH_BYTES (64u << 20)
+GIFT_API gift_status gift_filter_noalloc(gift_ctx *ctx, const gift_graph *graph, const gift_filter_spec *spec,
+                                         const float *g_in, int32_t num_signals, float *g_out, void *stream);
+
 /* ---- HPWL -----------------------------------------------------------------
  * out[s] = sum over nets of (max x - min x) + (max y - min y) of signal s, pin
  * locations = cell locations of xy [N][S][2] (memory `mem`).  Per-net extents

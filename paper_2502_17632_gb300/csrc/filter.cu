@@ -547,4 +547,129 @@ void filter_impl(gift_ctx *ctx, const gift_graph *cg, const gift_filter_spec *sp
     }
 }
 
+// ---------------------------------------------------------------------------
+// Filter on caller-provided scratch (see noalloc.cu): the same sweeps as
+// filter_impl, with every intermediate buffer carved from `scratch` and no
+// device allocation.  The kernel shape is the autotuner's cached choice for
+// this graph shape when one exists and needs no allocation, else row groups.
+size_t filter_scratch_bytes(const gift_graph *g, const gift_filter_spec *spec, int S) {
+    std::vector<float> sigmas;
+    std::vector<int> L;
+    for (int t = 0; t < spec->num_terms; ++t) {
+        size_t c = 0;
+        while (c < sigmas.size() && sigmas[c] != spec->term[t].sigma) ++c;
+        if (c == sigmas.size()) {
+            sigmas.push_back(spec->term[t].sigma);
+            L.push_back(0);
+        }
+        L[c] = std::max(L[c], spec->term[t].power);
+    }
+    const size_t sig = sizeof(float) * (size_t)g->n * 2 * S;
+    size_t bytes = sig;                                         // accumulator
+    for (int l : L) bytes += l >= 2 ? 2 * sig : 0;              // ping-pong inputs
+    bytes += sigmas.size() * ((sizeof(float) * g->n + 255) / 256 * 256);  // scale vectors
+    bytes += (sizeof(float2) * g->n + 255) / 256 * 256;         // packed first-sweep scales
+    return bytes + 256 * (8 + 2 * sigmas.size());               // alignment slack
+}
+
+__global__ void k_scale_into(int64_t n, const double *__restrict__ d, double sigma, int norm, float *__restrict__ out) {
+    for (int64_t i = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; i < n; i += (int64_t)gridDim.x * blockDim.x) {
+        double t = d[i] + sigma;
+        out[i] = norm == GIFT_NORM_SYM ? (float)(1.0 / sqrt(t)) : (float)(1.0 / t);
+    }
+}
+
+void filter_on_scratch(gift_ctx *ctx, const gift_graph *g, const gift_filter_spec *spec, const float *g_in, int S,
+                       float *g_out, void *scratch, size_t scratch_bytes, cudaStream_t st) {
+    GIFT_REQUIRE(S >= 1, "gift_filter_noalloc: num_signals must be >= 1");
+    GIFT_REQUIRE(g_in && g_out, "gift_filter_noalloc: NULL signal pointer");
+    GIFT_REQUIRE(spec->num_terms >= 1 && spec->num_terms <= GIFT_MAX_TERMS,
+                 "gift_filter_noalloc: num_terms out of range");
+    GIFT_REQUIRE(spec->norm == GIFT_NORM_SYM || spec->norm == GIFT_NORM_RW, "gift_filter_noalloc: unknown norm");
+    GIFT_REQUIRE(spec->reimpose_fixed == 0 || spec->reimpose_fixed == 1,
+                 "gift_filter_noalloc: reimpose_fixed is 0 or 1");
+    const int64_t N = g->n;
+    const int32_t K = 2 * S;
+    const size_t sig_bytes = sizeof(float) * (size_t)N * K;
+    GIFT_REQUIRE(!ranges_overlap(g_in, sig_bytes, g_out, sig_bytes), "gift_filter_noalloc: g_in and g_out overlap");
+    Plan p;
+    p.g = g;
+    p.K = K;
+    p.reimpose = spec->reimpose_fixed;
+    for (int t = 0; t < spec->num_terms; ++t) {
+        const gift_term &tm = spec->term[t];
+        GIFT_REQUIRE(std::isfinite(tm.sigma) && tm.sigma > 0.f, "gift_filter_noalloc: sigma must be finite and > 0");
+        GIFT_REQUIRE(tm.power >= 1 && tm.power <= 64, "gift_filter_noalloc: power must be in [1, 64]");
+        GIFT_REQUIRE(std::isfinite(tm.alpha), "gift_filter_noalloc: alpha must be finite");
+        Chain *c = nullptr;
+        for (auto &x : p.chains)
+            if (x.sigma == tm.sigma) c = &x;
+        if (!c) {
+            p.chains.push_back(Chain{});
+            c = &p.chains.back();
+            c->sigma = tm.sigma;
+        }
+        c->L = std::max(c->L, tm.power);
+        c->alpha_at[tm.power] += tm.alpha;
+        c->has_at[tm.power] = true;
+    }
+    p.Lmax = 0;
+    for (auto &c : p.chains) p.Lmax = std::max(p.Lmax, c.L);
+    GIFT_REQUIRE(filter_scratch_bytes(g, spec, S) <= scratch_bytes,
+                 "gift_filter_noalloc: graph and signal need more scratch than the fixed no-alloc area");
+    const bool al16 = (reinterpret_cast<uintptr_t>(g_in) % 16 == 0) && (reinterpret_cast<uintptr_t>(g_out) % 16 == 0);
+    const bool al8 = (reinterpret_cast<uintptr_t>(g_in) % 8 == 0) && (reinterpret_cast<uintptr_t>(g_out) % 8 == 0);
+    GIFT_REQUIRE(al8, "gift_filter_noalloc: device signal pointers must be 8-byte aligned");
+    p.vec = (K % 4 == 0 && al16) ? 4 : 2;
+    p.din = g_in;
+    p.dout = g_out;
+
+    // carve the scratch
+    unsigned char *cur = static_cast<unsigned char *>(scratch);
+    auto take = [&](size_t bytes) {
+        void *q = cur;
+        cur += (bytes + 255) / 256 * 256;
+        return q;
+    };
+    p.acc = static_cast<float *>(take(sig_bytes));
+    p.X.assign(p.chains.size(), {nullptr, nullptr});
+    for (size_t c = 0; c < p.chains.size(); ++c)
+        if (p.chains[c].L >= 2) {
+            p.X[c][0] = static_cast<float *>(take(sig_bytes));
+            p.X[c][1] = static_cast<float *>(take(sig_bytes));
+        }
+    p.sc.resize(p.chains.size());
+    const int grid = (int)std::max<int64_t>(1, std::min<int64_t>(ceil_div(N, 256), (int64_t)ctx->num_sms * 8));
+    for (size_t c = 0; c < p.chains.size(); ++c) {
+        float *v = static_cast<float *>(take(sizeof(float) * N));
+        k_scale_into<<<grid, 256, 0, st>>>(N, g->degree, (double)p.chains[c].sigma, spec->norm, v);
+        check_launch("k_scale_into");
+        p.sc[c].sigma = p.chains[c].sigma;
+        p.sc[c].norm = spec->norm;
+        p.sc[c].post = v;
+        p.sc[c].pre = spec->norm == GIFT_NORM_SYM ? v : nullptr;
+    }
+    p.gpre2 = nullptr;
+    if (p.chains.size() >= 2 && p.sc[0].pre && p.sc[1].pre) {
+        float2 *v = static_cast<float2 *>(take(sizeof(float2) * N));
+        k_pack2<<<grid, 256, 0, st>>>(N, p.sc[0].pre, p.sc[1].pre, v);
+        check_launch("k_pack2");
+        p.gpre2 = v;
+    }
+    p.counters = nullptr;
+    p.ncounters = 0;
+
+    Shape shape{0, 4, 8};
+    {
+        std::lock_guard<std::mutex> lk(ctx->tune_mu);
+        auto it = ctx->tuned.find(tune_key(g, p.vec, K, p));
+        if (it != ctx->tuned.end()) {
+            const Shape t = it->second;
+            const int rps = t.family == 3 ? 32 / (sell_width(p, t.a) / p.vec) : 0;
+            if (t.family == 0 || t.family == 1 || (t.family == 3 && g->sell.rps == rps)) shape = t;
+        }
+    }
+    run_sweeps(ctx, p, shape, st);
+}
+
 }  // namespace gift

@@ -215,6 +215,9 @@ void release_sell(gift_graph *g, cudaStream_t st);
 void filter_impl(gift_ctx *ctx, const gift_graph *g, const gift_filter_spec *spec, const float *g_in, int S,
                  float *g_out, int mem, cudaStream_t st);
 gift_graph::Scale graph_scale(gift_ctx *ctx, gift_graph *g, float sigma, int norm, cudaStream_t st);
+size_t filter_scratch_bytes(const gift_graph *g, const gift_filter_spec *spec, int S);
+void filter_on_scratch(gift_ctx *ctx, const gift_graph *g, const gift_filter_spec *spec, const float *g_in, int S,
+                       float *g_out, void *scratch, size_t scratch_bytes, cudaStream_t st);
 // hpwl.cu
 void hpwl_impl(gift_ctx *ctx, const gift_graph *g, const float *xy, int S, double *out, int mem, cudaStream_t st);
 }  // namespace gift

@@ -97,6 +97,7 @@ def load(build_if_missing: bool = True):
         "gift_graph_free_async": (None, [P, P]),
         "gift_filter": (I32, [P, P, P, P, I32, P, I32, P]),
         "gift_hpwl": (I32, [P, P, P, I32, P, I32, P]),
+        "gift_filter_noalloc": (I32, [P, P, P, P, I32, P, P]),
         "gift_last_error": (C.c_char_p, []),
     }
     for name, (res, args) in sig.items():
@@ -253,6 +254,24 @@ def gift_filter(ctx, graph, g_in, g_out, spec: gift_filter_spec | None = None, n
     _check(load().gift_filter(ctx, graph, C.byref(spec) if spec is not None else None, pi, S, po, mem,
                               _stream(stream)))
     return g_out
+
+
+def gift_filter_noalloc(ctx, graph, g_in, g_out, spec: gift_filter_spec | None = None,
+                        num_signals: int | None = None, stream=None):
+    """gift_filter on device tensors without any device allocation: scratch comes
+    from the library's fixed GIFT_NOALLOC_SCRATCH_BYTES area (for callers that
+    cannot allocate while filtering).  Overlapping calls race on that area."""
+    pi, mem = _ptr(g_in)
+    po, mem_o = _ptr(g_out)
+    if mem != GIFT_MEM_DEVICE or mem_o != GIFT_MEM_DEVICE:
+        raise ValueError("gift_filter_noalloc takes device tensors")
+    S = num_signals if num_signals is not None else int(g_in.shape[1])
+    _check(load().gift_filter_noalloc(ctx, graph, C.byref(spec) if spec is not None else None, pi, S, po,
+                                      _stream(stream)))
+    return g_out
+
+
+GIFT_NOALLOC_SCRATCH_BYTES = 64 << 20
 
 
 def gift_hpwl(ctx, graph, xy, num_signals: int | None = None, stream=None) -> np.ndarray:
