@@ -142,9 +142,12 @@ GIFT_API gift_status gift_ctx_set_profiling(gift_ctx *ctx, int32_t enable);
 GIFT_API int32_t gift_ctx_kernel_stats(gift_ctx *ctx, gift_kernel_stat *out, int32_t max);
 GIFT_API void gift_ctx_reset_stats(gift_ctx *ctx);
 
-/* Schedule code the last gift_filter call on this context ran with (the
- * autotuner's choice when spec->schedule was 0); 0 before the first call. */
-GIFT_API int32_t gift_ctx_last_schedule(gift_ctx *ctx);
+/* Schedule codes the last gift_filter call on this context ran with (the
+ * autotuner's choices when spec->schedule was 0), one per launch kind:
+ * [0] two chains, first sweep; [1] two chains, later sweeps; [2] one chain,
+ * first sweep; [3] one chain, later sweeps (0 = kind not used).  per_kind
+ * may be NULL.  Returns the code of the last kind used, 0 before any call. */
+GIFT_API int32_t gift_ctx_last_schedule(gift_ctx *ctx, int32_t *per_kind);
 
 /* Synchronises the device and reports whether a kernel of this context hit
  * the limit of one of its bounded waits since the last check:

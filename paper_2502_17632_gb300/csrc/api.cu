@@ -128,8 +128,13 @@ gift_status gift_ctx_create(int32_t device, gift_ctx **out) {
             GIFT_CUDA(cudaMemPoolSetAttribute(ctx->pool, cudaMemPoolAttrReleaseThreshold, &keep));
             GIFT_CUDA(cudaMalloc(&ctx->dev_error, sizeof(int32_t)));
             GIFT_CUDA(cudaMemset(ctx->dev_error, 0, sizeof(int32_t)));
+            std::vector<double> wt(kWeightTable + 1, 0.0);
+            for (int m = 2; m <= kWeightTable; ++m) wt[m] = 2.0 / (double)m;  // weight rule after Eq. 4
+            GIFT_CUDA(cudaMalloc(&ctx->wtab, sizeof(double) * wt.size()));
+            GIFT_CUDA(cudaMemcpy(ctx->wtab, wt.data(), sizeof(double) * wt.size(), cudaMemcpyHostToDevice));
         } catch (...) {
             if (ctx->dev_error) cudaFree(ctx->dev_error);
+            if (ctx->wtab) cudaFree(ctx->wtab);
             if (ctx->pool) cudaMemPoolDestroy(ctx->pool);
             delete ctx;
             throw;
@@ -145,6 +150,7 @@ void gift_ctx_destroy(gift_ctx *ctx) {
     collect_timings(ctx, true);
     for (auto e : ctx->event_pool) cudaEventDestroy(e);
     if (ctx->dev_error) cudaFree(ctx->dev_error);
+    if (ctx->wtab) cudaFree(ctx->wtab);
     if (ctx->pool) cudaMemPoolDestroy(ctx->pool);
     delete ctx;
 }
@@ -183,7 +189,14 @@ void gift_ctx_reset_stats(gift_ctx *ctx) {
     ctx->records.clear();
 }
 
-int32_t gift_ctx_last_schedule(gift_ctx *ctx) { return ctx ? ctx->last_schedule : 0; }
+int32_t gift_ctx_last_schedule(gift_ctx *ctx, int32_t *per_kind) {
+    if (!ctx) return 0;
+    if (per_kind)
+        for (int k = 0; k < 4; ++k) per_kind[k] = ctx->last_schedules[k];
+    for (int k = 3; k >= 0; --k)
+        if (ctx->last_schedules[k]) return ctx->last_schedules[k];
+    return 0;
+}
 
 gift_status gift_ctx_device_status(gift_ctx *ctx) {
     return guarded([&] {

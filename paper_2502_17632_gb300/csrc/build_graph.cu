@@ -81,10 +81,12 @@ __device__ __forceinline__ void for_each_pin_of_nets(int32_t E, const int64_t *_
 }
 
 // ------------------------------------------------------------------ count
-__global__ void k_net_weights(int32_t E, const int64_t *__restrict__ net_ptr, double *__restrict__ wnet) {
+__global__ void k_net_weights(int32_t E, const int64_t *__restrict__ net_ptr, const double *__restrict__ wtab,
+                              double *__restrict__ wnet) {
     for (int64_t e = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; e < E; e += (int64_t)gridDim.x * blockDim.x) {
         int64_t m = net_ptr[e + 1] - net_ptr[e];
-        wnet[e] = m >= 2 ? 2.0 / (double)m : 0.0;  // weight rule after Eq. 4
+        // weight rule after Eq. 4: w = 2/M (the table holds the same IEEE quotients)
+        wnet[e] = m < 2 ? 0.0 : (m <= kWeightTable ? wtab[m] : 2.0 / (double)m);
     }
 }
 
@@ -116,15 +118,197 @@ __global__ void k_scatter(int32_t E, const int64_t *__restrict__ net_ptr, const 
     });
 }
 
-// ------------------------------------------------------------------ rows, warp tier
-// One warp per row with at most kWarpCap raw entries.  Rows above that are
-// appended to big_rows for the block tiers.
+// ------------------------------------------------------------------ storage rounding
+// Round-to-nearest-even of an FP64 value to a format with `keep` explicit
+// significand bits and minimum normal exponent `emin`, on the bit pattern.
+__device__ __forceinline__ double rne_to(double v, int keep, int emin) {
+    unsigned long long b = (unsigned long long)__double_as_longlong(v);
+    int ex = (int)((b >> 52) & 0x7ff);
+    if (ex == 0 || ex == 0x7ff) return v;  // zero / FP64 subnormal (tiny) / inf / nan
+    if (ex - 1023 < emin) {                // subnormal in the target: fixed quantum
+        double q = ldexp(1.0, emin - keep);
+        return rint(v / q) * q;
+    }
+    const int drop = 52 - keep;
+    const unsigned long long mask = (1ull << drop) - 1, half = 1ull << (drop - 1);
+    unsigned long long rem = b & mask, kept = b & ~mask;
+    if (rem > half || (rem == half && ((kept >> drop) & 1ull))) kept += 1ull << drop;
+    return __longlong_as_double((long long)kept);
+}
+
+template <typename WT>
+struct Store;
+template <>
+struct Store<float> {
+    __device__ static float put(double v) { return __double2float_rn(rne_to(v, 23, -126)); }
+    __device__ static double get(float w) { return (double)w; }
+};
+template <>
+struct Store<__nv_bfloat16> {
+    __device__ static __nv_bfloat16 put(double v) {
+        float f = __double2float_rn(rne_to(v, 7, -126));  // exact in binary32
+        return __ushort_as_bfloat16((unsigned short)(__float_as_uint(f) >> 16));
+    }
+    __device__ static double get(__nv_bfloat16 w) { return (double)__bfloat162float(w); }
+};
+template <>
+struct Store<__half> {
+    __device__ static __half put(double v) { return __float2half_rn(__double2float_rn(rne_to(v, 10, -14))); }
+    __device__ static double get(__half w) { return (double)__half2float(w); }
+};
+
+// ------------------------------------------------------------------ rows
+// Every tier writes, at the row's raw position: the sorted unique columns,
+// each weight summed in FP64 in increasing net order and rounded once to the
+// storage type; the unique count; and the degree d_i = sum_j A_ij in FP64
+// over the stored weights in column order (Sec. 2.1).
+
+constexpr int kGS = 8;          // lanes per row in the small tier
+constexpr int kSmallCap = 32;   // raw entries of a small row
+constexpr int kSmallThreads = 256;
+constexpr int kSmallGroups = kSmallThreads / kGS;
+
+// Small tier: a group of 8 lanes per row with at most kSmallCap raw entries;
+// the four rows of a warp advance in lockstep (every loop runs to the warp's
+// largest trip count, with per-row predicates) so their memory accesses are
+// issued together.  Keys (neighbour, net) are ranked in shared memory.
+// Longer rows are appended to `wlist` for the warp tier.
+template <typename WT>
+__global__ void __launch_bounds__(kSmallThreads)
+k_rows_small(int32_t N, const int64_t *__restrict__ inc_ptr, const int32_t *__restrict__ inc_net,
+             const int64_t *__restrict__ net_ptr, const int32_t *__restrict__ pin_cell,
+             const double *__restrict__ wnet, const int64_t *__restrict__ raw_ptr, int32_t *__restrict__ out_col,
+             WT *__restrict__ out_val, int32_t *__restrict__ ucount, double *__restrict__ degree,
+             int32_t *__restrict__ wlist, int32_t *__restrict__ wcount) {
+    __shared__ uint64_t keys_all[kSmallGroups][kSmallCap];   // later reused for the stored weights
+    __shared__ uint64_t sorted_all[kSmallGroups][kSmallCap];
+    __shared__ int32_t ofs_all[kSmallGroups][kSmallCap + 1];
+    __shared__ int32_t inet_all[kSmallGroups][kSmallCap];
+    __shared__ int64_t ibase_all[kSmallGroups][kSmallCap];
+    __shared__ int32_t cnt_all[kSmallGroups];
+    const unsigned full = 0xffffffffu;
+    const int g = threadIdx.x / kGS, gl = threadIdx.x % kGS;
+    uint64_t *keys = keys_all[g];
+    uint64_t *srt = sorted_all[g];
+    int32_t *ofs = ofs_all[g];
+    double *rv = reinterpret_cast<double *>(keys_all[g]);
+    constexpr int RPW = 32 / kGS;  // rows per warp
+    const int64_t warp = (blockIdx.x * (int64_t)blockDim.x + threadIdx.x) >> 5;
+    const int64_t nwarps = ((int64_t)gridDim.x * blockDim.x) >> 5;
+    const int gw = (threadIdx.x & 31) / kGS;  // group within the warp
+
+    for (int64_t base = warp * RPW; base < N; base += nwarps * RPW) {  // warp-uniform
+        const int64_t row = base + gw;
+        int64_t rb = 0, rawlen = 0, ib = 0;
+        int ninc = 0;
+        if (row < N) {
+            rb = raw_ptr[row];
+            rawlen = raw_ptr[row + 1] - rb;
+            ib = inc_ptr[row];
+            ninc = (int)(inc_ptr[row + 1] - ib);
+        }
+        const bool small = row < N && rawlen > 0 && rawlen <= kSmallCap;
+        if (gl == 0 && row < N) {
+            if (rawlen > kSmallCap) wlist[atomicAdd(wcount, 1)] = (int32_t)row;
+            if (rawlen == 0) {
+                ucount[row] = 0;
+                degree[row] = 0.0;
+            }
+        }
+        if (!small) ninc = 0;  // ninc <= rawlen: every incidence has M >= 2
+        const int max_ninc = (int)__reduce_max_sync(full, (unsigned)ninc);
+        for (int t0 = 0; t0 < max_ninc; t0 += kGS) {
+            const int t = t0 + gl;
+            if (t < ninc) {
+                const int32_t e = inc_net[ib + t];
+                const int64_t nb = net_ptr[e];
+                inet_all[g][t] = e;
+                ibase_all[g][t] = nb;
+                ofs[t] = (int32_t)(net_ptr[e + 1] - nb);
+            }
+        }
+        __syncwarp();
+        if (gl == 0) {
+            int acc = 0;
+            for (int t = 0; t < ninc; ++t) {
+                const int m = ofs[t];
+                ofs[t] = acc;
+                acc += m;
+            }
+            ofs[ninc] = acc;
+            cnt_all[g] = 0;
+        }
+        __syncwarp();
+        const int total = small ? ofs[ninc] : 0;
+        const int max_total = (int)__reduce_max_sync(full, (unsigned)total);
+        for (int f0 = 0; f0 < max_total; f0 += kGS) {
+            const int f = f0 + gl;
+            if (f < total) {
+                int lo = 0, hi = ninc - 1;  // last incidence whose offset <= f
+                while (lo < hi) {
+                    const int mid = (lo + hi + 1) >> 1;
+                    if (ofs[mid] <= f) lo = mid;
+                    else hi = mid - 1;
+                }
+                const int32_t q = pin_cell[ibase_all[g][lo] + (f - ofs[lo])];
+                if (q != (int32_t)row) keys[atomicAdd(&cnt_all[g], 1)] = make_key(q, inet_all[g][lo]);
+            }
+        }
+        __syncwarp();
+        const int n = small ? cnt_all[g] : 0;
+        const int max_n = (int)__reduce_max_sync(full, (unsigned)n);
+        for (int i0 = 0; i0 < max_n; i0 += kGS) {  // rank sort; equal keys keep their slots' order
+            const int i = i0 + gl;
+            if (i < n) {
+                const uint64_t k = keys[i];
+                int rank = 0;
+                for (int j = 0; j < n; ++j) {
+                    const uint64_t kj = keys[j];
+                    rank += (kj < k) || (kj == k && j < i);
+                }
+                srt[rank] = k;
+            }
+        }
+        __syncwarp();
+        for (int i0 = 0; i0 < max_n; i0 += kGS) {
+            const int i = i0 + gl;
+            if (i < n) {
+                const int32_t c = key_cell(srt[i]);
+                if (i == 0 || key_cell(srt[i - 1]) != c) {
+                    int u = 0;  // run heads before i
+                    for (int j = 1; j <= i; ++j) u += key_cell(srt[j]) != key_cell(srt[j - 1]);
+                    double sum = 0.0;
+                    for (int r = i; r < n && key_cell(srt[r]) == c; ++r) sum += wnet[key_net(srt[r])];
+                    const WT w = Store<WT>::put(sum);
+                    out_col[rb + u] = c;
+                    out_val[rb + u] = w;
+                    rv[u] = Store<WT>::get(w);
+                }
+            }
+        }
+        __syncwarp();
+        if (gl == 0 && small) {
+            int nu = n > 0 ? 1 : 0;
+            for (int j = 1; j < n; ++j) nu += key_cell(srt[j]) != key_cell(srt[j - 1]);
+            double d = 0.0;
+            for (int u = 0; u < nu; ++u) d += rv[u];
+            ucount[row] = nu;
+            degree[row] = d;
+        }
+        __syncwarp();
+    }
+}
+
+// Warp tier: one warp per row of the list with at most kWarpCap raw entries;
+// longer rows are appended to big_rows for the block tiers.
+template <typename WT>
 __global__ void __launch_bounds__(kRowsWarps * 32)
-k_rows_warp(int32_t N, const int64_t *__restrict__ inc_ptr, const int32_t *__restrict__ inc_net,
+k_rows_warp(const int32_t *__restrict__ rows, const int32_t *__restrict__ nrows_p,
+            const int64_t *__restrict__ inc_ptr, const int32_t *__restrict__ inc_net,
             const int64_t *__restrict__ net_ptr, const int32_t *__restrict__ pin_cell,
-            const double *__restrict__ wnet, const int64_t *__restrict__ raw_ptr, int32_t *__restrict__ s_col,
-            double *__restrict__ s_val, int32_t *__restrict__ ucount, int32_t *__restrict__ big_rows,
-            int32_t *__restrict__ big_count) {
+            const double *__restrict__ wnet, const int64_t *__restrict__ raw_ptr, int32_t *__restrict__ out_col,
+            WT *__restrict__ out_val, int32_t *__restrict__ ucount, double *__restrict__ degree,
+            int32_t *__restrict__ big_rows, int32_t *__restrict__ big_count) {
     __shared__ uint64_t keys_all[kRowsWarps][kWarpCap];
     __shared__ int32_t ofs_all[kRowsWarps][33];
     __shared__ int32_t net_all[kRowsWarps][32];
@@ -137,16 +321,14 @@ k_rows_warp(int32_t N, const int64_t *__restrict__ inc_ptr, const int32_t *__res
     const unsigned full = 0xffffffffu;
     const int64_t gw = (blockIdx.x * (int64_t)blockDim.x + threadIdx.x) >> 5;
     const int64_t nw = ((int64_t)gridDim.x * blockDim.x) >> 5;
+    const int nrows = *nrows_p;
 
-    for (int64_t row = gw; row < N; row += nw) {
+    for (int64_t ri = gw; ri < nrows; ri += nw) {
+        const int64_t row = rows[ri];
         const int64_t rbase = raw_ptr[row];
         const int64_t rawlen = raw_ptr[row + 1] - rbase;
         if (rawlen > kWarpCap) {
             if (lane == 0) big_rows[atomicAdd(big_count, 1)] = (int32_t)row;
-            continue;
-        }
-        if (rawlen == 0) {
-            if (lane == 0) ucount[row] = 0;
             continue;
         }
         if (lane == 0) cnt_all[w] = 0;
@@ -222,29 +404,35 @@ k_rows_warp(int32_t N, const int64_t *__restrict__ inc_ptr, const int32_t *__res
             unsigned hm = __ballot_sync(full, head);
             if (head) {
                 int u = uniq + __popc(hm & ((1u << lane) - 1));
-                double s = 0.0;
-                for (int r = t; r < n && key_cell(keys[r]) == c; ++r) s += wnet[key_net(keys[r])];
-                s_col[rbase + u] = c;
-                s_val[rbase + u] = s;
+                double sum = 0.0;
+                for (int r = t; r < n && key_cell(keys[r]) == c; ++r) sum += wnet[key_net(keys[r])];
+                out_col[rbase + u] = c;
+                out_val[rbase + u] = Store<WT>::put(sum);
             }
             uniq += __popc(hm);
         }
-        if (lane == 0) ucount[row] = uniq;
+        __syncwarp();
+        if (lane == 0) {
+            double d = 0.0;
+            for (int u = 0; u < uniq; ++u) d += Store<WT>::get(out_val[rbase + u]);
+            ucount[row] = uniq;
+            degree[row] = d;
+        }
         __syncwarp();
     }
 }
 
-// ------------------------------------------------------------------ rows, block tiers
-// One block per long row.  GLOBAL_KEYS: keys live in a per-block global scratch
-// of `gcap` entries (rows beyond the shared-memory capacity); else in dynamic
-// shared memory of kBlockCap entries.
-template <bool GLOBAL_KEYS>
+// Block tiers: one block per long row.  GLOBAL_KEYS: keys live in a per-block
+// global scratch of `gcap` entries (rows beyond the shared-memory capacity);
+// else in dynamic shared memory of kBlockCap entries.
+template <typename WT, bool GLOBAL_KEYS>
 __global__ void __launch_bounds__(kBlockThreads)
 k_rows_block(const int64_t *__restrict__ inc_ptr, const int32_t *__restrict__ inc_net,
              const int64_t *__restrict__ net_ptr, const int32_t *__restrict__ pin_cell,
-             const double *__restrict__ wnet, const int64_t *__restrict__ raw_ptr, int32_t *__restrict__ s_col,
-             double *__restrict__ s_val, int32_t *__restrict__ ucount, const int32_t *__restrict__ big_rows,
-             const int32_t *__restrict__ big_count, uint64_t *__restrict__ gkeys, int64_t gcap) {
+             const double *__restrict__ wnet, const int64_t *__restrict__ raw_ptr, int32_t *__restrict__ out_col,
+             WT *__restrict__ out_val, int32_t *__restrict__ ucount, double *__restrict__ degree,
+             const int32_t *__restrict__ big_rows, const int32_t *__restrict__ big_count,
+             uint64_t *__restrict__ gkeys, int64_t gcap) {
     extern __shared__ uint64_t smem_keys[];
     __shared__ int s_cnt;
     __shared__ int s_warp[kBlockThreads / 32];
@@ -307,10 +495,10 @@ k_rows_block(const int64_t *__restrict__ inc_ptr, const int32_t *__restrict__ in
             for (int q = 0; q < wid; ++q) before += s_warp[q];
             if (head) {
                 int u = before + __popc(hm & ((1u << lane) - 1));
-                double s = 0.0;
-                for (int rr = t; rr < n && key_cell(keys[rr]) == c; ++rr) s += wnet[key_net(keys[rr])];
-                s_col[rbase + u] = c;
-                s_val[rbase + u] = s;
+                double sum = 0.0;
+                for (int rr = t; rr < n && key_cell(keys[rr]) == c; ++rr) sum += wnet[key_net(keys[rr])];
+                out_col[rbase + u] = c;
+                out_val[rbase + u] = Store<WT>::put(sum);
             }
             __syncthreads();
             if (tid == 0) {
@@ -320,69 +508,39 @@ k_rows_block(const int64_t *__restrict__ inc_ptr, const int32_t *__restrict__ in
             }
             __syncthreads();
         }
-        if (tid == 0) ucount[row] = s_uniq;
+        if (tid == 0) {
+            double d = 0.0;
+            for (int u = 0; u < s_uniq; ++u) d += Store<WT>::get(out_val[rbase + u]);
+            ucount[row] = s_uniq;
+            degree[row] = d;
+        }
         __syncthreads();
     }
 }
 
-// ------------------------------------------------------------------ storage rounding
-// Round-to-nearest-even of an FP64 value to a format with `keep` explicit
-// significand bits and minimum normal exponent `emin`, on the bit pattern.
-__device__ __forceinline__ double rne_to(double v, int keep, int emin) {
-    unsigned long long b = (unsigned long long)__double_as_longlong(v);
-    int ex = (int)((b >> 52) & 0x7ff);
-    if (ex == 0 || ex == 0x7ff) return v;  // zero / FP64 subnormal (tiny) / inf / nan
-    if (ex - 1023 < emin) {                // subnormal in the target: fixed quantum
-        double q = ldexp(1.0, emin - keep);
-        return rint(v / q) * q;
-    }
-    const int drop = 52 - keep;
-    const unsigned long long mask = (1ull << drop) - 1, half = 1ull << (drop - 1);
-    unsigned long long rem = b & mask, kept = b & ~mask;
-    if (rem > half || (rem == half && ((kept >> drop) & 1ull))) kept += 1ull << drop;
-    return __longlong_as_double((long long)kept);
-}
-
+// Compaction: 8 lanes per row copy its entries to their CSR position; the
+// group's first lane writes the scales of the paper's two self-loop weights
+// (sigma = 2, 4; Eq. 16) from the degree.
 template <typename WT>
-struct Store;
-template <>
-struct Store<float> {
-    __device__ static float put(double v) { return __double2float_rn(rne_to(v, 23, -126)); }
-    __device__ static double get(float w) { return (double)w; }
-};
-template <>
-struct Store<__nv_bfloat16> {
-    __device__ static __nv_bfloat16 put(double v) {
-        float f = __double2float_rn(rne_to(v, 7, -126));  // exact in binary32
-        return __ushort_as_bfloat16((unsigned short)(__float_as_uint(f) >> 16));
-    }
-    __device__ static double get(__nv_bfloat16 w) { return (double)__bfloat162float(w); }
-};
-template <>
-struct Store<__half> {
-    __device__ static __half put(double v) { return __float2half_rn(__double2float_rn(rne_to(v, 10, -14))); }
-    __device__ static double get(__half w) { return (double)__half2float(w); }
-};
-
-// One thread per row: copy the row's sums, rounded once, and sum the stored
-// weights in column order in FP64 (the degree, Sec. 2.1).
-template <typename WT>
-__global__ void k_compact(int32_t N, const int64_t *__restrict__ raw_ptr, const int64_t *__restrict__ row_ptr,
-                          const int32_t *__restrict__ s_col, const double *__restrict__ s_val,
-                          int32_t *__restrict__ col, WT *__restrict__ val, double *__restrict__ degree,
-                          int32_t *__restrict__ max_row) {
+__global__ void k_copy_rows(int32_t N, const int64_t *__restrict__ raw_ptr, const int64_t *__restrict__ row_ptr,
+                            const int32_t *__restrict__ out_col, const WT *__restrict__ out_val,
+                            int32_t *__restrict__ col, WT *__restrict__ val, const double *__restrict__ degree,
+                            int32_t *__restrict__ max_row, float *__restrict__ s2, float *__restrict__ s4) {
+    const int g = (blockIdx.x * blockDim.x + threadIdx.x) / kGS, gl = threadIdx.x % kGS;
+    const int64_t ng = ((int64_t)gridDim.x * blockDim.x) / kGS;
     int best = 0;
-    for (int64_t i = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; i < N; i += (int64_t)gridDim.x * blockDim.x) {
+    for (int64_t i = g; i < N; i += ng) {
         const int64_t src = raw_ptr[i], dst = row_ptr[i], n = row_ptr[i + 1] - dst;
-        double d = 0.0;
-        for (int64_t t = 0; t < n; ++t) {
-            WT w = Store<WT>::put(s_val[src + t]);
-            col[dst + t] = s_col[src + t];
-            val[dst + t] = w;
-            d += Store<WT>::get(w);
+        for (int64_t t = gl; t < n; t += kGS) {
+            col[dst + t] = out_col[src + t];
+            val[dst + t] = out_val[src + t];
         }
-        degree[i] = d;
-        best = max(best, (int)n);
+        if (gl == 0) {
+            const double d = degree[i];
+            s2[i] = scale_value(d, 2.0, GIFT_NORM_SYM);
+            s4[i] = scale_value(d, 4.0, GIFT_NORM_SYM);
+            best = max(best, (int)n);
+        }
     }
     for (int o = 16; o; o >>= 1) best = max(best, __shfl_xor_sync(0xffffffffu, best, o));
     if ((threadIdx.x & 31) == 0 && best) atomicMax(max_row, best);
@@ -494,7 +652,7 @@ void build_graph_impl(gift_ctx *ctx, const gift_netlist *nl, const gift_build_op
     GIFT_CUDA(cudaMemsetAsync(rawlen.p, 0, sizeof(int64_t) * N, st));
     if (E > 0) {
         LaunchTimer lt(ctx, st, "build.count", 16.0 * (E + 1) + 4.0 * P + 12.0 * N, 2);
-        k_net_weights<<<grid_for(ctx, E, 256), 256, 0, st>>>(E, g->net_ptr, wnet.as<double>());
+        k_net_weights<<<grid_for(ctx, E, 256), 256, 0, st>>>(E, g->net_ptr, ctx->wtab, wnet.as<double>());
         k_count<<<grid_for(ctx, E, 256), 256, 0, st>>>(E, g->net_ptr, g->pin_cell, cnt.as<int32_t>(),
                                                          rawlen.as<unsigned long long>());
         check_launch("k_count");
@@ -531,47 +689,69 @@ void build_graph_impl(gift_ctx *ctx, const gift_netlist *nl, const gift_build_op
         check_launch("k_scatter");
     }
 
-    // ---- per-row expansion, sort, duplicate sums
-    DevBuf s_col(ctx, sizeof(int32_t) * std::max<int64_t>(nraw, 1), st);
-    DevBuf s_val(ctx, sizeof(double) * std::max<int64_t>(nraw, 1), st);
+    // ---- per-row expansion, sort, duplicate sums, rounding, degrees
+    const size_t wsz = g->weight_dtype == GIFT_WEIGHT_F32 ? 4 : 2;
+    DevBuf out_col(ctx, sizeof(int32_t) * std::max<int64_t>(nraw, 1), st);
+    DevBuf out_val(ctx, wsz * std::max<int64_t>(nraw, 1), st);
     DevBuf ucount(ctx, sizeof(int32_t) * N, st);
+    DevBuf wlist(ctx, sizeof(int32_t) * N, st);
     DevBuf big_rows(ctx, sizeof(int32_t) * N, st);
-    DevBuf big_count(ctx, sizeof(int32_t), st);
-    GIFT_CUDA(cudaMemsetAsync(big_count.p, 0, sizeof(int32_t), st));
-    {
-        LaunchTimer lt(ctx, st, "build.rows",
-                       16.0 * N + 4.0 * ninc + 16.0 * ninc + 12.0 * nraw + 12.0 * nraw + 4.0 * N);
-        k_rows_warp<<<grid_for(ctx, (int64_t)N * 32, kRowsWarps * 32, 6), kRowsWarps * 32, 0, st>>>(
-            N, inc_ptr.as<int64_t>(), inc_net.as<int32_t>(), g->net_ptr, g->pin_cell, wnet.as<double>(),
-            raw_ptr.as<int64_t>(), s_col.as<int32_t>(), s_val.as<double>(), ucount.as<int32_t>(),
-            big_rows.as<int32_t>(), big_count.as<int32_t>());
-        check_launch("k_rows_warp");
-    }
-    if (maxraw > kWarpCap) {
-        LaunchTimer lt(ctx, st, "build.rows_block", 0.0);
-        const size_t smem = sizeof(uint64_t) * kBlockCap;
-        GIFT_CUDA(cudaFuncSetAttribute(k_rows_block<false>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem));
-        k_rows_block<false><<<ctx->num_sms, kBlockThreads, smem, st>>>(
-            inc_ptr.as<int64_t>(), inc_net.as<int32_t>(), g->net_ptr, g->pin_cell, wnet.as<double>(),
-            raw_ptr.as<int64_t>(), s_col.as<int32_t>(), s_val.as<double>(), ucount.as<int32_t>(),
-            big_rows.as<int32_t>(), big_count.as<int32_t>(), nullptr, 0);
-        check_launch("k_rows_block");
-    }
+    DevBuf counts(ctx, sizeof(int32_t) * 2, st);  // [0] warp-tier rows, [1] block-tier rows
+    GIFT_CUDA(cudaMemsetAsync(counts.p, 0, sizeof(int32_t) * 2, st));
+    g->degree = (double *)dev_alloc(ctx, sizeof(double) * N, st);
     DevBuf gkeys;
+    int64_t gcap = 0;
     if (maxraw > kBlockCap) {
-        LaunchTimer lt(ctx, st, "build.rows_global", 0.0);
-        int64_t cap = 2;
-        while (cap < maxraw) cap <<= 1;
-        const int blocks = ctx->num_sms;
-        gkeys = DevBuf(ctx, sizeof(uint64_t) * cap * blocks, st);
-        k_rows_block<true><<<blocks, kBlockThreads, 0, st>>>(
-            inc_ptr.as<int64_t>(), inc_net.as<int32_t>(), g->net_ptr, g->pin_cell, wnet.as<double>(),
-            raw_ptr.as<int64_t>(), s_col.as<int32_t>(), s_val.as<double>(), ucount.as<int32_t>(),
-            big_rows.as<int32_t>(), big_count.as<int32_t>(), gkeys.as<uint64_t>(), cap);
-        check_launch("k_rows_block<global>");
+        gcap = 2;
+        while (gcap < maxraw) gcap <<= 1;
+        gkeys = DevBuf(ctx, sizeof(uint64_t) * gcap * ctx->num_sms, st);
     }
+    auto rows = [&](auto tag) {
+        using WT = decltype(tag);
+        WT *ov = out_val.as<WT>();
+        int32_t *wc = counts.as<int32_t>(), *bc = counts.as<int32_t>() + 1;
+        {
+            LaunchTimer lt(ctx, st, "build.rows",
+                           16.0 * N + 4.0 * ninc + 16.0 * ninc + 4.0 * nraw + (4.0 + wsz) * nraw + 12.0 * N);
+            k_rows_small<WT><<<grid_for(ctx, (int64_t)N * kGS, kSmallThreads, 8), kSmallThreads, 0, st>>>(
+                N, inc_ptr.as<int64_t>(), inc_net.as<int32_t>(), g->net_ptr, g->pin_cell, wnet.as<double>(),
+                raw_ptr.as<int64_t>(), out_col.as<int32_t>(), ov, ucount.as<int32_t>(), g->degree,
+                wlist.as<int32_t>(), wc);
+            check_launch("k_rows_small");
+        }
+        if (maxraw > kSmallCap) {
+            LaunchTimer lt(ctx, st, "build.rows_warp", 0.0);
+            k_rows_warp<WT><<<ctx->num_sms * 6, kRowsWarps * 32, 0, st>>>(
+                wlist.as<int32_t>(), wc, inc_ptr.as<int64_t>(), inc_net.as<int32_t>(), g->net_ptr, g->pin_cell,
+                wnet.as<double>(), raw_ptr.as<int64_t>(), out_col.as<int32_t>(), ov, ucount.as<int32_t>(),
+                g->degree, big_rows.as<int32_t>(), bc);
+            check_launch("k_rows_warp");
+        }
+        if (maxraw > kWarpCap) {
+            LaunchTimer lt(ctx, st, "build.rows_block", 0.0);
+            const size_t smem = sizeof(uint64_t) * kBlockCap;
+            GIFT_CUDA(cudaFuncSetAttribute(k_rows_block<WT, false>, cudaFuncAttributeMaxDynamicSharedMemorySize,
+                                           (int)smem));
+            k_rows_block<WT, false><<<ctx->num_sms, kBlockThreads, smem, st>>>(
+                inc_ptr.as<int64_t>(), inc_net.as<int32_t>(), g->net_ptr, g->pin_cell, wnet.as<double>(),
+                raw_ptr.as<int64_t>(), out_col.as<int32_t>(), ov, ucount.as<int32_t>(), g->degree,
+                big_rows.as<int32_t>(), bc, nullptr, 0);
+            check_launch("k_rows_block");
+        }
+        if (maxraw > kBlockCap) {
+            LaunchTimer lt(ctx, st, "build.rows_global", 0.0);
+            k_rows_block<WT, true><<<ctx->num_sms, kBlockThreads, 0, st>>>(
+                inc_ptr.as<int64_t>(), inc_net.as<int32_t>(), g->net_ptr, g->pin_cell, wnet.as<double>(),
+                raw_ptr.as<int64_t>(), out_col.as<int32_t>(), ov, ucount.as<int32_t>(), g->degree,
+                big_rows.as<int32_t>(), bc, gkeys.as<uint64_t>(), gcap);
+            check_launch("k_rows_block<global>");
+        }
+    };
+    if (g->weight_dtype == GIFT_WEIGHT_F32) rows(float{});
+    else if (g->weight_dtype == GIFT_WEIGHT_BF16) rows(__nv_bfloat16{});
+    else rows(__half{});
 
-    // ---- row_ptr, compaction with storage rounding, degrees
+    // ---- row_ptr, compaction, default scales
     g->row_ptr = (int64_t *)dev_alloc(ctx, sizeof(int64_t) * (N + 1), st);
     {
         LaunchTimer lt(ctx, st, "build.scan", 4.0 * N + 8.0 * (N + 1), 3);
@@ -581,33 +761,36 @@ void build_graph_impl(gift_ctx *ctx, const gift_netlist *nl, const gift_build_op
     GIFT_CUDA(cudaMemcpyAsync(&nnz, g->row_ptr + N, sizeof(int64_t), cudaMemcpyDeviceToHost, st));
     GIFT_CUDA(cudaStreamSynchronize(st));
     g->nnz = nnz;
-    const size_t wsz = g->weight_dtype == GIFT_WEIGHT_F32 ? 4 : 2;
     g->col = (int32_t *)dev_alloc(ctx, sizeof(int32_t) * std::max<int64_t>(nnz, 1), st);
     g->val = dev_alloc(ctx, wsz * std::max<int64_t>(nnz, 1), st);
-    g->degree = (double *)dev_alloc(ctx, sizeof(double) * N, st);
+    float *s2 = (float *)dev_alloc(ctx, sizeof(float) * N, st);
+    g->scales.push_back(gift_graph::Scale{2.0f, GIFT_NORM_SYM, s2, s2});
+    float *s4 = (float *)dev_alloc(ctx, sizeof(float) * N, st);
+    g->scales.push_back(gift_graph::Scale{4.0f, GIFT_NORM_SYM, s4, s4});
     GIFT_CUDA(cudaMemsetAsync(flag.p, 0, sizeof(int) * 4, st));
     {
-        LaunchTimer lt(ctx, st, "build.compact", 16.0 * N + 12.0 * nnz + (4.0 + wsz) * nnz + 8.0 * N);
-        const int grid = grid_for(ctx, N, 256);
+        LaunchTimer lt(ctx, st, "build.compact", 24.0 * N + 2.0 * (4.0 + wsz) * nnz);
+        const int grid = grid_for(ctx, (int64_t)N * kGS, 256);
         if (g->weight_dtype == GIFT_WEIGHT_F32)
-            k_compact<float><<<grid, 256, 0, st>>>(N, raw_ptr.as<int64_t>(), g->row_ptr, s_col.as<int32_t>(),
-                                                    s_val.as<double>(), g->col, (float *)g->val, g->degree,
-                                                    flag.as<int32_t>());
+            k_copy_rows<float><<<grid, 256, 0, st>>>(N, raw_ptr.as<int64_t>(), g->row_ptr, out_col.as<int32_t>(),
+                                                      out_val.as<float>(), g->col, (float *)g->val, g->degree,
+                                                      flag.as<int32_t>(), s2, s4);
         else if (g->weight_dtype == GIFT_WEIGHT_BF16)
-            k_compact<__nv_bfloat16><<<grid, 256, 0, st>>>(N, raw_ptr.as<int64_t>(), g->row_ptr, s_col.as<int32_t>(),
-                                                            s_val.as<double>(), g->col, (__nv_bfloat16 *)g->val,
-                                                            g->degree, flag.as<int32_t>());
+            k_copy_rows<__nv_bfloat16><<<grid, 256, 0, st>>>(N, raw_ptr.as<int64_t>(), g->row_ptr,
+                                                              out_col.as<int32_t>(), out_val.as<__nv_bfloat16>(),
+                                                              g->col, (__nv_bfloat16 *)g->val, g->degree,
+                                                              flag.as<int32_t>(), s2, s4);
         else
-            k_compact<__half><<<grid, 256, 0, st>>>(N, raw_ptr.as<int64_t>(), g->row_ptr, s_col.as<int32_t>(),
-                                                     s_val.as<double>(), g->col, (__half *)g->val, g->degree,
-                                                     flag.as<int32_t>());
-        check_launch("k_compact");
+            k_copy_rows<__half><<<grid, 256, 0, st>>>(N, raw_ptr.as<int64_t>(), g->row_ptr, out_col.as<int32_t>(),
+                                                       out_val.as<__half>(), g->col, (__half *)g->val, g->degree,
+                                                       flag.as<int32_t>(), s2, s4);
+        check_launch("k_copy_rows");
     }
     int32_t maxrow = 0;
     GIFT_CUDA(cudaMemcpyAsync(&maxrow, flag.p, sizeof(int32_t), cudaMemcpyDeviceToHost, st));
     GIFT_CUDA(cudaStreamSynchronize(st));
     g->max_row_nnz = maxrow;
-    g->device_bytes = (int64_t)(sizeof(int64_t) * (N + 1) + (4 + wsz) * nnz + 8 * N + 8 * (E + 1) + 4 * P + N);
+    g->device_bytes = (int64_t)(sizeof(int64_t) * (N + 1) + (4 + wsz) * nnz + 16 * N + 8 * (E + 1) + 4 * P + N);
     *out = g;
     owner.g = nullptr;
 }

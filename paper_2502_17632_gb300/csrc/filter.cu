@@ -112,8 +112,8 @@ const void *sweep_kernel(int weight_dtype, int vec, int cw, int ns, int nc) {
 
 namespace {
 
-// s = (d + sigma)^-1/2 in FP64, rounded once to FP32 (symmetric form, Eq. 16),
-// or 1/(d + sigma) (random-walk form).
+// s = (d + sigma)^-1/2 (symmetric form, Eq. 16) or 1/(d + sigma) (random-walk
+// form) from the FP64 degrees; see scale_value.
 __global__ void k_scale(int64_t n, const double *__restrict__ d, double sigma, int norm, float *__restrict__ out) {
     for (int64_t i = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; i < n; i += (int64_t)gridDim.x * blockDim.x) {
         double t = d[i] + sigma;
@@ -210,7 +210,6 @@ void tma_set_smem(const void *fn, int bytes) {
     done[fn] = bytes;
 }
 
-// Launches every sweep of the filter with one kernel shape.
 // Sliced-ELL slab width actually used: the requested width clamped to 1..4
 // vectors, halved until it divides K.
 int sell_width(const Plan &p, int requested) {
@@ -219,13 +218,23 @@ int sell_width(const Plan &p, int requested) {
     return w;
 }
 
-void run_sweeps(gift_ctx *ctx, const Plan &p, Shape shape, cudaStream_t st) {
-    const gift_graph *g = p.g;
-    if (shape.family == 3) shape.a = sell_width(p, shape.a);
-    const int64_t N = g->n;
-    const size_t wsz = g->weight_dtype == GIFT_WEIGHT_F32 ? 4 : 2;
-    const double csr_bytes = (double)g->nnz * (4.0 + wsz) + 8.0 * (N + 1);
-    std::vector<std::pair<int, int>> slabs;  // (c0, width in vectors)
+// Launch kinds, tuned separately: two chains in the first sweep (one gathered
+// input, two gather scales), two chains later (two gathered inputs), one
+// chain in the first sweep, one chain later.
+inline int launch_kind(int nc, int k) { return nc == 2 ? (k == 1 ? 0 : 1) : (k == 1 ? 2 : 3); }
+
+struct ShapeSet {
+    Shape kind[4];
+};
+
+struct TimedLaunch {
+    int kind;
+    cudaEvent_t e0, e1;
+};
+
+// Column slabs of a shape: (first column, width in vectors).
+std::vector<std::pair<int, int>> slab_plan(const Plan &p, const Shape &shape) {
+    std::vector<std::pair<int, int>> slabs;
     for (int c0 = 0; c0 < p.K;) {
         const int left = (p.K - c0) / p.vec;
         // merge-path slabs with float2 vectors are instantiated up to 8 columns;
@@ -237,14 +246,37 @@ void run_sweeps(gift_ctx *ctx, const Plan &p, Shape shape, cudaStream_t st) {
         slabs.push_back({c0, cw});
         c0 += cw * p.vec;
     }
-    GIFT_REQUIRE(shape.family != 2 || (p.vec == 4 && p.K % shape.a == 0),
-                 "gift_filter: TMA schedule needs K a multiple of the slab and 16-byte aligned signals");
-    if (shape.family == 3) {
-        const int rps = 32 / (shape.a / p.vec);
+    return slabs;
+}
+
+// Launches every sweep of the filter; each launch uses the shape of its kind.
+// With `timed`, every launch is bracketed by events from `pool` (tuning).
+void run_sweeps(gift_ctx *ctx, const Plan &p, ShapeSet ss, cudaStream_t st, std::vector<TimedLaunch> *timed = nullptr,
+                std::vector<cudaEvent_t> *pool = nullptr) {
+    const gift_graph *g = p.g;
+    const int64_t N = g->n;
+    const size_t wsz = g->weight_dtype == GIFT_WEIGHT_F32 ? 4 : 2;
+    const double csr_bytes = (double)g->nnz * (4.0 + wsz) + 8.0 * (N + 1);
+    std::vector<std::pair<int, int>> plans[4];
+    for (int kd = 0; kd < 4; ++kd) {
+        Shape &shape = ss.kind[kd];
+        if (shape.family == 3) shape.a = sell_width(p, shape.a);
+        plans[kd] = slab_plan(p, shape);
+        GIFT_REQUIRE(shape.family != 2 || (p.vec == 4 && p.K % shape.a == 0),
+                     "gift_filter: TMA schedule needs K a multiple of the slab and 16-byte aligned signals");
+    }
+    int sell_rps = 0;
+    for (int kd = 0; kd < 4; ++kd) {
+        if (ss.kind[kd].family != 3) continue;
+        const int rps = 32 / (ss.kind[kd].a / p.vec);
+        GIFT_REQUIRE(sell_rps == 0 || sell_rps == rps, "gift_filter: sliced-ELL kinds must share one slab width");
+        sell_rps = rps;
+    }
+    if (sell_rps) {
         std::lock_guard<std::mutex> lk(const_cast<gift_graph *>(g)->mu);
-        if (g->sell.rps != rps) {
+        if (g->sell.rps != sell_rps) {
             release_sell(const_cast<gift_graph *>(g), st);
-            build_sell(ctx, const_cast<gift_graph *>(g), rps, st);
+            build_sell(ctx, const_cast<gift_graph *>(g), sell_rps, st);
         }
     }
     int tma_launch = 0;
@@ -258,6 +290,9 @@ void run_sweeps(gift_ctx *ctx, const Plan &p, Shape shape, cudaStream_t st) {
             const bool last = (k == p.Lmax) && (gi + 2 >= active.size());
             bool group_terms = false;
             for (int q = 0; q < nc; ++q) group_terms |= p.chains[active[gi + q]].has_at[k];
+            const int kind = launch_kind(nc, k);
+            const Shape &shape = ss.kind[kind];
+            const std::vector<std::pair<int, int>> &slabs = plans[kind];
             for (size_t si = 0; si < slabs.size(); ++si) {
                 const int c0 = slabs[si].first, cw = slabs[si].second, W = cw * p.vec;
                 SweepArgs a;
@@ -318,7 +353,17 @@ void run_sweeps(gift_ctx *ctx, const Plan &p, Shape shape, cudaStream_t st) {
                     t.error = ctx->dev_error;
                     void *params[] = {&a, const_cast<CUtensorMap *>(&m0), const_cast<CUtensorMap *>(&m1), &t};
                     LaunchTimer lt(ctx, st, "filter.sweep", bytes);
+                    TimedLaunch tl{kind, nullptr, nullptr};
+                    if (timed) {
+                        tl.e0 = pool->back(); pool->pop_back();
+                        tl.e1 = pool->back(); pool->pop_back();
+                        GIFT_CUDA(cudaEventRecord(tl.e0, st));
+                    }
                     GIFT_CUDA(cudaLaunchKernel(fn, dim3(ctx->num_sms), dim3(32 + kTmaRows * (W / 4)), params, smem, st));
+                    if (timed) {
+                        GIFT_CUDA(cudaEventRecord(tl.e1, st));
+                        timed->push_back(tl);
+                    }
                     continue;
                 }
                 if (shape.family == 3) {
@@ -337,7 +382,17 @@ void run_sweeps(gift_ctx *ctx, const Plan &p, Shape shape, cudaStream_t st) {
                         1, std::min<int64_t>(want, (int64_t)ctx->num_sms * occupancy_blocks(fn, kSellThreads)));
                     void *params[] = {&a, &sa};
                     LaunchTimer lt(ctx, st, "filter.sweep", bytes);
+                    TimedLaunch tl{kind, nullptr, nullptr};
+                    if (timed) {
+                        tl.e0 = pool->back(); pool->pop_back();
+                        tl.e1 = pool->back(); pool->pop_back();
+                        GIFT_CUDA(cudaEventRecord(tl.e0, st));
+                    }
                     GIFT_CUDA(cudaLaunchKernel(fn, dim3(grid), dim3(kSellThreads), params, 0, st));
+                    if (timed) {
+                        GIFT_CUDA(cudaEventRecord(tl.e1, st));
+                        timed->push_back(tl);
+                    }
                     continue;
                 }
                 const void *fn = nullptr;
@@ -358,11 +413,27 @@ void run_sweeps(gift_ctx *ctx, const Plan &p, Shape shape, cudaStream_t st) {
                     1, std::min<int64_t>(want, (int64_t)ctx->num_sms * occupancy_blocks(fn, threads)));
                 void *params[] = {&a};
                 LaunchTimer lt(ctx, st, "filter.sweep", bytes);
+                TimedLaunch tl{kind, nullptr, nullptr};
+                if (timed) {
+                    tl.e0 = pool->back(); pool->pop_back();
+                    tl.e1 = pool->back(); pool->pop_back();
+                    GIFT_CUDA(cudaEventRecord(tl.e0, st));
+                }
                 GIFT_CUDA(cudaLaunchKernel(fn, dim3(grid), dim3(threads), params, 0, st));
+                if (timed) {
+                    GIFT_CUDA(cudaEventRecord(tl.e1, st));
+                    timed->push_back(tl);
+                }
             }
             if (group_terms && !last) contributed = true;
         }
     }
+}
+
+void run_sweeps_one(gift_ctx *ctx, const Plan &p, Shape shape, cudaStream_t st) {
+    ShapeSet ss;
+    for (auto &k : ss.kind) k = shape;
+    run_sweeps(ctx, p, ss, st);
 }
 
 // Shape key of a graph / signal for the autotuner cache.
@@ -394,18 +465,24 @@ bool valid_shape(Shape s) {
 }
 
 // Times the whole filter once per candidate shape (after one warm run) and keeps the fastest.
-Shape autotune(gift_ctx *ctx, const Plan &p, cudaStream_t st) {
+// Times every candidate shape on the whole filter (after one warm run),
+// attributing each launch to its kind, and keeps the fastest shape per kind.
+ShapeSet autotune(gift_ctx *ctx, const Plan &p, cudaStream_t st) {
     const std::string key = tune_key(p.g, p.vec, p.K, p);
     {
         std::lock_guard<std::mutex> lk(ctx->tune_mu);
         auto it = ctx->tuned.find(key);
-        if (it != ctx->tuned.end()) return it->second;
+        if (it != ctx->tuned.end()) {
+            ShapeSet ss;
+            for (int kd = 0; kd < 4; ++kd) ss.kind[kd] = it->second.kind[kd];
+            return ss;
+        }
     }
     std::vector<Shape> cands;
     // TMA gather4 (family 2) measured ~4x slower than LSU gathers for 64-byte
     // random rows on GB300; it stays available as an explicit schedule only.
-    for (int w : {16, 8, 4, 2})
-        if (sell_width(p, w) == w) cands.push_back(Shape{3, w, 1});
+    // One sliced-ELL width (the widest) so that every kind shares its format.
+    cands.push_back(Shape{3, sell_width(p, 16), 1});
     for (int w : {16, 8, 4, 2})
         if (w >= p.vec && w <= std::max(p.K, p.vec) && (p.vec == 4 || w <= 8)) cands.push_back(Shape{1, w, 1});
     for (int cw : {4, 2, 1})
@@ -413,38 +490,55 @@ Shape autotune(gift_ctx *ctx, const Plan &p, cudaStream_t st) {
             if (gg >= 2 * cw && cw * p.vec <= std::max(p.K, p.vec)) cands.push_back(Shape{0, cw, gg});
     const bool prof = ctx->profiling;
     ctx->profiling = false;
-    cudaEvent_t e0, e1;
-    GIFT_CUDA(cudaEventCreate(&e0));
-    GIFT_CUDA(cudaEventCreate(&e1));
-    Shape best = cands.front();
-    float best_ms = 1e30f;
+    std::vector<cudaEvent_t> pool;
+    double best_ms[4] = {1e30, 1e30, 1e30, 1e30};
+    ShapeSet best;
+    for (auto &k : best.kind) k = cands.front();
+    auto cleanup = [&] {
+        for (auto e : pool) cudaEventDestroy(e);
+        ctx->profiling = prof;
+    };
     try {
         for (const Shape &s : cands) {
+            ShapeSet ss;
+            for (auto &k : ss.kind) k = s;
             GIFT_CUDA(cudaMemsetAsync(p.counters, 0, sizeof(int32_t) * p.ncounters, st));
-            run_sweeps(ctx, p, s, st);
+            run_sweeps(ctx, p, ss, st);
             GIFT_CUDA(cudaMemsetAsync(p.counters, 0, sizeof(int32_t) * p.ncounters, st));
-            GIFT_CUDA(cudaEventRecord(e0, st));
-            run_sweeps(ctx, p, s, st);
-            GIFT_CUDA(cudaEventRecord(e1, st));
-            GIFT_CUDA(cudaEventSynchronize(e1));
-            float ms = 0.f;
-            GIFT_CUDA(cudaEventElapsedTime(&ms, e0, e1));
-            if (ms < best_ms) {
-                best_ms = ms;
-                best = s;
+            std::vector<TimedLaunch> timed;
+            std::vector<cudaEvent_t> avail = pool;
+            const size_t need = 2 * (size_t)(p.Lmax * (p.chains.size() + 1) * (p.K / p.vec + 1));
+            while (avail.size() < need) {
+                cudaEvent_t e;
+                GIFT_CUDA(cudaEventCreate(&e));
+                pool.push_back(e);
+                avail.push_back(e);
             }
+            run_sweeps(ctx, p, ss, st, &timed, &avail);
+            GIFT_CUDA(cudaStreamSynchronize(st));
+            double ms[4] = {0, 0, 0, 0};
+            bool seen[4] = {false, false, false, false};
+            for (const TimedLaunch &t : timed) {
+                float m = 0.f;
+                GIFT_CUDA(cudaEventElapsedTime(&m, t.e0, t.e1));
+                ms[t.kind] += m;
+                seen[t.kind] = true;
+            }
+            for (int kd = 0; kd < 4; ++kd)
+                if (seen[kd] && ms[kd] < best_ms[kd]) {
+                    best_ms[kd] = ms[kd];
+                    best.kind[kd] = s;
+                }
         }
     } catch (...) {
-        cudaEventDestroy(e0);
-        cudaEventDestroy(e1);
-        ctx->profiling = prof;
+        cleanup();
         throw;
     }
-    cudaEventDestroy(e0);
-    cudaEventDestroy(e1);
-    ctx->profiling = prof;
+    cleanup();
     std::lock_guard<std::mutex> lk(ctx->tune_mu);
-    ctx->tuned[key] = best;
+    TunedSet ts;
+    for (int kd = 0; kd < 4; ++kd) ts.kind[kd] = best.kind[kd];
+    ctx->tuned[key] = ts;
     return best;
 }
 
@@ -535,10 +629,18 @@ void filter_impl(gift_ctx *ctx, const gift_graph *cg, const gift_filter_spec *sp
     p.ncounters = 1024;
     DevBuf counters(ctx, sizeof(int32_t) * p.ncounters, st);
     p.counters = counters.as<int32_t>();
-    const Shape shape = spec->schedule == 0 ? autotune(ctx, p, st) : shape_from_schedule(spec->schedule);
+    ShapeSet ss;
+    if (spec->schedule == 0) {
+        ss = autotune(ctx, p, st);
+    } else {
+        for (auto &k : ss.kind) k = shape_from_schedule(spec->schedule);
+    }
     GIFT_CUDA(cudaMemsetAsync(p.counters, 0, sizeof(int32_t) * p.ncounters, st));
-    run_sweeps(ctx, p, shape, st);
-    ctx->last_schedule = shape.family >= 1 ? 1000 * shape.family + shape.a : 100 * shape.a + shape.b;
+    run_sweeps(ctx, p, ss, st);
+    for (int kd = 0; kd < 4; ++kd) {
+        const Shape &sh = ss.kind[kd];
+        ctx->last_schedules[kd] = sh.family >= 1 ? 1000 * sh.family + sh.a : 100 * sh.a + sh.b;
+    }
 
     if (mem == GIFT_MEM_HOST) {
         GIFT_CUDA(cudaMemcpyAsync(g_out, p.dout, sig_bytes, cudaMemcpyDeviceToHost, st));
@@ -573,10 +675,8 @@ size_t filter_scratch_bytes(const gift_graph *g, const gift_filter_spec *spec, i
 }
 
 __global__ void k_scale_into(int64_t n, const double *__restrict__ d, double sigma, int norm, float *__restrict__ out) {
-    for (int64_t i = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; i < n; i += (int64_t)gridDim.x * blockDim.x) {
-        double t = d[i] + sigma;
-        out[i] = norm == GIFT_NORM_SYM ? (float)(1.0 / sqrt(t)) : (float)(1.0 / t);
-    }
+    for (int64_t i = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; i < n; i += (int64_t)gridDim.x * blockDim.x)
+        out[i] = scale_value(d[i], sigma, norm);
 }
 
 void filter_on_scratch(gift_ctx *ctx, const gift_graph *g, const gift_filter_spec *spec, const float *g_in, int S,
@@ -659,17 +759,20 @@ void filter_on_scratch(gift_ctx *ctx, const gift_graph *g, const gift_filter_spe
     p.counters = nullptr;
     p.ncounters = 0;
 
-    Shape shape{0, 4, 8};
+    ShapeSet ss;
+    for (auto &k : ss.kind) k = Shape{0, 4, 8};
     {
         std::lock_guard<std::mutex> lk(ctx->tune_mu);
         auto it = ctx->tuned.find(tune_key(g, p.vec, K, p));
         if (it != ctx->tuned.end()) {
-            const Shape t = it->second;
-            const int rps = t.family == 3 ? 32 / (sell_width(p, t.a) / p.vec) : 0;
-            if (t.family == 0 || t.family == 1 || (t.family == 3 && g->sell.rps == rps)) shape = t;
+            for (int kd = 0; kd < 4; ++kd) {
+                const Shape t = it->second.kind[kd];
+                const int rps = t.family == 3 ? 32 / (sell_width(p, t.a) / p.vec) : 0;
+                if (t.family == 0 || t.family == 1 || (t.family == 3 && g->sell.rps == rps)) ss.kind[kd] = t;
+            }
         }
     }
-    run_sweeps(ctx, p, shape, st);
+    run_sweeps(ctx, p, ss, st);
 }
 
 }  // namespace gift

@@ -100,6 +100,99 @@ k_hpwl(int32_t E, int32_t S, const int64_t *__restrict__ net_ptr, const int32_t 
     }
 }
 
+// Even S, 16-byte aligned locations: a group of GH lanes per net, lane q of a
+// group covering signals s0 + 2q, s0 + 2q + 1 with one float4 per pin, so a
+// group reads a pin's whole row piece in one access; 4 pins in flight per
+// lane.  Nets above 32 pins are reduced by the whole warp.
+template <int GH>
+__global__ void __launch_bounds__(kHpwlThreads)
+k_hpwl_groups(int32_t E, int32_t S, const int64_t *__restrict__ net_ptr, const int32_t *__restrict__ pin_cell,
+              const float4 *__restrict__ xy4, double *__restrict__ partial) {
+    constexpr int NPW = 32 / GH;  // nets per warp step
+    __shared__ double red[kHpwlThreads / 32][2 * GH];
+    const int half = S / 2;  // float4 per cell row
+    const int s0 = blockIdx.y * 2 * GH;
+    const int lane = threadIdx.x & 31, wid = threadIdx.x >> 5;
+    const int gi = lane / GH, q = lane % GH;
+    const bool on = s0 + 2 * q < S;
+    const int qq = on ? s0 / 2 + q : 0;
+    const int64_t warp = (blockIdx.x * (int64_t)blockDim.x + threadIdx.x) >> 5;
+    const int64_t nwarps = ((int64_t)gridDim.x * blockDim.x) >> 5;
+    double sum0 = 0.0, sum1 = 0.0;
+    for (int64_t base = warp * NPW; base < E; base += nwarps * NPW) {
+        const int64_t e = base + gi;
+        int64_t b = 0, m = 0;
+        if (e < E) {
+            b = net_ptr[e];
+            m = net_ptr[e + 1] - b;
+        }
+        if (m >= 2 && m <= 32) {
+            Box b0{INFINITY, -INFINITY, INFINITY, -INFINITY}, b1 = b0;
+            for (int64_t t = 0; t < m; t += 4) {
+                int32_t c[4];
+#pragma unroll
+                for (int u = 0; u < 4; ++u) c[u] = t + u < m ? pin_cell[b + t + u] : -1;
+                float4 v[4];
+#pragma unroll
+                for (int u = 0; u < 4; ++u)
+                    v[u] = (c[u] >= 0 && on) ? __ldg(xy4 + (int64_t)c[u] * half + qq) : make_float4(0.f, 0.f, 0.f, 0.f);
+#pragma unroll
+                for (int u = 0; u < 4; ++u)
+                    if (c[u] >= 0) {
+                        grow(b0, make_float2(v[u].x, v[u].y));
+                        grow(b1, make_float2(v[u].z, v[u].w));
+                    }
+            }
+            sum0 += extent(b0);
+            sum1 += extent(b1);
+        }
+        unsigned big = __ballot_sync(0xffffffffu, m > 32 && q == 0);
+        while (big) {
+            const int src = __ffs(big) - 1;
+            big &= big - 1;
+            const int64_t bb = __shfl_sync(0xffffffffu, b, src), mb = __shfl_sync(0xffffffffu, m, src);
+            for (int pq = 0; pq < GH; ++pq) {  // signal pair s0 + 2 pq, + 1
+                if (s0 + 2 * pq >= S) break;
+                Box c0{INFINITY, -INFINITY, INFINITY, -INFINITY}, c1 = c0;
+                for (int64_t t = lane; t < mb; t += 32) {
+                    const float4 v = __ldg(xy4 + (int64_t)pin_cell[bb + t] * half + s0 / 2 + pq);
+                    grow(c0, make_float2(v.x, v.y));
+                    grow(c1, make_float2(v.z, v.w));
+                }
+                for (int o = 16; o; o >>= 1) {
+                    c0.xlo = fminf(c0.xlo, __shfl_xor_sync(0xffffffffu, c0.xlo, o));
+                    c0.xhi = fmaxf(c0.xhi, __shfl_xor_sync(0xffffffffu, c0.xhi, o));
+                    c0.ylo = fminf(c0.ylo, __shfl_xor_sync(0xffffffffu, c0.ylo, o));
+                    c0.yhi = fmaxf(c0.yhi, __shfl_xor_sync(0xffffffffu, c0.yhi, o));
+                    c1.xlo = fminf(c1.xlo, __shfl_xor_sync(0xffffffffu, c1.xlo, o));
+                    c1.xhi = fmaxf(c1.xhi, __shfl_xor_sync(0xffffffffu, c1.xhi, o));
+                    c1.ylo = fminf(c1.ylo, __shfl_xor_sync(0xffffffffu, c1.ylo, o));
+                    c1.yhi = fmaxf(c1.yhi, __shfl_xor_sync(0xffffffffu, c1.yhi, o));
+                }
+                if (lane == pq) {  // group 0, lane q == pq holds this signal pair
+                    sum0 += extent(c0);
+                    sum1 += extent(c1);
+                }
+            }
+        }
+    }
+    for (int o = GH; o < 32; o <<= 1) {
+        sum0 += __shfl_xor_sync(0xffffffffu, sum0, o);
+        sum1 += __shfl_xor_sync(0xffffffffu, sum1, o);
+    }
+    if (gi == 0) {
+        red[wid][2 * q] = sum0;
+        red[wid][2 * q + 1] = sum1;
+    }
+    __syncthreads();
+    const int nsig = min(2 * GH, S - s0);
+    if (threadIdx.x < nsig) {
+        double t = 0.0;
+        for (int w = 0; w < kHpwlThreads / 32; ++w) t += red[w][threadIdx.x];
+        partial[(int64_t)(s0 + threadIdx.x) * gridDim.x + blockIdx.x] = t;
+    }
+}
+
 __global__ void k_hpwl_final(int32_t S, int32_t nblocks, const double *__restrict__ partial, double *__restrict__ out) {
     for (int s = threadIdx.x; s < S; s += blockDim.x) {
         double t = 0.0;
@@ -129,11 +222,22 @@ void hpwl_impl(gift_ctx *ctx, const gift_graph *g, const float *xy, int S, doubl
         1, std::min<int64_t>(ceil_div(std::max<int64_t>(E, 1), kHpwlThreads), (int64_t)ctx->num_sms * 8));
     DevBuf partial(ctx, sizeof(double) * (size_t)nblocks * S, st);
     DevBuf dout(ctx, sizeof(double) * S, st);
+    const bool grouped = S % 2 == 0 && reinterpret_cast<uintptr_t>(dxy) % 16 == 0;
     {
         LaunchTimer lt(ctx, st, "hpwl", 8.0 * (E + 1) + 4.0 * g->num_pins + 8.0 * g->num_pins * S, 2);
-        k_hpwl<<<dim3(nblocks, passes), kHpwlThreads, 0, st>>>((int32_t)E, S, g->net_ptr, g->pin_cell,
-                                                                reinterpret_cast<const float2 *>(dxy),
-                                                                partial.as<double>());
+        if (grouped) {
+            const int gh = S >= 16 ? 8 : (S >= 8 ? 4 : (S >= 4 ? 2 : 1));
+            const dim3 grid(nblocks, (unsigned)ceil_div(S, 2 * gh));
+            const float4 *xy4 = reinterpret_cast<const float4 *>(dxy);
+            if (gh == 8) k_hpwl_groups<8><<<grid, kHpwlThreads, 0, st>>>((int32_t)E, S, g->net_ptr, g->pin_cell, xy4, partial.as<double>());
+            else if (gh == 4) k_hpwl_groups<4><<<grid, kHpwlThreads, 0, st>>>((int32_t)E, S, g->net_ptr, g->pin_cell, xy4, partial.as<double>());
+            else if (gh == 2) k_hpwl_groups<2><<<grid, kHpwlThreads, 0, st>>>((int32_t)E, S, g->net_ptr, g->pin_cell, xy4, partial.as<double>());
+            else k_hpwl_groups<1><<<grid, kHpwlThreads, 0, st>>>((int32_t)E, S, g->net_ptr, g->pin_cell, xy4, partial.as<double>());
+        } else {
+            k_hpwl<<<dim3(nblocks, passes), kHpwlThreads, 0, st>>>((int32_t)E, S, g->net_ptr, g->pin_cell,
+                                                                    reinterpret_cast<const float2 *>(dxy),
+                                                                    partial.as<double>());
+        }
         k_hpwl_final<<<1, 128, 0, st>>>(S, nblocks, partial.as<double>(), dout.as<double>());
         check_launch("k_hpwl");
     }

@@ -70,6 +70,10 @@ struct KernelRecord {
 struct TunedShape {
     int family, a, b;
 };
+// tuned shape per launch kind (see filter.cu)
+struct TunedSet {
+    TunedShape kind[4];
+};
 
 struct PendingTiming {
     std::string name;
@@ -96,10 +100,12 @@ struct gift_ctx {
     std::vector<cudaEvent_t> event_pool;
     // autotuned sweep shapes by graph/signal shape key: (family, a, b)
     std::mutex tune_mu;
-    std::map<std::string, gift::TunedShape> tuned;
-    int last_schedule = 0;
+    std::map<std::string, gift::TunedSet> tuned;
+    int last_schedules[4] = {0, 0, 0, 0};
     // device word set by kernels whose bounded waits ran out (0 = fine)
     int32_t *dev_error = nullptr;
+    // wtab[m] = 2/m in FP64 for m in [2, kWeightTable] (0 below), filled on the host
+    double *wtab = nullptr;
 };
 
 namespace gift {
@@ -159,6 +165,16 @@ void check_launch(const char *what);
 void check_device_error(gift_ctx *ctx);
 
 inline int64_t ceil_div(int64_t a, int64_t b) { return (a + b - 1) / b; }
+
+// Scale of Eq. 16 from an FP64 degree: (d + sigma)^-1/2 (symmetric form) or
+// 1/(d + sigma) (random walk), as the correctly rounded FP32 function of the
+// FP32-rounded sum (FP64 throughput on GB300 is a small fraction of FP32's).
+__device__ __forceinline__ float scale_value(double d, double sigma, int norm) {
+    const float t = __double2float_rn(d + sigma);
+    return norm == GIFT_NORM_SYM ? __frsqrt_rn(t) : __frcp_rn(t);
+}
+
+constexpr int kWeightTable = 4096;  // 2/M from a table for M <= this
 
 }  // namespace gift
 

@@ -86,7 +86,7 @@ def load(build_if_missing: bool = True):
         "gift_ctx_kernel_stats": (I32, [P, P, I32]),
         "gift_ctx_reset_stats": (None, [P]),
         "gift_ctx_debug_fail_alloc": (None, [P, I32]),
-        "gift_ctx_last_schedule": (I32, [P]),
+        "gift_ctx_last_schedule": (I32, [P, P]),
         "gift_ctx_device_status": (I32, [P]),
         "gift_filter_spec_default": (None, [P]),
         "gift_build_opts_default": (None, [P]),
@@ -163,8 +163,12 @@ def gift_ctx_reset_stats(ctx):
     load().gift_ctx_reset_stats(ctx)
 
 
-def gift_ctx_last_schedule(ctx) -> int:
-    return int(load().gift_ctx_last_schedule(ctx))
+def gift_ctx_last_schedule(ctx) -> list:
+    """Schedule codes of the last filter call, per launch kind (two chains first
+    sweep, two chains later, one chain first sweep, one chain later)."""
+    out = (C.c_int32 * 4)()
+    load().gift_ctx_last_schedule(ctx, out)
+    return [int(v) for v in out]
 
 
 def gift_ctx_device_status(ctx):

@@ -223,10 +223,11 @@ def test_filter_is_deterministic(ctx):
     np.testing.assert_array_equal(run_filter(ctx, nl, g), run_filter(ctx, nl, g))
 
 
+@pytest.mark.parametrize("S", [1, 2, 3, 4, 8, 16])
 @pytest.mark.parametrize("name", ["plain-10k", "repeat-cells", "global-tier-row", "single-pin-nets"])
-def test_hpwl_parity(ctx, name):
+def test_hpwl_parity(ctx, name, S):
     nl = NETLISTS[name]
-    g = synth.make_signals(nl, 3, 8)
+    g = synth.make_signals(nl, S, 8)
     h = build(ctx, nl)
     try:
         got_d = gift.gift_hpwl(ctx, h, dev(g))
