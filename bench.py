@@ -46,6 +46,9 @@ def parse():
     p.add_argument("--scale", type=float, default=1.0, help="shrink the workload (profiling captures only)")
     p.add_argument("--no-cpu-baseline", action="store_true")
     p.add_argument("--no-e2e", action="store_true")
+    p.add_argument("--capture", action="store_true",
+                   help="tune and warm the filter, then run one filter call inside the NVTX range 'capture' and exit "
+                        "(the command an ncu capture of the sweep kernels runs)")
     return p.parse_args()
 
 
@@ -118,9 +121,13 @@ class ClockSampler:
 
 
 # ----------------------------------------------------------------- traffic record
+SWEEP_SOURCES = ("sweep.cuh", "sweep_mp.cuh", "sweep_tma.cuh", "sell.cuh", "sell.cu", "filter.cu",
+                 "sweep_f32.cu", "sweep_bf16.cu", "sweep_f16.cu", "internal.cuh")
+
+
 def sweep_source_hash() -> str:
     h = hashlib.sha256()
-    for f in ("sweep.cuh", "filter.cu"):
+    for f in SWEEP_SOURCES:
         with open(os.path.join(ROOT, "paper_2502_17632_gb300", "csrc", f), "rb") as fh:
             h.update(fh.read())
     return h.hexdigest()[:16]
@@ -185,6 +192,54 @@ def run_reference(args):
     print(json.dumps(line), flush=True)
 
 
+# ----------------------------------------------------------------- NVTX ranges
+class Range:
+    """NVTX push/pop range (lets an ncu capture select the launches inside)."""
+
+    def __init__(self, name: str):
+        self.name = name
+
+    def __enter__(self):
+        import torch
+        try:
+            torch.cuda.nvtx.range_push(self.name)
+            self.on = True
+        except Exception:
+            self.on = False
+
+    def __exit__(self, *a):
+        import torch
+        if self.on:
+            torch.cuda.nvtx.range_pop()
+
+
+def run_capture(args):
+    """One tuned filter call inside the NVTX range 'capture'."""
+    import torch
+    from paper_2502_17632_gb300 import gift
+
+    gift.load()
+    nl, g = synth.workload(args.workload, scale=args.scale)
+    ctx = gift.gift_ctx_create(0)
+    stream = torch.cuda.current_stream()
+    dev = lambda a: torch.from_numpy(np.ascontiguousarray(a)).cuda()  # noqa: E731
+    d_g = dev(g)
+    d_out = torch.empty_like(d_g)
+    h = gift.gift_build_graph(ctx, nl.num_cells, dev(nl.net_ptr), dev(nl.pin_cell), dev(nl.is_fixed),
+                              gift.WEIGHT[args.weights], stream=stream)
+    for _ in range(max(args.warmup, 1)):
+        gift.gift_filter(ctx, h, d_g, d_out, stream=stream)
+    torch.cuda.synchronize()
+    with Range("capture"):
+        gift.gift_filter(ctx, h, d_g, d_out, stream=stream)
+        torch.cuda.synchronize()
+    print(json.dumps({"capture": args.workload, "weights": args.weights, "scale": args.scale,
+                      "sweep_schedule": gift.gift_ctx_last_schedule(ctx), "nnz": int(gift.gift_graph_info(h).nnz),
+                      "sweep_source_hash": sweep_source_hash()}), flush=True)
+    gift.gift_graph_free(h)
+    gift.gift_ctx_destroy(ctx)
+
+
 # ----------------------------------------------------------------- GPU arm
 def run_ours(args):
     import torch
@@ -233,7 +288,7 @@ def run_ours(args):
 
     barrier()
     e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
-    with ClockSampler(local) as clk:
+    with ClockSampler(local) as clk, Range("timed"):
         e0.record(stream)
         for _ in range(args.steps):
             hp = step()
@@ -356,6 +411,8 @@ def main():
     args = parse()
     if args.impl == "reference":
         run_reference(args)
+    elif args.capture:
+        run_capture(args)
     else:
         run_ours(args)
 

@@ -105,6 +105,17 @@ typedef struct gift_filter_spec {
     int32_t compensated;            /* 1: compensated FP32 sums on long rows    */
     int32_t schedule;               /* 0: autotuned; else a fixed kernel choice */
 } gift_filter_spec;
+/* Schedule codes (every launch kind uses the one shape):
+ *   4..32 or 100*cw + g    row groups: cw vector lanes across the slab, g lanes per row
+ *   1000 + w               warp merge-path, slab of w columns
+ *   2000 + w               TMA gather4 pipeline, slab of w columns (K a multiple of w)
+ *   3000 + w               sliced ELL, slab of w columns
+ *   4000 + 100*n + 10*cw + u   direct row groups: cw lanes per row, u gathers in
+ *                          flight per lane; n bit 0: float2 lanes; n bit 1: rows
+ *                          in natural order (else sorted by length per 256 rows)
+ *   10000 + code           as code, with the two chains of a two-chain sweep
+ *                          run as separate launches
+ * Any other value is GIFT_ERR_INVALID. */
 
 typedef struct gift_graph_desc {
     int32_t num_cells;

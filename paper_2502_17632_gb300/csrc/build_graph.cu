@@ -569,6 +569,9 @@ void release_graph(gift_graph *g, cudaStream_t st) {
     }
     g->scales.clear();
     release_sell(g, st);
+    dev_free(g->order, st);
+    g->order = nullptr;
+    g->order_slots = 0;
 }
 
 void build_graph_impl(gift_ctx *ctx, const gift_netlist *nl, const gift_build_opts *opts, gift_graph **out,

@@ -16,6 +16,7 @@
 #include "sweep.cuh"
 #include "sweep_mp.cuh"
 #include "sweep_tma.cuh"
+#include "sweep_dr.cuh"
 #include "sell.cuh"
 
 namespace gift {
@@ -77,6 +78,19 @@ static CUtensorMap row_map(const float *base, int64_t n, int K, int W) {
     if (r != CUDA_SUCCESS)
         throw Failure{GIFT_ERR_UNSUPPORTED, "gift_filter: cuTensorMapEncodeTiled failed (" + std::to_string((int)r) + ")"};
     return m;
+}
+
+const void *sweep_dr_kernel_f32(int vec, int cw, int u, int nc, bool first);
+const void *sweep_dr_kernel_bf16(int vec, int cw, int u, int nc, bool first);
+const void *sweep_dr_kernel_f16(int vec, int cw, int u, int nc, bool first);
+
+const void *sweep_dr_kernel(int weight_dtype, int vec, int cw, int u, int nc, bool first) {
+    switch (weight_dtype) {
+    case GIFT_WEIGHT_F32: return sweep_dr_kernel_f32(vec, cw, u, nc, first);
+    case GIFT_WEIGHT_BF16: return sweep_dr_kernel_bf16(vec, cw, u, nc, first);
+    case GIFT_WEIGHT_F16: return sweep_dr_kernel_f16(vec, cw, u, nc, first);
+    default: return nullptr;
+    }
 }
 
 const void *sweep_sell_kernel_f32(int vec, int cw, int nx, int nc);
@@ -179,7 +193,10 @@ namespace {
 // Kernel shape.  family 0: row groups (k_sweep), a = lanes across the widest
 // slab (slab = vec * a columns), b = lanes per row.  family 1: warp merge-path
 // (k_sweep_mp), a = widest slab in columns.  family 2: TMA gathers
-// (k_sweep_tma), a = slab in columns (8 or 16).
+// (k_sweep_tma), a = slab in columns (8 or 16).  family 3: sliced ELL
+// (k_sweep_sell), a = slab in columns.  family 4: direct row groups
+// (k_sweep_dr), a = lanes per row, b = gathers in flight per lane, narrow =
+// float2 lanes.
 using Shape = TunedShape;
 
 struct Plan {
@@ -196,7 +213,9 @@ struct Plan {
     std::vector<std::array<float *, 2>> X;
     int32_t *counters;  // one zeroed tile counter per TMA launch
     int ncounters;
-    const float2 *gpre2;  // first-sweep gather scales of chains 0 and 1, packed
+    // first-sweep gather scales of chains (2q, 2q+1), packed: gpre2[q] (null
+    // when the chains carry no pre-scale, random-walk form)
+    std::vector<const float2 *> gpre2;
 };
 
 // Dynamic shared memory the TMA kernel is opted into, once per kernel.
@@ -225,38 +244,54 @@ inline int launch_kind(int nc, int k) { return nc == 2 ? (k == 1 ? 0 : 1) : (k =
 
 struct ShapeSet {
     Shape kind[4];
+    bool split[2] = {false, false};  // kinds 0 / 1: one launch per chain, with the one-chain shape
 };
 
 struct TimedLaunch {
-    int kind;
+    int kind;  // kind of the chain group as planned (before a split)
     cudaEvent_t e0, e1;
 };
 
-// Column slabs of a shape: (first column, width in vectors).
+// Vector width (floats per lane) of a shape.
+inline int shape_vec(const Plan &p, const Shape &s) { return (s.family == 4 && s.narrow) ? 2 : p.vec; }
+
+// Column slabs of a shape: (first column, lanes across the slab).
 std::vector<std::pair<int, int>> slab_plan(const Plan &p, const Shape &shape) {
     std::vector<std::pair<int, int>> slabs;
+    const int sv = shape_vec(p, shape);
     for (int c0 = 0; c0 < p.K;) {
-        const int left = (p.K - c0) / p.vec;
+        const int left = (p.K - c0) / sv;
         // merge-path slabs with float2 vectors are instantiated up to 8 columns;
         // TMA and sliced-ELL slabs are exactly shape.a columns (K is a multiple of it)
-        int cw = shape.family == 0 ? shape.a : std::min(shape.a, p.vec == 2 ? 8 : 16) / p.vec;
+        int cw = (shape.family == 0 || shape.family == 4) ? shape.a : std::min(shape.a, sv == 2 ? 8 : 16) / sv;
         cw = std::max(cw, 1);
         while (cw > left) cw >>= 1;
         GIFT_REQUIRE(cw >= 1, "gift_filter: empty column slab");
         slabs.push_back({c0, cw});
-        c0 += cw * p.vec;
+        c0 += cw * sv;
     }
     return slabs;
 }
 
+// A chain group of one sweep: one or two chains sharing a launch.
+struct Group {
+    int c[2];
+    int nc;
+    int kind;             // launch kind of the launch(es)
+    int planned;          // kind before a split (tuning attribution)
+    const float2 *gpre2;  // packed first-sweep scales of the pair
+};
+
 // Launches every sweep of the filter; each launch uses the shape of its kind.
 // With `timed`, every launch is bracketed by events from `pool` (tuning).
-void run_sweeps(gift_ctx *ctx, const Plan &p, ShapeSet ss, cudaStream_t st, std::vector<TimedLaunch> *timed = nullptr,
-                std::vector<cudaEvent_t> *pool = nullptr) {
+// Returns the mask of launch kinds used (bit kd, planned kinds).
+int run_sweeps(gift_ctx *ctx, const Plan &p, ShapeSet ss, cudaStream_t st, std::vector<TimedLaunch> *timed = nullptr,
+               std::vector<cudaEvent_t> *pool = nullptr) {
     const gift_graph *g = p.g;
     const int64_t N = g->n;
     const size_t wsz = g->weight_dtype == GIFT_WEIGHT_F32 ? 4 : 2;
     const double csr_bytes = (double)g->nnz * (4.0 + wsz) + 8.0 * (N + 1);
+    const double sig = 4.0 * (double)N * p.K;
     std::vector<std::pair<int, int>> plans[4];
     for (int kd = 0; kd < 4; ++kd) {
         Shape &shape = ss.kind[kd];
@@ -265,16 +300,43 @@ void run_sweeps(gift_ctx *ctx, const Plan &p, ShapeSet ss, cudaStream_t st, std:
         GIFT_REQUIRE(shape.family != 2 || (p.vec == 4 && p.K % shape.a == 0),
                      "gift_filter: TMA schedule needs K a multiple of the slab and 16-byte aligned signals");
     }
+    // chain groups of every sweep; only the kinds that launch prepare formats
+    std::vector<std::vector<Group>> sweep_groups(p.Lmax + 1);
+    std::vector<std::vector<int>> sweep_active(p.Lmax + 1);
+    bool used[4] = {false, false, false, false};
+    int planned_mask = 0;
+    for (int k = 1; k <= p.Lmax; ++k) {
+        std::vector<int> &active = sweep_active[k];
+        for (size_t c = 0; c < p.chains.size(); ++c)
+            if (p.chains[c].L >= k) active.push_back((int)c);
+        for (size_t gi = 0; gi < active.size(); gi += 2) {
+            const int nc = (int)std::min<size_t>(2, active.size() - gi);
+            const int planned = launch_kind(nc, k);
+            const float2 *gp2 = (k == 1 && nc == 2 && gi / 2 < p.gpre2.size()) ? p.gpre2[gi / 2] : nullptr;
+            if (nc == 2 && ss.split[planned]) {
+                for (int q = 0; q < 2; ++q)
+                    sweep_groups[k].push_back(Group{{active[gi + q], active[gi + q]}, 1, launch_kind(1, k), planned, nullptr});
+            } else {
+                sweep_groups[k].push_back(Group{{active[gi], active[gi + nc - 1]}, nc, planned, planned, gp2});
+            }
+            used[sweep_groups[k].back().kind] = true;
+            planned_mask |= 1 << planned;
+        }
+    }
     int sell_rps = 0;
+    bool direct = false;
     for (int kd = 0; kd < 4; ++kd) {
+        if (!used[kd]) continue;
+        direct |= ss.kind[kd].family == 4 && !ss.kind[kd].natural;
         if (ss.kind[kd].family != 3) continue;
         const int rps = 32 / (ss.kind[kd].a / p.vec);
         GIFT_REQUIRE(sell_rps == 0 || sell_rps == rps, "gift_filter: sliced-ELL kinds must share one slab width");
         sell_rps = rps;
     }
-    if (sell_rps) {
+    if (sell_rps || direct) {
         std::lock_guard<std::mutex> lk(const_cast<gift_graph *>(g)->mu);
-        if (g->sell.rps != sell_rps) {
+        if (direct) ensure_row_order(ctx, const_cast<gift_graph *>(g), st);
+        if (sell_rps && g->sell.rps != sell_rps) {
             release_sell(const_cast<gift_graph *>(g), st);
             build_sell(ctx, const_cast<gift_graph *>(g), sell_rps, st);
         }
@@ -282,19 +344,31 @@ void run_sweeps(gift_ctx *ctx, const Plan &p, ShapeSet ss, cudaStream_t st, std:
     int tma_launch = 0;
     bool contributed = false;
     for (int k = 1; k <= p.Lmax; ++k) {
-        std::vector<int> active;
-        for (size_t c = 0; c < p.chains.size(); ++c)
-            if (p.chains[c].L >= k) active.push_back((int)c);
-        for (size_t gi = 0; gi < active.size(); gi += 2) {
-            const int nc = (int)std::min<size_t>(2, active.size() - gi);
-            const bool last = (k == p.Lmax) && (gi + 2 >= active.size());
+        const std::vector<int> &active = sweep_active[k];
+        const std::vector<Group> &groups = sweep_groups[k];
+        bool sweep_terms = false;
+        for (int c : active) sweep_terms |= p.chains[c].has_at[k];
+        // algorithmic bytes of the sweep, whatever its launches: the CSR once,
+        // each distinct input, scale and output once, the accumulator once
+        const bool last_sweep = k == p.Lmax;
+        double sweep_bytes = csr_bytes + (k == 1 ? sig : sig * active.size());
+        for (int c : active) sweep_bytes += 4.0 * N + (p.chains[c].L > k ? sig : 0.0);
+        if (sweep_terms || last_sweep) sweep_bytes += (contributed ? sig : 0.0) + sig;
+        if (last_sweep && p.reimpose) sweep_bytes += (double)N;
+        bool first_launch = true;
+
+        for (size_t gx = 0; gx < groups.size(); ++gx) {
+            const Group &gr = groups[gx];
+            const int nc = gr.nc;
+            const bool last = last_sweep && gx + 1 == groups.size();
             bool group_terms = false;
-            for (int q = 0; q < nc; ++q) group_terms |= p.chains[active[gi + q]].has_at[k];
-            const int kind = launch_kind(nc, k);
+            for (int q = 0; q < nc; ++q) group_terms |= p.chains[gr.c[q]].has_at[k];
+            const int kind = gr.kind;
             const Shape &shape = ss.kind[kind];
+            const int sv = shape_vec(p, shape);
             const std::vector<std::pair<int, int>> &slabs = plans[kind];
             for (size_t si = 0; si < slabs.size(); ++si) {
-                const int c0 = slabs[si].first, cw = slabs[si].second, W = cw * p.vec;
+                const int c0 = slabs[si].first, cw = slabs[si].second, W = cw * sv;
                 SweepArgs a;
                 std::memset(&a, 0, sizeof(a));
                 a.row_ptr = g->row_ptr;
@@ -303,9 +377,11 @@ void run_sweeps(gift_ctx *ctx, const Plan &p, ShapeSet ss, cudaStream_t st, std:
                 a.n_rows = N;
                 a.K = p.K;
                 a.c0 = c0;
-                double bytes = si == 0 ? csr_bytes : 0.0;
+                a.gpre2 = gr.gpre2;
+                const double bytes = first_launch ? sweep_bytes : 0.0;
+                first_launch = false;
                 for (int q = 0; q < nc; ++q) {
-                    const int c = active[gi + q];
+                    const int c = gr.c[q];
                     const Chain &ch = p.chains[c];
                     ChainIO &io = a.ch[q];
                     io.x = k == 1 ? p.din : p.X[c][(k - 1) % 2];
@@ -316,8 +392,6 @@ void run_sweeps(gift_ctx *ctx, const Plan &p, ShapeSet ss, cudaStream_t st, std:
                     io.has_term = ch.has_at[k] ? 1 : 0;
                     io.xnext = ch.L > k ? p.X[c][k % 2] : nullptr;
                     io.pnext = p.sc[c].pre;
-                    bytes += 4.0 * N * W + (si == 0 ? 4.0 * N : 0.0);  // input slab + scale
-                    if (io.xnext) bytes += 4.0 * N * W;
                 }
                 if (last) {
                     a.acc_in = contributed ? p.acc : nullptr;
@@ -325,101 +399,86 @@ void run_sweeps(gift_ctx *ctx, const Plan &p, ShapeSet ss, cudaStream_t st, std:
                     if (p.reimpose) {
                         a.fixed = g->is_fixed;
                         a.g_fixed = p.din;
-                        bytes += si == 0 ? (double)N : 0.0;
                     }
                 } else if (group_terms) {
                     a.acc_in = contributed ? p.acc : nullptr;
                     a.acc_out = p.acc;
                 }
-                if (a.acc_in) bytes += 4.0 * N * W;
-                if (a.acc_out) bytes += 4.0 * N * W;
+                const int nx = k == 1 ? 1 : nc;
+                const void *fn = nullptr;
+                int threads = kSweepThreads;
+                int grid = 1;
+                int smem = 0;
+                TmaArgs t;
+                CUtensorMap m0, m1;
+                SellArgs sa;
+                std::vector<void *> params;
                 if (shape.family == 2) {
-                    const int nx = k == 1 ? 1 : nc;
-                    const void *fn = sweep_tma_kernel(g->weight_dtype, W, nx, nc);
+                    fn = sweep_tma_kernel(g->weight_dtype, W, nx, nc);
                     GIFT_REQUIRE(fn != nullptr, "gift_filter: no TMA kernel for this shape");
                     GIFT_REQUIRE(tma_launch < p.ncounters, "gift_filter: too many TMA launches");
                     const int stage_bytes = sweep_tma_stage_bytes_f32(W, nx, nc);
                     const int stages = std::min(16, (ctx->max_smem_optin - 2048) / stage_bytes);
                     GIFT_REQUIRE(stages >= 2, "gift_filter: not enough shared memory for the TMA pipeline");
-                    const int smem = stages * stage_bytes + 1024;
+                    smem = stages * stage_bytes + 1024;
                     tma_set_smem(fn, smem);
-                    const CUtensorMap m0 = row_map(a.ch[0].x, N, p.K, W);
-                    const CUtensorMap m1 = nx == 2 ? row_map(a.ch[1].x, N, p.K, W) : m0;
-                    TmaArgs t;
+                    m0 = row_map(a.ch[0].x, N, p.K, W);
+                    m1 = nx == 2 ? row_map(a.ch[1].x, N, p.K, W) : m0;
                     t.tiles = ceil_div(std::max<int64_t>(N, 1), kTmaRows);
                     t.stages = stages;
                     t.stage_bytes = stage_bytes;
                     t.tile_counter = p.counters + tma_launch++;
                     t.error = ctx->dev_error;
-                    void *params[] = {&a, const_cast<CUtensorMap *>(&m0), const_cast<CUtensorMap *>(&m1), &t};
-                    LaunchTimer lt(ctx, st, "filter.sweep", bytes);
-                    TimedLaunch tl{kind, nullptr, nullptr};
-                    if (timed) {
-                        tl.e0 = pool->back(); pool->pop_back();
-                        tl.e1 = pool->back(); pool->pop_back();
-                        GIFT_CUDA(cudaEventRecord(tl.e0, st));
-                    }
-                    GIFT_CUDA(cudaLaunchKernel(fn, dim3(ctx->num_sms), dim3(32 + kTmaRows * (W / 4)), params, smem, st));
-                    if (timed) {
-                        GIFT_CUDA(cudaEventRecord(tl.e1, st));
-                        timed->push_back(tl);
-                    }
-                    continue;
-                }
-                if (shape.family == 3) {
-                    const int nx = k == 1 ? 1 : nc;
-                    const void *fn = sweep_sell_kernel(g->weight_dtype, p.vec, cw, nx, nc);
+                    params = {&a, &m0, &m1, &t};
+                    grid = ctx->num_sms;
+                    threads = 32 + kTmaRows * (W / 4);
+                } else if (shape.family == 3) {
+                    fn = sweep_sell_kernel(g->weight_dtype, p.vec, cw, nx, nc);
                     GIFT_REQUIRE(fn != nullptr, "gift_filter: no sliced-ELL kernel for this shape");
-                    SellArgs sa;
                     sa.nslices = g->sell.nslices;
                     sa.slice_ptr = g->sell.slice_ptr;
                     sa.perm = g->sell.perm;
                     sa.col = g->sell.col;
                     sa.val = g->sell.val;
-                    sa.gpre2 = (k == 1 && nc == 2) ? p.gpre2 : nullptr;
+                    sa.gpre2 = (k == 1 && nc == 2) ? gr.gpre2 : nullptr;
+                    threads = kSellThreads;
                     const int64_t want = ceil_div(std::max<int64_t>(sa.nslices, 1), kSellWarps);
-                    const int grid = (int)std::max<int64_t>(
-                        1, std::min<int64_t>(want, (int64_t)ctx->num_sms * occupancy_blocks(fn, kSellThreads)));
-                    void *params[] = {&a, &sa};
-                    LaunchTimer lt(ctx, st, "filter.sweep", bytes);
-                    TimedLaunch tl{kind, nullptr, nullptr};
-                    if (timed) {
-                        tl.e0 = pool->back(); pool->pop_back();
-                        tl.e1 = pool->back(); pool->pop_back();
-                        GIFT_CUDA(cudaEventRecord(tl.e0, st));
-                    }
-                    GIFT_CUDA(cudaLaunchKernel(fn, dim3(grid), dim3(kSellThreads), params, 0, st));
-                    if (timed) {
-                        GIFT_CUDA(cudaEventRecord(tl.e1, st));
-                        timed->push_back(tl);
-                    }
-                    continue;
-                }
-                const void *fn = nullptr;
-                int threads = kSweepThreads;
-                int64_t rows_per_block = 0;
-                if (shape.family == 0) {
-                    const int gl = std::max(shape.b, cw);
-                    fn = sweep_kernel(g->weight_dtype, p.vec, cw, gl, nc);
-                    rows_per_block = (kSweepThreads / 32) * (32 / gl);
+                    grid = (int)std::max<int64_t>(
+                        1, std::min<int64_t>(want, (int64_t)ctx->num_sms * occupancy_blocks(fn, threads)));
+                    params = {&a, &sa};
                 } else {
-                    fn = sweep_mp_kernel(g->weight_dtype, p.vec, cw * p.vec, nc);
-                    threads = kMpThreads;
-                    rows_per_block = kMpWarps * 32;
+                    int64_t rows_per_block = 0;
+                    if (shape.family == 0) {
+                        const int gl = std::max(shape.b, cw);
+                        fn = sweep_kernel(g->weight_dtype, p.vec, cw, gl, nc);
+                        rows_per_block = (kSweepThreads / 32) * (32 / gl);
+                    } else if (shape.family == 4) {
+                        const int u = (sv == 4 || nc == 2) ? std::min(shape.b, 4) : shape.b;
+                        fn = sweep_dr_kernel(g->weight_dtype, sv, cw, u, nc, k == 1);
+                        rows_per_block = (kSweepThreads / 32) * (32 / cw);
+                        if (!shape.natural) {
+                            a.order = g->order;
+                            a.n_slots = g->order_slots;
+                        }
+                    } else {
+                        fn = sweep_mp_kernel(g->weight_dtype, p.vec, cw * p.vec, nc);
+                        threads = kMpThreads;
+                        rows_per_block = kMpWarps * 32;
+                    }
+                    GIFT_REQUIRE(fn != nullptr, "gift_filter: no kernel for this shape");
+                    const int64_t want = ceil_div(std::max<int64_t>(N, 1), rows_per_block);
+                    grid = (int)std::max<int64_t>(
+                        1, std::min<int64_t>(want, (int64_t)ctx->num_sms * occupancy_blocks(fn, threads)));
+                    params = {&a};
                 }
-                GIFT_REQUIRE(fn != nullptr, "gift_filter: no kernel for this shape");
-                const int64_t want = ceil_div(std::max<int64_t>(N, 1), rows_per_block);
-                const int grid = (int)std::max<int64_t>(
-                    1, std::min<int64_t>(want, (int64_t)ctx->num_sms * occupancy_blocks(fn, threads)));
-                void *params[] = {&a};
                 LaunchTimer lt(ctx, st, "filter.sweep", bytes);
-                TimedLaunch tl{kind, nullptr, nullptr};
+                TimedLaunch tl{gr.planned, nullptr, nullptr};
                 if (timed) {
                     tl.e0 = pool->back(); pool->pop_back();
                     tl.e1 = pool->back(); pool->pop_back();
                     GIFT_CUDA(cudaEventRecord(tl.e0, st));
                 }
-                GIFT_CUDA(cudaLaunchKernel(fn, dim3(grid), dim3(threads), params, 0, st));
+                GIFT_CUDA(cudaLaunchKernel(fn, dim3(grid), dim3(threads), params.data(), smem, st));
                 if (timed) {
                     GIFT_CUDA(cudaEventRecord(tl.e1, st));
                     timed->push_back(tl);
@@ -428,6 +487,7 @@ void run_sweeps(gift_ctx *ctx, const Plan &p, ShapeSet ss, cudaStream_t st, std:
             if (group_terms && !last) contributed = true;
         }
     }
+    return planned_mask;
 }
 
 void run_sweeps_one(gift_ctx *ctx, const Plan &p, Shape shape, cudaStream_t st) {
@@ -448,8 +508,18 @@ std::string tune_key(const gift_graph *g, int vec, int K, const Plan &p) {
 
 // schedule codes: 4..32 (row groups, widest slab), 100*cw + g (row groups),
 // 1000 + w (merge-path, slab of w columns), 2000 + w (TMA gathers),
-// 3000 + w (sliced ELL)
+// 3000 + w (sliced ELL), 4000 + 100*n + 10*cw + u (direct row groups:
+// cw lanes per row, u gathers in flight per lane; n bit 0: float2 lanes,
+// n bit 1: rows in natural order rather than the graph's row order)
 Shape shape_from_schedule(int schedule) {
+    if (schedule >= 4000) {
+        Shape s{4, (schedule / 10) % 10, schedule % 10};
+        const int n = (schedule - 4000) / 100;
+        s.narrow = n & 1;
+        s.natural = (n >> 1) & 1;
+        if (n > 3) s.narrow = 2;  // invalid
+        return s;
+    }
     if (schedule >= 3000) return Shape{3, schedule - 3000, 1};
     if (schedule >= 2000) return Shape{2, schedule - 2000, 1};
     if (schedule >= 1000) return Shape{1, schedule - 1000, 1};
@@ -457,16 +527,24 @@ Shape shape_from_schedule(int schedule) {
     return Shape{0, 4, schedule};
 }
 
+int schedule_code(const Shape &sh) {
+    if (sh.family == 4) return 4000 + 100 * (sh.narrow + 2 * sh.natural) + 10 * sh.a + sh.b;
+    return sh.family >= 1 ? 1000 * sh.family + sh.a : 100 * sh.a + sh.b;
+}
+
 bool valid_shape(Shape s) {
+    if (s.family == 4)
+        return (s.narrow == 0 || s.narrow == 1) && (s.a == 1 || s.a == 2 || s.a == 4 || s.a == 8) &&
+               (s.b == 2 || s.b == 4 || s.b == 8);
     if (s.family == 3) return s.a == 2 || s.a == 4 || s.a == 8 || s.a == 16;
     if (s.family == 2) return s.a == 8 || s.a == 16;
     if (s.family == 1) return s.a == 2 || s.a == 4 || s.a == 8 || s.a == 16;
     return (s.a == 1 || s.a == 2 || s.a == 4) && (s.b == 4 || s.b == 8 || s.b == 16 || s.b == 32) && s.b >= s.a;
 }
 
-// Times the whole filter once per candidate shape (after one warm run) and keeps the fastest.
 // Times every candidate shape on the whole filter (after one warm run),
-// attributing each launch to its kind, and keeps the fastest shape per kind.
+// attributing each launch to its kind, and keeps the fastest shape per kind;
+// then times the two-chain kinds split into one launch per chain.
 ShapeSet autotune(gift_ctx *ctx, const Plan &p, cudaStream_t st) {
     const std::string key = tune_key(p.g, p.vec, p.K, p);
     {
@@ -475,6 +553,7 @@ ShapeSet autotune(gift_ctx *ctx, const Plan &p, cudaStream_t st) {
         if (it != ctx->tuned.end()) {
             ShapeSet ss;
             for (int kd = 0; kd < 4; ++kd) ss.kind[kd] = it->second.kind[kd];
+            for (int kd = 0; kd < 2; ++kd) ss.split[kd] = it->second.split[kd];
             return ss;
         }
     }
@@ -488,6 +567,22 @@ ShapeSet autotune(gift_ctx *ctx, const Plan &p, cudaStream_t st) {
     for (int cw : {4, 2, 1})
         for (int gg : {8, 16})
             if (gg >= 2 * cw && cw * p.vec <= std::max(p.K, p.vec)) cands.push_back(Shape{0, cw, gg});
+    // direct row groups: the widest slab and half of it, both vector widths
+    for (int narrow = 0; narrow <= (p.vec == 4 ? 1 : 0); ++narrow) {
+        const int sv = narrow ? 2 : p.vec;
+        int cwmax = 8;
+        while (cwmax > 1 && cwmax * sv > p.K) cwmax >>= 1;
+        for (int cw : {cwmax, cwmax / 2})
+            if (cw >= 1)
+                for (int u : {2, 4, 8})
+                    for (int natural = 0; natural <= 1; ++natural) {
+                        if (u == 8 && sv == 4) continue;
+                        Shape sh{4, cw, u};
+                        sh.narrow = narrow;
+                        sh.natural = natural;
+                        cands.push_back(sh);
+                    }
+    }
     const bool prof = ctx->profiling;
     ctx->profiling = false;
     std::vector<cudaEvent_t> pool;
@@ -498,36 +593,64 @@ ShapeSet autotune(gift_ctx *ctx, const Plan &p, cudaStream_t st) {
         for (auto e : pool) cudaEventDestroy(e);
         ctx->profiling = prof;
     };
+    // one warm run and one timed run of the whole filter; per planned kind ms
+    auto measure = [&](const ShapeSet &ss, double (&ms)[4], bool (&seen)[4]) {
+        GIFT_CUDA(cudaMemsetAsync(p.counters, 0, sizeof(int32_t) * p.ncounters, st));
+        run_sweeps(ctx, p, ss, st);
+        GIFT_CUDA(cudaMemsetAsync(p.counters, 0, sizeof(int32_t) * p.ncounters, st));
+        std::vector<TimedLaunch> timed;
+        std::vector<cudaEvent_t> avail = pool;
+        const size_t need = 2 * (size_t)(p.Lmax * (p.chains.size() + 1) * (p.K / 2 + 1));
+        while (avail.size() < need) {
+            cudaEvent_t e;
+            GIFT_CUDA(cudaEventCreate(&e));
+            pool.push_back(e);
+            avail.push_back(e);
+        }
+        run_sweeps(ctx, p, ss, st, &timed, &avail);
+        GIFT_CUDA(cudaStreamSynchronize(st));
+        for (int kd = 0; kd < 4; ++kd) {
+            ms[kd] = 0.0;
+            seen[kd] = false;
+        }
+        for (const TimedLaunch &t : timed) {
+            float m = 0.f;
+            GIFT_CUDA(cudaEventElapsedTime(&m, t.e0, t.e1));
+            ms[t.kind] += m;
+            seen[t.kind] = true;
+        }
+    };
     try {
         for (const Shape &s : cands) {
             ShapeSet ss;
             for (auto &k : ss.kind) k = s;
-            GIFT_CUDA(cudaMemsetAsync(p.counters, 0, sizeof(int32_t) * p.ncounters, st));
-            run_sweeps(ctx, p, ss, st);
-            GIFT_CUDA(cudaMemsetAsync(p.counters, 0, sizeof(int32_t) * p.ncounters, st));
-            std::vector<TimedLaunch> timed;
-            std::vector<cudaEvent_t> avail = pool;
-            const size_t need = 2 * (size_t)(p.Lmax * (p.chains.size() + 1) * (p.K / p.vec + 1));
-            while (avail.size() < need) {
-                cudaEvent_t e;
-                GIFT_CUDA(cudaEventCreate(&e));
-                pool.push_back(e);
-                avail.push_back(e);
-            }
-            run_sweeps(ctx, p, ss, st, &timed, &avail);
-            GIFT_CUDA(cudaStreamSynchronize(st));
-            double ms[4] = {0, 0, 0, 0};
-            bool seen[4] = {false, false, false, false};
-            for (const TimedLaunch &t : timed) {
-                float m = 0.f;
-                GIFT_CUDA(cudaEventElapsedTime(&m, t.e0, t.e1));
-                ms[t.kind] += m;
-                seen[t.kind] = true;
-            }
+            double ms[4];
+            bool seen[4];
+            measure(ss, ms, seen);
             for (int kd = 0; kd < 4; ++kd)
                 if (seen[kd] && ms[kd] < best_ms[kd]) {
                     best_ms[kd] = ms[kd];
                     best.kind[kd] = s;
+                }
+        }
+        // the sliced-ELL format has one slab width per graph: keep SELL only
+        // where it matches the width of the first kind that chose it
+        int sell_a = 0;
+        for (int kd = 0; kd < 4; ++kd)
+            if (best.kind[kd].family == 3) {
+                if (sell_a == 0) sell_a = best.kind[kd].a;
+                else if (best.kind[kd].a != sell_a) best.kind[kd] = Shape{0, 4, 8};
+            }
+        if (p.chains.size() >= 2) {
+            ShapeSet ss = best;
+            ss.split[0] = ss.split[1] = true;
+            double ms[4];
+            bool seen[4];
+            measure(ss, ms, seen);
+            for (int kd = 0; kd < 2; ++kd)
+                if (seen[kd] && ms[kd] < best_ms[kd]) {
+                    best_ms[kd] = ms[kd];
+                    best.split[kd] = true;
                 }
         }
     } catch (...) {
@@ -538,6 +661,7 @@ ShapeSet autotune(gift_ctx *ctx, const Plan &p, cudaStream_t st) {
     std::lock_guard<std::mutex> lk(ctx->tune_mu);
     TunedSet ts;
     for (int kd = 0; kd < 4; ++kd) ts.kind[kd] = best.kind[kd];
+    for (int kd = 0; kd < 2; ++kd) ts.split[kd] = best.split[kd];
     ctx->tuned[key] = ts;
     return best;
 }
@@ -553,8 +677,10 @@ void filter_impl(gift_ctx *ctx, const gift_graph *cg, const gift_filter_spec *sp
     GIFT_REQUIRE(spec->num_terms >= 1 && spec->num_terms <= GIFT_MAX_TERMS, "gift_filter: num_terms out of range");
     GIFT_REQUIRE(spec->norm == GIFT_NORM_SYM || spec->norm == GIFT_NORM_RW, "gift_filter: unknown norm");
     GIFT_REQUIRE(spec->reimpose_fixed == 0 || spec->reimpose_fixed == 1, "gift_filter: reimpose_fixed is 0 or 1");
-    GIFT_REQUIRE(spec->schedule == 0 || valid_shape(shape_from_schedule(spec->schedule)),
-                 "gift_filter: schedule is 0 (autotune), 4..32, 100*cw + lanes, or 1000/2000/3000 + slab width");
+    const bool split_sched = spec->schedule >= 10000;
+    const int sched = split_sched ? spec->schedule - 10000 : spec->schedule;
+    GIFT_REQUIRE(spec->schedule == 0 || (sched >= 4 && valid_shape(shape_from_schedule(sched))),
+                 "gift_filter: schedule is 0 (autotune), a kernel shape code, or 10000 + a shape code");
     const int64_t N = g->n;
     const int32_t K = 2 * S;
     GIFT_REQUIRE((int64_t)K * N < (int64_t)1 << 40, "gift_filter: signal too large");
@@ -616,15 +742,18 @@ void filter_impl(gift_ctx *ctx, const gift_graph *cg, const gift_filter_spec *sp
     p.sc.resize(p.chains.size());
     for (size_t c = 0; c < p.chains.size(); ++c) p.sc[c] = graph_scale(ctx, g, p.chains[c].sigma, spec->norm, st);
 
-    DevBuf gpre2_buf;
-    p.gpre2 = nullptr;
-    if (p.chains.size() >= 2 && p.sc[0].pre && p.sc[1].pre) {
-        gpre2_buf = DevBuf(ctx, sizeof(float2) * (size_t)std::max<int64_t>(N, 1), st);
+    std::vector<DevBuf> gpre2_bufs;  // packed first-sweep scales per chain pair
+    for (size_t c = 0; c + 1 < p.chains.size(); c += 2) {
+        if (!p.sc[c].pre || !p.sc[c + 1].pre) {
+            p.gpre2.push_back(nullptr);
+            continue;
+        }
+        gpre2_bufs.emplace_back(ctx, sizeof(float2) * (size_t)std::max<int64_t>(N, 1), st);
         LaunchTimer lt(ctx, st, "filter.scale", 16.0 * N);
-        k_pack2<<<(int)std::min<int64_t>(ceil_div(N, 256), (int64_t)ctx->num_sms * 8), 256, 0, st>>>(
-            N, p.sc[0].pre, p.sc[1].pre, gpre2_buf.as<float2>());
+        k_pack2<<<(int)std::max<int64_t>(1, std::min<int64_t>(ceil_div(N, 256), (int64_t)ctx->num_sms * 8)), 256, 0,
+                  st>>>(N, p.sc[c].pre, p.sc[c + 1].pre, gpre2_bufs.back().as<float2>());
         check_launch("k_pack2");
-        p.gpre2 = gpre2_buf.as<float2>();
+        p.gpre2.push_back(gpre2_bufs.back().as<float2>());
     }
     p.ncounters = 1024;
     DevBuf counters(ctx, sizeof(int32_t) * p.ncounters, st);
@@ -633,13 +762,17 @@ void filter_impl(gift_ctx *ctx, const gift_graph *cg, const gift_filter_spec *sp
     if (spec->schedule == 0) {
         ss = autotune(ctx, p, st);
     } else {
-        for (auto &k : ss.kind) k = shape_from_schedule(spec->schedule);
+        for (auto &k : ss.kind) k = shape_from_schedule(sched);
+        ss.split[0] = ss.split[1] = split_sched;
     }
     GIFT_CUDA(cudaMemsetAsync(p.counters, 0, sizeof(int32_t) * p.ncounters, st));
-    run_sweeps(ctx, p, ss, st);
+    const int used = run_sweeps(ctx, p, ss, st);
     for (int kd = 0; kd < 4; ++kd) {
-        const Shape &sh = ss.kind[kd];
-        ctx->last_schedules[kd] = sh.family >= 1 ? 1000 * sh.family + sh.a : 100 * sh.a + sh.b;
+        // a split two-chain kind reports 10000 + the one-chain kind's code
+        const bool split = kd < 2 && ss.split[kd];
+        ctx->last_schedules[kd] = !(used >> kd & 1) ? 0
+                                  : split           ? 10000 + schedule_code(ss.kind[kd + 2])
+                                                    : schedule_code(ss.kind[kd]);
     }
 
     if (mem == GIFT_MEM_HOST) {
@@ -670,7 +803,7 @@ size_t filter_scratch_bytes(const gift_graph *g, const gift_filter_spec *spec, i
     size_t bytes = sig;                                         // accumulator
     for (int l : L) bytes += l >= 2 ? 2 * sig : 0;              // ping-pong inputs
     bytes += sigmas.size() * ((sizeof(float) * g->n + 255) / 256 * 256);  // scale vectors
-    bytes += (sizeof(float2) * g->n + 255) / 256 * 256;         // packed first-sweep scales
+    bytes += sigmas.size() / 2 * ((sizeof(float2) * g->n + 255) / 256 * 256);  // packed first-sweep scales
     return bytes + 256 * (8 + 2 * sigmas.size());               // alignment slack
 }
 
@@ -749,12 +882,15 @@ void filter_on_scratch(gift_ctx *ctx, const gift_graph *g, const gift_filter_spe
         p.sc[c].post = v;
         p.sc[c].pre = spec->norm == GIFT_NORM_SYM ? v : nullptr;
     }
-    p.gpre2 = nullptr;
-    if (p.chains.size() >= 2 && p.sc[0].pre && p.sc[1].pre) {
+    for (size_t c = 0; c + 1 < p.chains.size(); c += 2) {
+        if (!p.sc[c].pre || !p.sc[c + 1].pre) {
+            p.gpre2.push_back(nullptr);
+            continue;
+        }
         float2 *v = static_cast<float2 *>(take(sizeof(float2) * N));
-        k_pack2<<<grid, 256, 0, st>>>(N, p.sc[0].pre, p.sc[1].pre, v);
+        k_pack2<<<grid, 256, 0, st>>>(N, p.sc[c].pre, p.sc[c + 1].pre, v);
         check_launch("k_pack2");
-        p.gpre2 = v;
+        p.gpre2.push_back(v);
     }
     p.counters = nullptr;
     p.ncounters = 0;
@@ -765,11 +901,15 @@ void filter_on_scratch(gift_ctx *ctx, const gift_graph *g, const gift_filter_spe
         std::lock_guard<std::mutex> lk(ctx->tune_mu);
         auto it = ctx->tuned.find(tune_key(g, p.vec, K, p));
         if (it != ctx->tuned.end()) {
+            bool ok[4];
             for (int kd = 0; kd < 4; ++kd) {
                 const Shape t = it->second.kind[kd];
                 const int rps = t.family == 3 ? 32 / (sell_width(p, t.a) / p.vec) : 0;
-                if (t.family == 0 || t.family == 1 || (t.family == 3 && g->sell.rps == rps)) ss.kind[kd] = t;
+                ok[kd] = t.family == 0 || t.family == 1 || (t.family == 4 && (t.natural || g->order)) ||
+                         (t.family == 3 && g->sell.rps == rps);
+                if (ok[kd]) ss.kind[kd] = t;
             }
+            for (int kd = 0; kd < 2; ++kd) ss.split[kd] = it->second.split[kd] && ok[kd + 2];
         }
     }
     run_sweeps(ctx, p, ss, st);

@@ -69,10 +69,14 @@ struct KernelRecord {
 
 struct TunedShape {
     int family, a, b;
+    int narrow = 0;   // direct family: float2 lanes instead of the signal's widest vector
+    int natural = 0;  // direct family: rows in natural order instead of the graph's row order
 };
-// tuned shape per launch kind (see filter.cu)
+// tuned shape per launch kind (see filter.cu); split[kind] for the two-chain
+// kinds 0 and 1: run each chain as its own launch with the one-chain shape
 struct TunedSet {
     TunedShape kind[4];
+    bool split[2] = {false, false};
 };
 
 struct PendingTiming {
@@ -206,12 +210,17 @@ struct gift_graph {
         float *post;
     };
     std::vector<Scale> scales;
+    // rows sorted by length (longest first, ties by row) within windows of 256
+    // rows, -1 for the padding past N; built on first use by a schedule that
+    // walks rows in this order (direct row groups, sliced ELL)
+    int32_t *order = nullptr;
+    int64_t order_slots = 0;
     // sliced-ELL execution format (built on first use by a sliced-ELL schedule)
     struct Sell {
         int rps = 0;              // rows per slice (0: not built)
         int64_t nslices = 0;
         int64_t entries = 0;
-        int32_t *perm = nullptr;
+        int32_t *perm = nullptr;  // the graph's row order
         int64_t *slice_ptr = nullptr;
         int32_t *col = nullptr;
         void *val = nullptr;
@@ -224,6 +233,8 @@ namespace gift {
 void build_graph_impl(gift_ctx *ctx, const gift_netlist *nl, const gift_build_opts *opts, gift_graph **out,
                       cudaStream_t st);
 void release_graph(gift_graph *g, cudaStream_t st);
+// builds g->order if absent (caller holds g->mu)
+void ensure_row_order(gift_ctx *ctx, gift_graph *g, cudaStream_t st);
 // sell.cu
 void build_sell(gift_ctx *ctx, gift_graph *g, int rps, cudaStream_t st);
 void release_sell(gift_graph *g, cudaStream_t st);

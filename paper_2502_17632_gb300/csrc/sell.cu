@@ -95,21 +95,37 @@ __global__ void k_sell_fill(int64_t nslices, int rps, const int64_t *__restrict_
 
 }  // namespace
 
-void build_sell(gift_ctx *ctx, gift_graph *g, int rps, cudaStream_t st) {
-    GIFT_REQUIRE(rps == 8 || rps == 16 || rps == 32, "sell: rows per slice must be 8, 16 or 32");
+void ensure_row_order(gift_ctx *ctx, gift_graph *g, cudaStream_t st) {
+    if (g->order) return;
     const int64_t N = g->n;
     const int64_t windows = ceil_div(N, kSellWindow);
     const int64_t padded = windows * kSellWindow;
-    const int64_t nslices = padded / rps;
     DevBuf perm(ctx, sizeof(int32_t) * padded, st);
+    {
+        LaunchTimer lt(ctx, st, "build.row_order", 16.0 * N + 4.0 * padded);
+        k_sell_order<<<(unsigned)windows, kSellWindow, 0, st>>>(N, g->row_ptr, perm.as<int32_t>(), padded);
+        check_launch("k_sell_order");
+    }
+    g->order = perm.as<int32_t>();
+    g->order_slots = padded;
+    perm.release();
+    g->device_bytes += (int64_t)(4 * padded);
+}
+
+void build_sell(gift_ctx *ctx, gift_graph *g, int rps, cudaStream_t st) {
+    GIFT_REQUIRE(rps == 8 || rps == 16 || rps == 32, "sell: rows per slice must be 8, 16 or 32");
+    const int64_t N = g->n;
+    ensure_row_order(ctx, g, st);
+    const int64_t padded = g->order_slots;
+    const int64_t nslices = padded / rps;
+    const int32_t *perm = g->order;
     DevBuf sizes(ctx, sizeof(int64_t) * nslices, st);
     DevBuf slice_ptr(ctx, sizeof(int64_t) * (nslices + 1), st);
     {
-        LaunchTimer lt(ctx, st, "build.sell_order", 16.0 * N + 4.0 * padded);
-        k_sell_order<<<(unsigned)windows, kSellWindow, 0, st>>>(N, g->row_ptr, perm.as<int32_t>(), padded);
+        LaunchTimer lt(ctx, st, "build.sell_sizes", 16.0 * nslices);
         k_sell_sizes<<<(unsigned)std::min<int64_t>(ceil_div(nslices, 256), (int64_t)ctx->num_sms * 8), 256, 0, st>>>(
-            nslices, rps, g->row_ptr, perm.as<int32_t>(), sizes.as<int64_t>());
-        check_launch("k_sell_order");
+            nslices, rps, g->row_ptr, perm, sizes.as<int64_t>());
+        check_launch("k_sell_sizes");
     }
     {
         LaunchTimer lt(ctx, st, "build.scan", 16.0 * nslices, 3);
@@ -126,35 +142,33 @@ void build_sell(gift_ctx *ctx, gift_graph *g, int rps, cudaStream_t st) {
         const int grid = (int)std::min<int64_t>(ceil_div(nslices * 32, 256), (int64_t)ctx->num_sms * 16);
         if (g->weight_dtype == GIFT_WEIGHT_F32)
             k_sell_fill<float><<<grid, 256, 0, st>>>(nslices, rps, g->row_ptr, g->col, (const float *)g->val,
-                                                     perm.as<int32_t>(), slice_ptr.as<int64_t>(), scol.as<int32_t>(),
+                                                     perm, slice_ptr.as<int64_t>(), scol.as<int32_t>(),
                                                      sval.as<float>());
         else if (g->weight_dtype == GIFT_WEIGHT_BF16)
             k_sell_fill<__nv_bfloat16><<<grid, 256, 0, st>>>(nslices, rps, g->row_ptr, g->col,
-                                                             (const __nv_bfloat16 *)g->val, perm.as<int32_t>(),
+                                                             (const __nv_bfloat16 *)g->val, perm,
                                                              slice_ptr.as<int64_t>(), scol.as<int32_t>(),
                                                              sval.as<__nv_bfloat16>());
         else
             k_sell_fill<__half><<<grid, 256, 0, st>>>(nslices, rps, g->row_ptr, g->col, (const __half *)g->val,
-                                                      perm.as<int32_t>(), slice_ptr.as<int64_t>(), scol.as<int32_t>(),
+                                                      perm, slice_ptr.as<int64_t>(), scol.as<int32_t>(),
                                                       sval.as<__half>());
         check_launch("k_sell_fill");
     }
     g->sell.rps = rps;
     g->sell.nslices = nslices;
     g->sell.entries = total;
-    g->sell.perm = perm.as<int32_t>();
+    g->sell.perm = g->order;
     g->sell.slice_ptr = slice_ptr.as<int64_t>();
     g->sell.col = scol.as<int32_t>();
     g->sell.val = sval.p;
-    perm.release();
     slice_ptr.release();
     scol.release();
     sval.release();
-    g->device_bytes += (int64_t)(4 * padded + 8 * (nslices + 1) + (4 + wsz) * total);
+    g->device_bytes += (int64_t)(8 * (nslices + 1) + (4 + wsz) * total);
 }
 
 void release_sell(gift_graph *g, cudaStream_t st) {
-    dev_free(g->sell.perm, st);
     dev_free(g->sell.slice_ptr, st);
     dev_free(g->sell.col, st);
     dev_free(g->sell.val, st);

@@ -47,6 +47,9 @@ struct SweepArgs {
     float *acc_out;       // non-null: write contributions (+acc_in)
     const uint8_t *fixed; // non-null: rows with fixed[i] != 0 take g_fixed
     const float *g_fixed;
+    const float2 *gpre2;  // first sweep with two chains: (pre_0[j], pre_1[j]) packed, or null
+    const int32_t *order; // direct row groups: row of each slot (-1: none), or null = identity
+    int64_t n_slots;      // slots in order
 };
 
 // ---- loads with L2 eviction priority: the CSR is streamed once per pass

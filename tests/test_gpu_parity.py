@@ -132,7 +132,7 @@ def run_filter(ctx, nl, g, wd="f32", spec=None, device=True):
 
 @pytest.mark.parametrize("name", sorted(NETLISTS))
 @pytest.mark.parametrize("S", [1, 2, 3, 8])
-@pytest.mark.parametrize("schedule", [0, 416, 1016, 1004, 3002])
+@pytest.mark.parametrize("schedule", [0, 416, 1016, 1004, 3002, 4042, 14044, 4148, 4244])
 def test_filter_parity(ctx, name, S, schedule):
     nl = NETLISTS[name]
     g = synth.make_signals(nl, S, 1234 + S)
@@ -146,7 +146,9 @@ def test_filter_parity(ctx, name, S, schedule):
 
 @pytest.mark.parametrize("S", [1, 2, 4, 5, 8, 9, 16])
 @pytest.mark.parametrize("schedule", [0, 4, 8, 16, 32, 108, 132, 204, 216, 408, 416, 432,
-                                      1002, 1004, 1008, 1016, 2008, 2016, 3002, 3004, 3008, 3016])
+                                      1002, 1004, 1008, 1016, 2008, 2016, 3002, 3004, 3008, 3016,
+                                      4012, 4014, 4022, 4024, 4042, 4044, 4082, 4084, 4112, 4118, 4142,
+                                      4148, 4182, 4188, 4244, 4342, 4388, 10408, 13008, 14042, 14148, 14244])
 def test_filter_shapes_and_schedules(ctx, S, schedule):
     nl = NETLISTS["repeat-cells"]
     g = synth.make_signals(nl, S, 99 + S)
@@ -186,12 +188,17 @@ def test_filter_tma_and_sell(ctx, name, S, schedule):
     (((4.0, 4, 1.0),), "sym", True),
     (((2.0, 1, 0.3), (2.0, 3, 0.7)), "sym", True),
     (((1.0, 1, 0.2), (2.0, 2, 0.2), (3.0, 3, 0.2), (4.0, 4, 0.2), (5.0, 5, 0.2)), "sym", True),
+    (((1.0, 1, 0.25), (2.0, 2, 0.25), (3.0, 3, 0.25), (4.0, 4, 0.25)), "sym", True),  # two chain pairs
+    (((1.0, 1, 0.25), (2.0, 2, 0.25), (3.0, 3, 0.25), (4.0, 4, 0.25)), "rw", True),
 ])
-def test_filter_general_specs(ctx, terms, norm, reimpose):
+@pytest.mark.parametrize("schedule", [0, 3008, 4042, 14042, 408])
+def test_filter_general_specs(ctx, terms, norm, reimpose, schedule):
+    """Chains grouped in pairs, one chain left over, both normalisations; the
+    first sweep of every pair gathers g once with that pair's two scales."""
     nl = NETLISTS["plain-10k"]
     g = synth.make_signals(nl, 2, 5)
     spec = gift.make_spec(terms=terms, norm=gift.GIFT_NORM_RW if norm == "rw" else gift.GIFT_NORM_SYM,
-                          reimpose=reimpose)
+                          reimpose=reimpose, schedule=schedule)
     got = run_filter(ctx, nl, g, spec=spec)
     _, _, ref = oracle.run(nl, g.reshape(nl.num_cells, -1), terms=terms, norm=norm, reimpose=reimpose)
     assert rel_err(got, ref.reshape(g.shape), g).max() <= RTOL
@@ -279,7 +286,8 @@ def test_invalid_filter_args(ctx):
             gift.gift_filter(ctx, h, g, g, None)  # overlap
         with pytest.raises(gift.GiftError):
             gift.gift_filter(ctx, h, g, out, None, num_signals=0)
-        for bad in (1, 2, 3, 404 + 1, 800 + 16, 216 + 100, 1161, 1003, 1032):
+        for bad in (1, 2, 3, 404 + 1, 800 + 16, 216 + 100, 1161, 1003, 1032, 4043, 4062, 4442, 4041,
+                    10000, 10003, 19999, 20000):
             with pytest.raises(gift.GiftError) as e:
                 gift.gift_filter(ctx, h, g, out, gift.make_spec(schedule=bad))
             assert e.value.status == gift.GIFT_ERR_INVALID
