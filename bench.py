@@ -38,7 +38,7 @@ UNIT = "edge-updates/s"
 def parse():
     p = argparse.ArgumentParser()
     p.add_argument("--gpus", type=int, default=1)
-    p.add_argument("--steps", type=int, default=10)
+    p.add_argument("--steps", type=int, default=50)
     p.add_argument("--warmup", type=int, default=3)
     p.add_argument("--impl", default="ours", choices=["ours", "reference"])
     p.add_argument("--workload", default="large-2.2m", choices=sorted(synth.WORKLOADS))
@@ -80,10 +80,16 @@ class ClockSampler:
     def __enter__(self):
         try:
             self.proc = subprocess.Popen(["nvidia-smi", "-i", str(self.index), f"--query-gpu={self.Q}",
-                                          "--format=csv,noheader,nounits", "-lms", "200"],
+                                          "--format=csv,noheader,nounits", "-lms", "100"],
                                          stdout=subprocess.PIPE, stderr=subprocess.DEVNULL, text=True)
             self.t = threading.Thread(target=self._read, daemon=True)
             self.t.start()
+            # the sampler is running once its first line arrives; keep only
+            # the samples taken from here on (the timed region)
+            t0 = time.time()
+            while not self.lines and time.time() - t0 < 5.0:
+                time.sleep(0.01)
+            self.lines = []
         except Exception:
             self.proc = None
         return self
@@ -121,8 +127,11 @@ class ClockSampler:
 
 
 # ----------------------------------------------------------------- traffic record
-SWEEP_SOURCES = ("sweep.cuh", "sweep_mp.cuh", "sweep_tma.cuh", "sell.cuh", "sell.cu", "filter.cu",
-                 "sweep_f32.cu", "sweep_bf16.cu", "sweep_f16.cu", "internal.cuh")
+# device sources of the sweep kernels: a recorded DRAM traffic figure is void
+# once any of them changes
+SWEEP_SOURCES = ("sweep.cuh", "sweep_mp.cuh", "sweep_dr.cuh", "sweep_tma.cuh", "sell.cuh",
+                 "sweep_f32.cu", "sweep_bf16.cu", "sweep_f16.cu", "sweep_dr_f32.cu", "sweep_dr_bf16.cu",
+                 "sweep_dr_f16.cu")
 
 
 def sweep_source_hash() -> str:
@@ -133,15 +142,15 @@ def sweep_source_hash() -> str:
     return h.hexdigest()[:16]
 
 
-def recorded_traffic(kernel: str, workload: str, weights: str):
+def recorded_traffic(kernel: str, workload: str, weights: str, schedule):
     """DRAM bytes per launch from a committed ncu summary, if it was taken on
-    the current kernel source."""
+    the current kernel source with the same tuned schedule."""
     path = os.path.join(ROOT, "profiles", "traffic.json")
     try:
         with open(path) as f:
             rec = json.load(f)
         r = rec[kernel][f"{workload}/{weights}"]
-        if r.get("source_hash") != sweep_source_hash():
+        if r.get("source_hash") != sweep_source_hash() or list(r.get("sweep_schedule", [])) != list(schedule):
             return None
         return r["dram_bytes_per_launch"]
     except Exception:
@@ -317,7 +326,7 @@ def run_ours(args):
     roofline = {"bound": "hbm", "kernel": tname, "achieved": achieved, "peak": peak, "unit": "GB/s",
                 "frac": achieved / peak, "peak_source": f"hbm_gbs, {peak_src}",
                 "alg_bytes_per_launch": per_launch_bytes, "ms_per_launch": per_launch_ms,
-                "traffic": recorded_traffic(tname, args.workload, args.weights)}
+                "traffic": recorded_traffic(tname, args.workload, args.weights, schedule)}
     breakdown = {k: {"ms_per_step": v["total_ms"] / args.steps, "kernels_per_step": v["kernels"] / args.steps,
                      "alg_GBps": (v["alg_bytes"] / (v["total_ms"] * 1e-3) / 1e9) if v["total_ms"] > 0 else None}
                  for k, v in sorted(stats.items())}
@@ -333,7 +342,7 @@ def run_ours(args):
         gift.gift_ctx_set_profiling(ctx, True)
         f0, f1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
         f0.record(stream)
-        reps = max(args.steps, 5)
+        reps = 20
         for _ in range(reps):
             gift.gift_filter(ctx, h, d_g, d_out, stream=stream)
         f1.record(stream)

@@ -193,12 +193,17 @@ k_hpwl_groups(int32_t E, int32_t S, const int64_t *__restrict__ net_ptr, const i
     }
 }
 
+// Warp per signal: lane l sums partials l, l + 32, ... in order, then a fixed
+// xor tree combines the lanes (deterministic for a given block count).
 __global__ void k_hpwl_final(int32_t S, int32_t nblocks, const double *__restrict__ partial, double *__restrict__ out) {
-    for (int s = threadIdx.x; s < S; s += blockDim.x) {
-        double t = 0.0;
-        for (int b = 0; b < nblocks; ++b) t += partial[(int64_t)s * nblocks + b];
-        out[s] = t;
-    }
+    const int lane = threadIdx.x & 31;
+    const int64_t s = blockIdx.x * (int64_t)(blockDim.x / 32) + threadIdx.x / 32;
+    if (s >= S) return;  // whole warps
+    double t = 0.0;
+    for (int b = lane; b < nblocks; b += 32) t += partial[s * nblocks + b];
+#pragma unroll
+    for (int o = 16; o > 0; o >>= 1) t += __shfl_xor_sync(0xffffffffu, t, o);
+    if (lane == 0) out[s] = t;
 }
 
 }  // namespace
@@ -238,7 +243,7 @@ void hpwl_impl(gift_ctx *ctx, const gift_graph *g, const float *xy, int S, doubl
                                                                     reinterpret_cast<const float2 *>(dxy),
                                                                     partial.as<double>());
         }
-        k_hpwl_final<<<1, 128, 0, st>>>(S, nblocks, partial.as<double>(), dout.as<double>());
+        k_hpwl_final<<<(unsigned)ceil_div(S, 4), 128, 0, st>>>(S, nblocks, partial.as<double>(), dout.as<double>());
         check_launch("k_hpwl");
     }
     GIFT_CUDA(cudaMemcpyAsync(out, dout.p, sizeof(double) * S, cudaMemcpyDeviceToHost, st));
