@@ -46,6 +46,9 @@ def parse():
     p.add_argument("--scale", type=float, default=1.0, help="shrink the workload (profiling captures only)")
     p.add_argument("--no-cpu-baseline", action="store_true")
     p.add_argument("--no-e2e", action="store_true")
+    p.add_argument("--no-serve", action="store_true", help="skip the serving measurement")
+    p.add_argument("--serve-requests", type=int, default=240)
+    p.add_argument("--serve-rate", type=float, default=40.0, help="Poisson arrival rate, requests/s")
     p.add_argument("--capture", action="store_true",
                    help="tune and warm the filter, then run one filter call inside the NVTX range 'capture' and exit "
                         "(the command an ncu capture of the sweep kernels runs)")
@@ -159,17 +162,32 @@ def recorded_traffic(kernel: str, workload: str, weights: str, schedule):
 
 # ----------------------------------------------------------------- oracle (CPU)
 def oracle_sample(nl, g, num_signals: int = 1):
-    """Oracle build + filter on the netlist with `num_signals` signals; returns (seconds, edge-updates)."""
+    """Oracle build + filter + HPWL on the netlist with the first `num_signals`
+    signals; returns (seconds, edge-updates, output [N][num_signals][2], HPWL)."""
     import oracle  # CPU baseline leg only
 
     gs = np.ascontiguousarray(g[:, :num_signals, :]).reshape(nl.num_cells, -1)
     t0 = time.perf_counter()
     G = oracle.build_graph(nl.num_cells, nl.net_ptr, nl.pin_cell)
     d = oracle.degrees(G)
-    out = oracle.gift(G, d, gs, nl.is_fixed)
-    oracle.hpwl(nl.net_ptr, nl.pin_cell, out.reshape(nl.num_cells, num_signals, 2))
+    out = oracle.gift(G, d, gs, nl.is_fixed).reshape(nl.num_cells, num_signals, 2)
+    hp = oracle.hpwl(nl.net_ptr, nl.pin_cell, out)
     dt = time.perf_counter() - t0
-    return dt, 6.0 * G.nnz * num_signals
+    return dt, 6.0 * G.nnz * num_signals, out, hp
+
+
+def precision_report(g0, outs, hps, ref, hp_ref):
+    """Per weight type: coordinate error of signal 0 against the FP64 oracle
+    (exact weights) and the HPWL delta of the produced placement."""
+    floor = 1e-3 * max(float(np.abs(g0).max()), 1e-30)
+    rep = {}
+    for w, o in outs.items():
+        err = np.abs(o.astype(np.float64) - ref)
+        rel = err / np.maximum(np.abs(ref), floor)
+        rep[w] = {"max_rel_err": float(rel.max()), "mean_rel_err": float(rel.mean()),
+                  "max_abs_err": float(err.max()), "hpwl": hps[w], "hpwl_oracle": float(hp_ref),
+                  "hpwl_rel_delta": (hps[w] - float(hp_ref)) / float(hp_ref)}
+    return rep
 
 
 def run_reference(args):
@@ -185,7 +203,7 @@ def run_reference(args):
         oracle_sample(nl, g)
     times, units = [], 0.0
     for _ in range(args.steps):
-        dt, u = oracle_sample(nl, g)
+        dt, u, _, _ = oracle_sample(nl, g)
         times.append(dt)
         units += u
     total = sum(times)
@@ -199,6 +217,100 @@ def run_reference(args):
         "e2e": {"value": v, "unit": UNIT, "h2d_bytes_per_step": 0, "d2h_bytes_per_step": 0},
     }
     print(json.dumps(line), flush=True)
+
+
+# ----------------------------------------------------------------- serving
+def serve_pool(num: int = 12, seed: int = synth.SEED0 + 4):
+    """Netlists of the serving workload: cells log-uniform in [10k, 1.3M], 1 %
+    fixed IO, nets/cell uniform in [1.0, 1.2], the pin-count law of the other
+    workloads, 4 signals each."""
+    u = synth.uniform(seed, synth.T_MISC, np.arange(2 * num, dtype=np.uint64)).reshape(num, 2)
+    pool = []
+    for k in range(num):
+        n = int(round(np.exp(np.log(1e4) + u[k, 0] * (np.log(1.3e6) - np.log(1e4)))))
+        nf = max(1, n // 100)
+        nl = synth.make_netlist(n - nf, nf, int(round(n * (1.0 + 0.2 * u[k, 1]))), seed * 1000 + k)
+        pool.append((nl, synth.make_signals(nl, 4, seed * 1000 + k)))
+    return pool
+
+
+def run_serving(args, gift):
+    """Poisson arrivals through the request loop (FP32 and BF16 requests
+    alternating) against the serial plain FP32 path (one request at a time
+    through gift_build_graph + gift_filter + gift_hpwl, host buffers) on the
+    same arrival sequence.  Latency = result ready - arrival."""
+    import threading as th
+    pool = serve_pool()
+    warm = max(1, args.serve_requests // 10)
+    total = args.serve_requests + warm
+    arrivals = synth.arrival_times(total, args.serve_rate, synth.SEED0 + 4)
+    reqs = [(pool[k % len(pool)], "bf16" if k % 2 else "f32") for k in range(total)]
+
+    def summary(lat, t_first, t_last, eu):
+        lat = np.sort(np.asarray(lat))
+        pick = lambda q: float(lat[min(len(lat) - 1, max(0, int(np.ceil(q * len(lat))) - 1))])  # noqa: E731
+        span = t_last - t_first
+        return {"p50_ms": pick(0.5), "p99_ms": pick(0.99), "mean_ms": float(lat.mean()), "max_ms": float(lat[-1]),
+                "requests_per_s": len(lat) / span, "edge_updates_per_s": eu / span}
+
+    # served
+    srv = gift.gift_serve_create(max_slots=8)
+    tickets = [None] * total
+    t0 = time.perf_counter() + 0.2
+
+    def submitter():
+        for k, ((nl, g), wd) in enumerate(reqs):
+            dt = t0 + arrivals[k] - time.perf_counter()
+            if dt > 0:
+                time.sleep(dt)
+            tickets[k] = gift.gift_serve_submit(srv, nl.num_cells, nl.net_ptr, nl.pin_cell, nl.is_fixed, g,
+                                                gift.WEIGHT[wd])
+
+    th_sub = th.Thread(target=submitter)
+    th_sub.start()
+    lat, eu, done_t = [], 0.0, []
+    for k, ((nl, g), wd) in enumerate(reqs):
+        while tickets[k] is None:
+            time.sleep(0.0002)
+        out, hp, st = gift.gift_serve_wait(srv, tickets[k], nl.num_cells, g.shape[1])
+        if k >= warm:
+            lat.append(st.latency_ms)
+            eu += 6.0 * st.nnz * g.shape[1]
+            done_t.append(time.perf_counter())
+    th_sub.join()
+    sst = gift.gift_serve_stats_get(srv)
+    gift.gift_serve_destroy(srv)
+    served = summary(lat, t0 + arrivals[warm], max(done_t), eu)
+    served.update({"peak_running": sst.peak_running, "max_slots": sst.max_slots,
+                   "peak_footprint_gb": sst.peak_footprint_bytes / 1e9})
+
+    # serial plain FP32 path on the same arrivals
+    ctx = gift.gift_ctx_create(0)
+    spec = gift.make_spec(schedule=4244)
+    lat_s, eu_s, done_s = [], 0.0, []
+    t0 = time.perf_counter() + 0.2
+    for k, ((nl, g), _) in enumerate(reqs):
+        dt = t0 + arrivals[k] - time.perf_counter()
+        if dt > 0:
+            time.sleep(dt)
+        h = gift.gift_build_graph(ctx, nl.num_cells, nl.net_ptr, nl.pin_cell, nl.is_fixed, gift.WEIGHT["f32"])
+        out = np.empty_like(g)
+        gift.gift_filter(ctx, h, g, out, spec)
+        gift.gift_hpwl(ctx, h, out)
+        nnz = int(gift.gift_graph_info(h).nnz)
+        gift.gift_graph_free(h)
+        t_done = time.perf_counter()
+        if k >= warm:
+            lat_s.append(1e3 * (t_done - (t0 + arrivals[k])))
+            eu_s += 6.0 * nnz * g.shape[1]
+            done_s.append(t_done)
+    gift.gift_ctx_destroy(ctx)
+    serial = summary(lat_s, t0 + arrivals[warm], max(done_s), eu_s)
+    cells = [nl.num_cells for (nl, _), _ in reqs[warm:]]
+    return {"workload": f"Poisson {args.serve_rate:g} req/s, {args.serve_requests} requests after {warm} warm-up, "
+                        f"{len(pool)} distinct netlists of 10k-1.3M cells (mean {np.mean(cells):.0f}), 1 % fixed, "
+                        "S=4, FP32 and BF16 weights alternating; latency = result on the host - arrival",
+            "served": served, "serial_fp32": serial}
 
 
 # ----------------------------------------------------------------- NVTX ranges
@@ -331,8 +443,10 @@ def run_ours(args):
                      "alg_GBps": (v["alg_bytes"] / (v["total_ms"] * 1e-3) / 1e9) if v["total_ms"] > 0 else None}
                  for k, v in sorted(stats.items())}
 
-    # filter alone, per weight type (same graph, resident)
+    # filter alone, per weight type (same graph, resident); signal 0 of each
+    # output is kept for the precision report
     filt = {}
+    outs0, hps0 = {}, {}
     for wname in ("f32", "bf16", "f16"):
         h = gift.gift_build_graph(ctx, N, d_np, d_pc, d_fx, gift.WEIGHT[wname], stream=stream)
         for _ in range(3):
@@ -350,6 +464,8 @@ def run_ours(args):
         st = gift.gift_ctx_kernel_stats(ctx)
         gift.gift_ctx_set_profiling(ctx, False)
         fms = f0.elapsed_time(f1) / reps
+        outs0[wname] = d_out[:, 0, :].cpu().numpy().copy()
+        hps0[wname] = float(gift.gift_hpwl(ctx, h, d_out, stream=stream)[0])
         sw = st.get("filter.sweep", {"alg_bytes": 0, "total_ms": 1, "launches": 1})
         filt[wname] = {"ms": fms, "edge_updates_per_s": units / (fms * 1e-3),
                        "sweep_alg_GBps": sw["alg_bytes"] / (sw["total_ms"] * 1e-3) / 1e9,
@@ -390,13 +506,20 @@ def run_ours(args):
                "h2d_bytes_per_step": int(h2d), "d2h_bytes_per_step": int(d2h)}
 
     cpu = None
+    precision = None
     if rank == 0 and world == 1 and not args.no_cpu_baseline:
-        dt, u = oracle_sample(nl, g, 1)
+        dt, u, ref0, hp_ref = oracle_sample(nl, g, 1)
         cpu = {"value": u / dt, "unit": UNIT, "cores": 1, "kind": "oracle",
                "sample": f"{args.workload}: full netlist ({N} cells), build + filter + HPWL of 1 of {S} signals, "
                          f"FP64 single-threaded C, {dt:.1f} s"}
+        precision = precision_report(g[:, 0, :], outs0, hps0, ref0[:, 0, :], hp_ref[0])
+        precision["sample"] = (f"signal 0 of {S}, all {N} cells, against the FP64 oracle with exact weights; "
+                               "FP32 signal and accumulation")
     clocks = clk.summary()
     gift.gift_ctx_destroy(ctx)
+    serving = None
+    if rank == 0 and world == 1 and not args.no_serve:
+        serving = run_serving(args, gift)
     if rank == 0:
         line = {
             "metric": METRIC, "value": value, "unit": UNIT, "n_gpus": world, "steps": args.steps,
@@ -408,7 +531,8 @@ def run_ours(args):
                        "parallelism": f"replicas x{world}", "hpwl_out": float(hp[0]),
                        "sweep_schedule": schedule},
             "roofline": roofline, "cpu_baseline": cpu, "e2e": e2e, "gpu_launches": launches * world,
-            "clocks": clocks, "breakdown": breakdown, "filter_only": filt,
+            "clocks": clocks, "breakdown": breakdown, "filter_only": filt, "precision": precision,
+            "serving": serving,
         }
         print(json.dumps(line), flush=True)
     if world > 1:

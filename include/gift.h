@@ -241,6 +241,109 @@ GIFT_API gift_status gift_filter_noalloc(gift_ctx *ctx, const gift_graph *graph,
 GIFT_API gift_status gift_hpwl(gift_ctx *ctx, const gift_graph *graph, const float *xy, int32_t num_signals,
                       double *out, int32_t mem, void *stream);
 
+
+/* ---------------------------------------------------------------------------
+ * Batches.  gift_build_batch builds one graph from `num_graphs` netlists (all
+ * in the same memory kind): graph b's cells, nets and pins follow those of
+ * graphs 0..b-1, so the graph is block-diagonal and each row is exactly the
+ * row the netlist gives alone (same nonzeros, weights and degree).  One
+ * gift_filter on it filters every graph in the same launches; its signal is
+ * the graphs' signals stacked in order, [sum of cells][num_signals][2], and
+ * graph b's rows are bit-identical to filtering graph b alone with the same
+ * kernel shape.  cell_offsets (host, may be NULL) receives the first cell of
+ * every graph and the total, [num_graphs + 1].  A pin cell outside its own
+ * netlist is GIFT_ERR_INVALID.  Synchronises `stream`. */
+GIFT_API gift_status gift_build_batch(gift_ctx *ctx, const gift_netlist *netlists, int32_t num_graphs,
+                                      const gift_build_opts *opts, gift_graph **out, int64_t *cell_offsets,
+                                      void *stream);
+/* HPWL of every graph of a batch: out[b * num_signals + s] (host).  On a graph
+ * built by gift_build_graph it equals gift_hpwl (one graph).  Synchronises. */
+GIFT_API gift_status gift_hpwl_batch(gift_ctx *ctx, const gift_graph *graph, const float *xy, int32_t num_signals,
+                                     double *out, int32_t mem, void *stream);
+
+/* ---------------------------------------------------------------------------
+ * CUDA-graph replay.  gift_filter_capture runs the filter once (tuning the
+ * kernel shapes and building the formats they use), then records a second
+ * call -- every sweep, scale and packing kernel -- as a CUDA graph on scratch
+ * memory the handle owns.  gift_exec_launch replays it on `stream`: one graph
+ * launch filters the same device buffers g_in -> g_out again (write new
+ * signals into g_in between launches); the graph and both buffers must stay
+ * alive and unmoved while the handle is used.  Device memory only. */
+typedef struct gift_exec gift_exec;
+GIFT_API gift_status gift_filter_capture(gift_ctx *ctx, const gift_graph *graph, const gift_filter_spec *spec,
+                                         const float *g_in, int32_t num_signals, float *g_out, gift_exec **out);
+GIFT_API gift_status gift_exec_launch(gift_exec *exec, void *stream);
+GIFT_API void gift_exec_free(gift_exec *exec);
+
+/* ---------------------------------------------------------------------------
+ * Request loop (serving).  Netlists of different sizes arrive as requests;
+ * each is admitted when a slot and its estimated HBM footprint are free
+ * (strict FIFO, so a large request is never overtaken), then its whole path
+ * -- graph build, filter, HPWL of the result -- runs on the slot's own
+ * stream, so the work of admitted requests overlaps on the device, and a
+ * finished request frees its slot and memory for the next waiting one
+ * (continuous batching).  Results do not depend on what else runs: every
+ * kernel is deterministic per request.
+ *
+ * The server owns its own context on `device`.  All functions are
+ * thread-safe; tickets are unique per server. */
+typedef struct gift_server gift_server;
+
+typedef struct gift_serve_opts {
+    int32_t device;             /* CUDA device ordinal                               */
+    int32_t max_slots;          /* requests in flight at once, 1..64 (default 8)     */
+    int64_t hbm_budget_bytes;   /* admission budget; 0: half the free memory at create */
+    int32_t weight_dtype;       /* default edge-weight storage (GIFT_WEIGHT_*)       */
+    int32_t compute_hpwl;       /* 1: HPWL of each result (default 1)                */
+    gift_filter_spec spec;      /* filter of every request; spec.schedule 0 = a fixed
+                                   direct row-group shape (4244), not the autotuner  */
+    int32_t reserved[8];        /* zero                                              */
+} gift_serve_opts;
+
+typedef struct gift_req_stats {
+    double latency_ms;          /* submit -> result ready                            */
+    double queue_ms;            /* submit -> admitted                                */
+    double run_ms;              /* admitted -> result ready                          */
+    int64_t nnz;                /* stored nonzeros of the request's graph            */
+    int64_t footprint_bytes;    /* admission estimate                                */
+    int32_t weight_dtype;
+    int32_t num_signals;
+} gift_req_stats;
+
+typedef struct gift_serve_stats {
+    int64_t submitted, completed, failed, waiting, running;
+    double p50_ms, p99_ms, mean_ms, max_ms;   /* latency of completed requests      */
+    double uptime_s;                          /* since gift_serve_create            */
+    double requests_per_s;                    /* completed / (last done - first submit) */
+    double edge_updates_per_s;                /* 6 * nnz * S summed over completed, same span */
+    int64_t budget_bytes, peak_footprint_bytes;
+    int32_t max_slots, peak_running;
+} gift_serve_stats;
+
+GIFT_API void gift_serve_opts_default(gift_serve_opts *opts);
+/* Starts the server's worker threads.  opts may be NULL (defaults). */
+GIFT_API gift_status gift_serve_create(const gift_serve_opts *opts, gift_server **out);
+/* Copies the netlist (host memory, mem must be GIFT_MEM_HOST) and the signal
+ * g_in ([num_cells][num_signals][2] FP32, host) and queues the request.
+ * weight_dtype < 0 takes the server default.  Invalid netlists and requests
+ * whose footprint exceeds the budget are GIFT_ERR_INVALID (nothing queued). */
+GIFT_API gift_status gift_serve_submit(gift_server *srv, const gift_netlist *netlist, const float *g_in,
+                                       int32_t num_signals, int32_t weight_dtype, uint64_t *ticket);
+/* Result of a finished request: g_out [num_cells][num_signals][2] (host),
+ * hpwl [num_signals] (host, may be NULL), stats (may be NULL); the request is
+ * then forgotten.  GIFT_ERR_BUSY while it waits or runs; the request's own
+ * status if it failed; GIFT_ERR_INVALID for an unknown ticket. */
+GIFT_API gift_status gift_serve_poll(gift_server *srv, uint64_t ticket, float *g_out, double *hpwl,
+                                     gift_req_stats *stats);
+/* As gift_serve_poll, waiting up to timeout_ms (< 0: no limit) for the result;
+ * GIFT_ERR_BUSY if it is not ready by then. */
+GIFT_API gift_status gift_serve_wait(gift_server *srv, uint64_t ticket, int32_t timeout_ms, float *g_out,
+                                     double *hpwl, gift_req_stats *stats);
+GIFT_API gift_status gift_serve_stats_get(gift_server *srv, gift_serve_stats *out);
+/* Cancels waiting requests, lets running ones finish, stops the workers and
+ * frees everything. */
+GIFT_API void gift_serve_destroy(gift_server *srv);
+
 /* Message for the last non-OK status returned on this thread ("" if none). */
 GIFT_API const char *gift_last_error(void);
 

@@ -895,23 +895,40 @@ void filter_on_scratch(gift_ctx *ctx, const gift_graph *g, const gift_filter_spe
     p.counters = nullptr;
     p.ncounters = 0;
 
+    // shapes: the explicit schedule, else the autotuner's cached choice for
+    // this graph shape; a kind whose shape would need an allocation (a format
+    // not built yet, TMA tile counters) falls back to row groups
     ShapeSet ss;
-    for (auto &k : ss.kind) k = Shape{0, 4, 8};
-    {
+    bool have = false;
+    if (spec->schedule != 0) {
+        const bool split = spec->schedule >= 10000;
+        const Shape sh = shape_from_schedule(split ? spec->schedule - 10000 : spec->schedule);
+        GIFT_REQUIRE((split ? spec->schedule - 10000 : spec->schedule) >= 4 && valid_shape(sh),
+                     "gift_filter_noalloc: bad schedule");
+        for (auto &k : ss.kind) k = sh;
+        ss.split[0] = ss.split[1] = split;
+        have = true;
+    } else {
         std::lock_guard<std::mutex> lk(ctx->tune_mu);
         auto it = ctx->tuned.find(tune_key(g, p.vec, K, p));
         if (it != ctx->tuned.end()) {
-            bool ok[4];
-            for (int kd = 0; kd < 4; ++kd) {
-                const Shape t = it->second.kind[kd];
-                const int rps = t.family == 3 ? 32 / (sell_width(p, t.a) / p.vec) : 0;
-                ok[kd] = t.family == 0 || t.family == 1 || (t.family == 4 && (t.natural || g->order)) ||
-                         (t.family == 3 && g->sell.rps == rps);
-                if (ok[kd]) ss.kind[kd] = t;
-            }
-            for (int kd = 0; kd < 2; ++kd) ss.split[kd] = it->second.split[kd] && ok[kd + 2];
+            for (int kd = 0; kd < 4; ++kd) ss.kind[kd] = it->second.kind[kd];
+            for (int kd = 0; kd < 2; ++kd) ss.split[kd] = it->second.split[kd];
+            have = true;
         }
     }
+    if (!have) {
+        for (auto &k : ss.kind) k = Shape{0, 4, 8};
+    }
+    bool ok[4];
+    for (int kd = 0; kd < 4; ++kd) {
+        const Shape t = ss.kind[kd];
+        const int rps = t.family == 3 ? 32 / (sell_width(p, t.a) / p.vec) : 0;
+        ok[kd] = t.family == 0 || t.family == 1 || (t.family == 4 && (t.natural || g->order)) ||
+                 (t.family == 3 && g->sell.rps == rps);
+        if (!ok[kd]) ss.kind[kd] = Shape{0, 4, 8};
+    }
+    for (int kd = 0; kd < 2; ++kd) ss.split[kd] = ss.split[kd] && ok[kd + 2];
     run_sweeps(ctx, p, ss, st);
 }
 

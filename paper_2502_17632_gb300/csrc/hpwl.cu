@@ -32,9 +32,12 @@ __device__ __forceinline__ double extent(const Box &b) {
 // of its warp's 32 (nets of up to 32 pins) and reads each pin's locations for
 // all signals of the pass (one contiguous row piece); larger nets are reduced
 // by the whole warp.
+//
+// With chunk_lo, block b sums the nets [chunk_lo[b], chunk_lo[b + 1]) only
+// (chunks never cross a graph of a batch); else the grid strides over all nets.
 __global__ void __launch_bounds__(kHpwlThreads)
 k_hpwl(int32_t E, int32_t S, const int64_t *__restrict__ net_ptr, const int32_t *__restrict__ pin_cell,
-       const float2 *__restrict__ xy, double *__restrict__ partial) {
+       const float2 *__restrict__ xy, const int64_t *__restrict__ chunk_lo, double *__restrict__ partial) {
     __shared__ double red[kSC][kHpwlThreads / 32];
     const int s0 = blockIdx.y * kSC;
     const int ns = min(kSC, S - s0);
@@ -44,10 +47,13 @@ k_hpwl(int32_t E, int32_t S, const int64_t *__restrict__ net_ptr, const int32_t 
     double sum[kSC];
 #pragma unroll
     for (int q = 0; q < kSC; ++q) sum[q] = 0.0;
-    for (int64_t base = warp * 32; base < E; base += nwarps * 32) {
+    const int64_t hi = chunk_lo ? chunk_lo[blockIdx.x + 1] : E;
+    const int64_t start = chunk_lo ? chunk_lo[blockIdx.x] + (int64_t)wid * 32 : warp * 32;
+    const int64_t step = chunk_lo ? (int64_t)blockDim.x : nwarps * 32;
+    for (int64_t base = start; base < hi; base += step) {
         const int64_t e = base + lane;
         int64_t b = 0, m = 0;
-        if (e < E) {
+        if (e < hi) {
             b = net_ptr[e];
             m = net_ptr[e + 1] - b;
         }
@@ -107,7 +113,7 @@ k_hpwl(int32_t E, int32_t S, const int64_t *__restrict__ net_ptr, const int32_t 
 template <int GH>
 __global__ void __launch_bounds__(kHpwlThreads)
 k_hpwl_groups(int32_t E, int32_t S, const int64_t *__restrict__ net_ptr, const int32_t *__restrict__ pin_cell,
-              const float4 *__restrict__ xy4, double *__restrict__ partial) {
+              const float4 *__restrict__ xy4, const int64_t *__restrict__ chunk_lo, double *__restrict__ partial) {
     constexpr int NPW = 32 / GH;  // nets per warp step
     __shared__ double red[kHpwlThreads / 32][2 * GH];
     const int half = S / 2;  // float4 per cell row
@@ -119,10 +125,13 @@ k_hpwl_groups(int32_t E, int32_t S, const int64_t *__restrict__ net_ptr, const i
     const int64_t warp = (blockIdx.x * (int64_t)blockDim.x + threadIdx.x) >> 5;
     const int64_t nwarps = ((int64_t)gridDim.x * blockDim.x) >> 5;
     double sum0 = 0.0, sum1 = 0.0;
-    for (int64_t base = warp * NPW; base < E; base += nwarps * NPW) {
+    const int64_t hi = chunk_lo ? chunk_lo[blockIdx.x + 1] : E;
+    const int64_t start = chunk_lo ? chunk_lo[blockIdx.x] + (int64_t)wid * NPW : warp * NPW;
+    const int64_t step = chunk_lo ? (int64_t)(blockDim.x / 32) * NPW : nwarps * NPW;
+    for (int64_t base = start; base < hi; base += step) {
         const int64_t e = base + gi;
         int64_t b = 0, m = 0;
-        if (e < E) {
+        if (e < hi) {
             b = net_ptr[e];
             m = net_ptr[e + 1] - b;
         }
@@ -206,6 +215,29 @@ __global__ void k_hpwl_final(int32_t S, int32_t nblocks, const double *__restric
     if (lane == 0) out[s] = t;
 }
 
+void launch_groups(int gh, dim3 grid, cudaStream_t st, int32_t E, int32_t S, const int64_t *net_ptr,
+                   const int32_t *pin_cell, const float4 *xy4, const int64_t *chunk_lo, double *partial) {
+    if (gh == 8) k_hpwl_groups<8><<<grid, kHpwlThreads, 0, st>>>(E, S, net_ptr, pin_cell, xy4, chunk_lo, partial);
+    else if (gh == 4) k_hpwl_groups<4><<<grid, kHpwlThreads, 0, st>>>(E, S, net_ptr, pin_cell, xy4, chunk_lo, partial);
+    else if (gh == 2) k_hpwl_groups<2><<<grid, kHpwlThreads, 0, st>>>(E, S, net_ptr, pin_cell, xy4, chunk_lo, partial);
+    else k_hpwl_groups<1><<<grid, kHpwlThreads, 0, st>>>(E, S, net_ptr, pin_cell, xy4, chunk_lo, partial);
+}
+
+// Batches: warp per (graph b, signal s) sums the partials of b's chunks in
+// order (lane-strided, fixed xor tree).
+__global__ void k_hpwl_final_seg(int32_t S, int32_t B, int64_t nchunks, const int64_t *__restrict__ seg_chunk,
+                                 const double *__restrict__ partial, double *__restrict__ out) {
+    const int lane = threadIdx.x & 31;
+    const int64_t w = blockIdx.x * (int64_t)(blockDim.x / 32) + threadIdx.x / 32;
+    if (w >= (int64_t)B * S) return;  // whole warps
+    const int64_t b = w / S, s = w % S;
+    double t = 0.0;
+    for (int64_t c = seg_chunk[b] + lane; c < seg_chunk[b + 1]; c += 32) t += partial[s * nchunks + c];
+#pragma unroll
+    for (int o = 16; o > 0; o >>= 1) t += __shfl_xor_sync(0xffffffffu, t, o);
+    if (lane == 0) out[b * S + s] = t;
+}
+
 }  // namespace
 
 void hpwl_impl(gift_ctx *ctx, const gift_graph *g, const float *xy, int S, double *out, int mem, cudaStream_t st) {
@@ -234,19 +266,78 @@ void hpwl_impl(gift_ctx *ctx, const gift_graph *g, const float *xy, int S, doubl
             const int gh = S >= 16 ? 8 : (S >= 8 ? 4 : (S >= 4 ? 2 : 1));
             const dim3 grid(nblocks, (unsigned)ceil_div(S, 2 * gh));
             const float4 *xy4 = reinterpret_cast<const float4 *>(dxy);
-            if (gh == 8) k_hpwl_groups<8><<<grid, kHpwlThreads, 0, st>>>((int32_t)E, S, g->net_ptr, g->pin_cell, xy4, partial.as<double>());
-            else if (gh == 4) k_hpwl_groups<4><<<grid, kHpwlThreads, 0, st>>>((int32_t)E, S, g->net_ptr, g->pin_cell, xy4, partial.as<double>());
-            else if (gh == 2) k_hpwl_groups<2><<<grid, kHpwlThreads, 0, st>>>((int32_t)E, S, g->net_ptr, g->pin_cell, xy4, partial.as<double>());
-            else k_hpwl_groups<1><<<grid, kHpwlThreads, 0, st>>>((int32_t)E, S, g->net_ptr, g->pin_cell, xy4, partial.as<double>());
+            launch_groups(gh, grid, st, (int32_t)E, S, g->net_ptr, g->pin_cell, xy4, nullptr, partial.as<double>());
         } else {
             k_hpwl<<<dim3(nblocks, passes), kHpwlThreads, 0, st>>>((int32_t)E, S, g->net_ptr, g->pin_cell,
-                                                                    reinterpret_cast<const float2 *>(dxy),
+                                                                    reinterpret_cast<const float2 *>(dxy), nullptr,
                                                                     partial.as<double>());
         }
         k_hpwl_final<<<(unsigned)ceil_div(S, 4), 128, 0, st>>>(S, nblocks, partial.as<double>(), dout.as<double>());
         check_launch("k_hpwl");
     }
     GIFT_CUDA(cudaMemcpyAsync(out, dout.p, sizeof(double) * S, cudaMemcpyDeviceToHost, st));
+    GIFT_CUDA(cudaStreamSynchronize(st));
+    check_device_error(ctx);
+}
+
+}  // namespace gift
+
+namespace gift {
+
+// HPWL of every graph of a batch: out[b * S + s].  Nets are cut into chunks
+// that never cross a graph; each block sums one chunk per signal, then each
+// graph's chunks are summed in order (deterministic).
+void hpwl_batch_impl(gift_ctx *ctx, const gift_graph *g, const float *xy, int S, double *out, int mem,
+                     cudaStream_t st) {
+    GIFT_REQUIRE(S >= 1 && S <= 65535 * kSC, "gift_hpwl_batch: num_signals out of range");
+    GIFT_REQUIRE(xy && out, "gift_hpwl_batch: NULL pointer");
+    GIFT_REQUIRE(mem == GIFT_MEM_HOST || mem == GIFT_MEM_DEVICE, "gift_hpwl_batch: bad mem kind");
+    GIFT_REQUIRE(reinterpret_cast<uintptr_t>(xy) % 8 == 0, "gift_hpwl_batch: xy must be 8-byte aligned");
+    std::vector<int64_t> seg = g->seg_nets;
+    if (seg.empty()) seg = {0, (int64_t)g->num_nets};
+    const int B = (int)seg.size() - 1;
+    const int64_t E = g->num_nets;
+    const int64_t chunk = std::max<int64_t>(1024, ceil_div(std::max<int64_t>(E, 1), (int64_t)ctx->num_sms * 8));
+    std::vector<int64_t> lo, seg_chunk(B + 1, 0);
+    for (int b = 0; b < B; ++b) {
+        seg_chunk[b] = (int64_t)lo.size();
+        for (int64_t e = seg[b]; e < seg[b + 1]; e += chunk) lo.push_back(e);
+    }
+    seg_chunk[B] = (int64_t)lo.size();
+    const int64_t C = (int64_t)lo.size();
+    lo.push_back(E);
+    const size_t sig_bytes = sizeof(float) * (size_t)g->n * 2 * S;
+    DevBuf dxy_buf;
+    const float *dxy = xy;
+    if (mem == GIFT_MEM_HOST) {
+        dxy_buf = DevBuf(ctx, sig_bytes, st);
+        GIFT_CUDA(cudaMemcpyAsync(dxy_buf.p, xy, sig_bytes, cudaMemcpyHostToDevice, st));
+        dxy = dxy_buf.as<float>();
+    }
+    DevBuf dlo(ctx, sizeof(int64_t) * lo.size(), st), dseg(ctx, sizeof(int64_t) * seg_chunk.size(), st);
+    GIFT_CUDA(cudaMemcpyAsync(dlo.p, lo.data(), sizeof(int64_t) * lo.size(), cudaMemcpyHostToDevice, st));
+    GIFT_CUDA(cudaMemcpyAsync(dseg.p, seg_chunk.data(), sizeof(int64_t) * seg_chunk.size(), cudaMemcpyHostToDevice, st));
+    DevBuf partial(ctx, sizeof(double) * (size_t)std::max<int64_t>(C, 1) * S, st);
+    DevBuf dout(ctx, sizeof(double) * (size_t)B * S, st);
+    {
+        LaunchTimer lt(ctx, st, "hpwl", 8.0 * (E + 1) + 4.0 * g->num_pins + 8.0 * g->num_pins * S, 2);
+        if (C > 0) {
+            const bool grouped = S % 2 == 0 && reinterpret_cast<uintptr_t>(dxy) % 16 == 0;
+            if (grouped) {
+                const int gh = S >= 16 ? 8 : (S >= 8 ? 4 : (S >= 4 ? 2 : 1));
+                launch_groups(gh, dim3((unsigned)C, (unsigned)ceil_div(S, 2 * gh)), st, (int32_t)E, S, g->net_ptr,
+                              g->pin_cell, reinterpret_cast<const float4 *>(dxy), dlo.as<int64_t>(), partial.as<double>());
+            } else {
+                k_hpwl<<<dim3((unsigned)C, (unsigned)ceil_div(S, kSC)), kHpwlThreads, 0, st>>>(
+                    (int32_t)E, S, g->net_ptr, g->pin_cell, reinterpret_cast<const float2 *>(dxy), dlo.as<int64_t>(),
+                    partial.as<double>());
+            }
+        }
+        k_hpwl_final_seg<<<(unsigned)std::max<int64_t>(1, ceil_div((int64_t)B * S, 4)), 128, 0, st>>>(
+            S, B, C, dseg.as<int64_t>(), partial.as<double>(), dout.as<double>());
+        check_launch("k_hpwl_batch");
+    }
+    GIFT_CUDA(cudaMemcpyAsync(out, dout.p, sizeof(double) * B * S, cudaMemcpyDeviceToHost, st));
     GIFT_CUDA(cudaStreamSynchronize(st));
     check_device_error(ctx);
 }

@@ -215,6 +215,8 @@ struct gift_graph {
     // walks rows in this order (direct row groups, sliced ELL)
     int32_t *order = nullptr;
     int64_t order_slots = 0;
+    // batches (gift_build_batch): first cell / net of every graph, [B + 1]
+    std::vector<int64_t> seg_cells, seg_nets;
     // sliced-ELL execution format (built on first use by a sliced-ELL schedule)
     struct Sell {
         int rps = 0;              // rows per slice (0: not built)
@@ -247,4 +249,6 @@ void filter_on_scratch(gift_ctx *ctx, const gift_graph *g, const gift_filter_spe
                        float *g_out, void *scratch, size_t scratch_bytes, cudaStream_t st);
 // hpwl.cu
 void hpwl_impl(gift_ctx *ctx, const gift_graph *g, const float *xy, int S, double *out, int mem, cudaStream_t st);
+void hpwl_batch_impl(gift_ctx *ctx, const gift_graph *g, const float *xy, int S, double *out, int mem,
+                     cudaStream_t st);
 }  // namespace gift

@@ -62,6 +62,26 @@ class gift_kernel_stat(C.Structure):
                 ("total_ms", C.c_double), ("alg_bytes", C.c_double)]
 
 
+class gift_serve_opts(C.Structure):
+    _fields_ = [("device", C.c_int32), ("max_slots", C.c_int32), ("hbm_budget_bytes", C.c_int64),
+                ("weight_dtype", C.c_int32), ("compute_hpwl", C.c_int32), ("spec", gift_filter_spec),
+                ("reserved", C.c_int32 * 8)]
+
+
+class gift_req_stats(C.Structure):
+    _fields_ = [("latency_ms", C.c_double), ("queue_ms", C.c_double), ("run_ms", C.c_double),
+                ("nnz", C.c_int64), ("footprint_bytes", C.c_int64), ("weight_dtype", C.c_int32),
+                ("num_signals", C.c_int32)]
+
+
+class gift_serve_stats(C.Structure):
+    _fields_ = [("submitted", C.c_int64), ("completed", C.c_int64), ("failed", C.c_int64),
+                ("waiting", C.c_int64), ("running", C.c_int64), ("p50_ms", C.c_double), ("p99_ms", C.c_double),
+                ("mean_ms", C.c_double), ("max_ms", C.c_double), ("uptime_s", C.c_double),
+                ("requests_per_s", C.c_double), ("edge_updates_per_s", C.c_double), ("budget_bytes", C.c_int64),
+                ("peak_footprint_bytes", C.c_int64), ("max_slots", C.c_int32), ("peak_running", C.c_int32)]
+
+
 _lib = None
 
 
@@ -98,6 +118,18 @@ def load(build_if_missing: bool = True):
         "gift_filter": (I32, [P, P, P, P, I32, P, I32, P]),
         "gift_hpwl": (I32, [P, P, P, I32, P, I32, P]),
         "gift_filter_noalloc": (I32, [P, P, P, P, I32, P, P]),
+        "gift_build_batch": (I32, [P, P, I32, P, C.POINTER(P), P, P]),
+        "gift_hpwl_batch": (I32, [P, P, P, I32, P, I32, P]),
+        "gift_filter_capture": (I32, [P, P, P, P, I32, P, C.POINTER(P)]),
+        "gift_exec_launch": (I32, [P, P]),
+        "gift_exec_free": (None, [P]),
+        "gift_serve_opts_default": (None, [P]),
+        "gift_serve_create": (I32, [P, C.POINTER(P)]),
+        "gift_serve_submit": (I32, [P, P, P, I32, I32, C.POINTER(C.c_uint64)]),
+        "gift_serve_poll": (I32, [P, C.c_uint64, P, P, P]),
+        "gift_serve_wait": (I32, [P, C.c_uint64, I32, P, P, P]),
+        "gift_serve_stats_get": (I32, [P, P]),
+        "gift_serve_destroy": (None, [P]),
         "gift_last_error": (C.c_char_p, []),
     }
     for name, (res, args) in sig.items():
@@ -284,3 +316,116 @@ def gift_hpwl(ctx, graph, xy, num_signals: int | None = None, stream=None) -> np
     out = np.zeros(S, dtype=np.float64)
     _check(load().gift_hpwl(ctx, graph, p, S, out.ctypes.data, mem, _stream(stream)))
     return out
+
+
+# ------------------------------------------------------------------ serving
+def gift_serve_opts_default() -> gift_serve_opts:
+    o = gift_serve_opts()
+    load().gift_serve_opts_default(C.byref(o))
+    return o
+
+
+def gift_serve_create(opts: gift_serve_opts | None = None, **fields):
+    """Start a server; ``fields`` override members of the default options."""
+    o = opts if opts is not None else gift_serve_opts_default()
+    for k, v in fields.items():
+        setattr(o, k, v)
+    h = C.c_void_p()
+    _check(load().gift_serve_create(C.byref(o), C.byref(h)))
+    return h
+
+
+def gift_serve_submit(srv, num_cells: int, net_ptr, pin_cell, is_fixed, g_in, weight_dtype: int = -1) -> int:
+    """Queue a request (host numpy arrays); returns its ticket."""
+    g_in = np.ascontiguousarray(g_in, dtype=np.float32)
+    net_ptr = np.ascontiguousarray(net_ptr, dtype=np.int64)
+    pin_cell = np.ascontiguousarray(pin_cell, dtype=np.int32)
+    fx = None if is_fixed is None else np.ascontiguousarray(is_fixed, dtype=np.uint8)
+    nl = gift_netlist(num_cells, len(net_ptr) - 1, net_ptr.ctypes.data, pin_cell.ctypes.data,
+                      None if fx is None else fx.ctypes.data, GIFT_MEM_HOST)
+    t = C.c_uint64()
+    _check(load().gift_serve_submit(srv, C.byref(nl), g_in.ctypes.data, g_in.shape[1], weight_dtype, C.byref(t)))
+    return t.value
+
+
+def _result(fn, srv, ticket, num_cells, num_signals, *extra):
+    out = np.empty((num_cells, num_signals, 2), dtype=np.float32)
+    hp = np.empty(num_signals, dtype=np.float64)
+    st = gift_req_stats()
+    s = fn(srv, ticket, *extra, out.ctypes.data, hp.ctypes.data, C.byref(st))
+    if s == GIFT_ERR_BUSY:
+        return None
+    _check(s)
+    return out, hp, st
+
+
+def gift_serve_poll(srv, ticket: int, num_cells: int, num_signals: int):
+    """(output, hpwl, stats) of a finished request, None while it waits or runs."""
+    return _result(load().gift_serve_poll, srv, ticket, num_cells, num_signals)
+
+
+def gift_serve_wait(srv, ticket: int, num_cells: int, num_signals: int, timeout_ms: int = -1):
+    """As gift_serve_poll, waiting up to timeout_ms (-1: no limit)."""
+    return _result(load().gift_serve_wait, srv, ticket, num_cells, num_signals, timeout_ms)
+
+
+def gift_serve_stats_get(srv) -> gift_serve_stats:
+    s = gift_serve_stats()
+    _check(load().gift_serve_stats_get(srv, C.byref(s)))
+    return s
+
+
+def gift_serve_destroy(srv):
+    load().gift_serve_destroy(srv)
+
+
+# ------------------------------------------------------------------ batches
+def gift_build_batch(ctx, netlists, weight_dtype: int = GIFT_WEIGHT_F32, stream=None):
+    """netlists: sequence of (num_cells, net_ptr, pin_cell, is_fixed), all numpy
+    arrays or all torch CUDA tensors.  Returns (graph, cell_offsets [B+1])."""
+    B = len(netlists)
+    arr = (gift_netlist * B)()
+    keep = []
+    for b, (n, net_ptr, pin_cell, is_fixed) in enumerate(netlists):
+        p_np, mem = _ptr(net_ptr)
+        p_pc, _ = _ptr(pin_cell)
+        p_fx, _ = _ptr(is_fixed)
+        arr[b] = gift_netlist(n, (len(net_ptr) if isinstance(net_ptr, np.ndarray) else net_ptr.numel()) - 1,
+                              p_np, p_pc, p_fx, mem)
+        keep.append((net_ptr, pin_cell, is_fixed))
+    opts = gift_build_opts()
+    load().gift_build_opts_default(C.byref(opts))
+    opts.weight_dtype = weight_dtype
+    h = C.c_void_p()
+    offs = np.zeros(B + 1, dtype=np.int64)
+    _check(load().gift_build_batch(ctx, arr, B, C.byref(opts), C.byref(h), offs.ctypes.data, _stream(stream)))
+    return h, offs
+
+
+def gift_hpwl_batch(ctx, graph, xy, num_graphs: int, stream=None) -> np.ndarray:
+    """HPWL per graph and signal, [num_graphs][S]."""
+    p, mem = _ptr(xy)
+    S = xy.shape[1]
+    out = np.empty((num_graphs, S), dtype=np.float64)
+    _check(load().gift_hpwl_batch(ctx, graph, p, S, out.ctypes.data, mem, _stream(stream)))
+    return out
+
+
+def gift_filter_capture(ctx, graph, g_in, g_out, spec=None):
+    """Record the filter g_in -> g_out (torch CUDA tensors) as a CUDA graph."""
+    pi, mi = _ptr(g_in)
+    po, mo = _ptr(g_out)
+    if mi != GIFT_MEM_DEVICE or mo != GIFT_MEM_DEVICE:
+        raise ValueError("gift_filter_capture takes device tensors")
+    h = C.c_void_p()
+    _check(load().gift_filter_capture(ctx, graph, None if spec is None else C.byref(spec), pi, g_in.shape[1], po,
+                                      C.byref(h)))
+    return h
+
+
+def gift_exec_launch(exec_, stream=None):
+    _check(load().gift_exec_launch(exec_, _stream(stream)))
+
+
+def gift_exec_free(exec_):
+    load().gift_exec_free(exec_)

@@ -92,3 +92,47 @@ def test_no_gpu_fails_loudly():
     with pytest.raises(gift.GiftError) as ei:
         gift.gift_ctx_create(0)
     assert ei.value.status in (gift.GIFT_ERR_CUDA, gift.GIFT_ERR_INVALID)
+
+
+def test_no_gpu_server_fails_loudly():
+    """The request loop needs a device too: creating a server without one is
+    an error status, not a silent host fallback."""
+    torch = pytest.importorskip("torch")
+    if torch.cuda.is_available():
+        pytest.skip("a GPU is present")
+    with pytest.raises(gift.GiftError) as ei:
+        gift.gift_serve_create()
+    assert ei.value.status in (gift.GIFT_ERR_CUDA, gift.GIFT_ERR_INVALID)
+
+
+def test_serve_structs_match_header():
+    """ctypes layouts of the serving structs equal the C compiler's."""
+    import shutil
+    import subprocess
+    import tempfile
+    cc = shutil.which("gcc") or shutil.which("cc")
+    if cc is None:
+        pytest.skip("no C compiler")
+    src = r"""
+#include <stdio.h>
+#include <stddef.h>
+#include "gift.h"
+int main(void) {
+  printf("%zu %zu %zu %zu\n", sizeof(gift_serve_opts), offsetof(gift_serve_opts, spec),
+         offsetof(gift_serve_opts, reserved), sizeof(gift_req_stats));
+  printf("%zu %zu %zu\n", sizeof(gift_serve_stats), offsetof(gift_serve_stats, budget_bytes),
+         offsetof(gift_serve_stats, peak_running));
+  return 0;
+}
+"""
+    import ctypes as C
+    root = __import__("os").path.dirname(__import__("os").path.dirname(__import__("os").path.abspath(__file__)))
+    with tempfile.TemporaryDirectory() as d:
+        with open(f"{d}/t.c", "w") as f:
+            f.write(src)
+        subprocess.run([cc, "-I", f"{root}/include", f"{d}/t.c", "-o", f"{d}/t"], check=True)
+        out = subprocess.run([f"{d}/t"], check=True, capture_output=True, text=True).stdout.split()
+    want = [C.sizeof(gift.gift_serve_opts), gift.gift_serve_opts.spec.offset, gift.gift_serve_opts.reserved.offset,
+            C.sizeof(gift.gift_req_stats), C.sizeof(gift.gift_serve_stats),
+            gift.gift_serve_stats.budget_bytes.offset, gift.gift_serve_stats.peak_running.offset]
+    assert [int(x) for x in out] == want
