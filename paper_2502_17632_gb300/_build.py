@@ -65,7 +65,9 @@ def build(force: bool = False, verbose: bool = False, jobs: int | None = None) -
     with cf.ThreadPoolExecutor(jobs) as ex:
         list(ex.map(lambda so: _compile(so[0], so[1], verbose), zip(srcs, objs)))
     tmp = LIB + f".tmp{os.getpid()}"
-    r = subprocess.run([NVCC, ARCH, "-shared", "-o", tmp, *objs, "-lcudart_static", "-lrt", "-ldl", "-lpthread"],
+    # --no-undefined: a symbol no object defines fails the link, not the load
+    r = subprocess.run([NVCC, ARCH, "-shared", "-Xlinker", "--no-undefined", "-o", tmp, *objs, "-lcudart_static",
+                        "-lrt", "-ldl", "-lpthread"],
                        capture_output=True, text=True)
     if r.returncode != 0:
         raise RuntimeError(f"link failed:\n{r.stdout}\n{r.stderr}")

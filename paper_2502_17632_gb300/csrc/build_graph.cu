@@ -424,7 +424,10 @@ k_rows_warp(const int32_t *__restrict__ rows, const int32_t *__restrict__ nrows_
 
 // Block tiers: one block per long row.  GLOBAL_KEYS: keys live in a per-block
 // global scratch of `gcap` entries (rows beyond the shared-memory capacity);
-// else in dynamic shared memory of kBlockCap entries.
+// else in dynamic shared memory of `cap` keys followed by `cap` stored
+// weights, and the block takes the rows of the list with lo < raw length <=
+// cap (launched once per size class, so that short rows do not reserve the
+// shared memory of the longest and many blocks share an SM).
 template <typename WT, bool GLOBAL_KEYS>
 __global__ void __launch_bounds__(kBlockThreads)
 k_rows_block(const int64_t *__restrict__ inc_ptr, const int32_t *__restrict__ inc_net,
@@ -432,19 +435,20 @@ k_rows_block(const int64_t *__restrict__ inc_ptr, const int32_t *__restrict__ in
              const double *__restrict__ wnet, const int64_t *__restrict__ raw_ptr, int32_t *__restrict__ out_col,
              WT *__restrict__ out_val, int32_t *__restrict__ ucount, double *__restrict__ degree,
              const int32_t *__restrict__ big_rows, const int32_t *__restrict__ big_count,
-             uint64_t *__restrict__ gkeys, int64_t gcap) {
+             uint64_t *__restrict__ gkeys, int64_t gcap, int64_t lo, int64_t cap) {
     extern __shared__ uint64_t smem_keys[];
     __shared__ int s_cnt;
     __shared__ int s_warp[kBlockThreads / 32];
     __shared__ int s_uniq;
     uint64_t *keys = GLOBAL_KEYS ? gkeys + blockIdx.x * gcap : smem_keys;
+    WT *svals = GLOBAL_KEYS ? nullptr : reinterpret_cast<WT *>(smem_keys + cap);
     const int tid = threadIdx.x, lane = tid & 31, wid = tid >> 5;
     const int nrows = *big_count;
     for (int r = blockIdx.x; r < nrows; r += gridDim.x) {
         const int32_t row = big_rows[r];
         const int64_t rbase = raw_ptr[row];
         const int64_t rawlen = raw_ptr[row + 1] - rbase;
-        if (GLOBAL_KEYS != (rawlen > kBlockCap)) continue;
+        if (GLOBAL_KEYS ? rawlen <= kBlockCap : (rawlen <= lo || rawlen > cap)) continue;
         if (tid == 0) {
             s_cnt = 0;
             s_uniq = 0;
@@ -497,8 +501,10 @@ k_rows_block(const int64_t *__restrict__ inc_ptr, const int32_t *__restrict__ in
                 int u = before + __popc(hm & ((1u << lane) - 1));
                 double sum = 0.0;
                 for (int rr = t; rr < n && key_cell(keys[rr]) == c; ++rr) sum += wnet[key_net(keys[rr])];
+                const WT w = Store<WT>::put(sum);
                 out_col[rbase + u] = c;
-                out_val[rbase + u] = Store<WT>::put(sum);
+                out_val[rbase + u] = w;
+                if (!GLOBAL_KEYS) svals[u] = w;
             }
             __syncthreads();
             if (tid == 0) {
@@ -508,9 +514,12 @@ k_rows_block(const int64_t *__restrict__ inc_ptr, const int32_t *__restrict__ in
             }
             __syncthreads();
         }
-        if (tid == 0) {
+        if (tid == 0) {  // degree in column order, from shared memory where it fits
             double d = 0.0;
-            for (int u = 0; u < s_uniq; ++u) d += Store<WT>::get(out_val[rbase + u]);
+            if (GLOBAL_KEYS)
+                for (int u = 0; u < s_uniq; ++u) d += Store<WT>::get(out_val[rbase + u]);
+            else
+                for (int u = 0; u < s_uniq; ++u) d += Store<WT>::get(svals[u]);
             ucount[row] = s_uniq;
             degree[row] = d;
         }
@@ -732,21 +741,26 @@ void build_graph_impl(gift_ctx *ctx, const gift_netlist *nl, const gift_build_op
         }
         if (maxraw > kWarpCap) {
             LaunchTimer lt(ctx, st, "build.rows_block", 0.0);
-            const size_t smem = sizeof(uint64_t) * kBlockCap;
-            GIFT_CUDA(cudaFuncSetAttribute(k_rows_block<WT, false>, cudaFuncAttributeMaxDynamicSharedMemorySize,
-                                           (int)smem));
-            k_rows_block<WT, false><<<ctx->num_sms, kBlockThreads, smem, st>>>(
-                inc_ptr.as<int64_t>(), inc_net.as<int32_t>(), g->net_ptr, g->pin_cell, wnet.as<double>(),
-                raw_ptr.as<int64_t>(), out_col.as<int32_t>(), ov, ucount.as<int32_t>(), g->degree,
-                big_rows.as<int32_t>(), bc, nullptr, 0);
-            check_launch("k_rows_block");
+            const void *fn = (const void *)k_rows_block<WT, false>;
+            GIFT_CUDA(cudaFuncSetAttribute(fn, cudaFuncAttributeMaxDynamicSharedMemorySize,
+                                           (int)((sizeof(uint64_t) + sizeof(WT)) * kBlockCap)));
+            for (int64_t lo = kWarpCap, cap = 1024; lo < std::min<int64_t>(maxraw, kBlockCap); lo = cap, cap <<= 1) {
+                const size_t smem = (sizeof(uint64_t) + sizeof(WT)) * cap;
+                int per_sm = 0;
+                GIFT_CUDA(cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, fn, kBlockThreads, smem));
+                k_rows_block<WT, false><<<ctx->num_sms * std::max(per_sm, 1), kBlockThreads, smem, st>>>(
+                    inc_ptr.as<int64_t>(), inc_net.as<int32_t>(), g->net_ptr, g->pin_cell, wnet.as<double>(),
+                    raw_ptr.as<int64_t>(), out_col.as<int32_t>(), ov, ucount.as<int32_t>(), g->degree,
+                    big_rows.as<int32_t>(), bc, nullptr, 0, lo, cap);
+                check_launch("k_rows_block");
+            }
         }
         if (maxraw > kBlockCap) {
             LaunchTimer lt(ctx, st, "build.rows_global", 0.0);
             k_rows_block<WT, true><<<ctx->num_sms, kBlockThreads, 0, st>>>(
                 inc_ptr.as<int64_t>(), inc_net.as<int32_t>(), g->net_ptr, g->pin_cell, wnet.as<double>(),
                 raw_ptr.as<int64_t>(), out_col.as<int32_t>(), ov, ucount.as<int32_t>(), g->degree,
-                big_rows.as<int32_t>(), bc, gkeys.as<uint64_t>(), gcap);
+                big_rows.as<int32_t>(), bc, gkeys.as<uint64_t>(), gcap, kBlockCap, kBlockCap);
             check_launch("k_rows_block<global>");
         }
     };

@@ -80,15 +80,15 @@ static CUtensorMap row_map(const float *base, int64_t n, int K, int W) {
     return m;
 }
 
-const void *sweep_dr_kernel_f32(int vec, int cw, int u, int nc, bool first);
-const void *sweep_dr_kernel_bf16(int vec, int cw, int u, int nc, bool first);
-const void *sweep_dr_kernel_f16(int vec, int cw, int u, int nc, bool first);
+const void *sweep_dr_kernel_f32(int vec, int cw, int u, int nc, bool first, bool wr, bool comp);
+const void *sweep_dr_kernel_bf16(int vec, int cw, int u, int nc, bool first, bool wr, bool comp);
+const void *sweep_dr_kernel_f16(int vec, int cw, int u, int nc, bool first, bool wr, bool comp);
 
-const void *sweep_dr_kernel(int weight_dtype, int vec, int cw, int u, int nc, bool first) {
+const void *sweep_dr_kernel(int weight_dtype, int vec, int cw, int u, int nc, bool first, bool wr, bool comp) {
     switch (weight_dtype) {
-    case GIFT_WEIGHT_F32: return sweep_dr_kernel_f32(vec, cw, u, nc, first);
-    case GIFT_WEIGHT_BF16: return sweep_dr_kernel_bf16(vec, cw, u, nc, first);
-    case GIFT_WEIGHT_F16: return sweep_dr_kernel_f16(vec, cw, u, nc, first);
+    case GIFT_WEIGHT_F32: return sweep_dr_kernel_f32(vec, cw, u, nc, first, wr, comp);
+    case GIFT_WEIGHT_BF16: return sweep_dr_kernel_bf16(vec, cw, u, nc, first, wr, comp);
+    case GIFT_WEIGHT_F16: return sweep_dr_kernel_f16(vec, cw, u, nc, first, wr, comp);
     default: return nullptr;
     }
 }
@@ -216,6 +216,9 @@ struct Plan {
     // first-sweep gather scales of chains (2q, 2q+1), packed: gpre2[q] (null
     // when the chains carry no pre-scale, random-walk form)
     std::vector<const float2 *> gpre2;
+    // compensated sums: every launch uses warp-row direct kernels with
+    // Neumaier summation (the shapes' lane counts are kept)
+    bool comp = false;
 };
 
 // Dynamic shared memory the TMA kernel is opted into, once per kernel.
@@ -453,9 +456,10 @@ int run_sweeps(gift_ctx *ctx, const Plan &p, ShapeSet ss, cudaStream_t st, std::
                         fn = sweep_kernel(g->weight_dtype, p.vec, cw, gl, nc);
                         rows_per_block = (kSweepThreads / 32) * (32 / gl);
                     } else if (shape.family == 4) {
-                        const int u = (sv == 4 || nc == 2) ? std::min(shape.b, 4) : shape.b;
-                        fn = sweep_dr_kernel(g->weight_dtype, sv, cw, u, nc, k == 1);
-                        rows_per_block = (kSweepThreads / 32) * (32 / cw);
+                        const bool wr = shape.warp_rows || p.comp;
+                        const int u = wr ? 4 : (sv == 4 || nc == 2) ? std::min(shape.b, 4) : shape.b;
+                        fn = sweep_dr_kernel(g->weight_dtype, sv, cw, u, nc, k == 1, wr, p.comp);
+                        rows_per_block = (kSweepThreads / 32) * (wr ? 1 : 32 / cw);
                         if (!shape.natural) {
                             a.order = g->order;
                             a.n_slots = g->order_slots;
@@ -510,14 +514,16 @@ std::string tune_key(const gift_graph *g, int vec, int K, const Plan &p) {
 // 1000 + w (merge-path, slab of w columns), 2000 + w (TMA gathers),
 // 3000 + w (sliced ELL), 4000 + 100*n + 10*cw + u (direct row groups:
 // cw lanes per row, u gathers in flight per lane; n bit 0: float2 lanes,
-// n bit 1: rows in natural order rather than the graph's row order)
+// n bit 1: rows in natural order rather than the graph's row order, n bit 2:
+// a whole warp per row, its nonzeros split over 32 / cw lane groups)
 Shape shape_from_schedule(int schedule) {
     if (schedule >= 4000) {
         Shape s{4, (schedule / 10) % 10, schedule % 10};
         const int n = (schedule - 4000) / 100;
         s.narrow = n & 1;
         s.natural = (n >> 1) & 1;
-        if (n > 3) s.narrow = 2;  // invalid
+        s.warp_rows = (n >> 2) & 1;
+        if (n > 7) s.narrow = 2;  // invalid
         return s;
     }
     if (schedule >= 3000) return Shape{3, schedule - 3000, 1};
@@ -527,15 +533,24 @@ Shape shape_from_schedule(int schedule) {
     return Shape{0, 4, schedule};
 }
 
+// Default shape of compensated filters: a warp per row, float4 lanes, 4
+// lanes across the slab, 4 gathers in flight.
+Shape comp_shape() {
+    Shape s{4, 4, 4};
+    s.natural = 1;
+    s.warp_rows = 1;
+    return s;
+}
+
 int schedule_code(const Shape &sh) {
-    if (sh.family == 4) return 4000 + 100 * (sh.narrow + 2 * sh.natural) + 10 * sh.a + sh.b;
+    if (sh.family == 4) return 4000 + 100 * (sh.narrow + 2 * sh.natural + 4 * sh.warp_rows) + 10 * sh.a + sh.b;
     return sh.family >= 1 ? 1000 * sh.family + sh.a : 100 * sh.a + sh.b;
 }
 
 bool valid_shape(Shape s) {
     if (s.family == 4)
         return (s.narrow == 0 || s.narrow == 1) && (s.a == 1 || s.a == 2 || s.a == 4 || s.a == 8) &&
-               (s.b == 2 || s.b == 4 || s.b == 8);
+               (s.b == 2 || s.b == 4 || s.b == 8) && (!s.warp_rows || s.b == 4);
     if (s.family == 3) return s.a == 2 || s.a == 4 || s.a == 8 || s.a == 16;
     if (s.family == 2) return s.a == 8 || s.a == 16;
     if (s.family == 1) return s.a == 2 || s.a == 4 || s.a == 8 || s.a == 16;
@@ -581,6 +596,10 @@ ShapeSet autotune(gift_ctx *ctx, const Plan &p, cudaStream_t st) {
                         sh.narrow = narrow;
                         sh.natural = natural;
                         cands.push_back(sh);
+                        if (u == 4 && natural) {  // a warp per row, for long rows
+                            sh.warp_rows = 1;
+                            cands.push_back(sh);
+                        }
                     }
     }
     const bool prof = ctx->profiling;
@@ -677,6 +696,7 @@ void filter_impl(gift_ctx *ctx, const gift_graph *cg, const gift_filter_spec *sp
     GIFT_REQUIRE(spec->num_terms >= 1 && spec->num_terms <= GIFT_MAX_TERMS, "gift_filter: num_terms out of range");
     GIFT_REQUIRE(spec->norm == GIFT_NORM_SYM || spec->norm == GIFT_NORM_RW, "gift_filter: unknown norm");
     GIFT_REQUIRE(spec->reimpose_fixed == 0 || spec->reimpose_fixed == 1, "gift_filter: reimpose_fixed is 0 or 1");
+    GIFT_REQUIRE(spec->compensated == 0 || spec->compensated == 1, "gift_filter: compensated is 0 or 1");
     const bool split_sched = spec->schedule >= 10000;
     const int sched = split_sched ? spec->schedule - 10000 : spec->schedule;
     GIFT_REQUIRE(spec->schedule == 0 || (sched >= 4 && valid_shape(shape_from_schedule(sched))),
@@ -691,6 +711,7 @@ void filter_impl(gift_ctx *ctx, const gift_graph *cg, const gift_filter_spec *sp
     p.g = g;
     p.K = K;
     p.reimpose = spec->reimpose_fixed;
+    p.comp = spec->compensated == 1;
     // ---- chains by sigma
     for (int t = 0; t < spec->num_terms; ++t) {
         const gift_term &tm = spec->term[t];
@@ -759,7 +780,13 @@ void filter_impl(gift_ctx *ctx, const gift_graph *cg, const gift_filter_spec *sp
     DevBuf counters(ctx, sizeof(int32_t) * p.ncounters, st);
     p.counters = counters.as<int32_t>();
     ShapeSet ss;
-    if (spec->schedule == 0) {
+    if (p.comp) {
+        // compensated sums run on warp-row direct kernels: the explicit
+        // schedule's lane count if it is a direct shape, else 4 lanes per row
+        const Shape given = shape_from_schedule(sched);
+        for (auto &k : ss.kind) k = spec->schedule != 0 && given.family == 4 ? given : comp_shape();
+        ss.split[0] = ss.split[1] = split_sched;
+    } else if (spec->schedule == 0) {
         ss = autotune(ctx, p, st);
     } else {
         for (auto &k : ss.kind) k = shape_from_schedule(sched);
@@ -821,6 +848,7 @@ void filter_on_scratch(gift_ctx *ctx, const gift_graph *g, const gift_filter_spe
     GIFT_REQUIRE(spec->norm == GIFT_NORM_SYM || spec->norm == GIFT_NORM_RW, "gift_filter_noalloc: unknown norm");
     GIFT_REQUIRE(spec->reimpose_fixed == 0 || spec->reimpose_fixed == 1,
                  "gift_filter_noalloc: reimpose_fixed is 0 or 1");
+    GIFT_REQUIRE(spec->compensated == 0 || spec->compensated == 1, "gift_filter_noalloc: compensated is 0 or 1");
     const int64_t N = g->n;
     const int32_t K = 2 * S;
     const size_t sig_bytes = sizeof(float) * (size_t)N * K;
@@ -829,6 +857,7 @@ void filter_on_scratch(gift_ctx *ctx, const gift_graph *g, const gift_filter_spe
     p.g = g;
     p.K = K;
     p.reimpose = spec->reimpose_fixed;
+    p.comp = spec->compensated == 1;
     for (int t = 0; t < spec->num_terms; ++t) {
         const gift_term &tm = spec->term[t];
         GIFT_REQUIRE(std::isfinite(tm.sigma) && tm.sigma > 0.f, "gift_filter_noalloc: sigma must be finite and > 0");
@@ -929,6 +958,9 @@ void filter_on_scratch(gift_ctx *ctx, const gift_graph *g, const gift_filter_spe
         if (!ok[kd]) ss.kind[kd] = Shape{0, 4, 8};
     }
     for (int kd = 0; kd < 2; ++kd) ss.split[kd] = ss.split[kd] && ok[kd + 2];
+    if (p.comp)
+        for (auto &k : ss.kind)
+            if (k.family != 4) k = comp_shape();
     run_sweeps(ctx, p, ss, st);
 }
 

@@ -71,6 +71,7 @@ struct TunedShape {
     int family, a, b;
     int narrow = 0;   // direct family: float2 lanes instead of the signal's widest vector
     int natural = 0;  // direct family: rows in natural order instead of the graph's row order
+    int warp_rows = 0;  // direct family: a whole warp per row (nonzeros split over lane groups)
 };
 // tuned shape per launch kind (see filter.cu); split[kind] for the two-chain
 // kinds 0 and 1: run each chain as its own launch with the one-chain shape

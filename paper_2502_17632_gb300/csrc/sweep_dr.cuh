@@ -28,15 +28,32 @@ constexpr int dr_min_blocks(int vec, int u, int nc, int nx) {
          : (u * nx * vec + nc * vec + 2 * u + 24) <= 48 ? 5 : (u * nx * vec + nc * vec + 2 * u + 24) <= 64 ? 4 : 3;
 }
 
+// Neumaier's compensated addition: s + e tracks the running sum exactly up
+// to the rounding of e itself.
+__device__ __forceinline__ void comp_add(float &s, float &e, float x) {
+    const float t = s + x;
+    e += fabsf(s) >= fabsf(x) ? (s - t) + x : (x - t) + s;
+    s = t;
+}
+
 // FIRST: the first sweep, whose input is the unscaled g (row j of chain c is
 // multiplied by pre_c[j]); NX = 1 there, and NC otherwise.
-template <typename WT, int VEC, int CW, int U, int NC, bool FIRST>
-__global__ void __launch_bounds__(kSweepThreads, dr_min_blocks(VEC, U, NC, FIRST ? 1 : NC)) k_sweep_dr(const SweepArgs a) {
+// WR: a whole warp per row -- NS = 32 / CW groups of CW lanes, group ns taking
+// the row's nonzeros ns, ns + NS, ... (U at a time), then a fixed xor tree
+// over the groups; for rows of hundreds to thousands of nonzeros.
+// COMP (with WR): compensated FP32 sums (Neumaier) per lane and in the tree.
+template <typename WT, int VEC, int CW, int U, int NC, bool FIRST, bool WR = false, bool COMP = false>
+__global__ void __launch_bounds__(kSweepThreads, dr_min_blocks(VEC, U, (COMP ? 2 : 1) * NC, FIRST ? 1 : NC))
+k_sweep_dr(const SweepArgs a) {
     static_assert(CW >= 1 && CW <= 32 && 32 % CW == 0, "lanes per row divide the warp");
+    static_assert(WR || !COMP, "compensated sums come with warp rows");
     constexpr int NX = FIRST ? 1 : NC;
-    constexpr int RPW = 32 / CW;
+    constexpr int G = WR ? 32 : CW;  // lanes per row
+    constexpr int NS = G / CW;       // nonzero groups per row
+    constexpr int RPW = 32 / G;
     const int lane = threadIdx.x & 31;
-    const int q = lane % CW;
+    const int gi = lane / G, gl = lane % G;
+    const int q = gl % CW, ns = gl / CW;
     const int col = a.c0 + q * VEC;
     const int64_t warp = (blockIdx.x * (int64_t)blockDim.x + threadIdx.x) >> 5;
     const int64_t nwarps = ((int64_t)gridDim.x * blockDim.x) >> 5;
@@ -47,31 +64,32 @@ __global__ void __launch_bounds__(kSweepThreads, dr_min_blocks(VEC, U, NC, FIRST
     const float *gp1 = FIRST ? a.ch[NC - 1].gpre : nullptr;
 
     const int64_t nslots = a.order ? a.n_slots : a.n_rows;
-    for (int64_t slot = warp * RPW + lane / CW; slot - lane / CW < nslots; slot += nwarps * RPW) {
+    for (int64_t slot = warp * RPW + gi; slot - gi < nslots; slot += nwarps * RPW) {
         const int64_t row = slot < nslots ? (a.order ? (int64_t)__ldg(a.order + slot) : slot) : -1;
-        float acc[NC][VEC];
+        float acc[NC][VEC], err[NC][VEC];
 #pragma unroll
         for (int c = 0; c < NC; ++c)
 #pragma unroll
-            for (int v = 0; v < VEC; ++v) acc[c][v] = 0.f;
+            for (int v = 0; v < VEC; ++v) acc[c][v] = err[c][v] = 0.f;
         int64_t kb = 0, ke = 0;
         if (row >= 0) {
             kb = __ldg(a.row_ptr + row);
             ke = __ldg(a.row_ptr + row + 1);
         }
-        for (int64_t k0 = kb; k0 < ke; k0 += U) {
+        for (int64_t k0 = kb + ns; k0 < ke; k0 += (int64_t)NS * U) {
             int32_t j[U];
             float w[U];
 #pragma unroll
             for (int u = 0; u < U; ++u) {
-                const bool in = k0 + u < ke;
-                j[u] = in ? __ldg(a.col + k0 + u) : 0;
-                w[u] = in ? ld_weight_plain<WT>(a.val, k0 + u) : 0.f;
+                const int64_t k = k0 + (int64_t)u * NS;
+                const bool in = k < ke;
+                j[u] = in ? __ldg(a.col + k) : 0;
+                w[u] = in ? ld_weight_plain<WT>(a.val, k) : 0.f;
             }
             float xv[U][NX][VEC];
 #pragma unroll
             for (int u = 0; u < U; ++u) {
-                if (k0 + u < ke) {
+                if (k0 + (int64_t)u * NS < ke) {
                     const int64_t off = (int64_t)j[u] * a.K;
                     ldv<VEC>(x0 + off, xv[u][0]);
                     if (NX == 2) ldv<VEC>(x1 + off, xv[u][NX - 1]);
@@ -83,7 +101,7 @@ __global__ void __launch_bounds__(kSweepThreads, dr_min_blocks(VEC, U, NC, FIRST
                 if (!FIRST) {
 #pragma unroll
                     for (int c = 0; c < NC; ++c) wc[u][c] = w[u];
-                } else if (k0 + u < ke) {
+                } else if (k0 + (int64_t)u * NS < ke) {
                     if (gp2) {
                         const float2 s = __ldg(gp2 + j[u]);
                         wc[u][0] = w[u] * s.x;
@@ -96,40 +114,69 @@ __global__ void __launch_bounds__(kSweepThreads, dr_min_blocks(VEC, U, NC, FIRST
             }
 #pragma unroll
             for (int u = 0; u < U; ++u) {
-                if (k0 + u < ke) {
+                if (k0 + (int64_t)u * NS < ke) {
 #pragma unroll
                     for (int c = 0; c < NC; ++c)
 #pragma unroll
-                        for (int v = 0; v < VEC; ++v)
-                            acc[c][v] = fmaf(wc[u][c], xv[u][NX == 2 ? c : 0][v], acc[c][v]);
+                        for (int v = 0; v < VEC; ++v) {
+                            if (COMP) comp_add(acc[c][v], err[c][v], wc[u][c] * xv[u][NX == 2 ? c : 0][v]);
+                            else acc[c][v] = fmaf(wc[u][c], xv[u][NX == 2 ? c : 0][v], acc[c][v]);
+                        }
                 }
             }
         }
-        if (row >= 0) mp_finish<VEC, NC>(a, row, col, acc);
+        if (WR) {  // fixed tree over the nonzero groups of the row
+#pragma unroll
+            for (int o = CW; o < 32; o <<= 1)
+#pragma unroll
+                for (int c = 0; c < NC; ++c)
+#pragma unroll
+                    for (int v = 0; v < VEC; ++v) {
+                        const float b = __shfl_xor_sync(0xffffffffu, acc[c][v], o);
+                        if (COMP) {
+                            const float eb = __shfl_xor_sync(0xffffffffu, err[c][v], o);
+                            err[c][v] += eb;
+                            comp_add(acc[c][v], err[c][v], b);
+                        } else {
+                            acc[c][v] += b;
+                        }
+                    }
+        }
+        if (COMP) {
+#pragma unroll
+            for (int c = 0; c < NC; ++c)
+#pragma unroll
+                for (int v = 0; v < VEC; ++v) acc[c][v] += err[c][v];
+        }
+        if (row >= 0 && ns == 0) mp_finish<VEC, NC>(a, row, col, acc);
     }
 }
 
 // Kernel for a configuration; nullptr if not instantiated (u = 8 exists for
-// one chain with float2 lanes only).
-const void *sweep_dr_kernel(int weight_dtype, int vec, int cw, int u, int nc, bool first);
+// one chain with float2 lanes in row groups only; warp rows have u = 4).
+const void *sweep_dr_kernel(int weight_dtype, int vec, int cw, int u, int nc, bool first, bool wr, bool comp);
 
-#define GIFT_DR_CASE(WT, VEC, CW, U, NC, F) \
-    if (vec == VEC && cw == CW && u == U && nc == NC && first == F) return (const void *)k_sweep_dr<WT, VEC, CW, U, NC, F>;
+#define GIFT_DR_CASE(WT, VEC, CW, U, NC, F, WR, CP)                                           \
+    if (vec == VEC && cw == CW && u == U && nc == NC && first == F && wr == WR && comp == CP) \
+        return (const void *)k_sweep_dr<WT, VEC, CW, U, NC, F, WR, CP>;
 
-#define GIFT_DR_U(WT, VEC, CW, U)                                                                          \
-    GIFT_DR_CASE(WT, VEC, CW, U, 1, false) GIFT_DR_CASE(WT, VEC, CW, U, 1, true)                         \
-    GIFT_DR_CASE(WT, VEC, CW, U, 2, false) GIFT_DR_CASE(WT, VEC, CW, U, 2, true)
+#define GIFT_DR_U(WT, VEC, CW, U, WR, CP)                                                      \
+    GIFT_DR_CASE(WT, VEC, CW, U, 1, false, WR, CP) GIFT_DR_CASE(WT, VEC, CW, U, 1, true, WR, CP) \
+    GIFT_DR_CASE(WT, VEC, CW, U, 2, false, WR, CP) GIFT_DR_CASE(WT, VEC, CW, U, 2, true, WR, CP)
 
-#define GIFT_DR_CW4(WT, CW) GIFT_DR_U(WT, 4, CW, 2) GIFT_DR_U(WT, 4, CW, 4)
-#define GIFT_DR_CW2(WT, CW)                                   \
-    GIFT_DR_U(WT, 2, CW, 2) GIFT_DR_U(WT, 2, CW, 4)             \
-    GIFT_DR_CASE(WT, 2, CW, 8, 1, false) GIFT_DR_CASE(WT, 2, CW, 8, 1, true)
+#define GIFT_DR_CW4(WT, CW) GIFT_DR_U(WT, 4, CW, 2, false, false) GIFT_DR_U(WT, 4, CW, 4, false, false)
+#define GIFT_DR_CW2(WT, CW)                                                                    \
+    GIFT_DR_U(WT, 2, CW, 2, false, false) GIFT_DR_U(WT, 2, CW, 4, false, false)                \
+    GIFT_DR_CASE(WT, 2, CW, 8, 1, false, false, false) GIFT_DR_CASE(WT, 2, CW, 8, 1, true, false, false)
+#define GIFT_DR_WR(WT, VEC, CW) GIFT_DR_U(WT, VEC, CW, 4, true, false) GIFT_DR_U(WT, VEC, CW, 4, true, true)
 
-#define GIFT_DR_TABLE(WT)                                                                       \
-    const void *sweep_dr_kernel_##WT(int vec, int cw, int u, int nc, bool first) {              \
-        GIFT_DR_CW4(WT, 1) GIFT_DR_CW4(WT, 2) GIFT_DR_CW4(WT, 4) GIFT_DR_CW4(WT, 8)             \
-        GIFT_DR_CW2(WT, 1) GIFT_DR_CW2(WT, 2) GIFT_DR_CW2(WT, 4) GIFT_DR_CW2(WT, 8)             \
-        return nullptr;                                                                         \
+#define GIFT_DR_TABLE(WT)                                                                             \
+    const void *sweep_dr_kernel_##WT(int vec, int cw, int u, int nc, bool first, bool wr, bool comp) { \
+        GIFT_DR_CW4(WT, 1) GIFT_DR_CW4(WT, 2) GIFT_DR_CW4(WT, 4) GIFT_DR_CW4(WT, 8)                   \
+        GIFT_DR_CW2(WT, 1) GIFT_DR_CW2(WT, 2) GIFT_DR_CW2(WT, 4) GIFT_DR_CW2(WT, 8)                   \
+        GIFT_DR_WR(WT, 4, 1) GIFT_DR_WR(WT, 4, 2) GIFT_DR_WR(WT, 4, 4) GIFT_DR_WR(WT, 4, 8)           \
+        GIFT_DR_WR(WT, 2, 1) GIFT_DR_WR(WT, 2, 2) GIFT_DR_WR(WT, 2, 4) GIFT_DR_WR(WT, 2, 8)           \
+        return nullptr;                                                                               \
     }
 
 }  // namespace gift

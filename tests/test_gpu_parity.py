@@ -132,7 +132,7 @@ def run_filter(ctx, nl, g, wd="f32", spec=None, device=True):
 
 @pytest.mark.parametrize("name", sorted(NETLISTS))
 @pytest.mark.parametrize("S", [1, 2, 3, 8])
-@pytest.mark.parametrize("schedule", [0, 416, 1016, 1004, 3002, 4042, 14044, 4148, 4244])
+@pytest.mark.parametrize("schedule", [0, 416, 1016, 1004, 3002, 4042, 14044, 4148, 4244, 4644, 4724])
 def test_filter_parity(ctx, name, S, schedule):
     nl = NETLISTS[name]
     g = synth.make_signals(nl, S, 1234 + S)
@@ -148,7 +148,8 @@ def test_filter_parity(ctx, name, S, schedule):
 @pytest.mark.parametrize("schedule", [0, 4, 8, 16, 32, 108, 132, 204, 216, 408, 416, 432,
                                       1002, 1004, 1008, 1016, 2008, 2016, 3002, 3004, 3008, 3016,
                                       4012, 4014, 4022, 4024, 4042, 4044, 4082, 4084, 4112, 4118, 4142,
-                                      4148, 4182, 4188, 4244, 4342, 4388, 10408, 13008, 14042, 14148, 14244])
+                                      4148, 4182, 4188, 4244, 4342, 4388, 4414, 4424, 4444, 4484, 4514, 4524,
+                                      4644, 4744, 4784, 10408, 13008, 14042, 14148, 14244, 14644])
 def test_filter_shapes_and_schedules(ctx, S, schedule):
     nl = NETLISTS["repeat-cells"]
     g = synth.make_signals(nl, S, 99 + S)
@@ -202,6 +203,24 @@ def test_filter_general_specs(ctx, terms, norm, reimpose, schedule):
     got = run_filter(ctx, nl, g, spec=spec)
     _, _, ref = oracle.run(nl, g.reshape(nl.num_cells, -1), terms=terms, norm=norm, reimpose=reimpose)
     assert rel_err(got, ref.reshape(g.shape), g).max() <= RTOL
+
+
+@pytest.mark.parametrize("name", sorted(NETLISTS))
+@pytest.mark.parametrize("schedule", [0, 4644, 4424, 408])
+def test_compensated_sums(ctx, name, schedule):
+    """spec.compensated = 1: warp-row kernels with Neumaier sums (the schedule's
+    lane count kept for direct shapes, the default warp-row shape otherwise);
+    the same 1e-5 bar, including the star netlists' hub rows of 1,000 and
+    17,000 nonzeros."""
+    nl = NETLISTS[name]
+    g = synth.make_signals(nl, 4, 2024)
+    got = run_filter(ctx, nl, g, spec=gift.make_spec(schedule=schedule, compensated=True))
+    _, _, ref = oracle.run(nl, g.reshape(nl.num_cells, -1))
+    assert rel_err(got, ref.reshape(g.shape), g).max() <= RTOL
+    fx = nl.is_fixed.astype(bool)
+    np.testing.assert_array_equal(got[fx], g[fx])
+    sched = gift.gift_ctx_last_schedule(ctx)
+    assert all(c == 0 or 4400 <= c % 10000 < 4800 for c in sched)  # warp-row direct kernels
 
 
 @pytest.mark.parametrize("wd", ["bf16", "f16"])
@@ -279,6 +298,10 @@ def test_invalid_filter_args(ctx):
                 gift.gift_filter(ctx, h, g, out, gift.make_spec(terms=terms))
             assert e.value.status == gift.GIFT_ERR_INVALID
         spec = gift.make_spec()
+        spec.compensated = 2
+        with pytest.raises(gift.GiftError):
+            gift.gift_filter(ctx, h, g, out, spec)
+        spec = gift.make_spec()
         spec.num_terms = 9
         with pytest.raises(gift.GiftError):
             gift.gift_filter(ctx, h, g, out, spec)
@@ -287,7 +310,7 @@ def test_invalid_filter_args(ctx):
         with pytest.raises(gift.GiftError):
             gift.gift_filter(ctx, h, g, out, None, num_signals=0)
         for bad in (1, 2, 3, 404 + 1, 800 + 16, 216 + 100, 1161, 1003, 1032, 4043, 4062, 4442, 4041,
-                    10000, 10003, 19999, 20000):
+                    4842, 4642, 10000, 10003, 19999, 20000):
             with pytest.raises(gift.GiftError) as e:
                 gift.gift_filter(ctx, h, g, out, gift.make_spec(schedule=bad))
             assert e.value.status == gift.GIFT_ERR_INVALID
