@@ -59,6 +59,10 @@ def lib():
         P = C.c_void_p
         L.oracle_build.restype = P
         L.oracle_build.argtypes = [C.c_int32, C.c_int32, P, P]
+        L.oracle_build_cut.restype = P
+        L.oracle_build_cut.argtypes = [C.c_int32, C.c_int32, P, P, C.c_int64]
+        L.oracle_implicit_degrees.restype = C.c_int
+        L.oracle_implicit_degrees.argtypes = [C.c_int32, C.c_int32, P, P, C.c_int64, P]
         L.oracle_graph_nnz.restype = C.c_int64
         L.oracle_graph_nnz.argtypes = [P]
         L.oracle_graph_copy.argtypes = [P, P, P, P]
@@ -90,13 +94,17 @@ class Graph:
         return int(self.row_ptr[-1])
 
 
-def build_graph(num_cells: int, net_ptr: np.ndarray, pin_cell: np.ndarray) -> Graph:
-    """Clique expansion (weight 2/M, duplicates summed in net order) to CSR."""
+def build_graph(num_cells: int, net_ptr: np.ndarray, pin_cell: np.ndarray, cut: int = 0) -> Graph:
+    """Clique expansion (weight 2/M, duplicates summed in net order) to CSR.
+    cut > 0 leaves out the nets of at least `cut` pins (implicit cliques)."""
     net_ptr = np.ascontiguousarray(net_ptr, dtype=np.int64)
     pin_cell = np.ascontiguousarray(pin_cell, dtype=np.int32)
     if pin_cell.size == 0:
         pin_cell = np.zeros(1, dtype=np.int32)
-    h = lib().oracle_build(int(num_cells), int(net_ptr.size - 1), _p(net_ptr), _p(pin_cell))
+    if cut > 0:
+        h = lib().oracle_build_cut(int(num_cells), int(net_ptr.size - 1), _p(net_ptr), _p(pin_cell), int(cut))
+    else:
+        h = lib().oracle_build(int(num_cells), int(net_ptr.size - 1), _p(net_ptr), _p(pin_cell))
     if not h:
         raise ValueError("oracle_build rejected the netlist")
     try:
@@ -128,6 +136,21 @@ def degrees(g: Graph) -> np.ndarray:
     val = g.val if g.val.size else np.zeros(1)
     lib().oracle_degrees(g.n, _p(g.row_ptr), _p(val), _p(d))
     return d
+
+
+def implicit_degrees(d: np.ndarray, net_ptr: np.ndarray, pin_cell: np.ndarray, cut: int) -> np.ndarray:
+    """d plus the degrees of the cliques of the nets of at least `cut` pins
+    (nets in increasing order; k pins of a net of M on one cell add
+    (k * 2/M) * (M - k))."""
+    out = np.array(d, dtype=np.float64, copy=True)
+    net_ptr = np.ascontiguousarray(net_ptr, dtype=np.int64)
+    pin_cell = np.ascontiguousarray(pin_cell, dtype=np.int32)
+    if pin_cell.size == 0:
+        pin_cell = np.zeros(1, dtype=np.int32)
+    if lib().oracle_implicit_degrees(out.size, int(net_ptr.size - 1), _p(net_ptr), _p(pin_cell), int(cut),
+                                     _p(out)) != 0:
+        raise MemoryError("oracle_implicit_degrees")
+    return out
 
 
 def _csr_args(g: Graph):

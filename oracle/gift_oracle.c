@@ -53,15 +53,17 @@ static int cmp_pair(const void *pa, const void *pb) {
 }
 
 /* Step 1: clique expansion into CSR with summed duplicates.  Returns NULL on
- * bad input (cell id out of range, decreasing net_ptr) or allocation failure. */
-oracle_graph *oracle_build(int32_t num_cells, int32_t num_nets, const int64_t *net_ptr,
-                           const int32_t *pin_cell) {
+ * bad input (cell id out of range, decreasing net_ptr) or allocation failure.
+ * cut > 0 leaves out the nets of at least `cut` pins (their cliques are then
+ * applied implicitly; see oracle_implicit_degrees). */
+static oracle_graph *build_cut(int32_t num_cells, int32_t num_nets, const int64_t *net_ptr,
+                               const int32_t *pin_cell, int64_t cut) {
     if (num_cells <= 0 || num_nets < 0 || net_ptr[0] != 0) return NULL;
     int64_t npairs = 0;
     for (int32_t e = 0; e < num_nets; ++e) {
         int64_t m = net_ptr[e + 1] - net_ptr[e];
         if (m < 0) return NULL;
-        if (m >= 2) npairs += m * (m - 1);
+        if (m >= 2 && (cut <= 0 || m < cut)) npairs += m * (m - 1);
     }
     for (int64_t p = 0; p < net_ptr[num_nets]; ++p)
         if (pin_cell[p] < 0 || pin_cell[p] >= num_cells) return NULL;
@@ -72,6 +74,7 @@ oracle_graph *oracle_build(int32_t num_cells, int32_t num_nets, const int64_t *n
     for (int32_t e = 0; e < num_nets; ++e) {
         int64_t b = net_ptr[e], m = net_ptr[e + 1] - net_ptr[e];
         if (m < 2) continue;
+        if (cut > 0 && m >= cut) continue;
         double w = 2.0 / (double)m;
         for (int64_t p = 0; p < m; ++p)
             for (int64_t q = 0; q < m; ++q) {
@@ -107,6 +110,49 @@ oracle_graph *oracle_build(int32_t num_cells, int32_t num_nets, const int64_t *n
     g->nnz = nnz;
     free(pairs);
     return g;
+}
+
+oracle_graph *oracle_build(int32_t num_cells, int32_t num_nets, const int64_t *net_ptr,
+                           const int32_t *pin_cell) {
+    return build_cut(num_cells, num_nets, net_ptr, pin_cell, 0);
+}
+
+oracle_graph *oracle_build_cut(int32_t num_cells, int32_t num_nets, const int64_t *net_ptr,
+                               const int32_t *pin_cell, int64_t cut) {
+    return build_cut(num_cells, num_nets, net_ptr, pin_cell, cut);
+}
+
+static int cmp_i32(const void *pa, const void *pb) {
+    const int32_t a = *(const int32_t *)pa, b = *(const int32_t *)pb;
+    return a < b ? -1 : (a > b ? 1 : 0);
+}
+
+/* Degrees of the cliques left out by oracle_build_cut: a net of M >= cut pins
+ * with k of its pins on cell i adds, for each of those k pins, w = 2/M to the
+ * pairs with its M - k pins on other cells: d_i += (k * w) * (M - k).  Nets in
+ * increasing order, after the expanded part (d holds it on entry).  Returns 0,
+ * or -1 on allocation failure. */
+int oracle_implicit_degrees(int32_t num_cells, int32_t num_nets, const int64_t *net_ptr, const int32_t *pin_cell,
+                            int64_t cut, double *d) {
+    (void)num_cells;
+    if (cut <= 0) return 0;
+    for (int32_t e = 0; e < num_nets; ++e) {
+        int64_t b = net_ptr[e], m = net_ptr[e + 1] - net_ptr[e];
+        if (m < 2 || m < cut) continue;
+        int32_t *cells = (int32_t *)malloc((size_t)m * sizeof(int32_t));
+        if (!cells) return -1;
+        memcpy(cells, pin_cell + b, (size_t)m * sizeof(int32_t));
+        qsort(cells, (size_t)m, sizeof(int32_t), cmp_i32);
+        double w = 2.0 / (double)m;
+        for (int64_t r = 0; r < m;) {
+            int64_t k = 1;
+            while (r + k < m && cells[r + k] == cells[r]) ++k;
+            d[cells[r]] += ((double)k * w) * (double)(m - k);
+            r += k;
+        }
+        free(cells);
+    }
+    return 0;
 }
 
 int64_t oracle_graph_nnz(const oracle_graph *g) { return g->nnz; }

@@ -339,3 +339,45 @@ def test_hpwl_brute_force():
             p = xy[cs, s, :]
             tot += (p[:, 0].max() - p[:, 0].min()) + (p[:, 1].max() - p[:, 1].min())
         assert got[s] == pytest.approx(tot, rel=1e-14)
+
+
+# ------------------------------------------------------------ implicit cliques
+@pytest.mark.parametrize("cut", [2, 3, 4, 6, 50])
+@pytest.mark.parametrize("repeat", [False, True])
+def test_cut_graph_plus_implicit_degrees_equal_full_degrees(cut, repeat):
+    """Leaving the nets of >= cut pins out of the expansion and adding their
+    cliques' degrees gives the full clique's degrees (FP64 weights, sums in
+    another order)."""
+    nl = synth.random_small(41 + cut, 60, 90, 9, num_fixed=2, allow_repeat=repeat)
+    full = oracle.degrees(oracle.build_graph(nl.num_cells, nl.net_ptr, nl.pin_cell))
+    G = oracle.build_graph(nl.num_cells, nl.net_ptr, nl.pin_cell, cut=cut)
+    d = oracle.implicit_degrees(oracle.degrees(G), nl.net_ptr, nl.pin_cell, cut)
+    np.testing.assert_allclose(d, full, rtol=1e-14, atol=1e-15)
+    # the cut graph holds exactly the pairs of the smaller nets
+    M = np.diff(nl.net_ptr)
+    small = synth.Netlist(nl.num_cells, 0, np.array([0], dtype=np.int64), np.zeros(0, np.int32),
+                          nl.is_fixed, nl.fixed_xy)
+    keep = [e for e in range(nl.num_nets) if M[e] < cut]
+    ptr = np.concatenate([[0], np.cumsum([M[e] for e in keep])]).astype(np.int64)
+    pins = np.concatenate([nl.pin_cell[nl.net_ptr[e]:nl.net_ptr[e + 1]] for e in keep] or
+                          [np.zeros(0, np.int32)]).astype(np.int32)
+    Gs = oracle.build_graph(small.num_cells, ptr, pins)
+    np.testing.assert_array_equal(G.row_ptr, Gs.row_ptr)
+    np.testing.assert_array_equal(G.col, Gs.col)
+    np.testing.assert_array_equal(G.val, Gs.val)
+
+
+@pytest.mark.parametrize("M,k", [(2, 1), (5, 1), (5, 2), (7, 3), (9, 4)])
+def test_implicit_degree_of_one_net_by_pair_count(M, k):
+    """One net of M pins, k of them on cell 0 and the rest on distinct cells:
+    cell 0 has k (M - k) ordered pairs with other cells, each of weight 2/M."""
+    cells = [0] * k + list(range(1, M - k + 1))
+    nl_ptr = np.array([0, M], dtype=np.int64)
+    pins = np.array(cells, dtype=np.int32)
+    n = M - k + 1
+    d = oracle.implicit_degrees(np.zeros(n), nl_ptr, pins, cut=2)
+    assert d[0] == (k * (2.0 / M)) * (M - k)
+    for c in range(1, n):
+        assert d[c] == (1 * (2.0 / M)) * (M - 1)
+    G = oracle.build_graph(n, nl_ptr, pins, cut=2)
+    assert G.nnz == 0
