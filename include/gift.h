@@ -87,7 +87,11 @@ typedef struct gift_netlist {
 
 typedef struct gift_build_opts {
     int32_t weight_dtype;    /* GIFT_WEIGHT_*; default F32                    */
-    int32_t reserved[7];     /* must be zero                                  */
+    int32_t implicit_min_pins; /* 0: every net expanded (default).  >= 2: the
+                                cliques of nets with at least this many pins are
+                                not stored; the filter applies them through net
+                                sums (same operator, O(M) per net and sweep)  */
+    int32_t reserved[6];     /* must be zero                                  */
 } gift_build_opts;
 
 /* One filter term alpha * A~_sigma^power (Eq. 15-16). */
@@ -130,6 +134,10 @@ typedef struct gift_graph_desc {
     const int32_t *col;
     const void *val;        /* weight_dtype elements                           */
     const double *degree;   /* d_i = sum_j A_ij over the stored weights (FP64) */
+    int32_t implicit_min_pins; /* build option (0: none)                       */
+    int32_t reserved0;
+    int64_t implicit_nets;  /* nets applied implicitly                          */
+    int64_t implicit_pins;  /* their pins                                       */
 } gift_graph_desc;
 
 typedef struct gift_kernel_stat {
@@ -182,7 +190,14 @@ GIFT_API void gift_build_opts_default(gift_build_opts *opts);
  * to weight_dtype), CSR with sorted columns and no diagonal, degrees
  * d_i = sum_j A_ij in FP64 over the stored weights.  Copies the netlist into
  * the graph (for gift_hpwl).  Synchronises `stream` (sizes are data-dependent).
- * Errors: GIFT_ERR_INVALID (bad netlist), GIFT_ERR_OOM, GIFT_ERR_CUDA. */
+ *
+ * With opts->implicit_min_pins = T >= 2, nets of at least T pins are left out
+ * of the CSR: a sweep adds their cliques as sum over the cell's pins in the
+ * net of (2/M)(S_e - k x_i), S_e = the net's sum of the gathered signal, k =
+ * the net's pins on the cell -- the same operator as the expansion (without
+ * the rounding of those weights to weight_dtype).  The degree then is the
+ * CSR part plus, net by net in increasing order, (k * 2/M) * (M - k) in FP64.
+ * Errors: GIFT_ERR_INVALID (bad netlist or option), GIFT_ERR_OOM, GIFT_ERR_CUDA. */
 GIFT_API gift_status gift_build_graph(gift_ctx *ctx, const gift_netlist *netlist, const gift_build_opts *opts,
                              gift_graph **out, void *stream);
 GIFT_API gift_status gift_graph_info(const gift_graph *graph, gift_graph_desc *info);

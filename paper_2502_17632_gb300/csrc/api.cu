@@ -256,6 +256,9 @@ gift_status gift_graph_info(const gift_graph *g, gift_graph_desc *info) {
         info->col = g->col;
         info->val = g->val;
         info->degree = g->degree;
+        info->implicit_min_pins = g->imp_min;
+        info->implicit_nets = g->imp_nets;
+        info->implicit_pins = g->imp_pins;
     });
 }
 

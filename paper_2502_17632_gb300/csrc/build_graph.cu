@@ -53,9 +53,11 @@ __global__ void k_validate(int32_t E, int64_t P, int32_t N, const int64_t *__res
 }
 
 // Each lane owns one net of the warp's 32; nets above 32 pins are then done by
-// the whole warp, one after another.
+// the whole warp, one after another.  Nets of fewer than 2 pins, and with
+// imin > 0 the nets of at least imin pins (implicit cliques), are skipped.
 template <class F>
-__device__ __forceinline__ void for_each_pin_of_nets(int32_t E, const int64_t *__restrict__ net_ptr, F &&f) {
+__device__ __forceinline__ void for_each_pin_of_nets(int32_t E, const int64_t *__restrict__ net_ptr, int64_t imin,
+                                                     F &&f) {
     const int lane = threadIdx.x & 31;
     const int64_t warp = (blockIdx.x * (int64_t)blockDim.x + threadIdx.x) >> 5;
     const int64_t nwarps = ((int64_t)gridDim.x * blockDim.x) >> 5;
@@ -65,6 +67,7 @@ __device__ __forceinline__ void for_each_pin_of_nets(int32_t E, const int64_t *_
         if (e < E) {
             b = net_ptr[e];
             m = net_ptr[e + 1] - b;
+            if (imin > 0 && m >= imin) m = 0;
         }
         if (m >= 2 && m <= 32)
             for (int64_t t = 0; t < m; ++t) f((int32_t)e, b, m, t);
@@ -91,8 +94,8 @@ __global__ void k_net_weights(int32_t E, const int64_t *__restrict__ net_ptr, co
 }
 
 __global__ void k_count(int32_t E, const int64_t *__restrict__ net_ptr, const int32_t *__restrict__ pin_cell,
-                        int32_t *__restrict__ cnt, unsigned long long *__restrict__ rawlen) {
-    for_each_pin_of_nets(E, net_ptr, [&](int32_t, int64_t b, int64_t m, int64_t t) {
+                        int64_t imin, int32_t *__restrict__ cnt, unsigned long long *__restrict__ rawlen) {
+    for_each_pin_of_nets(E, net_ptr, imin, [&](int32_t, int64_t b, int64_t m, int64_t t) {
         int32_t c = pin_cell[b + t];
         atomicAdd(&cnt[c], 1);
         atomicAdd(&rawlen[c], (unsigned long long)(m - 1));
@@ -109,13 +112,84 @@ __global__ void k_max_rawlen(int32_t N, const int64_t *__restrict__ raw_ptr, uns
 
 // ------------------------------------------------------------------ scatter
 __global__ void k_scatter(int32_t E, const int64_t *__restrict__ net_ptr, const int32_t *__restrict__ pin_cell,
-                          const int64_t *__restrict__ inc_ptr, int32_t *__restrict__ fill,
+                          int64_t imin, const int64_t *__restrict__ inc_ptr, int32_t *__restrict__ fill,
                           int32_t *__restrict__ inc_net) {
-    for_each_pin_of_nets(E, net_ptr, [&](int32_t e, int64_t b, int64_t, int64_t t) {
+    for_each_pin_of_nets(E, net_ptr, imin, [&](int32_t e, int64_t b, int64_t, int64_t t) {
         int32_t c = pin_cell[b + t];
         int64_t pos = inc_ptr[c] + atomicAdd(&fill[c], 1);
         inc_net[pos] = e;
     });
+}
+
+// ------------------------------------------------------------------ implicit cliques
+// flag[e] = 1 for the nets applied implicitly (at least imin >= 2 pins).
+__global__ void k_imp_flag(int32_t E, const int64_t *__restrict__ net_ptr, int64_t imin, int32_t *__restrict__ flag) {
+    for (int64_t e = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; e < E; e += (int64_t)gridDim.x * blockDim.x)
+        flag[e] = net_ptr[e + 1] - net_ptr[e] >= imin ? 1 : 0;
+}
+
+// Net list in net order, with the FP32 weight 2/M the sweeps use.
+__global__ void k_imp_compact(int32_t E, const int64_t *__restrict__ net_ptr, const int32_t *__restrict__ flag,
+                              const int64_t *__restrict__ pos, const double *__restrict__ wtab,
+                              int32_t *__restrict__ imp_net, float *__restrict__ imp_w) {
+    for (int64_t e = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; e < E; e += (int64_t)gridDim.x * blockDim.x) {
+        if (!flag[e]) continue;
+        const int64_t m = net_ptr[e + 1] - net_ptr[e];
+        imp_net[pos[e]] = (int32_t)e;
+        imp_w[pos[e]] = __double2float_rn(m <= kWeightTable ? wtab[m] : 2.0 / (double)m);
+    }
+}
+
+// Warp per implicit net: count (fill == nullptr) or place each pin's
+// incidence (net index b) in its cell's list.
+__global__ void k_imp_pins(int64_t Eb, const int32_t *__restrict__ imp_net, const int64_t *__restrict__ net_ptr,
+                           const int32_t *__restrict__ pin_cell, int32_t *__restrict__ cnt,
+                           const int64_t *__restrict__ imp_ptr, int32_t *__restrict__ fill, int32_t *__restrict__ imp_idx) {
+    const int lane = threadIdx.x & 31;
+    const int64_t warp = (blockIdx.x * (int64_t)blockDim.x + threadIdx.x) >> 5;
+    const int64_t nwarps = ((int64_t)gridDim.x * blockDim.x) >> 5;
+    for (int64_t b = warp; b < Eb; b += nwarps) {
+        const int32_t e = imp_net[b];
+        const int64_t nb = net_ptr[e], m = net_ptr[e + 1] - nb;
+        for (int64_t t = lane; t < m; t += 32) {
+            const int32_t c = pin_cell[nb + t];
+            if (fill) imp_idx[imp_ptr[c] + atomicAdd(&fill[c], 1)] = (int32_t)b;
+            else atomicAdd(&cnt[c], 1);
+        }
+    }
+}
+
+// Thread per cell: sort its implicit incidences (increasing net), then add
+// the degrees of those cliques to the CSR part, nets in increasing order:
+// a run of k incidences of a net of M pins adds (k * 2/M) * (M - k) (FP64,
+// rounded products and sums, no contraction).
+__global__ void k_imp_rows(int32_t N, const int64_t *__restrict__ imp_ptr, int32_t *__restrict__ imp_idx,
+                           const int32_t *__restrict__ imp_net, const int64_t *__restrict__ net_ptr,
+                           const double *__restrict__ wtab, double *__restrict__ degree) {
+    for (int64_t i = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; i < N; i += (int64_t)gridDim.x * blockDim.x) {
+        const int64_t t0 = imp_ptr[i], t1 = imp_ptr[i + 1];
+        for (int64_t t = t0 + 1; t < t1; ++t) {  // insertion sort: lists are short
+            const int32_t v = imp_idx[t];
+            int64_t u = t - 1;
+            while (u >= t0 && imp_idx[u] > v) {
+                imp_idx[u + 1] = imp_idx[u];
+                --u;
+            }
+            imp_idx[u + 1] = v;
+        }
+        double d = degree[i];
+        for (int64_t t = t0; t < t1;) {
+            const int32_t b = imp_idx[t];
+            int64_t k = 1;
+            while (t + k < t1 && imp_idx[t + k] == b) ++k;
+            const int32_t e = imp_net[b];
+            const int64_t m = net_ptr[e + 1] - net_ptr[e];
+            const double w = m <= kWeightTable ? wtab[m] : 2.0 / (double)m;
+            d = __dadd_rn(d, __dmul_rn(__dmul_rn((double)k, w), (double)(m - k)));
+            t += k;
+        }
+        degree[i] = d;
+    }
 }
 
 // ------------------------------------------------------------------ storage rounding
@@ -570,7 +644,8 @@ void h2d_or_d2d(T *dst, const T *src, size_t count, int mem, cudaStream_t st) {
 }  // namespace
 
 void release_graph(gift_graph *g, cudaStream_t st) {
-    void *ptrs[] = {g->row_ptr, g->col, g->val, g->degree, g->net_ptr, g->pin_cell, g->is_fixed};
+    void *ptrs[] = {g->row_ptr, g->col,    g->val,     g->degree,  g->net_ptr, g->pin_cell,
+                    g->is_fixed, g->imp_net, g->imp_w, g->imp_ptr, g->imp_idx};
     for (void *p : ptrs) dev_free(p, st);
     for (auto &s : g->scales) {
         if (s.pre && s.pre != s.post) dev_free(s.pre, st);
@@ -594,6 +669,9 @@ void build_graph_impl(gift_ctx *ctx, const gift_netlist *nl, const gift_build_op
                      opts->weight_dtype == GIFT_WEIGHT_F16,
                  "gift_build_graph: unknown weight_dtype");
     for (int r : opts->reserved) GIFT_REQUIRE(r == 0, "gift_build_graph: reserved option fields must be zero");
+    GIFT_REQUIRE(opts->implicit_min_pins == 0 || opts->implicit_min_pins >= 2,
+                 "gift_build_graph: implicit_min_pins is 0 or at least 2");
+    const int64_t imin = opts->implicit_min_pins;
     GIFT_REQUIRE(nl->num_cells > 0, "gift_build_graph: num_cells must be > 0");
     GIFT_REQUIRE(nl->num_nets >= 0, "gift_build_graph: num_nets must be >= 0");
     GIFT_REQUIRE(nl->mem == GIFT_MEM_HOST || nl->mem == GIFT_MEM_DEVICE, "gift_build_graph: bad mem kind");
@@ -665,7 +743,7 @@ void build_graph_impl(gift_ctx *ctx, const gift_netlist *nl, const gift_build_op
     if (E > 0) {
         LaunchTimer lt(ctx, st, "build.count", 16.0 * (E + 1) + 4.0 * P + 12.0 * N, 2);
         k_net_weights<<<grid_for(ctx, E, 256), 256, 0, st>>>(E, g->net_ptr, ctx->wtab, wnet.as<double>());
-        k_count<<<grid_for(ctx, E, 256), 256, 0, st>>>(E, g->net_ptr, g->pin_cell, cnt.as<int32_t>(),
+        k_count<<<grid_for(ctx, E, 256), 256, 0, st>>>(E, g->net_ptr, g->pin_cell, imin, cnt.as<int32_t>(),
                                                          rawlen.as<unsigned long long>());
         check_launch("k_count");
     }
@@ -696,7 +774,7 @@ void build_graph_impl(gift_ctx *ctx, const gift_netlist *nl, const gift_build_op
     GIFT_CUDA(cudaMemsetAsync(fill.p, 0, sizeof(int32_t) * N, st));
     if (E > 0 && ninc > 0) {
         LaunchTimer lt(ctx, st, "build.scatter", 8.0 * (E + 1) + 4.0 * P + 8.0 * N + 4.0 * ninc + 4.0 * N);
-        k_scatter<<<grid_for(ctx, E, 256), 256, 0, st>>>(E, g->net_ptr, g->pin_cell, inc_ptr.as<int64_t>(),
+        k_scatter<<<grid_for(ctx, E, 256), 256, 0, st>>>(E, g->net_ptr, g->pin_cell, imin, inc_ptr.as<int64_t>(),
                                                            fill.as<int32_t>(), inc_net.as<int32_t>());
         check_launch("k_scatter");
     }
@@ -767,6 +845,46 @@ void build_graph_impl(gift_ctx *ctx, const gift_netlist *nl, const gift_build_op
     if (g->weight_dtype == GIFT_WEIGHT_F32) rows(float{});
     else if (g->weight_dtype == GIFT_WEIGHT_BF16) rows(__nv_bfloat16{});
     else rows(__half{});
+
+    // ---- implicit cliques: net list, per-cell incidences, their degrees
+    g->imp_min = (int32_t)imin;
+    if (imin > 0 && E > 0) {
+        LaunchTimer lt(ctx, st, "build.implicit", 16.0 * (E + 1) + 8.0 * N, 6);
+        DevBuf iflag(ctx, sizeof(int32_t) * E, st);
+        DevBuf ipos(ctx, sizeof(int64_t) * (E + 1), st);
+        k_imp_flag<<<grid_for(ctx, E, 256), 256, 0, st>>>(E, g->net_ptr, imin, iflag.as<int32_t>());
+        exclusive_scan(ctx, iflag.as<int32_t>(), ipos.as<int64_t>(), E, st);
+        int64_t eb = 0;
+        GIFT_CUDA(cudaMemcpyAsync(&eb, ipos.as<int64_t>() + E, sizeof(int64_t), cudaMemcpyDeviceToHost, st));
+        GIFT_CUDA(cudaStreamSynchronize(st));
+        g->imp_nets = eb;
+        g->imp_ptr = (int64_t *)dev_alloc(ctx, sizeof(int64_t) * (N + 1), st);
+        if (eb > 0) {
+            g->imp_net = (int32_t *)dev_alloc(ctx, sizeof(int32_t) * eb, st);
+            g->imp_w = (float *)dev_alloc(ctx, sizeof(float) * eb, st);
+            k_imp_compact<<<grid_for(ctx, E, 256), 256, 0, st>>>(E, g->net_ptr, iflag.as<int32_t>(), ipos.as<int64_t>(),
+                                                               ctx->wtab, g->imp_net, g->imp_w);
+            DevBuf icnt(ctx, sizeof(int32_t) * N, st);
+            GIFT_CUDA(cudaMemsetAsync(icnt.p, 0, sizeof(int32_t) * N, st));
+            const int wgrid = grid_for(ctx, eb * 32, 256);
+            k_imp_pins<<<wgrid, 256, 0, st>>>(eb, g->imp_net, g->net_ptr, g->pin_cell, icnt.as<int32_t>(), nullptr,
+                                              nullptr, nullptr);
+            exclusive_scan(ctx, icnt.as<int32_t>(), g->imp_ptr, N, st);
+            GIFT_CUDA(cudaMemcpyAsync(&g->imp_inc, g->imp_ptr + N, sizeof(int64_t), cudaMemcpyDeviceToHost, st));
+            GIFT_CUDA(cudaStreamSynchronize(st));
+            g->imp_pins = g->imp_inc;
+            g->imp_idx = (int32_t *)dev_alloc(ctx, sizeof(int32_t) * std::max<int64_t>(g->imp_inc, 1), st);
+            GIFT_CUDA(cudaMemsetAsync(icnt.p, 0, sizeof(int32_t) * N, st));
+            k_imp_pins<<<wgrid, 256, 0, st>>>(eb, g->imp_net, g->net_ptr, g->pin_cell, nullptr, g->imp_ptr,
+                                              icnt.as<int32_t>(), g->imp_idx);
+            k_imp_rows<<<grid_for(ctx, N, 256), 256, 0, st>>>(N, g->imp_ptr, g->imp_idx, g->imp_net, g->net_ptr,
+                                                              ctx->wtab, g->degree);
+            check_launch("k_imp");
+        } else {
+            GIFT_CUDA(cudaMemsetAsync(g->imp_ptr, 0, sizeof(int64_t) * (N + 1), st));
+        }
+        g->device_bytes += (int64_t)(8 * (N + 1) + 8 * eb + 4 * g->imp_inc);
+    }
 
     // ---- row_ptr, compaction, default scales
     g->row_ptr = (int64_t *)dev_alloc(ctx, sizeof(int64_t) * (N + 1), st);

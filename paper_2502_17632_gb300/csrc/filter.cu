@@ -135,6 +135,63 @@ __global__ void k_scale(int64_t n, const double *__restrict__ d, double sigma, i
     }
 }
 
+// Implicit cliques: warp per implicit net, S[b][c][:] = sum over the net's
+// pins of the gathered pre-scaled signal of chain c (the first sweep scales
+// g by the chain's pre vector).  Lane sums in FP64, pins lane-strided, a fixed
+// xor tree, one rounding to FP32.
+template <int NC, bool FIRST>
+__global__ void k_net_sums(int64_t Eb, const int32_t *__restrict__ imp_net, const int64_t *__restrict__ net_ptr,
+                           const int32_t *__restrict__ pin_cell, int K, const float *__restrict__ x0,
+                           const float *__restrict__ x1, const float *__restrict__ gp0, const float *__restrict__ gp1,
+                           float *__restrict__ S) {
+    const int lane = threadIdx.x & 31;
+    const int64_t warp = (blockIdx.x * (int64_t)blockDim.x + threadIdx.x) >> 5;
+    const int64_t nwarps = ((int64_t)gridDim.x * blockDim.x) >> 5;
+    for (int64_t b = warp; b < Eb; b += nwarps) {
+        const int32_t e = imp_net[b];
+        const int64_t nb = net_ptr[e], m = net_ptr[e + 1] - nb;
+        for (int c0 = 0; c0 < K; c0 += 2) {
+            double s[NC][2];
+#pragma unroll
+            for (int c = 0; c < NC; ++c) s[c][0] = s[c][1] = 0.0;
+            for (int64_t t = lane; t < m; t += 32) {
+                const int32_t cell = pin_cell[nb + t];
+                const float2 v0 = __ldg(reinterpret_cast<const float2 *>(x0 + (int64_t)cell * K + c0));
+                if (FIRST) {
+                    const float a0 = gp0 ? __ldg(gp0 + cell) : 1.f;
+                    s[0][0] += (double)(v0.x * a0);
+                    s[0][1] += (double)(v0.y * a0);
+                    if (NC == 2) {
+                        const float a1 = gp1 ? __ldg(gp1 + cell) : 1.f;
+                        s[NC - 1][0] += (double)(v0.x * a1);
+                        s[NC - 1][1] += (double)(v0.y * a1);
+                    }
+                } else {
+                    s[0][0] += (double)v0.x;
+                    s[0][1] += (double)v0.y;
+                    if (NC == 2) {
+                        const float2 v1 = __ldg(reinterpret_cast<const float2 *>(x1 + (int64_t)cell * K + c0));
+                        s[NC - 1][0] += (double)v1.x;
+                        s[NC - 1][1] += (double)v1.y;
+                    }
+                }
+            }
+#pragma unroll
+            for (int o = 16; o > 0; o >>= 1)
+#pragma unroll
+                for (int c = 0; c < NC; ++c) {
+                    s[c][0] += __shfl_xor_sync(0xffffffffu, s[c][0], o);
+                    s[c][1] += __shfl_xor_sync(0xffffffffu, s[c][1], o);
+                }
+            if (lane == 0)
+#pragma unroll
+                for (int c = 0; c < NC; ++c)
+                    *reinterpret_cast<float2 *>(S + (b * NC + c) * K + c0) =
+                        make_float2(__double2float_rn(s[c][0]), __double2float_rn(s[c][1]));
+        }
+    }
+}
+
 __global__ void k_pack2(int64_t n, const float *__restrict__ a, const float *__restrict__ b, float2 *__restrict__ out) {
     for (int64_t i = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; i < n; i += (int64_t)gridDim.x * blockDim.x)
         out[i] = make_float2(a[i], b[i]);
@@ -219,6 +276,8 @@ struct Plan {
     // compensated sums: every launch uses warp-row direct kernels with
     // Neumaier summation (the shapes' lane counts are kept)
     bool comp = false;
+    // implicit cliques: net sums of the current chain group, [nets][2][K]
+    float *S = nullptr;
 };
 
 // Dynamic shared memory the TMA kernel is opted into, once per kernel.
@@ -370,6 +429,31 @@ int run_sweeps(gift_ctx *ctx, const Plan &p, ShapeSet ss, cudaStream_t st, std::
             const Shape &shape = ss.kind[kind];
             const int sv = shape_vec(p, shape);
             const std::vector<std::pair<int, int>> &slabs = plans[kind];
+            ImplicitArgs imp{nullptr, nullptr, nullptr, nullptr, 0};
+            if (g->imp_nets > 0) {  // the group's net sums, all K columns
+                const int c0 = gr.c[0], c1 = gr.c[nc - 1];
+                const float *x0 = k == 1 ? p.din : p.X[c0][(k - 1) % 2];
+                const float *x1 = k == 1 ? p.din : p.X[c1][(k - 1) % 2];
+                const float *gp0 = k == 1 ? p.sc[c0].pre : nullptr, *gp1 = k == 1 ? p.sc[c1].pre : nullptr;
+                const int grid = (int)std::max<int64_t>(
+                    1, std::min<int64_t>(ceil_div(g->imp_nets * 32, 256), (int64_t)ctx->num_sms * 8));
+                LaunchTimer lt(ctx, st, "filter.netsums",
+                               4.0 * g->imp_pins * (1 + p.K * (k == 1 ? 1 : nc)) + 4.0 * g->imp_nets * nc * p.K);
+                if (k == 1 && nc == 2)
+                    k_net_sums<2, true><<<grid, 256, 0, st>>>(g->imp_nets, g->imp_net, g->net_ptr, g->pin_cell, p.K,
+                                                              x0, x1, gp0, gp1, p.S);
+                else if (k == 1)
+                    k_net_sums<1, true><<<grid, 256, 0, st>>>(g->imp_nets, g->imp_net, g->net_ptr, g->pin_cell, p.K,
+                                                              x0, x1, gp0, gp1, p.S);
+                else if (nc == 2)
+                    k_net_sums<2, false><<<grid, 256, 0, st>>>(g->imp_nets, g->imp_net, g->net_ptr, g->pin_cell, p.K,
+                                                               x0, x1, gp0, gp1, p.S);
+                else
+                    k_net_sums<1, false><<<grid, 256, 0, st>>>(g->imp_nets, g->imp_net, g->net_ptr, g->pin_cell, p.K,
+                                                               x0, x1, gp0, gp1, p.S);
+                check_launch("k_net_sums");
+                imp = ImplicitArgs{g->imp_ptr, g->imp_idx, g->imp_w, p.S, nc * p.K};
+            }
             for (size_t si = 0; si < slabs.size(); ++si) {
                 const int c0 = slabs[si].first, cw = slabs[si].second, W = cw * sv;
                 SweepArgs a;
@@ -381,6 +465,7 @@ int run_sweeps(gift_ctx *ctx, const Plan &p, ShapeSet ss, cudaStream_t st, std::
                 a.K = p.K;
                 a.c0 = c0;
                 a.gpre2 = gr.gpre2;
+                a.imp = imp;
                 const double bytes = first_launch ? sweep_bytes : 0.0;
                 first_launch = false;
                 for (int q = 0; q < nc; ++q) {
@@ -760,6 +845,11 @@ void filter_impl(gift_ctx *ctx, const gift_graph *cg, const gift_filter_spec *sp
         }
     DevBuf acc_buf(ctx, sig_bytes, st);
     p.acc = acc_buf.as<float>();
+    DevBuf s_buf;
+    if (g->imp_nets > 0) {
+        s_buf = DevBuf(ctx, sizeof(float) * (size_t)g->imp_nets * 2 * K, st);
+        p.S = s_buf.as<float>();
+    }
     p.sc.resize(p.chains.size());
     for (size_t c = 0; c < p.chains.size(); ++c) p.sc[c] = graph_scale(ctx, g, p.chains[c].sigma, spec->norm, st);
 
@@ -831,6 +921,7 @@ size_t filter_scratch_bytes(const gift_graph *g, const gift_filter_spec *spec, i
     for (int l : L) bytes += l >= 2 ? 2 * sig : 0;              // ping-pong inputs
     bytes += sigmas.size() * ((sizeof(float) * g->n + 255) / 256 * 256);  // scale vectors
     bytes += sigmas.size() / 2 * ((sizeof(float2) * g->n + 255) / 256 * 256);  // packed first-sweep scales
+    bytes += (sizeof(float) * (size_t)g->imp_nets * 2 * 2 * S + 255) / 256 * 256;  // implicit net sums
     return bytes + 256 * (8 + 2 * sigmas.size());               // alignment slack
 }
 
@@ -894,6 +985,7 @@ void filter_on_scratch(gift_ctx *ctx, const gift_graph *g, const gift_filter_spe
         return q;
     };
     p.acc = static_cast<float *>(take(sig_bytes));
+    if (g->imp_nets > 0) p.S = static_cast<float *>(take(sizeof(float) * (size_t)g->imp_nets * 2 * K));
     p.X.assign(p.chains.size(), {nullptr, nullptr});
     for (size_t c = 0; c < p.chains.size(); ++c)
         if (p.chains[c].L >= 2) {

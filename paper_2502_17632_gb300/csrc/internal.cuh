@@ -218,6 +218,13 @@ struct gift_graph {
     int64_t order_slots = 0;
     // batches (gift_build_batch): first cell / net of every graph, [B + 1]
     std::vector<int64_t> seg_cells, seg_nets;
+    // implicit cliques: nets of at least imp_min pins, kept out of the CSR
+    int32_t imp_min = 0;
+    int64_t imp_nets = 0, imp_pins = 0, imp_inc = 0;
+    int32_t *imp_net = nullptr;  // [imp_nets] net ids, increasing
+    float *imp_w = nullptr;      // [imp_nets] 2/M rounded to FP32
+    int64_t *imp_ptr = nullptr;  // [N + 1] each cell's implicit incidences
+    int32_t *imp_idx = nullptr;  // [imp_inc] index into imp_net, increasing per cell (repeated per pin)
     // sliced-ELL execution format (built on first use by a sliced-ELL schedule)
     struct Sell {
         int rps = 0;              // rows per slice (0: not built)

@@ -35,6 +35,17 @@ struct ChainIO {
     const float *pnext; // null: 1
 };
 
+// Implicit cliques in a sweep: row i adds, for each implicit net e it has k
+// pins in (a run of k equal entries of idx), k * w_e * (S_e - k * xh_i), with
+// S_e the net's sum of the gathered (pre-scaled) signal: [nets][NC][K].
+struct ImplicitArgs {
+    const int64_t *ptr;  // null: no implicit nets
+    const int32_t *idx;
+    const float *w;
+    const float *S;
+    int32_t ld;          // floats per net in S (NC * K)
+};
+
 struct SweepArgs {
     const int64_t *row_ptr;
     const int32_t *col;
@@ -50,6 +61,7 @@ struct SweepArgs {
     const float2 *gpre2;  // first sweep with two chains: (pre_0[j], pre_1[j]) packed, or null
     const int32_t *order; // direct row groups: row of each slot (-1: none), or null = identity
     int64_t n_slots;      // slots in order
+    ImplicitArgs imp;
 };
 
 // ---- loads with L2 eviction priority: the CSR is streamed once per pass
@@ -163,6 +175,25 @@ __device__ __forceinline__ void stv(float *p, const float (&r)[VEC]) {
     }
 }
 
+// Adds row i's implicit-clique terms for chain c to acc (VEC columns from col).
+template <int VEC>
+__device__ __forceinline__ void add_implicit(const SweepArgs &a, int c, int64_t row, int col, const float (&xh)[VEC],
+                                             float (&acc)[VEC]) {
+    const int64_t t1 = __ldg(a.imp.ptr + row + 1);
+    for (int64_t t = __ldg(a.imp.ptr + row); t < t1;) {
+        const int32_t e = __ldg(a.imp.idx + t);
+        int k = 1;
+        while (t + k < t1 && __ldg(a.imp.idx + t + k) == e) ++k;
+        const float kw = (float)k * __ldg(a.imp.w + e);
+        const float *S = a.imp.S + (int64_t)e * a.imp.ld + (int64_t)c * a.K + col;
+        float sv[VEC];
+        ldv<VEC>(S, sv);
+#pragma unroll
+        for (int v = 0; v < VEC; ++v) acc[v] = fmaf(kw, fmaf(-(float)k, xh[v], sv[v]), acc[v]);
+        t += k;
+    }
+}
+
 // Row group of G lanes: CW lanes across the slab's columns (VEC floats each),
 // NS = G / CW nonzeros at a time.  Each chunk of G nonzeros of the row is
 // loaded with one coalesced access (one (col, val) per lane), then broadcast
@@ -262,6 +293,7 @@ __global__ void __launch_bounds__(kSweepThreads) k_sweep(const SweepArgs a) {
                 for (int v = 0; v < VEC; ++v) xi[v] *= s;
             }
             const float p = __ldg(ch.post + row);
+            if (a.imp.ptr) add_implicit<VEC>(a, c, row, colo, xi, acc[c]);
             float y[VEC];
 #pragma unroll
             for (int v = 0; v < VEC; ++v) y[v] = p * fmaf(ch.sigma, xi[v], acc[c][v]);

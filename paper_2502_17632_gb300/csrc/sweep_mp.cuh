@@ -54,10 +54,16 @@ __device__ __forceinline__ void mp_finish(const SweepArgs &a, int64_t row, int c
         const ChainIO &ch = a.ch[c];
         const float s = ch.gpre ? __ldg(ch.gpre + row) : 1.f;
         const float p = __ldg(ch.post + row);
-        float xi[VEC], y[VEC];
+        float xi[VEC], y[VEC], ac[VEC];
         ldv<VEC>(ch.x + off, xi);
 #pragma unroll
-        for (int v = 0; v < VEC; ++v) y[v] = p * fmaf(ch.sigma, xi[v] * s, acc[c][v]);
+        for (int v = 0; v < VEC; ++v) {
+            xi[v] *= s;  // the row's pre-scaled input
+            ac[v] = acc[c][v];
+        }
+        if (a.imp.ptr) add_implicit<VEC>(a, c, row, col, xi, ac);
+#pragma unroll
+        for (int v = 0; v < VEC; ++v) y[v] = p * fmaf(ch.sigma, xi[v], ac[v]);
         if (ch.xnext) {
             const float qn = ch.pnext ? __ldg(ch.pnext + row) : 1.f;
             float t[VEC];

@@ -38,7 +38,7 @@ class gift_netlist(C.Structure):
 
 
 class gift_build_opts(C.Structure):
-    _fields_ = [("weight_dtype", C.c_int32), ("reserved", C.c_int32 * 7)]
+    _fields_ = [("weight_dtype", C.c_int32), ("implicit_min_pins", C.c_int32), ("reserved", C.c_int32 * 6)]
 
 
 class gift_term(C.Structure):
@@ -54,7 +54,8 @@ class gift_graph_desc(C.Structure):
     _fields_ = [("num_cells", C.c_int32), ("num_nets", C.c_int32), ("num_pins", C.c_int64), ("nnz", C.c_int64),
                 ("raw_pairs", C.c_int64), ("weight_dtype", C.c_int32), ("max_row_nnz", C.c_int32),
                 ("device_bytes", C.c_int64), ("row_ptr", C.c_void_p), ("col", C.c_void_p), ("val", C.c_void_p),
-                ("degree", C.c_void_p)]
+                ("degree", C.c_void_p), ("implicit_min_pins", C.c_int32), ("reserved0", C.c_int32),
+                ("implicit_nets", C.c_int64), ("implicit_pins", C.c_int64)]
 
 
 class gift_kernel_stat(C.Structure):
@@ -239,7 +240,7 @@ def gift_build_opts_default() -> gift_build_opts:
 
 # ------------------------------------------------------------------ graph
 def gift_build_graph(ctx, num_cells: int, net_ptr, pin_cell, is_fixed=None, weight_dtype: int = GIFT_WEIGHT_F32,
-                     stream=None):
+                     stream=None, implicit_min_pins: int = 0):
     """Build the clique graph; arrays are all host (numpy) or all device (torch)."""
     npp, mem = _ptr(net_ptr)
     pcp, mem2 = _ptr(pin_cell)
@@ -248,6 +249,7 @@ def gift_build_graph(ctx, num_cells: int, net_ptr, pin_cell, is_fixed=None, weig
     nl = gift_netlist(num_cells, nets, npp, pcp, fxp, mem)
     opts = gift_build_opts_default()
     opts.weight_dtype = weight_dtype
+    opts.implicit_min_pins = implicit_min_pins
     h = C.c_void_p()
     _check(load().gift_build_graph(ctx, C.byref(nl), C.byref(opts), C.byref(h), _stream(stream)))
     return h
@@ -380,7 +382,7 @@ def gift_serve_destroy(srv):
 
 
 # ------------------------------------------------------------------ batches
-def gift_build_batch(ctx, netlists, weight_dtype: int = GIFT_WEIGHT_F32, stream=None):
+def gift_build_batch(ctx, netlists, weight_dtype: int = GIFT_WEIGHT_F32, stream=None, implicit_min_pins: int = 0):
     """netlists: sequence of (num_cells, net_ptr, pin_cell, is_fixed), all numpy
     arrays or all torch CUDA tensors.  Returns (graph, cell_offsets [B+1])."""
     B = len(netlists)
@@ -396,6 +398,7 @@ def gift_build_batch(ctx, netlists, weight_dtype: int = GIFT_WEIGHT_F32, stream=
     opts = gift_build_opts()
     load().gift_build_opts_default(C.byref(opts))
     opts.weight_dtype = weight_dtype
+    opts.implicit_min_pins = implicit_min_pins
     h = C.c_void_p()
     offs = np.zeros(B + 1, dtype=np.int64)
     _check(load().gift_build_batch(ctx, arr, B, C.byref(opts), C.byref(h), offs.ctypes.data, _stream(stream)))
