@@ -135,59 +135,122 @@ __global__ void k_scale(int64_t n, const double *__restrict__ d, double sigma, i
     }
 }
 
-// Implicit cliques: warp per implicit net, S[b][c][:] = sum over the net's
-// pins of the gathered pre-scaled signal of chain c (the first sweep scales
-// g by the chain's pre vector).  Lane sums in FP64, pins lane-strided, a fixed
-// xor tree, one rounding to FP32.
+// Implicit cliques: S[b][c][:] = sum over net b's pins of the gathered
+// pre-scaled signal of chain c (the first sweep scales g by the chain's pre
+// vector), in compensated FP32 (Neumaier: the result is within about 2 ulp
+// of the exact sum, in a fixed order).  A group of LN lanes owns a net, lane
+// l of the group the float2 column pairs l, l + LN, ...; it sums the net's
+// pins in order, four loads in flight.  Nets above kBigNet pins are taken by
+// the whole warp: its 32 / LN groups take every (32 / LN)-th pin, then a
+// fixed xor tree.
+constexpr int kBigNet = 128;
+
+__device__ __forceinline__ void neu_add(float &s, float &e, float x) {
+    const float t = s + x;
+    e += fabsf(s) >= fabsf(x) ? (s - t) + x : (x - t) + s;
+    s = t;
+}
+
 template <int NC, bool FIRST>
-__global__ void k_net_sums(int64_t Eb, const int32_t *__restrict__ imp_net, const int64_t *__restrict__ net_ptr,
-                           const int32_t *__restrict__ pin_cell, int K, const float *__restrict__ x0,
-                           const float *__restrict__ x1, const float *__restrict__ gp0, const float *__restrict__ gp1,
-                           float *__restrict__ S) {
-    const int lane = threadIdx.x & 31;
-    const int64_t warp = (blockIdx.x * (int64_t)blockDim.x + threadIdx.x) >> 5;
-    const int64_t nwarps = ((int64_t)gridDim.x * blockDim.x) >> 5;
-    for (int64_t b = warp; b < Eb; b += nwarps) {
-        const int32_t e = imp_net[b];
-        const int64_t nb = net_ptr[e], m = net_ptr[e + 1] - nb;
-        for (int c0 = 0; c0 < K; c0 += 2) {
-            double s[NC][2];
+struct NetSum {
+    float s[NC][2], e[NC][2];
+    __device__ __forceinline__ NetSum() {
 #pragma unroll
-            for (int c = 0; c < NC; ++c) s[c][0] = s[c][1] = 0.0;
-            for (int64_t t = lane; t < m; t += 32) {
-                const int32_t cell = pin_cell[nb + t];
-                const float2 v0 = __ldg(reinterpret_cast<const float2 *>(x0 + (int64_t)cell * K + c0));
+        for (int c = 0; c < NC; ++c) s[c][0] = s[c][1] = e[c][0] = e[c][1] = 0.f;
+    }
+    // pins t0, t0 + step, ... below m of the net starting at nb, four at a time
+    __device__ __forceinline__ void run(const int32_t *__restrict__ pin_cell, int64_t nb, int64_t t0, int64_t m,
+                                        int64_t step, int K, int c0, const float *__restrict__ x0,
+                                        const float *__restrict__ x1, const float *__restrict__ gp0,
+                                        const float *__restrict__ gp1) {
+        for (int64_t t = t0; t < m; t += 4 * step) {
+            int32_t cell[4];
+#pragma unroll
+            for (int u = 0; u < 4; ++u) cell[u] = t + u * step < m ? __ldg(pin_cell + nb + t + u * step) : -1;
+            float2 v[4][NC];
+            float sc[4][NC];
+#pragma unroll
+            for (int u = 0; u < 4; ++u) {
+                if (cell[u] < 0) continue;
+                v[u][0] = __ldg(reinterpret_cast<const float2 *>(x0 + (int64_t)cell[u] * K + c0));
                 if (FIRST) {
-                    const float a0 = gp0 ? __ldg(gp0 + cell) : 1.f;
-                    s[0][0] += (double)(v0.x * a0);
-                    s[0][1] += (double)(v0.y * a0);
-                    if (NC == 2) {
-                        const float a1 = gp1 ? __ldg(gp1 + cell) : 1.f;
-                        s[NC - 1][0] += (double)(v0.x * a1);
-                        s[NC - 1][1] += (double)(v0.y * a1);
-                    }
-                } else {
-                    s[0][0] += (double)v0.x;
-                    s[0][1] += (double)v0.y;
-                    if (NC == 2) {
-                        const float2 v1 = __ldg(reinterpret_cast<const float2 *>(x1 + (int64_t)cell * K + c0));
-                        s[NC - 1][0] += (double)v1.x;
-                        s[NC - 1][1] += (double)v1.y;
-                    }
+                    sc[u][0] = gp0 ? __ldg(gp0 + cell[u]) : 1.f;
+                    if (NC == 2) sc[u][NC - 1] = gp1 ? __ldg(gp1 + cell[u]) : 1.f;
+                } else if (NC == 2) {
+                    v[u][NC - 1] = __ldg(reinterpret_cast<const float2 *>(x1 + (int64_t)cell[u] * K + c0));
                 }
             }
 #pragma unroll
-            for (int o = 16; o > 0; o >>= 1)
+            for (int u = 0; u < 4; ++u) {
+                if (cell[u] < 0) continue;
 #pragma unroll
                 for (int c = 0; c < NC; ++c) {
-                    s[c][0] += __shfl_xor_sync(0xffffffffu, s[c][0], o);
-                    s[c][1] += __shfl_xor_sync(0xffffffffu, s[c][1], o);
+                    const float2 x = v[u][FIRST ? 0 : c];
+                    const float a = FIRST ? sc[u][c] : 1.f;
+                    neu_add(s[c][0], e[c][0], FIRST ? x.x * a : x.x);
+                    neu_add(s[c][1], e[c][1], FIRST ? x.y * a : x.y);
                 }
-            if (lane == 0)
+            }
+        }
+    }
+    // fixed xor tree over the lanes o, 2o, ... < 32
+    __device__ __forceinline__ void tree(int o0) {
+        for (int o = o0; o < 32; o <<= 1)
 #pragma unroll
-                for (int c = 0; c < NC; ++c)
-                    *reinterpret_cast<float2 *>(S + (b * NC + c) * K + c0) =
-                        make_float2(__double2float_rn(s[c][0]), __double2float_rn(s[c][1]));
+            for (int c = 0; c < NC; ++c)
+#pragma unroll
+                for (int h = 0; h < 2; ++h) {
+                    const float bs = __shfl_xor_sync(0xffffffffu, s[c][h], o);
+                    const float be = __shfl_xor_sync(0xffffffffu, e[c][h], o);
+                    e[c][h] += be;
+                    neu_add(s[c][h], e[c][h], bs);
+                }
+    }
+    __device__ __forceinline__ void store(float *__restrict__ S, int64_t b, int K, int c0) const {
+#pragma unroll
+        for (int c = 0; c < NC; ++c)
+            *reinterpret_cast<float2 *>(S + (b * NC + c) * K + c0) = make_float2(s[c][0] + e[c][0], s[c][1] + e[c][1]);
+    }
+};
+
+template <int NC, bool FIRST>
+__global__ void k_net_sums(int64_t Eb, const int32_t *__restrict__ imp_net, const int64_t *__restrict__ net_ptr,
+                           const int32_t *__restrict__ pin_cell, int K, int LN, const float *__restrict__ x0,
+                           const float *__restrict__ x1, const float *__restrict__ gp0, const float *__restrict__ gp1,
+                           float *__restrict__ S) {
+    const int lane = threadIdx.x & 31;
+    const int NPW = 32 / LN;  // nets per warp step
+    const int grp = lane / LN, gl = lane % LN;
+    const int64_t warp = (blockIdx.x * (int64_t)blockDim.x + threadIdx.x) >> 5;
+    const int64_t nwarps = ((int64_t)gridDim.x * blockDim.x) >> 5;
+    for (int64_t base = warp * NPW; base < Eb; base += nwarps * NPW) {  // warp-uniform
+        const int64_t b = base + grp;
+        int64_t nb = 0, m = 0;
+        if (b < Eb) {
+            const int32_t e = imp_net[b];
+            nb = net_ptr[e];
+            m = net_ptr[e + 1] - nb;
+        }
+        if (m <= kBigNet && b < Eb) {
+            for (int c0 = 2 * gl; c0 < K; c0 += 2 * LN) {
+                NetSum<NC, FIRST> ns;
+                ns.run(pin_cell, nb, 0, m, 1, K, c0, x0, x1, gp0, gp1);
+                ns.store(S, b, K, c0);
+            }
+        }
+        unsigned big = __ballot_sync(0xffffffffu, m > kBigNet && gl == 0);
+        while (big) {
+            const int src = __ffs(big) - 1;
+            big &= big - 1;
+            const int64_t bb = base + src / LN;
+            const int64_t nbb = __shfl_sync(0xffffffffu, nb, src), mb = __shfl_sync(0xffffffffu, m, src);
+            for (int cb = 0; cb < K; cb += 2 * LN) {  // all lanes iterate together
+                const int c0 = cb + 2 * gl;
+                NetSum<NC, FIRST> ns;
+                if (c0 < K) ns.run(pin_cell, nbb, grp, mb, NPW, K, c0, x0, x1, gp0, gp1);
+                ns.tree(LN);
+                if (grp == 0 && c0 < K) ns.store(S, bb, K, c0);
+            }
         }
     }
 }
@@ -435,21 +498,23 @@ int run_sweeps(gift_ctx *ctx, const Plan &p, ShapeSet ss, cudaStream_t st, std::
                 const float *x0 = k == 1 ? p.din : p.X[c0][(k - 1) % 2];
                 const float *x1 = k == 1 ? p.din : p.X[c1][(k - 1) % 2];
                 const float *gp0 = k == 1 ? p.sc[c0].pre : nullptr, *gp1 = k == 1 ? p.sc[c1].pre : nullptr;
+                int LN = 1;
+                while (LN < 32 && 2 * LN < p.K) LN <<= 1;
                 const int grid = (int)std::max<int64_t>(
-                    1, std::min<int64_t>(ceil_div(g->imp_nets * 32, 256), (int64_t)ctx->num_sms * 8));
+                    1, std::min<int64_t>(ceil_div(g->imp_nets * LN, 256), (int64_t)ctx->num_sms * 16));
                 LaunchTimer lt(ctx, st, "filter.netsums",
                                4.0 * g->imp_pins * (1 + p.K * (k == 1 ? 1 : nc)) + 4.0 * g->imp_nets * nc * p.K);
                 if (k == 1 && nc == 2)
-                    k_net_sums<2, true><<<grid, 256, 0, st>>>(g->imp_nets, g->imp_net, g->net_ptr, g->pin_cell, p.K,
+                    k_net_sums<2, true><<<grid, 256, 0, st>>>(g->imp_nets, g->imp_net, g->net_ptr, g->pin_cell, p.K, LN,
                                                               x0, x1, gp0, gp1, p.S);
                 else if (k == 1)
-                    k_net_sums<1, true><<<grid, 256, 0, st>>>(g->imp_nets, g->imp_net, g->net_ptr, g->pin_cell, p.K,
+                    k_net_sums<1, true><<<grid, 256, 0, st>>>(g->imp_nets, g->imp_net, g->net_ptr, g->pin_cell, p.K, LN,
                                                               x0, x1, gp0, gp1, p.S);
                 else if (nc == 2)
-                    k_net_sums<2, false><<<grid, 256, 0, st>>>(g->imp_nets, g->imp_net, g->net_ptr, g->pin_cell, p.K,
+                    k_net_sums<2, false><<<grid, 256, 0, st>>>(g->imp_nets, g->imp_net, g->net_ptr, g->pin_cell, p.K, LN,
                                                                x0, x1, gp0, gp1, p.S);
                 else
-                    k_net_sums<1, false><<<grid, 256, 0, st>>>(g->imp_nets, g->imp_net, g->net_ptr, g->pin_cell, p.K,
+                    k_net_sums<1, false><<<grid, 256, 0, st>>>(g->imp_nets, g->imp_net, g->net_ptr, g->pin_cell, p.K, LN,
                                                                x0, x1, gp0, gp1, p.S);
                 check_launch("k_net_sums");
                 imp = ImplicitArgs{g->imp_ptr, g->imp_idx, g->imp_w, p.S, nc * p.K};
