@@ -48,6 +48,7 @@ def parse():
     p.add_argument("--no-e2e", action="store_true")
     p.add_argument("--no-serve", action="store_true", help="skip the serving measurement")
     p.add_argument("--no-batch", action="store_true", help="skip the batched measurement")
+    p.add_argument("--no-implicit", action="store_true", help="skip the implicit-clique and high-fanout measurements")
     p.add_argument("--serve-requests", type=int, default=240)
     p.add_argument("--serve-rate", type=float, default=40.0, help="Poisson arrival rate, requests/s")
     p.add_argument("--capture", action="store_true",
@@ -372,6 +373,66 @@ def run_batched(args, gift, ctx, stream):
             "schedule": sched_batch}
 
 
+# ----------------------------------------------------------------- implicit cliques
+def time_steps(gift, ctx, stream, nl, d_np, d_pc, d_fx, d_g, d_out, cut, steps, wd=0):
+    """ms per step (build + filter + HPWL + free) with implicit cliques from `cut` pins (0: none)."""
+    import torch
+
+    def step():
+        h = gift.gift_build_graph(ctx, nl.num_cells, d_np, d_pc, d_fx, wd, stream=stream, implicit_min_pins=cut)
+        gift.gift_filter(ctx, h, d_g, d_out, stream=stream)
+        gift.gift_hpwl(ctx, h, d_out, stream=stream)
+        gift.gift_graph_free_async(h, stream)
+
+    for _ in range(3):
+        step()
+    torch.cuda.synchronize()
+    e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+    e0.record(stream)
+    for _ in range(steps):
+        step()
+    e1.record(stream)
+    torch.cuda.synchronize()
+    h = gift.gift_build_graph(ctx, nl.num_cells, d_np, d_pc, d_fx, wd, stream=stream, implicit_min_pins=cut)
+    info = gift.gift_graph_info(h)
+    sched = gift.gift_ctx_last_schedule(ctx)
+    gift.gift_graph_free(h)
+    return e0.elapsed_time(e1) / steps, info, sched
+
+
+def run_implicit(args, gift, ctx, stream, nl, d_np, d_pc, d_fx, d_g, d_out, nnz_full, S, cut=4):
+    """The benchmark step with the cliques of nets of >= cut pins applied
+    through net sums (the same operator; edge-updates counted on the full
+    expansion's nonzeros)."""
+    ms, info, sched = time_steps(gift, ctx, stream, nl, d_np, d_pc, d_fx, d_g, d_out, cut, max(args.steps, 10))
+    out0 = d_out[:, 0, :].cpu().numpy().copy()
+    return {"implicit_min_pins": cut, "ms_per_step": ms, "value": 6.0 * nnz_full * S / (ms * 1e-3),
+            "stored_nnz": int(info.nnz), "implicit_nets": int(info.implicit_nets),
+            "implicit_pins": int(info.implicit_pins), "sweep_schedule": sched}, out0
+
+
+def run_high_fanout(args, gift, ctx, stream):
+    """The high-fanout workload (1.3M cells, Zipf(2.2) pin counts capped at
+    2,000): the step with every net expanded vs implicit cliques from 8 pins."""
+    import torch
+    nl, g = synth.workload("fanout-1.3m")
+    dev = lambda a: torch.from_numpy(np.ascontiguousarray(a)).cuda()  # noqa: E731
+    d_np, d_pc, d_fx, d_g = dev(nl.net_ptr), dev(nl.pin_cell), dev(nl.is_fixed), dev(g)
+    d_out = torch.empty_like(d_g)
+    S = g.shape[1]
+    ms_e, info_e, sched_e = time_steps(gift, ctx, stream, nl, d_np, d_pc, d_fx, d_g, d_out, 0, 3)
+    ms_i, info_i, sched_i = time_steps(gift, ctx, stream, nl, d_np, d_pc, d_fx, d_g, d_out, 8, 10)
+    units = 6.0 * info_e.nnz * S
+    return {"workload": f"fanout-1.3m: {nl.num_cells} cells, {nl.num_nets} nets, {nl.num_pins} pins, Zipf(2.2) "
+                        f"pin counts capped at 2000, S={S}, FP32 weights",
+            "nnz_expanded": int(info_e.nnz),
+            "expanded": {"ms_per_step": ms_e, "value": units / (ms_e * 1e-3), "sweep_schedule": sched_e},
+            "implicit": {"implicit_min_pins": 8, "ms_per_step": ms_i, "value": units / (ms_i * 1e-3),
+                         "stored_nnz": int(info_i.nnz), "implicit_nets": int(info_i.implicit_nets),
+                         "sweep_schedule": sched_i},
+            "speedup": ms_e / ms_i}
+
+
 # ----------------------------------------------------------------- NVTX ranges
 class Range:
     """NVTX push/pop range (lets an ncu capture select the launches inside)."""
@@ -564,6 +625,9 @@ def run_ours(args):
         e2e = {"value": units * world / et, "unit": UNIT, "ms_per_step": et * 1e3,
                "h2d_bytes_per_step": int(h2d), "d2h_bytes_per_step": int(d2h)}
 
+    implicit, out_imp = None, None
+    if rank == 0 and world == 1 and not args.no_implicit:
+        implicit, out_imp = run_implicit(args, gift, ctx, stream, nl, d_np, d_pc, d_fx, d_g, d_out, nnz, S)
     cpu = None
     precision = None
     if rank == 0 and world == 1 and not args.no_cpu_baseline:
@@ -574,10 +638,18 @@ def run_ours(args):
         precision = precision_report(g[:, 0, :], outs0, hps0, ref0[:, 0, :], hp_ref[0])
         precision["sample"] = (f"signal 0 of {S}, all {N} cells, against the FP64 oracle with exact weights; "
                                "FP32 signal and accumulation")
+        if implicit is not None:
+            floor = 1e-3 * max(float(np.abs(g[:, 0, :]).max()), 1e-30)
+            err = np.abs(out_imp.astype(np.float64) - ref0[:, 0, :]) / np.maximum(np.abs(ref0[:, 0, :]), floor)
+            implicit["max_rel_err"] = float(err.max())
+            implicit["mean_rel_err"] = float(err.mean())
     clocks = clk.summary()
     batched = None
     if rank == 0 and world == 1 and not args.no_batch:
         batched = run_batched(args, gift, ctx, stream)
+    fanout = None
+    if rank == 0 and world == 1 and not args.no_implicit:
+        fanout = run_high_fanout(args, gift, ctx, stream)
     gift.gift_ctx_destroy(ctx)
     serving = None
     if rank == 0 and world == 1 and not args.no_serve:
@@ -594,7 +666,7 @@ def run_ours(args):
                        "sweep_schedule": schedule},
             "roofline": roofline, "cpu_baseline": cpu, "e2e": e2e, "gpu_launches": launches * world,
             "clocks": clocks, "breakdown": breakdown, "filter_only": filt, "precision": precision,
-            "serving": serving, "batched": batched,
+            "serving": serving, "batched": batched, "implicit_cliques": implicit, "high_fanout": fanout,
         }
         print(json.dumps(line), flush=True)
     if world > 1:
