@@ -17,6 +17,7 @@ from __future__ import annotations
 import argparse
 import hashlib
 import json
+import math
 import os
 import statistics
 import subprocess
@@ -49,6 +50,8 @@ def parse():
     p.add_argument("--no-serve", action="store_true", help="skip the serving measurement")
     p.add_argument("--no-batch", action="store_true", help="skip the batched measurement")
     p.add_argument("--no-implicit", action="store_true", help="skip the implicit-clique and high-fanout measurements")
+    p.add_argument("--no-tikhonov", action="store_true", help="skip the Tikhonov measurement")
+    p.add_argument("--no-density", action="store_true", help="skip the density measurement")
     p.add_argument("--serve-requests", type=int, default=240)
     p.add_argument("--serve-rate", type=float, default=40.0, help="Poisson arrival rate, requests/s")
     p.add_argument("--capture", action="store_true",
@@ -433,6 +436,65 @@ def run_high_fanout(args, gift, ctx, stream):
             "speedup": ms_e / ms_i}
 
 
+# ----------------------------------------------------------------- Tikhonov
+def run_tikhonov(args, gift, ctx, stream, nl, d_np, d_pc, d_fx, d_g, d_out, hp_gift):
+    """The exact smoothing GiFt approximates, (I + (I - A~_2))^-1 g by CG with
+    the default step count, on the benchmark graph: time, residual, and the
+    HPWL of its placement beside GiFt's."""
+    import torch
+    h = gift.gift_build_graph(ctx, nl.num_cells, d_np, d_pc, d_fx, stream=stream)
+    res = gift.gift_tikhonov(ctx, h, d_g, d_out, 2.0, 1.0, 0, stream=stream)  # warm (tunes the sweep)
+    torch.cuda.synchronize()
+    e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+    reps = 3
+    e0.record(stream)
+    for _ in range(reps):
+        gift.gift_tikhonov(ctx, h, d_g, d_out, 2.0, 1.0, 0, stream=stream)
+    e1.record(stream)
+    torch.cuda.synchronize()
+    hp = gift.gift_hpwl(ctx, h, d_out, stream=stream)
+    gift.gift_graph_free(h)
+    return {"system": "((1 + lam) I - lam A~_sigma) g' = g, sigma = 2, lam = 1, conjugate gradients from 0",
+            "iterations": math.ceil(math.log(5e-7) / math.log((math.sqrt(3.0) - 1) / (math.sqrt(3.0) + 1))),
+            "ms": e0.elapsed_time(e1) / reps, "max_relative_residual": float(res.max()),
+            "hpwl_signal0": float(hp[0]), "gift_hpwl_signal0": float(hp_gift)}
+
+
+# ----------------------------------------------------------------- density / over-smoothing
+def run_density(args, gift, ctx, stream, nl, d_np, d_pc, d_fx, d_g):
+    """Overflow (Eq. 5 bins, 64 x 64 on the die, square cells sized for 70 %
+    utilisation, target density 0.7) of signal 0 for the initial placement,
+    GiFt's filter, the exact Tikhonov smoothing and single terms of the
+    filter: how far each output piles cells up (over-smoothing)."""
+    import torch
+    N = nl.num_cells
+    die = (0.0, 0.0, float(nl.die), float(nl.die))
+    side = float(np.sqrt(0.7 * nl.die * nl.die / N))
+    h = gift.gift_build_graph(ctx, N, d_np, d_pc, d_fx, stream=stream)
+    out = torch.empty_like(d_g)
+    res = {}
+
+    def ov(x):
+        return float(gift.gift_density(ctx, x, die, (64, 64), 0.7, (side, side), stream=stream)[1][0])
+
+    res["initial"] = ov(d_g)
+    for name, terms in (("gift", None), ("A2^2 alone", ((2.0, 2, 1.0),)), ("A4^4 alone", ((4.0, 4, 1.0),))):
+        gift.gift_filter(ctx, h, d_g, out, gift.make_spec(terms=terms), stream=stream)
+        res[name] = ov(out)
+    gift.gift_tikhonov(ctx, h, d_g, out, 2.0, 1.0, 0, stream=stream)
+    res["tikhonov"] = ov(out)
+    torch.cuda.synchronize()
+    e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+    e0.record(stream)
+    for _ in range(5):
+        gift.gift_density(ctx, out, die, (64, 64), 0.7, (side, side), stream=stream)
+    e1.record(stream)
+    torch.cuda.synchronize()
+    gift.gift_graph_free(h)
+    return {"bins": [64, 64], "cell_side": side, "target_density": 0.7, "overflow_signal0": res,
+            "density_ms_8_signals": e0.elapsed_time(e1) / 5}
+
+
 # ----------------------------------------------------------------- NVTX ranges
 class Range:
     """NVTX push/pop range (lets an ncu capture select the launches inside)."""
@@ -625,6 +687,12 @@ def run_ours(args):
         e2e = {"value": units * world / et, "unit": UNIT, "ms_per_step": et * 1e3,
                "h2d_bytes_per_step": int(h2d), "d2h_bytes_per_step": int(d2h)}
 
+    tikh = None
+    if rank == 0 and world == 1 and not args.no_tikhonov:
+        tikh = run_tikhonov(args, gift, ctx, stream, nl, d_np, d_pc, d_fx, d_g, d_out, hp[0])
+    dens = None
+    if rank == 0 and world == 1 and not args.no_density:
+        dens = run_density(args, gift, ctx, stream, nl, d_np, d_pc, d_fx, d_g)
     implicit, out_imp = None, None
     if rank == 0 and world == 1 and not args.no_implicit:
         implicit, out_imp = run_implicit(args, gift, ctx, stream, nl, d_np, d_pc, d_fx, d_g, d_out, nnz, S)
@@ -667,6 +735,7 @@ def run_ours(args):
             "roofline": roofline, "cpu_baseline": cpu, "e2e": e2e, "gpu_launches": launches * world,
             "clocks": clocks, "breakdown": breakdown, "filter_only": filt, "precision": precision,
             "serving": serving, "batched": batched, "implicit_cliques": implicit, "high_fanout": fanout,
+            "tikhonov": tikh, "density": dens,
         }
         print(json.dumps(line), flush=True)
     if world > 1:

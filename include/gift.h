@@ -258,6 +258,38 @@ GIFT_API gift_status gift_hpwl(gift_ctx *ctx, const gift_graph *graph, const flo
 
 
 /* ---------------------------------------------------------------------------
+ * Exact Tikhonov smoothing, the filter GiFt approximates (Sec. 3.2.2): the
+ * minimiser of ||g - g'||^2 + lambda tr(g'^T L~ g') is g' = (I + lambda L~)^-1 g
+ * (Eq. 18 with lambda = 1), here with the self-loop Laplacian L~ = I - A~_sigma
+ * (A~_sigma of Eq. 16).  Conjugate gradients on (1 + lambda) I - lambda A~_sigma
+ * (symmetric positive definite, spectrum in [1, 1 + 2 lambda)) from g' = 0,
+ * `iterations` steps (0: enough for a 5e-7 error bound, 12 at lambda = 1),
+ * each column independently; one sweep of the filter machinery per step.
+ * reimpose_fixed = 1 puts the fixed rows of g back afterwards.  residual
+ * (host, [2 * num_signals], may be NULL): ||r|| / ||g|| per column after the
+ * last step.  num_signals <= 128; sigma > 0; lambda >= 0. */
+GIFT_API gift_status gift_tikhonov(gift_ctx *ctx, const gift_graph *graph, float sigma, float lambda,
+                                   int32_t iterations, int32_t reimpose_fixed, const float *g_in,
+                                   int32_t num_signals, float *g_out, double *residual, int32_t mem, void *stream);
+
+/* ---------------------------------------------------------------------------
+ * Bin density of a placement (Eq. 5): the die [die[0], die[2]) x [die[1],
+ * die[3]) cut into bins_x x bins_y equal bins; cell v is a w_v x h_v rectangle
+ * centred on its location (cell_w / cell_h per cell, or NULL for unit_w x
+ * unit_h); rho_b = sum over cells of the area of the cell inside bin b.  The
+ * overlaps are computed in FP64 (no contraction), quantised to q = (bin area)
+ * * 2^-40 and summed as integers, so the result does not depend on the order
+ * of the sums.  For every signal s of xy ([num_cells][num_signals][2]):
+ * density (host, [num_signals][bins_y][bins_x], may be NULL) = rho_b / bin
+ * area; overflow (host, [num_signals], may be NULL) = sum over bins of
+ * max(0, rho_b - target * bin area) / (total cell area).  bins_x * bins_y <=
+ * 2^24. */
+GIFT_API gift_status gift_density(gift_ctx *ctx, const float *xy, int32_t num_cells, int32_t num_signals,
+                                  const float *cell_w, const float *cell_h, float unit_w, float unit_h,
+                                  const double *die, int32_t bins_x, int32_t bins_y, double target,
+                                  double *density, double *overflow, int32_t mem, void *stream);
+
+/* ---------------------------------------------------------------------------
  * Batches.  gift_build_batch builds one graph from `num_graphs` netlists (all
  * in the same memory kind): graph b's cells, nets and pins follow those of
  * graphs 0..b-1, so the graph is block-diagonal and each row is exactly the

@@ -216,6 +216,7 @@ template <>
 struct Store<float> {
     __device__ static float put(double v) { return __double2float_rn(rne_to(v, 23, -126)); }
     __device__ static double get(float w) { return (double)w; }
+    __device__ static float getf(float w) { return w; }
 };
 template <>
 struct Store<__nv_bfloat16> {
@@ -224,12 +225,22 @@ struct Store<__nv_bfloat16> {
         return __ushort_as_bfloat16((unsigned short)(__float_as_uint(f) >> 16));
     }
     __device__ static double get(__nv_bfloat16 w) { return (double)__bfloat162float(w); }
+    __device__ static float getf(__nv_bfloat16 w) { return __bfloat162float(w); }
 };
 template <>
 struct Store<__half> {
     __device__ static __half put(double v) { return __float2half_rn(__double2float_rn(rne_to(v, 10, -14))); }
     __device__ static double get(__half w) { return (double)__half2float(w); }
+    __device__ static float getf(__half w) { return __half2float(w); }
 };
+
+// Each net's weight 2/M as stored (one rounding): the weight of every pair
+// that only this net contributes.
+template <typename WT>
+__global__ void k_net_stored(int32_t E, const double *__restrict__ wnet, WT *__restrict__ wst) {
+    for (int64_t e = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; e < E; e += (int64_t)gridDim.x * blockDim.x)
+        wst[e] = Store<WT>::put(wnet[e]);
+}
 
 // ------------------------------------------------------------------ rows
 // Every tier writes, at the row's raw position: the sorted unique columns,
@@ -251,9 +262,9 @@ template <typename WT>
 __global__ void __launch_bounds__(kSmallThreads)
 k_rows_small(int32_t N, const int64_t *__restrict__ inc_ptr, const int32_t *__restrict__ inc_net,
              const int64_t *__restrict__ net_ptr, const int32_t *__restrict__ pin_cell,
-             const double *__restrict__ wnet, const int64_t *__restrict__ raw_ptr, int32_t *__restrict__ out_col,
-             WT *__restrict__ out_val, int32_t *__restrict__ ucount, double *__restrict__ degree,
-             int32_t *__restrict__ wlist, int32_t *__restrict__ wcount) {
+             const double *__restrict__ wnet, const WT *__restrict__ wst, const int64_t *__restrict__ raw_ptr,
+             int32_t *__restrict__ out_col, WT *__restrict__ out_val, int32_t *__restrict__ ucount,
+             double *__restrict__ degree, int32_t *__restrict__ wlist, int32_t *__restrict__ wcount) {
     __shared__ uint64_t keys_all[kSmallGroups][kSmallCap];   // later reused for the stored weights
     __shared__ uint64_t sorted_all[kSmallGroups][kSmallCap];
     __shared__ int32_t ofs_all[kSmallGroups][kSmallCap + 1];
@@ -344,29 +355,59 @@ k_rows_small(int32_t N, const int64_t *__restrict__ inc_ptr, const int32_t *__re
             }
         }
         __syncwarp();
-        for (int i0 = 0; i0 < max_n; i0 += kGS) {
+        // Unique columns: run heads found by ballot (u = heads before).  A run
+        // of several nets sums their weights in FP64 in net order and rounds
+        // once; a run of one net takes the net's stored weight.  The degree:
+        // when every stored weight is >= 2^-11 and the row's sum < 2^19, all
+        // partial sums are multiples of 2^-34 below 2^53 units, so FP64 adds
+        // them exactly in any order -- summed here as integers across the
+        // group; otherwise one lane adds them in column order.
+        const unsigned gmask = ((1u << kGS) - 1u) << (gw * kGS);
+        int ubase = 0;
+        long long qsum = 0;
+        bool exact = true;
+        for (int i0 = 0; i0 < max_n; i0 += kGS) {  // warp-uniform
             const int i = i0 + gl;
+            bool head = false;
+            int32_t c = 0;
             if (i < n) {
-                const int32_t c = key_cell(srt[i]);
-                if (i == 0 || key_cell(srt[i - 1]) != c) {
-                    int u = 0;  // run heads before i
-                    for (int j = 1; j <= i; ++j) u += key_cell(srt[j]) != key_cell(srt[j - 1]);
-                    double sum = 0.0;
-                    for (int r = i; r < n && key_cell(srt[r]) == c; ++r) sum += wnet[key_net(srt[r])];
-                    const WT w = Store<WT>::put(sum);
-                    out_col[rb + u] = c;
-                    out_val[rb + u] = w;
-                    rv[u] = Store<WT>::get(w);
-                }
+                c = key_cell(srt[i]);
+                head = i == 0 || key_cell(srt[i - 1]) != c;
             }
+            const unsigned gh = (__ballot_sync(full, head) & gmask) >> (gw * kGS);
+            if (head) {
+                const int u = ubase + __popc(gh & ((1u << gl) - 1u));
+                int r = i + 1;
+                while (r < n && key_cell(srt[r]) == c) ++r;
+                WT w;
+                if (r == i + 1) {
+                    w = wst[key_net(srt[i])];
+                } else {
+                    double sum = 0.0;
+                    for (int t = i; t < r; ++t) sum += wnet[key_net(srt[t])];
+                    w = Store<WT>::put(sum);
+                }
+                out_col[rb + u] = c;
+                out_val[rb + u] = w;
+                const float wf = Store<WT>::getf(w);
+                rv[u] = (double)wf;
+                if (wf >= 0x1p-11f && wf < 0x1p19f) qsum += (long long)(wf * 0x1p34f);
+                else exact = false;
+            }
+            ubase += __popc(gh);
         }
+#pragma unroll
+        for (int o = 1; o < kGS; o <<= 1) qsum += __shfl_xor_sync(full, qsum, o);
+        const bool gexact = (__ballot_sync(full, !exact) & gmask) == 0;
         __syncwarp();
         if (gl == 0 && small) {
-            int nu = n > 0 ? 1 : 0;
-            for (int j = 1; j < n; ++j) nu += key_cell(srt[j]) != key_cell(srt[j - 1]);
             double d = 0.0;
-            for (int u = 0; u < nu; ++u) d += rv[u];
-            ucount[row] = nu;
+            if (gexact && qsum < (1ll << 53)) {
+                d = (double)qsum * 0x1p-34;
+            } else {
+                for (int u = 0; u < ubase; ++u) d += rv[u];
+            }
+            ucount[row] = ubase;
             degree[row] = d;
         }
         __syncwarp();
@@ -803,9 +844,12 @@ void build_graph_impl(gift_ctx *ctx, const gift_netlist *nl, const gift_build_op
         {
             LaunchTimer lt(ctx, st, "build.rows",
                            16.0 * N + 4.0 * ninc + 16.0 * ninc + 4.0 * nraw + (4.0 + wsz) * nraw + 12.0 * N);
+            DevBuf wst(ctx, sizeof(WT) * std::max<int32_t>(E, 1), st);
+            if (E > 0)
+                k_net_stored<WT><<<grid_for(ctx, E, 256), 256, 0, st>>>(E, wnet.as<double>(), wst.as<WT>());
             k_rows_small<WT><<<grid_for(ctx, (int64_t)N * kGS, kSmallThreads, 8), kSmallThreads, 0, st>>>(
                 N, inc_ptr.as<int64_t>(), inc_net.as<int32_t>(), g->net_ptr, g->pin_cell, wnet.as<double>(),
-                raw_ptr.as<int64_t>(), out_col.as<int32_t>(), ov, ucount.as<int32_t>(), g->degree,
+                wst.as<WT>(), raw_ptr.as<int64_t>(), out_col.as<int32_t>(), ov, ucount.as<int32_t>(), g->degree,
                 wlist.as<int32_t>(), wc);
             check_launch("k_rows_small");
         }

@@ -124,6 +124,8 @@ def load(build_if_missing: bool = True):
         "gift_filter_capture": (I32, [P, P, P, P, I32, P, C.POINTER(P)]),
         "gift_exec_launch": (I32, [P, P]),
         "gift_exec_free": (None, [P]),
+        "gift_tikhonov": (I32, [P, P, C.c_float, C.c_float, I32, I32, P, I32, P, P, I32, P]),
+        "gift_density": (I32, [P, P, I32, I32, P, P, C.c_float, C.c_float, P, I32, I32, C.c_double, P, P, I32, P]),
         "gift_serve_opts_default": (None, [P]),
         "gift_serve_create": (I32, [P, C.POINTER(P)]),
         "gift_serve_submit": (I32, [P, P, P, I32, I32, C.POINTER(C.c_uint64)]),
@@ -432,3 +434,35 @@ def gift_exec_launch(exec_, stream=None):
 
 def gift_exec_free(exec_):
     load().gift_exec_free(exec_)
+
+
+# ------------------------------------------------------------------ Tikhonov
+def gift_tikhonov(ctx, graph, g_in, g_out, sigma: float = 2.0, lam: float = 1.0, iterations: int = 0,
+                  reimpose: bool = True, stream=None) -> np.ndarray:
+    """g_out = (I + lam (I - A~_sigma))^-1 g_in by CG; returns ||r|| / ||g|| per column."""
+    pi, mi = _ptr(g_in)
+    po, mo = _ptr(g_out)
+    if mi != mo:
+        raise ValueError("g_in and g_out must be in the same memory")
+    S = g_in.shape[1]
+    res = np.zeros(2 * S, dtype=np.float64)
+    _check(load().gift_tikhonov(ctx, graph, sigma, lam, iterations, 1 if reimpose else 0, pi, S, po,
+                                res.ctypes.data, mi, _stream(stream)))
+    return res
+
+
+# ------------------------------------------------------------------ density
+def gift_density(ctx, xy, die=(0.0, 0.0, 1000.0, 1000.0), bins=(32, 32), target: float = 1.0, unit=(1.0, 1.0),
+                 cell_w=None, cell_h=None, stream=None):
+    """Bin density (Eq. 5) of every signal of xy [N][S][2] and its overflow:
+    returns (density [S][bins_y][bins_x], overflow [S])."""
+    p, mem = _ptr(xy)
+    N, S = xy.shape[0], xy.shape[1]
+    pw, _ = _ptr(cell_w)
+    ph, _ = _ptr(cell_h)
+    d = np.ascontiguousarray(die, dtype=np.float64)
+    out = np.empty((S, bins[1], bins[0]), dtype=np.float64)
+    ov = np.empty(S, dtype=np.float64)
+    _check(load().gift_density(ctx, p, N, S, pw, ph, unit[0], unit[1], d.ctypes.data, bins[0], bins[1], target,
+                               out.ctypes.data, ov.ctypes.data, mem, _stream(stream)))
+    return out, ov

@@ -5,6 +5,7 @@ closed forms derived by hand (tests/golden), Theorem 1 and spectral facts,
 a brute-force dense construction on tiny inputs, scipy's COO->CSR duplicate
 summation, numpy's own float conversions, and hand-computed HPWL.
 """
+import math
 import os
 from fractions import Fraction
 
@@ -381,3 +382,83 @@ def test_implicit_degree_of_one_net_by_pair_count(M, k):
         assert d[c] == (1 * (2.0 / M)) * (M - 1)
     G = oracle.build_graph(n, nl_ptr, pins, cut=2)
     assert G.nnz == 0
+
+
+# ------------------------------------------------------------ Tikhonov smoothing
+@pytest.mark.parametrize("M", [2, 3, 7])
+@pytest.mark.parametrize("sigma,lam", [(2.0, 1.0), (4.0, 0.5), (1.0, 3.0)])
+def test_tikhonov_single_net_closed_form(M, sigma, lam):
+    """One M-pin clique: A~_sigma keeps constants (eigenvalue 1) and scales the
+    zero-mean part by r = (sigma - w) / (d + sigma), w = 2/M, d = (M - 1) w, so
+    ((1 + lam) I - lam A~)^-1 g = mean + (g - mean) / (1 + lam (1 - r))."""
+    N, ptr, pins = _single_net(M)
+    G = oracle.build_graph(N, ptr, pins)
+    d = oracle.degrees(G)
+    g = np.linspace(0.0, 7.0, 2 * N).reshape(N, 2) ** 1.5
+    got = oracle.tikhonov(G, d, g, sigma, lam, reimpose=False)
+    w = 2.0 / M
+    r = (sigma - w) / ((M - 1) * w + sigma)
+    mean = g.mean(axis=0)
+    np.testing.assert_allclose(got, mean + (g - mean) / (1.0 + lam * (1.0 - r)), rtol=1e-12, atol=1e-12)
+
+
+@pytest.mark.parametrize("seed", [1, 2, 3])
+@pytest.mark.parametrize("sigma,lam", [(2.0, 1.0), (4.0, 2.0)])
+def test_tikhonov_dense_brute_force(seed, sigma, lam):
+    nl = synth.random_small(seed + 60, 30, 40, 6, num_fixed=3, allow_repeat=seed == 3)
+    x = synth.make_signals(nl, 2, seed).reshape(nl.num_cells, -1).astype(np.float64)
+    A, _ = _dense_reference(nl, x)
+    deg = A.sum(axis=1)
+    S = np.diag(1.0 / np.sqrt(deg + sigma))
+    T = S @ (A + sigma * np.eye(nl.num_cells)) @ S
+    want = np.linalg.solve((1.0 + lam) * np.eye(nl.num_cells) - lam * T, x)
+    fx = nl.is_fixed.astype(bool)
+    want[fx] = x[fx]
+    G = oracle.build_graph(nl.num_cells, nl.net_ptr, nl.pin_cell)
+    got = oracle.tikhonov(G, oracle.degrees(G), x, sigma, lam, nl.is_fixed)
+    np.testing.assert_allclose(got, want, rtol=1e-10, atol=1e-10)
+
+
+def test_tikhonov_without_smoothing_is_identity():
+    nl = synth.random_small(71, 25, 30, 5)
+    x = synth.make_signals(nl, 1, 3).reshape(nl.num_cells, -1).astype(np.float64)
+    G = oracle.build_graph(nl.num_cells, nl.net_ptr, nl.pin_cell)
+    np.testing.assert_allclose(oracle.tikhonov(G, oracle.degrees(G), x, 2.0, 0.0, reimpose=False), x, rtol=1e-14)
+
+
+# ------------------------------------------------------------ bin density (Eq. 5)
+def test_density_hand_cases():
+    """4 x 4 bins of 10 x 10 on [0, 40)^2.  A 2 x 2 cell centred in bin (1, 2)
+    puts its area 4 there (density 0.04); a 2 x 2 cell centred on the corner
+    shared by bins (2,2), (3,2), (2,3), (3,3) puts 1 in each; a cell outside
+    the die adds nothing."""
+    xy = np.array([[[15.0, 25.0]], [[30.0, 30.0]], [[-50.0, 5.0]]], dtype=np.float32)  # [N=3][S=1][2]
+    counts, dens, over = oracle.density(xy, (0, 0, 40, 40), 4, 4, target=1.0, unit=(2.0, 2.0))
+    q = math.ldexp(1.0, 40) / 100.0  # quanta per unit area
+    want = np.zeros((4, 4))
+    want[2, 1] = 4.0
+    for j, i in ((2, 2), (2, 3), (3, 2), (3, 3)):
+        want[j, i] = 1.0
+    np.testing.assert_array_equal(counts[0], np.rint(want * q).astype(np.int64))
+    np.testing.assert_allclose(dens[0], want / 100.0, rtol=0, atol=math.ldexp(1.0, -40))  # one quantum
+    assert over[0] == 0.0  # every bin far below its area
+
+
+def test_density_conserves_area_and_counts_overflow():
+    rng_xy = synth.uniform(5, synth.T_MISC, np.arange(2000, dtype=np.uint64)).reshape(1000, 1, 2) * 900.0 + 50.0
+    xy = rng_xy.astype(np.float32)
+    counts, dens, over = oracle.density(xy, (0, 0, 1000, 1000), 16, 16, target=0.0, unit=(3.0, 5.0))
+    q = math.ldexp(1.0, 40) / (62.5 * 62.5)
+    total = round(15.0 * q) * 1000
+    # every cell lies inside the die: the pieces add up to the cells' area, up
+    # to half a quantum per piece (at most 4 pieces per cell here)
+    assert abs(int(counts.sum()) - total) <= 4 * 1000
+    # target 0: every quantum is overflow
+    assert abs(over[0] - counts.sum() / total) <= 1e-12
+    # one cell per bin, each bin exactly half covered by a cell, target 0.5: no overflow
+    c = (np.arange(4) + 0.5) * 25.0
+    X, Y = np.meshgrid(c, c)
+    xy = np.stack([X.ravel(), Y.ravel()], axis=1)[:, None, :].astype(np.float32)
+    _, dens, over = oracle.density(xy, (0, 0, 100, 100), 4, 4, target=0.5, unit=(25.0, 12.5))
+    np.testing.assert_allclose(dens[0], 0.5, rtol=0, atol=math.ldexp(1.0, -40))
+    assert over[0] == 0.0
