@@ -64,6 +64,24 @@ def dist_env():
     return int(os.environ.get("RANK", 0)), int(os.environ.get("WORLD_SIZE", 1)), int(os.environ.get("LOCAL_RANK", 0))
 
 
+def max_over_ranks(x: float, world: int, device: str = "cuda") -> float:
+    """The largest of every rank's value (the slowest replica's time); the
+    process group is NCCL on GPUs, gloo in the CPU tests."""
+    if world <= 1:
+        return x
+    import torch
+    import torch.distributed as dist
+    t = torch.tensor([x], dtype=torch.float64, device=device)
+    dist.all_reduce(t, op=dist.ReduceOp.MAX)
+    return float(t.item())
+
+
+def job_value(units_per_replica: float, world: int, seconds: float) -> float:
+    """Whole-job throughput of `world` replicas: all their units over the
+    slowest replica's time (weak scaling)."""
+    return units_per_replica * world / seconds
+
+
 def peaks():
     try:
         with open(os.path.join(ROOT, "MEASURED_PEAKS.json")) as f:
@@ -602,12 +620,8 @@ def run_ours(args):
     schedule = gift.gift_ctx_last_schedule(ctx)
     stats = gift.gift_ctx_kernel_stats(ctx)
     gift.gift_ctx_set_profiling(ctx, False)
-    if world > 1:
-        import torch.distributed as dist
-        t = torch.tensor([ms], device="cuda")
-        dist.all_reduce(t, op=dist.ReduceOp.MAX)
-        ms = float(t.item())
-    value = units * world / (ms * 1e-3)
+    ms = max_over_ranks(ms, world)
+    value = job_value(units, world, ms * 1e-3)
     launches = int(sum(r["kernels"] for r in stats.values()))
 
     # dominant kernel and its roofline
@@ -677,14 +691,10 @@ def run_ours(args):
             estep()
         torch.cuda.synchronize()
         et = (time.perf_counter() - t0) / args.steps
-        if world > 1:
-            import torch.distributed as dist
-            t = torch.tensor([et], device="cuda")
-            dist.all_reduce(t, op=dist.ReduceOp.MAX)
-            et = float(t.item())
+        et = max_over_ranks(et, world)
         h2d = nl.net_ptr.nbytes + nl.pin_cell.nbytes + nl.is_fixed.nbytes + g.nbytes + g.nbytes
         d2h = g.nbytes + 8 * S
-        e2e = {"value": units * world / et, "unit": UNIT, "ms_per_step": et * 1e3,
+        e2e = {"value": job_value(units, world, et), "unit": UNIT, "ms_per_step": et * 1e3,
                "h2d_bytes_per_step": int(h2d), "d2h_bytes_per_step": int(d2h)}
 
     tikh = None

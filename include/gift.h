@@ -344,7 +344,8 @@ typedef struct gift_serve_opts {
     int32_t compute_hpwl;       /* 1: HPWL of each result (default 1)                */
     gift_filter_spec spec;      /* filter of every request; spec.schedule 0 = a fixed
                                    direct row-group shape (4244), not the autotuner  */
-    int32_t reserved[8];        /* zero                                              */
+    int32_t implicit_min_pins;  /* build option of every request (0: expand all)    */
+    int32_t reserved[7];        /* zero                                              */
 } gift_serve_opts;
 
 typedef struct gift_req_stats {

@@ -421,9 +421,9 @@ __global__ void __launch_bounds__(kRowsWarps * 32)
 k_rows_warp(const int32_t *__restrict__ rows, const int32_t *__restrict__ nrows_p,
             const int64_t *__restrict__ inc_ptr, const int32_t *__restrict__ inc_net,
             const int64_t *__restrict__ net_ptr, const int32_t *__restrict__ pin_cell,
-            const double *__restrict__ wnet, const int64_t *__restrict__ raw_ptr, int32_t *__restrict__ out_col,
-            WT *__restrict__ out_val, int32_t *__restrict__ ucount, double *__restrict__ degree,
-            int32_t *__restrict__ big_rows, int32_t *__restrict__ big_count) {
+            const double *__restrict__ wnet, const WT *__restrict__ wst, const int64_t *__restrict__ raw_ptr,
+            int32_t *__restrict__ out_col, WT *__restrict__ out_val, int32_t *__restrict__ ucount,
+            double *__restrict__ degree, int32_t *__restrict__ big_rows, int32_t *__restrict__ big_count) {
     __shared__ uint64_t keys_all[kRowsWarps][kWarpCap];
     __shared__ int32_t ofs_all[kRowsWarps][33];
     __shared__ int32_t net_all[kRowsWarps][32];
@@ -506,8 +506,13 @@ k_rows_warp(const int32_t *__restrict__ rows, const int32_t *__restrict__ nrows_
                 __syncwarp();
             }
         }
-        // run heads -> unique index; each head sums its run in sorted (net) order
+        // run heads -> unique index; each head sums its run in sorted (net)
+        // order (a run of one net takes the net's stored weight); the degree
+        // as in the small tier: an exact integer sum across the warp where it
+        // equals the column-order FP64 sum, else one lane in FP64
         int uniq = 0;
+        long long qsum = 0;
+        bool exact = true;
         for (int base = 0; base < n; base += 32) {
             int t = base + lane;
             bool head = false;
@@ -519,17 +524,35 @@ k_rows_warp(const int32_t *__restrict__ rows, const int32_t *__restrict__ nrows_
             unsigned hm = __ballot_sync(full, head);
             if (head) {
                 int u = uniq + __popc(hm & ((1u << lane) - 1));
-                double sum = 0.0;
-                for (int r = t; r < n && key_cell(keys[r]) == c; ++r) sum += wnet[key_net(keys[r])];
+                int r = t + 1;
+                while (r < n && key_cell(keys[r]) == c) ++r;
+                WT w;
+                if (r == t + 1) {
+                    w = wst[key_net(keys[t])];
+                } else {
+                    double sum = 0.0;
+                    for (int q = t; q < r; ++q) sum += wnet[key_net(keys[q])];
+                    w = Store<WT>::put(sum);
+                }
                 out_col[rbase + u] = c;
-                out_val[rbase + u] = Store<WT>::put(sum);
+                out_val[rbase + u] = w;
+                const float wf = Store<WT>::getf(w);
+                if (wf >= 0x1p-11f && wf < 0x1p19f) qsum += (long long)(wf * 0x1p34f);
+                else exact = false;
             }
             uniq += __popc(hm);
         }
+#pragma unroll
+        for (int o = 16; o > 0; o >>= 1) qsum += __shfl_xor_sync(full, qsum, o);
+        const bool wexact = __ballot_sync(full, !exact) == 0u;
         __syncwarp();
         if (lane == 0) {
             double d = 0.0;
-            for (int u = 0; u < uniq; ++u) d += Store<WT>::get(out_val[rbase + u]);
+            if (wexact && qsum < (1ll << 53)) {
+                d = (double)qsum * 0x1p-34;
+            } else {
+                for (int u = 0; u < uniq; ++u) d += Store<WT>::get(out_val[rbase + u]);
+            }
             ucount[row] = uniq;
             degree[row] = d;
         }
@@ -642,29 +665,50 @@ k_rows_block(const int64_t *__restrict__ inc_ptr, const int32_t *__restrict__ in
     }
 }
 
-// Compaction: 8 lanes per row copy its entries to their CSR position; the
-// group's first lane writes the scales of the paper's two self-loop weights
-// (sigma = 2, 4; Eq. 16) from the degree.
+// Compaction: block per chunk of kCopyRows rows.  The chunk's raw entries are
+// contiguous and so are its CSR entries: threads stride over the raw range
+// (coalesced reads), find each entry's row by binary search over the
+// chunk's raw row pointers in shared memory, and write the row's first
+// ucount entries to their CSR position (coalesced writes).  Thread r also
+// writes row r's scales for the paper's two self-loop weights (sigma = 2, 4;
+// Eq. 16) from the degree.
+constexpr int kCopyRows = 256;
+
 template <typename WT>
-__global__ void k_copy_rows(int32_t N, const int64_t *__restrict__ raw_ptr, const int64_t *__restrict__ row_ptr,
-                            const int32_t *__restrict__ out_col, const WT *__restrict__ out_val,
-                            int32_t *__restrict__ col, WT *__restrict__ val, const double *__restrict__ degree,
-                            int32_t *__restrict__ max_row, float *__restrict__ s2, float *__restrict__ s4) {
-    const int g = (blockIdx.x * blockDim.x + threadIdx.x) / kGS, gl = threadIdx.x % kGS;
-    const int64_t ng = ((int64_t)gridDim.x * blockDim.x) / kGS;
+__global__ void __launch_bounds__(kCopyRows)
+k_copy_rows(int32_t N, const int64_t *__restrict__ raw_ptr, const int64_t *__restrict__ row_ptr,
+            const int32_t *__restrict__ out_col, const WT *__restrict__ out_val, int32_t *__restrict__ col,
+            WT *__restrict__ val, const double *__restrict__ degree, int32_t *__restrict__ max_row,
+            float *__restrict__ s2, float *__restrict__ s4) {
+    __shared__ int64_t rraw[kCopyRows + 1], rout[kCopyRows + 1];
+    const int64_t r0 = (int64_t)blockIdx.x * kCopyRows;
+    const int nr = (int)min((int64_t)kCopyRows, (int64_t)N - r0);
+    for (int t = threadIdx.x; t <= nr; t += blockDim.x) {
+        rraw[t] = raw_ptr[r0 + t];
+        rout[t] = row_ptr[r0 + t];
+    }
+    __syncthreads();
+    const int64_t k0 = rraw[0], k1 = rraw[nr];
+    for (int64_t k = k0 + threadIdx.x; k < k1; k += blockDim.x) {
+        int lo = 0, hi = nr - 1;  // last row whose raw start <= k
+        while (lo < hi) {
+            const int mid = (lo + hi + 1) >> 1;
+            if (rraw[mid] <= k) lo = mid;
+            else hi = mid - 1;
+        }
+        const int64_t t = k - rraw[lo];
+        if (t < rout[lo + 1] - rout[lo]) {
+            col[rout[lo] + t] = out_col[k];
+            val[rout[lo] + t] = out_val[k];
+        }
+    }
     int best = 0;
-    for (int64_t i = g; i < N; i += ng) {
-        const int64_t src = raw_ptr[i], dst = row_ptr[i], n = row_ptr[i + 1] - dst;
-        for (int64_t t = gl; t < n; t += kGS) {
-            col[dst + t] = out_col[src + t];
-            val[dst + t] = out_val[src + t];
-        }
-        if (gl == 0) {
-            const double d = degree[i];
-            s2[i] = scale_value(d, 2.0, GIFT_NORM_SYM);
-            s4[i] = scale_value(d, 4.0, GIFT_NORM_SYM);
-            best = max(best, (int)n);
-        }
+    if ((int)threadIdx.x < nr) {
+        const int64_t i = r0 + threadIdx.x;
+        const double d = degree[i];
+        s2[i] = scale_value(d, 2.0, GIFT_NORM_SYM);
+        s4[i] = scale_value(d, 4.0, GIFT_NORM_SYM);
+        best = (int)(rout[threadIdx.x + 1] - rout[threadIdx.x]);
     }
     for (int o = 16; o; o >>= 1) best = max(best, __shfl_xor_sync(0xffffffffu, best, o));
     if ((threadIdx.x & 31) == 0 && best) atomicMax(max_row, best);
@@ -841,10 +885,10 @@ void build_graph_impl(gift_ctx *ctx, const gift_netlist *nl, const gift_build_op
         using WT = decltype(tag);
         WT *ov = out_val.as<WT>();
         int32_t *wc = counts.as<int32_t>(), *bc = counts.as<int32_t>() + 1;
+        DevBuf wst(ctx, sizeof(WT) * std::max<int32_t>(E, 1), st);
         {
             LaunchTimer lt(ctx, st, "build.rows",
                            16.0 * N + 4.0 * ninc + 16.0 * ninc + 4.0 * nraw + (4.0 + wsz) * nraw + 12.0 * N);
-            DevBuf wst(ctx, sizeof(WT) * std::max<int32_t>(E, 1), st);
             if (E > 0)
                 k_net_stored<WT><<<grid_for(ctx, E, 256), 256, 0, st>>>(E, wnet.as<double>(), wst.as<WT>());
             k_rows_small<WT><<<grid_for(ctx, (int64_t)N * kGS, kSmallThreads, 8), kSmallThreads, 0, st>>>(
@@ -857,8 +901,8 @@ void build_graph_impl(gift_ctx *ctx, const gift_netlist *nl, const gift_build_op
             LaunchTimer lt(ctx, st, "build.rows_warp", 0.0);
             k_rows_warp<WT><<<ctx->num_sms * 6, kRowsWarps * 32, 0, st>>>(
                 wlist.as<int32_t>(), wc, inc_ptr.as<int64_t>(), inc_net.as<int32_t>(), g->net_ptr, g->pin_cell,
-                wnet.as<double>(), raw_ptr.as<int64_t>(), out_col.as<int32_t>(), ov, ucount.as<int32_t>(),
-                g->degree, big_rows.as<int32_t>(), bc);
+                wnet.as<double>(), wst.as<WT>(), raw_ptr.as<int64_t>(), out_col.as<int32_t>(), ov,
+                ucount.as<int32_t>(), g->degree, big_rows.as<int32_t>(), bc);
             check_launch("k_rows_warp");
         }
         if (maxraw > kWarpCap) {
@@ -949,18 +993,18 @@ void build_graph_impl(gift_ctx *ctx, const gift_netlist *nl, const gift_build_op
     GIFT_CUDA(cudaMemsetAsync(flag.p, 0, sizeof(int) * 4, st));
     {
         LaunchTimer lt(ctx, st, "build.compact", 24.0 * N + 2.0 * (4.0 + wsz) * nnz);
-        const int grid = grid_for(ctx, (int64_t)N * kGS, 256);
+        const int grid = (int)ceil_div(N, kCopyRows);
         if (g->weight_dtype == GIFT_WEIGHT_F32)
-            k_copy_rows<float><<<grid, 256, 0, st>>>(N, raw_ptr.as<int64_t>(), g->row_ptr, out_col.as<int32_t>(),
+            k_copy_rows<float><<<grid, kCopyRows, 0, st>>>(N, raw_ptr.as<int64_t>(), g->row_ptr, out_col.as<int32_t>(),
                                                       out_val.as<float>(), g->col, (float *)g->val, g->degree,
                                                       flag.as<int32_t>(), s2, s4);
         else if (g->weight_dtype == GIFT_WEIGHT_BF16)
-            k_copy_rows<__nv_bfloat16><<<grid, 256, 0, st>>>(N, raw_ptr.as<int64_t>(), g->row_ptr,
+            k_copy_rows<__nv_bfloat16><<<grid, kCopyRows, 0, st>>>(N, raw_ptr.as<int64_t>(), g->row_ptr,
                                                               out_col.as<int32_t>(), out_val.as<__nv_bfloat16>(),
                                                               g->col, (__nv_bfloat16 *)g->val, g->degree,
                                                               flag.as<int32_t>(), s2, s4);
         else
-            k_copy_rows<__half><<<grid, 256, 0, st>>>(N, raw_ptr.as<int64_t>(), g->row_ptr, out_col.as<int32_t>(),
+            k_copy_rows<__half><<<grid, kCopyRows, 0, st>>>(N, raw_ptr.as<int64_t>(), g->row_ptr, out_col.as<int32_t>(),
                                                        out_val.as<__half>(), g->col, (__half *)g->val, g->degree,
                                                        flag.as<int32_t>(), s2, s4);
         check_launch("k_copy_rows");

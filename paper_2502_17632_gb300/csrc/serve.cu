@@ -110,6 +110,7 @@ void gift_server::run(Request &r, cudaStream_t st) {
     gift_build_opts bo;
     gift_build_opts_default(&bo);
     bo.weight_dtype = r.weight_dtype;
+    bo.implicit_min_pins = opts.implicit_min_pins;
     gift_graph *g = nullptr;
     build_graph_impl(ctx, &nl, &bo, &g, st);
     std::unique_ptr<gift_graph, void (*)(gift_graph *)> own(g, [](gift_graph *p) {
@@ -206,6 +207,8 @@ gift_status gift_serve_create(const gift_serve_opts *opts, gift_server **out) {
                          o.weight_dtype == GIFT_WEIGHT_F16,
                      "gift_serve_create: unknown weight_dtype");
         GIFT_REQUIRE(o.hbm_budget_bytes >= 0, "gift_serve_create: negative budget");
+        GIFT_REQUIRE(o.implicit_min_pins == 0 || o.implicit_min_pins >= 2,
+                     "gift_serve_create: implicit_min_pins is 0 or at least 2");
         for (int r : o.reserved) GIFT_REQUIRE(r == 0, "gift_serve_create: reserved fields must be zero");
         GIFT_REQUIRE(o.spec.num_terms >= 1 && o.spec.num_terms <= GIFT_MAX_TERMS,
                      "gift_serve_create: num_terms out of range");
@@ -265,11 +268,12 @@ gift_status gift_serve_submit(gift_server *srv, const gift_netlist *nl, const fl
         r->S = S;
         r->weight_dtype = wd;
         GIFT_REQUIRE(nl->net_ptr[0] == 0, "gift_serve_submit: net_ptr[0] must be 0");
-        int64_t R = 0;
+        int64_t R = 0;  // expanded pairs (implicit nets add none)
+        const int64_t imin = srv->opts.implicit_min_pins;
         for (int32_t e = 0; e < nl->num_nets; ++e) {
             const int64_t m = nl->net_ptr[e + 1] - nl->net_ptr[e];
             GIFT_REQUIRE(m >= 0, "gift_serve_submit: net_ptr must be non-decreasing");
-            if (m >= 2) R += m * (m - 1);
+            if (m >= 2 && (imin == 0 || m < imin)) R += m * (m - 1);
         }
         const int64_t P = nl->net_ptr[nl->num_nets];
         r->net_ptr.assign(nl->net_ptr, nl->net_ptr + nl->num_nets + 1);

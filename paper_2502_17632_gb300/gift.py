@@ -66,7 +66,7 @@ class gift_kernel_stat(C.Structure):
 class gift_serve_opts(C.Structure):
     _fields_ = [("device", C.c_int32), ("max_slots", C.c_int32), ("hbm_budget_bytes", C.c_int64),
                 ("weight_dtype", C.c_int32), ("compute_hpwl", C.c_int32), ("spec", gift_filter_spec),
-                ("reserved", C.c_int32 * 8)]
+                ("implicit_min_pins", C.c_int32), ("reserved", C.c_int32 * 7)]
 
 
 class gift_req_stats(C.Structure):

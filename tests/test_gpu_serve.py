@@ -41,9 +41,10 @@ def mix(num=12, seed=11):
     return out
 
 
-def alone(ctx, nl, g, wd):
+def alone(ctx, nl, g, wd, cut=0):
     dev = lambda a: torch.from_numpy(np.ascontiguousarray(a)).cuda()  # noqa: E731
-    h = gift.gift_build_graph(ctx, nl.num_cells, dev(nl.net_ptr), dev(nl.pin_cell), dev(nl.is_fixed), gift.WEIGHT[wd])
+    h = gift.gift_build_graph(ctx, nl.num_cells, dev(nl.net_ptr), dev(nl.pin_cell), dev(nl.is_fixed), gift.WEIGHT[wd],
+                              implicit_min_pins=cut)
     try:
         gi = dev(g)
         go = torch.empty_like(gi)
@@ -167,3 +168,22 @@ def test_destroy_with_requests_pending(requests):
     srv = gift.gift_serve_create(max_slots=1)
     submit_all(srv, requests)  # most are still waiting when the server stops
     gift.gift_serve_destroy(srv)  # cancels the waiting ones, lets the running one finish
+
+
+def test_implicit_cliques_in_the_mix(requests):
+    """Requests built with implicit cliques (nets of 6+ pins) give the same
+    results as the same builds alone."""
+    ctx = gift.gift_ctx_create(0)
+    try:
+        ref = [alone(ctx, nl, g, wd, cut=6) for nl, g, wd in requests[:6]]
+    finally:
+        gift.gift_ctx_destroy(ctx)
+    srv = gift.gift_serve_create(max_slots=3, implicit_min_pins=6)
+    try:
+        tickets = submit_all(srv, requests[:6])
+        got = [gift.gift_serve_wait(srv, t, nl.num_cells, g.shape[1]) for t, (nl, g, _) in zip(tickets, requests[:6])]
+    finally:
+        gift.gift_serve_destroy(srv)
+    for (out, hp, _), (out_a, hp_a) in zip(got, ref):
+        np.testing.assert_array_equal(out, out_a)
+        np.testing.assert_array_equal(hp, hp_a)
