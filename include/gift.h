@@ -257,6 +257,17 @@ GIFT_API gift_status gift_hpwl(gift_ctx *ctx, const gift_graph *graph, const flo
                       double *out, int32_t mem, void *stream);
 
 
+/* The whole path in one call from host memory: builds the graph of `netlist`
+ * (host arrays; opts may be NULL), filters g_in ([num_cells][num_signals][2],
+ * host) with spec (NULL: the paper's filter) into g_out (host) and writes
+ * the HPWL of every filtered signal to hpwl (host, [num_signals], may be
+ * NULL).  The signal's upload overlaps the graph build (a side stream of the
+ * context); everything else runs on `stream`, which is synchronised on
+ * return.  Results equal gift_build_graph + gift_filter + gift_hpwl. */
+GIFT_API gift_status gift_run(gift_ctx *ctx, const gift_netlist *netlist, const gift_build_opts *opts,
+                              const gift_filter_spec *spec, const float *g_in, int32_t num_signals, float *g_out,
+                              double *hpwl, void *stream);
+
 /* ---------------------------------------------------------------------------
  * Exact Tikhonov smoothing, the filter GiFt approximates (Sec. 3.2.2): the
  * minimiser of ||g - g'||^2 + lambda tr(g'^T L~ g') is g' = (I + lambda L~)^-1 g

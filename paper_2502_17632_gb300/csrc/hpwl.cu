@@ -24,9 +24,32 @@ __device__ __forceinline__ void grow(Box &b, float2 p) {
     b.yhi = fmaxf(b.yhi, p.y);
 }
 
-__device__ __forceinline__ double extent(const Box &b) {
-    return ((double)b.xhi - (double)b.xlo) + ((double)b.yhi - (double)b.ylo);
+// Float-float numbers (hi + lo, |lo| <= ulp(hi) / 2): FP32 arithmetic with
+// about 48 significant bits.  Extents are exact in this form (Knuth's
+// TwoSum of the FP32 bounds), and a lane adds its nets' extents with a
+// relative error near 2^-47 per addition; lanes convert to FP64 once.
+struct FF {
+    float hi, lo;
+};
+
+__device__ __forceinline__ FF two_sum(float a, float b) {
+    const float s = __fadd_rn(a, b);
+    const float bb = __fsub_rn(s, a);
+    const float e = __fadd_rn(__fsub_rn(a, __fsub_rn(s, bb)), __fsub_rn(b, bb));
+    return FF{s, e};
 }
+
+__device__ __forceinline__ FF ff_add(FF x, FF y) {
+    FF s = two_sum(x.hi, y.hi);
+    const float e = __fadd_rn(s.lo, __fadd_rn(x.lo, y.lo));
+    const float hi = __fadd_rn(s.hi, e);
+    return FF{hi, __fsub_rn(e, __fsub_rn(hi, s.hi))};
+}
+
+// (xhi - xlo) + (yhi - ylo), the two differences exact
+__device__ __forceinline__ FF extent_ff(const Box &b) { return ff_add(two_sum(b.xhi, -b.xlo), two_sum(b.yhi, -b.ylo)); }
+
+__device__ __forceinline__ double ff_double(FF x) { return (double)x.hi + (double)x.lo; }
 
 // grid.y = pass over signals [kSC * y, kSC * y + kSC).  Each lane owns one net
 // of its warp's 32 (nets of up to 32 pins) and reads each pin's locations for
@@ -44,9 +67,9 @@ k_hpwl(int32_t E, int32_t S, const int64_t *__restrict__ net_ptr, const int32_t 
     const int lane = threadIdx.x & 31, wid = threadIdx.x >> 5;
     const int64_t warp = (blockIdx.x * (int64_t)blockDim.x + threadIdx.x) >> 5;
     const int64_t nwarps = ((int64_t)gridDim.x * blockDim.x) >> 5;
-    double sum[kSC];
+    FF sum[kSC];
 #pragma unroll
-    for (int q = 0; q < kSC; ++q) sum[q] = 0.0;
+    for (int q = 0; q < kSC; ++q) sum[q] = FF{0.f, 0.f};
     const int64_t hi = chunk_lo ? chunk_lo[blockIdx.x + 1] : E;
     const int64_t start = chunk_lo ? chunk_lo[blockIdx.x] + (int64_t)wid * 32 : warp * 32;
     const int64_t step = chunk_lo ? (int64_t)blockDim.x : nwarps * 32;
@@ -72,7 +95,7 @@ k_hpwl(int32_t E, int32_t S, const int64_t *__restrict__ net_ptr, const int32_t 
                     if (q < ns) grow(bx[q], __ldg(r + q));
             }
 #pragma unroll
-            for (int q = 0; q < kSC; ++q) sum[q] += extent(bx[q]);
+            for (int q = 0; q < kSC; ++q) sum[q] = ff_add(sum[q], extent_ff(bx[q]));
         }
         unsigned big = __ballot_sync(0xffffffffu, m > 32);
         while (big) {
@@ -88,13 +111,13 @@ k_hpwl(int32_t E, int32_t S, const int64_t *__restrict__ net_ptr, const int32_t 
                     bx.ylo = fminf(bx.ylo, __shfl_xor_sync(0xffffffffu, bx.ylo, o));
                     bx.yhi = fmaxf(bx.yhi, __shfl_xor_sync(0xffffffffu, bx.yhi, o));
                 }
-                if (lane == src) sum[q] += extent(bx);
+                if (lane == src) sum[q] = ff_add(sum[q], extent_ff(bx));
             }
         }
     }
 #pragma unroll
     for (int q = 0; q < kSC; ++q) {
-        double v = sum[q];
+        double v = ff_double(sum[q]);
         for (int o = 16; o; o >>= 1) v += __shfl_xor_sync(0xffffffffu, v, o);
         if (lane == 0) red[q][wid] = v;
     }
@@ -124,7 +147,7 @@ k_hpwl_groups(int32_t E, int32_t S, const int64_t *__restrict__ net_ptr, const i
     const int qq = on ? s0 / 2 + q : 0;
     const int64_t warp = (blockIdx.x * (int64_t)blockDim.x + threadIdx.x) >> 5;
     const int64_t nwarps = ((int64_t)gridDim.x * blockDim.x) >> 5;
-    double sum0 = 0.0, sum1 = 0.0;
+    FF sum0{0.f, 0.f}, sum1{0.f, 0.f};
     const int64_t hi = chunk_lo ? chunk_lo[blockIdx.x + 1] : E;
     const int64_t start = chunk_lo ? chunk_lo[blockIdx.x] + (int64_t)wid * NPW : warp * NPW;
     const int64_t step = chunk_lo ? (int64_t)(blockDim.x / 32) * NPW : nwarps * NPW;
@@ -152,8 +175,8 @@ k_hpwl_groups(int32_t E, int32_t S, const int64_t *__restrict__ net_ptr, const i
                         grow(b1, make_float2(v[u].z, v[u].w));
                     }
             }
-            sum0 += extent(b0);
-            sum1 += extent(b1);
+            sum0 = ff_add(sum0, extent_ff(b0));
+            sum1 = ff_add(sum1, extent_ff(b1));
         }
         unsigned big = __ballot_sync(0xffffffffu, m > 32 && q == 0);
         while (big) {
@@ -179,19 +202,20 @@ k_hpwl_groups(int32_t E, int32_t S, const int64_t *__restrict__ net_ptr, const i
                     c1.yhi = fmaxf(c1.yhi, __shfl_xor_sync(0xffffffffu, c1.yhi, o));
                 }
                 if (lane == pq) {  // group 0, lane q == pq holds this signal pair
-                    sum0 += extent(c0);
-                    sum1 += extent(c1);
+                    sum0 = ff_add(sum0, extent_ff(c0));
+                    sum1 = ff_add(sum1, extent_ff(c1));
                 }
             }
         }
     }
+    double d0 = ff_double(sum0), d1 = ff_double(sum1);
     for (int o = GH; o < 32; o <<= 1) {
-        sum0 += __shfl_xor_sync(0xffffffffu, sum0, o);
-        sum1 += __shfl_xor_sync(0xffffffffu, sum1, o);
+        d0 += __shfl_xor_sync(0xffffffffu, d0, o);
+        d1 += __shfl_xor_sync(0xffffffffu, d1, o);
     }
     if (gi == 0) {
-        red[wid][2 * q] = sum0;
-        red[wid][2 * q + 1] = sum1;
+        red[wid][2 * q] = d0;
+        red[wid][2 * q + 1] = d1;
     }
     __syncthreads();
     const int nsig = min(2 * GH, S - s0);

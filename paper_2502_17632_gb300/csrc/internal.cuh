@@ -111,6 +111,9 @@ struct gift_ctx {
     int32_t *dev_error = nullptr;
     // wtab[m] = 2/m in FP64 for m in [2, kWeightTable] (0 below), filled on the host
     double *wtab = nullptr;
+    // side stream for uploads that overlap work on the caller's stream (gift_run)
+    std::mutex side_mu;
+    cudaStream_t side = nullptr;
 };
 
 namespace gift {

@@ -1,0 +1,76 @@
+// run.cu -- the whole path in one call from host memory (gift_run): the
+// signal's upload runs on a side stream while the graph is built on the
+// caller's stream; the filter waits for it, HPWL follows on the device, and
+// the result comes back in one copy.
+#include <cstring>
+
+#include "internal.cuh"
+
+using namespace gift;
+
+extern "C" gift_status gift_run(gift_ctx *ctx, const gift_netlist *netlist, const gift_build_opts *opts,
+                                const gift_filter_spec *spec, const float *g_in, int32_t num_signals, float *g_out,
+                                double *hpwl, void *stream) {
+    return guarded([&] {
+        GIFT_REQUIRE(ctx && netlist, "gift_run: NULL context or netlist");
+        GIFT_REQUIRE(netlist->mem == GIFT_MEM_HOST, "gift_run: the netlist must be in host memory");
+        GIFT_REQUIRE(g_in && g_out, "gift_run: NULL signal pointer");
+        GIFT_REQUIRE(num_signals >= 1, "gift_run: num_signals must be >= 1");
+        GIFT_REQUIRE(netlist->num_cells > 0, "gift_run: num_cells must be > 0");
+        GIFT_CUDA(cudaSetDevice(ctx->device));
+        cudaStream_t st = static_cast<cudaStream_t>(stream);
+        gift_filter_spec def;
+        if (!spec) {
+            gift_filter_spec_default(&def);
+            spec = &def;
+        }
+        {
+            std::lock_guard<std::mutex> lk(ctx->side_mu);
+            if (!ctx->side) GIFT_CUDA(cudaStreamCreateWithFlags(&ctx->side, cudaStreamNonBlocking));
+        }
+        const size_t bytes = sizeof(float) * (size_t)netlist->num_cells * 2 * num_signals;
+        DevBuf din(ctx, bytes, st), dout(ctx, bytes, st);
+        cudaEvent_t ready = nullptr, loaded = nullptr;
+        GIFT_CUDA(cudaEventCreateWithFlags(&ready, cudaEventDisableTiming));
+        struct Events {
+            cudaEvent_t &a, &b;
+            ~Events() {
+                if (a) cudaEventDestroy(a);
+                if (b) cudaEventDestroy(b);
+            }
+        } own{ready, loaded};
+        GIFT_CUDA(cudaEventCreateWithFlags(&loaded, cudaEventDisableTiming));
+        // upload g on the side stream once its buffer exists, overlapping the build
+        GIFT_CUDA(cudaEventRecord(ready, st));
+        {
+            std::lock_guard<std::mutex> lk(ctx->side_mu);
+            GIFT_CUDA(cudaStreamWaitEvent(ctx->side, ready, 0));
+            GIFT_CUDA(cudaMemcpyAsync(din.p, g_in, bytes, cudaMemcpyHostToDevice, ctx->side));
+            GIFT_CUDA(cudaEventRecord(loaded, ctx->side));
+        }
+        // on every way out (an invalid netlist throws from the build), the
+        // stream waits for the upload before din is freed on it
+        struct WaitUpload {
+            cudaStream_t st;
+            cudaEvent_t ev;
+            ~WaitUpload() { cudaStreamWaitEvent(st, ev, 0); }
+        } wait_upload{st, loaded};
+        gift_graph *g = nullptr;
+        build_graph_impl(ctx, netlist, opts, &g, st);
+        struct Graph {
+            gift_graph *g;
+            cudaStream_t st;
+            ~Graph() {
+                release_graph(g, st);
+                cudaStreamSynchronize(st);
+                delete g;
+            }
+        } gown{g, st};
+        GIFT_CUDA(cudaStreamWaitEvent(st, loaded, 0));
+        filter_impl(ctx, g, spec, din.as<float>(), num_signals, dout.as<float>(), GIFT_MEM_DEVICE, st);
+        if (hpwl) hpwl_impl(ctx, g, dout.as<float>(), num_signals, hpwl, GIFT_MEM_DEVICE, st);
+        GIFT_CUDA(cudaMemcpyAsync(g_out, dout.p, bytes, cudaMemcpyDeviceToHost, st));
+        GIFT_CUDA(cudaStreamSynchronize(st));
+        check_device_error(ctx);
+    });
+}

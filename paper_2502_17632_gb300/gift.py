@@ -125,6 +125,7 @@ def load(build_if_missing: bool = True):
         "gift_exec_launch": (I32, [P, P]),
         "gift_exec_free": (None, [P]),
         "gift_tikhonov": (I32, [P, P, C.c_float, C.c_float, I32, I32, P, I32, P, P, I32, P]),
+        "gift_run": (I32, [P, P, P, P, P, I32, P, P, P]),
         "gift_density": (I32, [P, P, I32, I32, P, P, C.c_float, C.c_float, P, I32, I32, C.c_double, P, P, I32, P]),
         "gift_serve_opts_default": (None, [P]),
         "gift_serve_create": (I32, [P, C.POINTER(P)]),
@@ -466,3 +467,24 @@ def gift_density(ctx, xy, die=(0.0, 0.0, 1000.0, 1000.0), bins=(32, 32), target:
     _check(load().gift_density(ctx, p, N, S, pw, ph, unit[0], unit[1], d.ctypes.data, bins[0], bins[1], target,
                                out.ctypes.data, ov.ctypes.data, mem, _stream(stream)))
     return out, ov
+
+
+# ------------------------------------------------------------------ whole path
+def gift_run(ctx, num_cells: int, net_ptr, pin_cell, is_fixed, g_in, g_out, spec=None,
+             weight_dtype: int = GIFT_WEIGHT_F32, implicit_min_pins: int = 0, stream=None) -> np.ndarray:
+    """Build + filter + HPWL from host (numpy) arrays in one call; returns the HPWL per signal."""
+    net_ptr = np.ascontiguousarray(net_ptr, dtype=np.int64)
+    pin_cell = np.ascontiguousarray(pin_cell, dtype=np.int32)
+    fx = None if is_fixed is None else np.ascontiguousarray(is_fixed, dtype=np.uint8)
+    nl = gift_netlist(num_cells, len(net_ptr) - 1, net_ptr.ctypes.data, pin_cell.ctypes.data,
+                      None if fx is None else fx.ctypes.data, GIFT_MEM_HOST)
+    opts = gift_build_opts_default()
+    opts.weight_dtype = weight_dtype
+    opts.implicit_min_pins = implicit_min_pins
+    if not (isinstance(g_in, np.ndarray) and isinstance(g_out, np.ndarray)):
+        raise ValueError("gift_run takes host (numpy) signals")
+    S = g_in.shape[1]
+    hp = np.empty(S, dtype=np.float64)
+    _check(load().gift_run(ctx, C.byref(nl), C.byref(opts), None if spec is None else C.byref(spec),
+                           g_in.ctypes.data, S, g_out.ctypes.data, hp.ctypes.data, _stream(stream)))
+    return hp

@@ -158,3 +158,29 @@ def test_batch_rejects_pins_outside_their_netlist(ctx, batch, device):
     with pytest.raises(gift.GiftError) as e:
         gift.gift_build_batch(ctx, nets)
     assert e.value.status == gift.GIFT_ERR_INVALID
+
+
+def test_gift_run_equals_separate_calls(ctx, batch):
+    """gift_run (host netlist and signal, upload overlapping the build) gives
+    the same output and HPWL as build + filter + HPWL called one by one; an
+    invalid netlist is rejected and leaves the context usable."""
+    nl, g = batch[0]
+    out = np.empty_like(g)
+    hp = gift.gift_run(ctx, nl.num_cells, nl.net_ptr, nl.pin_cell, nl.is_fixed, g, out)
+    h = gift.gift_build_graph(ctx, nl.num_cells, nl.net_ptr, nl.pin_cell, nl.is_fixed)
+    try:
+        ref = np.empty_like(g)
+        gift.gift_filter(ctx, h, g, ref)
+        hp_ref = gift.gift_hpwl(ctx, h, ref)
+    finally:
+        gift.gift_graph_free(h)
+    np.testing.assert_array_equal(out, ref)
+    np.testing.assert_array_equal(hp, hp_ref)
+    bad = nl.pin_cell.copy()
+    bad[0] = nl.num_cells + 5
+    with pytest.raises(gift.GiftError) as e:
+        gift.gift_run(ctx, nl.num_cells, nl.net_ptr, bad, nl.is_fixed, g, out)
+    assert e.value.status == gift.GIFT_ERR_INVALID
+    hp2 = gift.gift_run(ctx, nl.num_cells, nl.net_ptr, nl.pin_cell, nl.is_fixed, g, out,
+                        implicit_min_pins=4, weight_dtype=gift.GIFT_WEIGHT_BF16)
+    assert np.all(np.isfinite(hp2)) and np.all(np.isfinite(out))
