@@ -52,6 +52,7 @@ def parse():
     p.add_argument("--no-implicit", action="store_true", help="skip the implicit-clique and high-fanout measurements")
     p.add_argument("--no-tikhonov", action="store_true", help="skip the Tikhonov measurement")
     p.add_argument("--no-density", action="store_true", help="skip the density measurement")
+    p.add_argument("--no-small", action="store_true", help="skip the small-netlist latency measurement")
     p.add_argument("--serve-requests", type=int, default=240)
     p.add_argument("--serve-rate", type=float, default=40.0, help="Poisson arrival rate, requests/s")
     p.add_argument("--capture", action="store_true",
@@ -513,6 +514,49 @@ def run_density(args, gift, ctx, stream, nl, d_np, d_pc, d_fx, d_g):
             "density_ms_8_signals": e0.elapsed_time(e1) / 5}
 
 
+# ----------------------------------------------------------------- small netlist latency
+def run_small(args, gift, ctx, stream):
+    """The plain 10k-cell netlist (one signal): everything fits in L2, so the
+    path is bound by launches and host round trips.  Latency of the
+    device-resident step, of gift_run from host memory, and of the filter
+    alone as a call and as one captured CUDA-graph launch."""
+    import torch
+    nl, g = synth.workload("plain-10k")
+    dev = lambda a: torch.from_numpy(np.ascontiguousarray(a)).cuda()  # noqa: E731
+    d_np, d_pc, d_fx, d_g = dev(nl.net_ptr), dev(nl.pin_cell), dev(nl.is_fixed), dev(g)
+    d_out = torch.empty_like(d_g)
+    reps = 50
+
+    def per_call_us(fn):  # latency: each call and its completion
+        for _ in range(5):
+            fn()
+        torch.cuda.synchronize()
+        t0 = time.perf_counter()
+        for _ in range(reps):
+            fn()
+            torch.cuda.synchronize()
+        return 1e6 * (time.perf_counter() - t0) / reps
+
+    def step():
+        h = gift.gift_build_graph(ctx, nl.num_cells, d_np, d_pc, d_fx, stream=stream)
+        gift.gift_filter(ctx, h, d_g, d_out, stream=stream)
+        gift.gift_hpwl(ctx, h, d_out, stream=stream)
+        gift.gift_graph_free_async(h, stream)
+
+    out_h = np.empty_like(g)
+    res = {"workload": f"plain-10k: {nl.num_cells} cells, {nl.num_nets} nets, 1 signal, FP32",
+           "step_us": per_call_us(step),
+           "gift_run_us": per_call_us(lambda: gift.gift_run(ctx, nl.num_cells, nl.net_ptr, nl.pin_cell, nl.is_fixed,
+                                                             g, out_h, stream=stream))}
+    h = gift.gift_build_graph(ctx, nl.num_cells, d_np, d_pc, d_fx, stream=stream)
+    res["filter_call_us"] = per_call_us(lambda: gift.gift_filter(ctx, h, d_g, d_out, stream=stream))
+    ex = gift.gift_filter_capture(ctx, h, d_g, d_out)
+    res["filter_graph_launch_us"] = per_call_us(lambda: gift.gift_exec_launch(ex, stream))
+    gift.gift_exec_free(ex)
+    gift.gift_graph_free(h)
+    return res
+
+
 # ----------------------------------------------------------------- NVTX ranges
 class Range:
     """NVTX push/pop range (lets an ncu capture select the launches inside)."""
@@ -724,6 +768,9 @@ def run_ours(args):
     fanout = None
     if rank == 0 and world == 1 and not args.no_implicit:
         fanout = run_high_fanout(args, gift, ctx, stream)
+    small = None
+    if rank == 0 and world == 1 and not args.no_small:
+        small = run_small(args, gift, ctx, stream)
     gift.gift_ctx_destroy(ctx)
     serving = None
     if rank == 0 and world == 1 and not args.no_serve:
@@ -741,7 +788,7 @@ def run_ours(args):
             "roofline": roofline, "cpu_baseline": cpu, "e2e": e2e, "gpu_launches": launches * world,
             "clocks": clocks, "breakdown": breakdown, "filter_only": filt, "precision": precision,
             "serving": serving, "batched": batched, "implicit_cliques": implicit, "high_fanout": fanout,
-            "tikhonov": tikh, "density": dens,
+            "tikhonov": tikh, "density": dens, "small": small,
         }
         print(json.dumps(line), flush=True)
     if world > 1:
