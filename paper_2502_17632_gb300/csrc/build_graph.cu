@@ -17,6 +17,7 @@
 //   compact  round each sum once to the storage type, write col/val, and
 //            d_i = sum_j A_ij in FP64 over the stored weights in column order.
 #include <algorithm>
+#include <utility>
 
 #include "internal.cuh"
 #include "scan.cuh"
@@ -248,169 +249,248 @@ __global__ void k_net_stored(int32_t E, const double *__restrict__ wnet, WT *__r
 // storage type; the unique count; and the degree d_i = sum_j A_ij in FP64
 // over the stored weights in column order (Sec. 2.1).
 
-constexpr int kGS = 8;          // lanes per row in the small tier
-constexpr int kSmallCap = 32;   // raw entries of a small row
-constexpr int kSmallThreads = 256;
-constexpr int kSmallGroups = kSmallThreads / kGS;
+constexpr int kLaneCap = 32;  // raw entries of a row in the lane tier
+constexpr int kLaneThreads = 128;
 
-// Small tier: a group of 8 lanes per row with at most kSmallCap raw entries;
-// the four rows of a warp advance in lockstep (every loop runs to the warp's
-// largest trip count, with per-row predicates) so their memory accesses are
-// issued together.  Keys (neighbour, net) are ranked in shared memory.
-// Longer rows are appended to `wlist` for the warp tier.
-template <typename WT>
-__global__ void __launch_bounds__(kSmallThreads)
-k_rows_small(int32_t N, const int64_t *__restrict__ inc_ptr, const int32_t *__restrict__ inc_net,
-             const int64_t *__restrict__ net_ptr, const int32_t *__restrict__ pin_cell,
-             const double *__restrict__ wnet, const WT *__restrict__ wst, const int64_t *__restrict__ raw_ptr,
-             int32_t *__restrict__ out_col, WT *__restrict__ out_val, int32_t *__restrict__ ucount,
-             double *__restrict__ degree, int32_t *__restrict__ wlist, int32_t *__restrict__ wcount) {
-    __shared__ uint64_t keys_all[kSmallGroups][kSmallCap];   // later reused for the stored weights
-    __shared__ uint64_t sorted_all[kSmallGroups][kSmallCap];
-    __shared__ int32_t ofs_all[kSmallGroups][kSmallCap + 1];
-    __shared__ int32_t inet_all[kSmallGroups][kSmallCap];
-    __shared__ int64_t ibase_all[kSmallGroups][kSmallCap];
-    __shared__ int32_t cnt_all[kSmallGroups];
+// Batcher's odd-even merge sort, ascending, on R registers (R a power of two).
+// The comparator list is generated at compile time and expanded into
+// straight-line code, so the array stays in registers and each comparator is
+// a min and a max.
+template <typename K>
+__device__ __forceinline__ void cmp_swap(K &a, K &b) {
+    const K lo = a < b ? a : b, hi = a < b ? b : a;
+    a = lo;
+    b = hi;
+}
+
+struct CmpPair {
+    int a, b;
+};
+
+template <int R>
+struct OddEvenNet {
+    template <class F>
+    static constexpr void visit(F &&f) {
+        for (int p = 1; p < R; p *= 2)
+            for (int s = p; s >= 1; s /= 2)
+                for (int j = s % p; j + s < R; j += 2 * s)
+                    for (int i = 0; i < s && i + j + s < R; ++i)
+                        if ((i + j) / (2 * p) == (i + j + s) / (2 * p)) f(i + j, i + j + s);
+    }
+    static constexpr int count() {
+        int c = 0;
+        visit([&](int, int) { ++c; });
+        return c;
+    }
+    static constexpr int kCount = count();
+    struct Table {
+        CmpPair v[kCount];
+    };
+    static constexpr Table table() {
+        Table t{};
+        int c = 0;
+        visit([&](int a, int b) { t.v[c++] = CmpPair{a, b}; });
+        return t;
+    }
+    static constexpr Table kTable = table();
+};
+
+template <int A, int B, int R, typename K>
+__device__ __forceinline__ void cmp_swap_at(K (&k)[R]) {
+    cmp_swap(k[A], k[B]);
+}
+
+template <int R, typename K, int... Is>
+__device__ __forceinline__ void apply_net(K (&k)[R], std::integer_sequence<int, Is...>) {
+    (cmp_swap_at<OddEvenNet<R>::kTable.v[Is].a, OddEvenNet<R>::kTable.v[Is].b>(k), ...);
+}
+
+template <int R, typename K>
+__device__ __forceinline__ void oddeven_merge_sort(K (&k)[R]) {
+    apply_net<R>(k, std::make_integer_sequence<int, OddEvenNet<R>::kCount>{});
+}
+
+// The row's incidences (net ids) in increasing order, into sinc[.][tid].
+template <int R, int T>
+__device__ __forceinline__ void lane_sort_incidences(const int32_t *__restrict__ inc, int ninc, int32_t (*sinc)[T],
+                                                     int tid) {
+    int32_t e[R];
+#pragma unroll
+    for (int i = 0; i < R; ++i) e[i] = i < ninc ? inc[i] : INT32_MAX;
+    oddeven_merge_sort<R>(e);
+#pragma unroll
+    for (int i = 0; i < R; ++i)
+        if (i < ninc) sinc[i][tid] = e[i];
+}
+
+// The row's n keys (neighbour << 5 | incidence), sorted in place in skey[.][tid].
+template <int R, typename K, int T>
+__device__ __forceinline__ void lane_sort_keys(int n, K (*skey)[T], int tid) {
+    K k[R];
+#pragma unroll
+    for (int i = 0; i < R; ++i) k[i] = i < n ? skey[i][tid] : ~K(0);
+    oddeven_merge_sort<R>(k);
+#pragma unroll
+    for (int i = 0; i < R; ++i)
+        if (i < n) skey[i][tid] = k[i];
+}
+
+// A stored weight w in [2^-11, 2^19) as an integer count of 2^-34 (exact:
+// a binary32 value there is m * 2^(e-150) with a 24-bit m and e >= 116).
+__device__ __forceinline__ unsigned long long units34(float w) {
+    const unsigned b = __float_as_uint(w);
+    return (unsigned long long)((b & 0x7fffffu) | 0x800000u) << ((int)(b >> 23) - 116);
+}
+
+// Lane tier: one thread per row with 1..kLaneCap raw entries.  The row's
+// incidences are sorted by net id (a sorting network in registers); every
+// pin of those nets other than the row's own cell gives a key
+// (neighbour << 5 | incidence index), so sorting the keys orders columns and,
+// within a column, nets.  Pins are fetched four incidences at a time, the
+// first four pins of each at once, so a thread has up to 16 loads in flight.
+// A row here has M <= kLaneCap + 1 for each of its nets, so weights come
+// from a per-block table over M: a column reached through one net takes the
+// stored 2/M, several nets sum their FP64 2/M in net order and round once.
+// The degree: every stored weight in [2^-11, 2^19) and the row's sum below
+// 2^19 make each partial FP64 sum a multiple of 2^-34 below 2^53 units, so
+// the integer sum of units equals the column-order FP64 sum; otherwise the
+// row adds its stored weights in FP64 in column order.  Rows with more raw
+// entries go to `wlist` for the warp tier.  K is uint32 for at most 2^27
+// cells, else uint64 (with half the threads per block).
+template <typename K>
+__host__ __device__ constexpr int lane_threads() {
+    return sizeof(K) == 4 ? kLaneThreads : kLaneThreads / 2;
+}
+
+template <typename WT, typename K>
+__global__ void __launch_bounds__(lane_threads<K>(), 6)
+k_rows_lane(int32_t N, const int64_t *__restrict__ inc_ptr, const int32_t *__restrict__ inc_net,
+            const int64_t *__restrict__ net_ptr, const int32_t *__restrict__ pin_cell,
+            const double *__restrict__ wtab, const int64_t *__restrict__ raw_ptr, int32_t *__restrict__ out_col,
+            WT *__restrict__ out_val, int32_t *__restrict__ ucount, double *__restrict__ degree,
+            int32_t *__restrict__ wlist, int32_t *__restrict__ wcount) {
+    constexpr int kMaxM = kLaneCap + 1;
+    constexpr int T = lane_threads<K>();
+    __shared__ K skey[kLaneCap][T];
+    __shared__ int32_t sinc[kLaneCap][T];  // net id, then the net's pin count M
+    __shared__ double dtab[kMaxM + 1];                // 2/M in FP64 (weight rule after Eq. 4)
+    __shared__ WT stab[kMaxM + 1];                    // 2/M as stored
     const unsigned full = 0xffffffffu;
-    const int g = threadIdx.x / kGS, gl = threadIdx.x % kGS;
-    uint64_t *keys = keys_all[g];
-    uint64_t *srt = sorted_all[g];
-    int32_t *ofs = ofs_all[g];
-    double *rv = reinterpret_cast<double *>(keys_all[g]);
-    constexpr int RPW = 32 / kGS;  // rows per warp
-    const int64_t warp = (blockIdx.x * (int64_t)blockDim.x + threadIdx.x) >> 5;
-    const int64_t nwarps = ((int64_t)gridDim.x * blockDim.x) >> 5;
-    const int gw = (threadIdx.x & 31) / kGS;  // group within the warp
-
-    for (int64_t base = warp * RPW; base < N; base += nwarps * RPW) {  // warp-uniform
-        const int64_t row = base + gw;
-        int64_t rb = 0, rawlen = 0, ib = 0;
+    const int tid = threadIdx.x, lane = tid & 31;
+    for (int m = tid; m <= kMaxM; m += T) {
+        const double w = m >= 2 ? wtab[m] : 0.0;
+        dtab[m] = w;
+        stab[m] = Store<WT>::put(w);
+    }
+    __syncthreads();
+    for (int64_t base = blockIdx.x * (int64_t)T; base < N; base += (int64_t)gridDim.x * T) {
+        const int64_t row = base + tid;  // the loop is block-uniform
+        int64_t rb = 0, raw = 0, ib = 0;
         int ninc = 0;
         if (row < N) {
             rb = raw_ptr[row];
-            rawlen = raw_ptr[row + 1] - rb;
+            raw = raw_ptr[row + 1] - rb;
             ib = inc_ptr[row];
             ninc = (int)(inc_ptr[row + 1] - ib);
         }
-        const bool small = row < N && rawlen > 0 && rawlen <= kSmallCap;
-        if (gl == 0 && row < N) {
-            if (rawlen > kSmallCap) wlist[atomicAdd(wcount, 1)] = (int32_t)row;
-            if (rawlen == 0) {
-                ucount[row] = 0;
-                degree[row] = 0.0;
-            }
+        const bool lane_row = row < N && raw > 0 && raw <= kLaneCap;
+        const bool longer = row < N && raw > kLaneCap;
+        const unsigned lm = __ballot_sync(full, longer);
+        if (lm) {
+            const int leader = __ffs(lm) - 1;
+            int at = 0;
+            if (lane == leader) at = atomicAdd(wcount, __popc(lm));
+            at = __shfl_sync(full, at, leader);
+            if (longer) wlist[at + __popc(lm & ((1u << lane) - 1u))] = (int32_t)row;
         }
-        if (!small) ninc = 0;  // ninc <= rawlen: every incidence has M >= 2
-        const int max_ninc = (int)__reduce_max_sync(full, (unsigned)ninc);
-        for (int t0 = 0; t0 < max_ninc; t0 += kGS) {
-            const int t = t0 + gl;
-            if (t < ninc) {
-                const int32_t e = inc_net[ib + t];
-                const int64_t nb = net_ptr[e];
-                inet_all[g][t] = e;
-                ibase_all[g][t] = nb;
-                ofs[t] = (int32_t)(net_ptr[e + 1] - nb);
-            }
+        if (row < N && raw == 0) {
+            ucount[row] = 0;
+            degree[row] = 0.0;
         }
-        __syncwarp();
-        if (gl == 0) {
-            int acc = 0;
-            for (int t = 0; t < ninc; ++t) {
-                const int m = ofs[t];
-                ofs[t] = acc;
-                acc += m;
-            }
-            ofs[ninc] = acc;
-            cnt_all[g] = 0;
-        }
-        __syncwarp();
-        const int total = small ? ofs[ninc] : 0;
-        const int max_total = (int)__reduce_max_sync(full, (unsigned)total);
-        for (int f0 = 0; f0 < max_total; f0 += kGS) {
-            const int f = f0 + gl;
-            if (f < total) {
-                int lo = 0, hi = ninc - 1;  // last incidence whose offset <= f
-                while (lo < hi) {
-                    const int mid = (lo + hi + 1) >> 1;
-                    if (ofs[mid] <= f) lo = mid;
-                    else hi = mid - 1;
-                }
-                const int32_t q = pin_cell[ibase_all[g][lo] + (f - ofs[lo])];
-                if (q != (int32_t)row) keys[atomicAdd(&cnt_all[g], 1)] = make_key(q, inet_all[g][lo]);
-            }
-        }
-        __syncwarp();
-        const int n = small ? cnt_all[g] : 0;
-        const int max_n = (int)__reduce_max_sync(full, (unsigned)n);
-        for (int i0 = 0; i0 < max_n; i0 += kGS) {  // rank sort; equal keys keep their slots' order
-            const int i = i0 + gl;
-            if (i < n) {
-                const uint64_t k = keys[i];
-                int rank = 0;
-                for (int j = 0; j < n; ++j) {
-                    const uint64_t kj = keys[j];
-                    rank += (kj < k) || (kj == k && j < i);
-                }
-                srt[rank] = k;
-            }
-        }
-        __syncwarp();
-        // Unique columns: run heads found by ballot (u = heads before).  A run
-        // of several nets sums their weights in FP64 in net order and rounds
-        // once; a run of one net takes the net's stored weight.  The degree:
-        // when every stored weight is >= 2^-11 and the row's sum < 2^19, all
-        // partial sums are multiples of 2^-34 below 2^53 units, so FP64 adds
-        // them exactly in any order -- summed here as integers across the
-        // group; otherwise one lane adds them in column order.
-        const unsigned gmask = ((1u << kGS) - 1u) << (gw * kGS);
-        int ubase = 0;
-        long long qsum = 0;
-        bool exact = true;
-        for (int i0 = 0; i0 < max_n; i0 += kGS) {  // warp-uniform
-            const int i = i0 + gl;
-            bool head = false;
-            int32_t c = 0;
-            if (i < n) {
-                c = key_cell(srt[i]);
-                head = i == 0 || key_cell(srt[i - 1]) != c;
-            }
-            const unsigned gh = (__ballot_sync(full, head) & gmask) >> (gw * kGS);
-            if (head) {
-                const int u = ubase + __popc(gh & ((1u << gl) - 1u));
-                int r = i + 1;
-                while (r < n && key_cell(srt[r]) == c) ++r;
-                WT w;
-                if (r == i + 1) {
-                    w = wst[key_net(srt[i])];
-                } else {
-                    double sum = 0.0;
-                    for (int t = i; t < r; ++t) sum += wnet[key_net(srt[t])];
-                    w = Store<WT>::put(sum);
-                }
-                out_col[rb + u] = c;
-                out_val[rb + u] = w;
-                const float wf = Store<WT>::getf(w);
-                rv[u] = (double)wf;
-                if (wf >= 0x1p-11f && wf < 0x1p19f) qsum += (long long)(wf * 0x1p34f);
-                else exact = false;
-            }
-            ubase += __popc(gh);
-        }
+        if (!lane_row) ninc = 0;  // ninc <= raw: every incidence has M >= 2
+        const int max_inc = (int)__reduce_max_sync(full, (unsigned)ninc);
+        if (max_inc == 0) continue;
+        if (max_inc <= 8) lane_sort_incidences<8>(inc_net + ib, ninc, sinc, tid);
+        else if (max_inc <= 16) lane_sort_incidences<16>(inc_net + ib, ninc, sinc, tid);
+        else lane_sort_incidences<32>(inc_net + ib, ninc, sinc, tid);
+
+        int n = 0;
+        const int32_t self = (int32_t)row;
+        for (int c = 0; c < max_inc; c += 4) {  // warp-uniform
+            int64_t nb[4];
+            int m[4];
 #pragma unroll
-        for (int o = 1; o < kGS; o <<= 1) qsum += __shfl_xor_sync(full, qsum, o);
-        const bool gexact = (__ballot_sync(full, !exact) & gmask) == 0;
-        __syncwarp();
-        if (gl == 0 && small) {
-            double d = 0.0;
-            if (gexact && qsum < (1ll << 53)) {
-                d = (double)qsum * 0x1p-34;
-            } else {
-                for (int u = 0; u < ubase; ++u) d += rv[u];
+            for (int j = 0; j < 4; ++j) {
+                nb[j] = 0;
+                m[j] = 0;
+                if (c + j < ninc) {
+                    const int32_t e = sinc[c + j][tid];
+                    nb[j] = net_ptr[e];
+                    m[j] = (int)(net_ptr[e + 1] - nb[j]);
+                }
             }
-            ucount[row] = ubase;
-            degree[row] = d;
+            int32_t q[4][4];
+#pragma unroll
+            for (int j = 0; j < 4; ++j)
+#pragma unroll
+                for (int k = 0; k < 4; ++k) q[j][k] = k < m[j] ? pin_cell[nb[j] + k] : self;
+#pragma unroll
+            for (int j = 0; j < 4; ++j) {
+                if (c + j < ninc) sinc[c + j][tid] = m[j];
+#pragma unroll
+                for (int k = 0; k < 4; ++k)
+                    if (q[j][k] != self && n < kLaneCap) skey[n++][tid] = ((K)(uint32_t)q[j][k] << 5) | (K)(c + j);
+                for (int k0 = 4; k0 < m[j]; k0 += 4) {  // nets of more than four pins
+                    int32_t r[4];
+#pragma unroll
+                    for (int k = 0; k < 4; ++k) r[k] = k0 + k < m[j] ? pin_cell[nb[j] + k0 + k] : self;
+#pragma unroll
+                    for (int k = 0; k < 4; ++k)
+                        if (r[k] != self && n < kLaneCap) skey[n++][tid] = ((K)(uint32_t)r[k] << 5) | (K)(c + j);
+                }
+            }
         }
-        __syncwarp();
+        const int max_n = (int)__reduce_max_sync(full, (unsigned)n);
+        if (max_n <= 8) lane_sort_keys<8>(n, skey, tid);
+        else if (max_n <= 16) lane_sort_keys<16>(n, skey, tid);
+        else lane_sort_keys<32>(n, skey, tid);
+        if (!lane_row) continue;
+
+        int u = 0;
+        unsigned long long units = 0;
+        bool exact = true;
+        for (int i = 0; i < n;) {
+            const K ki = skey[i][tid];
+            const int32_t c = (int32_t)(ki >> 5);
+            const int mi = min(sinc[(int)(ki & 31)][tid], kMaxM);
+            int r = i + 1;
+            WT w;
+            if (r < n && (int32_t)(skey[r][tid] >> 5) == c) {
+                double sum = dtab[mi];
+                do {
+                    sum = __dadd_rn(sum, dtab[min(sinc[(int)(skey[r][tid] & 31)][tid], kMaxM)]);
+                    ++r;
+                } while (r < n && (int32_t)(skey[r][tid] >> 5) == c);
+                w = Store<WT>::put(sum);
+            } else {
+                w = stab[mi];
+            }
+            out_col[rb + u] = c;
+            out_val[rb + u] = w;
+            const float wf = Store<WT>::getf(w);
+            if (wf >= 0x1p-11f && wf < 0x1p19f) units += units34(wf);
+            else exact = false;
+            ++u;
+            i = r;
+        }
+        double d = 0.0;
+        if (exact && units < (1ull << 53)) {
+            d = (double)units * 0x1p-34;
+        } else {
+            for (int j = 0; j < u; ++j) d = __dadd_rn(d, (double)Store<WT>::getf(out_val[rb + j]));
+        }
+        ucount[row] = u;
+        degree[row] = d;
     }
 }
 
@@ -891,13 +971,21 @@ void build_graph_impl(gift_ctx *ctx, const gift_netlist *nl, const gift_build_op
                            16.0 * N + 4.0 * ninc + 16.0 * ninc + 4.0 * nraw + (4.0 + wsz) * nraw + 12.0 * N);
             if (E > 0)
                 k_net_stored<WT><<<grid_for(ctx, E, 256), 256, 0, st>>>(E, wnet.as<double>(), wst.as<WT>());
-            k_rows_small<WT><<<grid_for(ctx, (int64_t)N * kGS, kSmallThreads, 8), kSmallThreads, 0, st>>>(
-                N, inc_ptr.as<int64_t>(), inc_net.as<int32_t>(), g->net_ptr, g->pin_cell, wnet.as<double>(),
-                wst.as<WT>(), raw_ptr.as<int64_t>(), out_col.as<int32_t>(), ov, ucount.as<int32_t>(), g->degree,
-                wlist.as<int32_t>(), wc);
-            check_launch("k_rows_small");
+            if (N <= (1 << 27))
+                k_rows_lane<WT, uint32_t><<<grid_for(ctx, N, lane_threads<uint32_t>(), 6),
+                                            lane_threads<uint32_t>(), 0, st>>>(
+                    N, inc_ptr.as<int64_t>(), inc_net.as<int32_t>(), g->net_ptr, g->pin_cell, ctx->wtab,
+                    raw_ptr.as<int64_t>(), out_col.as<int32_t>(), ov, ucount.as<int32_t>(), g->degree,
+                    wlist.as<int32_t>(), wc);
+            else
+                k_rows_lane<WT, uint64_t><<<grid_for(ctx, N, lane_threads<uint64_t>(), 12),
+                                            lane_threads<uint64_t>(), 0, st>>>(
+                    N, inc_ptr.as<int64_t>(), inc_net.as<int32_t>(), g->net_ptr, g->pin_cell, ctx->wtab,
+                    raw_ptr.as<int64_t>(), out_col.as<int32_t>(), ov, ucount.as<int32_t>(), g->degree,
+                    wlist.as<int32_t>(), wc);
+            check_launch("k_rows_lane");
         }
-        if (maxraw > kSmallCap) {
+        if (maxraw > kLaneCap) {
             LaunchTimer lt(ctx, st, "build.rows_warp", 0.0);
             k_rows_warp<WT><<<ctx->num_sms * 6, kRowsWarps * 32, 0, st>>>(
                 wlist.as<int32_t>(), wc, inc_ptr.as<int64_t>(), inc_net.as<int32_t>(), g->net_ptr, g->pin_cell,

@@ -104,3 +104,28 @@ def test_large_workload_against_oracle(ctx, large, wd):
     per_net = np.maximum.reduceat(per_pin, nl.net_ptr[:-1], axis=0)
     lipschitz = 2.0 * per_net.sum(axis=(0, 2))
     assert np.all(np.abs(hp[SAMPLE] - hp_ref) <= lipschitz + 1e-9 * hp_ref)
+
+
+def test_cell_ids_beyond_2_27(ctx):
+    """Designs of more than 2^27 cells take the lane tier's 64-bit keys (a
+    32-bit key holds a cell id below 2^27 and the incidence index).  The nets
+    live among the top 8192 cells of a 2^27 + 4096-cell design, across the
+    2^27 boundary; the rows equal the oracle's rows of the same nets on cells
+    relabelled to 0..8191 (an order-preserving shift), the other rows are
+    empty."""
+    N, W = (1 << 27) + 4096, 8192
+    lo = N - W
+    nl = synth.random_small(31, W, 12_000, 9, allow_repeat=True)
+    pins = (nl.pin_cell.astype(np.int64) + lo).astype(np.int32)
+    h = gift.gift_build_graph(ctx, N, nl.net_ptr, pins, None)
+    try:
+        rp, col, val, deg = gift.gift_graph_export(h)
+    finally:
+        gift.gift_graph_free(h)
+    og = oracle.stored(oracle.build_graph(W, nl.net_ptr, nl.pin_cell), "f32")
+    assert rp[lo] == 0 and np.all(rp[:lo + 1] == 0)
+    np.testing.assert_array_equal(rp[lo:], og.row_ptr)
+    np.testing.assert_array_equal(col.astype(np.int64) - lo, og.col)
+    np.testing.assert_array_equal(val, og.val)
+    assert not deg[:lo].any()
+    np.testing.assert_array_equal(deg[lo:], oracle.degrees(og))
