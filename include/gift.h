@@ -125,19 +125,24 @@ typedef struct gift_graph_desc {
     int32_t num_cells;
     int32_t num_nets;
     int64_t num_pins;
-    int64_t nnz;            /* stored off-diagonal entries (both halves)       */
+    int64_t nnz;            /* nonzeros: unique cell pairs (both halves)       */
     int64_t raw_pairs;      /* ordered pin pairs before duplicates are summed  */
     int32_t weight_dtype;
     int32_t max_row_nnz;
     int64_t device_bytes;   /* device memory the graph owns                    */
-    const int64_t *row_ptr; /* device pointers owned by the graph              */
-    const int32_t *col;
-    const void *val;        /* weight_dtype elements                           */
+    const int64_t *row_ptr; /* device pointers owned by the graph: row i holds */
+    const int32_t *col;     /* entries row_ptr[i] .. row_ptr[i+1]-1, columns   */
+    const void *val;        /* ascending, then (when stored > nnz) padding     */
+                            /* entries (column i, weight 0) at the row's end;  */
+                            /* val has weight_dtype elements                   */
     const double *degree;   /* d_i = sum_j A_ij over the stored weights (FP64) */
     int32_t implicit_min_pins; /* build option (0: none)                       */
     int32_t reserved0;
     int64_t implicit_nets;  /* nets applied implicitly                          */
     int64_t implicit_pins;  /* their pins                                       */
+    int64_t stored;         /* entries in col/val: nnz, or raw_pairs when the  */
+                            /* rows keep their raw positions (at most 1/1024   */
+                            /* of them padding, so no compaction pass)         */
 } gift_graph_desc;
 
 typedef struct gift_kernel_stat {
@@ -202,7 +207,8 @@ GIFT_API gift_status gift_build_graph(gift_ctx *ctx, const gift_netlist *netlist
                              gift_graph **out, void *stream);
 GIFT_API gift_status gift_graph_info(const gift_graph *graph, gift_graph_desc *info);
 /* Host copies for parity checks: row_ptr [N+1], col [nnz], val [nnz] (stored
- * weights widened exactly to FP64), degree [N].  Any pointer may be NULL. */
+ * weights widened exactly to FP64; padding entries left out), degree [N].
+ * Any pointer may be NULL. */
 GIFT_API gift_status gift_graph_export(const gift_graph *graph, int64_t *row_ptr, int32_t *col, double *val,
                               double *degree);
 /* Synchronises the device, then releases the graph. */

@@ -260,6 +260,7 @@ gift_status gift_graph_info(const gift_graph *g, gift_graph_desc *info) {
         info->implicit_min_pins = g->imp_min;
         info->implicit_nets = g->imp_nets;
         info->implicit_pins = g->imp_pins;
+        info->stored = g->stored;
     });
 }
 
@@ -274,13 +275,36 @@ gift_status gift_graph_export(const gift_graph *g, int64_t *row_ptr, int32_t *co
         GIFT_REQUIRE(g != nullptr, "gift_graph_export: graph is NULL");
         GIFT_CUDA(cudaSetDevice(g->ctx->device));
         GIFT_CUDA(cudaStreamSynchronize(g->home));
-        if (row_ptr) GIFT_CUDA(cudaMemcpy(row_ptr, g->row_ptr, sizeof(int64_t) * (g->n + 1), cudaMemcpyDeviceToHost));
-        if (col && g->nnz) GIFT_CUDA(cudaMemcpy(col, g->col, sizeof(int32_t) * g->nnz, cudaMemcpyDeviceToHost));
-        if (val && g->nnz) {
-            size_t es = g->weight_dtype == GIFT_WEIGHT_F32 ? 4 : 2;
-            std::vector<unsigned char> tmp(es * g->nnz);
-            GIFT_CUDA(cudaMemcpy(tmp.data(), g->val, es * g->nnz, cudaMemcpyDeviceToHost));
-            for (int64_t k = 0; k < g->nnz; ++k) val[k] = widen(tmp.data(), g->weight_dtype, k);
+        const size_t es = g->weight_dtype == GIFT_WEIGHT_F32 ? 4 : 2;
+        if (g->stored == g->nnz) {
+            if (row_ptr)
+                GIFT_CUDA(cudaMemcpy(row_ptr, g->row_ptr, sizeof(int64_t) * (g->n + 1), cudaMemcpyDeviceToHost));
+            if (col && g->nnz) GIFT_CUDA(cudaMemcpy(col, g->col, sizeof(int32_t) * g->nnz, cudaMemcpyDeviceToHost));
+            if (val && g->nnz) {
+                std::vector<unsigned char> tmp(es * g->nnz);
+                GIFT_CUDA(cudaMemcpy(tmp.data(), g->val, es * g->nnz, cudaMemcpyDeviceToHost));
+                for (int64_t k = 0; k < g->nnz; ++k) val[k] = widen(tmp.data(), g->weight_dtype, k);
+            }
+        } else {
+            // padded layout: drop the padding entries (a row's own column)
+            std::vector<int64_t> rp(g->n + 1);
+            std::vector<int32_t> c(g->stored);
+            std::vector<unsigned char> v(es * g->stored);
+            GIFT_CUDA(cudaMemcpy(rp.data(), g->row_ptr, sizeof(int64_t) * (g->n + 1), cudaMemcpyDeviceToHost));
+            GIFT_CUDA(cudaMemcpy(c.data(), g->col, sizeof(int32_t) * g->stored, cudaMemcpyDeviceToHost));
+            if (val) GIFT_CUDA(cudaMemcpy(v.data(), g->val, es * g->stored, cudaMemcpyDeviceToHost));
+            int64_t at = 0;
+            for (int32_t i = 0; i < g->n; ++i) {
+                if (row_ptr) row_ptr[i] = at;
+                for (int64_t k = rp[i]; k < rp[i + 1]; ++k) {
+                    if (c[k] == i) continue;
+                    if (col) col[at] = c[k];
+                    if (val) val[at] = widen(v.data(), g->weight_dtype, k);
+                    ++at;
+                }
+            }
+            if (row_ptr) row_ptr[g->n] = at;
+            GIFT_REQUIRE(at == g->nnz, "gift_graph_export: padded rows disagree with the nonzero count");
         }
         if (degree) GIFT_CUDA(cudaMemcpy(degree, g->degree, sizeof(double) * g->n, cudaMemcpyDeviceToHost));
     });

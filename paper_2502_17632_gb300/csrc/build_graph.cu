@@ -30,6 +30,7 @@ constexpr int kRowsWarps = 8;      // warps per block in the warp tier
 constexpr int kBlockCap = 16384;   // keys in shared memory in the block tier (128 KiB)
 constexpr int kBlockThreads = 512;
 constexpr uint64_t kPadKey = ~0ull;
+constexpr int64_t kPadFraction = 1024;  // keep the padded raw layout when at most 1/1024 of it is padding
 
 __device__ __forceinline__ uint64_t make_key(int32_t cell, int32_t net) {
     return (static_cast<uint64_t>(static_cast<uint32_t>(cell)) << 32) | static_cast<uint32_t>(net);
@@ -745,21 +746,53 @@ k_rows_block(const int64_t *__restrict__ inc_ptr, const int32_t *__restrict__ in
     }
 }
 
+constexpr int kCopyRows = 256;
+
+// Per row: the default scales for the paper's two self-loop weights
+// (sigma = 2, 4; Eq. 16, symmetric form) from the degree; the entries past the row's unique columns (left where a column was
+// reached through several nets, or a net held the row's cell twice) padded
+// with (the row itself, weight 0), which no kernel's sum notices (x + 0 w = x)
+// and which no real entry can be (A has no diagonal); and the count and
+// longest row of unique columns.
+template <typename WT>
+__global__ void __launch_bounds__(kCopyRows)
+k_finish_rows(int32_t N, const int64_t *__restrict__ raw_ptr, const int32_t *__restrict__ ucount,
+              const double *__restrict__ degree, int32_t *__restrict__ out_col, WT *__restrict__ out_val,
+              float *__restrict__ s2, float *__restrict__ s4, unsigned long long *__restrict__ agg) {
+    unsigned long long sum = 0, best = 0;
+    for (int64_t i = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; i < N; i += (int64_t)gridDim.x * blockDim.x) {
+        const double d = degree[i];
+        s2[i] = scale_value(d, 2.0, GIFT_NORM_SYM);
+        s4[i] = scale_value(d, 4.0, GIFT_NORM_SYM);
+        const int64_t rb = raw_ptr[i], re = raw_ptr[i + 1];
+        const int32_t u = ucount[i];
+        for (int64_t k = rb + u; k < re; ++k) {
+            out_col[k] = (int32_t)i;
+            out_val[k] = Store<WT>::put(0.0);
+        }
+        sum += (unsigned long long)u;
+        best = max(best, (unsigned long long)u);
+    }
+    for (int o = 16; o; o >>= 1) {
+        sum += __shfl_xor_sync(0xffffffffu, sum, o);
+        best = max(best, __shfl_xor_sync(0xffffffffu, best, o));
+    }
+    if ((threadIdx.x & 31) == 0) {
+        if (sum) atomicAdd(&agg[0], sum);
+        if (best) atomicMax(&agg[1], best);
+    }
+}
+
 // Compaction: block per chunk of kCopyRows rows.  The chunk's raw entries are
 // contiguous and so are its CSR entries: threads stride over the raw range
 // (coalesced reads), find each entry's row by binary search over the
 // chunk's raw row pointers in shared memory, and write the row's first
-// ucount entries to their CSR position (coalesced writes).  Thread r also
-// writes row r's scales for the paper's two self-loop weights (sigma = 2, 4;
-// Eq. 16) from the degree.
-constexpr int kCopyRows = 256;
-
+// ucount entries to their CSR position (coalesced writes).
 template <typename WT>
 __global__ void __launch_bounds__(kCopyRows)
 k_copy_rows(int32_t N, const int64_t *__restrict__ raw_ptr, const int64_t *__restrict__ row_ptr,
             const int32_t *__restrict__ out_col, const WT *__restrict__ out_val, int32_t *__restrict__ col,
-            WT *__restrict__ val, const double *__restrict__ degree, int32_t *__restrict__ max_row,
-            float *__restrict__ s2, float *__restrict__ s4) {
+            WT *__restrict__ val) {
     __shared__ int64_t rraw[kCopyRows + 1], rout[kCopyRows + 1];
     const int64_t r0 = (int64_t)blockIdx.x * kCopyRows;
     const int nr = (int)min((int64_t)kCopyRows, (int64_t)N - r0);
@@ -782,16 +815,6 @@ k_copy_rows(int32_t N, const int64_t *__restrict__ raw_ptr, const int64_t *__res
             val[rout[lo] + t] = out_val[k];
         }
     }
-    int best = 0;
-    if ((int)threadIdx.x < nr) {
-        const int64_t i = r0 + threadIdx.x;
-        const double d = degree[i];
-        s2[i] = scale_value(d, 2.0, GIFT_NORM_SYM);
-        s4[i] = scale_value(d, 4.0, GIFT_NORM_SYM);
-        best = (int)(rout[threadIdx.x + 1] - rout[threadIdx.x]);
-    }
-    for (int o = 16; o; o >>= 1) best = max(best, __shfl_xor_sync(0xffffffffu, best, o));
-    if ((threadIdx.x & 31) == 0 && best) atomicMax(max_row, best);
 }
 
 int grid_for(gift_ctx *ctx, int64_t work, int threads, int per_sm = 8) {
@@ -1062,46 +1085,64 @@ void build_graph_impl(gift_ctx *ctx, const gift_netlist *nl, const gift_build_op
         g->device_bytes += (int64_t)(8 * (N + 1) + 8 * eb + 4 * g->imp_inc);
     }
 
-    // ---- row_ptr, compaction, default scales
-    g->row_ptr = (int64_t *)dev_alloc(ctx, sizeof(int64_t) * (N + 1), st);
-    {
-        LaunchTimer lt(ctx, st, "build.scan", 4.0 * N + 8.0 * (N + 1), 3);
-        exclusive_scan(ctx, ucount.as<int32_t>(), g->row_ptr, N, st);
-    }
-    int64_t nnz = 0;
-    GIFT_CUDA(cudaMemcpyAsync(&nnz, g->row_ptr + N, sizeof(int64_t), cudaMemcpyDeviceToHost, st));
-    GIFT_CUDA(cudaStreamSynchronize(st));
-    g->nnz = nnz;
-    g->col = (int32_t *)dev_alloc(ctx, sizeof(int32_t) * std::max<int64_t>(nnz, 1), st);
-    g->val = dev_alloc(ctx, wsz * std::max<int64_t>(nnz, 1), st);
+    // ---- scales, row padding, unique counts; then keep the raw layout or compact
     float *s2 = (float *)dev_alloc(ctx, sizeof(float) * N, st);
     g->scales.push_back(gift_graph::Scale{2.0f, GIFT_NORM_SYM, s2, s2});
     float *s4 = (float *)dev_alloc(ctx, sizeof(float) * N, st);
     g->scales.push_back(gift_graph::Scale{4.0f, GIFT_NORM_SYM, s4, s4});
     GIFT_CUDA(cudaMemsetAsync(flag.p, 0, sizeof(int) * 4, st));
+    unsigned long long *agg = (unsigned long long *)flag.p;  // [0] unique entries, [1] longest row
     {
-        LaunchTimer lt(ctx, st, "build.compact", 24.0 * N + 2.0 * (4.0 + wsz) * nnz);
+        LaunchTimer lt(ctx, st, "build.finish", 24.0 * N + 4.0 * N + 8.0 * (N + 1));
+        const int grid = grid_for(ctx, N, kCopyRows);
+        if (g->weight_dtype == GIFT_WEIGHT_F32)
+            k_finish_rows<float><<<grid, kCopyRows, 0, st>>>(N, raw_ptr.as<int64_t>(), ucount.as<int32_t>(), g->degree,
+                                                          out_col.as<int32_t>(), out_val.as<float>(), s2, s4, agg);
+        else if (g->weight_dtype == GIFT_WEIGHT_BF16)
+            k_finish_rows<__nv_bfloat16><<<grid, kCopyRows, 0, st>>>(N, raw_ptr.as<int64_t>(), ucount.as<int32_t>(),
+                                                                  g->degree, out_col.as<int32_t>(),
+                                                                  out_val.as<__nv_bfloat16>(), s2, s4, agg);
+        else
+            k_finish_rows<__half><<<grid, kCopyRows, 0, st>>>(N, raw_ptr.as<int64_t>(), ucount.as<int32_t>(), g->degree,
+                                                           out_col.as<int32_t>(), out_val.as<__half>(), s2, s4, agg);
+        check_launch("k_finish_rows");
+    }
+    unsigned long long hagg[2] = {0, 0};
+    GIFT_CUDA(cudaMemcpyAsync(hagg, agg, sizeof(hagg), cudaMemcpyDeviceToHost, st));
+    GIFT_CUDA(cudaStreamSynchronize(st));
+    const int64_t nnz = (int64_t)hagg[0];
+    g->nnz = nnz;
+    g->max_row_nnz = (int32_t)hagg[1];
+    if (nraw - nnz <= nraw / kPadFraction) {
+        // few raw entries collapsed: the raw layout, padded, is the CSR
+        g->row_ptr = static_cast<int64_t *>(raw_ptr.release());
+        g->col = static_cast<int32_t *>(out_col.release());
+        g->val = out_val.release();
+        g->stored = nraw;
+    } else {
+        g->row_ptr = (int64_t *)dev_alloc(ctx, sizeof(int64_t) * (N + 1), st);
+        {
+            LaunchTimer lt(ctx, st, "build.scan", 4.0 * N + 8.0 * (N + 1), 3);
+            exclusive_scan(ctx, ucount.as<int32_t>(), g->row_ptr, N, st);
+        }
+        g->col = (int32_t *)dev_alloc(ctx, sizeof(int32_t) * std::max<int64_t>(nnz, 1), st);
+        g->val = dev_alloc(ctx, wsz * std::max<int64_t>(nnz, 1), st);
+        g->stored = nnz;
+        LaunchTimer lt(ctx, st, "build.compact", 16.0 * (N + 1) + (4.0 + wsz) * (nraw + nnz));
         const int grid = (int)ceil_div(N, kCopyRows);
         if (g->weight_dtype == GIFT_WEIGHT_F32)
             k_copy_rows<float><<<grid, kCopyRows, 0, st>>>(N, raw_ptr.as<int64_t>(), g->row_ptr, out_col.as<int32_t>(),
-                                                      out_val.as<float>(), g->col, (float *)g->val, g->degree,
-                                                      flag.as<int32_t>(), s2, s4);
+                                                      out_val.as<float>(), g->col, (float *)g->val);
         else if (g->weight_dtype == GIFT_WEIGHT_BF16)
             k_copy_rows<__nv_bfloat16><<<grid, kCopyRows, 0, st>>>(N, raw_ptr.as<int64_t>(), g->row_ptr,
                                                               out_col.as<int32_t>(), out_val.as<__nv_bfloat16>(),
-                                                              g->col, (__nv_bfloat16 *)g->val, g->degree,
-                                                              flag.as<int32_t>(), s2, s4);
+                                                              g->col, (__nv_bfloat16 *)g->val);
         else
             k_copy_rows<__half><<<grid, kCopyRows, 0, st>>>(N, raw_ptr.as<int64_t>(), g->row_ptr, out_col.as<int32_t>(),
-                                                       out_val.as<__half>(), g->col, (__half *)g->val, g->degree,
-                                                       flag.as<int32_t>(), s2, s4);
+                                                       out_val.as<__half>(), g->col, (__half *)g->val);
         check_launch("k_copy_rows");
     }
-    int32_t maxrow = 0;
-    GIFT_CUDA(cudaMemcpyAsync(&maxrow, flag.p, sizeof(int32_t), cudaMemcpyDeviceToHost, st));
-    GIFT_CUDA(cudaStreamSynchronize(st));
-    g->max_row_nnz = maxrow;
-    g->device_bytes = (int64_t)(sizeof(int64_t) * (N + 1) + (4 + wsz) * nnz + 16 * N + 8 * (E + 1) + 4 * P + N);
+    g->device_bytes += (int64_t)(sizeof(int64_t) * (N + 1) + (4 + wsz) * g->stored + 16 * N + 8 * (E + 1) + 4 * P + N);
     *out = g;
     owner.g = nullptr;
 }

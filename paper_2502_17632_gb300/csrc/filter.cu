@@ -415,7 +415,7 @@ int run_sweeps(gift_ctx *ctx, const Plan &p, ShapeSet ss, cudaStream_t st, std::
     const gift_graph *g = p.g;
     const int64_t N = g->n;
     const size_t wsz = g->weight_dtype == GIFT_WEIGHT_F32 ? 4 : 2;
-    const double csr_bytes = (double)g->nnz * (4.0 + wsz) + 8.0 * (N + 1);
+    const double csr_bytes = (double)g->stored * (4.0 + wsz) + 8.0 * (N + 1);
     const double sig = 4.0 * (double)N * p.K;
     std::vector<std::pair<int, int>> plans[4];
     for (int kd = 0; kd < 4; ++kd) {
@@ -652,7 +652,7 @@ void run_sweeps_one(gift_ctx *ctx, const Plan &p, Shape shape, cudaStream_t st) 
 
 // Shape key of a graph / signal for the autotuner cache.
 std::string tune_key(const gift_graph *g, int vec, int K, const Plan &p) {
-    const double avg = g->n > 0 ? (double)g->nnz / g->n : 0.0;
+    const double avg = g->n > 0 ? (double)g->stored / g->n : 0.0;
     int lg = 0;
     while ((1ll << (lg + 1)) <= (int64_t)g->n) ++lg;
     return std::to_string(g->weight_dtype) + "/" + std::to_string(vec) + "/" + std::to_string(K) + "/" +

@@ -192,7 +192,8 @@ struct gift_graph {
     int32_t n = 0;            // cells
     int32_t num_nets = 0;
     int64_t num_pins = 0;
-    int64_t nnz = 0;
+    int64_t nnz = 0;              // nonzeros (unique cell pairs)
+    int64_t stored = 0;           // entries in col/val: nnz, or the raw pairs with zero padding
     int64_t raw_pairs = 0;
     int32_t weight_dtype = GIFT_WEIGHT_F32;
     int32_t max_row_nnz = 0;
@@ -200,8 +201,8 @@ struct gift_graph {
     cudaStream_t home = nullptr;  // stream of the build
     // device arrays owned by the graph
     int64_t *row_ptr = nullptr;   // [n+1]
-    int32_t *col = nullptr;       // [nnz]
-    void *val = nullptr;          // [nnz] weight_dtype
+    int32_t *col = nullptr;       // [stored]
+    void *val = nullptr;          // [stored] weight_dtype
     double *degree = nullptr;     // [n]
     int64_t *net_ptr = nullptr;   // [E+1]
     int32_t *pin_cell = nullptr;  // [P]

@@ -138,7 +138,7 @@ void build_sell(gift_ctx *ctx, gift_graph *g, int rps, cudaStream_t st) {
     DevBuf scol(ctx, sizeof(int32_t) * std::max<int64_t>(total, 1), st);
     DevBuf sval(ctx, wsz * std::max<int64_t>(total, 1), st);
     {
-        LaunchTimer lt(ctx, st, "build.sell_fill", (double)g->nnz * (4.0 + wsz) + (double)total * (4.0 + wsz));
+        LaunchTimer lt(ctx, st, "build.sell_fill", (double)g->stored * (4.0 + wsz) + (double)total * (4.0 + wsz));
         const int grid = (int)std::min<int64_t>(ceil_div(nslices * 32, 256), (int64_t)ctx->num_sms * 16);
         if (g->weight_dtype == GIFT_WEIGHT_F32)
             k_sell_fill<float><<<grid, 256, 0, st>>>(nslices, rps, g->row_ptr, g->col, (const float *)g->val,

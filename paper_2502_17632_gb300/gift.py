@@ -55,7 +55,7 @@ class gift_graph_desc(C.Structure):
                 ("raw_pairs", C.c_int64), ("weight_dtype", C.c_int32), ("max_row_nnz", C.c_int32),
                 ("device_bytes", C.c_int64), ("row_ptr", C.c_void_p), ("col", C.c_void_p), ("val", C.c_void_p),
                 ("degree", C.c_void_p), ("implicit_min_pins", C.c_int32), ("reserved0", C.c_int32),
-                ("implicit_nets", C.c_int64), ("implicit_pins", C.c_int64)]
+                ("implicit_nets", C.c_int64), ("implicit_pins", C.c_int64), ("stored", C.c_int64)]
 
 
 class gift_kernel_stat(C.Structure):

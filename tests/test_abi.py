@@ -53,6 +53,7 @@ int main(void) {
   P(gift_term) O(gift_term, alpha)
   P(gift_filter_spec) O(gift_filter_spec, term) O(gift_filter_spec, norm) O(gift_filter_spec, schedule)
   P(gift_graph_desc) O(gift_graph_desc, nnz) O(gift_graph_desc, device_bytes) O(gift_graph_desc, degree)
+  O(gift_graph_desc, stored)
   P(gift_kernel_stat) O(gift_kernel_stat, launches) O(gift_kernel_stat, kernels) O(gift_kernel_stat, alg_bytes)
   return 0;
 }
