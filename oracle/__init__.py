@@ -17,6 +17,10 @@ Every function states the paper passage it follows:
 * :func:`gift`          -- Eq. 15 with the Sec. 4.1 coefficients; fixed cells
   reimposed (Sec. 3.2.2, Algorithm 1).
 * :func:`hpwl`          -- half-perimeter wirelength (Sec. 4.1 reports it).
+* :func:`largest_component`, :func:`eigen_placement` -- the eigenvector
+  placer the paper analyses (Sec. 3.3.1, Eq. 23-24): eigenvectors of the
+  graph Laplacian L = D - A (Sec. 2.1) for its second and third smallest
+  eigenvalues, on the largest connected component.
 
 Parity pins live in ``tests/test_oracle_*.py``.
 """
@@ -312,3 +316,55 @@ def run(nl, sig: np.ndarray, fmt: str = "f64", terms=DEFAULT_TERMS, norm: str = 
     d = degrees(g)
     out = gift(g, d, sig, nl.is_fixed, terms, norm, reimpose)
     return g, d, out
+
+
+def largest_component(g: Graph) -> np.ndarray:
+    """Mask of the largest connected component of the graph (ties: the
+    component holding the smallest cell id).  A library routine (scipy's
+    breadth-first labelling) serves as the step."""
+    from scipy.sparse import csr_matrix
+    from scipy.sparse.csgraph import connected_components
+    a = csr_matrix((np.ones(g.nnz), np.asarray(g.col, dtype=np.int64), g.row_ptr), shape=(g.n, g.n))
+    ncomp, lab = connected_components(a, directed=False)
+    sizes = np.bincount(lab, minlength=ncomp)
+    first = np.full(ncomp, g.n, dtype=np.int64)
+    np.minimum.at(first, lab, np.arange(g.n, dtype=np.int64))
+    best = np.lexsort((first, -sizes))[0]
+    return lab == best
+
+
+def eigen_placement(g: Graph, d: np.ndarray):
+    """Hall's eigenvector placement as the paper analyses it (Sec. 3.3.1,
+    Eq. 23-24, an ideal low-pass filter keeping u_2 and u_3): the
+    eigenvectors of the graph Laplacian L = D - A (Sec. 2.1, d_i the row sums
+    of the stored weights) for its second and third smallest eigenvalues.
+
+    The eigenvector placer assumes one connected graph; a netlist graph has
+    cells without nets and small components, each adding an eigenvalue 0, so
+    u_2 and u_3 are taken on the largest connected component and are 0 on
+    every other cell.  Returns (u [n][2] FP64, unit 2-norm, sign arbitrary;
+    (lambda_2, lambda_3); the component mask).  Dense symmetric
+    eigendecomposition (numpy) for up to 2,000 component cells, else
+    shift-invert Lanczos (scipy's ARPACK) around -1e-3 for the three
+    eigenvalues nearest it (0, lambda_2, lambda_3)."""
+    from scipy.sparse import csr_matrix, diags
+    mask = largest_component(g)
+    idx = np.flatnonzero(mask)
+    m = idx.size
+    if m < 3:
+        raise ValueError("eigen_placement: the largest component has fewer than 3 cells")
+    a = csr_matrix((np.asarray(g.val, dtype=np.float64), np.asarray(g.col, dtype=np.int64), g.row_ptr),
+                   shape=(g.n, g.n))
+    a = a[idx][:, idx]
+    lap = (diags(np.asarray(d, dtype=np.float64)[idx]) - a).tocsc()
+    if m <= 2000:
+        w, v = np.linalg.eigh(lap.toarray())
+    else:
+        from scipy.sparse.linalg import eigsh
+        w, v = eigsh(lap, k=3, sigma=-1e-3, which="LM", tol=0.0)
+        order = np.argsort(w)
+        w, v = w[order], v[:, order]
+    u = np.zeros((g.n, 2), dtype=np.float64)
+    u[idx, 0] = v[:, 1]
+    u[idx, 1] = v[:, 2]
+    return u, (float(w[1]), float(w[2])), mask
