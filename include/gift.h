@@ -290,6 +290,42 @@ GIFT_API gift_status gift_tikhonov(gift_ctx *ctx, const gift_graph *graph, float
                                    int32_t num_signals, float *g_out, double *residual, int32_t mem, void *stream);
 
 /* ---------------------------------------------------------------------------
+ * Eigenvector placement (Sec. 3.3.1, Eq. 23-24): the eigenvectors of the graph
+ * Laplacian L = D - A (Sec. 2.1; A the stored weights, D the graph's FP64
+ * degrees) for its second and third smallest eigenvalues, as cell
+ * coordinates.  They are taken on the largest connected component (ties: the
+ * component holding the smallest cell id), where L's null space is the
+ * constant vector; every other cell gets 0.  Lanczos with full
+ * reorthogonalisation (two classical Gram-Schmidt passes per step, FP64
+ * vectors, deterministic sums) on L restricted to that component and to the
+ * complement of its constant vector, from a start vector drawn from `seed`;
+ * it stops when both Ritz residual estimates are <= tol * ||T|| (T the
+ * Lanczos tridiagonal), when the Krylov space is exhausted, or after
+ * max_iterations steps (2..4096).  The basis takes (steps + 2) * num_cells
+ * doubles of device memory.
+ * u ([num_cells][2] FP64, `mem` kind): (u_2, u_3) per cell, unit 2-norm, each
+ * signed so that its entry of largest magnitude (smallest index among equal
+ * ones) is positive.  result: lambda (the two Ritz values), residual
+ * (||L u_k - lambda_k u_k||_2, measured), iterations, component_cells, and
+ * converged = both residuals <= max(tol, 64 eps) * ||T||.
+ * A single Lanczos vector sees one vector per distinct eigenvalue: when
+ * lambda_2 is a multiple eigenvalue, lambda_3 is the next distinct one.
+ * Errors: GIFT_ERR_INVALID (bad argument; a largest component of fewer than
+ * 3 cells), GIFT_ERR_UNSUPPORTED (a graph built with implicit nets; a Krylov
+ * space of dimension 1), GIFT_ERR_OOM, GIFT_ERR_CUDA. */
+typedef struct gift_eigen_result {
+    double lambda[2];        /* Ritz values for lambda_2 <= lambda_3                 */
+    double residual[2];      /* ||L u_k - lambda_k u_k||_2 of the unit output vectors */
+    int32_t iterations;      /* Lanczos steps taken                                   */
+    int32_t component_cells; /* cells of the largest connected component             */
+    int32_t converged;       /* 1 when both residuals met the tolerance              */
+    int32_t reserved;
+} gift_eigen_result;
+GIFT_API gift_status gift_eigen_placement(gift_ctx *ctx, const gift_graph *graph, int32_t max_iterations, double tol,
+                                          uint64_t seed, double *u, gift_eigen_result *result, int32_t mem,
+                                          void *stream);
+
+/* ---------------------------------------------------------------------------
  * Bin density of a placement (Eq. 5): the die [die[0], die[2]) x [die[1],
  * die[3]) cut into bins_x x bins_y equal bins; cell v is a w_v x h_v rectangle
  * centred on its location (cell_w / cell_h per cell, or NULL for unit_w x

@@ -58,6 +58,11 @@ class gift_graph_desc(C.Structure):
                 ("implicit_nets", C.c_int64), ("implicit_pins", C.c_int64), ("stored", C.c_int64)]
 
 
+class gift_eigen_result(C.Structure):
+    _fields_ = [("lambda_", C.c_double * 2), ("residual", C.c_double * 2), ("iterations", C.c_int32),
+                ("component_cells", C.c_int32), ("converged", C.c_int32), ("reserved", C.c_int32)]
+
+
 class gift_kernel_stat(C.Structure):
     _fields_ = [("name", C.c_char * 48), ("launches", C.c_int64), ("kernels", C.c_int64),
                 ("total_ms", C.c_double), ("alg_bytes", C.c_double)]
@@ -125,6 +130,7 @@ def load(build_if_missing: bool = True):
         "gift_exec_launch": (I32, [P, P]),
         "gift_exec_free": (None, [P]),
         "gift_tikhonov": (I32, [P, P, C.c_float, C.c_float, I32, I32, P, I32, P, P, I32, P]),
+        "gift_eigen_placement": (I32, [P, P, I32, C.c_double, C.c_uint64, P, P, I32, P]),
         "gift_run": (I32, [P, P, P, P, P, I32, P, P, P]),
         "gift_density": (I32, [P, P, I32, I32, P, P, C.c_float, C.c_float, P, I32, I32, C.c_double, P, P, I32, P]),
         "gift_serve_opts_default": (None, [P]),
@@ -450,6 +456,21 @@ def gift_tikhonov(ctx, graph, g_in, g_out, sigma: float = 2.0, lam: float = 1.0,
     _check(load().gift_tikhonov(ctx, graph, sigma, lam, iterations, 1 if reimpose else 0, pi, S, po,
                                 res.ctypes.data, mi, _stream(stream)))
     return res
+
+
+# ------------------------------------------------------------------ eigenvector placement
+def gift_eigen_placement(ctx, graph, out=None, max_iterations: int = 300, tol: float = 1e-10, seed: int = 1,
+                         stream=None):
+    """(u_2, u_3) of L = D - A on the largest component into out ([N][2]
+    float64, numpy or CUDA tensor; a new numpy array if None); returns
+    (out, gift_eigen_result)."""
+    if out is None:
+        out = np.zeros((gift_graph_info(graph).num_cells, 2), dtype=np.float64)
+    p, mem = _ptr(out)
+    res = gift_eigen_result()
+    _check(load().gift_eigen_placement(ctx, graph, max_iterations, tol, seed, p, C.byref(res), mem,
+                                       _stream(stream)))
+    return out, res
 
 
 # ------------------------------------------------------------------ density

@@ -163,6 +163,37 @@ def make_netlist(num_movable: int, num_fixed: int, num_nets: int, seed: int,
                    dict(law=law, seed=seed, num_movable=num_movable, num_fixed=num_fixed))
 
 
+def lattice_netlist(nx: int, ny: int, num_nets: int, seed: int, max_pins: int = 4, radius: int = 2) -> Netlist:
+    """A netlist with locality: cells on an nx x ny lattice (cell r * nx + c),
+    each net an anchor cell drawn uniformly plus 1..max_pins-1 cells at
+    offsets drawn uniformly in [-radius, radius]^2 (clamped to the lattice;
+    repeated cells dropped, so a net may shrink).  Placement-like structure:
+    the graph's low Laplacian eigenvalues are separated, unlike a uniform
+    random netlist's."""
+    N = nx * ny
+    idx = np.arange(num_nets, dtype=np.uint64)
+    anchor = np.minimum(np.floor(uniform(seed, T_CELL, idx) * N), N - 1).astype(np.int64)
+    extra = 1 + np.floor(uniform(seed, T_PINCOUNT, idx) * (max_pins - 1)).astype(np.int64)
+    off = np.floor(uniform(seed, T_GEOM, np.arange(num_nets * (max_pins - 1) * 2, dtype=np.uint64))
+                   * (2 * radius + 1)).astype(np.int64).reshape(num_nets, max_pins - 1, 2) - radius
+    ar, ac = anchor // nx, anchor % nx
+    rr = np.clip(ar[:, None] + off[:, :, 0], 0, ny - 1)
+    cc = np.clip(ac[:, None] + off[:, :, 1], 0, nx - 1)
+    others = rr * nx + cc
+    nets = []
+    for e in range(num_nets):
+        cells = [int(anchor[e])]
+        for c in others[e, :extra[e]]:
+            if int(c) not in cells:
+                cells.append(int(c))
+        nets.append(cells)
+    net_ptr = np.zeros(num_nets + 1, dtype=np.int64)
+    np.cumsum([len(c) for c in nets], out=net_ptr[1:])
+    pin_cell = np.array([c for n in nets for c in n], dtype=np.int32)
+    return Netlist(N, num_nets, net_ptr, pin_cell, np.zeros(N, dtype=np.uint8), np.zeros((N, 2), np.float32),
+                   1000.0, dict(law="lattice", seed=seed, nx=nx, ny=ny))
+
+
 def make_signals(nl: Netlist, num_signals: int, seed: int, mode: str = "uniform") -> np.ndarray:
     """Initial locations g, float32 [N, S, 2]; fixed rows hold their positions."""
     N, S = nl.num_cells, num_signals

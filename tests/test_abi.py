@@ -55,6 +55,7 @@ int main(void) {
   P(gift_graph_desc) O(gift_graph_desc, nnz) O(gift_graph_desc, device_bytes) O(gift_graph_desc, degree)
   O(gift_graph_desc, stored)
   P(gift_kernel_stat) O(gift_kernel_stat, launches) O(gift_kernel_stat, kernels) O(gift_kernel_stat, alg_bytes)
+  P(gift_eigen_result) O(gift_eigen_result, residual) O(gift_eigen_result, iterations) O(gift_eigen_result, converged)
   return 0;
 }
 """
@@ -69,7 +70,7 @@ def test_struct_layout_matches_c(tmp_path):
     py = {
         "gift_netlist": gift.gift_netlist, "gift_build_opts": gift.gift_build_opts, "gift_term": gift.gift_term,
         "gift_filter_spec": gift.gift_filter_spec, "gift_graph_desc": gift.gift_graph_desc,
-        "gift_kernel_stat": gift.gift_kernel_stat,
+        "gift_kernel_stat": gift.gift_kernel_stat, "gift_eigen_result": gift.gift_eigen_result,
     }
     for key, val in ref.items():
         if "." in key:
