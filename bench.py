@@ -53,6 +53,7 @@ def parse():
     p.add_argument("--no-tikhonov", action="store_true", help="skip the Tikhonov measurement")
     p.add_argument("--no-density", action="store_true", help="skip the density measurement")
     p.add_argument("--no-small", action="store_true", help="skip the small-netlist latency measurement")
+    p.add_argument("--no-eigen", action="store_true", help="skip the eigenvector-placement measurement")
     p.add_argument("--serve-requests", type=int, default=240)
     p.add_argument("--serve-rate", type=float, default=40.0, help="Poisson arrival rate, requests/s")
     p.add_argument("--capture", action="store_true",
@@ -479,6 +480,62 @@ def run_tikhonov(args, gift, ctx, stream, nl, d_np, d_pc, d_fx, d_g, d_out, hp_g
             "hpwl_signal0": float(hp[0]), "gift_hpwl_signal0": float(hp_gift)}
 
 
+# ----------------------------------------------------------------- eigenvector placement
+def run_eigen(args, gift, ctx, stream, nl, d_np, d_pc, d_fx):
+    """The eigenvector placer (u_2, u_3 of L = D - A on the largest component)
+    against GiFt's cost: on a 30,000-cell lattice netlist (placement-like
+    locality; the smallest of the paper's design sizes) run to a 1e-8
+    residual, and on the benchmark graph with a 100-step budget (its low
+    eigenvalues crowd together).  One warm call, then one timed call per
+    case."""
+    import torch
+
+    def timed(h, **kw):
+        gift.gift_eigen_placement(ctx, h, stream=stream, **kw)
+        torch.cuda.synchronize()
+        e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+        e0.record(stream)
+        u, r = gift.gift_eigen_placement(ctx, h, stream=stream, **kw)
+        e1.record(stream)
+        torch.cuda.synchronize()
+        ms = e0.elapsed_time(e1)
+        return {"ms": ms, "iterations": int(r.iterations), "ms_per_step": ms / max(int(r.iterations), 1),
+                "lambda": [float(r.lambda_[0]), float(r.lambda_[1])],
+                "residual": [float(r.residual[0]), float(r.residual[1])], "converged": bool(r.converged),
+                "component_cells": int(r.component_cells)}
+
+    def gift_ms(h, g):
+        gi = torch.from_numpy(g).cuda()
+        go = torch.empty_like(gi)
+        gift.gift_filter(ctx, h, gi, go, stream=stream)
+        torch.cuda.synchronize()
+        e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+        e0.record(stream)
+        for _ in range(5):
+            gift.gift_filter(ctx, h, gi, go, stream=stream)
+        e1.record(stream)
+        torch.cuda.synchronize()
+        return e0.elapsed_time(e1) / 5
+
+    lat = synth.lattice_netlist(200, 150, 35_000, synth.SEED0 + 7)
+    dev = lambda a: torch.from_numpy(np.ascontiguousarray(a)).cuda()
+    h = gift.gift_build_graph(ctx, lat.num_cells, dev(lat.net_ptr), dev(lat.pin_cell), None, stream=stream)
+    try:
+        out = {"lattice": timed(h, max_iterations=4000, tol=1e-8)}
+        out["lattice"]["workload"] = "lattice 200 x 150 (30,000 cells, 35,000 nets of 2-4 pins within +-2 cells)"
+        out["lattice"]["gift_filter_ms_1_signal"] = gift_ms(h, synth.make_signals(lat, 1, 5))
+    finally:
+        gift.gift_graph_free(h)
+    h = gift.gift_build_graph(ctx, nl.num_cells, d_np, d_pc, d_fx, stream=stream)
+    try:
+        out["benchmark_graph"] = timed(h, max_iterations=100, tol=1e-8)
+        out["benchmark_graph"]["workload"] = f"{args.workload}, 100 Lanczos steps"
+        out["benchmark_graph"]["gift_filter_ms_1_signal"] = gift_ms(h, synth.make_signals(nl, 1, 5))
+    finally:
+        gift.gift_graph_free(h)
+    return out
+
+
 # ----------------------------------------------------------------- density / over-smoothing
 def run_density(args, gift, ctx, stream, nl, d_np, d_pc, d_fx, d_g):
     """Overflow (Eq. 5 bins, 64 x 64 on the die, square cells sized for 70 %
@@ -740,6 +797,9 @@ def run_ours(args):
     tikh = None
     if rank == 0 and world == 1 and not args.no_tikhonov:
         tikh = run_tikhonov(args, gift, ctx, stream, nl, d_np, d_pc, d_fx, d_g, d_out, hp[0])
+    eig = None
+    if rank == 0 and world == 1 and not args.no_eigen:
+        eig = run_eigen(args, gift, ctx, stream, nl, d_np, d_pc, d_fx)
     dens = None
     if rank == 0 and world == 1 and not args.no_density:
         dens = run_density(args, gift, ctx, stream, nl, d_np, d_pc, d_fx, d_g)
@@ -788,7 +848,7 @@ def run_ours(args):
             "roofline": roofline, "cpu_baseline": cpu, "e2e": e2e, "gpu_launches": launches * world,
             "clocks": clocks, "breakdown": breakdown, "filter_only": filt, "precision": precision,
             "serving": serving, "batched": batched, "implicit_cliques": implicit, "high_fanout": fanout,
-            "tikhonov": tikh, "density": dens, "small": small,
+            "tikhonov": tikh, "density": dens, "small": small, "eigen_placement": eig,
         }
         print(json.dumps(line), flush=True)
     if world > 1:

@@ -16,10 +16,11 @@
 //                its null vector (the component's normalised indicator, kept
 //                as a locked first basis vector): each step w = L v_j (FP64
 //                vectors, FP32 weights as stored, FP64 degrees and sums),
-//                then two passes of classical Gram-Schmidt against every
-//                earlier basis vector, which also yield the tridiagonal
-//                entries; dot products are summed per block and then across
-//                blocks in a fixed order, so a run is deterministic.
+//                then classical Gram-Schmidt against every earlier basis
+//                vector (a second pass when the first cancelled more than
+//                half the norm), which also yields the tridiagonal entries;
+//                dot products are summed per block and then across blocks in
+//                a fixed order, so a run is deterministic.
 //   Ritz pairs   of the tridiagonal on the host (bisection on Sturm counts for
 //                the two smallest eigenvalues, inverse iteration for their
 //                vectors), every kCheck steps and at the end; the Ritz vectors
@@ -145,33 +146,44 @@ __global__ void k_lap(int32_t n, const int64_t *__restrict__ row_ptr, const int3
 }
 
 // part[b][k] = sum over block b's rows of V[k][i] * w[i], k < nv (V holds
-// nv vectors of stride ld).  Fixed row ranges per block, fixed tree inside.
+// nv vectors of stride ld).  blockIdx.y picks 32 vectors, each warp four of
+// them: its lanes stride the block's rows (coalesced), four sums in flight,
+// then a fixed shuffle tree.  Fixed row ranges per block, so the sums do not
+// depend on scheduling.  Nothing happens when *skip is set.
+constexpr int kDotWarps = kEigThreads / 32;
+constexpr int kDotPerWarp = 4;
+constexpr int kDotPerBlock = kDotWarps * kDotPerWarp;
+
 __global__ void __launch_bounds__(kEigThreads)
 k_dots(int64_t n, int nv, const double *__restrict__ V, int64_t ld, const double *__restrict__ w,
-       double *__restrict__ part) {
-    __shared__ double red[kEigThreads / 32];
+       double *__restrict__ part, const int32_t *__restrict__ skip) {
+    if (skip && *skip) return;
     const int64_t chunk = (n + gridDim.x - 1) / gridDim.x;
     const int64_t r0 = blockIdx.x * chunk, r1 = min(n, r0 + chunk);
-    for (int k = 0; k < nv; ++k) {
-        const double *vk = V + (int64_t)k * ld;
-        double s = 0.0;
-        for (int64_t i = r0 + threadIdx.x; i < r1; i += blockDim.x) s = fma(vk[i], w[i], s);
-        for (int o = 16; o; o >>= 1) s += __shfl_xor_sync(0xffffffffu, s, o);
-        if ((threadIdx.x & 31) == 0) red[threadIdx.x >> 5] = s;
-        __syncthreads();
-        if (threadIdx.x == 0) {
-            double t = 0.0;
-            for (int q = 0; q < kEigThreads / 32; ++q) t += red[q];
-            part[(int64_t)blockIdx.x * nv + k] = t;
-        }
-        __syncthreads();
+    const int lane = threadIdx.x & 31;
+    const int k0 = blockIdx.y * kDotPerBlock + (threadIdx.x >> 5) * kDotPerWarp;
+    if (k0 >= nv) return;
+    double s[kDotPerWarp];
+#pragma unroll
+    for (int q = 0; q < kDotPerWarp; ++q) s[q] = 0.0;
+    for (int64_t i = r0 + lane; i < r1; i += 32) {
+        const double wi = w[i];
+#pragma unroll
+        for (int q = 0; q < kDotPerWarp; ++q)
+            if (k0 + q < nv) s[q] = fma(V[(int64_t)(k0 + q) * ld + i], wi, s[q]);
+    }
+#pragma unroll
+    for (int q = 0; q < kDotPerWarp; ++q) {
+        for (int o = 16; o; o >>= 1) s[q] += __shfl_xor_sync(0xffffffffu, s[q], o);
+        if (lane == 0 && k0 + q < nv) part[(int64_t)blockIdx.x * nv + k0 + q] = s[q];
     }
 }
 
 // h[k] = sum over blocks in order of part[b][k]; hsum[k] += h[k] (or = h[k]
 // when first), for the coefficients summed over the Gram-Schmidt passes.
 __global__ void k_dots_final(int nblocks, int nv, const double *__restrict__ part, double *__restrict__ h,
-                             double *__restrict__ hsum, int first) {
+                             double *__restrict__ hsum, int first, const int32_t *__restrict__ skip) {
+    if (skip && *skip) return;
     for (int k = blockIdx.x * blockDim.x + threadIdx.x; k < nv; k += gridDim.x * blockDim.x) {
         double t = 0.0;
         for (int b = 0; b < nblocks; ++b) t += part[(int64_t)b * nv + k];
@@ -180,10 +192,19 @@ __global__ void k_dots_final(int nblocks, int nv, const double *__restrict__ par
     }
 }
 
+// The second Gram-Schmidt pass is needed only when the first cancelled
+// more than half of the vector's norm (||w after|| <= ||w before|| / sqrt 2;
+// Daniel, Gragg, Kaufman and Stewart, 1976).
+__global__ void k_second_pass(const double *__restrict__ before, const double *__restrict__ after,
+                              int32_t *__restrict__ skip) {
+    *skip = *after > 0.5 * *before ? 1 : 0;
+}
+
 // w[i] = scale * w[i] + sum_k c[k] V[k][i]  (c on the device, nv <= kMaxLanczos + 2)
 __global__ void __launch_bounds__(kEigThreads)
 k_combine(int64_t n, int nv, const double *__restrict__ V, int64_t ld, const double *__restrict__ c, double sign,
-          double scale, double *__restrict__ w) {
+          double scale, double *__restrict__ w, const int32_t *__restrict__ skip) {
+    if (skip && *skip) return;
     extern __shared__ double cs[];
     for (int k = threadIdx.x; k < nv; k += blockDim.x) cs[k] = sign * c[k];
     __syncthreads();
@@ -402,18 +423,30 @@ void eigen_impl(gift_ctx *ctx, const gift_graph *g, int32_t max_iter, double tol
     DevBuf part(ctx, sizeof(double) * (size_t)nblk * (m + 2), st);
     DevBuf h(ctx, sizeof(double) * (m + 2), st);     // one pass's coefficients
     DevBuf proj(ctx, sizeof(double) * (m + 2), st);  // a step's coefficients over both passes
-    DevBuf scal(ctx, sizeof(double) * 4, st);        // [0] squared norm, [1] beta
+    DevBuf scal(ctx, sizeof(double) * 6, st);  // [0] squared norm, [1] beta, [2], [3] norms around a pass, [4] flag
     double *Vp = dptr<double>(V), *wp = dptr<double>(w), *hp = dptr<double>(h), *partp = dptr<double>(part);
     double *projp = dptr<double>(proj), *sq = dptr<double>(scal), *beta = sq + 1;
+    int32_t *skipp = reinterpret_cast<int32_t *>(sq + 4);
     const size_t cs_bytes = sizeof(double) * (m + 2);
 
-    // x -= V[0..nv) V[0..nv)^T x, two passes; proj = the summed coefficients
+    auto dots = [&](int nv, const double *Vs, const double *x, double *out, double *sum, int first,
+                    const int32_t *skip) {
+        k_dots<<<dim3(nblk, (nv + kDotPerBlock - 1) / kDotPerBlock), kEigThreads, 0, st>>>(N, nv, Vs, ld, x, partp,
+                                                                                          skip);
+        k_dots_final<<<(nv + 127) / 128, 128, 0, st>>>(nblk, nv, partp, out, sum, first, skip);
+    };
+    // *out = ||x||^2 through the same fixed-order sums
+    auto sqnorm = [&](const double *x, double *out) { dots(1, x, x, out, nullptr, 1, nullptr); };
+    // x -= V[0..nv) V[0..nv)^T x; a second pass when the first cancelled
+    // more than half the norm; proj = the coefficients summed over passes
     auto orthogonalise = [&](int nv, double *x) {
-        for (int pass = 0; pass < 2; ++pass) {
-            k_dots<<<nblk, kEigThreads, 0, st>>>(N, nv, Vp, ld, x, partp);
-            k_dots_final<<<(nv + 127) / 128, 128, 0, st>>>(nblk, nv, partp, hp, projp, pass == 0);
-            k_combine<<<grid, kEigThreads, cs_bytes, st>>>(N, nv, Vp, ld, hp, -1.0, 1.0, x);
-        }
+        sqnorm(x, sq + 2);
+        dots(nv, Vp, x, hp, projp, 1, nullptr);
+        k_combine<<<grid, kEigThreads, cs_bytes, st>>>(N, nv, Vp, ld, hp, -1.0, 1.0, x, nullptr);
+        sqnorm(x, sq + 3);
+        k_second_pass<<<1, 1, 0, st>>>(sq + 2, sq + 3, skipp);
+        dots(nv, Vp, x, hp, projp, 0, skipp);
+        k_combine<<<grid, kEigThreads, cs_bytes, st>>>(N, nv, Vp, ld, hp, -1.0, 1.0, x, skipp);
     };
     auto lap = [&](const double *x, double *y) {
         const int lg = (int)std::max<int64_t>(1, std::min<int64_t>(ceil_div((int64_t)N * 4, kEigThreads),
@@ -425,11 +458,6 @@ void eigen_impl(gift_ctx *ctx, const gift_graph *g, int32_t max_iter, double tol
                                                               g->degree, x, y);
         else
             k_lap<__half><<<lg, kEigThreads, 0, st>>>(N, g->row_ptr, g->col, (const __half *)g->val, g->degree, x, y);
-    };
-    // *out = ||x||^2 through the same fixed-order sums
-    auto sqnorm = [&](const double *x, double *out) {
-        k_dots<<<nblk, kEigThreads, 0, st>>>(N, 1, x, ld, x, partp);
-        k_dots_final<<<1, 128, 0, st>>>(nblk, 1, partp, out, nullptr, 1);
     };
 
     Tridiag T;
@@ -501,7 +529,8 @@ void eigen_impl(gift_ctx *ctx, const gift_graph *g, int32_t max_iter, double tol
             GIFT_CUDA(cudaMemcpyAsync(coef.p, c.data(), sizeof(double) * (steps + 1), cudaMemcpyHostToDevice, st));
             GIFT_CUDA(cudaMemsetAsync(wp, 0, sizeof(double) * N, st));
             k_combine<<<grid, kEigThreads, sizeof(double) * (steps + 1), st>>>(N, steps + 1, Vp, ld,
-                                                                               coef.as<double>(), 1.0, 0.0, wp);
+                                                                               coef.as<double>(), 1.0, 0.0, wp,
+                                                                               nullptr);
             // sign: the entry of largest magnitude (smallest index among equals) positive
             GIFT_CUDA(cudaMemsetAsync(flags.p, 0, sizeof(unsigned long long), st));
             GIFT_CUDA(cudaMemsetAsync(dptr<unsigned long long>(flags) + 1, 0xff, sizeof(unsigned long long), st));
@@ -522,7 +551,7 @@ void eigen_impl(gift_ctx *ctx, const gift_graph *g, int32_t max_iter, double tol
             lap(wp, dptr<double>(r));
             GIFT_CUDA(cudaMemcpyAsync(coef.p, &theta[k], sizeof(double), cudaMemcpyHostToDevice, st));
             k_combine<<<grid, kEigThreads, sizeof(double), st>>>(N, 1, wp, ld, coef.as<double>(), -1.0, 1.0,
-                                                                 dptr<double>(r));
+                                                                 dptr<double>(r), nullptr);
             sqnorm(dptr<double>(r), hp);
             double rr = 0.0;
             GIFT_CUDA(cudaMemcpyAsync(&rr, hp, sizeof(double), cudaMemcpyDeviceToHost, st));
