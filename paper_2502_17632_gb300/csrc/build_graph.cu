@@ -847,7 +847,7 @@ void release_graph(gift_graph *g, cudaStream_t st) {
 }
 
 void build_graph_impl(gift_ctx *ctx, const gift_netlist *nl, const gift_build_opts *opts, gift_graph **out,
-                      cudaStream_t st) {
+                      cudaStream_t st, const std::function<void()> &netlist_queued) {
     gift_build_opts def;
     if (!opts) {
         gift_build_opts_default(&def);
@@ -905,6 +905,7 @@ void build_graph_impl(gift_ctx *ctx, const gift_netlist *nl, const gift_build_op
     h2d_or_d2d(g->pin_cell, nl->pin_cell, P, nl->mem, st);
     if (nl->is_fixed) h2d_or_d2d(g->is_fixed, nl->is_fixed, N, nl->mem, st);
     else GIFT_CUDA(cudaMemsetAsync(g->is_fixed, 0, N, st));
+    if (netlist_queued) netlist_queued();
 
     // ---- validate on the device
     DevBuf flag(ctx, sizeof(int) * 4, st);

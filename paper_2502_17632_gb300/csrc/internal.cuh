@@ -8,6 +8,7 @@
 
 #include <cstdint>
 #include <cstdio>
+#include <functional>
 #include <map>
 #include <mutex>
 #include <string>
@@ -244,8 +245,10 @@ struct gift_graph {
 
 namespace gift {
 // build_graph.cu
+// netlist_queued (optional) runs once the netlist's copies are queued on st,
+// before any host wait: a caller can start other transfers behind them.
 void build_graph_impl(gift_ctx *ctx, const gift_netlist *nl, const gift_build_opts *opts, gift_graph **out,
-                      cudaStream_t st);
+                      cudaStream_t st, const std::function<void()> &netlist_queued = {});
 void release_graph(gift_graph *g, cudaStream_t st);
 // builds g->order if absent (caller holds g->mu)
 void ensure_row_order(gift_ctx *ctx, gift_graph *g, cudaStream_t st);

@@ -40,23 +40,31 @@ extern "C" gift_status gift_run(gift_ctx *ctx, const gift_netlist *netlist, cons
             }
         } own{ready, loaded};
         GIFT_CUDA(cudaEventCreateWithFlags(&loaded, cudaEventDisableTiming));
-        // upload g on the side stream once its buffer exists, overlapping the build
-        GIFT_CUDA(cudaEventRecord(ready, st));
-        {
+        // g goes up on the side stream behind the netlist's copies (so the
+        // two do not share the link while the build waits for the netlist),
+        // overlapping the build's kernels
+        bool queued = false;
+        auto upload = [&] {
+            GIFT_CUDA(cudaEventRecord(ready, st));
             std::lock_guard<std::mutex> lk(ctx->side_mu);
             GIFT_CUDA(cudaStreamWaitEvent(ctx->side, ready, 0));
             GIFT_CUDA(cudaMemcpyAsync(din.p, g_in, bytes, cudaMemcpyHostToDevice, ctx->side));
             GIFT_CUDA(cudaEventRecord(loaded, ctx->side));
-        }
+            queued = true;
+        };
         // on every way out (an invalid netlist throws from the build), the
-        // stream waits for the upload before din is freed on it
-        struct WaitUpload {
+        // stream waits for the side stream's copies before din and dout are
+        // freed on it
+        struct WaitSide {
             cudaStream_t st;
-            cudaEvent_t ev;
-            ~WaitUpload() { cudaStreamWaitEvent(st, ev, 0); }
-        } wait_upload{st, loaded};
+            cudaEvent_t &ev;
+            const bool &armed;
+            ~WaitSide() {
+                if (armed) cudaStreamWaitEvent(st, ev, 0);
+            }
+        } wait_side{st, loaded, queued};
         gift_graph *g = nullptr;
-        build_graph_impl(ctx, netlist, opts, &g, st);
+        build_graph_impl(ctx, netlist, opts, &g, st, upload);
         struct Graph {
             gift_graph *g;
             cudaStream_t st;
@@ -66,10 +74,19 @@ extern "C" gift_status gift_run(gift_ctx *ctx, const gift_netlist *netlist, cons
                 delete g;
             }
         } gown{g, st};
+        if (!queued) upload();
         GIFT_CUDA(cudaStreamWaitEvent(st, loaded, 0));
         filter_impl(ctx, g, spec, din.as<float>(), num_signals, dout.as<float>(), GIFT_MEM_DEVICE, st);
+        // the result goes down on the side stream while HPWL reads it on st
+        GIFT_CUDA(cudaEventRecord(ready, st));
+        {
+            std::lock_guard<std::mutex> lk(ctx->side_mu);
+            GIFT_CUDA(cudaStreamWaitEvent(ctx->side, ready, 0));
+            GIFT_CUDA(cudaMemcpyAsync(g_out, dout.p, bytes, cudaMemcpyDeviceToHost, ctx->side));
+            GIFT_CUDA(cudaEventRecord(loaded, ctx->side));
+        }
         if (hpwl) hpwl_impl(ctx, g, dout.as<float>(), num_signals, hpwl, GIFT_MEM_DEVICE, st);
-        GIFT_CUDA(cudaMemcpyAsync(g_out, dout.p, bytes, cudaMemcpyDeviceToHost, st));
+        GIFT_CUDA(cudaEventSynchronize(loaded));
         GIFT_CUDA(cudaStreamSynchronize(st));
         check_device_error(ctx);
     });
