@@ -46,6 +46,17 @@ void check_device_error(gift_ctx *ctx) {
     }
 }
 
+void sync_and_check(gift_ctx *ctx, cudaStream_t st) {
+    int32_t code = 0;
+    GIFT_CUDA(cudaMemcpyAsync(&code, ctx->dev_error, sizeof(int32_t), cudaMemcpyDeviceToHost, st));
+    GIFT_CUDA(cudaStreamSynchronize(st));
+    if (code != 0) {
+        GIFT_CUDA(cudaMemsetAsync(ctx->dev_error, 0, sizeof(int32_t), st));
+        GIFT_CUDA(cudaStreamSynchronize(st));
+        throw Failure{GIFT_ERR_TIMEOUT, "a bounded device wait ran out (code " + std::to_string(code) + ")"};
+    }
+}
+
 static cudaEvent_t take_event(gift_ctx *ctx) {
     if (!ctx->event_pool.empty()) {
         cudaEvent_t e = ctx->event_pool.back();

@@ -39,36 +39,53 @@ __device__ __forceinline__ int32_t key_cell(uint64_t k) { return static_cast<int
 __device__ __forceinline__ int32_t key_net(uint64_t k) { return static_cast<int32_t>(k & 0xffffffffu); }
 
 // ------------------------------------------------------------------ validate
-__global__ void k_validate(int32_t E, int64_t P, int32_t N, const int64_t *__restrict__ net_ptr,
-                           const int32_t *__restrict__ pin_cell, int *__restrict__ flag) {
-    int64_t tid = blockIdx.x * (int64_t)blockDim.x + threadIdx.x;
-    int64_t stride = (int64_t)gridDim.x * blockDim.x;
-    int bad = 0;
-    if (tid == 0 && net_ptr[0] != 0) bad |= 4;
+// The build's summary, read back in one copy: [0] flags (1: net_ptr
+// decreases, 2: a pin outside [0, N), 4: net_ptr[0] != 0, 8: net_ptr[E] < 0),
+// [1] net_ptr[0], [2] net_ptr[E] = P, [3] incidences, [4] raw pairs, [5] the
+// longest row's raw pairs, [6] the finishing pass's unique entries, [7] its
+// longest row.
+enum { kSumFlags, kSumFirst, kSumPins, kSumInc, kSumRaw, kSumMaxRaw, kSumUnique, kSumMaxRow, kSumSize };
+
+__global__ void k_validate(int32_t E, int32_t N, const int64_t *__restrict__ net_ptr,
+                           const int32_t *__restrict__ pin_cell, unsigned long long *__restrict__ summary) {
+    const int64_t tid = blockIdx.x * (int64_t)blockDim.x + threadIdx.x;
+    const int64_t stride = (int64_t)gridDim.x * blockDim.x;
+    const int64_t P = net_ptr[E];
+    unsigned long long bad = 0;
+    if (tid == 0) {
+        if (net_ptr[0] != 0) bad |= 4;
+        if (P < 0) bad |= 8;
+        summary[kSumFirst] = (unsigned long long)net_ptr[0];
+        summary[kSumPins] = (unsigned long long)P;
+    }
     for (int64_t e = tid; e < E; e += stride)
         if (net_ptr[e + 1] < net_ptr[e]) bad |= 1;
     for (int64_t p = tid; p < P; p += stride) {
         int32_t c = pin_cell[p];
         if (c < 0 || c >= N) bad |= 2;
     }
-    if (bad) atomicOr(flag, bad);
+    if (bad) atomicOr(summary + kSumFlags, bad);
 }
 
 // Each lane owns one net of the warp's 32; nets above 32 pins are then done by
 // the whole warp, one after another.  Nets of fewer than 2 pins, and with
-// imin > 0 the nets of at least imin pins (implicit cliques), are skipped.
+// imin > 0 the nets of at least imin pins (implicit cliques), are skipped; so
+// is a net whose pin range leaves [0, net_ptr[E]) (only an invalid netlist
+// has one: the counting pass runs before the validation result is read).
 template <class F>
 __device__ __forceinline__ void for_each_pin_of_nets(int32_t E, const int64_t *__restrict__ net_ptr, int64_t imin,
                                                      F &&f) {
     const int lane = threadIdx.x & 31;
     const int64_t warp = (blockIdx.x * (int64_t)blockDim.x + threadIdx.x) >> 5;
     const int64_t nwarps = ((int64_t)gridDim.x * blockDim.x) >> 5;
+    const int64_t P = net_ptr[E];
     for (int64_t base = warp * 32; base < E; base += nwarps * 32) {
         int64_t e = base + lane;
         int64_t b = 0, m = 0;
         if (e < E) {
             b = net_ptr[e];
             m = net_ptr[e + 1] - b;
+            if (b < 0 || m < 0 || m > P - b) m = 0;
             if (imin > 0 && m >= imin) m = 0;
         }
         if (m >= 2 && m <= 32)
@@ -95,10 +112,12 @@ __global__ void k_net_weights(int32_t E, const int64_t *__restrict__ net_ptr, co
     }
 }
 
-__global__ void k_count(int32_t E, const int64_t *__restrict__ net_ptr, const int32_t *__restrict__ pin_cell,
-                        int64_t imin, int32_t *__restrict__ cnt, unsigned long long *__restrict__ rawlen) {
+__global__ void k_count(int32_t E, int32_t N, const int64_t *__restrict__ net_ptr,
+                        const int32_t *__restrict__ pin_cell, int64_t imin, int32_t *__restrict__ cnt,
+                        unsigned long long *__restrict__ rawlen) {
     for_each_pin_of_nets(E, net_ptr, imin, [&](int32_t, int64_t b, int64_t m, int64_t t) {
         int32_t c = pin_cell[b + t];
+        if (c < 0 || c >= N) return;  // invalid netlist, rejected after the pass
         atomicAdd(&cnt[c], 1);
         atomicAdd(&rawlen[c], (unsigned long long)(m - 1));
     });
@@ -866,8 +885,14 @@ void build_graph_impl(gift_ctx *ctx, const gift_netlist *nl, const gift_build_op
     GIFT_REQUIRE(nl->net_ptr != nullptr, "gift_build_graph: net_ptr is NULL");
     const int32_t N = nl->num_cells, E = nl->num_nets;
 
+    // The netlist's ends (host input: read directly; device input: one small
+    // read, so no kernel touches pin_cell beyond net_ptr[E]); then the graph
+    // takes its copies, and validation, counting and the scans run before the
+    // next host wait (every pass memory-safe on an invalid netlist), which
+    // reads their results in one copy.
+    const bool host_in = nl->mem == GIFT_MEM_HOST;
     int64_t ends[2] = {0, 0};
-    if (nl->mem == GIFT_MEM_HOST) {
+    if (host_in) {
         ends[0] = nl->net_ptr[0];
         ends[1] = nl->net_ptr[E];
     } else {
@@ -894,10 +919,9 @@ void build_graph_impl(gift_ctx *ctx, const gift_netlist *nl, const gift_build_op
     g->ctx = ctx;
     g->n = N;
     g->num_nets = E;
-    g->num_pins = P;
     g->weight_dtype = opts->weight_dtype;
     g->home = st;
-
+    g->num_pins = P;
     g->net_ptr = (int64_t *)dev_alloc(ctx, sizeof(int64_t) * (E + 1), st);
     g->pin_cell = (int32_t *)dev_alloc(ctx, sizeof(int32_t) * std::max<int64_t>(P, 1), st);
     g->is_fixed = (uint8_t *)dev_alloc(ctx, N, st);
@@ -906,22 +930,19 @@ void build_graph_impl(gift_ctx *ctx, const gift_netlist *nl, const gift_build_op
     if (nl->is_fixed) h2d_or_d2d(g->is_fixed, nl->is_fixed, N, nl->mem, st);
     else GIFT_CUDA(cudaMemsetAsync(g->is_fixed, 0, N, st));
     if (netlist_queued) netlist_queued();
+    const int64_t *src_np = g->net_ptr;
+    const int32_t *src_pc = g->pin_cell;
 
     // ---- validate on the device
-    DevBuf flag(ctx, sizeof(int) * 4, st);
-    GIFT_CUDA(cudaMemsetAsync(flag.p, 0, sizeof(int) * 4, st));
+    DevBuf summary(ctx, sizeof(unsigned long long) * kSumSize, st);
+    unsigned long long *sum_d = summary.as<unsigned long long>();
+    GIFT_CUDA(cudaMemsetAsync(summary.p, 0, sizeof(unsigned long long) * kSumSize, st));
     {
         LaunchTimer lt(ctx, st, "build.validate", 8.0 * (E + 1) + 4.0 * P);
-        k_validate<<<grid_for(ctx, std::max<int64_t>(E, P), 256), 256, 0, st>>>(E, P, N, g->net_ptr, g->pin_cell,
-                                                                              flag.as<int>());
+        k_validate<<<grid_for(ctx, std::max<int64_t>({(int64_t)E, (int64_t)N, P}), 256), 256, 0, st>>>(
+            E, N, src_np, src_pc, sum_d);
         check_launch("k_validate");
     }
-    int hflag = 0;
-    GIFT_CUDA(cudaMemcpyAsync(&hflag, flag.p, sizeof(int), cudaMemcpyDeviceToHost, st));
-    GIFT_CUDA(cudaStreamSynchronize(st));
-    GIFT_REQUIRE(!(hflag & 4), "gift_build_graph: net_ptr[0] must be 0");
-    GIFT_REQUIRE(!(hflag & 1), "gift_build_graph: net_ptr decreases");
-    GIFT_REQUIRE(!(hflag & 2), "gift_build_graph: pin_cell id out of [0, num_cells)");
 
     // ---- count incidences and raw pairs per cell
     DevBuf wnet(ctx, sizeof(double) * std::max(E, 1), st);
@@ -931,8 +952,8 @@ void build_graph_impl(gift_ctx *ctx, const gift_netlist *nl, const gift_build_op
     GIFT_CUDA(cudaMemsetAsync(rawlen.p, 0, sizeof(int64_t) * N, st));
     if (E > 0) {
         LaunchTimer lt(ctx, st, "build.count", 16.0 * (E + 1) + 4.0 * P + 12.0 * N, 2);
-        k_net_weights<<<grid_for(ctx, E, 256), 256, 0, st>>>(E, g->net_ptr, ctx->wtab, wnet.as<double>());
-        k_count<<<grid_for(ctx, E, 256), 256, 0, st>>>(E, g->net_ptr, g->pin_cell, imin, cnt.as<int32_t>(),
+        k_net_weights<<<grid_for(ctx, E, 256), 256, 0, st>>>(E, src_np, ctx->wtab, wnet.as<double>());
+        k_count<<<grid_for(ctx, E, 256), 256, 0, st>>>(E, N, src_np, src_pc, imin, cnt.as<int32_t>(),
                                                          rawlen.as<unsigned long long>());
         check_launch("k_count");
     }
@@ -943,18 +964,23 @@ void build_graph_impl(gift_ctx *ctx, const gift_netlist *nl, const gift_build_op
         exclusive_scan(ctx, cnt.as<int32_t>(), inc_ptr.as<int64_t>(), N, st);
         exclusive_scan(ctx, rawlen.as<int64_t>(), raw_ptr.as<int64_t>(), N, st);
     }
-    GIFT_CUDA(cudaMemsetAsync(flag.p, 0, sizeof(int) * 4, st));
     {
         LaunchTimer lt(ctx, st, "build.maxraw", 8.0 * (N + 1));
-        k_max_rawlen<<<grid_for(ctx, N, 256), 256, 0, st>>>(N, raw_ptr.as<int64_t>(), (unsigned long long *)flag.p);
+        k_max_rawlen<<<grid_for(ctx, N, 256), 256, 0, st>>>(N, raw_ptr.as<int64_t>(), sum_d + kSumMaxRaw);
         check_launch("k_max_rawlen");
     }
-    int64_t totals[3] = {0, 0, 0};
-    GIFT_CUDA(cudaMemcpyAsync(&totals[0], inc_ptr.as<int64_t>() + N, sizeof(int64_t), cudaMemcpyDeviceToHost, st));
-    GIFT_CUDA(cudaMemcpyAsync(&totals[1], raw_ptr.as<int64_t>() + N, sizeof(int64_t), cudaMemcpyDeviceToHost, st));
-    GIFT_CUDA(cudaMemcpyAsync(&totals[2], flag.p, sizeof(int64_t), cudaMemcpyDeviceToHost, st));
+    GIFT_CUDA(cudaMemcpyAsync(sum_d + kSumInc, inc_ptr.as<int64_t>() + N, sizeof(int64_t), cudaMemcpyDeviceToDevice,
+                              st));
+    GIFT_CUDA(cudaMemcpyAsync(sum_d + kSumRaw, raw_ptr.as<int64_t>() + N, sizeof(int64_t), cudaMemcpyDeviceToDevice,
+                              st));
+    unsigned long long hs[kSumSize] = {};
+    GIFT_CUDA(cudaMemcpyAsync(hs, sum_d, sizeof(hs), cudaMemcpyDeviceToHost, st));
     GIFT_CUDA(cudaStreamSynchronize(st));
-    const int64_t ninc = totals[0], nraw = totals[1], maxraw = totals[2];
+    GIFT_REQUIRE(!(hs[kSumFlags] & 4), "gift_build_graph: net_ptr[0] must be 0");
+    GIFT_REQUIRE(!(hs[kSumFlags] & 8), "gift_build_graph: net_ptr[E] must be >= 0");
+    GIFT_REQUIRE(!(hs[kSumFlags] & 1), "gift_build_graph: net_ptr decreases");
+    GIFT_REQUIRE(!(hs[kSumFlags] & 2), "gift_build_graph: pin_cell id out of [0, num_cells)");
+    const int64_t ninc = (int64_t)hs[kSumInc], nraw = (int64_t)hs[kSumRaw], maxraw = (int64_t)hs[kSumMaxRaw];
     g->raw_pairs = nraw;
 
     // ---- scatter nets to cells
@@ -1091,8 +1117,7 @@ void build_graph_impl(gift_ctx *ctx, const gift_netlist *nl, const gift_build_op
     g->scales.push_back(gift_graph::Scale{2.0f, GIFT_NORM_SYM, s2, s2});
     float *s4 = (float *)dev_alloc(ctx, sizeof(float) * N, st);
     g->scales.push_back(gift_graph::Scale{4.0f, GIFT_NORM_SYM, s4, s4});
-    GIFT_CUDA(cudaMemsetAsync(flag.p, 0, sizeof(int) * 4, st));
-    unsigned long long *agg = (unsigned long long *)flag.p;  // [0] unique entries, [1] longest row
+    unsigned long long *agg = sum_d + kSumUnique;  // [0] unique entries, [1] longest row (zeroed above)
     {
         LaunchTimer lt(ctx, st, "build.finish", 24.0 * N + 4.0 * N + 8.0 * (N + 1));
         const int grid = grid_for(ctx, N, kCopyRows);

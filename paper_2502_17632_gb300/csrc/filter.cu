@@ -959,8 +959,7 @@ void filter_impl(gift_ctx *ctx, const gift_graph *cg, const gift_filter_spec *sp
 
     if (mem == GIFT_MEM_HOST) {
         GIFT_CUDA(cudaMemcpyAsync(g_out, p.dout, sig_bytes, cudaMemcpyDeviceToHost, st));
-        GIFT_CUDA(cudaStreamSynchronize(st));
-        check_device_error(ctx);
+        sync_and_check(ctx, st);
     }
 }
 

@@ -300,8 +300,7 @@ void hpwl_impl(gift_ctx *ctx, const gift_graph *g, const float *xy, int S, doubl
         check_launch("k_hpwl");
     }
     GIFT_CUDA(cudaMemcpyAsync(out, dout.p, sizeof(double) * S, cudaMemcpyDeviceToHost, st));
-    GIFT_CUDA(cudaStreamSynchronize(st));
-    check_device_error(ctx);
+    sync_and_check(ctx, st);
 }
 
 }  // namespace gift
@@ -362,8 +361,7 @@ void hpwl_batch_impl(gift_ctx *ctx, const gift_graph *g, const float *xy, int S,
         check_launch("k_hpwl_batch");
     }
     GIFT_CUDA(cudaMemcpyAsync(out, dout.p, sizeof(double) * B * S, cudaMemcpyDeviceToHost, st));
-    GIFT_CUDA(cudaStreamSynchronize(st));
-    check_device_error(ctx);
+    sync_and_check(ctx, st);
 }
 
 }  // namespace gift

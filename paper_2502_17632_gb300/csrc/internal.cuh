@@ -172,6 +172,9 @@ void check_launch(const char *what);
 // Reads (and clears) the context's device error word; throws GIFT_ERR_TIMEOUT if set.
 // Call only after the work that may set it has been synchronised.
 void check_device_error(gift_ctx *ctx);
+// Waits for st and checks the device error word in the same round trip (its
+// read is queued on st behind the work).
+void sync_and_check(gift_ctx *ctx, cudaStream_t st);
 
 inline int64_t ceil_div(int64_t a, int64_t b) { return (a + b - 1) / b; }
 

@@ -87,7 +87,6 @@ extern "C" gift_status gift_run(gift_ctx *ctx, const gift_netlist *netlist, cons
         }
         if (hpwl) hpwl_impl(ctx, g, dout.as<float>(), num_signals, hpwl, GIFT_MEM_DEVICE, st);
         GIFT_CUDA(cudaEventSynchronize(loaded));
-        GIFT_CUDA(cudaStreamSynchronize(st));
-        check_device_error(ctx);
+        sync_and_check(ctx, st);
     });
 }

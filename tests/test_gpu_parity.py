@@ -349,3 +349,50 @@ def test_injected_oom_leaves_library_usable(ctx):
         assert rel_err(go.cpu().numpy(), ref.reshape(g.shape), g).max() <= RTOL
     finally:
         gift.gift_graph_free(h)
+
+
+def lane_tier_netlist(seed):
+    """Rows that drive every width of the lane tier's sorting networks (8,
+    16 and 32 incidences, 8 / 16 / 32 keys): cell 0 in 32 two-pin nets (32
+    raw entries, the tier's cap), cell 1 in 20, cell 2 in 12; cells 3..5 share
+    the same cell pairs through several nets (runs of 2, 3 and 5 nets, summed
+    in FP64 in net order), cell 6 holds a net twice (a repeated pin); the rest
+    random small nets with repeats on cells 100..699."""
+    nets = []
+    for c, k in ((0, 32), (1, 20), (2, 12)):
+        for t in range(k):
+            nets.append([c, 100 + (7 * t + 13 * c) % 600])
+    for c, run in ((3, 2), (4, 3), (5, 5)):
+        for r in range(run):
+            nets.append([c, 50, 51 + r])  # cell pair (c, 50) in `run` nets of 3 pins
+    nets.append([6, 60, 6, 61])  # cell 6 twice in one net
+    small = synth.random_small(seed, 700, 900, 7, allow_repeat=True, min_pins=2)
+    for e in range(small.num_nets):  # on cells 100..699, away from the rows above
+        nets.append([100 + int(c) % 600 for c in small.pin_cell[small.net_ptr[e]:small.net_ptr[e + 1]]])
+    order = synth.u64(seed, 91, np.arange(len(nets), dtype=np.uint64)).argsort(kind="stable")  # shuffle the net ids
+    nets = [nets[i] for i in order]
+    net_ptr = np.concatenate([[0], np.cumsum([len(n) for n in nets])]).astype(np.int64)
+    pin_cell = np.array([c for n in nets for c in n], dtype=np.int32)
+    return synth.Netlist(700, len(nets), net_ptr, pin_cell, np.zeros(700, np.uint8), np.zeros((700, 2), np.float32))
+
+
+@pytest.mark.parametrize("wd", ["f32", "bf16", "f16"])
+@pytest.mark.parametrize("seed", [1, 2])
+def test_lane_tier_network_widths(ctx, wd, seed):
+    nl = lane_tier_netlist(seed)
+    raw = np.zeros(nl.num_cells, dtype=np.int64)
+    for e in range(nl.num_nets):
+        cells = nl.pin_cell[nl.net_ptr[e]:nl.net_ptr[e + 1]]
+        for c in cells:
+            raw[c] += len(cells) - 1
+    assert raw[0] == 32 and raw[1] == 20 and raw[2] == 12  # cap, and the 32- and 16-wide incidence networks
+    h = build(ctx, nl, wd)
+    try:
+        rp, col, val, deg = gift.gift_graph_export(h)
+    finally:
+        gift.gift_graph_free(h)
+    og = oracle.stored(oracle.build_graph(nl.num_cells, nl.net_ptr, nl.pin_cell), wd)
+    np.testing.assert_array_equal(rp, og.row_ptr)
+    np.testing.assert_array_equal(col, og.col)
+    np.testing.assert_array_equal(val, og.val)
+    np.testing.assert_array_equal(deg, oracle.degrees(og))
