@@ -56,6 +56,12 @@ def parse():
     p.add_argument("--no-eigen", action="store_true", help="skip the eigenvector-placement measurement")
     p.add_argument("--serve-requests", type=int, default=240)
     p.add_argument("--serve-rate", type=float, default=40.0, help="Poisson arrival rate, requests/s")
+    p.add_argument("--record-traffic", metavar="CSV",
+                   help="write profiles/traffic.json from the CSV of an ncu capture of 'bench.py --capture' "
+                        "(dram__bytes_read.sum, dram__bytes_write.sum, gpu__time_duration.sum of the k_sweep "
+                        "launches) and exit; --schedule names the tuned schedule that capture ran")
+    p.add_argument("--schedule", default="", help="with --record-traffic: the capture's sweep schedule, e.g. "
+                                                   "4242,4244,0,4244")
     p.add_argument("--capture", action="store_true",
                    help="tune and warm the filter, then run one filter call inside the NVTX range 'capture' and exit "
                         "(the command an ncu capture of the sweep kernels runs)")
@@ -183,6 +189,43 @@ def recorded_traffic(kernel: str, workload: str, weights: str, schedule):
         return r["dram_bytes_per_launch"]
     except Exception:
         return None
+
+
+def record_traffic(args):
+    """profiles/traffic.json from an ncu CSV: one entry per sweep launch of the
+    captured filter call, keyed by the sweep kernels' source hash and the
+    tuned schedule, so the benchmark uses it only while both still hold."""
+    import csv
+    launches = {}
+    with open(args.record_traffic, newline="") as f:
+        rows = [r for r in csv.reader(f) if len(r) > 5]
+    head = rows[0]
+    col = {k: head.index(k) for k in ("ID", "Kernel Name", "Metric Name", "Metric Value")}
+    for r in rows[1:]:
+        if "k_sweep" not in r[col["Kernel Name"]]:
+            continue
+        d = launches.setdefault(int(r[col["ID"]]), {"kernel": r[col["Kernel Name"]].split("(")[0]})
+        d[r[col["Metric Name"]]] = float(r[col["Metric Value"]].replace(",", ""))
+    per = [{"sweep": i + 1, "kernel": d["kernel"], "dram_read": d["dram__bytes_read.sum"],
+            "dram_write": d["dram__bytes_write.sum"], "ncu_ns": d["gpu__time_duration.sum"]}
+           for i, (_, d) in enumerate(sorted(launches.items()))]
+    path = os.path.join(ROOT, "profiles", "traffic.json")
+    rec = {}
+    if os.path.exists(path):
+        with open(path) as f:
+            rec = json.load(f)
+    rec.setdefault("filter.sweep", {})[f"{args.workload}/{args.weights}"] = {
+        "dram_bytes_per_launch": sum(p["dram_read"] + p["dram_write"] for p in per) / max(len(per), 1),
+        "per_launch": per, "source_hash": sweep_source_hash(),
+        "sweep_schedule": [int(x) for x in args.schedule.split(",")] if args.schedule else [],
+        "command": "ncu --metrics dram__bytes_read.sum,dram__bytes_write.sum,gpu__time_duration.sum "
+                   "--clock-control none --nvtx --nvtx-include capture/ -k regex:k_sweep --csv --log-file "
+                   "traffic_full.csv python bench.py --capture",
+        "note": "all sweep launches of one tuned filter call on the full workload (1 pass per launch)"}
+    with open(path, "w") as f:
+        json.dump(rec, f, indent=1)
+        f.write("\n")
+    print(json.dumps(rec["filter.sweep"][f"{args.workload}/{args.weights}"]["dram_bytes_per_launch"]))
 
 
 # ----------------------------------------------------------------- oracle (CPU)
@@ -858,7 +901,9 @@ def run_ours(args):
 
 def main():
     args = parse()
-    if args.impl == "reference":
+    if args.record_traffic:
+        record_traffic(args)
+    elif args.impl == "reference":
         run_reference(args)
     elif args.capture:
         run_capture(args)

@@ -21,11 +21,20 @@
 namespace gift {
 
 // Blocks of kSweepThreads per SM the register allocation must allow: the
-// in-flight gathers (U * NX * VEC floats per lane) plus about 24 registers of
-// addresses, indices and accumulators.
-constexpr int dr_min_blocks(int vec, int u, int nc, int nx) {
-    return (u * nx * vec + nc * vec + 2 * u + 24) <= 32 ? 8 : (u * nx * vec + nc * vec + 2 * u + 24) <= 40 ? 6
-         : (u * nx * vec + nc * vec + 2 * u + 24) <= 48 ? 5 : (u * nx * vec + nc * vec + 2 * u + 24) <= 64 ? 4 : 3;
+// in-flight gathers (U * NX * VEC floats per lane) plus the addresses,
+// indices and accumulators -- about 20 registers for later sweeps with four
+// float4 gathers in flight, 24 otherwise (the first sweep's scale gathers,
+// the two-gather loops and the float2 lanes need the extra four; checked
+// against ptxas spill reports for all three weight types).
+constexpr int dr_regs(int vec, int u, int nc, int nx, bool first) {
+    return u * nx * vec + nc * vec + 2 * u + (!first && u == 4 && vec == 4 ? 20 : 24);
+}
+constexpr int dr_min_blocks(int vec, int u, int nc, int nx, bool first) {
+    return dr_regs(vec, u, nc, nx, first) <= 32   ? 8
+           : dr_regs(vec, u, nc, nx, first) <= 40 ? 6
+           : dr_regs(vec, u, nc, nx, first) <= 48 ? 5
+           : dr_regs(vec, u, nc, nx, first) <= 64 ? 4
+                                                  : 3;
 }
 
 // Neumaier's compensated addition: s + e tracks the running sum exactly up
@@ -43,7 +52,7 @@ __device__ __forceinline__ void comp_add(float &s, float &e, float x) {
 // over the groups; for rows of hundreds to thousands of nonzeros.
 // COMP (with WR): compensated FP32 sums (Neumaier) per lane and in the tree.
 template <typename WT, int VEC, int CW, int U, int NC, bool FIRST, bool WR = false, bool COMP = false>
-__global__ void __launch_bounds__(kSweepThreads, dr_min_blocks(VEC, U, (COMP ? 2 : 1) * NC, FIRST ? 1 : NC))
+__global__ void __launch_bounds__(kSweepThreads, dr_min_blocks(VEC, U, (COMP ? 2 : 1) * NC, FIRST ? 1 : NC, FIRST))
 k_sweep_dr(const SweepArgs a) {
     static_assert(CW >= 1 && CW <= 32 && 32 % CW == 0, "lanes per row divide the warp");
     static_assert(WR || !COMP, "compensated sums come with warp rows");
