@@ -644,12 +644,6 @@ int run_sweeps(gift_ctx *ctx, const Plan &p, ShapeSet ss, cudaStream_t st, std::
     return planned_mask;
 }
 
-void run_sweeps_one(gift_ctx *ctx, const Plan &p, Shape shape, cudaStream_t st) {
-    ShapeSet ss;
-    for (auto &k : ss.kind) k = shape;
-    run_sweeps(ctx, p, ss, st);
-}
-
 // Shape key of a graph / signal for the autotuner cache.
 std::string tune_key(const gift_graph *g, int vec, int K, const Plan &p) {
     const double avg = g->n > 0 ? (double)g->stored / g->n : 0.0;

@@ -114,7 +114,6 @@ void ensure_row_order(gift_ctx *ctx, gift_graph *g, cudaStream_t st) {
 
 void build_sell(gift_ctx *ctx, gift_graph *g, int rps, cudaStream_t st) {
     GIFT_REQUIRE(rps == 8 || rps == 16 || rps == 32, "sell: rows per slice must be 8, 16 or 32");
-    const int64_t N = g->n;
     ensure_row_order(ctx, g, st);
     const int64_t padded = g->order_slots;
     const int64_t nslices = padded / rps;

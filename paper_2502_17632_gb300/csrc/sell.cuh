@@ -98,7 +98,7 @@ __global__ void __launch_bounds__(kSellThreads) k_sweep_sell(const SweepArgs a, 
             p.row = -1;
         }
     };
-    SellPos pf;  // metadata of the slice after nn's (prefetched one step ahead)
+    SellPos pf{};  // metadata of the slice after nn's (prefetched one step ahead)
     auto advance = [&](SellPos &p) {
         if (p.sl >= s.nslices) return;
         if (p.k0 + U < p.width) {
