@@ -222,7 +222,9 @@ GIFT_API void gift_graph_free_async(gift_graph *graph, void *stream);
  * the [N][S][2] signal filtered independently; with spec->reimpose_fixed the
  * fixed rows of g_out equal those of g_in.  spec NULL = paper defaults.
  * g_in and g_out (same memory kind, `mem`) must not overlap; device pointers
- * must be 8-byte aligned.  FP32 signal and accumulation.
+ * must be 8-byte aligned.  FP32 signal and accumulation.  With host memory
+ * the call is synchronous; a page-locked, 16-byte aligned g_out is written
+ * by the last sweep directly (no copy after it).
  * Errors: GIFT_ERR_INVALID, GIFT_ERR_OOM, GIFT_ERR_CUDA. */
 GIFT_API gift_status gift_filter(gift_ctx *ctx, const gift_graph *graph, const gift_filter_spec *spec,
                         const float *g_in, int32_t num_signals, float *g_out, int32_t mem, void *stream);
@@ -269,7 +271,10 @@ GIFT_API gift_status gift_hpwl(gift_ctx *ctx, const gift_graph *graph, const flo
  * the HPWL of every filtered signal to hpwl (host, [num_signals], may be
  * NULL).  The signal's upload overlaps the graph build (a side stream of the
  * context); everything else runs on `stream`, which is synchronised on
- * return.  Results equal gift_build_graph + gift_filter + gift_hpwl. */
+ * return.  When g_out is page-locked host memory (pinned or registered,
+ * 16-byte aligned) the last filter sweep stores the result into it directly,
+ * so its transfer overlaps the sweep; otherwise it is copied back while HPWL
+ * runs.  Results equal gift_build_graph + gift_filter + gift_hpwl. */
 GIFT_API gift_status gift_run(gift_ctx *ctx, const gift_netlist *netlist, const gift_build_opts *opts,
                               const gift_filter_spec *spec, const float *g_in, int32_t num_signals, float *g_out,
                               double *hpwl, void *stream);

@@ -329,6 +329,7 @@ struct Plan {
     int reimpose;
     const float *din;
     float *dout;
+    float *mirror = nullptr;  // the last sweep's output also goes here (mapped host memory)
     float *acc;
     std::vector<std::array<float *, 2>> X;
     int32_t *counters;  // one zeroed tile counter per TMA launch
@@ -549,6 +550,7 @@ int run_sweeps(gift_ctx *ctx, const Plan &p, ShapeSet ss, cudaStream_t st, std::
                 if (last) {
                     a.acc_in = contributed ? p.acc : nullptr;
                     a.acc_out = p.dout;
+                    a.acc_mirror = p.mirror;
                     if (p.reimpose) {
                         a.fixed = g->is_fixed;
                         a.g_fixed = p.din;
@@ -831,8 +833,19 @@ ShapeSet autotune(gift_ctx *ctx, const Plan &p, cudaStream_t st) {
 
 }  // namespace
 
+float *host_mirror(void *p, size_t bytes) {
+    if (!p || bytes == 0 || reinterpret_cast<uintptr_t>(p) % 16 != 0) return nullptr;
+    cudaPointerAttributes at{};
+    if (cudaPointerGetAttributes(&at, p) != cudaSuccess) {
+        cudaGetLastError();
+        return nullptr;
+    }
+    if (at.type != cudaMemoryTypeHost || !at.devicePointer) return nullptr;
+    return static_cast<float *>(at.devicePointer);
+}
+
 void filter_impl(gift_ctx *ctx, const gift_graph *cg, const gift_filter_spec *spec, const float *g_in, int S,
-                 float *g_out, int mem, cudaStream_t st) {
+                 float *g_out, int mem, cudaStream_t st, float *mirror) {
     gift_graph *g = const_cast<gift_graph *>(cg);
     GIFT_REQUIRE(S >= 1, "gift_filter: num_signals must be >= 1");
     GIFT_REQUIRE(mem == GIFT_MEM_HOST || mem == GIFT_MEM_DEVICE, "gift_filter: bad mem kind");
@@ -941,6 +954,9 @@ void filter_impl(gift_ctx *ctx, const gift_graph *cg, const gift_filter_spec *sp
         for (auto &k : ss.kind) k = shape_from_schedule(sched);
         ss.split[0] = ss.split[1] = split_sched;
     }
+    // host output in page-locked memory: the last sweep stores it there directly
+    if (mem == GIFT_MEM_HOST && !mirror) mirror = host_mirror(g_out, sig_bytes);
+    p.mirror = mirror;
     GIFT_CUDA(cudaMemsetAsync(p.counters, 0, sizeof(int32_t) * p.ncounters, st));
     const int used = run_sweeps(ctx, p, ss, st);
     for (int kd = 0; kd < 4; ++kd) {
@@ -952,7 +968,7 @@ void filter_impl(gift_ctx *ctx, const gift_graph *cg, const gift_filter_spec *sp
     }
 
     if (mem == GIFT_MEM_HOST) {
-        GIFT_CUDA(cudaMemcpyAsync(g_out, p.dout, sig_bytes, cudaMemcpyDeviceToHost, st));
+        if (!p.mirror) GIFT_CUDA(cudaMemcpyAsync(g_out, p.dout, sig_bytes, cudaMemcpyDeviceToHost, st));
         sync_and_check(ctx, st);
     }
 }

@@ -259,8 +259,14 @@ void ensure_row_order(gift_ctx *ctx, gift_graph *g, cudaStream_t st);
 void build_sell(gift_ctx *ctx, gift_graph *g, int rps, cudaStream_t st);
 void release_sell(gift_graph *g, cudaStream_t st);
 // filter.cu
+// mirror (optional): the last sweep also stores the output there -- mapped
+// host memory (host_mirror), so the result reaches the host while the sweep
+// runs instead of by a copy after it.
 void filter_impl(gift_ctx *ctx, const gift_graph *g, const gift_filter_spec *spec, const float *g_in, int S,
-                 float *g_out, int mem, cudaStream_t st);
+                 float *g_out, int mem, cudaStream_t st, float *mirror = nullptr);
+// The device-usable address of page-locked (pinned or registered) host memory
+// of `bytes` bytes, 16-byte aligned; nullptr for any other memory.
+float *host_mirror(void *p, size_t bytes);
 gift_graph::Scale graph_scale(gift_ctx *ctx, gift_graph *g, float sigma, int norm, cudaStream_t st);
 size_t filter_scratch_bytes(const gift_graph *g, const gift_filter_spec *spec, int S);
 void filter_on_scratch(gift_ctx *ctx, const gift_graph *g, const gift_filter_spec *spec, const float *g_in, int S,

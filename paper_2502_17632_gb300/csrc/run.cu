@@ -76,10 +76,13 @@ extern "C" gift_status gift_run(gift_ctx *ctx, const gift_netlist *netlist, cons
         } gown{g, st};
         if (!queued) upload();
         GIFT_CUDA(cudaStreamWaitEvent(st, loaded, 0));
-        filter_impl(ctx, g, spec, din.as<float>(), num_signals, dout.as<float>(), GIFT_MEM_DEVICE, st);
-        // the result goes down on the side stream while HPWL reads it on st
-        GIFT_CUDA(cudaEventRecord(ready, st));
-        {
+        // g_out in page-locked host memory: the last sweep stores the result
+        // there as it goes; otherwise it goes down on the side stream while
+        // HPWL reads the device copy on st
+        float *mirror = host_mirror(g_out, bytes);
+        filter_impl(ctx, g, spec, din.as<float>(), num_signals, dout.as<float>(), GIFT_MEM_DEVICE, st, mirror);
+        if (!mirror) {
+            GIFT_CUDA(cudaEventRecord(ready, st));
             std::lock_guard<std::mutex> lk(ctx->side_mu);
             GIFT_CUDA(cudaStreamWaitEvent(ctx->side, ready, 0));
             GIFT_CUDA(cudaMemcpyAsync(g_out, dout.p, bytes, cudaMemcpyDeviceToHost, ctx->side));

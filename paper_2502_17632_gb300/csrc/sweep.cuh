@@ -56,6 +56,7 @@ struct SweepArgs {
     ChainIO ch[2];
     const float *acc_in;  // non-null: add to the contributions
     float *acc_out;       // non-null: write contributions (+acc_in)
+    float *acc_mirror;    // non-null: the final output is stored here too (mapped host memory)
     const uint8_t *fixed; // non-null: rows with fixed[i] != 0 take g_fixed
     const float *g_fixed;
     const float2 *gpre2;  // first sweep with two chains: (pre_0[j], pre_1[j]) packed, or null
@@ -318,6 +319,7 @@ __global__ void __launch_bounds__(kSweepThreads) k_sweep(const SweepArgs a) {
             }
             if (a.fixed && a.fixed[row]) ldv<VEC>(a.g_fixed + off, out);
             stv<VEC>(a.acc_out + off, out);
+            if (a.acc_mirror) stv<VEC>(a.acc_mirror + off, out);
         }
     }
 }

@@ -89,6 +89,7 @@ __device__ __forceinline__ void mp_finish(const SweepArgs &a, int64_t row, int c
             for (int v = 0; v < VEC; ++v) r[v] = out[v];
         }
         stv<VEC>(a.acc_out + off, r);
+        if (a.acc_mirror) stv<VEC>(a.acc_mirror + off, r);
     }
 }
 

@@ -184,3 +184,29 @@ def test_gift_run_equals_separate_calls(ctx, batch):
     hp2 = gift.gift_run(ctx, nl.num_cells, nl.net_ptr, nl.pin_cell, nl.is_fixed, g, out,
                         implicit_min_pins=4, weight_dtype=gift.GIFT_WEIGHT_BF16)
     assert np.all(np.isfinite(hp2)) and np.all(np.isfinite(out))
+
+
+def test_results_written_straight_to_pinned_host_memory(ctx, batch):
+    """Page-locked output: the last sweep stores the result into it directly
+    (no copy after the filter).  Same bits as pageable output, through
+    gift_run and through gift_filter with host buffers, for every kernel
+    family's epilogue."""
+    nl, g = batch[0]
+    pinned = torch.empty(g.shape, dtype=torch.float32).pin_memory()
+    out_p = pinned.numpy()
+    out = np.empty_like(g)
+    hp_p = gift.gift_run(ctx, nl.num_cells, nl.net_ptr, nl.pin_cell, nl.is_fixed, g, out_p)
+    hp = gift.gift_run(ctx, nl.num_cells, nl.net_ptr, nl.pin_cell, nl.is_fixed, g, out)
+    np.testing.assert_array_equal(out_p, out)
+    np.testing.assert_array_equal(hp_p, hp)
+    h = gift.gift_build_graph(ctx, nl.num_cells, nl.net_ptr, nl.pin_cell, nl.is_fixed)
+    try:
+        for schedule in (0, 408, 1004, 3008, 4244, 4644):
+            spec = gift.make_spec(schedule=schedule)
+            ref = np.empty_like(g)
+            gift.gift_filter(ctx, h, g, ref, spec)
+            out_p[...] = np.nan
+            gift.gift_filter(ctx, h, g, out_p, spec)
+            np.testing.assert_array_equal(out_p, ref)
+    finally:
+        gift.gift_graph_free(h)
