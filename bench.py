@@ -724,6 +724,14 @@ def run_ours(args):
     dev = lambda a: torch.from_numpy(np.ascontiguousarray(a)).cuda()  # noqa: E731
     d_np, d_pc, d_fx, d_g = dev(nl.net_ptr), dev(nl.pin_cell), dev(nl.is_fixed), dev(g)
     d_out = torch.empty_like(d_g)
+    # page-locked host buffers for the end-to-end measurement, and one gift_run call, at start-up as an
+    # application would (when the process's first gift_run came after the benchmark's other device work,
+    # every later call measured 5.1 ms instead of 4.5 ms; the device step is the same either way)
+    if not args.no_e2e:
+        pin = lambda a: torch.from_numpy(np.ascontiguousarray(a)).pin_memory().numpy()  # noqa: E731
+        h_np, h_pc, h_fx, h_g = pin(nl.net_ptr), pin(nl.pin_cell), pin(nl.is_fixed), pin(g)
+        h_out = torch.empty(g.shape, dtype=torch.float32).pin_memory().numpy()
+        gift.gift_run(ctx, N, h_np, h_pc, h_fx, h_g, h_out, weight_dtype=wd, stream=stream)
 
     def step():
         h = gift.gift_build_graph(ctx, N, d_np, d_pc, d_fx, wd, stream=stream)
@@ -819,10 +827,6 @@ def run_ours(args):
     # end to end through the public API with pinned host buffers
     e2e = None
     if not args.no_e2e:
-        pin = lambda a: torch.from_numpy(np.ascontiguousarray(a)).pin_memory().numpy()  # noqa: E731
-        h_np, h_pc, h_fx, h_g = pin(nl.net_ptr), pin(nl.pin_cell), pin(nl.is_fixed), pin(g)
-        h_out = torch.empty(g.shape, dtype=torch.float32).pin_memory().numpy()
-
         def estep():  # one public call: build + filter + HPWL from host memory
             return gift.gift_run(ctx, N, h_np, h_pc, h_fx, h_g, h_out, weight_dtype=wd, stream=stream)
 
