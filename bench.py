@@ -54,6 +54,7 @@ def parse():
     p.add_argument("--no-density", action="store_true", help="skip the density measurement")
     p.add_argument("--no-small", action="store_true", help="skip the small-netlist latency measurement")
     p.add_argument("--no-eigen", action="store_true", help="skip the eigenvector-placement measurement")
+    p.add_argument("--no-paper-sizes", action="store_true", help="skip the paper-design-size measurement")
     p.add_argument("--serve-requests", type=int, default=240)
     p.add_argument("--serve-rate", type=float, default=40.0, help="Poisson arrival rate, requests/s")
     p.add_argument("--record-traffic", metavar="CSV",
@@ -523,6 +524,50 @@ def run_tikhonov(args, gift, ctx, stream, nl, d_np, d_pc, d_fx, d_g, d_out, hp_g
             "hpwl_signal0": float(hp[0]), "gift_hpwl_signal0": float(hp_gift)}
 
 
+# ----------------------------------------------------------------- the paper's design sizes
+# (cells, nets, the paper's GPU GiFt time in s) of the designs in its Table 1, for scale only: the
+# netlists here are synthetic (same pin-count law, 1 % fixed IO), the paper's times were taken on other
+# hardware and include its Python overheads.
+PAPER_SIZES = [(30_675, 30_835, 0.11), (32_281, 33_307, 0.43), (112_644, 112_878, 0.25),
+               (130_661, 133_223, 0.43), (155_325, 158_527, 0.17)]
+
+
+def run_paper_sizes(args, gift, ctx, stream):
+    """Build + filter + HPWL of one (x, y) placement signal on synthetic
+    netlists of the paper's design sizes, device-resident, CUDA events over
+    10 steps after 3 warm-up steps."""
+    import torch
+    dev = lambda a: torch.from_numpy(np.ascontiguousarray(a)).cuda()  # noqa: E731
+    out = []
+    for i, (cells, nets, paper_s) in enumerate(PAPER_SIZES):
+        fixed = max(cells // 100, 1)
+        nl = synth.make_netlist(cells - fixed, fixed, nets, synth.SEED0 + 20 + i)
+        g = synth.make_signals(nl, 1, synth.SEED0 + 20 + i)
+        d_np, d_pc, d_fx, d_g = dev(nl.net_ptr), dev(nl.pin_cell), dev(nl.is_fixed), dev(g)
+        d_out = torch.empty_like(d_g)
+
+        def step():
+            h = gift.gift_build_graph(ctx, nl.num_cells, d_np, d_pc, d_fx, stream=stream)
+            gift.gift_filter(ctx, h, d_g, d_out, stream=stream)
+            hp = gift.gift_hpwl(ctx, h, d_out, stream=stream)
+            gift.gift_graph_free_async(h, stream)
+            return hp
+
+        for _ in range(3):
+            step()
+        torch.cuda.synchronize()
+        e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+        e0.record(stream)
+        for _ in range(10):
+            step()
+        e1.record(stream)
+        torch.cuda.synchronize()
+        ms = e0.elapsed_time(e1) / 10
+        out.append({"cells": cells, "nets": nets, "pins": int(nl.num_pins), "step_ms": ms,
+                    "paper_gpu_gift_s": paper_s})
+    return out
+
+
 # ----------------------------------------------------------------- eigenvector placement
 def run_eigen(args, gift, ctx, stream, nl, d_np, d_pc, d_fx):
     """The eigenvector placer (u_2, u_3 of L = D - A on the largest component)
@@ -848,6 +893,9 @@ def run_ours(args):
     tikh = None
     if rank == 0 and world == 1 and not args.no_tikhonov:
         tikh = run_tikhonov(args, gift, ctx, stream, nl, d_np, d_pc, d_fx, d_g, d_out, hp[0])
+    sizes = None
+    if rank == 0 and world == 1 and not args.no_paper_sizes:
+        sizes = run_paper_sizes(args, gift, ctx, stream)
     eig = None
     if rank == 0 and world == 1 and not args.no_eigen:
         eig = run_eigen(args, gift, ctx, stream, nl, d_np, d_pc, d_fx)
@@ -899,7 +947,7 @@ def run_ours(args):
             "roofline": roofline, "cpu_baseline": cpu, "e2e": e2e, "gpu_launches": launches * world,
             "clocks": clocks, "breakdown": breakdown, "filter_only": filt, "precision": precision,
             "serving": serving, "batched": batched, "implicit_cliques": implicit, "high_fanout": fanout,
-            "tikhonov": tikh, "density": dens, "small": small, "eigen_placement": eig,
+            "tikhonov": tikh, "density": dens, "small": small, "eigen_placement": eig, "paper_sizes": sizes,
         }
         print(json.dumps(line), flush=True)
     if world > 1:
