@@ -17,7 +17,11 @@
  *     On a non-OK status gift_last_error() gives a message (thread-local).
  *   - Invalid input (ids out of range, decreasing net_ptr, N <= 0, S <= 0,
  *     unknown enum values, null pointers) yields GIFT_ERR_INVALID and leaves
- *     no allocation behind.  The filter does not scan its input for NaN.
+ *     no allocation behind.  A signal given in host memory (gift_filter with
+ *     GIFT_MEM_HOST, gift_run, gift_serve_submit) is scanned on arrival: a NaN
+ *     or an infinity in it yields GIFT_ERR_INVALID before any output is
+ *     written.  A signal in device memory is not scanned, so that those calls
+ *     stay asynchronous.
  *   - Input arrays are borrowed for the duration of the call only.  Host
  *     inputs are copied before the call returns; device inputs must stay valid
  *     until the work queued on `stream` has completed.

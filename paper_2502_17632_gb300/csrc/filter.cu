@@ -833,6 +833,29 @@ ShapeSet autotune(gift_ctx *ctx, const Plan &p, cudaStream_t st) {
 
 }  // namespace
 
+namespace {
+__global__ void k_nonfinite(int64_t n, const float *__restrict__ x, int32_t *__restrict__ flag) {
+    const int64_t n4 = n / 4;
+    const float4 *x4 = reinterpret_cast<const float4 *>(x);
+    int bad = 0;
+    for (int64_t i = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; i < n4; i += (int64_t)gridDim.x * blockDim.x) {
+        const float4 v = x4[i];
+        bad |= !isfinite(v.x) || !isfinite(v.y) || !isfinite(v.z) || !isfinite(v.w);
+    }
+    for (int64_t i = 4 * n4 + blockIdx.x * (int64_t)blockDim.x + threadIdx.x; i < n;
+         i += (int64_t)gridDim.x * blockDim.x)
+        bad |= !isfinite(x[i]);
+    if (__syncthreads_or(bad) && threadIdx.x == 0) atomicOr(flag, 1);
+}
+}  // namespace
+
+void scan_nonfinite(gift_ctx *ctx, const float *x, int64_t n, int32_t *flag, cudaStream_t st) {
+    const int grid = (int)std::max<int64_t>(1, std::min<int64_t>(ceil_div(std::max<int64_t>(n / 4, 1), 256),
+                                                                 (int64_t)ctx->num_sms * 8));
+    k_nonfinite<<<grid, 256, 0, st>>>(n, x, flag);
+    check_launch("k_nonfinite");
+}
+
 float *host_mirror(void *p, size_t bytes) {
     if (!p || bytes == 0 || reinterpret_cast<uintptr_t>(p) % 16 != 0) return nullptr;
     cudaPointerAttributes at{};
@@ -900,6 +923,14 @@ void filter_impl(gift_ctx *ctx, const gift_graph *cg, const gift_filter_spec *sp
         GIFT_CUDA(cudaMemcpyAsync(din_buf.p, g_in, sig_bytes, cudaMemcpyHostToDevice, st));
         p.din = din_buf.as<float>();
         p.dout = dout_buf.as<float>();
+        // host signals are checked before any sweep runs (a host call is synchronous anyway)
+        DevBuf bad(ctx, sizeof(int32_t), st);
+        GIFT_CUDA(cudaMemsetAsync(bad.p, 0, sizeof(int32_t), st));
+        scan_nonfinite(ctx, p.din, (int64_t)N * K, bad.as<int32_t>(), st);
+        int32_t hbad = 0;
+        GIFT_CUDA(cudaMemcpyAsync(&hbad, bad.p, sizeof(int32_t), cudaMemcpyDeviceToHost, st));
+        GIFT_CUDA(cudaStreamSynchronize(st));
+        GIFT_REQUIRE(!hbad, "gift_filter: g_in holds a NaN or an infinity");
     }
     const bool al16 = (reinterpret_cast<uintptr_t>(p.din) % 16 == 0) && (reinterpret_cast<uintptr_t>(p.dout) % 16 == 0);
     const bool al8 = (reinterpret_cast<uintptr_t>(p.din) % 8 == 0) && (reinterpret_cast<uintptr_t>(p.dout) % 8 == 0);

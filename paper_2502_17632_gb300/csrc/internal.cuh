@@ -264,6 +264,9 @@ void release_sell(gift_graph *g, cudaStream_t st);
 // runs instead of by a copy after it.
 void filter_impl(gift_ctx *ctx, const gift_graph *g, const gift_filter_spec *spec, const float *g_in, int S,
                  float *g_out, int mem, cudaStream_t st, float *mirror = nullptr);
+// Sets *flag (device) to 1 when any of the n floats at x (device, 16-byte
+// aligned) is NaN or infinite; queued on st.
+void scan_nonfinite(gift_ctx *ctx, const float *x, int64_t n, int32_t *flag, cudaStream_t st);
 // The device-usable address of page-locked (pinned or registered) host memory
 // of `bytes` bytes, 16-byte aligned; nullptr for any other memory.
 float *host_mirror(void *p, size_t bytes);

@@ -29,7 +29,8 @@ extern "C" gift_status gift_run(gift_ctx *ctx, const gift_netlist *netlist, cons
             if (!ctx->side) GIFT_CUDA(cudaStreamCreateWithFlags(&ctx->side, cudaStreamNonBlocking));
         }
         const size_t bytes = sizeof(float) * (size_t)netlist->num_cells * 2 * num_signals;
-        DevBuf din(ctx, bytes, st), dout(ctx, bytes, st);
+        DevBuf din(ctx, bytes, st), dout(ctx, bytes, st), bad(ctx, sizeof(int32_t), st);
+        GIFT_CUDA(cudaMemsetAsync(bad.p, 0, sizeof(int32_t), st));
         cudaEvent_t ready = nullptr, loaded = nullptr;
         GIFT_CUDA(cudaEventCreateWithFlags(&ready, cudaEventDisableTiming));
         struct Events {
@@ -49,6 +50,8 @@ extern "C" gift_status gift_run(gift_ctx *ctx, const gift_netlist *netlist, cons
             std::lock_guard<std::mutex> lk(ctx->side_mu);
             GIFT_CUDA(cudaStreamWaitEvent(ctx->side, ready, 0));
             GIFT_CUDA(cudaMemcpyAsync(din.p, g_in, bytes, cudaMemcpyHostToDevice, ctx->side));
+            scan_nonfinite(ctx, din.as<float>(), (int64_t)netlist->num_cells * 2 * num_signals, bad.as<int32_t>(),
+                           ctx->side);
             GIFT_CUDA(cudaEventRecord(loaded, ctx->side));
             queued = true;
         };
@@ -75,7 +78,12 @@ extern "C" gift_status gift_run(gift_ctx *ctx, const gift_netlist *netlist, cons
             }
         } gown{g, st};
         if (!queued) upload();
+        // a signal with a NaN or an infinity is rejected before the filter runs
         GIFT_CUDA(cudaStreamWaitEvent(st, loaded, 0));
+        int32_t hbad = 0;
+        GIFT_CUDA(cudaMemcpyAsync(&hbad, bad.p, sizeof(int32_t), cudaMemcpyDeviceToHost, st));
+        GIFT_CUDA(cudaStreamSynchronize(st));
+        GIFT_REQUIRE(!hbad, "gift_run: g_in holds a NaN or an infinity");
         // g_out in page-locked host memory: the last sweep stores the result
         // there as it goes; otherwise it goes down on the side stream while
         // HPWL reads the device copy on st

@@ -210,3 +210,29 @@ def test_results_written_straight_to_pinned_host_memory(ctx, batch):
             np.testing.assert_array_equal(out_p, ref)
     finally:
         gift.gift_graph_free(h)
+
+
+def test_nonfinite_host_signals_rejected(ctx, batch):
+    """A NaN or an infinity in a host signal: GIFT_ERR_INVALID from gift_filter
+    (host memory) and gift_run, the output left untouched, the context
+    usable afterwards."""
+    nl, g = batch[0]
+    h = gift.gift_build_graph(ctx, nl.num_cells, nl.net_ptr, nl.pin_cell, nl.is_fixed)
+    try:
+        for val in (np.nan, np.inf, -np.inf):
+            bad = g.copy()
+            bad[nl.num_cells // 2, 0, 1] = val
+            out = np.full_like(g, 7.0)
+            with pytest.raises(gift.GiftError) as e:
+                gift.gift_filter(ctx, h, bad, out)
+            assert e.value.status == gift.GIFT_ERR_INVALID
+            assert np.all(out == 7.0)
+            with pytest.raises(gift.GiftError) as e:
+                gift.gift_run(ctx, nl.num_cells, nl.net_ptr, nl.pin_cell, nl.is_fixed, bad, out)
+            assert e.value.status == gift.GIFT_ERR_INVALID
+            assert np.all(out == 7.0)
+        ref = np.empty_like(g)
+        gift.gift_filter(ctx, h, g, ref)
+        assert np.all(np.isfinite(ref))
+    finally:
+        gift.gift_graph_free(h)
