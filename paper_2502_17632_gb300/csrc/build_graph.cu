@@ -30,7 +30,20 @@ constexpr int kRowsWarps = 8;      // warps per block in the warp tier
 constexpr int kBlockCap = 16384;   // keys in shared memory in the block tier (128 KiB)
 constexpr int kBlockThreads = 512;
 constexpr uint64_t kPadKey = ~0ull;
-constexpr int64_t kPadFraction = 1024;  // keep the padded raw layout when at most 1/1024 of it is padding
+constexpr int64_t kPadFraction = 1024;
+
+// Sub-buffers of one device allocation, each 256-byte aligned: the build's
+// temporaries come from two such arenas (one allocation, one memset each
+// instead of one per array), which matters when the graph is small and the
+// build is bound by host calls.
+struct Carve {
+    size_t off = 0;
+    size_t take(size_t bytes) {
+        const size_t o = off;
+        off += (bytes + 255) & ~(size_t)255;
+        return o;
+    }
+};  // keep the padded raw layout when at most 1/1024 of it is padding
 
 __device__ __forceinline__ uint64_t make_key(int32_t cell, int32_t net) {
     return (static_cast<uint64_t>(static_cast<uint32_t>(cell)) << 32) | static_cast<uint32_t>(net);
@@ -933,10 +946,23 @@ void build_graph_impl(gift_ctx *ctx, const gift_netlist *nl, const gift_build_op
     const int64_t *src_np = g->net_ptr;
     const int32_t *src_pc = g->pin_cell;
 
+    // ---- temporaries before the totals are known: the summary and the
+    // counters (zeroed together), the per-net weights, the incidence offsets
+    Carve ca;
+    const size_t o_sum = ca.take(sizeof(unsigned long long) * kSumSize), o_cnt = ca.take(sizeof(int32_t) * N),
+                 o_rawlen = ca.take(sizeof(int64_t) * N);
+    const size_t zeroed_a = ca.off;
+    const size_t o_wnet = ca.take(sizeof(double) * std::max(E, 1)), o_inc = ca.take(sizeof(int64_t) * (N + 1));
+    DevBuf arena_a(ctx, ca.off, st);
+    char *A = static_cast<char *>(arena_a.p);
+    unsigned long long *sum_d = reinterpret_cast<unsigned long long *>(A + o_sum);
+    int32_t *cnt_p = reinterpret_cast<int32_t *>(A + o_cnt);
+    unsigned long long *rawlen_p = reinterpret_cast<unsigned long long *>(A + o_rawlen);
+    double *wnet_p = reinterpret_cast<double *>(A + o_wnet);
+    int64_t *inc_ptr_p = reinterpret_cast<int64_t *>(A + o_inc);
+    GIFT_CUDA(cudaMemsetAsync(A, 0, zeroed_a, st));
+
     // ---- validate on the device
-    DevBuf summary(ctx, sizeof(unsigned long long) * kSumSize, st);
-    unsigned long long *sum_d = summary.as<unsigned long long>();
-    GIFT_CUDA(cudaMemsetAsync(summary.p, 0, sizeof(unsigned long long) * kSumSize, st));
     {
         LaunchTimer lt(ctx, st, "build.validate", 8.0 * (E + 1) + 4.0 * P);
         k_validate<<<grid_for(ctx, std::max<int64_t>({(int64_t)E, (int64_t)N, P}), 256), 256, 0, st>>>(
@@ -945,31 +971,25 @@ void build_graph_impl(gift_ctx *ctx, const gift_netlist *nl, const gift_build_op
     }
 
     // ---- count incidences and raw pairs per cell
-    DevBuf wnet(ctx, sizeof(double) * std::max(E, 1), st);
-    DevBuf cnt(ctx, sizeof(int32_t) * N, st);
-    DevBuf rawlen(ctx, sizeof(int64_t) * N, st);
-    GIFT_CUDA(cudaMemsetAsync(cnt.p, 0, sizeof(int32_t) * N, st));
-    GIFT_CUDA(cudaMemsetAsync(rawlen.p, 0, sizeof(int64_t) * N, st));
     if (E > 0) {
         LaunchTimer lt(ctx, st, "build.count", 16.0 * (E + 1) + 4.0 * P + 12.0 * N, 2);
-        k_net_weights<<<grid_for(ctx, E, 256), 256, 0, st>>>(E, src_np, ctx->wtab, wnet.as<double>());
-        k_count<<<grid_for(ctx, E, 256), 256, 0, st>>>(E, N, src_np, src_pc, imin, cnt.as<int32_t>(),
-                                                         rawlen.as<unsigned long long>());
+        k_net_weights<<<grid_for(ctx, E, 256), 256, 0, st>>>(E, src_np, ctx->wtab, wnet_p);
+        k_count<<<grid_for(ctx, E, 256), 256, 0, st>>>(E, N, src_np, src_pc, imin, cnt_p,
+                                                         rawlen_p);
         check_launch("k_count");
     }
-    DevBuf inc_ptr(ctx, sizeof(int64_t) * (N + 1), st);
-    DevBuf raw_ptr(ctx, sizeof(int64_t) * (N + 1), st);
+    DevBuf raw_ptr(ctx, sizeof(int64_t) * (N + 1), st);  // may become the graph's row_ptr
     {
         LaunchTimer lt(ctx, st, "build.scan", 4.0 * N + 8.0 * N + 16.0 * (N + 1), 6);
-        exclusive_scan(ctx, cnt.as<int32_t>(), inc_ptr.as<int64_t>(), N, st);
-        exclusive_scan(ctx, rawlen.as<int64_t>(), raw_ptr.as<int64_t>(), N, st);
+        exclusive_scan(ctx, cnt_p, inc_ptr_p, N, st);
+        exclusive_scan(ctx, reinterpret_cast<int64_t *>(rawlen_p), raw_ptr.as<int64_t>(), N, st);
     }
     {
         LaunchTimer lt(ctx, st, "build.maxraw", 8.0 * (N + 1));
         k_max_rawlen<<<grid_for(ctx, N, 256), 256, 0, st>>>(N, raw_ptr.as<int64_t>(), sum_d + kSumMaxRaw);
         check_launch("k_max_rawlen");
     }
-    GIFT_CUDA(cudaMemcpyAsync(sum_d + kSumInc, inc_ptr.as<int64_t>() + N, sizeof(int64_t), cudaMemcpyDeviceToDevice,
+    GIFT_CUDA(cudaMemcpyAsync(sum_d + kSumInc, inc_ptr_p + N, sizeof(int64_t), cudaMemcpyDeviceToDevice,
                               st));
     GIFT_CUDA(cudaMemcpyAsync(sum_d + kSumRaw, raw_ptr.as<int64_t>() + N, sizeof(int64_t), cudaMemcpyDeviceToDevice,
                               st));
@@ -983,26 +1003,38 @@ void build_graph_impl(gift_ctx *ctx, const gift_netlist *nl, const gift_build_op
     const int64_t ninc = (int64_t)hs[kSumInc], nraw = (int64_t)hs[kSumRaw], maxraw = (int64_t)hs[kSumMaxRaw];
     g->raw_pairs = nraw;
 
+    // ---- temporaries once the totals are known: the fill counters and the
+    // tier counts (zeroed together), incidence lists, row lists, unique
+    // counts and the per-net stored weights
+    const size_t wsz = g->weight_dtype == GIFT_WEIGHT_F32 ? 4 : 2;
+    Carve cb;
+    const size_t o_fill = cb.take(sizeof(int32_t) * N), o_counts = cb.take(sizeof(int32_t) * 2);
+    const size_t zeroed_b = cb.off;
+    const size_t o_incnet = cb.take(sizeof(int32_t) * std::max<int64_t>(ninc, 1)),
+                 o_ucount = cb.take(sizeof(int32_t) * N), o_wlist = cb.take(sizeof(int32_t) * N),
+                 o_big = cb.take(sizeof(int32_t) * N), o_wst = cb.take(wsz * std::max(E, 1));
+    DevBuf arena_b(ctx, cb.off, st);
+    char *B = static_cast<char *>(arena_b.p);
+    int32_t *fill_p = reinterpret_cast<int32_t *>(B + o_fill);
+    int32_t *counts_p = reinterpret_cast<int32_t *>(B + o_counts);  // [0] warp-tier rows, [1] block-tier rows
+    int32_t *inc_net_p = reinterpret_cast<int32_t *>(B + o_incnet);
+    int32_t *ucount_p = reinterpret_cast<int32_t *>(B + o_ucount);
+    int32_t *wlist_p = reinterpret_cast<int32_t *>(B + o_wlist);
+    int32_t *big_p = reinterpret_cast<int32_t *>(B + o_big);
+    void *wst_p = B + o_wst;
+    GIFT_CUDA(cudaMemsetAsync(B, 0, zeroed_b, st));
+
     // ---- scatter nets to cells
-    DevBuf inc_net(ctx, sizeof(int32_t) * std::max<int64_t>(ninc, 1), st);
-    DevBuf fill(ctx, sizeof(int32_t) * N, st);
-    GIFT_CUDA(cudaMemsetAsync(fill.p, 0, sizeof(int32_t) * N, st));
     if (E > 0 && ninc > 0) {
         LaunchTimer lt(ctx, st, "build.scatter", 8.0 * (E + 1) + 4.0 * P + 8.0 * N + 4.0 * ninc + 4.0 * N);
-        k_scatter<<<grid_for(ctx, E, 256), 256, 0, st>>>(E, g->net_ptr, g->pin_cell, imin, inc_ptr.as<int64_t>(),
-                                                           fill.as<int32_t>(), inc_net.as<int32_t>());
+        k_scatter<<<grid_for(ctx, E, 256), 256, 0, st>>>(E, g->net_ptr, g->pin_cell, imin, inc_ptr_p,
+                                                           fill_p, inc_net_p);
         check_launch("k_scatter");
     }
 
     // ---- per-row expansion, sort, duplicate sums, rounding, degrees
-    const size_t wsz = g->weight_dtype == GIFT_WEIGHT_F32 ? 4 : 2;
-    DevBuf out_col(ctx, sizeof(int32_t) * std::max<int64_t>(nraw, 1), st);
-    DevBuf out_val(ctx, wsz * std::max<int64_t>(nraw, 1), st);
-    DevBuf ucount(ctx, sizeof(int32_t) * N, st);
-    DevBuf wlist(ctx, sizeof(int32_t) * N, st);
-    DevBuf big_rows(ctx, sizeof(int32_t) * N, st);
-    DevBuf counts(ctx, sizeof(int32_t) * 2, st);  // [0] warp-tier rows, [1] block-tier rows
-    GIFT_CUDA(cudaMemsetAsync(counts.p, 0, sizeof(int32_t) * 2, st));
+    DevBuf out_col(ctx, sizeof(int32_t) * std::max<int64_t>(nraw, 1), st);  // may become the graph's col
+    DevBuf out_val(ctx, wsz * std::max<int64_t>(nraw, 1), st);             // and val
     g->degree = (double *)dev_alloc(ctx, sizeof(double) * N, st);
     DevBuf gkeys;
     int64_t gcap = 0;
@@ -1014,33 +1046,33 @@ void build_graph_impl(gift_ctx *ctx, const gift_netlist *nl, const gift_build_op
     auto rows = [&](auto tag) {
         using WT = decltype(tag);
         WT *ov = out_val.as<WT>();
-        int32_t *wc = counts.as<int32_t>(), *bc = counts.as<int32_t>() + 1;
-        DevBuf wst(ctx, sizeof(WT) * std::max<int32_t>(E, 1), st);
+        int32_t *wc = counts_p, *bc = counts_p + 1;
+        WT *wst = static_cast<WT *>(wst_p);
         {
             LaunchTimer lt(ctx, st, "build.rows",
                            16.0 * N + 4.0 * ninc + 16.0 * ninc + 4.0 * nraw + (4.0 + wsz) * nraw + 12.0 * N);
             if (E > 0)
-                k_net_stored<WT><<<grid_for(ctx, E, 256), 256, 0, st>>>(E, wnet.as<double>(), wst.as<WT>());
+                k_net_stored<WT><<<grid_for(ctx, E, 256), 256, 0, st>>>(E, wnet_p, wst);
             if (N <= (1 << 27))
                 k_rows_lane<WT, uint32_t><<<grid_for(ctx, N, lane_threads<uint32_t>(), 6),
                                             lane_threads<uint32_t>(), 0, st>>>(
-                    N, inc_ptr.as<int64_t>(), inc_net.as<int32_t>(), g->net_ptr, g->pin_cell, ctx->wtab,
-                    raw_ptr.as<int64_t>(), out_col.as<int32_t>(), ov, ucount.as<int32_t>(), g->degree,
-                    wlist.as<int32_t>(), wc);
+                    N, inc_ptr_p, inc_net_p, g->net_ptr, g->pin_cell, ctx->wtab,
+                    raw_ptr.as<int64_t>(), out_col.as<int32_t>(), ov, ucount_p, g->degree,
+                    wlist_p, wc);
             else
                 k_rows_lane<WT, uint64_t><<<grid_for(ctx, N, lane_threads<uint64_t>(), 12),
                                             lane_threads<uint64_t>(), 0, st>>>(
-                    N, inc_ptr.as<int64_t>(), inc_net.as<int32_t>(), g->net_ptr, g->pin_cell, ctx->wtab,
-                    raw_ptr.as<int64_t>(), out_col.as<int32_t>(), ov, ucount.as<int32_t>(), g->degree,
-                    wlist.as<int32_t>(), wc);
+                    N, inc_ptr_p, inc_net_p, g->net_ptr, g->pin_cell, ctx->wtab,
+                    raw_ptr.as<int64_t>(), out_col.as<int32_t>(), ov, ucount_p, g->degree,
+                    wlist_p, wc);
             check_launch("k_rows_lane");
         }
         if (maxraw > kLaneCap) {
             LaunchTimer lt(ctx, st, "build.rows_warp", 0.0);
             k_rows_warp<WT><<<ctx->num_sms * 6, kRowsWarps * 32, 0, st>>>(
-                wlist.as<int32_t>(), wc, inc_ptr.as<int64_t>(), inc_net.as<int32_t>(), g->net_ptr, g->pin_cell,
-                wnet.as<double>(), wst.as<WT>(), raw_ptr.as<int64_t>(), out_col.as<int32_t>(), ov,
-                ucount.as<int32_t>(), g->degree, big_rows.as<int32_t>(), bc);
+                wlist_p, wc, inc_ptr_p, inc_net_p, g->net_ptr, g->pin_cell,
+                wnet_p, wst, raw_ptr.as<int64_t>(), out_col.as<int32_t>(), ov,
+                ucount_p, g->degree, big_p, bc);
             check_launch("k_rows_warp");
         }
         if (maxraw > kWarpCap) {
@@ -1053,18 +1085,18 @@ void build_graph_impl(gift_ctx *ctx, const gift_netlist *nl, const gift_build_op
                 int per_sm = 0;
                 GIFT_CUDA(cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, fn, kBlockThreads, smem));
                 k_rows_block<WT, false><<<ctx->num_sms * std::max(per_sm, 1), kBlockThreads, smem, st>>>(
-                    inc_ptr.as<int64_t>(), inc_net.as<int32_t>(), g->net_ptr, g->pin_cell, wnet.as<double>(),
-                    raw_ptr.as<int64_t>(), out_col.as<int32_t>(), ov, ucount.as<int32_t>(), g->degree,
-                    big_rows.as<int32_t>(), bc, nullptr, 0, lo, cap);
+                    inc_ptr_p, inc_net_p, g->net_ptr, g->pin_cell, wnet_p,
+                    raw_ptr.as<int64_t>(), out_col.as<int32_t>(), ov, ucount_p, g->degree,
+                    big_p, bc, nullptr, 0, lo, cap);
                 check_launch("k_rows_block");
             }
         }
         if (maxraw > kBlockCap) {
             LaunchTimer lt(ctx, st, "build.rows_global", 0.0);
             k_rows_block<WT, true><<<ctx->num_sms, kBlockThreads, 0, st>>>(
-                inc_ptr.as<int64_t>(), inc_net.as<int32_t>(), g->net_ptr, g->pin_cell, wnet.as<double>(),
-                raw_ptr.as<int64_t>(), out_col.as<int32_t>(), ov, ucount.as<int32_t>(), g->degree,
-                big_rows.as<int32_t>(), bc, gkeys.as<uint64_t>(), gcap, kBlockCap, kBlockCap);
+                inc_ptr_p, inc_net_p, g->net_ptr, g->pin_cell, wnet_p,
+                raw_ptr.as<int64_t>(), out_col.as<int32_t>(), ov, ucount_p, g->degree,
+                big_p, bc, gkeys.as<uint64_t>(), gcap, kBlockCap, kBlockCap);
             check_launch("k_rows_block<global>");
         }
     };
@@ -1122,14 +1154,14 @@ void build_graph_impl(gift_ctx *ctx, const gift_netlist *nl, const gift_build_op
         LaunchTimer lt(ctx, st, "build.finish", 24.0 * N + 4.0 * N + 8.0 * (N + 1));
         const int grid = grid_for(ctx, N, kCopyRows);
         if (g->weight_dtype == GIFT_WEIGHT_F32)
-            k_finish_rows<float><<<grid, kCopyRows, 0, st>>>(N, raw_ptr.as<int64_t>(), ucount.as<int32_t>(), g->degree,
+            k_finish_rows<float><<<grid, kCopyRows, 0, st>>>(N, raw_ptr.as<int64_t>(), ucount_p, g->degree,
                                                           out_col.as<int32_t>(), out_val.as<float>(), s2, s4, agg);
         else if (g->weight_dtype == GIFT_WEIGHT_BF16)
-            k_finish_rows<__nv_bfloat16><<<grid, kCopyRows, 0, st>>>(N, raw_ptr.as<int64_t>(), ucount.as<int32_t>(),
+            k_finish_rows<__nv_bfloat16><<<grid, kCopyRows, 0, st>>>(N, raw_ptr.as<int64_t>(), ucount_p,
                                                                   g->degree, out_col.as<int32_t>(),
                                                                   out_val.as<__nv_bfloat16>(), s2, s4, agg);
         else
-            k_finish_rows<__half><<<grid, kCopyRows, 0, st>>>(N, raw_ptr.as<int64_t>(), ucount.as<int32_t>(), g->degree,
+            k_finish_rows<__half><<<grid, kCopyRows, 0, st>>>(N, raw_ptr.as<int64_t>(), ucount_p, g->degree,
                                                            out_col.as<int32_t>(), out_val.as<__half>(), s2, s4, agg);
         check_launch("k_finish_rows");
     }
@@ -1149,7 +1181,7 @@ void build_graph_impl(gift_ctx *ctx, const gift_netlist *nl, const gift_build_op
         g->row_ptr = (int64_t *)dev_alloc(ctx, sizeof(int64_t) * (N + 1), st);
         {
             LaunchTimer lt(ctx, st, "build.scan", 4.0 * N + 8.0 * (N + 1), 3);
-            exclusive_scan(ctx, ucount.as<int32_t>(), g->row_ptr, N, st);
+            exclusive_scan(ctx, ucount_p, g->row_ptr, N, st);
         }
         g->col = (int32_t *)dev_alloc(ctx, sizeof(int32_t) * std::max<int64_t>(nnz, 1), st);
         g->val = dev_alloc(ctx, wsz * std::max<int64_t>(nnz, 1), st);
