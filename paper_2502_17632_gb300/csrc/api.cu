@@ -14,7 +14,7 @@ void clear_error() { g_last_error.clear(); }
 void *dev_alloc(gift_ctx *ctx, size_t bytes, cudaStream_t st) {
     if (bytes == 0) bytes = 16;
     if (ctx->fail_alloc_in > 0) {
-        if (--ctx->fail_alloc_in == 0)
+        if (ctx->fail_alloc_in.fetch_sub(1) == 1)
             throw Failure{GIFT_ERR_OOM, "device allocation failed (injected)"};
     }
     void *p = nullptr;
@@ -68,9 +68,16 @@ static cudaEvent_t take_event(gift_ctx *ctx) {
     return e;
 }
 
+namespace {
+thread_local int timer_pauses = 0;
+}
+
+TimerPause::TimerPause() { ++timer_pauses; }
+TimerPause::~TimerPause() { --timer_pauses; }
+
 LaunchTimer::LaunchTimer(gift_ctx *c, cudaStream_t s, const char *n, double alg_bytes, int k)
     : ctx(c), st(s), name(n), bytes(alg_bytes), kernels(k) {
-    if (!ctx->profiling) return;
+    if (!ctx->profiling || timer_pauses > 0) return;
     std::lock_guard<std::mutex> lk(ctx->prof_mu);
     a = take_event(ctx);
     b = take_event(ctx);
@@ -203,6 +210,7 @@ void gift_ctx_reset_stats(gift_ctx *ctx) {
 
 int32_t gift_ctx_last_schedule(gift_ctx *ctx, int32_t *per_kind) {
     if (!ctx) return 0;
+    std::lock_guard<std::mutex> lk(ctx->tune_mu);
     if (per_kind)
         for (int k = 0; k < 4; ++k) per_kind[k] = ctx->last_schedules[k];
     for (int k = 3; k >= 0; --k)

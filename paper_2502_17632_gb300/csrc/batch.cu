@@ -180,7 +180,6 @@ gift_status gift_filter_capture(gift_ctx *ctx, const gift_graph *graph, const gi
         GIFT_CUDA(cudaStreamCreateWithFlags(&cs, cudaStreamNonBlocking));
         auto ex = std::make_unique<gift_exec>();
         ex->ctx = ctx;
-        const bool prof = ctx->profiling;
         try {
             // one ordinary call first: tunes the shapes and builds the formats
             // they use, so the captured call allocates nothing and never waits
@@ -188,21 +187,21 @@ gift_status gift_filter_capture(gift_ctx *ctx, const gift_graph *graph, const gi
             const size_t bytes = filter_scratch_bytes(graph, spec, num_signals);
             GIFT_CUDA(cudaMalloc(&ex->scratch, bytes));
             GIFT_CUDA(cudaStreamSynchronize(cs));
-            ctx->profiling = false;
-            GIFT_CUDA(cudaStreamBeginCapture(cs, cudaStreamCaptureModeThreadLocal));
-            try {
-                filter_on_scratch(ctx, graph, spec, g_in, num_signals, g_out, ex->scratch, bytes, cs);
-            } catch (...) {
-                cudaGraph_t broken = nullptr;
-                cudaStreamEndCapture(cs, &broken);
-                if (broken) cudaGraphDestroy(broken);
-                throw;
+            {
+                TimerPause pause;  // no timing events inside the capture
+                GIFT_CUDA(cudaStreamBeginCapture(cs, cudaStreamCaptureModeThreadLocal));
+                try {
+                    filter_on_scratch(ctx, graph, spec, g_in, num_signals, g_out, ex->scratch, bytes, cs);
+                } catch (...) {
+                    cudaGraph_t broken = nullptr;
+                    cudaStreamEndCapture(cs, &broken);
+                    if (broken) cudaGraphDestroy(broken);
+                    throw;
+                }
+                GIFT_CUDA(cudaStreamEndCapture(cs, &ex->graph));
             }
-            GIFT_CUDA(cudaStreamEndCapture(cs, &ex->graph));
-            ctx->profiling = prof;
             GIFT_CUDA(cudaGraphInstantiate(&ex->exec, ex->graph, 0));
         } catch (...) {
-            ctx->profiling = prof;
             if (ex->exec) cudaGraphExecDestroy(ex->exec);
             if (ex->graph) cudaGraphDestroy(ex->graph);
             if (ex->scratch) cudaFree(ex->scratch);

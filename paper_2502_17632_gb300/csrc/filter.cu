@@ -748,15 +748,13 @@ ShapeSet autotune(gift_ctx *ctx, const Plan &p, cudaStream_t st) {
                         }
                     }
     }
-    const bool prof = ctx->profiling;
-    ctx->profiling = false;
+    TimerPause pause;  // the trial runs are not the caller's launches
     std::vector<cudaEvent_t> pool;
     double best_ms[4] = {1e30, 1e30, 1e30, 1e30};
     ShapeSet best;
     for (auto &k : best.kind) k = cands.front();
     auto cleanup = [&] {
         for (auto e : pool) cudaEventDestroy(e);
-        ctx->profiling = prof;
     };
     // one warm run and one timed run of the whole filter; per planned kind ms
     auto measure = [&](const ShapeSet &ss, double (&ms)[4], bool (&seen)[4]) {
@@ -990,12 +988,15 @@ void filter_impl(gift_ctx *ctx, const gift_graph *cg, const gift_filter_spec *sp
     p.mirror = mirror;
     GIFT_CUDA(cudaMemsetAsync(p.counters, 0, sizeof(int32_t) * p.ncounters, st));
     const int used = run_sweeps(ctx, p, ss, st);
-    for (int kd = 0; kd < 4; ++kd) {
-        // a split two-chain kind reports 10000 + the one-chain kind's code
-        const bool split = kd < 2 && ss.split[kd];
-        ctx->last_schedules[kd] = !(used >> kd & 1) ? 0
-                                  : split           ? 10000 + schedule_code(ss.kind[kd + 2])
-                                                    : schedule_code(ss.kind[kd]);
+    {
+        std::lock_guard<std::mutex> lk(ctx->tune_mu);
+        for (int kd = 0; kd < 4; ++kd) {
+            // a split two-chain kind reports 10000 + the one-chain kind's code
+            const bool split = kd < 2 && ss.split[kd];
+            ctx->last_schedules[kd] = !(used >> kd & 1) ? 0
+                                      : split           ? 10000 + schedule_code(ss.kind[kd + 2])
+                                                        : schedule_code(ss.kind[kd]);
+        }
     }
 
     if (mem == GIFT_MEM_HOST) {

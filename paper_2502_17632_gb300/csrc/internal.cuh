@@ -8,6 +8,7 @@
 
 #include <cstdint>
 #include <cstdio>
+#include <atomic>
 #include <functional>
 #include <map>
 #include <mutex>
@@ -97,9 +98,9 @@ struct gift_ctx {
     int max_smem_optin = 0;
     cudaMemPool_t pool = nullptr;
     // fault injection: countdown to a failing allocation (0 = off)
-    int fail_alloc_in = 0;
+    std::atomic<int> fail_alloc_in{0};
     // profiling
-    bool profiling = false;
+    std::atomic<bool> profiling{false};
     std::mutex prof_mu;
     std::map<std::string, gift::KernelRecord> records;
     std::vector<gift::PendingTiming> pending;
@@ -107,7 +108,7 @@ struct gift_ctx {
     // autotuned sweep shapes by graph/signal shape key: (family, a, b)
     std::mutex tune_mu;
     std::map<std::string, gift::TunedSet> tuned;
-    int last_schedules[4] = {0, 0, 0, 0};
+    int last_schedules[4] = {0, 0, 0, 0};  // guarded by tune_mu (filter calls may run on several threads)
     // device word set by kernels whose bounded waits ran out (0 = fine)
     int32_t *dev_error = nullptr;
     // wtab[m] = 2/m in FP64 for m in [2, kWeightTable] (0 below), filled on the host
@@ -153,6 +154,13 @@ struct DevBuf {
     T *as() const { return static_cast<T *>(p); }
 };
 
+// Launch timing: wraps one kernel launch in events when profiling is on and
+// this thread is not inside a TimerPause (the autotuner's trial runs, a
+// CUDA-graph capture).
+struct TimerPause {
+    TimerPause();
+    ~TimerPause();
+};
 // Launch timing: wraps one kernel launch in events when profiling is on.
 struct LaunchTimer {
     gift_ctx *ctx;

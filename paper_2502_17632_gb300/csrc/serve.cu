@@ -36,13 +36,63 @@ constexpr int32_t kServeSchedule = 4244;  // direct row groups, natural row orde
 
 enum ReqState { kWaiting, kRunning, kDone, kFailed };
 
+// Page-locked host buffers reused across requests, in power-of-two size
+// classes: a request's signal goes up and its result comes down at the
+// link's full rate, the last sweep writes the result into its buffer
+// directly (no copy after the filter), and no request pays for pinning or
+// for zero-filling a fresh buffer once the pool is warm.
+struct PinnedPool {
+    std::mutex mu;
+    std::map<size_t, std::vector<void *>> free_;
+    static size_t size_class(size_t bytes) {
+        size_t c = (size_t)1 << 16;
+        while (c < bytes) c <<= 1;
+        return c;
+    }
+    void *take(size_t bytes) {
+        const size_t c = size_class(bytes);
+        {
+            std::lock_guard<std::mutex> lk(mu);
+            auto &v = free_[c];
+            if (!v.empty()) {
+                void *p = v.back();
+                v.pop_back();
+                return p;
+            }
+        }
+        void *p = nullptr;
+        if (cudaHostAlloc(&p, c, cudaHostAllocDefault) != cudaSuccess) {
+            cudaGetLastError();
+            throw Failure{GIFT_ERR_OOM, "gift_serve: page-locked host allocation failed"};
+        }
+        return p;
+    }
+    void give(void *p, size_t bytes) {
+        if (!p) return;
+        std::lock_guard<std::mutex> lk(mu);
+        free_[size_class(bytes)].push_back(p);
+    }
+    ~PinnedPool() {
+        for (auto &kv : free_)
+            for (void *p : kv.second) cudaFreeHost(p);
+    }
+};
+
 struct Request {
     uint64_t ticket = 0;
     int32_t n = 0, e = 0, S = 0, weight_dtype = GIFT_WEIGHT_F32;
     std::vector<int64_t> net_ptr;
     std::vector<int32_t> pin_cell;
     std::vector<uint8_t> is_fixed;
-    std::vector<float> g_in, g_out;
+    PinnedPool *pool = nullptr;
+    size_t sig_bytes = 0;
+    float *g_in = nullptr, *g_out = nullptr;  // page-locked, from the pool
+    ~Request() {
+        if (pool) {
+            pool->give(g_in, sig_bytes);
+            pool->give(g_out, sig_bytes);
+        }
+    }
     std::vector<double> hpwl;
     int64_t footprint = 0, nnz = 0;
     ReqState state = kWaiting;
@@ -73,6 +123,7 @@ using namespace gift;
 struct gift_server {
     gift_serve_opts opts;
     gift_ctx *ctx = nullptr;
+    PinnedPool pinned;  // declared before reqs: outlives every request
     int chains = 1;
     std::mutex mu;
     std::condition_variable cv_work, cv_done;
@@ -120,20 +171,22 @@ void gift_server::run(Request &r, cudaStream_t st) {
     });
     g->home = st;
     r.nnz = g->nnz;
-    const size_t sig_bytes = sizeof(float) * (size_t)r.n * 2 * r.S;
+    const size_t sig_bytes = r.sig_bytes;
     DevBuf din(ctx, sig_bytes, st), dout(ctx, sig_bytes, st);
-    GIFT_CUDA(cudaMemcpyAsync(din.p, r.g_in.data(), sig_bytes, cudaMemcpyHostToDevice, st));
+    GIFT_CUDA(cudaMemcpyAsync(din.p, r.g_in, sig_bytes, cudaMemcpyHostToDevice, st));
     gift_filter_spec spec = opts.spec;
     if (spec.schedule == 0) spec.schedule = kServeSchedule;
-    filter_impl(ctx, g, &spec, din.as<float>(), r.S, dout.as<float>(), GIFT_MEM_DEVICE, st);
+    r.g_out = static_cast<float *>(pinned.take(sig_bytes));
+    float *mirror = host_mirror(r.g_out, sig_bytes);  // the last sweep stores the result into it
+    filter_impl(ctx, g, &spec, din.as<float>(), r.S, dout.as<float>(), GIFT_MEM_DEVICE, st, mirror);
     if (opts.compute_hpwl) {
         r.hpwl.assign(r.S, 0.0);
         hpwl_impl(ctx, g, dout.as<float>(), r.S, r.hpwl.data(), GIFT_MEM_DEVICE, st);
     }
-    r.g_out.resize((size_t)r.n * 2 * r.S);
-    GIFT_CUDA(cudaMemcpyAsync(r.g_out.data(), dout.p, sig_bytes, cudaMemcpyDeviceToHost, st));
-    GIFT_CUDA(cudaStreamSynchronize(st));
-    check_device_error(ctx);
+    if (!mirror) GIFT_CUDA(cudaMemcpyAsync(r.g_out, dout.p, sig_bytes, cudaMemcpyDeviceToHost, st));
+    sync_and_check(ctx, st);
+    pinned.give(r.g_in, sig_bytes);  // the input is on the device now
+    r.g_in = nullptr;
 }
 
 void gift_server::worker(int w) {
@@ -282,8 +335,12 @@ gift_status gift_serve_submit(gift_server *srv, const gift_netlist *nl, const fl
             GIFT_REQUIRE(c >= 0 && c < nl->num_cells, "gift_serve_submit: pin cell out of range");
         if (nl->is_fixed) r->is_fixed.assign(nl->is_fixed, nl->is_fixed + nl->num_cells);
         else r->is_fixed.assign(nl->num_cells, 0);
-        r->g_in.assign(g_in, g_in + (size_t)nl->num_cells * 2 * S);
-        for (float v : r->g_in) GIFT_REQUIRE(std::isfinite(v), "gift_serve_submit: g_in must be finite");
+        const size_t count = (size_t)nl->num_cells * 2 * S;
+        for (size_t i = 0; i < count; ++i) GIFT_REQUIRE(std::isfinite(g_in[i]), "gift_serve_submit: g_in must be finite");
+        r->pool = &srv->pinned;
+        r->sig_bytes = sizeof(float) * count;
+        r->g_in = static_cast<float *>(srv->pinned.take(r->sig_bytes));
+        std::memcpy(r->g_in, g_in, r->sig_bytes);
         r->footprint = footprint_bytes(nl->num_cells, nl->num_nets, P, R, S, wd, srv->chains);
         GIFT_REQUIRE(r->footprint <= srv->opts.hbm_budget_bytes,
                      "gift_serve_submit: the request's footprint exceeds the server's HBM budget");
@@ -333,7 +390,7 @@ static gift_status take_result(gift_server *srv, std::unique_lock<std::mutex> &l
         set_error(own->error);
         return own->status;
     }
-    if (g_out) std::memcpy(g_out, own->g_out.data(), sizeof(float) * own->g_out.size());
+    if (g_out) std::memcpy(g_out, own->g_out, own->sig_bytes);
     if (hpwl) {
         for (int s = 0; s < own->S; ++s) hpwl[s] = s < (int)own->hpwl.size() ? own->hpwl[s] : 0.0;
     }
