@@ -26,18 +26,40 @@ namespace gift {
 // float4 gathers in flight, 24 otherwise (the first sweep's scale gathers,
 // the two-gather loops and the float2 lanes need the extra four; checked
 // against ptxas spill reports for all three weight types).
-constexpr int dr_regs(int vec, int u, int nc, int nx, bool first) {
-    return u * nx * vec + nc * vec + 2 * u + (!first && u == 4 && vec == 4 ? 20 : 24);
+// Warp rows hold the next step's U (col, val) pairs as well.
+constexpr int dr_regs(int vec, int u, int nc, int nx, bool first, bool wr) {
+    return u * nx * vec + nc * vec + 2 * u + (wr ? 2 * u + 24 : (!first && u == 4 && vec == 4 ? 20 : 24));
 }
-constexpr int dr_min_blocks(int vec, int u, int nc, int nx, bool first) {
-    return dr_regs(vec, u, nc, nx, first) <= 32   ? 8
-           : dr_regs(vec, u, nc, nx, first) <= 40 ? 6
-           : dr_regs(vec, u, nc, nx, first) <= 48 ? 5
-           : dr_regs(vec, u, nc, nx, first) <= 64 ? 4
-                                                  : 3;
+constexpr int dr_min_blocks(int vec, int u, int nc, int nx, bool first, bool wr) {
+    return dr_regs(vec, u, nc, nx, first, wr) <= 32   ? 8
+           : dr_regs(vec, u, nc, nx, first, wr) <= 40 ? 6
+           : dr_regs(vec, u, nc, nx, first, wr) <= 48 ? 5
+           : dr_regs(vec, u, nc, nx, first, wr) <= 64 ? 4
+                                                      : 3;
 }
 
-// Neumaier's compensated addition: s + e tracks the running sum exactly up
+// U (col, val) pairs of a row: entries k0, k0 + ns, ..., those at or past ke
+// read as (0, 0).
+template <int U>
+struct DrIdx {
+    int32_t j[U];
+    float w[U];
+};
+
+template <typename WT, int U>
+__device__ __forceinline__ DrIdx<U> dr_load_idx(const SweepArgs &a, int64_t k0, int64_t ke, int ns) {
+    DrIdx<U> r;
+#pragma unroll
+    for (int u = 0; u < U; ++u) {
+        const int64_t k = k0 + (int64_t)u * ns;
+        const bool in = k < ke;
+        r.j[u] = in ? __ldg(a.col + k) : 0;
+        r.w[u] = in ? ld_weight_plain<WT>(a.val, k) : 0.f;
+    }
+    return r;
+}
+
+// Neumaier's compensated addition// Neumaier's compensated addition: s + e tracks the running sum exactly up
 // to the rounding of e itself.
 __device__ __forceinline__ void comp_add(float &s, float &e, float x) {
     const float t = s + x;
@@ -52,7 +74,7 @@ __device__ __forceinline__ void comp_add(float &s, float &e, float x) {
 // over the groups; for rows of hundreds to thousands of nonzeros.
 // COMP (with WR): compensated FP32 sums (Neumaier) per lane and in the tree.
 template <typename WT, int VEC, int CW, int U, int NC, bool FIRST, bool WR = false, bool COMP = false>
-__global__ void __launch_bounds__(kSweepThreads, dr_min_blocks(VEC, U, (COMP ? 2 : 1) * NC, FIRST ? 1 : NC, FIRST))
+__global__ void __launch_bounds__(kSweepThreads, dr_min_blocks(VEC, U, (COMP ? 2 : 1) * NC, FIRST ? 1 : NC, FIRST, WR))
 k_sweep_dr(const SweepArgs a) {
     static_assert(CW >= 1 && CW <= 32 && 32 % CW == 0, "lanes per row divide the warp");
     static_assert(WR || !COMP, "compensated sums come with warp rows");
@@ -85,16 +107,16 @@ k_sweep_dr(const SweepArgs a) {
             kb = __ldg(a.row_ptr + row);
             ke = __ldg(a.row_ptr + row + 1);
         }
+        // Warp rows (rows of hundreds to thousands of nonzeros): the next
+        // step's (col, val) are loaded while this step's rows are gathered,
+        // so the CSR stream's DRAM latency overlaps the gathers.
+        DrIdx<U> nx;
+        if (WR) nx = dr_load_idx<WT, U>(a, kb + ns, ke, NS);
         for (int64_t k0 = kb + ns; k0 < ke; k0 += (int64_t)NS * U) {
-            int32_t j[U];
-            float w[U];
-#pragma unroll
-            for (int u = 0; u < U; ++u) {
-                const int64_t k = k0 + (int64_t)u * NS;
-                const bool in = k < ke;
-                j[u] = in ? __ldg(a.col + k) : 0;
-                w[u] = in ? ld_weight_plain<WT>(a.val, k) : 0.f;
-            }
+            const DrIdx<U> cur = WR ? nx : dr_load_idx<WT, U>(a, k0, ke, NS);
+            if (WR) nx = dr_load_idx<WT, U>(a, k0 + (int64_t)NS * U, ke, NS);
+            const int32_t(&j)[U] = cur.j;
+            const float(&w)[U] = cur.w;
             float xv[U][NX][VEC];
 #pragma unroll
             for (int u = 0; u < U; ++u) {
