@@ -1,96 +1,214 @@
 """The pins catch plausible oracle mistakes.
 
-Each case compiles a copy of the oracle source with one planted mistake into a
-temporary directory (the committed oracle is untouched) and checks that at
-least one pin -- the hand-derived K_M closed form or the dense brute force --
-rejects the mutant.
+Each case plants one mistake in a copy of the oracle (the committed oracle is
+untouched) and runs every pin of tests/test_oracle_pins.py and
+tests/test_oracle_eigen.py, with all their parameters, against the copy: at
+least one pin must fail.  C mistakes are compiled from a patched copy of
+gift_oracle.c into a temporary directory and swapped in as the oracle's
+library; Python mistakes are executed from a patched copy of the package
+source and their functions swapped into the ``oracle`` module.  Every planted
+mistake keeps its memory accesses in bounds.
 """
 import ctypes as C
+import itertools
 import os
 import subprocess
+import sys
+import types
+import warnings
 
-import numpy as np
 import pytest
 
 import oracle
-from paper_2502_17632_gb300 import synth
+from tests import test_oracle_eigen, test_oracle_pins
 
-SRC = os.path.join(os.path.dirname(oracle.__file__), "gift_oracle.c")
+C_SRC = os.path.join(os.path.dirname(oracle.__file__), "gift_oracle.c")
+PY_SRC = os.path.join(os.path.dirname(oracle.__file__), "__init__.py")
 
-MUTANTS = {
-    # weight rule: the classic clique weight 1/(M-1) instead of 2/M
-    "weight_1_over_m_minus_1": ("double w = 2.0 / (double)m;", "double w = 1.0 / (double)(m - 1);"),
-    # self-loop dropped from A + sigma I
-    "no_self_loop": ("acc += sigma * si * x[(int64_t)i * K + c];", "acc += 0.0;"),
-    # normaliser D instead of D + sigma I
-    "scale_without_sigma": ("double sj = 1.0 / sqrt(d[j] + sigma);", "double sj = 1.0 / sqrt(d[j] + 1e-300);"),
-    # wrong sign of the neighbour sum
-    "neighbour_sign": ("acc += val[k] * sj * x[(int64_t)j * K + c];", "acc -= val[k] * sj * x[(int64_t)j * K + c];"),
-    # own row used instead of the neighbour (wrong index)
-    "wrong_index": ("acc += val[k] * sj * x[(int64_t)j * K + c];", "acc += val[k] * sj * x[(int64_t)i * K + c];"),
-    # one application short for every term
-    "power_off_by_one": ("for (int32_t p = 0; p < power[term]; ++p)", "for (int32_t p = 1; p < power[term]; ++p)"),
-    # self pairs kept
-    "self_pairs_kept": ("if (i == j) continue;", "if (0) continue;"),
-    # fixed rows not reimposed
-    "no_reimpose": ("if (reimpose && is_fixed)", "if (0)"),
+# name -> [(text, replacement, occurrence)] applied to gift_oracle.c
+C_MUTANTS = {
+    # clique expansion (Sec. 3.2.3, weight rule after Eq. 4)
+    "weight_1_over_m_minus_1": [("double w = 2.0 / (double)m;", "double w = 1.0 / (double)(m - 1);", 0)],
+    "self_pairs_kept": [("if (i == j) continue;", "if (0) continue;", 0)],
+    "duplicates_overwritten": [("g->val[nnz - 1] += pairs[t].w;", "g->val[nnz - 1] = pairs[t].w;", 0)],
+    "columns_descending": [("if (a->j != b->j) return a->j < b->j ? -1 : 1;",
+                            "if (a->j != b->j) return a->j > b->j ? -1 : 1;", 0)],
+    "cut_off_by_one": [("if (m >= 2 && (cut <= 0 || m < cut)) npairs", "if (m >= 2 && (cut <= 0 || m <= cut)) npairs", 0),
+                       ("if (cut > 0 && m >= cut) continue;", "if (cut > 0 && m > cut) continue;", 0)],
+    "accepts_decreasing_net_ptr": [("if (m < 0) return NULL;", "if (m < 0) continue;", 0)],
+    # implicit clique degrees
+    "implicit_weight": [("double w = 2.0 / (double)m;", "double w = 1.0 / (double)(m - 1);", 1)],
+    "implicit_ignores_repeats": [("d[cells[r]] += ((double)k * w) * (double)(m - k);",
+                                  "d[cells[r]] += ((double)k * w) * (double)(m - 1);", 0)],
+    "implicit_cut_off_by_one": [("if (m < 2 || m < cut) continue;", "if (m < 2 || m <= cut) continue;", 0)],
+    # degrees (Sec. 2.1)
+    "degree_drops_first_entry": [("for (int64_t k = row_ptr[i]; k < row_ptr[i + 1]; ++k) s += val[k];",
+                                  "for (int64_t k = row_ptr[i] + 1; k < row_ptr[i + 1]; ++k) s += val[k];", 0)],
+    # storage rounding
+    "round_truncates": [("return nearbyint(v / ulp) * ulp;", "return trunc(v / ulp) * ulp;", 0)],
+    "round_ties_away": [("return nearbyint(v / ulp) * ulp;", "return round(v / ulp) * ulp;", 0)],
+    "round_one_bit_short": [("double ulp = ldexp(1.0, lead - (prec - 1));",
+                             "double ulp = ldexp(1.0, lead - (prec - 2));", 0)],
+    "f16_without_subnormals": [("case 3: out[t] = round_to(in[t], 11, -14);", "case 3: out[t] = round_to(in[t], 11, -126);", 0)],
+    # augmented normalised adjacency (Eq. 16)
+    "no_self_loop": [("acc += sigma * si * x[(int64_t)i * K + c];", "acc += 0.0;", 0)],
+    "scale_without_sigma": [("double sj = 1.0 / sqrt(d[j] + sigma);", "double sj = 1.0 / sqrt(d[j] + 1e-300);", 0)],
+    "neighbour_sign": [("acc += val[k] * sj * x[(int64_t)j * K + c];", "acc -= val[k] * sj * x[(int64_t)j * K + c];", 0)],
+    "wrong_index": [("acc += val[k] * sj * x[(int64_t)j * K + c];", "acc += val[k] * sj * x[(int64_t)i * K + c];", 0)],
+    "missing_post_scale": [("y[(int64_t)i * K + c] = si * acc;", "y[(int64_t)i * K + c] = acc;", 0)],
+    "random_walk_normaliser": [("y[(int64_t)i * K + c] = acc / (d[i] + sigma);", "y[(int64_t)i * K + c] = acc / (d[i] + 1.0);", 0)],
+    # the filter (Eq. 15) and the fixed cells
+    "power_off_by_one": [("for (int32_t p = 0; p < power[term]; ++p)", "for (int32_t p = 1; p < power[term]; ++p)", 0)],
+    "terms_chained": [("memcpy(v, g, len * sizeof(double));", "if (term == 0) memcpy(v, g, len * sizeof(double));", 0)],
+    "first_alpha_everywhere": [("out[q] += alpha[term] * v[q];", "out[q] += alpha[0] * v[q];", 0)],
+    "first_sigma_everywhere": [("oracle_apply(n, K, row_ptr, col, val, d, sigma[term], norm, v, t);",
+                                "oracle_apply(n, K, row_ptr, col, val, d, sigma[0], norm, v, t);", 0)],
+    "no_reimpose": [("if (reimpose && is_fixed)", "if (0)", 0)],
+    # HPWL
+    "hpwl_x_only": [("total += (xhi - xlo) + (yhi - ylo);", "total += (xhi - xlo);", 0)],
+    "hpwl_y_reads_x": [("y = xy[(c * S + s) * 2 + 1];", "y = xy[(c * S + s) * 2 + 0];", 0)],
+    "hpwl_first_signal_only": [("double x = xy[(c * S + s) * 2 + 0], y = xy[(c * S + s) * 2 + 1];",
+                                "double x = xy[(c * S) * 2 + 0], y = xy[(c * S) * 2 + 1];", 0)],
+    "hpwl_last_pin_dropped": [("for (int64_t p = 0; p < m; ++p) {", "for (int64_t p = 0; p < m - 1; ++p) {", 0)],
 }
 
+# name -> [(text, replacement)] applied to the oracle package source
+PY_MUTANTS = {
+    # exact smoothing (Sec. 3.2.2, Eq. 18)
+    "tikhonov_identity_unweighted": [("return (1.0 + lam) * v - lam * At_v", "return v - lam * At_v")],
+    "tikhonov_self_loop_dropped": [("At_v = s[:, None] * (A @ (s[:, None] * v) + sigma * s[:, None] * v)",
+                                    "At_v = s[:, None] * (A @ (s[:, None] * v))")],
+    "tikhonov_loose_stop": [("<= 1e-13 * np.maximum(bn, 1e-300)", "<= 1e-3 * np.maximum(bn, 1e-300)")],
+    "tikhonov_no_reimpose": [("out[fx] = np.asarray(sig, dtype=np.float64)[fx]", "out[fx] = out[fx]")],
+    # bin density (Eq. 5)
+    "density_full_extent": [("hw, hh = 0.5 * w.astype(np.float64), 0.5 * h.astype(np.float64)",
+                             "hw, hh = w.astype(np.float64), h.astype(np.float64)")],
+    "density_left_edge_unclipped": [("np.maximum(np.minimum(hi, b1) - np.maximum(lo, b0), 0.0)",
+                                     "np.maximum(np.minimum(hi, b1) - lo, 0.0)")],
+    "density_bin_index_rounded": [("np.clip(np.floor((lo - o) / step), 0, n - 1)", "np.clip(np.rint((lo - o) / step), 0, n - 1)")],
+    "density_y_reads_x": [("x, y = xy[:, s, 0].astype(np.float64), xy[:, s, 1].astype(np.float64)",
+                           "x, y = xy[:, s, 0].astype(np.float64), xy[:, s, 0].astype(np.float64)")],
+    "density_overflow_whole_bin": [("acc += c - tq", "acc += c")],
+    "density_overflow_unclamped": [("if c > tq:\n                acc += c - tq", "if True:\n                acc += c - tq")],
+    # storage format applied after the degrees
+    "degrees_before_rounding": [("    g = build_graph(nl.num_cells, nl.net_ptr, nl.pin_cell)\n    if fmt != \"f64\":\n"
+                                 "        g = stored(g, fmt)\n    d = degrees(g)",
+                                 "    g = build_graph(nl.num_cells, nl.net_ptr, nl.pin_cell)\n    d = degrees(g)\n"
+                                 "    if fmt != \"f64\":\n        g = stored(g, fmt)")],
+    "implicit_drops_expanded_part": [("out = np.array(d, dtype=np.float64, copy=True)",
+                                      "out = np.zeros(np.shape(d), dtype=np.float64)")],
+    # eigenvector placement (Sec. 3.3.1, Eq. 23-24)
+    "component_smallest": [("best = np.lexsort((first, -sizes))[0]", "best = np.lexsort((first, sizes))[0]")],
+    "component_tie_largest_id": [("best = np.lexsort((first, -sizes))[0]", "best = np.lexsort((-first, -sizes))[0]")],
+    "eigen_signless_laplacian": [("lap = (diags(np.asarray(d, dtype=np.float64)[idx]) - a).tocsc()",
+                                  "lap = (diags(np.asarray(d, dtype=np.float64)[idx]) + a).tocsc()")],
+    "eigen_constant_vector": [("u[idx, 0] = v[:, 1]", "u[idx, 0] = v[:, 0]")],
+    "eigen_u2_twice": [("u[idx, 1] = v[:, 2]", "u[idx, 1] = v[:, 1]")],
+    "eigen_lambda_shifted": [("return u, (float(w[1]), float(w[2])), mask", "return u, (float(w[0]), float(w[1])), mask")],
+}
 
-def _compile(tmp_path, name, old, new):
-    src = open(SRC).read()
-    assert src.count(old) >= 1, name
-    mut = src.replace(old, new, 1)
+_OUTCOME = (pytest.fail.Exception, pytest.skip.Exception)
+
+
+def _pin_cases():
+    """(label, function, kwargs) for every pin, parameters expanded."""
+    for mod in (test_oracle_pins, test_oracle_eigen):
+        for name in sorted(vars(mod)):
+            f = getattr(mod, name)
+            if not (name.startswith("test_") and callable(f)):
+                continue
+            axes = []
+            for m in getattr(f, "pytestmark", []):
+                if m.name != "parametrize":
+                    continue
+                names = [a.strip() for a in m.args[0].split(",")]
+                axes.append([dict(zip(names, v if len(names) > 1 else (v,))) for v in m.args[1]])
+            for combo in itertools.product(*axes):
+                kw = {k: v for part in combo for k, v in part.items()}
+                yield f"{mod.__name__.split('.')[-1]}::{name}{kw or ''}", f, kw
+
+
+def _failing_pins():
+    failed = []
+    for label, f, kw in _pin_cases():
+        try:
+            with warnings.catch_warnings():
+                warnings.simplefilter("ignore")
+                f(**kw)
+        except pytest.skip.Exception:
+            pass
+        except (Exception, pytest.fail.Exception):
+            failed.append(label)
+    return failed
+
+
+def _patch(src, edits):
+    for edit in edits:
+        old, new, nth = edit if len(edit) == 3 else (*edit, 0)
+        at = -1
+        for _ in range(nth + 1):
+            at = src.find(old, at + 1)
+            assert at >= 0, old
+        src = src[:at] + new + src[at + len(old):]
+    return src
+
+
+def _compile(tmp_path, name, src):
     c = tmp_path / f"{name}.c"
     so = tmp_path / f"{name}.so"
-    c.write_text(mut)
-    subprocess.check_call(["gcc", "-O1", "-std=c11", "-fPIC", "-shared", "-o", str(so), str(c), "-lm"])
+    c.write_text(src)
+    subprocess.check_call(["gcc", "-O1", "-std=c11", "-fPIC", "-shared", "-fno-fast-math", "-ffp-contract=off",
+                           "-o", str(so), str(c), "-lm"])
     return str(so)
 
 
-def _pins_pass(so_path):
-    """Run two pins against the library at so_path; True if both pass."""
-    saved = oracle._lib
+def _with_c_library(so_path, run):
+    """Run `run()` with the oracle bound to the library at so_path."""
+    saved_lib, saved_build = oracle._lib, oracle.build
     try:
         oracle._lib = None
-        L = C.CDLL(so_path)
-        orig_build = oracle.build
         oracle.build = lambda: so_path
-        try:
-            L2 = oracle.lib()
-        finally:
-            oracle.build = orig_build
-        assert L2 is not None
-        ok = True
-        # closed form on K_3 with no fixed cells
-        M = 3
-        g = oracle.build_graph(M, np.array([0, M]), np.arange(M, dtype=np.int32))
-        x = np.array([[1.0, 2.0], [5.0, 7.0], [9.0, 3.0]])
-        y = oracle.gift(g, oracle.degrees(g), x, None)
-        f = 163817 / 512000
-        ok &= np.allclose(y, x.mean(0) + f * (x - x.mean(0)), rtol=1e-12)
-        # dense brute force with fixed cells and a repeated cell
-        from tests.test_oracle_pins import _dense_reference
-        nl = synth.random_small(2, num_cells=20, num_nets=25, max_pins=6, num_fixed=3, allow_repeat=True)
-        xs = synth.uniform(1, 1, np.arange(40, dtype=np.uint64)).reshape(20, 2) * 100
-        try:
-            _, want = _dense_reference(nl, xs)
-            _, _, got = oracle.run(nl, xs)
-            ok &= np.allclose(got, want, rtol=1e-10, atol=1e-8)
-        except Exception:
-            ok = False
-        return bool(ok)
+        oracle.lib()
+        return run()
     finally:
-        oracle._lib = saved
+        oracle._lib, oracle.build = saved_lib, saved_build
 
 
-def test_unmutated_copy_passes(tmp_path):
-    so = _compile(tmp_path, "identity", "#include <math.h>", "#include <math.h>")
-    assert _pins_pass(so)
+def _with_python_source(src, run):
+    """Run `run()` with the oracle's functions taken from the source src."""
+    mod = types.ModuleType("oracle_mutant")
+    mod.__file__ = PY_SRC
+    sys.modules["oracle_mutant"] = mod  # the dataclass decorator looks its module up
+    try:
+        exec(compile(src, PY_SRC, "exec"), mod.__dict__)
+    finally:
+        del sys.modules["oracle_mutant"]
+    swapped = {k: v for k, v in vars(mod).items()
+               if isinstance(v, types.FunctionType) and v.__module__ == "oracle_mutant" and k not in ("build", "lib")}
+    saved = {k: getattr(oracle, k) for k in swapped}
+    try:
+        for k, v in swapped.items():
+            setattr(oracle, k, v)
+        return run()
+    finally:
+        for k, v in saved.items():
+            setattr(oracle, k, v)
 
 
-@pytest.mark.parametrize("name", sorted(MUTANTS))
-def test_mutant_is_caught(tmp_path, name):
-    old, new = MUTANTS[name]
-    so = _compile(tmp_path, name, old, new)
-    assert not _pins_pass(so), f"planted mistake {name} passed the pins"
+def test_unmutated_copies_pass_every_pin(tmp_path):
+    so = _compile(tmp_path, "identity", open(C_SRC).read())
+    assert _with_c_library(so, _failing_pins) == []
+    assert _with_python_source(open(PY_SRC).read(), _failing_pins) == []
+    assert len(list(_pin_cases())) >= 60
+
+
+@pytest.mark.parametrize("name", sorted(C_MUTANTS))
+def test_c_mutant_is_caught(tmp_path, name):
+    so = _compile(tmp_path, name, _patch(open(C_SRC).read(), C_MUTANTS[name]))
+    assert _with_c_library(so, _failing_pins), f"planted mistake {name} passed every pin"
+
+
+@pytest.mark.parametrize("name", sorted(PY_MUTANTS))
+def test_python_mutant_is_caught(name):
+    src = _patch(open(PY_SRC).read(), PY_MUTANTS[name])
+    assert _with_python_source(src, _failing_pins), f"planted mistake {name} passed every pin"

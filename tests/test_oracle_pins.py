@@ -306,6 +306,15 @@ def test_bf16_degrees_use_stored_weights():
     d = oracle.degrees(g)
     v = np.sqrt(d + 4.0)
     np.testing.assert_allclose(oracle.apply(g, d, 4.0, v), v, rtol=1e-13)
+    # the whole path rounds before it takes the degrees: every weight is a
+    # bf16 value and each degree is the plain sum of its row's stored weights
+    x = synth.uniform(19, 19, np.arange(80, dtype=np.uint64)).reshape(40, 2)
+    g2, d2, _ = oracle.run(nl, x, fmt="bf16")
+    np.testing.assert_array_equal(g2.val, g.val)
+    for i in range(40):
+        assert d2[i] == pytest.approx(math.fsum(g2.val[g2.row_ptr[i]:g2.row_ptr[i + 1]]), rel=1e-15)
+    assert any(abs(d2[i] - oracle.degrees(oracle.build_graph(40, nl.net_ptr, nl.pin_cell))[i]) > 1e-6
+               for i in range(40))  # the rounding is visible in the degrees
 
 
 # ------------------------------------------------------------------ HPWL
@@ -462,3 +471,17 @@ def test_density_conserves_area_and_counts_overflow():
     _, dens, over = oracle.density(xy, (0, 0, 100, 100), 4, 4, target=0.5, unit=(25.0, 12.5))
     np.testing.assert_allclose(dens[0], 0.5, rtol=0, atol=math.ldexp(1.0, -40))
     assert over[0] == 0.0
+
+
+def test_density_overflow_hand_case():
+    """Two bins of 10 x 10 on [0, 20) x [0, 10), target 0.5 (capacity 50 per
+    bin).  Three 5 x 5 cells stacked in bin 0 (area 75) and one in bin 1
+    (area 25): only bin 0 overflows, by 25, over a total cell area of 100.
+    The same three cells alone in one bin overflow it by 25 of 75."""
+    xy = np.array([[[5.0, 5.0]], [[5.0, 5.0]], [[5.0, 5.0]], [[15.0, 5.0]]], dtype=np.float32)
+    counts, dens, over = oracle.density(xy, (0, 0, 20, 10), 2, 1, target=0.5, unit=(5.0, 5.0))
+    np.testing.assert_array_equal(dens[0], [[0.75, 0.25]])
+    assert over[0] == 0.25
+    _, dens, over = oracle.density(xy[:3], (0, 0, 10, 10), 1, 1, target=0.5, unit=(5.0, 5.0))
+    assert dens[0, 0, 0] == 0.75
+    assert over[0] == 25.0 / 75.0
