@@ -673,12 +673,27 @@ k_rows_warp(const int32_t *__restrict__ rows, const int32_t *__restrict__ nrows_
     }
 }
 
+// Fixed-point sums for exact degrees: stored weights in [2^-11, 2^19) are
+// multiples of 2^-34, and while their total stays below 2^53 units of 2^-34
+// every partial sum is exactly representable in FP64, so the column-order FP64
+// sum equals the integer sum in any order.  Sums saturate at kExactCap, which
+// marks them unusable.
+constexpr long long kExactCap = 1ll << 53;
+__device__ __forceinline__ long long sat_add(long long a, long long b) {
+    const long long s = a + b;  // a, b <= kExactCap: no overflow
+    return s < kExactCap ? s : kExactCap;
+}
+
 // Block tiers: one block per long row.  GLOBAL_KEYS: keys live in a per-block
 // global scratch of `gcap` entries (rows beyond the shared-memory capacity);
 // else in dynamic shared memory of `cap` keys followed by `cap` stored
 // weights, and the block takes the rows of the list with lo < raw length <=
 // cap (launched once per size class, so that short rows do not reserve the
-// shared memory of the longest and many blocks share an SM).
+// shared memory of the longest and many blocks share an SM).  The degree is
+// the block's exact fixed-point sum of the stored weights where that equals
+// the column-order FP64 sum (above), else one thread's FP64 sum in column
+// order: a serial FP64 chain of one active lane per entry occupies the SM's
+// narrow FP64 pipe for a full warp instruction per step.
 template <typename WT, bool GLOBAL_KEYS>
 __global__ void __launch_bounds__(kBlockThreads)
 k_rows_block(const int64_t *__restrict__ inc_ptr, const int32_t *__restrict__ inc_net,
@@ -691,6 +706,8 @@ k_rows_block(const int64_t *__restrict__ inc_ptr, const int32_t *__restrict__ in
     __shared__ int s_cnt;
     __shared__ int s_warp[kBlockThreads / 32];
     __shared__ int s_uniq;
+    __shared__ long long s_q[kBlockThreads / 32];
+    __shared__ int s_ex[kBlockThreads / 32];
     uint64_t *keys = GLOBAL_KEYS ? gkeys + blockIdx.x * gcap : smem_keys;
     WT *svals = GLOBAL_KEYS ? nullptr : reinterpret_cast<WT *>(smem_keys + cap);
     const int tid = threadIdx.x, lane = tid & 31, wid = tid >> 5;
@@ -735,6 +752,8 @@ k_rows_block(const int64_t *__restrict__ inc_ptr, const int32_t *__restrict__ in
                 __syncthreads();
             }
         }
+        long long qsum = 0;
+        bool exact = true;
         for (int base = 0; base < n; base += blockDim.x) {
             int t = base + tid;
             bool head = false;
@@ -756,6 +775,9 @@ k_rows_block(const int64_t *__restrict__ inc_ptr, const int32_t *__restrict__ in
                 out_col[rbase + u] = c;
                 out_val[rbase + u] = w;
                 if (!GLOBAL_KEYS) svals[u] = w;
+                const float wf = Store<WT>::getf(w);
+                if (wf >= 0x1p-11f && wf < 0x1p19f) qsum = sat_add(qsum, (long long)(wf * 0x1p34f));
+                else exact = false;
             }
             __syncthreads();
             if (tid == 0) {
@@ -765,12 +787,30 @@ k_rows_block(const int64_t *__restrict__ inc_ptr, const int32_t *__restrict__ in
             }
             __syncthreads();
         }
-        if (tid == 0) {  // degree in column order, from shared memory where it fits
+#pragma unroll
+        for (int o = 16; o > 0; o >>= 1) qsum = sat_add(qsum, __shfl_xor_sync(0xffffffffu, qsum, o));
+        const int wexact = __all_sync(0xffffffffu, exact);
+        if (lane == 0) {
+            s_q[wid] = qsum;
+            s_ex[wid] = wexact;
+        }
+        __syncthreads();
+        if (tid == 0) {
+            long long q = 0;
+            bool ex = true;
+            for (int k = 0; k < (int)(blockDim.x >> 5); ++k) {
+                q = sat_add(q, s_q[k]);
+                ex = ex && s_ex[k] != 0;
+            }
             double d = 0.0;
-            if (GLOBAL_KEYS)
-                for (int u = 0; u < s_uniq; ++u) d += Store<WT>::get(out_val[rbase + u]);
-            else
-                for (int u = 0; u < s_uniq; ++u) d += Store<WT>::get(svals[u]);
+            if (ex && q < kExactCap) {
+                d = (double)q * 0x1p-34;
+            } else {  // column order, from shared memory where it fits
+                if (GLOBAL_KEYS)
+                    for (int u = 0; u < s_uniq; ++u) d += Store<WT>::get(out_val[rbase + u]);
+                else
+                    for (int u = 0; u < s_uniq; ++u) d += Store<WT>::get(svals[u]);
+            }
             ucount[row] = s_uniq;
             degree[row] = d;
         }
