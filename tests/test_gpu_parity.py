@@ -106,6 +106,44 @@ def test_graph_bit_exact(ctx, name, wd):
         assert info.max_row_nnz == int((og.row_ptr[1:] - og.row_ptr[:-1]).max())
 
 
+_WIDE = {}
+
+
+def wide_net_case():
+    """One net of 4,200 pins over cells 0..4199 of 4,400 plus 600 small nets:
+    the wide net's weight 2/4200 lies below 2^-11, so the degrees of its rows
+    (block tier, 4,199 or more raw entries) take the one-thread FP64 sum, not
+    the integer count; the other rows mix both."""
+    if not _WIDE:
+        M, N = 4200, 4400
+        nets = [list(range(M))]
+        small = synth.random_small(12, N, 600, 6, min_pins=2)
+        for e in range(small.num_nets):
+            nets.append([int(c) for c in small.pin_cell[small.net_ptr[e]:small.net_ptr[e + 1]]])
+        net_ptr = np.concatenate([[0], np.cumsum([len(n) for n in nets])]).astype(np.int64)
+        pin_cell = np.array([c for n in nets for c in n], dtype=np.int32)
+        nl = synth.Netlist(N, len(nets), net_ptr, pin_cell, np.zeros(N, np.uint8), np.zeros((N, 2), np.float32))
+        _WIDE["nl"] = nl
+        _WIDE["og"] = oracle.build_graph(N, net_ptr, pin_cell)
+    return _WIDE["nl"], _WIDE["og"]
+
+
+@pytest.mark.parametrize("wd", ["f32", "bf16", "f16"])
+def test_block_tier_fp64_degrees(ctx, wd):
+    nl, og64 = wide_net_case()
+    assert 2.0 / 4200 < 2.0 ** -11
+    h = build(ctx, nl, wd)
+    try:
+        rp, col, val, deg = gift.gift_graph_export(h)
+    finally:
+        gift.gift_graph_free(h)
+    og = oracle.stored(og64, wd)
+    np.testing.assert_array_equal(rp, og.row_ptr)
+    np.testing.assert_array_equal(col, og.col)
+    np.testing.assert_array_equal(val, og.val)
+    np.testing.assert_array_equal(deg, oracle.degrees(og))
+
+
 def test_host_and_device_inputs_agree(ctx):
     nl = NETLISTS["repeat-cells"]
     a, b = build(ctx, nl, device=True), build(ctx, nl, device=False)
