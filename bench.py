@@ -39,7 +39,7 @@ UNIT = "edge-updates/s"
 def parse():
     p = argparse.ArgumentParser()
     p.add_argument("--gpus", type=int, default=1)
-    p.add_argument("--steps", type=int, default=50)
+    p.add_argument("--steps", type=int, default=150)  # ~0.6 s timed: several clock samples at 100 ms
     p.add_argument("--warmup", type=int, default=3)
     p.add_argument("--impl", default="ours", choices=["ours", "reference"])
     p.add_argument("--workload", default="large-2.2m", choices=sorted(synth.WORKLOADS))
@@ -265,7 +265,7 @@ def run_reference(args):
         return
     import oracle
     oracle.build()
-    scale = 0.1
+    scale = 0.05  # about 0.4 s of single-threaded oracle work per step
     nl, g = synth.workload(args.workload, scale=scale)
     sample = f"{args.workload} law at {scale:g} scale ({nl.num_cells} cells, {nl.num_nets} nets), 1 of {g.shape[1]} signals; build + filter + HPWL"
     for _ in range(args.warmup):
