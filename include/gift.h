@@ -159,7 +159,10 @@ typedef struct gift_kernel_stat {
 
 /* ---- context -------------------------------------------------------------
  * gift_ctx_create: binds to CUDA device `device` (made current on the calling
- * thread), sets up the stream-ordered allocator.  *out receives the handle. */
+ * thread), sets up the stream-ordered allocator.  *out receives the handle.
+ * Errors: GIFT_ERR_INVALID (out is NULL, no such device), GIFT_ERR_OOM,
+ * GIFT_ERR_CUDA.  gift_ctx_destroy synchronises the device first; NULL is a
+ * no-op. */
 GIFT_API gift_status gift_ctx_create(int32_t device, gift_ctx **out);
 GIFT_API void gift_ctx_destroy(gift_ctx *ctx);
 
@@ -262,14 +265,21 @@ GIFT_API gift_status gift_filter_noalloc(gift_ctx *ctx, const gift_graph *graph,
 
 /* ---- HPWL -----------------------------------------------------------------
  * out[s] = sum over nets of (max x - min x) + (max y - min y) of signal s, pin
- * locations = cell locations of xy [N][S][2] (memory `mem`).  Per-net extents
- * exact, sum in FP64 in a fixed order.  `out` is a HOST array of S doubles;
- * the call synchronises `stream`. */
+ * locations = cell locations of xy [N][S][2] (memory `mem`).  The paper
+ * reports HPWL (Sec. 4.1) without defining it; this is the standard
+ * half-perimeter of each net's bounding box, nets of fewer than 2 pins
+ * adding 0.  Per-net extents exact, sum in FP64 in a fixed order.  `out` is
+ * a HOST array of S doubles; the call synchronises `stream`.
+ * Errors: GIFT_ERR_INVALID (NULL pointer, S out of 1..524280, bad mem
+ * kind, xy not 8-byte aligned), GIFT_ERR_OOM, GIFT_ERR_CUDA,
+ * GIFT_ERR_TIMEOUT (as gift_ctx_device_status). */
 GIFT_API gift_status gift_hpwl(gift_ctx *ctx, const gift_graph *graph, const float *xy, int32_t num_signals,
                       double *out, int32_t mem, void *stream);
 
 
-/* The whole path in one call from host memory: builds the graph of `netlist`
+/* The whole path in one call from host memory (Algorithm 1 without the
+ * placer: the graph of Sec. 2.2 and 3.2.3, the filter of Eq. 15-16 with the
+ * fixed cells put back, the HPWL Sec. 4.1 reports): builds the graph of `netlist`
  * (host arrays; opts may be NULL), filters g_in ([num_cells][num_signals][2],
  * host) with spec (NULL: the paper's filter) into g_out (host) and writes
  * the HPWL of every filtered signal to hpwl (host, [num_signals], may be
@@ -278,7 +288,11 @@ GIFT_API gift_status gift_hpwl(gift_ctx *ctx, const gift_graph *graph, const flo
  * return.  When g_out is page-locked host memory (pinned or registered,
  * 16-byte aligned) the last filter sweep stores the result into it directly,
  * so its transfer overlaps the sweep; otherwise it is copied back while HPWL
- * runs.  Results equal gift_build_graph + gift_filter + gift_hpwl. */
+ * runs.  Results equal gift_build_graph + gift_filter + gift_hpwl.
+ * Errors: GIFT_ERR_INVALID (NULL context, netlist or signal; a netlist not in
+ * host memory; num_signals < 1; a bad netlist as for gift_build_graph; a NaN
+ * or an infinity in g_in, found before any output is written),
+ * GIFT_ERR_OOM, GIFT_ERR_CUDA, GIFT_ERR_TIMEOUT. */
 GIFT_API gift_status gift_run(gift_ctx *ctx, const gift_netlist *netlist, const gift_build_opts *opts,
                               const gift_filter_spec *spec, const float *g_in, int32_t num_signals, float *g_out,
                               double *hpwl, void *stream);
@@ -345,7 +359,11 @@ GIFT_API gift_status gift_eigen_placement(gift_ctx *ctx, const gift_graph *graph
  * density (host, [num_signals][bins_y][bins_x], may be NULL) = rho_b / bin
  * area; overflow (host, [num_signals], may be NULL) = sum over bins of
  * max(0, rho_b - target * bin area) / (total cell area).  bins_x * bins_y <=
- * 2^24. */
+ * 2^24.  Errors: GIFT_ERR_INVALID (NULL xy or die; num_cells < 1; num_signals
+ * out of 1..65535; a bin grid out of range; a die that is not finite with
+ * die[2] > die[0] and die[3] > die[1]; target not finite or < 0; only one of
+ * cell_w, cell_h; unit sizes not finite or < 0; bad mem kind; xy not 8-byte
+ * aligned), GIFT_ERR_OOM, GIFT_ERR_CUDA. */
 GIFT_API gift_status gift_density(gift_ctx *ctx, const float *xy, int32_t num_cells, int32_t num_signals,
                                   const float *cell_w, const float *cell_h, float unit_w, float unit_h,
                                   const double *die, int32_t bins_x, int32_t bins_y, double target,
@@ -366,7 +384,9 @@ GIFT_API gift_status gift_build_batch(gift_ctx *ctx, const gift_netlist *netlist
                                       const gift_build_opts *opts, gift_graph **out, int64_t *cell_offsets,
                                       void *stream);
 /* HPWL of every graph of a batch: out[b * num_signals + s] (host).  On a graph
- * built by gift_build_graph it equals gift_hpwl (one graph).  Synchronises. */
+ * built by gift_build_graph it equals gift_hpwl (one graph).  Synchronises.
+ * Errors: as gift_hpwl.  Batches and graph replay have no counterpart in the
+ * paper: they serve many netlists per launch. */
 GIFT_API gift_status gift_hpwl_batch(gift_ctx *ctx, const gift_graph *graph, const float *xy, int32_t num_signals,
                                      double *out, int32_t mem, void *stream);
 
@@ -377,7 +397,9 @@ GIFT_API gift_status gift_hpwl_batch(gift_ctx *ctx, const gift_graph *graph, con
  * memory the handle owns.  gift_exec_launch replays it on `stream`: one graph
  * launch filters the same device buffers g_in -> g_out again (write new
  * signals into g_in between launches); the graph and both buffers must stay
- * alive and unmoved while the handle is used.  Device memory only. */
+ * alive and unmoved while the handle is used.  Device memory only.
+ * Errors: GIFT_ERR_INVALID (NULL argument, a bad spec as for gift_filter),
+ * GIFT_ERR_OOM, GIFT_ERR_CUDA (also from a failed capture or launch). */
 typedef struct gift_exec gift_exec;
 GIFT_API gift_status gift_filter_capture(gift_ctx *ctx, const gift_graph *graph, const gift_filter_spec *spec,
                                          const float *g_in, int32_t num_signals, float *g_out, gift_exec **out);
