@@ -155,18 +155,36 @@ def _check(st: int):
         raise GiftError(st, load().gift_last_error().decode())
 
 
-def _ptr(a):
-    """(pointer, mem kind) of a numpy array or a torch tensor."""
+# element types the C ABI reads through each kind of pointer
+_KINDS = {"i64": ("int64",), "i32": ("int32",), "u8": ("uint8", "bool"), "f32": ("float32",),
+          "f64": ("float64",)}
+
+
+def _ptr(a, kind: str | None = None, count: int | None = None, what: str = "array"):
+    """(pointer, mem kind) of a numpy array or a torch tensor.  `kind` names
+    the element type the library reads through the pointer and `count` the
+    elements it reads at most; an array of another type or fewer elements is
+    rejected here, before the library could read past its end."""
     if a is None:
         return None, None
     if isinstance(a, np.ndarray):
         if not a.flags["C_CONTIGUOUS"]:
-            raise ValueError("arrays must be C-contiguous")
-        return a.ctypes.data, GIFT_MEM_HOST
-    # torch tensor
-    if not a.is_contiguous():
-        raise ValueError("tensors must be contiguous")
-    return a.data_ptr(), (GIFT_MEM_DEVICE if a.is_cuda else GIFT_MEM_HOST)
+            raise ValueError(f"{what}: arrays must be C-contiguous")
+        dtype, n, p, mem = a.dtype.name, a.size, a.ctypes.data, GIFT_MEM_HOST
+    else:  # torch tensor
+        if not a.is_contiguous():
+            raise ValueError(f"{what}: tensors must be contiguous")
+        dtype = str(a.dtype).replace("torch.", "")
+        n, p, mem = a.numel(), a.data_ptr(), (GIFT_MEM_DEVICE if a.is_cuda else GIFT_MEM_HOST)
+    if kind is not None and dtype not in _KINDS[kind]:
+        raise TypeError(f"{what}: element type {dtype}, the library reads {_KINDS[kind][0]}")
+    if count is not None and n < count:
+        raise ValueError(f"{what}: {n} elements, the library reads {count}")
+    return p, mem
+
+
+def _cells(graph) -> int:
+    return int(gift_graph_info(graph).num_cells)
 
 
 def _stream(stream):
@@ -251,9 +269,10 @@ def gift_build_opts_default() -> gift_build_opts:
 def gift_build_graph(ctx, num_cells: int, net_ptr, pin_cell, is_fixed=None, weight_dtype: int = GIFT_WEIGHT_F32,
                      stream=None, implicit_min_pins: int = 0):
     """Build the clique graph; arrays are all host (numpy) or all device (torch)."""
-    npp, mem = _ptr(net_ptr)
-    pcp, mem2 = _ptr(pin_cell)
-    fxp, mem3 = _ptr(is_fixed)
+    npp, mem = _ptr(net_ptr, "i64", 1, "net_ptr")
+    pins = int(net_ptr[-1]) if isinstance(net_ptr, np.ndarray) else None  # device: the library checks
+    pcp, mem2 = _ptr(pin_cell, "i32", pins, "pin_cell")
+    fxp, mem3 = _ptr(is_fixed, "u8", num_cells, "is_fixed")
     nets = (net_ptr.shape[0] if hasattr(net_ptr, "shape") else len(net_ptr)) - 1
     nl = gift_netlist(num_cells, nets, npp, pcp, fxp, mem)
     opts = gift_build_opts_default()
@@ -293,11 +312,12 @@ def gift_graph_free_async(graph, stream=None):
 def gift_filter(ctx, graph, g_in, g_out, spec: gift_filter_spec | None = None, num_signals: int | None = None,
                 stream=None):
     """g_out <- GiFt(g_in); g_in/g_out are [N, S, 2] float32 (both numpy or both CUDA tensors)."""
-    pi, mem = _ptr(g_in)
-    po, mem_o = _ptr(g_out)
+    S = num_signals if num_signals is not None else int(g_in.shape[1])
+    n = _cells(graph) * 2 * max(S, 0)
+    pi, mem = _ptr(g_in, "f32", n, "g_in")
+    po, mem_o = _ptr(g_out, "f32", n, "g_out")
     if mem != mem_o:
         raise ValueError("g_in and g_out must live in the same memory")
-    S = num_signals if num_signals is not None else int(g_in.shape[1])
     _check(load().gift_filter(ctx, graph, C.byref(spec) if spec is not None else None, pi, S, po, mem,
                               _stream(stream)))
     return g_out
@@ -308,11 +328,12 @@ def gift_filter_noalloc(ctx, graph, g_in, g_out, spec: gift_filter_spec | None =
     """gift_filter on device tensors without any device allocation: scratch comes
     from the library's fixed GIFT_NOALLOC_SCRATCH_BYTES area (for callers that
     cannot allocate while filtering).  Overlapping calls race on that area."""
-    pi, mem = _ptr(g_in)
-    po, mem_o = _ptr(g_out)
+    S = num_signals if num_signals is not None else int(g_in.shape[1])
+    n = _cells(graph) * 2 * max(S, 0)
+    pi, mem = _ptr(g_in, "f32", n, "g_in")
+    po, mem_o = _ptr(g_out, "f32", n, "g_out")
     if mem != GIFT_MEM_DEVICE or mem_o != GIFT_MEM_DEVICE:
         raise ValueError("gift_filter_noalloc takes device tensors")
-    S = num_signals if num_signals is not None else int(g_in.shape[1])
     _check(load().gift_filter_noalloc(ctx, graph, C.byref(spec) if spec is not None else None, pi, S, po,
                                       _stream(stream)))
     return g_out
@@ -322,8 +343,8 @@ GIFT_NOALLOC_SCRATCH_BYTES = 64 << 20
 
 
 def gift_hpwl(ctx, graph, xy, num_signals: int | None = None, stream=None) -> np.ndarray:
-    p, mem = _ptr(xy)
     S = num_signals if num_signals is not None else int(xy.shape[1])
+    p, mem = _ptr(xy, "f32", _cells(graph) * 2 * max(S, 0), "xy")
     out = np.zeros(S, dtype=np.float64)
     _check(load().gift_hpwl(ctx, graph, p, S, out.ctypes.data, mem, _stream(stream)))
     return out
@@ -398,9 +419,10 @@ def gift_build_batch(ctx, netlists, weight_dtype: int = GIFT_WEIGHT_F32, stream=
     arr = (gift_netlist * B)()
     keep = []
     for b, (n, net_ptr, pin_cell, is_fixed) in enumerate(netlists):
-        p_np, mem = _ptr(net_ptr)
-        p_pc, _ = _ptr(pin_cell)
-        p_fx, _ = _ptr(is_fixed)
+        p_np, mem = _ptr(net_ptr, "i64", 1, "net_ptr")
+        pins = int(net_ptr[-1]) if isinstance(net_ptr, np.ndarray) else None
+        p_pc, _ = _ptr(pin_cell, "i32", pins, "pin_cell")
+        p_fx, _ = _ptr(is_fixed, "u8", n, "is_fixed")
         arr[b] = gift_netlist(n, (len(net_ptr) if isinstance(net_ptr, np.ndarray) else net_ptr.numel()) - 1,
                               p_np, p_pc, p_fx, mem)
         keep.append((net_ptr, pin_cell, is_fixed))
@@ -416,8 +438,8 @@ def gift_build_batch(ctx, netlists, weight_dtype: int = GIFT_WEIGHT_F32, stream=
 
 def gift_hpwl_batch(ctx, graph, xy, num_graphs: int, stream=None) -> np.ndarray:
     """HPWL per graph and signal, [num_graphs][S]."""
-    p, mem = _ptr(xy)
     S = xy.shape[1]
+    p, mem = _ptr(xy, "f32", _cells(graph) * 2 * S, "xy")
     out = np.empty((num_graphs, S), dtype=np.float64)
     _check(load().gift_hpwl_batch(ctx, graph, p, S, out.ctypes.data, mem, _stream(stream)))
     return out
@@ -425,8 +447,9 @@ def gift_hpwl_batch(ctx, graph, xy, num_graphs: int, stream=None) -> np.ndarray:
 
 def gift_filter_capture(ctx, graph, g_in, g_out, spec=None):
     """Record the filter g_in -> g_out (torch CUDA tensors) as a CUDA graph."""
-    pi, mi = _ptr(g_in)
-    po, mo = _ptr(g_out)
+    n = _cells(graph) * 2 * int(g_in.shape[1])
+    pi, mi = _ptr(g_in, "f32", n, "g_in")
+    po, mo = _ptr(g_out, "f32", n, "g_out")
     if mi != GIFT_MEM_DEVICE or mo != GIFT_MEM_DEVICE:
         raise ValueError("gift_filter_capture takes device tensors")
     h = C.c_void_p()
@@ -447,11 +470,12 @@ def gift_exec_free(exec_):
 def gift_tikhonov(ctx, graph, g_in, g_out, sigma: float = 2.0, lam: float = 1.0, iterations: int = 0,
                   reimpose: bool = True, stream=None) -> np.ndarray:
     """g_out = (I + lam (I - A~_sigma))^-1 g_in by CG; returns ||r|| / ||g|| per column."""
-    pi, mi = _ptr(g_in)
-    po, mo = _ptr(g_out)
+    S = g_in.shape[1]
+    n = _cells(graph) * 2 * S
+    pi, mi = _ptr(g_in, "f32", n, "g_in")
+    po, mo = _ptr(g_out, "f32", n, "g_out")
     if mi != mo:
         raise ValueError("g_in and g_out must be in the same memory")
-    S = g_in.shape[1]
     res = np.zeros(2 * S, dtype=np.float64)
     _check(load().gift_tikhonov(ctx, graph, sigma, lam, iterations, 1 if reimpose else 0, pi, S, po,
                                 res.ctypes.data, mi, _stream(stream)))
@@ -464,9 +488,10 @@ def gift_eigen_placement(ctx, graph, out=None, max_iterations: int = 300, tol: f
     """(u_2, u_3) of L = D - A on the largest component into out ([N][2]
     float64, numpy or CUDA tensor; a new numpy array if None); returns
     (out, gift_eigen_result)."""
+    N = _cells(graph)
     if out is None:
-        out = np.zeros((gift_graph_info(graph).num_cells, 2), dtype=np.float64)
-    p, mem = _ptr(out)
+        out = np.zeros((N, 2), dtype=np.float64)
+    p, mem = _ptr(out, "f64", 2 * N, "out")
     res = gift_eigen_result()
     _check(load().gift_eigen_placement(ctx, graph, max_iterations, tol, seed, p, C.byref(res), mem,
                                        _stream(stream)))
@@ -478,10 +503,10 @@ def gift_density(ctx, xy, die=(0.0, 0.0, 1000.0, 1000.0), bins=(32, 32), target:
                  cell_w=None, cell_h=None, stream=None):
     """Bin density (Eq. 5) of every signal of xy [N][S][2] and its overflow:
     returns (density [S][bins_y][bins_x], overflow [S])."""
-    p, mem = _ptr(xy)
     N, S = xy.shape[0], xy.shape[1]
-    pw, _ = _ptr(cell_w)
-    ph, _ = _ptr(cell_h)
+    p, mem = _ptr(xy, "f32", N * S * 2, "xy")
+    pw, _ = _ptr(cell_w, "f32", N, "cell_w")
+    ph, _ = _ptr(cell_h, "f32", N, "cell_h")
     d = np.ascontiguousarray(die, dtype=np.float64)
     out = np.empty((S, bins[1], bins[0]), dtype=np.float64)
     ov = np.empty(S, dtype=np.float64)
@@ -505,6 +530,10 @@ def gift_run(ctx, num_cells: int, net_ptr, pin_cell, is_fixed, g_in, g_out, spec
     if not (isinstance(g_in, np.ndarray) and isinstance(g_out, np.ndarray)):
         raise ValueError("gift_run takes host (numpy) signals")
     S = g_in.shape[1]
+    _ptr(g_in, "f32", num_cells * 2 * S, "g_in")
+    _ptr(g_out, "f32", num_cells * 2 * S, "g_out")
+    if len(pin_cell) < int(net_ptr[-1]):
+        raise ValueError(f"pin_cell: {len(pin_cell)} elements, the netlist has {int(net_ptr[-1])} pins")
     hp = np.empty(S, dtype=np.float64)
     _check(load().gift_run(ctx, C.byref(nl), C.byref(opts), None if spec is None else C.byref(spec),
                            g_in.ctypes.data, S, g_out.ctypes.data, hp.ctypes.data, _stream(stream)))
