@@ -232,6 +232,13 @@ GIFT_API void gift_graph_free_async(gift_graph *graph, void *stream);
  * must be 8-byte aligned.  FP32 signal and accumulation.  With host memory
  * the call is synchronous; a page-locked, 16-byte aligned g_out is written
  * by the last sweep directly (no copy after it).
+ * A graph caches what its filters derive from it: the scale vectors of each
+ * sigma and the row order or sliced-ELL format of the kernel shape in use,
+ * built by the first call that needs them, on that call's stream (a new
+ * sliced-ELL width replaces the old format).  Calls on one stream need
+ * nothing more; calls that share a graph across streams or threads must be
+ * ordered by the caller (synchronise, or make the next stream wait on an
+ * event recorded after the previous call).
  * Errors: GIFT_ERR_INVALID, GIFT_ERR_OOM, GIFT_ERR_CUDA. */
 GIFT_API gift_status gift_filter(gift_ctx *ctx, const gift_graph *graph, const gift_filter_spec *spec,
                         const float *g_in, int32_t num_signals, float *g_out, int32_t mem, void *stream);
