@@ -97,6 +97,13 @@ PY_MUTANTS = {
                                  "    if fmt != \"f64\":\n        g = stored(g, fmt)")],
     "implicit_drops_expanded_part": [("out = np.array(d, dtype=np.float64, copy=True)",
                                       "out = np.zeros(np.shape(d), dtype=np.float64)")],
+    # the wrappers' arguments to the C library
+    "apply_norm_flag_swapped": [("float(sigma), 0 if norm == \"sym\" else 1, _p(x), _p(y))",
+                                 "float(sigma), 1 if norm == \"sym\" else 0, _p(x), _p(y))")],
+    "filter_norm_flag_swapped": [("_p(al), 0 if norm == \"sym\" else 1,", "_p(al), 1 if norm == \"sym\" else 0,")],
+    "rounding_format_ignored": [("_p(out), FMT[fmt])", "_p(out), FMT[\"f32\"])")],
+    "stored_weights_unrounded": [("return Graph(g.n, g.row_ptr, g.col, round_values(g.val, fmt))",
+                                  "return Graph(g.n, g.row_ptr, g.col, np.array(g.val, copy=True))")],
     # eigenvector placement (Sec. 3.3.1, Eq. 23-24)
     "component_smallest": [("best = np.lexsort((first, -sizes))[0]", "best = np.lexsort((first, sizes))[0]")],
     "component_tie_largest_id": [("best = np.lexsort((first, -sizes))[0]", "best = np.lexsort((-first, -sizes))[0]")],
