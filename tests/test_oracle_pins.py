@@ -54,6 +54,23 @@ def test_single_net_closed_form():
         np.testing.assert_allclose(y, want, rtol=1e-13, atol=1e-11)
 
 
+def test_golden_values_follow_their_derivation():
+    """The fixture's rationals are the closed form its header derives, in
+    exact arithmetic: r_s = (s - w) / (d + s), w = 2/M, d = w (M - 1),
+    f_M = 0.1 r_2^2 + 0.7 r_4^2 + 0.2 r_4^4; the worked example is
+    1/2 -+ f_2 / 2."""
+    fm, ex = _golden_f()
+    assert sorted(fm) == [2, 3, 4, 50]
+    for M, f in fm.items():
+        w = Fraction(2, M)
+        d = w * (M - 1)
+        r2, r4 = (2 - w) / (d + 2), (4 - w) / (d + 4)
+        assert f == Fraction(1, 10) * r2 ** 2 + Fraction(7, 10) * r4 ** 2 + Fraction(2, 10) * r4 ** 4
+    assert ex[:2] == [0.0, 1.0]
+    assert ex[2] == pytest.approx(float(Fraction(1, 2) - fm[2] / 2), rel=0, abs=1e-16)
+    assert ex[3] == pytest.approx(float(Fraction(1, 2) + fm[2] / 2), rel=0, abs=1e-16)
+
+
 def test_worked_example_two_pin():
     _, ex = _golden_f()
     g = oracle.build_graph(2, np.array([0, 2]), np.array([0, 1], dtype=np.int32))
