@@ -251,19 +251,22 @@ GIFT_API gift_status gift_filter(gift_ctx *ctx, const gift_graph *graph, const g
  *
  * Same result as gift_filter for DEVICE buffers g_in / g_out ([N][S][2]
  * float32, 8-byte aligned, not overlapping), but every scratch buffer comes
- * from one fixed device array of GIFT_NOALLOC_SCRATCH_BYTES, allocated when
- * the library is loaded and held by every GPU that loads it until the
- * process exits.  The call allocates nothing: no cudaMalloc, no cudaFree, no
+ * from one fixed device array of GIFT_NOALLOC_SCRATCH_BYTES, held by every
+ * GPU that loads the library until the process exits.  The array is reserved
+ * when gift_ctx_create runs on a device (it looks up the array's device
+ * address, once per device, which makes the driver load it); a context whose
+ * creation cannot reserve it fails there, so this call never meets that
+ * failure.  The call allocates nothing: no cudaMalloc, no cudaFree, no
  * allocating library routine.  A graph/signal that needs more scratch
  * (about 4 + 2 x (chains with power >= 2) times N x S x 8 bytes) is rejected
- * with GIFT_ERR_INVALID and a message giving both sizes.
+ * with GIFT_ERR_INVALID and a message giving both sizes, as is a spec with
+ * num_terms outside [1, GIFT_MAX_TERMS] (checked before anything else reads
+ * the spec's terms).
  *
- * The first call on a device looks up the array's device address (once per
- * device); make that first call before any stream capture.  Every call uses
- * the same array, so calls whose work overlaps on the GPU (other streams,
- * other threads, other contexts of the process) race and corrupt each other;
- * serialise them.  Each call rewrites all scratch it reads before reading it,
- * so nothing needs clearing between calls.  The kernel shape is the
+ * Every call uses the same array, so calls whose work overlaps on the GPU
+ * (other streams, other threads, other contexts of the process) race and
+ * corrupt each other; serialise them.  Each call rewrites all scratch it
+ * reads before reading it, so nothing needs clearing between calls.  The kernel shape is the
  * autotuner's cached choice for this graph shape if an earlier gift_filter
  * call made one, else a fixed default. */
 #define GIFT_NOALLOC_SCRATCH_BYTES (64u << 20)

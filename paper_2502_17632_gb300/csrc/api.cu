@@ -150,6 +150,7 @@ gift_status gift_ctx_create(int32_t device, gift_ctx **out) {
             for (int m = 2; m <= kWeightTable; ++m) wt[m] = 2.0 / (double)m;  // weight rule after Eq. 4
             GIFT_CUDA(cudaMalloc(&ctx->wtab, sizeof(double) * wt.size()));
             GIFT_CUDA(cudaMemcpy(ctx->wtab, wt.data(), sizeof(double) * wt.size(), cudaMemcpyHostToDevice));
+            noalloc_reserve(device);  // gift_filter_noalloc's fixed array, reserved now rather than in that call
         } catch (...) {
             if (ctx->dev_error) cudaFree(ctx->dev_error);
             if (ctx->wtab) cudaFree(ctx->wtab);

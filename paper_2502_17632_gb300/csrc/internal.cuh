@@ -280,6 +280,9 @@ void scan_nonfinite(gift_ctx *ctx, const float *x, int64_t n, int32_t *flag, cud
 float *host_mirror(void *p, size_t bytes);
 gift_graph::Scale graph_scale(gift_ctx *ctx, gift_graph *g, float sigma, int norm, cudaStream_t st);
 size_t filter_scratch_bytes(const gift_graph *g, const gift_filter_spec *spec, int S);
+// noalloc.cu: loads the no-alloc scratch array on `device` (current) and
+// caches its device address; throws on failure.
+void noalloc_reserve(int device);
 void filter_on_scratch(gift_ctx *ctx, const gift_graph *g, const gift_filter_spec *spec, const float *g_in, int S,
                        float *g_out, void *scratch, size_t scratch_bytes, cudaStream_t st);
 // hpwl.cu

@@ -5,9 +5,14 @@
 // where an allocation's latency or a failure mid-loop is not acceptable, or
 // hosts that hand this library device buffers but own the allocator.  For
 // them the filter's scratch (intermediate signals, accumulator, scale
-// vectors) lives in one file-scope device array of fixed size, allocated
-// when the library is loaded and held by every GPU that loads it until the
-// process exits.
+// vectors) lives in one file-scope device array of fixed size, held by every
+// GPU that loads it until the process exits.
+//
+// With lazy module loading the array is only reserved when its module is
+// first loaded on a device, which the address lookup below triggers.
+// gift_ctx_create does that lookup (noalloc_reserve), so the reservation, and
+// any failure to make it, happens when a context is created and never inside
+// a gift_filter_noalloc call.
 #include <map>
 #include <mutex>
 
@@ -33,6 +38,9 @@ void *scratch_address(int device) {
 }
 
 }  // namespace
+
+void noalloc_reserve(int device) { (void)scratch_address(device); }
+
 }  // namespace gift
 
 using namespace gift;
@@ -48,6 +56,9 @@ extern "C" gift_status gift_filter_noalloc(gift_ctx *ctx, const gift_graph *grap
             spec = &def;
         }
         GIFT_REQUIRE(num_signals >= 1, "gift_filter_noalloc: num_signals must be >= 1");
+        // the size estimate walks spec->term[0 .. num_terms): check the count first
+        GIFT_REQUIRE(spec->num_terms >= 1 && spec->num_terms <= GIFT_MAX_TERMS,
+                     "gift_filter_noalloc: num_terms out of range");
         const size_t need = filter_scratch_bytes(graph, spec, num_signals);
         if (need > (size_t)GIFT_NOALLOC_SCRATCH_BYTES)
             throw Failure{GIFT_ERR_INVALID, "gift_filter_noalloc: needs " + std::to_string(need) +

@@ -211,7 +211,14 @@ void gift_server::worker(int w) {
         cv_work.notify_all();  // the next request may fit as well
         std::string err;
         const gift_status s = guarded([&] { run(*r, st); });
-        if (s != GIFT_OK) err = gift_last_error();
+        if (s != GIFT_OK) {
+            err = gift_last_error();
+            // work queued before the failure may still read the request's
+            // input buffer or write its output buffer: let it finish before
+            // the buffers can go back to the pool
+            cudaStreamSynchronize(st);
+            cudaGetLastError();
+        }
         {
             std::lock_guard<std::mutex> lk(mu);
             r->t_done = Clock::now();

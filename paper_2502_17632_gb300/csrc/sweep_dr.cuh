@@ -59,7 +59,7 @@ __device__ __forceinline__ DrIdx<U> dr_load_idx(const SweepArgs &a, int64_t k0, 
     return r;
 }
 
-// Neumaier's compensated addition// Neumaier's compensated addition: s + e tracks the running sum exactly up
+// Neumaier's compensated addition: s + e tracks the running sum exactly up
 // to the rounding of e itself.
 __device__ __forceinline__ void comp_add(float &s, float &e, float x) {
     const float t = s + x;
