@@ -120,7 +120,13 @@ typedef struct gift_filter_spec {
  *   3000 + w               sliced ELL, slab of w columns
  *   4000 + 100*n + 10*cw + u   direct row groups: cw lanes per row, u gathers in
  *                          flight per lane; n bit 0: float2 lanes; n bit 1: rows
- *                          in natural order (else sorted by length per 256 rows)
+ *                          in natural order (else sorted by length per 256 rows);
+ *                          n bit 2: a whole warp per row (u = 4); n bit 3: rows
+ *                          sorted by length over the whole graph, read from a
+ *                          copy of the CSR in that order, or from the CSR
+ *                          itself when bit 1 is set too; n bit 4: the first
+ *                          sweep of two chains gathers a pre-scaled copy of g
+ *                          holding both chains' rows side by side
  *   10000 + code           as code, with the two chains of a two-chain sweep
  *                          run as separate launches
  * Any other value is GIFT_ERR_INVALID. */

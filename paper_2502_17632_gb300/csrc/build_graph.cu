@@ -913,6 +913,7 @@ void release_graph(gift_graph *g, cudaStream_t st) {
     }
     g->scales.clear();
     release_sell(g, st);
+    release_sorted(g, st);
     dev_free(g->order, st);
     g->order = nullptr;
     g->order_slots = 0;

@@ -62,12 +62,13 @@ static EncodeTiledFn encode_tiled() {
     return fn;
 }
 
-// 2-D map over a row-major [n][K] float signal, box = W columns x 1 row (gather4 rows).
-static CUtensorMap row_map(const float *base, int64_t n, int K, int W) {
+// 2-D map over a row-major float signal of n rows of K columns, rows ld floats
+// apart, box = W columns x 1 row (gather4 rows).
+static CUtensorMap row_map(const float *base, int64_t n, int K, int ld, int W) {
     CUtensorMap m;
     std::memset(&m, 0, sizeof(m));
     const cuuint64_t dims[2] = {(cuuint64_t)K, (cuuint64_t)std::max<int64_t>(n, 1)};
-    const cuuint64_t strides[1] = {(cuuint64_t)K * 4};
+    const cuuint64_t strides[1] = {(cuuint64_t)ld * 4};
     const cuuint32_t box[2] = {(cuuint32_t)W, 1};
     const cuuint32_t es[2] = {1, 1};
     EncodeTiledFn fn = encode_tiled();
@@ -160,7 +161,7 @@ struct NetSum {
     }
     // pins t0, t0 + step, ... below m of the net starting at nb, four at a time
     __device__ __forceinline__ void run(const int32_t *__restrict__ pin_cell, int64_t nb, int64_t t0, int64_t m,
-                                        int64_t step, int K, int c0, const float *__restrict__ x0,
+                                        int64_t step, int ld0, int ld1, int c0, const float *__restrict__ x0,
                                         const float *__restrict__ x1, const float *__restrict__ gp0,
                                         const float *__restrict__ gp1) {
         for (int64_t t = t0; t < m; t += 4 * step) {
@@ -172,12 +173,12 @@ struct NetSum {
 #pragma unroll
             for (int u = 0; u < 4; ++u) {
                 if (cell[u] < 0) continue;
-                v[u][0] = __ldg(reinterpret_cast<const float2 *>(x0 + (int64_t)cell[u] * K + c0));
+                v[u][0] = __ldg(reinterpret_cast<const float2 *>(x0 + (int64_t)cell[u] * ld0 + c0));
                 if (FIRST) {
                     sc[u][0] = gp0 ? __ldg(gp0 + cell[u]) : 1.f;
                     if (NC == 2) sc[u][NC - 1] = gp1 ? __ldg(gp1 + cell[u]) : 1.f;
                 } else if (NC == 2) {
-                    v[u][NC - 1] = __ldg(reinterpret_cast<const float2 *>(x1 + (int64_t)cell[u] * K + c0));
+                    v[u][NC - 1] = __ldg(reinterpret_cast<const float2 *>(x1 + (int64_t)cell[u] * ld1 + c0));
                 }
             }
 #pragma unroll
@@ -215,7 +216,8 @@ struct NetSum {
 
 template <int NC, bool FIRST>
 __global__ void k_net_sums(int64_t Eb, const int32_t *__restrict__ imp_net, const int64_t *__restrict__ net_ptr,
-                           const int32_t *__restrict__ pin_cell, int K, int LN, const float *__restrict__ x0,
+                           const int32_t *__restrict__ pin_cell, int K, int ld0, int ld1, int LN,
+                           const float *__restrict__ x0,
                            const float *__restrict__ x1, const float *__restrict__ gp0, const float *__restrict__ gp1,
                            float *__restrict__ S) {
     const int lane = threadIdx.x & 31;
@@ -234,7 +236,7 @@ __global__ void k_net_sums(int64_t Eb, const int32_t *__restrict__ imp_net, cons
         if (m <= kBigNet && b < Eb) {
             for (int c0 = 2 * gl; c0 < K; c0 += 2 * LN) {
                 NetSum<NC, FIRST> ns;
-                ns.run(pin_cell, nb, 0, m, 1, K, c0, x0, x1, gp0, gp1);
+                ns.run(pin_cell, nb, 0, m, 1, ld0, ld1, c0, x0, x1, gp0, gp1);
                 ns.store(S, b, K, c0);
             }
         }
@@ -247,7 +249,7 @@ __global__ void k_net_sums(int64_t Eb, const int32_t *__restrict__ imp_net, cons
             for (int cb = 0; cb < K; cb += 2 * LN) {  // all lanes iterate together
                 const int c0 = cb + 2 * gl;
                 NetSum<NC, FIRST> ns;
-                if (c0 < K) ns.run(pin_cell, nbb, grp, mb, NPW, K, c0, x0, x1, gp0, gp1);
+                if (c0 < K) ns.run(pin_cell, nbb, grp, mb, NPW, ld0, ld1, c0, x0, x1, gp0, gp1);
                 ns.tree(LN);
                 if (grp == 0 && c0 < K) ns.store(S, bb, K, c0);
             }
@@ -258,6 +260,36 @@ __global__ void k_net_sums(int64_t Eb, const int32_t *__restrict__ imp_net, cons
 __global__ void k_pack2(int64_t n, const float *__restrict__ a, const float *__restrict__ b, float2 *__restrict__ out) {
     for (int64_t i = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; i < n; i += (int64_t)gridDim.x * blockDim.x)
         out[i] = make_float2(a[i], b[i]);
+}
+
+// First sweep of a chain pair from a pre-scaled copy of g: out[i] = [pa_i g_i | pb_i g_i]
+// ([N][2][K]), so that one gathered 2K-float row serves both chains.  One
+// thread per float4 of the output.
+__global__ void k_prescale_pair(int64_t n, int K, const float *__restrict__ g, const float *__restrict__ pa,
+                                const float *__restrict__ pb, float *__restrict__ out) {
+    const int q4 = K / 4;  // float4 per chain half-row
+    const int64_t total = n * 2 * q4;
+    for (int64_t t = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; t < total; t += (int64_t)gridDim.x * blockDim.x) {
+        const int64_t i = t / (2 * q4);
+        const int r = (int)(t - i * 2 * q4);
+        const int half = r / q4, v = r - half * q4;
+        const float sc = __ldg((half ? pb : pa) + i);
+        const float4 x = __ldg(reinterpret_cast<const float4 *>(g + i * K) + v);
+        reinterpret_cast<float4 *>(out + i * 2 * K)[r] = make_float4(sc * x.x, sc * x.y, sc * x.z, sc * x.w);
+    }
+}
+__global__ void k_prescale_pair2(int64_t n, int K, const float *__restrict__ g, const float *__restrict__ pa,
+                                 const float *__restrict__ pb, float *__restrict__ out) {
+    const int q2 = K / 2;  // float2 per chain half-row
+    const int64_t total = n * 2 * q2;
+    for (int64_t t = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; t < total; t += (int64_t)gridDim.x * blockDim.x) {
+        const int64_t i = t / (2 * q2);
+        const int r = (int)(t - i * 2 * q2);
+        const int half = r / q2, v = r - half * q2;
+        const float sc = __ldg((half ? pb : pa) + i);
+        const float2 x = __ldg(reinterpret_cast<const float2 *>(g + i * K) + v);
+        reinterpret_cast<float2 *>(out + i * 2 * K)[r] = make_float2(sc * x.x, sc * x.y);
+    }
 }
 
 struct Chain {
@@ -331,7 +363,10 @@ struct Plan {
     float *dout;
     float *mirror = nullptr;  // the last sweep's output also goes here (mapped host memory)
     float *acc;
-    std::vector<std::array<float *, 2>> X;
+    // Y[gi][par]: input rows of chain group gi in the sweeps k >= 2 with
+    // k % 2 == par (and of a pre-scaled first sweep, par 1), the group's
+    // chains side by side ([N][nc][K]); sized by buffer_widths
+    std::vector<std::array<float *, 2>> Y;
     int32_t *counters;  // one zeroed tile counter per TMA launch
     int ncounters;
     // first-sweep gather scales of chains (2q, 2q+1), packed: gpre2[q] (null
@@ -343,6 +378,40 @@ struct Plan {
     // implicit cliques: net sums of the current chain group, [nets][2][K]
     float *S = nullptr;
 };
+
+// Where chain c runs in sweep k: chain group gi (pairs of consecutive active
+// chains share a group), its slot q in the group and the group's size nc.
+struct Place {
+    int gi = -1, q = 0, nc = 0;
+};
+std::vector<std::vector<Place>> placements(const std::vector<Chain> &chains, int Lmax) {
+    std::vector<std::vector<Place>> pl(Lmax + 2, std::vector<Place>(chains.size()));
+    for (int k = 1; k <= Lmax; ++k) {
+        std::vector<int> active;
+        for (size_t c = 0; c < chains.size(); ++c)
+            if (chains[c].L >= k) active.push_back((int)c);
+        for (size_t i = 0; i < active.size(); ++i) {
+            const int gi = (int)i / 2;
+            pl[k][active[i]] = Place{gi, (int)(i % 2), (int)std::min<size_t>(2, active.size() - 2 * (size_t)gi)};
+        }
+    }
+    return pl;
+}
+// Row width, in units of K, of every buffer Y[gi][par] (0: not needed).  A
+// group of two chains in the first sweep may gather a pre-scaled pair copy of
+// g (symmetric form), which lives in Y[gi][1].
+std::vector<std::array<int, 2>> buffer_widths(const std::vector<Chain> &chains, int Lmax, bool prescale_possible) {
+    const auto pl = placements(chains, Lmax);
+    std::vector<std::array<int, 2>> w((chains.size() + 1) / 2, std::array<int, 2>{0, 0});
+    for (int k = 1; k <= Lmax; ++k)
+        for (size_t c = 0; c < chains.size(); ++c) {
+            const Place &q = pl[k][c];
+            if (q.gi < 0) continue;
+            if (k >= 2) w[q.gi][k % 2] = std::max(w[q.gi][k % 2], q.nc);
+            else if (prescale_possible && q.nc == 2) w[q.gi][1] = std::max(w[q.gi][1], 2);
+        }
+    return w;
+}
 
 // Dynamic shared memory the TMA kernel is opted into, once per kernel.
 void tma_set_smem(const void *fn, int bytes) {
@@ -399,13 +468,15 @@ std::vector<std::pair<int, int>> slab_plan(const Plan &p, const Shape &shape) {
     return slabs;
 }
 
-// A chain group of one sweep: one or two chains sharing a launch.
+// A launch group of one sweep: one or two chains sharing a launch.
 struct Group {
     int c[2];
     int nc;
     int kind;             // launch kind of the launch(es)
     int planned;          // kind before a split (tuning attribution)
     const float2 *gpre2;  // packed first-sweep scales of the pair
+    int gi;               // chain group (layout of the signal rows)
+    bool prescaled;       // first sweep from the pre-scaled pair copy of g
 };
 
 // Launches every sweep of the filter; each launch uses the shape of its kind.
@@ -415,6 +486,7 @@ int run_sweeps(gift_ctx *ctx, const Plan &p, ShapeSet ss, cudaStream_t st, std::
                std::vector<cudaEvent_t> *pool = nullptr) {
     const gift_graph *g = p.g;
     const int64_t N = g->n;
+    const int K = p.K;
     const size_t wsz = g->weight_dtype == GIFT_WEIGHT_F32 ? 4 : 2;
     const double csr_bytes = (double)g->stored * (4.0 + wsz) + 8.0 * (N + 1);
     const double sig = 4.0 * (double)N * p.K;
@@ -426,6 +498,7 @@ int run_sweeps(gift_ctx *ctx, const Plan &p, ShapeSet ss, cudaStream_t st, std::
         GIFT_REQUIRE(shape.family != 2 || (p.vec == 4 && p.K % shape.a == 0),
                      "gift_filter: TMA schedule needs K a multiple of the slab and 16-byte aligned signals");
     }
+    const auto pl = placements(p.chains, p.Lmax);
     // chain groups of every sweep; only the kinds that launch prepare formats
     std::vector<std::vector<Group>> sweep_groups(p.Lmax + 1);
     std::vector<std::vector<int>> sweep_active(p.Lmax + 1);
@@ -438,30 +511,39 @@ int run_sweeps(gift_ctx *ctx, const Plan &p, ShapeSet ss, cudaStream_t st, std::
         for (size_t gi = 0; gi < active.size(); gi += 2) {
             const int nc = (int)std::min<size_t>(2, active.size() - gi);
             const int planned = launch_kind(nc, k);
-            const float2 *gp2 = (k == 1 && nc == 2 && gi / 2 < p.gpre2.size()) ? p.gpre2[gi / 2] : nullptr;
+            const int grp = (int)gi / 2;
+            const float2 *gp2 = (k == 1 && nc == 2 && grp < (int)p.gpre2.size()) ? p.gpre2[grp] : nullptr;
+            // a pre-scaled first sweep needs both chains' scales (symmetric form)
+            const bool pre = k == 1 && nc == 2 && ss.kind[0].prescale && p.sc[active[gi]].pre &&
+                             p.sc[active[gi + 1]].pre && p.Y[grp][1] != nullptr;
             if (nc == 2 && ss.split[planned]) {
                 for (int q = 0; q < 2; ++q)
-                    sweep_groups[k].push_back(Group{{active[gi + q], active[gi + q]}, 1, launch_kind(1, k), planned, nullptr});
+                    sweep_groups[k].push_back(
+                        Group{{active[gi + q], active[gi + q]}, 1, launch_kind(1, k), planned, nullptr, grp, pre});
             } else {
-                sweep_groups[k].push_back(Group{{active[gi], active[gi + nc - 1]}, nc, planned, planned, gp2});
+                sweep_groups[k].push_back(
+                    Group{{active[gi], active[gi + nc - 1]}, nc, planned, planned, gp2, grp, pre});
             }
             used[sweep_groups[k].back().kind] = true;
             planned_mask |= 1 << planned;
         }
     }
     int sell_rps = 0;
-    bool direct = false;
+    bool direct = false, sorted = false, sorted_copy = false;
     for (int kd = 0; kd < 4; ++kd) {
         if (!used[kd]) continue;
-        direct |= ss.kind[kd].family == 4 && !ss.kind[kd].natural;
+        direct |= ss.kind[kd].family == 4 && !ss.kind[kd].natural && !ss.kind[kd].sorted;
+        sorted |= ss.kind[kd].family == 4 && ss.kind[kd].sorted;
+        sorted_copy |= ss.kind[kd].family == 4 && ss.kind[kd].sorted && !ss.kind[kd].natural;
         if (ss.kind[kd].family != 3) continue;
         const int rps = 32 / (ss.kind[kd].a / p.vec);
         GIFT_REQUIRE(sell_rps == 0 || sell_rps == rps, "gift_filter: sliced-ELL kinds must share one slab width");
         sell_rps = rps;
     }
-    if (sell_rps || direct) {
+    if (sell_rps || direct || sorted) {
         std::lock_guard<std::mutex> lk(const_cast<gift_graph *>(g)->mu);
         if (direct) ensure_row_order(ctx, const_cast<gift_graph *>(g), st);
+        if (sorted) ensure_sorted(ctx, const_cast<gift_graph *>(g), sorted_copy, st);
         if (sell_rps && g->sell.rps != sell_rps) {
             release_sell(const_cast<gift_graph *>(g), st);
             build_sell(ctx, const_cast<gift_graph *>(g), sell_rps, st);
@@ -482,6 +564,7 @@ int run_sweeps(gift_ctx *ctx, const Plan &p, ShapeSet ss, cudaStream_t st, std::
         if (sweep_terms || last_sweep) sweep_bytes += (contributed ? sig : 0.0) + sig;
         if (last_sweep && p.reimpose) sweep_bytes += (double)N;
         bool first_launch = true;
+        int prescaled_done = -1;
 
         for (size_t gx = 0; gx < groups.size(); ++gx) {
             const Group &gr = groups[gx];
@@ -493,30 +576,74 @@ int run_sweeps(gift_ctx *ctx, const Plan &p, ShapeSet ss, cudaStream_t st, std::
             const Shape &shape = ss.kind[kind];
             const int sv = shape_vec(p, shape);
             const std::vector<std::pair<int, int>> &slabs = plans[kind];
+            // the group's input rows (chain c of the launch reads x_in[q], ld_in[q])
+            const float *x_in[2];
+            int ld_in[2];
+            const float *gp_in[2];
+            for (int q = 0; q < 2; ++q) {
+                const int c = gr.c[q];
+                const Place &at = pl[k][c];
+                if (k == 1 && gr.prescaled) {
+                    x_in[q] = p.Y[gr.gi][1] + at.q * K;
+                    ld_in[q] = 2 * K;
+                    gp_in[q] = nullptr;
+                } else if (k == 1) {
+                    x_in[q] = p.din;
+                    ld_in[q] = K;
+                    gp_in[q] = p.sc[c].pre;
+                } else {
+                    x_in[q] = p.Y[at.gi][k % 2] + at.q * K;
+                    ld_in[q] = at.nc * K;
+                    gp_in[q] = nullptr;
+                }
+            }
+            const bool first = k == 1 && !gr.prescaled;  // gathers the unscaled g
+            if (k == 1 && gr.prescaled && prescaled_done != gr.gi) {
+                // [pre_a g | pre_b g], timed with the sweeps (it replaces the first sweep's scale gathers)
+                const int ca = active[2 * gr.gi], cb = active[2 * gr.gi + 1];
+                LaunchTimer lt(ctx, st, "filter.sweep", 0.0);
+                TimedLaunch tl{gr.planned, nullptr, nullptr};
+                if (timed) {  // tuning: the copy counts towards the first sweep's kind
+                    tl.e0 = pool->back(); pool->pop_back();
+                    tl.e1 = pool->back(); pool->pop_back();
+                    GIFT_CUDA(cudaEventRecord(tl.e0, st));
+                }
+                const int64_t work = N * 2 * (K / p.vec);
+                const int grid = (int)std::max<int64_t>(1, std::min<int64_t>(ceil_div(work, 256), (int64_t)ctx->num_sms * 8));
+                if (p.vec == 4)
+                    k_prescale_pair<<<grid, 256, 0, st>>>(N, K, p.din, p.sc[ca].pre, p.sc[cb].pre, p.Y[gr.gi][1]);
+                else
+                    k_prescale_pair2<<<grid, 256, 0, st>>>(N, K, p.din, p.sc[ca].pre, p.sc[cb].pre, p.Y[gr.gi][1]);
+                check_launch("k_prescale_pair");
+                if (timed) {
+                    GIFT_CUDA(cudaEventRecord(tl.e1, st));
+                    timed->push_back(tl);
+                }
+                prescaled_done = gr.gi;
+            }
             ImplicitArgs imp{nullptr, nullptr, nullptr, nullptr, 0};
             if (g->imp_nets > 0) {  // the group's net sums, all K columns
-                const int c0 = gr.c[0], c1 = gr.c[nc - 1];
-                const float *x0 = k == 1 ? p.din : p.X[c0][(k - 1) % 2];
-                const float *x1 = k == 1 ? p.din : p.X[c1][(k - 1) % 2];
-                const float *gp0 = k == 1 ? p.sc[c0].pre : nullptr, *gp1 = k == 1 ? p.sc[c1].pre : nullptr;
+                const float *x0 = x_in[0], *x1 = x_in[nc - 1];
+                const float *gp0 = first ? gp_in[0] : nullptr, *gp1 = first ? gp_in[nc - 1] : nullptr;
                 int LN = 1;
                 while (LN < 32 && 2 * LN < p.K) LN <<= 1;
                 const int grid = (int)std::max<int64_t>(
                     1, std::min<int64_t>(ceil_div(g->imp_nets * LN, 256), (int64_t)ctx->num_sms * 16));
                 LaunchTimer lt(ctx, st, "filter.netsums",
                                4.0 * g->imp_pins * (1 + p.K * (k == 1 ? 1 : nc)) + 4.0 * g->imp_nets * nc * p.K);
-                if (k == 1 && nc == 2)
-                    k_net_sums<2, true><<<grid, 256, 0, st>>>(g->imp_nets, g->imp_net, g->net_ptr, g->pin_cell, p.K, LN,
-                                                              x0, x1, gp0, gp1, p.S);
-                else if (k == 1)
-                    k_net_sums<1, true><<<grid, 256, 0, st>>>(g->imp_nets, g->imp_net, g->net_ptr, g->pin_cell, p.K, LN,
-                                                              x0, x1, gp0, gp1, p.S);
+                const int l0 = ld_in[0], l1 = ld_in[nc - 1];
+                if (first && nc == 2)
+                    k_net_sums<2, true><<<grid, 256, 0, st>>>(g->imp_nets, g->imp_net, g->net_ptr, g->pin_cell, p.K, l0,
+                                                              l1, LN, x0, x1, gp0, gp1, p.S);
+                else if (first)
+                    k_net_sums<1, true><<<grid, 256, 0, st>>>(g->imp_nets, g->imp_net, g->net_ptr, g->pin_cell, p.K, l0,
+                                                              l1, LN, x0, x1, gp0, gp1, p.S);
                 else if (nc == 2)
-                    k_net_sums<2, false><<<grid, 256, 0, st>>>(g->imp_nets, g->imp_net, g->net_ptr, g->pin_cell, p.K, LN,
-                                                               x0, x1, gp0, gp1, p.S);
+                    k_net_sums<2, false><<<grid, 256, 0, st>>>(g->imp_nets, g->imp_net, g->net_ptr, g->pin_cell, p.K,
+                                                               l0, l1, LN, x0, x1, gp0, gp1, p.S);
                 else
-                    k_net_sums<1, false><<<grid, 256, 0, st>>>(g->imp_nets, g->imp_net, g->net_ptr, g->pin_cell, p.K, LN,
-                                                               x0, x1, gp0, gp1, p.S);
+                    k_net_sums<1, false><<<grid, 256, 0, st>>>(g->imp_nets, g->imp_net, g->net_ptr, g->pin_cell, p.K,
+                                                               l0, l1, LN, x0, x1, gp0, gp1, p.S);
                 check_launch("k_net_sums");
                 imp = ImplicitArgs{g->imp_ptr, g->imp_idx, g->imp_w, p.S, nc * p.K};
             }
@@ -530,7 +657,7 @@ int run_sweeps(gift_ctx *ctx, const Plan &p, ShapeSet ss, cudaStream_t st, std::
                 a.n_rows = N;
                 a.K = p.K;
                 a.c0 = c0;
-                a.gpre2 = gr.gpre2;
+                a.gpre2 = first ? gr.gpre2 : nullptr;
                 a.imp = imp;
                 const double bytes = first_launch ? sweep_bytes : 0.0;
                 first_launch = false;
@@ -538,13 +665,21 @@ int run_sweeps(gift_ctx *ctx, const Plan &p, ShapeSet ss, cudaStream_t st, std::
                     const int c = gr.c[q];
                     const Chain &ch = p.chains[c];
                     ChainIO &io = a.ch[q];
-                    io.x = k == 1 ? p.din : p.X[c][(k - 1) % 2];
-                    io.gpre = k == 1 ? p.sc[c].pre : nullptr;
+                    io.x = x_in[q];
+                    io.ldx = ld_in[q];
+                    io.gpre = first ? gp_in[q] : nullptr;
                     io.post = p.sc[c].post;
                     io.sigma = ch.sigma;
                     io.alpha = (float)ch.alpha_at[k];
                     io.has_term = ch.has_at[k] ? 1 : 0;
-                    io.xnext = ch.L > k ? p.X[c][k % 2] : nullptr;
+                    if (ch.L > k) {
+                        const Place &nx = pl[k + 1][c];
+                        io.xnext = p.Y[nx.gi][(k + 1) % 2] + nx.q * K;
+                        io.ldn = nx.nc * K;
+                    } else {
+                        io.xnext = nullptr;
+                        io.ldn = K;
+                    }
                     io.pnext = p.sc[c].pre;
                 }
                 if (last) {
@@ -559,7 +694,7 @@ int run_sweeps(gift_ctx *ctx, const Plan &p, ShapeSet ss, cudaStream_t st, std::
                     a.acc_in = contributed ? p.acc : nullptr;
                     a.acc_out = p.acc;
                 }
-                const int nx = k == 1 ? 1 : nc;
+                const int nx = first ? 1 : nc;
                 const void *fn = nullptr;
                 int threads = kSweepThreads;
                 int grid = 1;
@@ -577,8 +712,8 @@ int run_sweeps(gift_ctx *ctx, const Plan &p, ShapeSet ss, cudaStream_t st, std::
                     GIFT_REQUIRE(stages >= 2, "gift_filter: not enough shared memory for the TMA pipeline");
                     smem = stages * stage_bytes + 1024;
                     tma_set_smem(fn, smem);
-                    m0 = row_map(a.ch[0].x, N, p.K, W);
-                    m1 = nx == 2 ? row_map(a.ch[1].x, N, p.K, W) : m0;
+                    m0 = row_map(a.ch[0].x, N, p.K, a.ch[0].ldx, W);
+                    m1 = nx == 2 ? row_map(a.ch[1].x, N, p.K, a.ch[1].ldx, W) : m0;
                     t.tiles = ceil_div(std::max<int64_t>(N, 1), kTmaRows);
                     t.stages = stages;
                     t.stage_bytes = stage_bytes;
@@ -595,7 +730,7 @@ int run_sweeps(gift_ctx *ctx, const Plan &p, ShapeSet ss, cudaStream_t st, std::
                     sa.perm = g->sell.perm;
                     sa.col = g->sell.col;
                     sa.val = g->sell.val;
-                    sa.gpre2 = (k == 1 && nc == 2) ? gr.gpre2 : nullptr;
+                    sa.gpre2 = (first && nc == 2) ? gr.gpre2 : nullptr;
                     threads = kSellThreads;
                     const int64_t want = ceil_div(std::max<int64_t>(sa.nslices, 1), kSellWarps);
                     grid = (int)std::max<int64_t>(
@@ -610,9 +745,19 @@ int run_sweeps(gift_ctx *ctx, const Plan &p, ShapeSet ss, cudaStream_t st, std::
                     } else if (shape.family == 4) {
                         const bool wr = shape.warp_rows || p.comp;
                         const int u = wr ? 4 : (sv == 4 || nc == 2) ? std::min(shape.b, 4) : shape.b;
-                        fn = sweep_dr_kernel(g->weight_dtype, sv, cw, u, nc, k == 1, wr, p.comp);
+                        fn = sweep_dr_kernel(g->weight_dtype, sv, cw, u, nc, first, wr, p.comp);
                         rows_per_block = (kSweepThreads / 32) * (wr ? 1 : 32 / cw);
-                        if (!shape.natural) {
+                        if (shape.sorted && !shape.natural) {  // the sorted copy
+                            a.row_ptr = g->srt.rp;
+                            a.col = g->srt.col;
+                            a.val = g->srt.val;
+                            a.order = g->srt.perm;
+                            a.n_slots = N;
+                            a.slot_csr = 1;
+                        } else if (shape.sorted) {  // sorted order over the CSR itself
+                            a.order = g->srt.perm;
+                            a.n_slots = N;
+                        } else if (!shape.natural) {
                             a.order = g->order;
                             a.n_slots = g->order_slots;
                         }
@@ -661,7 +806,10 @@ std::string tune_key(const gift_graph *g, int vec, int K, const Plan &p) {
 // 3000 + w (sliced ELL), 4000 + 100*n + 10*cw + u (direct row groups:
 // cw lanes per row, u gathers in flight per lane; n bit 0: float2 lanes,
 // n bit 1: rows in natural order rather than the graph's row order, n bit 2:
-// a whole warp per row, its nonzeros split over 32 / cw lane groups)
+// a whole warp per row, its nonzeros split over 32 / cw lane groups, n bit 3:
+// rows sorted by length over the whole graph, read from a copy of the CSR in
+// that order or, with bit 1 also set, from the CSR itself, n bit 4: the first
+// sweep of a chain pair gathers a pre-scaled pair copy of g)
 Shape shape_from_schedule(int schedule) {
     if (schedule >= 4000) {
         Shape s{4, (schedule / 10) % 10, schedule % 10};
@@ -669,7 +817,9 @@ Shape shape_from_schedule(int schedule) {
         s.narrow = n & 1;
         s.natural = (n >> 1) & 1;
         s.warp_rows = (n >> 2) & 1;
-        if (n > 7) s.narrow = 2;  // invalid
+        s.sorted = (n >> 3) & 1;
+        s.prescale = (n >> 4) & 1;
+        if (n > 31) s.narrow = 2;  // invalid
         return s;
     }
     if (schedule >= 3000) return Shape{3, schedule - 3000, 1};
@@ -689,7 +839,9 @@ Shape comp_shape() {
 }
 
 int schedule_code(const Shape &sh) {
-    if (sh.family == 4) return 4000 + 100 * (sh.narrow + 2 * sh.natural + 4 * sh.warp_rows) + 10 * sh.a + sh.b;
+    if (sh.family == 4)
+        return 4000 + 100 * (sh.narrow + 2 * sh.natural + 4 * sh.warp_rows + 8 * sh.sorted + 16 * sh.prescale) +
+               10 * sh.a + sh.b;
     return sh.family >= 1 ? 1000 * sh.family + sh.a : 100 * sh.a + sh.b;
 }
 
@@ -719,6 +871,10 @@ ShapeSet autotune(gift_ctx *ctx, const Plan &p, cudaStream_t st) {
         }
     }
     std::vector<Shape> cands;
+    // a first sweep of two chains with pre scales: the pre-scaled pair copy applies
+    bool pair_first = false;
+    for (size_t c = 0; c + 1 < p.chains.size(); c += 2)
+        pair_first |= p.sc[c].pre && p.sc[c + 1].pre && !p.Y.empty() && p.Y[c / 2][1] != nullptr;
     // TMA gather4 (family 2) measured ~4x slower than LSU gathers for 64-byte
     // random rows on GB300; it stays available as an explicit schedule only.
     // One sliced-ELL width (the widest) so that every kind shares its format.
@@ -736,15 +892,23 @@ ShapeSet autotune(gift_ctx *ctx, const Plan &p, cudaStream_t st) {
         for (int cw : {cwmax, cwmax / 2})
             if (cw >= 1)
                 for (int u : {2, 4, 8})
-                    for (int natural = 0; natural <= 1; ++natural) {
+                    // window order, natural, sorted over the CSR, sorted copy
+                    for (int order = 0; order <= 3; ++order) {
                         if (u == 8 && sv == 4) continue;
                         Shape sh{4, cw, u};
                         sh.narrow = narrow;
-                        sh.natural = natural;
+                        sh.natural = order == 1 || order == 2;
+                        sh.sorted = order >= 2;
                         cands.push_back(sh);
-                        if (u == 4 && natural) {  // a warp per row, for long rows
-                            sh.warp_rows = 1;
-                            cands.push_back(sh);
+                        if (u == 4 && order >= 1) {  // a warp per row, for long rows
+                            Shape w = sh;
+                            w.warp_rows = 1;
+                            cands.push_back(w);
+                        }
+                        if (order >= 1 && pair_first && cw == cwmax && u == 4) {  // pre-scaled pair copy
+                            Shape w = sh;
+                            w.prescale = 1;
+                            cands.push_back(w);
                         }
                     }
     }
@@ -935,15 +1099,17 @@ void filter_impl(gift_ctx *ctx, const gift_graph *cg, const gift_filter_spec *sp
     GIFT_REQUIRE(al8, "gift_filter: device signal pointers must be 8-byte aligned");
     p.vec = (K % 4 == 0 && al16) ? 4 : 2;
 
-    std::vector<DevBuf> xbuf;  // two per chain with L >= 2
-    p.X.assign(p.chains.size(), {nullptr, nullptr});
-    for (size_t c = 0; c < p.chains.size(); ++c)
-        if (p.chains[c].L >= 2) {
-            xbuf.emplace_back(ctx, sig_bytes, st);
-            p.X[c][0] = xbuf.back().as<float>();
-            xbuf.emplace_back(ctx, sig_bytes, st);
-            p.X[c][1] = xbuf.back().as<float>();
-        }
+    std::vector<DevBuf> ybuf;  // chain-group input rows, two parities per group
+    {
+        const auto widths = buffer_widths(p.chains, p.Lmax, spec->norm == GIFT_NORM_SYM);
+        p.Y.assign(widths.size(), {nullptr, nullptr});
+        for (size_t gi = 0; gi < widths.size(); ++gi)
+            for (int par = 0; par < 2; ++par)
+                if (widths[gi][par] > 0) {
+                    ybuf.emplace_back(ctx, sig_bytes * widths[gi][par], st);
+                    p.Y[gi][par] = ybuf.back().as<float>();
+                }
+    }
     DevBuf acc_buf(ctx, sig_bytes, st);
     p.acc = acc_buf.as<float>();
     DevBuf s_buf;
@@ -1011,24 +1177,26 @@ void filter_impl(gift_ctx *ctx, const gift_graph *cg, const gift_filter_spec *sp
 // device allocation.  The kernel shape is the autotuner's cached choice for
 // this graph shape when one exists and needs no allocation, else row groups.
 size_t filter_scratch_bytes(const gift_graph *g, const gift_filter_spec *spec, int S) {
-    std::vector<float> sigmas;
-    std::vector<int> L;
+    std::vector<Chain> chains;
+    int Lmax = 0;
     for (int t = 0; t < spec->num_terms; ++t) {
         size_t c = 0;
-        while (c < sigmas.size() && sigmas[c] != spec->term[t].sigma) ++c;
-        if (c == sigmas.size()) {
-            sigmas.push_back(spec->term[t].sigma);
-            L.push_back(0);
+        while (c < chains.size() && chains[c].sigma != spec->term[t].sigma) ++c;
+        if (c == chains.size()) {
+            chains.push_back(Chain{});
+            chains.back().sigma = spec->term[t].sigma;
         }
-        L[c] = std::max(L[c], spec->term[t].power);
+        chains[c].L = std::max(chains[c].L, std::min(std::max(spec->term[t].power, 1), 64));
+        Lmax = std::max(Lmax, chains[c].L);
     }
     const size_t sig = sizeof(float) * (size_t)g->n * 2 * S;
-    size_t bytes = sig;                                         // accumulator
-    for (int l : L) bytes += l >= 2 ? 2 * sig : 0;              // ping-pong inputs
-    bytes += sigmas.size() * ((sizeof(float) * g->n + 255) / 256 * 256);  // scale vectors
-    bytes += sigmas.size() / 2 * ((sizeof(float2) * g->n + 255) / 256 * 256);  // packed first-sweep scales
+    size_t bytes = sig;  // accumulator
+    for (const auto &w : buffer_widths(chains, Lmax, spec->norm == GIFT_NORM_SYM))  // chain-group inputs
+        bytes += (w[0] + w[1]) * ((sig + 255) / 256 * 256);
+    bytes += chains.size() * ((sizeof(float) * g->n + 255) / 256 * 256);  // scale vectors
+    bytes += chains.size() / 2 * ((sizeof(float2) * g->n + 255) / 256 * 256);  // packed first-sweep scales
     bytes += (sizeof(float) * (size_t)g->imp_nets * 2 * 2 * S + 255) / 256 * 256;  // implicit net sums
-    return bytes + 256 * (8 + 2 * sigmas.size());               // alignment slack
+    return bytes + 256 * (8 + 2 * chains.size());  // alignment slack
 }
 
 __global__ void k_scale_into(int64_t n, const double *__restrict__ d, double sigma, int norm, float *__restrict__ out) {
@@ -1092,12 +1260,13 @@ void filter_on_scratch(gift_ctx *ctx, const gift_graph *g, const gift_filter_spe
     };
     p.acc = static_cast<float *>(take(sig_bytes));
     if (g->imp_nets > 0) p.S = static_cast<float *>(take(sizeof(float) * (size_t)g->imp_nets * 2 * K));
-    p.X.assign(p.chains.size(), {nullptr, nullptr});
-    for (size_t c = 0; c < p.chains.size(); ++c)
-        if (p.chains[c].L >= 2) {
-            p.X[c][0] = static_cast<float *>(take(sig_bytes));
-            p.X[c][1] = static_cast<float *>(take(sig_bytes));
-        }
+    {
+        const auto widths = buffer_widths(p.chains, p.Lmax, spec->norm == GIFT_NORM_SYM);
+        p.Y.assign(widths.size(), {nullptr, nullptr});
+        for (size_t gi = 0; gi < widths.size(); ++gi)
+            for (int par = 0; par < 2; ++par)
+                if (widths[gi][par] > 0) p.Y[gi][par] = static_cast<float *>(take(sig_bytes * widths[gi][par]));
+    }
     p.sc.resize(p.chains.size());
     const int grid = (int)std::max<int64_t>(1, std::min<int64_t>(ceil_div(N, 256), (int64_t)ctx->num_sms * 8));
     for (size_t c = 0; c < p.chains.size(); ++c) {
@@ -1151,7 +1320,8 @@ void filter_on_scratch(gift_ctx *ctx, const gift_graph *g, const gift_filter_spe
     for (int kd = 0; kd < 4; ++kd) {
         const Shape t = ss.kind[kd];
         const int rps = t.family == 3 ? 32 / (sell_width(p, t.a) / p.vec) : 0;
-        ok[kd] = t.family == 0 || t.family == 1 || (t.family == 4 && (t.natural || g->order)) ||
+        ok[kd] = t.family == 0 || t.family == 1 ||
+                 (t.family == 4 && (t.sorted ? g->srt.perm && (t.natural || g->srt.col) : (t.natural || g->order))) ||
                  (t.family == 3 && g->sell.rps == rps);
         if (!ok[kd]) ss.kind[kd] = Shape{0, 4, 8};
     }

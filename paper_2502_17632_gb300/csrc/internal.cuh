@@ -74,6 +74,10 @@ struct TunedShape {
     int narrow = 0;   // direct family: float2 lanes instead of the signal's widest vector
     int natural = 0;  // direct family: rows in natural order instead of the graph's row order
     int warp_rows = 0;  // direct family: a whole warp per row (nonzeros split over lane groups)
+    int sorted = 0;   // direct family: rows sorted by length over the whole graph; read from
+                      // the CSR copied in that order, or (with natural = 1) from the CSR itself
+    int prescale = 0;  // first sweep of a chain pair: gather a pre-scaled [N][2][K] copy of g
+                       // instead of g and the scale pair (kind 0 only)
 };
 // tuned shape per launch kind (see filter.cu); split[kind] for the two-chain
 // kinds 0 and 1: run each chain as its own launch with the one-chain shape
@@ -241,6 +245,16 @@ struct gift_graph {
     float *imp_w = nullptr;      // [imp_nets] 2/M rounded to FP32
     int64_t *imp_ptr = nullptr;  // [N + 1] each cell's implicit incidences
     int32_t *imp_idx = nullptr;  // [imp_inc] index into imp_net, increasing per cell (repeated per pin)
+    // rows sorted by length over the whole graph (longest first): slot s holds
+    // row perm[s]; with the copy, its entries are [rp[s], rp[s + 1]) of col /
+    // val (built on first use by a schedule that walks it; each row keeps its
+    // entries in CSR order)
+    struct Sorted {
+        int32_t *perm = nullptr;
+        int64_t *rp = nullptr;
+        int32_t *col = nullptr;
+        void *val = nullptr;
+    } srt;
     // sliced-ELL execution format (built on first use by a sliced-ELL schedule)
     struct Sell {
         int rps = 0;              // rows per slice (0: not built)
@@ -266,6 +280,10 @@ void ensure_row_order(gift_ctx *ctx, gift_graph *g, cudaStream_t st);
 // sell.cu
 void build_sell(gift_ctx *ctx, gift_graph *g, int rps, cudaStream_t st);
 void release_sell(gift_graph *g, cudaStream_t st);
+// builds g->srt's row order (and, with copy, the CSR copy in that order) if
+// absent (caller holds g->mu)
+void ensure_sorted(gift_ctx *ctx, gift_graph *g, bool copy, cudaStream_t st);
+void release_sorted(gift_graph *g, cudaStream_t st);
 // filter.cu
 // mirror (optional): the last sweep also stores the output there -- mapped
 // host memory (host_mirror), so the result reaches the host while the sweep

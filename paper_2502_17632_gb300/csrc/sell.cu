@@ -93,7 +93,176 @@ __global__ void k_sell_fill(int64_t nslices, int rps, const int64_t *__restrict_
     }
 }
 
+// ---- rows sorted by length over the whole graph (the sorted CSR copy).
+// A counting sort on a key of the row length, longest first: lengths below
+// 192 exactly, longer rows in buckets 64 entries wide (the last one open).
+// Blocks own chunks of kSortChunk rows: each counts its rows per key, a scan
+// of the (key, block) counts gives every block its range inside every key, and
+// a row's rank inside its block's range comes from a shared-memory counter, so
+// equal-length rows may be placed in another order from one build to the next.
+// No result depends on it: every row is summed alone in its own CSR order,
+// whatever slot it takes.
+constexpr int kSortKeys = 256;
+constexpr int kSortChunk = 4096;
+
+__device__ __forceinline__ int len_key(int64_t len) {
+    const int64_t over = len < 192 ? 0 : (len - 192) >> 6;
+    const int b = len < 192 ? (int)len : 192 + (int)(over < 63 ? over : 63);
+    return kSortKeys - 1 - b;
+}
+
+// Rank of this lane among the active lanes of its warp with the same key, after
+// adding the group's count to ctr[key] once per key (returns the old value + rank).
+__device__ __forceinline__ int warp_add(int *ctr, int key, unsigned act) {
+    const int lane = threadIdx.x & 31;
+    const unsigned peers = __match_any_sync(act, key);
+    const int leader = __ffs(peers) - 1;
+    int base = 0;
+    if (lane == leader) base = atomicAdd(&ctr[key], __popc(peers));
+    base = __shfl_sync(peers, base, leader);
+    return base + __popc(peers & ((1u << lane) - 1u));
+}
+
+__global__ void __launch_bounds__(256) k_sort_count(int64_t n, const int64_t *__restrict__ row_ptr, int64_t nblocks,
+                                                    int32_t *__restrict__ counts) {
+    __shared__ int cnt[kSortKeys];
+    for (int k = threadIdx.x; k < kSortKeys; k += blockDim.x) cnt[k] = 0;
+    __syncthreads();
+    const int64_t r0 = blockIdx.x * (int64_t)kSortChunk;
+    for (int i = 0; i < kSortChunk; i += blockDim.x) {
+        const int64_t r = r0 + i + threadIdx.x;
+        const bool valid = r < n;
+        const unsigned act = __ballot_sync(0xffffffffu, valid);
+        if (valid) warp_add(cnt, len_key(row_ptr[r + 1] - row_ptr[r]), act);
+    }
+    __syncthreads();
+    for (int k = threadIdx.x; k < kSortKeys; k += blockDim.x) counts[(int64_t)k * nblocks + blockIdx.x] = cnt[k];
+}
+
+__global__ void __launch_bounds__(256) k_sort_place(int64_t n, const int64_t *__restrict__ row_ptr, int64_t nblocks,
+                                                    const int64_t *__restrict__ offs, int32_t *__restrict__ perm,
+                                                    int64_t *__restrict__ len) {
+    __shared__ int cur[kSortKeys];
+    __shared__ int64_t base[kSortKeys];
+    for (int k = threadIdx.x; k < kSortKeys; k += blockDim.x) {
+        cur[k] = 0;
+        base[k] = offs[(int64_t)k * nblocks + blockIdx.x];
+    }
+    __syncthreads();
+    const int64_t r0 = blockIdx.x * (int64_t)kSortChunk;
+    for (int i = 0; i < kSortChunk; i += blockDim.x) {
+        const int64_t r = r0 + i + threadIdx.x;
+        const bool valid = r < n;
+        const unsigned act = __ballot_sync(0xffffffffu, valid);
+        if (valid) {
+            const int64_t l = row_ptr[r + 1] - row_ptr[r];
+            const int key = len_key(l);
+            const int64_t slot = base[key] + warp_add(cur, key, act);
+            perm[slot] = (int32_t)r;
+            len[slot] = l;
+        }
+    }
+}
+
+// A warp per 32 consecutive slots: their entries are one contiguous range of
+// the copy, written lane by lane (coalesced); lane l finds the slot of its
+// entry by a binary search over the 32 slot starts held one per lane.
+template <typename WT>
+__global__ void k_copy_sorted(int64_t n, const int64_t *__restrict__ row_ptr, const int32_t *__restrict__ col,
+                              const WT *__restrict__ val, const int32_t *__restrict__ perm,
+                              const int64_t *__restrict__ rp2, int32_t *__restrict__ col2, WT *__restrict__ val2) {
+    const int lane = threadIdx.x & 31;
+    const int64_t warp = (blockIdx.x * (int64_t)blockDim.x + threadIdx.x) >> 5;
+    const int64_t nwarps = ((int64_t)gridDim.x * blockDim.x) >> 5;
+    for (int64_t s0 = warp * 32; s0 < n; s0 += nwarps * 32) {
+        const int64_t s = s0 + lane;
+        const int64_t start = rp2[s < n ? s : n];                    // slot start (n: the end)
+        const int64_t src = s < n ? row_ptr[perm[s]] : 0;            // the row's first entry in the CSR
+        const int64_t b = __shfl_sync(0xffffffffu, start, 0);
+        const int64_t e = rp2[s0 + 32 < n ? s0 + 32 : n];
+        for (int64_t p0 = b; p0 < e; p0 += 32) {  // same trip count on every lane
+            const int64_t p = p0 + lane;
+            int lo = 0;  // last slot i of the 32 with start_i <= p
+#pragma unroll
+            for (int step = 16; step >= 1; step >>= 1) {
+                const int64_t v = __shfl_sync(0xffffffffu, start, lo + step);
+                if (v <= p) lo += step;
+            }
+            const int64_t si = __shfl_sync(0xffffffffu, start, lo);
+            const int64_t sr = __shfl_sync(0xffffffffu, src, lo);
+            if (p < e) {
+                col2[p] = col[sr + (p - si)];
+                val2[p] = val[sr + (p - si)];
+            }
+        }
+    }
+}
+
 }  // namespace
+
+void ensure_sorted(gift_ctx *ctx, gift_graph *g, bool copy, cudaStream_t st) {
+    const int64_t N = g->n;
+    const size_t wsz = g->weight_dtype == GIFT_WEIGHT_F32 ? 4 : 2;
+    if (!g->srt.perm) {
+        const int64_t nblocks = std::max<int64_t>(1, ceil_div(N, kSortChunk));
+        DevBuf counts(ctx, sizeof(int32_t) * kSortKeys * nblocks, st);
+        DevBuf offs(ctx, sizeof(int64_t) * (kSortKeys * nblocks + 1), st);
+        DevBuf perm(ctx, sizeof(int32_t) * std::max<int64_t>(N, 1), st);
+        DevBuf len(ctx, sizeof(int64_t) * std::max<int64_t>(N, 1), st);
+        DevBuf rp(ctx, sizeof(int64_t) * (N + 1), st);
+        {
+            LaunchTimer lt(ctx, st, "build.sorted", 36.0 * N, 8);
+            k_sort_count<<<(unsigned)nblocks, 256, 0, st>>>(N, g->row_ptr, nblocks, counts.as<int32_t>());
+            check_launch("k_sort_count");
+            exclusive_scan(ctx, counts.as<int32_t>(), offs.as<int64_t>(), kSortKeys * nblocks, st);
+            k_sort_place<<<(unsigned)nblocks, 256, 0, st>>>(N, g->row_ptr, nblocks, offs.as<int64_t>(),
+                                                            perm.as<int32_t>(), len.as<int64_t>());
+            check_launch("k_sort_place");
+            exclusive_scan(ctx, len.as<int64_t>(), rp.as<int64_t>(), N, st);
+        }
+        g->srt.perm = perm.as<int32_t>();
+        g->srt.rp = rp.as<int64_t>();
+        perm.release();
+        rp.release();
+        g->device_bytes += (int64_t)(4 * N + 8 * (N + 1));
+    }
+    if (copy && !g->srt.col) {
+        DevBuf col(ctx, sizeof(int32_t) * std::max<int64_t>(g->stored, 1), st);
+        DevBuf val(ctx, wsz * std::max<int64_t>(g->stored, 1), st);
+        {
+            LaunchTimer lt(ctx, st, "build.sorted_copy", 12.0 * N + (double)g->stored * 2.0 * (4.0 + wsz));
+            const int cgrid =
+                (int)std::max<int64_t>(1, std::min<int64_t>(ceil_div(N, 256), (int64_t)ctx->num_sms * 8));
+            if (g->weight_dtype == GIFT_WEIGHT_F32)
+                k_copy_sorted<float><<<cgrid, 256, 0, st>>>(N, g->row_ptr, g->col, (const float *)g->val,
+                                                            g->srt.perm, g->srt.rp, col.as<int32_t>(),
+                                                            val.as<float>());
+            else if (g->weight_dtype == GIFT_WEIGHT_BF16)
+                k_copy_sorted<__nv_bfloat16><<<cgrid, 256, 0, st>>>(N, g->row_ptr, g->col,
+                                                                    (const __nv_bfloat16 *)g->val, g->srt.perm,
+                                                                    g->srt.rp, col.as<int32_t>(),
+                                                                    val.as<__nv_bfloat16>());
+            else
+                k_copy_sorted<__half><<<cgrid, 256, 0, st>>>(N, g->row_ptr, g->col, (const __half *)g->val,
+                                                             g->srt.perm, g->srt.rp, col.as<int32_t>(),
+                                                             val.as<__half>());
+            check_launch("k_copy_sorted");
+        }
+        g->srt.col = col.as<int32_t>();
+        g->srt.val = val.p;
+        col.release();
+        val.release();
+        g->device_bytes += (int64_t)((4 + wsz) * g->stored);
+    }
+}
+
+void release_sorted(gift_graph *g, cudaStream_t st) {
+    dev_free(g->srt.perm, st);
+    dev_free(g->srt.rp, st);
+    dev_free(g->srt.col, st);
+    dev_free(g->srt.val, st);
+    g->srt = gift_graph::Sorted{};
+}
 
 void ensure_row_order(gift_ctx *ctx, gift_graph *g, cudaStream_t st) {
     if (g->order) return;

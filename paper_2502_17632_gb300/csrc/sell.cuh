@@ -117,9 +117,9 @@ __global__ void __launch_bounds__(kSellThreads) k_sweep_sell(const SweepArgs a, 
 #pragma unroll
         for (int u = 0; u < U; ++u) {
             if (p.sl < s.nslices && p.k0 + u < p.width) {
-                const int64_t off = (int64_t)j[u] * a.K + col;
-                cp_async<XB>(&xs_all[wid][st][u][0][lane * VEC], x0 + off);
-                if (NX == 2) cp_async<XB>(&xs_all[wid][st][u][NX - 1][lane * VEC], x1 + off);
+                cp_async<XB>(&xs_all[wid][st][u][0][lane * VEC], x0 + (int64_t)j[u] * a.ch[0].ldx + col);
+                if (NX == 2)
+                    cp_async<XB>(&xs_all[wid][st][u][NX - 1][lane * VEC], x1 + (int64_t)j[u] * a.ch[1].ldx + col);
                 if (q == 0) {
                     const int64_t e = p.base + (int64_t)(p.k0 + u) * RPS + r;
                     const int64_t e2 = sizeof(WT) == 4 ? e : (e & ~(int64_t)1);

@@ -24,15 +24,21 @@ namespace gift {
 
 constexpr int kSweepThreads = 256;
 
+// Signal rows of a chain: row i of x starts at x + i * ldx.  ldx is K for a
+// chain stored alone, 2K when two chains that share a sweep keep their rows
+// side by side ([N][2][K]: one gathered 2K-float row serves both chains), and
+// x then points at this chain's half.
 struct ChainIO {
-    const float *x;     // input rows, stride K (pre-scaled unless gpre)
+    const float *x;     // input rows, stride ldx (pre-scaled unless gpre)
     const float *gpre;  // non-null: input is unscaled; multiply row j by gpre[j]
     const float *post;  // post scale [N]
     float sigma;
     float alpha;        // weight of the term ending at this sweep
     int has_term;       // 1 if a term of this chain ends at this sweep
-    float *xnext;       // non-null: write pnext_i * y_i (next sweep's input)
+    float *xnext;       // non-null: write pnext_i * y_i (next sweep's input), stride ldn
     const float *pnext; // null: 1
+    int32_t ldx;        // row stride of x (floats)
+    int32_t ldn;        // row stride of xnext (floats)
 };
 
 // Implicit cliques in a sweep: row i adds, for each implicit net e it has k
@@ -51,7 +57,7 @@ struct SweepArgs {
     const int32_t *col;
     const void *val;
     int64_t n_rows;
-    int32_t K;   // row stride of every signal buffer (floats)
+    int32_t K;   // columns of a signal; row stride of g, the output and the accumulator (floats)
     int32_t c0;  // first column of the slab
     ChainIO ch[2];
     const float *acc_in;  // non-null: add to the contributions
@@ -62,6 +68,8 @@ struct SweepArgs {
     const float2 *gpre2;  // first sweep with two chains: (pre_0[j], pre_1[j]) packed, or null
     const int32_t *order; // direct row groups: row of each slot (-1: none), or null = identity
     int64_t n_slots;      // slots in order
+    int32_t slot_csr;     // 1: row_ptr / col / val hold the rows in slot order (row_ptr[slot]);
+                          // 0: they are indexed by row
     ImplicitArgs imp;
 };
 
@@ -244,11 +252,11 @@ __global__ void __launch_bounds__(kSweepThreads) k_sweep(const SweepArgs a) {
                 const int32_t j = __shfl_sync(gmask, jl, src, G);
                 const float w = __shfl_sync(gmask, wl, src, G);
                 wv[t] = src < cnt ? w : 0.f;
-                const int64_t off = (int64_t)(src < cnt ? j : 0) * a.K + colo;
+                const int64_t jr = src < cnt ? j : 0;
 #pragma unroll
                 for (int c = 0; c < NC; ++c) {
                     if (src < cnt) {
-                        ld_keep<VEC>(a.ch[c].x + off, xv[t][c], pol_keep);
+                        ld_keep<VEC>(a.ch[c].x + jr * a.ch[c].ldx + colo, xv[t][c], pol_keep);
                     } else {
 #pragma unroll
                         for (int v = 0; v < VEC; ++v) xv[t][c][v] = 0.f;
@@ -287,7 +295,7 @@ __global__ void __launch_bounds__(kSweepThreads) k_sweep(const SweepArgs a) {
         for (int c = 0; c < NC; ++c) {
             const ChainIO &ch = a.ch[c];
             float xi[VEC];
-            ldv<VEC>(ch.x + off, xi);
+            ldv<VEC>(ch.x + row * ch.ldx + colo, xi);
             if (ch.gpre) {
                 const float s = __ldg(ch.gpre + row);
 #pragma unroll
@@ -303,7 +311,7 @@ __global__ void __launch_bounds__(kSweepThreads) k_sweep(const SweepArgs a) {
                 float t[VEC];
 #pragma unroll
                 for (int v = 0; v < VEC; ++v) t[v] = q * y[v];
-                stv<VEC>(ch.xnext + off, t);
+                stv<VEC>(ch.xnext + row * ch.ldn + colo, t);
             }
             if (ch.has_term) {
 #pragma unroll

@@ -95,6 +95,7 @@ k_sweep_dr(const SweepArgs a) {
     const float *gp1 = FIRST ? a.ch[NC - 1].gpre : nullptr;
 
     const int64_t nslots = a.order ? a.n_slots : a.n_rows;
+    const int ldx0 = a.ch[0].ldx, ldx1 = a.ch[NX - 1].ldx;
     for (int64_t slot = warp * RPW + gi; slot - gi < nslots; slot += nwarps * RPW) {
         const int64_t row = slot < nslots ? (a.order ? (int64_t)__ldg(a.order + slot) : slot) : -1;
         float acc[NC][VEC], err[NC][VEC];
@@ -104,8 +105,10 @@ k_sweep_dr(const SweepArgs a) {
             for (int v = 0; v < VEC; ++v) acc[c][v] = err[c][v] = 0.f;
         int64_t kb = 0, ke = 0;
         if (row >= 0) {
-            kb = __ldg(a.row_ptr + row);
-            ke = __ldg(a.row_ptr + row + 1);
+            // the sorted copy of the CSR holds the rows in slot order
+            const int64_t ci = a.slot_csr ? slot : row;
+            kb = __ldg(a.row_ptr + ci);
+            ke = __ldg(a.row_ptr + ci + 1);
         }
         // Warp rows (rows of hundreds to thousands of nonzeros): the next
         // step's (col, val) are loaded while this step's rows are gathered,
@@ -121,9 +124,8 @@ k_sweep_dr(const SweepArgs a) {
 #pragma unroll
             for (int u = 0; u < U; ++u) {
                 if (k0 + (int64_t)u * NS < ke) {
-                    const int64_t off = (int64_t)j[u] * a.K;
-                    ldv<VEC>(x0 + off, xv[u][0]);
-                    if (NX == 2) ldv<VEC>(x1 + off, xv[u][NX - 1]);
+                    ldv<VEC>(x0 + (int64_t)j[u] * ldx0, xv[u][0]);
+                    if (NX == 2) ldv<VEC>(x1 + (int64_t)j[u] * ldx1, xv[u][NX - 1]);
                 }
             }
             float wc[U][NC];

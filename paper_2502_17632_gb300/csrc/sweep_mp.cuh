@@ -55,7 +55,7 @@ __device__ __forceinline__ void mp_finish(const SweepArgs &a, int64_t row, int c
         const float s = ch.gpre ? __ldg(ch.gpre + row) : 1.f;
         const float p = __ldg(ch.post + row);
         float xi[VEC], y[VEC], ac[VEC];
-        ldv<VEC>(ch.x + off, xi);
+        ldv<VEC>(ch.x + row * ch.ldx + col, xi);
 #pragma unroll
         for (int v = 0; v < VEC; ++v) {
             xi[v] *= s;  // the row's pre-scaled input
@@ -69,7 +69,7 @@ __device__ __forceinline__ void mp_finish(const SweepArgs &a, int64_t row, int c
             float t[VEC];
 #pragma unroll
             for (int v = 0; v < VEC; ++v) t[v] = qn * y[v];
-            stv<VEC>(ch.xnext + off, t);
+            stv<VEC>(ch.xnext + row * ch.ldn + col, t);
         }
         if (ch.has_term) {
 #pragma unroll
@@ -177,7 +177,7 @@ __global__ void __launch_bounds__(kMpThreads) k_sweep_mp(const SweepArgs a) {
 #pragma unroll
                     for (int c = 0; c < NC; ++c) {
                         if (valid) {
-                            ldv<VEC>(a.ch[c].x + (int64_t)j * a.K + col, xv[u][c]);
+                            ldv<VEC>(a.ch[c].x + (int64_t)j * a.ch[c].ldx + col, xv[u][c]);
                             if (a.ch[c].gpre) {
                                 const float sj = __ldg(a.ch[c].gpre + j);
 #pragma unroll
@@ -227,7 +227,7 @@ __global__ void __launch_bounds__(kMpThreads) k_sweep_mp(const SweepArgs a) {
 #pragma unroll
                     for (int c = 0; c < NC; ++c) {
                         if (valid) {
-                            ldv<VEC>(a.ch[c].x + (int64_t)j * a.K + col, xv[u][c]);
+                            ldv<VEC>(a.ch[c].x + (int64_t)j * a.ch[c].ldx + col, xv[u][c]);
                             if (a.ch[c].gpre) {
                                 const float sj = __ldg(a.ch[c].gpre + j);
 #pragma unroll

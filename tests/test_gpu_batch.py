@@ -201,7 +201,7 @@ def test_results_written_straight_to_pinned_host_memory(ctx, batch):
     np.testing.assert_array_equal(hp_p, hp)
     h = gift.gift_build_graph(ctx, nl.num_cells, nl.net_ptr, nl.pin_cell, nl.is_fixed)
     try:
-        for schedule in (0, 408, 1004, 3008, 4244, 4644):
+        for schedule in (0, 408, 1004, 3008, 4244, 4644, 4844, 6444):
             spec = gift.make_spec(schedule=schedule)
             ref = np.empty_like(g)
             gift.gift_filter(ctx, h, g, ref, spec)

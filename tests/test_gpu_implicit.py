@@ -89,7 +89,7 @@ def test_structure_and_degrees_bit_exact(ctx, name, cut, wd):
 @pytest.mark.parametrize("name", sorted(NETLISTS))
 @pytest.mark.parametrize("cut", [3, 8, 40])
 @pytest.mark.parametrize("S", [1, 4, 8])
-@pytest.mark.parametrize("schedule", [0, 408, 1016, 3008, 4244, 4644, 14244])
+@pytest.mark.parametrize("schedule", [0, 408, 1016, 3008, 4244, 4644, 14244, 4844, 6444, 16444])
 def test_filter_matches_full_expansion(ctx, name, cut, S, schedule):
     nl = NETLISTS[name]
     g = synth.make_signals(nl, S, 300 + S)

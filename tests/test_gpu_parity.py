@@ -173,7 +173,8 @@ def run_filter(ctx, nl, g, wd="f32", spec=None, device=True):
 
 @pytest.mark.parametrize("name", sorted(NETLISTS))
 @pytest.mark.parametrize("S", [1, 2, 3, 8])
-@pytest.mark.parametrize("schedule", [0, 416, 1016, 1004, 3002, 4042, 14044, 4148, 4244, 4644, 4724])
+@pytest.mark.parametrize("schedule", [0, 416, 1016, 1004, 3002, 4042, 14044, 4148, 4244, 4644, 4724,
+                                      4844, 5044, 5244, 5844, 6444, 14844, 16444])
 def test_filter_parity(ctx, name, S, schedule):
     nl = NETLISTS[name]
     g = synth.make_signals(nl, S, 1234 + S)
@@ -190,7 +191,9 @@ def test_filter_parity(ctx, name, S, schedule):
                                       1002, 1004, 1008, 1016, 2008, 2016, 3002, 3004, 3008, 3016,
                                       4012, 4014, 4022, 4024, 4042, 4044, 4082, 4084, 4112, 4118, 4142,
                                       4148, 4182, 4188, 4244, 4342, 4388, 4414, 4424, 4444, 4484, 4514, 4524,
-                                      4644, 4744, 4784, 10408, 13008, 14042, 14148, 14244, 14644])
+                                      4644, 4744, 4784, 10408, 13008, 14042, 14148, 14244, 14644,
+                                      4812, 4822, 4842, 4844, 4914, 4988, 5014, 5044, 5244, 5644, 5814, 5844,
+                                      6412, 6444, 6544, 6644, 14844, 15044, 16444])
 def test_filter_shapes_and_schedules(ctx, S, schedule):
     nl = NETLISTS["repeat-cells"]
     g = synth.make_signals(nl, S, 99 + S)
@@ -233,7 +236,7 @@ def test_filter_tma_and_sell(ctx, name, S, schedule):
     (((1.0, 1, 0.25), (2.0, 2, 0.25), (3.0, 3, 0.25), (4.0, 4, 0.25)), "sym", True),  # two chain pairs
     (((1.0, 1, 0.25), (2.0, 2, 0.25), (3.0, 3, 0.25), (4.0, 4, 0.25)), "rw", True),
 ])
-@pytest.mark.parametrize("schedule", [0, 3008, 4042, 14042, 408])
+@pytest.mark.parametrize("schedule", [0, 3008, 4042, 14042, 408, 4842, 5842, 6442, 16442])
 def test_filter_general_specs(ctx, terms, norm, reimpose, schedule):
     """Chains grouped in pairs, one chain left over, both normalisations; the
     first sweep of every pair gathers g once with that pair's two scales."""
@@ -244,6 +247,28 @@ def test_filter_general_specs(ctx, terms, norm, reimpose, schedule):
     got = run_filter(ctx, nl, g, spec=spec)
     _, _, ref = oracle.run(nl, g.reshape(nl.num_cells, -1), terms=terms, norm=norm, reimpose=reimpose)
     assert rel_err(got, ref.reshape(g.shape), g).max() <= RTOL
+
+
+@pytest.mark.parametrize("name", sorted(NETLISTS))
+@pytest.mark.parametrize("S", [1, 8])
+def test_row_order_does_not_change_sums(ctx, name, S):
+    """Direct row groups sum every row alone in CSR order, so walking the rows
+    in natural order, in the window order, in length order over the CSR or
+    from the sorted copy of the CSR gives the same bits.  (Running a chain
+    pair as two launches combines the terms in another order, and the
+    pre-scaled first sweep rounds s_j g_j once more: each is compared with its
+    own kind, and all meet the FP32 bar.)"""
+    nl = NETLISTS[name]
+    g = synth.make_signals(nl, S, 77)
+    for base_sched, same in ((4244, (4044, 4844, 5044)), (14244, (14044, 14844, 15044))):
+        base = run_filter(ctx, nl, g, spec=gift.make_spec(schedule=base_sched))
+        for sched in same:
+            np.testing.assert_array_equal(run_filter(ctx, nl, g, spec=gift.make_spec(schedule=sched)), base,
+                                          err_msg=f"schedule {sched} vs {base_sched}")
+    pre = run_filter(ctx, nl, g, spec=gift.make_spec(schedule=6444))
+    np.testing.assert_array_equal(run_filter(ctx, nl, g, spec=gift.make_spec(schedule=5844)), pre)
+    _, _, ref = oracle.run(nl, g.reshape(nl.num_cells, -1))
+    assert rel_err(pre, ref.reshape(g.shape), g).max() <= RTOL
 
 
 @pytest.mark.parametrize("name", sorted(NETLISTS))
@@ -351,7 +376,7 @@ def test_invalid_filter_args(ctx):
         with pytest.raises(gift.GiftError):
             gift.gift_filter(ctx, h, g, out, None, num_signals=0)
         for bad in (1, 2, 3, 404 + 1, 800 + 16, 216 + 100, 1161, 1003, 1032, 4043, 4062, 4442, 4041,
-                    4842, 4642, 10000, 10003, 19999, 20000):
+                    4642, 5046, 5644 + 2, 7244, 9999, 10000, 10003, 19999, 20000):
             with pytest.raises(gift.GiftError) as e:
                 gift.gift_filter(ctx, h, g, out, gift.make_spec(schedule=bad))
             assert e.value.status == gift.GIFT_ERR_INVALID
