@@ -55,8 +55,11 @@ def parse():
     p.add_argument("--no-small", action="store_true", help="skip the small-netlist latency measurement")
     p.add_argument("--no-eigen", action="store_true", help="skip the eigenvector-placement measurement")
     p.add_argument("--no-paper-sizes", action="store_true", help="skip the paper-design-size measurement")
-    p.add_argument("--serve-requests", type=int, default=240)
+    p.add_argument("--serve-requests", type=int, default=2000)
     p.add_argument("--serve-rate", type=float, default=40.0, help="Poisson arrival rate, requests/s")
+    p.add_argument("--serve-rate-high", type=float, default=1000.0,
+                   help="a second arrival rate that keeps several requests in flight (0: skip)")
+    p.add_argument("--serve-requests-high", type=int, default=2000)
     p.add_argument("--record-traffic", metavar="CSV",
                    help="write profiles/traffic.json from the CSV of an ncu capture of 'bench.py --capture' "
                         "(dram__bytes_read.sum, dram__bytes_write.sum, gpu__time_duration.sum of the k_sweep "
@@ -305,15 +308,18 @@ def serve_pool(num: int = 12, seed: int = synth.SEED0 + 4):
 
 def run_serving(args, gift):
     """Poisson arrivals through the request loop (FP32 and BF16 requests
-    alternating) against the serial plain FP32 path (one request at a time
-    through gift_build_graph + gift_filter + gift_hpwl, host buffers) on the
-    same arrival sequence.  Latency = result ready - arrival."""
+    alternating; the requests' filters share sweep launches) against the
+    serial plain FP32 path (one request at a time through gift_build_graph +
+    gift_filter + gift_hpwl) on the same arrival sequence, at the workload's
+    rate and at a rate that keeps several requests in flight.  Signals in
+    page-locked host memory on both arms (the server's own pool; pinned
+    buffers for the serial path).  Latency = result ready on the host -
+    arrival."""
     import threading as th
+    import torch
     pool = serve_pool()
-    warm = max(1, args.serve_requests // 10)
-    total = args.serve_requests + warm
-    arrivals = synth.arrival_times(total, args.serve_rate, synth.SEED0 + 4)
-    reqs = [(pool[k % len(pool)], "bf16" if k % 2 else "f32") for k in range(total)]
+    pinned = [(torch.from_numpy(g).pin_memory().numpy(), torch.empty(g.shape, dtype=torch.float32).pin_memory().numpy())
+              for _, g in pool]
 
     def summary(lat, t_first, t_last, eu):
         lat = np.sort(np.asarray(lat))
@@ -322,64 +328,86 @@ def run_serving(args, gift):
         return {"p50_ms": pick(0.5), "p99_ms": pick(0.99), "mean_ms": float(lat.mean()), "max_ms": float(lat[-1]),
                 "requests_per_s": len(lat) / span, "edge_updates_per_s": eu / span}
 
-    # served
-    srv = gift.gift_serve_create(max_slots=8)
-    tickets = [None] * total
-    t0 = time.perf_counter() + 0.2
+    def one_rate(rate, count):
+        warm = max(1, count // 10)
+        total = count + warm
+        arrivals = synth.arrival_times(total, rate, synth.SEED0 + 4)
+        reqs = [(k % len(pool), "bf16" if k % 2 else "f32") for k in range(total)]
+        # served: several submitting threads (a submit copies and checks the netlist on the host), each
+        # request submitted at its arrival time; latency = (submit returned - arrival) + the server's
+        # submit-to-result-ready time
+        srv = gift.gift_serve_create(max_slots=8)
+        tickets = [None] * total
+        lag = [0.0] * total
+        t0 = time.perf_counter() + 0.2
+        nsub = 4
 
-    def submitter():
-        for k, ((nl, g), wd) in enumerate(reqs):
+        def submitter(part):
+            for k in range(part, total, nsub):
+                i, wd = reqs[k]
+                nl = pool[i][0]
+                dt = t0 + arrivals[k] - time.perf_counter()
+                if dt > 0:
+                    time.sleep(dt)
+                tickets[k] = gift.gift_serve_submit(srv, nl.num_cells, nl.net_ptr, nl.pin_cell, nl.is_fixed,
+                                                    pinned[i][0], gift.WEIGHT[wd])
+                lag[k] = time.perf_counter() - (t0 + arrivals[k])
+
+        subs = [th.Thread(target=submitter, args=(q,)) for q in range(nsub)]
+        for t in subs:
+            t.start()
+        lat, eu, done_t = [], 0.0, []
+        for k, (i, wd) in enumerate(reqs):
+            nl, g = pool[i]
+            while tickets[k] is None:
+                time.sleep(0.0002)
+            _, _, st = gift.gift_serve_wait(srv, tickets[k], nl.num_cells, g.shape[1])
+            if k >= warm:
+                lat.append(1e3 * lag[k] + st.latency_ms)
+                eu += 6.0 * st.nnz * g.shape[1]
+                done_t.append(t0 + arrivals[k] + lat[-1] * 1e-3)
+        for t in subs:
+            t.join()
+        sst = gift.gift_serve_stats_get(srv)
+        gift.gift_serve_destroy(srv)
+        served = summary(lat, t0 + arrivals[warm], max(done_t), eu)
+        served.update({"submit_ms_mean": 1e3 * float(np.mean(lag[warm:])),
+                       "peak_running": sst.peak_running, "max_slots": sst.max_slots,
+                       "peak_footprint_gb": sst.peak_footprint_bytes / 1e9, "filter_batches": sst.batches,
+                       "requests_per_batch": sst.batched_requests / max(sst.batches, 1),
+                       "peak_batch": sst.peak_batch})
+        # serial plain FP32 path on the same arrivals, same page-locked signal buffers
+        ctx = gift.gift_ctx_create(0)
+        spec = gift.make_spec(schedule=4244)
+        lat_s, eu_s, done_s = [], 0.0, []
+        t0 = time.perf_counter() + 0.2
+        for k, (i, _) in enumerate(reqs):
+            nl, g = pool[i]
             dt = t0 + arrivals[k] - time.perf_counter()
             if dt > 0:
                 time.sleep(dt)
-            tickets[k] = gift.gift_serve_submit(srv, nl.num_cells, nl.net_ptr, nl.pin_cell, nl.is_fixed, g,
-                                                gift.WEIGHT[wd])
+            h = gift.gift_build_graph(ctx, nl.num_cells, nl.net_ptr, nl.pin_cell, nl.is_fixed, gift.WEIGHT["f32"])
+            gift.gift_filter(ctx, h, pinned[i][0], pinned[i][1], spec)
+            gift.gift_hpwl(ctx, h, pinned[i][1])
+            nnz = int(gift.gift_graph_info(h).nnz)
+            gift.gift_graph_free(h)
+            t_done = time.perf_counter()
+            if k >= warm:
+                lat_s.append(1e3 * (t_done - (t0 + arrivals[k])))
+                eu_s += 6.0 * nnz * g.shape[1]
+                done_s.append(t_done)
+        gift.gift_ctx_destroy(ctx)
+        serial = summary(lat_s, t0 + arrivals[warm], max(done_s), eu_s)
+        cells = [pool[i][0].num_cells for i, _ in reqs[warm:]]
+        return {"workload": f"Poisson {rate:g} req/s, {count} requests after {warm} warm-up, {len(pool)} distinct "
+                            f"netlists of 10k-1.3M cells (mean {np.mean(cells):.0f}), 1 % fixed, S=4, FP32 and BF16 "
+                            "weights alternating; latency = result on the host - arrival",
+                "served": served, "serial_fp32": serial}
 
-    th_sub = th.Thread(target=submitter)
-    th_sub.start()
-    lat, eu, done_t = [], 0.0, []
-    for k, ((nl, g), wd) in enumerate(reqs):
-        while tickets[k] is None:
-            time.sleep(0.0002)
-        out, hp, st = gift.gift_serve_wait(srv, tickets[k], nl.num_cells, g.shape[1])
-        if k >= warm:
-            lat.append(st.latency_ms)
-            eu += 6.0 * st.nnz * g.shape[1]
-            done_t.append(time.perf_counter())
-    th_sub.join()
-    sst = gift.gift_serve_stats_get(srv)
-    gift.gift_serve_destroy(srv)
-    served = summary(lat, t0 + arrivals[warm], max(done_t), eu)
-    served.update({"peak_running": sst.peak_running, "max_slots": sst.max_slots,
-                   "peak_footprint_gb": sst.peak_footprint_bytes / 1e9})
-
-    # serial plain FP32 path on the same arrivals
-    ctx = gift.gift_ctx_create(0)
-    spec = gift.make_spec(schedule=4244)
-    lat_s, eu_s, done_s = [], 0.0, []
-    t0 = time.perf_counter() + 0.2
-    for k, ((nl, g), _) in enumerate(reqs):
-        dt = t0 + arrivals[k] - time.perf_counter()
-        if dt > 0:
-            time.sleep(dt)
-        h = gift.gift_build_graph(ctx, nl.num_cells, nl.net_ptr, nl.pin_cell, nl.is_fixed, gift.WEIGHT["f32"])
-        out = np.empty_like(g)
-        gift.gift_filter(ctx, h, g, out, spec)
-        gift.gift_hpwl(ctx, h, out)
-        nnz = int(gift.gift_graph_info(h).nnz)
-        gift.gift_graph_free(h)
-        t_done = time.perf_counter()
-        if k >= warm:
-            lat_s.append(1e3 * (t_done - (t0 + arrivals[k])))
-            eu_s += 6.0 * nnz * g.shape[1]
-            done_s.append(t_done)
-    gift.gift_ctx_destroy(ctx)
-    serial = summary(lat_s, t0 + arrivals[warm], max(done_s), eu_s)
-    cells = [nl.num_cells for (nl, _), _ in reqs[warm:]]
-    return {"workload": f"Poisson {args.serve_rate:g} req/s, {args.serve_requests} requests after {warm} warm-up, "
-                        f"{len(pool)} distinct netlists of 10k-1.3M cells (mean {np.mean(cells):.0f}), 1 % fixed, "
-                        "S=4, FP32 and BF16 weights alternating; latency = result on the host - arrival",
-            "served": served, "serial_fp32": serial}
+    out = one_rate(args.serve_rate, args.serve_requests)
+    if args.serve_rate_high > 0:
+        out["high_load"] = one_rate(args.serve_rate_high, args.serve_requests_high)
+    return out
 
 
 # ----------------------------------------------------------------- batched

@@ -445,7 +445,17 @@ typedef struct gift_serve_opts {
     gift_filter_spec spec;      /* filter of every request; spec.schedule 0 = a fixed
                                    direct row-group shape (4244), not the autotuner  */
     int32_t implicit_min_pins;  /* build option of every request (0: expand all)    */
-    int32_t reserved[7];        /* zero                                              */
+    int32_t separate_filters;   /* 0 (default): requests in their filter stage share
+                                   sweep launches (up to 16 requests with the same
+                                   number of signals per launch; needs a direct
+                                   row-group shape in natural order, no compensated
+                                   sums, no implicit cliques -- other requests run
+                                   their own launches); 1: every request its own   */
+    int32_t batch_window_us;    /* shared filters: how long a batch stays open for
+                                   more requests once the previous batch has left
+                                   the device (0, default: it closes at once; it
+                                   also closes when 16 requests wait)              */
+    int32_t reserved[5];        /* zero                                              */
 } gift_serve_opts;
 
 typedef struct gift_req_stats {
@@ -466,6 +476,10 @@ typedef struct gift_serve_stats {
     double edge_updates_per_s;                /* 6 * nnz * S summed over completed, same span */
     int64_t budget_bytes, peak_footprint_bytes;
     int32_t max_slots, peak_running;
+    int64_t batches;                          /* shared filter batches run          */
+    int64_t batched_requests;                 /* requests filtered in them          */
+    int32_t peak_batch;                       /* largest batch                      */
+    int32_t reserved0;
 } gift_serve_stats;
 
 GIFT_API void gift_serve_opts_default(gift_serve_opts *opts);

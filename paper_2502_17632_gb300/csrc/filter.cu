@@ -479,6 +479,84 @@ struct Group {
     bool prescaled;       // first sweep from the pre-scaled pair copy of g
 };
 
+// Input rows of the chains of launch group gr in sweep k: chain gr.c[q] reads
+// x_in[q] (row stride ld_in[q]), scaled on the fly by gp_in[q] when it is g.
+void group_inputs(const Plan &p, const std::vector<std::vector<Place>> &pl, int k, const Group &gr,
+                  const float *(&x_in)[2], int (&ld_in)[2], const float *(&gp_in)[2]) {
+    for (int q = 0; q < 2; ++q) {
+        const int c = gr.c[q];
+        const Place &at = pl[k][c];
+        if (k == 1 && gr.prescaled) {
+            x_in[q] = p.Y[gr.gi][1] + at.q * p.K;
+            ld_in[q] = 2 * p.K;
+            gp_in[q] = nullptr;
+        } else if (k == 1) {
+            x_in[q] = p.din;
+            ld_in[q] = p.K;
+            gp_in[q] = p.sc[c].pre;
+        } else {
+            x_in[q] = p.Y[at.gi][k % 2] + at.q * p.K;
+            ld_in[q] = at.nc * p.K;
+            gp_in[q] = nullptr;
+        }
+    }
+}
+
+// Arguments of a launch of group gr in sweep k over the slab from column c0:
+// the chains' inputs, scales and outputs (the next sweep's input rows where
+// the chain goes on), the accumulator and, in the last launch, the result
+// with the fixed rows.  The CSR is the graph's; the caller may swap in an
+// execution format (row order, sorted copy) and the implicit-clique sums.
+SweepArgs make_sweep_args(const Plan &p, const std::vector<std::vector<Place>> &pl, int k, const Group &gr,
+                          const float *const (&x_in)[2], const int (&ld_in)[2], const float *const (&gp_in)[2],
+                          bool first, int c0, bool last, bool group_terms, bool contributed) {
+    const gift_graph *g = p.g;
+    SweepArgs a;
+    std::memset(&a, 0, sizeof(a));
+    a.row_ptr = g->row_ptr;
+    a.col = g->col;
+    a.val = g->val;
+    a.weight_dtype = g->weight_dtype;
+    a.n_rows = g->n;
+    a.K = p.K;
+    a.c0 = c0;
+    a.gpre2 = first ? gr.gpre2 : nullptr;
+    for (int q = 0; q < gr.nc; ++q) {
+        const int c = gr.c[q];
+        const Chain &ch = p.chains[c];
+        ChainIO &io = a.ch[q];
+        io.x = x_in[q];
+        io.ldx = ld_in[q];
+        io.gpre = first ? gp_in[q] : nullptr;
+        io.post = p.sc[c].post;
+        io.sigma = ch.sigma;
+        io.alpha = (float)ch.alpha_at[k];
+        io.has_term = ch.has_at[k] ? 1 : 0;
+        if (ch.L > k) {
+            const Place &nx = pl[k + 1][c];
+            io.xnext = p.Y[nx.gi][(k + 1) % 2] + nx.q * p.K;
+            io.ldn = nx.nc * p.K;
+        } else {
+            io.xnext = nullptr;
+            io.ldn = p.K;
+        }
+        io.pnext = p.sc[c].pre;
+    }
+    if (last) {
+        a.acc_in = contributed ? p.acc : nullptr;
+        a.acc_out = p.dout;
+        a.acc_mirror = p.mirror;
+        if (p.reimpose) {
+            a.fixed = g->is_fixed;
+            a.g_fixed = p.din;
+        }
+    } else if (group_terms) {
+        a.acc_in = contributed ? p.acc : nullptr;
+        a.acc_out = p.acc;
+    }
+    return a;
+}
+
 // Launches every sweep of the filter; each launch uses the shape of its kind.
 // With `timed`, every launch is bracketed by events from `pool` (tuning).
 // Returns the mask of launch kinds used (bit kd, planned kinds).
@@ -580,23 +658,7 @@ int run_sweeps(gift_ctx *ctx, const Plan &p, ShapeSet ss, cudaStream_t st, std::
             const float *x_in[2];
             int ld_in[2];
             const float *gp_in[2];
-            for (int q = 0; q < 2; ++q) {
-                const int c = gr.c[q];
-                const Place &at = pl[k][c];
-                if (k == 1 && gr.prescaled) {
-                    x_in[q] = p.Y[gr.gi][1] + at.q * K;
-                    ld_in[q] = 2 * K;
-                    gp_in[q] = nullptr;
-                } else if (k == 1) {
-                    x_in[q] = p.din;
-                    ld_in[q] = K;
-                    gp_in[q] = p.sc[c].pre;
-                } else {
-                    x_in[q] = p.Y[at.gi][k % 2] + at.q * K;
-                    ld_in[q] = at.nc * K;
-                    gp_in[q] = nullptr;
-                }
-            }
+            group_inputs(p, pl, k, gr, x_in, ld_in, gp_in);
             const bool first = k == 1 && !gr.prescaled;  // gathers the unscaled g
             if (k == 1 && gr.prescaled && prescaled_done != gr.gi) {
                 // [pre_a g | pre_b g], timed with the sweeps (it replaces the first sweep's scale gathers)
@@ -649,51 +711,11 @@ int run_sweeps(gift_ctx *ctx, const Plan &p, ShapeSet ss, cudaStream_t st, std::
             }
             for (size_t si = 0; si < slabs.size(); ++si) {
                 const int c0 = slabs[si].first, cw = slabs[si].second, W = cw * sv;
-                SweepArgs a;
-                std::memset(&a, 0, sizeof(a));
-                a.row_ptr = g->row_ptr;
-                a.col = g->col;
-                a.val = g->val;
-                a.n_rows = N;
-                a.K = p.K;
-                a.c0 = c0;
-                a.gpre2 = first ? gr.gpre2 : nullptr;
+                SweepArgs a = make_sweep_args(p, pl, k, gr, x_in, ld_in, gp_in, first, c0, last, group_terms,
+                                              contributed);
                 a.imp = imp;
                 const double bytes = first_launch ? sweep_bytes : 0.0;
                 first_launch = false;
-                for (int q = 0; q < nc; ++q) {
-                    const int c = gr.c[q];
-                    const Chain &ch = p.chains[c];
-                    ChainIO &io = a.ch[q];
-                    io.x = x_in[q];
-                    io.ldx = ld_in[q];
-                    io.gpre = first ? gp_in[q] : nullptr;
-                    io.post = p.sc[c].post;
-                    io.sigma = ch.sigma;
-                    io.alpha = (float)ch.alpha_at[k];
-                    io.has_term = ch.has_at[k] ? 1 : 0;
-                    if (ch.L > k) {
-                        const Place &nx = pl[k + 1][c];
-                        io.xnext = p.Y[nx.gi][(k + 1) % 2] + nx.q * K;
-                        io.ldn = nx.nc * K;
-                    } else {
-                        io.xnext = nullptr;
-                        io.ldn = K;
-                    }
-                    io.pnext = p.sc[c].pre;
-                }
-                if (last) {
-                    a.acc_in = contributed ? p.acc : nullptr;
-                    a.acc_out = p.dout;
-                    a.acc_mirror = p.mirror;
-                    if (p.reimpose) {
-                        a.fixed = g->is_fixed;
-                        a.g_fixed = p.din;
-                    }
-                } else if (group_terms) {
-                    a.acc_in = contributed ? p.acc : nullptr;
-                    a.acc_out = p.acc;
-                }
                 const int nx = first ? 1 : nc;
                 const void *fn = nullptr;
                 int threads = kSweepThreads;
@@ -1029,6 +1051,31 @@ float *host_mirror(void *p, size_t bytes) {
     return static_cast<float *>(at.devicePointer);
 }
 
+// The spec's terms grouped by sigma into chains (term (sigma, k, alpha) ends
+// chain sigma's k-th product), and the longest chain.
+void plan_chains(const gift_filter_spec *spec, Plan &p, const char *who) {
+    const std::string w(who);
+    for (int t = 0; t < spec->num_terms; ++t) {
+        const gift_term &tm = spec->term[t];
+        GIFT_REQUIRE(std::isfinite(tm.sigma) && tm.sigma > 0.f, w + ": sigma must be finite and > 0");
+        GIFT_REQUIRE(tm.power >= 1 && tm.power <= 64, w + ": power must be in [1, 64]");
+        GIFT_REQUIRE(std::isfinite(tm.alpha), w + ": alpha must be finite");
+        Chain *c = nullptr;
+        for (auto &x : p.chains)
+            if (x.sigma == tm.sigma) c = &x;
+        if (!c) {
+            p.chains.push_back(Chain{});
+            c = &p.chains.back();
+            c->sigma = tm.sigma;
+        }
+        c->L = std::max(c->L, tm.power);
+        c->alpha_at[tm.power] += tm.alpha;
+        c->has_at[tm.power] = true;
+    }
+    p.Lmax = 0;
+    for (auto &c : p.chains) p.Lmax = std::max(p.Lmax, c.L);
+}
+
 void filter_impl(gift_ctx *ctx, const gift_graph *cg, const gift_filter_spec *spec, const float *g_in, int S,
                  float *g_out, int mem, cudaStream_t st, float *mirror) {
     gift_graph *g = const_cast<gift_graph *>(cg);
@@ -1054,26 +1101,7 @@ void filter_impl(gift_ctx *ctx, const gift_graph *cg, const gift_filter_spec *sp
     p.K = K;
     p.reimpose = spec->reimpose_fixed;
     p.comp = spec->compensated == 1;
-    // ---- chains by sigma
-    for (int t = 0; t < spec->num_terms; ++t) {
-        const gift_term &tm = spec->term[t];
-        GIFT_REQUIRE(std::isfinite(tm.sigma) && tm.sigma > 0.f, "gift_filter: sigma must be finite and > 0");
-        GIFT_REQUIRE(tm.power >= 1 && tm.power <= 64, "gift_filter: power must be in [1, 64]");
-        GIFT_REQUIRE(std::isfinite(tm.alpha), "gift_filter: alpha must be finite");
-        Chain *c = nullptr;
-        for (auto &x : p.chains)
-            if (x.sigma == tm.sigma) c = &x;
-        if (!c) {
-            p.chains.push_back(Chain{});
-            c = &p.chains.back();
-            c->sigma = tm.sigma;
-        }
-        c->L = std::max(c->L, tm.power);
-        c->alpha_at[tm.power] += tm.alpha;
-        c->has_at[tm.power] = true;
-    }
-    p.Lmax = 0;
-    for (auto &c : p.chains) p.Lmax = std::max(p.Lmax, c.L);
+    plan_chains(spec, p, "gift_filter");
 
     // ---- signal buffers
     DevBuf din_buf, dout_buf;
@@ -1223,25 +1251,7 @@ void filter_on_scratch(gift_ctx *ctx, const gift_graph *g, const gift_filter_spe
     p.K = K;
     p.reimpose = spec->reimpose_fixed;
     p.comp = spec->compensated == 1;
-    for (int t = 0; t < spec->num_terms; ++t) {
-        const gift_term &tm = spec->term[t];
-        GIFT_REQUIRE(std::isfinite(tm.sigma) && tm.sigma > 0.f, "gift_filter_noalloc: sigma must be finite and > 0");
-        GIFT_REQUIRE(tm.power >= 1 && tm.power <= 64, "gift_filter_noalloc: power must be in [1, 64]");
-        GIFT_REQUIRE(std::isfinite(tm.alpha), "gift_filter_noalloc: alpha must be finite");
-        Chain *c = nullptr;
-        for (auto &x : p.chains)
-            if (x.sigma == tm.sigma) c = &x;
-        if (!c) {
-            p.chains.push_back(Chain{});
-            c = &p.chains.back();
-            c->sigma = tm.sigma;
-        }
-        c->L = std::max(c->L, tm.power);
-        c->alpha_at[tm.power] += tm.alpha;
-        c->has_at[tm.power] = true;
-    }
-    p.Lmax = 0;
-    for (auto &c : p.chains) p.Lmax = std::max(p.Lmax, c.L);
+    plan_chains(spec, p, "gift_filter_noalloc");
     GIFT_REQUIRE(filter_scratch_bytes(g, spec, S) <= scratch_bytes,
                  "gift_filter_noalloc: graph and signal need more scratch than the fixed no-alloc area");
     const bool al16 = (reinterpret_cast<uintptr_t>(g_in) % 16 == 0) && (reinterpret_cast<uintptr_t>(g_out) % 16 == 0);
@@ -1330,6 +1340,154 @@ void filter_on_scratch(gift_ctx *ctx, const gift_graph *g, const gift_filter_spe
         for (auto &k : ss.kind)
             if (k.family != 4) k = comp_shape();
     run_sweeps(ctx, p, ss, st);
+}
+
+// ---------------------------------------------------------------------------
+// Several graphs filtered in the same launches (see filter_batch in
+// internal.cuh): one multi-graph direct sweep launch per launch of the
+// single-graph schedule, each graph with its own arguments.
+bool batchable_shape(int schedule) {
+    if (schedule < 4000 || schedule >= 10000) return false;
+    const Shape s = shape_from_schedule(schedule);
+    return valid_shape(s) && s.natural && !s.sorted && !s.warp_rows && !s.prescale && (s.b == 2 || s.b == 4);
+}
+
+void filter_batch(gift_ctx *ctx, const std::vector<BatchItem> &items, const gift_filter_spec *spec, int S,
+                  int schedule, cudaStream_t st, void *staging, size_t staging_bytes) {
+    GIFT_REQUIRE(!items.empty() && items.size() <= (size_t)kMaxMulti, "filter_batch: 1 to 16 graphs");
+    GIFT_REQUIRE(S >= 1, "filter_batch: num_signals must be >= 1");
+    GIFT_REQUIRE(spec->num_terms >= 1 && spec->num_terms <= GIFT_MAX_TERMS, "filter_batch: num_terms out of range");
+    GIFT_REQUIRE(spec->norm == GIFT_NORM_SYM || spec->norm == GIFT_NORM_RW, "filter_batch: unknown norm");
+    GIFT_REQUIRE(spec->compensated == 0, "filter_batch: compensated sums are not batched");
+    GIFT_REQUIRE(batchable_shape(schedule), "filter_batch: the shape must be direct row groups in natural order");
+    const Shape shape = shape_from_schedule(schedule);
+    const int K = 2 * S;
+    std::vector<Plan> ps(items.size());
+    std::vector<DevBuf> bufs;
+    bool al16 = K % 4 == 0;
+    for (const BatchItem &it : items) {
+        GIFT_REQUIRE(it.g && it.din && it.dout, "filter_batch: NULL graph or signal");
+        GIFT_REQUIRE(it.g->imp_nets == 0, "filter_batch: graphs with implicit cliques are not batched");
+        al16 = al16 && reinterpret_cast<uintptr_t>(it.din) % 16 == 0 && reinterpret_cast<uintptr_t>(it.dout) % 16 == 0;
+    }
+    for (size_t i = 0; i < items.size(); ++i) {
+        Plan &p = ps[i];
+        gift_graph *g = const_cast<gift_graph *>(items[i].g);
+        const size_t sig_bytes = sizeof(float) * (size_t)g->n * K;
+        p.g = g;
+        p.K = K;
+        p.reimpose = spec->reimpose_fixed;
+        plan_chains(spec, p, "filter_batch");
+        p.din = items[i].din;
+        p.dout = items[i].dout;
+        p.mirror = items[i].mirror;
+        p.vec = al16 ? 4 : 2;
+        const auto widths = buffer_widths(p.chains, p.Lmax, false);
+        p.Y.assign(widths.size(), {nullptr, nullptr});
+        for (size_t gi = 0; gi < widths.size(); ++gi)
+            for (int par = 0; par < 2; ++par)
+                if (widths[gi][par] > 0) {
+                    bufs.emplace_back(ctx, sig_bytes * widths[gi][par], st);
+                    p.Y[gi][par] = bufs.back().as<float>();
+                }
+        bufs.emplace_back(ctx, sig_bytes, st);
+        p.acc = bufs.back().as<float>();
+        p.sc.resize(p.chains.size());
+        for (size_t c = 0; c < p.chains.size(); ++c) p.sc[c] = graph_scale(ctx, g, p.chains[c].sigma, spec->norm, st);
+        for (size_t c = 0; c + 1 < p.chains.size(); c += 2) {
+            if (!p.sc[c].pre || !p.sc[c + 1].pre) {
+                p.gpre2.push_back(nullptr);
+                continue;
+            }
+            bufs.emplace_back(ctx, sizeof(float2) * (size_t)std::max<int64_t>(g->n, 1), st);
+            k_pack2<<<(int)std::max<int64_t>(1, std::min<int64_t>(ceil_div(g->n, 256), (int64_t)ctx->num_sms * 8)),
+                      256, 0, st>>>(g->n, p.sc[c].pre, p.sc[c + 1].pre, bufs.back().as<float2>());
+            check_launch("k_pack2");
+            p.gpre2.push_back(bufs.back().as<float2>());
+        }
+    }
+    const Plan &p0 = ps[0];
+    const auto pl = placements(p0.chains, p0.Lmax);
+    const int sv = shape.narrow ? 2 : p0.vec;
+    const std::vector<std::pair<int, int>> slabs = slab_plan(p0, shape);
+    // every launch of the single-graph schedule, with each graph's arguments
+    struct Launch {
+        const void *fn;
+        int cw;  // lanes per row
+        double bytes;
+    };
+    std::vector<Launch> launches;
+    std::vector<SweepArgs> table;
+    bool contributed = false;
+    for (int k = 1; k <= p0.Lmax; ++k) {
+        std::vector<int> active;
+        for (size_t c = 0; c < p0.chains.size(); ++c)
+            if (p0.chains[c].L >= k) active.push_back((int)c);
+        bool sweep_terms = false;
+        for (int c : active) sweep_terms |= p0.chains[c].has_at[k];
+        for (size_t gx = 0; gx < active.size(); gx += 2) {
+            const int nc = (int)std::min<size_t>(2, active.size() - gx);
+            const bool last = k == p0.Lmax && gx + 2 >= active.size();
+            bool group_terms = false;
+            for (int q = 0; q < nc; ++q) group_terms |= p0.chains[active[gx + q]].has_at[k];
+            const bool first = k == 1;
+            for (const auto &slab : slabs) {
+                const int c0 = slab.first, cw = slab.second;
+                const int u = std::min(shape.b, 4);
+                const void *kf = sweep_multi_kernel(sv, cw, u, nc, first);
+                GIFT_REQUIRE(kf != nullptr, "filter_batch: no multi-graph kernel for this shape");
+                double bytes = 0.0;
+                for (const Plan &p : ps) {
+                    Group gr{{active[gx], active[gx + nc - 1]}, nc, launch_kind(nc, k), launch_kind(nc, k),
+                             first && nc == 2 && gx / 2 < p.gpre2.size() ? p.gpre2[gx / 2] : nullptr, (int)gx / 2,
+                             false};
+                    const float *x_in[2];
+                    int ld_in[2];
+                    const float *gp_in[2];
+                    group_inputs(p, pl, k, gr, x_in, ld_in, gp_in);
+                    table.push_back(make_sweep_args(p, pl, k, gr, x_in, ld_in, gp_in, first, c0, last, group_terms,
+                                                    contributed));
+                    if (c0 == 0 && gx == 0) {  // the sweep's algorithmic bytes, counted once per graph
+                        const size_t wsz = p.g->weight_dtype == GIFT_WEIGHT_F32 ? 4 : 2;
+                        const double sig = 4.0 * (double)p.g->n * K;
+                        bytes += (double)p.g->stored * (4.0 + wsz) + 8.0 * (p.g->n + 1) +
+                                 (k == 1 ? sig : sig * active.size());
+                        for (int c : active) bytes += 4.0 * p.g->n + (p0.chains[c].L > k ? sig : 0.0);
+                        if (sweep_terms || k == p0.Lmax) bytes += (contributed ? sig : 0.0) + sig;
+                        if (k == p0.Lmax && p0.reimpose) bytes += (double)p.g->n;
+                    }
+                }
+                launches.push_back(Launch{kf, cw, bytes});
+            }
+            if (group_terms && !last) contributed = true;
+        }
+    }
+    // upload the arguments and the graphs' row ranges
+    const int ng = (int)items.size();
+    std::vector<int64_t> begin(ng + 1, 0);
+    for (int i = 0; i < ng; ++i) begin[i + 1] = begin[i] + ps[i].g->n;
+    const size_t tab_bytes = sizeof(SweepArgs) * table.size(), beg_bytes = sizeof(int64_t) * (ng + 1);
+    DevBuf dtab(ctx, tab_bytes + beg_bytes, st);
+    const int64_t *dbeg = reinterpret_cast<const int64_t *>(static_cast<unsigned char *>(dtab.p) + tab_bytes);
+    if (staging && tab_bytes + beg_bytes <= staging_bytes) {  // one asynchronous copy from page-locked memory
+        std::memcpy(staging, table.data(), tab_bytes);
+        std::memcpy(static_cast<unsigned char *>(staging) + tab_bytes, begin.data(), beg_bytes);
+        GIFT_CUDA(cudaMemcpyAsync(dtab.p, staging, tab_bytes + beg_bytes, cudaMemcpyHostToDevice, st));
+    } else {
+        GIFT_CUDA(cudaMemcpyAsync(dtab.p, table.data(), tab_bytes, cudaMemcpyHostToDevice, st));
+        GIFT_CUDA(cudaMemcpyAsync(const_cast<int64_t *>(dbeg), begin.data(), beg_bytes, cudaMemcpyHostToDevice, st));
+    }
+    const int64_t total = begin[ng];
+    for (size_t li = 0; li < launches.size(); ++li) {
+        MultiArgs m{dtab.as<SweepArgs>() + li * ng, dbeg, ng};
+        const int64_t rows_per_block = (kSweepThreads / 32) * (32 / launches[li].cw);
+        const int grid = (int)std::max<int64_t>(
+            1, std::min<int64_t>(ceil_div(std::max<int64_t>(total, 1), rows_per_block),
+                                 (int64_t)ctx->num_sms * occupancy_blocks(launches[li].fn, kSweepThreads)));
+        void *params[] = {&m};
+        LaunchTimer lt(ctx, st, "filter.sweep", launches[li].bytes);
+        GIFT_CUDA(cudaLaunchKernel(launches[li].fn, dim3(grid), dim3(kSweepThreads), params, 0, st));
+    }
 }
 
 }  // namespace gift

@@ -298,6 +298,25 @@ void scan_nonfinite(gift_ctx *ctx, const float *x, int64_t n, int32_t *flag, cud
 float *host_mirror(void *p, size_t bytes);
 gift_graph::Scale graph_scale(gift_ctx *ctx, gift_graph *g, float sigma, int norm, cudaStream_t st);
 size_t filter_scratch_bytes(const gift_graph *g, const gift_filter_spec *spec, int S);
+// Several graphs filtered together: every sweep of every graph runs in the
+// same launches (a multi-graph direct row-group kernel), each graph with its
+// own signals and buffers; every result equals the graph's own gift_filter
+// result with the same schedule, bit for bit.  All graphs share the spec and
+// S; none has implicit cliques; at most 16 graphs; device signals.
+constexpr int kMaxMulti = 16;  // graphs per shared launch
+struct BatchItem {
+    const gift_graph *g;
+    const float *din;
+    float *dout;
+    float *mirror;  // optional: the last sweep also stores the result here (mapped host memory)
+};
+// true for the direct row-group shapes (natural order, 2 or 4 gathers in
+// flight, no warp rows) the batched filter runs
+bool batchable_shape(int schedule);
+// staging (optional): page-locked host memory for the launch arguments, not
+// reused by the caller before the work queued on st has run
+void filter_batch(gift_ctx *ctx, const std::vector<BatchItem> &items, const gift_filter_spec *spec, int S,
+                  int schedule, cudaStream_t st, void *staging = nullptr, size_t staging_bytes = 0);
 // noalloc.cu: loads the no-alloc scratch array on `device` (current) and
 // caches its device address; throws on failure.
 void noalloc_reserve(int device);

@@ -5,12 +5,22 @@
 // server's slots is idle and its estimated HBM footprint fits in the budget
 // next to the requests already running (strict FIFO: the head is never
 // overtaken).  Each slot is a worker thread with its own CUDA stream that runs
-// the admitted request's whole path -- graph build, filter, HPWL, copies -- on
-// that stream, so admitted requests overlap on the device; when one finishes,
-// its slot and footprint are released and the next waiting request is
-// admitted at once.  All slots share one context (stream-ordered memory pool,
-// cached scales); every kernel is deterministic per request, so a result does
-// not depend on the other requests in flight.
+// the admitted request's graph build, HPWL and copies on that stream, so
+// admitted requests overlap on the device; when one finishes, its slot and
+// footprint are released and the next waiting request is admitted at once.
+//
+// The filter passes are shared: a request whose graph is built joins the
+// filter queue, and one slot at a time -- the first whose request is queued
+// while no other slot leads -- runs every queued request's filter in the same
+// sweep launches (filter_batch: one multi-graph launch per sweep and chain
+// group, up to 16 requests with the same number of signals) on the batch
+// stream.  A leader first waits for the previous batch to finish on the
+// device, so requests arriving meanwhile gather into the next batch: under
+// load the batches grow and the launches per request shrink, and a lone
+// request pays no hand-over to another thread.  Every row is computed as the
+// request's own filter computes it, so a result does not depend on the other
+// requests in flight (bit-identical to gift_filter with the server's shape).
+// All slots share one context (stream-ordered memory pool, cached scales).
 #include <algorithm>
 #include <chrono>
 #include <condition_variable>
@@ -81,14 +91,20 @@ struct PinnedPool {
 struct Request {
     uint64_t ticket = 0;
     int32_t n = 0, e = 0, S = 0, weight_dtype = GIFT_WEIGHT_F32;
-    std::vector<int64_t> net_ptr;
-    std::vector<int32_t> pin_cell;
-    std::vector<uint8_t> is_fixed;
+    int64_t P = 0;
     PinnedPool *pool = nullptr;
+    // the request's copies, page-locked, from the pool (uploaded by the build
+    // without a staging copy)
+    int64_t *net_ptr = nullptr;  // [e + 1]
+    int32_t *pin_cell = nullptr;  // [P]
+    uint8_t *is_fixed = nullptr;  // [n]
     size_t sig_bytes = 0;
-    float *g_in = nullptr, *g_out = nullptr;  // page-locked, from the pool
+    float *g_in = nullptr, *g_out = nullptr;
     ~Request() {
         if (pool) {
+            pool->give(net_ptr, sizeof(int64_t) * (e + 1));
+            pool->give(pin_cell, sizeof(int32_t) * std::max<int64_t>(P, 1));
+            pool->give(is_fixed, (size_t)n);
             pool->give(g_in, sig_bytes);
             pool->give(g_out, sig_bytes);
         }
@@ -120,6 +136,24 @@ int64_t footprint_bytes(int64_t N, int64_t E, int64_t P, int64_t R, int S, int w
 
 using namespace gift;
 
+namespace gift {
+namespace {
+// A request in (or waiting for) a shared filter batch.
+struct FilterJob {
+    gift_graph *g = nullptr;
+    const float *din = nullptr;
+    float *dout = nullptr;
+    float *mirror = nullptr;
+    int S = 0;
+    cudaEvent_t ready = nullptr;     // recorded on the request's stream once its inputs are on the device
+    cudaEvent_t finished = nullptr;  // recorded on the batch stream after the batch's last sweep
+    bool done = false;
+    gift_status status = GIFT_OK;
+    std::string error;
+};
+}  // namespace
+}  // namespace gift
+
 struct gift_server {
     gift_serve_opts opts;
     gift_ctx *ctx = nullptr;
@@ -140,9 +174,26 @@ struct gift_server {
     bool any_submit = false, any_done = false;
     std::vector<std::thread> workers;
     std::vector<cudaStream_t> streams;
+    std::vector<cudaEvent_t> ev_ready, ev_done;  // per slot
+    // shared filter batches
+    int32_t schedule = 0;    // the shape every request's filter runs with
+    bool batching = false;
+    std::mutex fmu;
+    std::condition_variable fcv;
+    std::deque<FilterJob *> fqueue;
+    bool leading = false;           // a slot is forming or launching a batch (guarded by fmu)
+    cudaStream_t bstream = nullptr;
+    cudaEvent_t prev = nullptr;     // recorded after the last batch's sweeps
+    void *staging = nullptr;        // page-locked launch arguments of a batch (reused after prev)
+    static constexpr size_t kStagingBytes = 1 << 18;
+    bool prev_pending = false;      // guarded by fmu
+    int64_t batches = 0, batched_requests = 0;
+    int peak_batch = 0;
 
     void worker(int w);
-    void run(Request &r, cudaStream_t st);
+    void run(Request &r, int w);
+    void lead();
+    void filter_shared(FilterJob &job);
     bool head_fits() const {
         if (waiting.empty() || running >= opts.max_slots) return false;
         const Request &r = *reqs.at(waiting.front());
@@ -150,13 +201,14 @@ struct gift_server {
     }
 };
 
-void gift_server::run(Request &r, cudaStream_t st) {
+void gift_server::run(Request &r, int w) {
+    cudaStream_t st = streams[w];
     gift_netlist nl;
     nl.num_cells = r.n;
     nl.num_nets = r.e;
-    nl.net_ptr = r.net_ptr.data();
-    nl.pin_cell = r.pin_cell.data();
-    nl.is_fixed = r.is_fixed.data();
+    nl.net_ptr = r.net_ptr;
+    nl.pin_cell = r.pin_cell;
+    nl.is_fixed = r.is_fixed;
     nl.mem = GIFT_MEM_HOST;
     gift_build_opts bo;
     gift_build_opts_default(&bo);
@@ -175,10 +227,26 @@ void gift_server::run(Request &r, cudaStream_t st) {
     DevBuf din(ctx, sig_bytes, st), dout(ctx, sig_bytes, st);
     GIFT_CUDA(cudaMemcpyAsync(din.p, r.g_in, sig_bytes, cudaMemcpyHostToDevice, st));
     gift_filter_spec spec = opts.spec;
-    if (spec.schedule == 0) spec.schedule = kServeSchedule;
+    spec.schedule = schedule;
     r.g_out = static_cast<float *>(pinned.take(sig_bytes));
     float *mirror = host_mirror(r.g_out, sig_bytes);  // the last sweep stores the result into it
-    filter_impl(ctx, g, &spec, din.as<float>(), r.S, dout.as<float>(), GIFT_MEM_DEVICE, st, mirror);
+    if (batching && g->imp_nets == 0) {
+        // join the next shared filter batch and wait for it
+        FilterJob job;
+        job.g = g;
+        job.din = din.as<float>();
+        job.dout = dout.as<float>();
+        job.mirror = mirror;
+        job.S = r.S;
+        job.ready = ev_ready[w];
+        job.finished = ev_done[w];
+        GIFT_CUDA(cudaEventRecord(job.ready, st));
+        filter_shared(job);
+        if (job.status != GIFT_OK) throw Failure{job.status, job.error};
+        GIFT_CUDA(cudaStreamWaitEvent(st, job.finished, 0));
+    } else {
+        filter_impl(ctx, g, &spec, din.as<float>(), r.S, dout.as<float>(), GIFT_MEM_DEVICE, st, mirror);
+    }
     if (opts.compute_hpwl) {
         r.hpwl.assign(r.S, 0.0);
         hpwl_impl(ctx, g, dout.as<float>(), r.S, r.hpwl.data(), GIFT_MEM_DEVICE, st);
@@ -187,6 +255,87 @@ void gift_server::run(Request &r, cudaStream_t st) {
     sync_and_check(ctx, st);
     pinned.give(r.g_in, sig_bytes);  // the input is on the device now
     r.g_in = nullptr;
+}
+
+// Queues the job and waits until a batch has run it, leading batches itself
+// whenever no other slot does.
+void gift_server::filter_shared(FilterJob &job) {
+    std::unique_lock<std::mutex> lk(fmu);
+    fqueue.push_back(&job);
+    fcv.notify_all();  // a leader waiting out its batch window counts the queue
+    while (!job.done) {
+        if (!leading) {
+            leading = true;
+            lk.unlock();
+            lead();
+            lk.lock();
+            leading = false;
+            fcv.notify_all();
+        } else {
+            fcv.wait(lk);
+        }
+    }
+}
+
+// One batch: waits for the previous batch to finish on the device (requests
+// gather meanwhile), takes every queued request with the head's number of
+// signals (at most kMaxMulti, FIFO), waits for their inputs on the batch
+// stream, runs their filters in shared launches and releases them.
+void gift_server::lead() {
+    bool wait_prev;
+    {
+        std::lock_guard<std::mutex> lk(fmu);
+        wait_prev = prev_pending;
+    }
+    if (wait_prev) cudaEventSynchronize(prev);
+    std::vector<FilterJob *> batch;
+    {
+        std::unique_lock<std::mutex> lk(fmu);
+        if (opts.batch_window_us > 0)  // hold the batch open a while unless it is full
+            fcv.wait_for(lk, std::chrono::microseconds(opts.batch_window_us),
+                         [&] { return (int)fqueue.size() >= kMaxMulti; });
+        if (fqueue.empty()) return;
+        const int S = fqueue.front()->S;
+        for (auto it = fqueue.begin(); it != fqueue.end() && (int)batch.size() < kMaxMulti;) {
+            if ((*it)->S == S) {
+                batch.push_back(*it);
+                it = fqueue.erase(it);
+            } else {
+                ++it;
+            }
+        }
+    }
+    std::vector<BatchItem> items;
+    for (FilterJob *j : batch) items.push_back(BatchItem{j->g, j->din, j->dout, j->mirror});
+    gift_filter_spec spec = opts.spec;
+    std::string err;
+    const gift_status s = guarded([&] {
+        for (FilterJob *j : batch) GIFT_CUDA(cudaStreamWaitEvent(bstream, j->ready, 0));
+        filter_batch(ctx, items, &spec, batch.front()->S, schedule, bstream, staging, kStagingBytes);
+        for (FilterJob *j : batch) GIFT_CUDA(cudaEventRecord(j->finished, bstream));
+        GIFT_CUDA(cudaEventRecord(prev, bstream));
+    });
+    if (s != GIFT_OK) {
+        err = gift_last_error();
+        cudaStreamSynchronize(bstream);  // nothing of the batch may still run when the requests fail
+        cudaGetLastError();
+    }
+    {
+        std::lock_guard<std::mutex> lk(fmu);
+        prev_pending = s == GIFT_OK;
+        for (FilterJob *j : batch) {
+            j->status = s;
+            j->error = err;
+            j->done = true;
+        }
+    }
+    {
+        std::lock_guard<std::mutex> lk(mu);
+        ++batches;
+        batched_requests += (int64_t)batch.size();
+        peak_batch = std::max(peak_batch, (int)batch.size());
+    }
+    fcv.notify_all();
 }
 
 void gift_server::worker(int w) {
@@ -210,7 +359,7 @@ void gift_server::worker(int w) {
         }
         cv_work.notify_all();  // the next request may fit as well
         std::string err;
-        const gift_status s = guarded([&] { run(*r, st); });
+        const gift_status s = guarded([&] { run(*r, w); });
         if (s != GIFT_OK) {
             err = gift_last_error();
             // work queued before the failure may still read the request's
@@ -269,6 +418,10 @@ gift_status gift_serve_create(const gift_serve_opts *opts, gift_server **out) {
         GIFT_REQUIRE(o.hbm_budget_bytes >= 0, "gift_serve_create: negative budget");
         GIFT_REQUIRE(o.implicit_min_pins == 0 || o.implicit_min_pins >= 2,
                      "gift_serve_create: implicit_min_pins is 0 or at least 2");
+        GIFT_REQUIRE(o.separate_filters == 0 || o.separate_filters == 1,
+                     "gift_serve_create: separate_filters is 0 or 1");
+        GIFT_REQUIRE(o.batch_window_us >= 0 && o.batch_window_us <= 1000000,
+                     "gift_serve_create: batch_window_us must be in [0, 1e6]");
         for (int r : o.reserved) GIFT_REQUIRE(r == 0, "gift_serve_create: reserved fields must be zero");
         GIFT_REQUIRE(o.spec.num_terms >= 1 && o.spec.num_terms <= GIFT_MAX_TERMS,
                      "gift_serve_create: num_terms out of range");
@@ -287,12 +440,24 @@ gift_status gift_serve_create(const gift_serve_opts *opts, gift_server **out) {
             GIFT_CUDA(cudaMemGetInfo(&fr, &tot));
             srv->opts.hbm_budget_bytes = (int64_t)(fr / 2);
         }
+        srv->schedule = o.spec.schedule != 0 ? o.spec.schedule : kServeSchedule;
+        srv->batching = o.separate_filters == 0 && o.spec.compensated == 0 && batchable_shape(srv->schedule);
         srv->t_create = Clock::now();
         try {
             for (int w = 0; w < o.max_slots; ++w) {
                 cudaStream_t s;
                 GIFT_CUDA(cudaStreamCreateWithFlags(&s, cudaStreamNonBlocking));
                 srv->streams.push_back(s);
+                cudaEvent_t e0, e1;
+                GIFT_CUDA(cudaEventCreateWithFlags(&e0, cudaEventDisableTiming));
+                srv->ev_ready.push_back(e0);
+                GIFT_CUDA(cudaEventCreateWithFlags(&e1, cudaEventDisableTiming));
+                srv->ev_done.push_back(e1);
+            }
+            if (srv->batching) {
+                GIFT_CUDA(cudaStreamCreateWithFlags(&srv->bstream, cudaStreamNonBlocking));
+                GIFT_CUDA(cudaEventCreateWithFlags(&srv->prev, cudaEventDisableTiming));
+                GIFT_CUDA(cudaHostAlloc(&srv->staging, gift_server::kStagingBytes, cudaHostAllocDefault));
             }
             for (int w = 0; w < o.max_slots; ++w) srv->workers.emplace_back([p = srv.get(), w] { p->worker(w); });
         } catch (...) {
@@ -303,6 +468,11 @@ gift_status gift_serve_create(const gift_serve_opts *opts, gift_server **out) {
             srv->cv_work.notify_all();
             for (auto &t : srv->workers) t.join();
             for (auto s : srv->streams) cudaStreamDestroy(s);
+            for (auto e : srv->ev_ready) cudaEventDestroy(e);
+            for (auto e : srv->ev_done) cudaEventDestroy(e);
+            if (srv->bstream) cudaStreamDestroy(srv->bstream);
+            if (srv->prev) cudaEventDestroy(srv->prev);
+            if (srv->staging) cudaFreeHost(srv->staging);
             gift_ctx_destroy(srv->ctx);
             throw;
         }
@@ -327,27 +497,52 @@ gift_status gift_serve_submit(gift_server *srv, const gift_netlist *nl, const fl
         r->e = nl->num_nets;
         r->S = S;
         r->weight_dtype = wd;
+        r->pool = &srv->pinned;
         GIFT_REQUIRE(nl->net_ptr[0] == 0, "gift_serve_submit: net_ptr[0] must be 0");
+        // Each array is copied into the request's page-locked buffers and
+        // checked in the same pass (branch-free flags, so the loops vectorise).
         int64_t R = 0;  // expanded pairs (implicit nets add none)
         const int64_t imin = srv->opts.implicit_min_pins;
+        r->net_ptr = static_cast<int64_t *>(srv->pinned.take(sizeof(int64_t) * (nl->num_nets + 1)));
+        r->net_ptr[0] = 0;
+        int64_t decreasing = 0;
         for (int32_t e = 0; e < nl->num_nets; ++e) {
-            const int64_t m = nl->net_ptr[e + 1] - nl->net_ptr[e];
-            GIFT_REQUIRE(m >= 0, "gift_serve_submit: net_ptr must be non-decreasing");
-            if (m >= 2 && (imin == 0 || m < imin)) R += m * (m - 1);
+            const int64_t b = nl->net_ptr[e], f = nl->net_ptr[e + 1], m = f - b;
+            r->net_ptr[e + 1] = f;
+            decreasing |= m < 0;
+            R += (m >= 2 && (imin == 0 || m < imin)) ? m * (m - 1) : 0;
         }
+        GIFT_REQUIRE(!decreasing, "gift_serve_submit: net_ptr must be non-decreasing");
         const int64_t P = nl->net_ptr[nl->num_nets];
-        r->net_ptr.assign(nl->net_ptr, nl->net_ptr + nl->num_nets + 1);
-        r->pin_cell.assign(nl->pin_cell, nl->pin_cell + P);
-        for (int32_t c : r->pin_cell)
-            GIFT_REQUIRE(c >= 0 && c < nl->num_cells, "gift_serve_submit: pin cell out of range");
-        if (nl->is_fixed) r->is_fixed.assign(nl->is_fixed, nl->is_fixed + nl->num_cells);
-        else r->is_fixed.assign(nl->num_cells, 0);
+        r->P = P;
+        r->pin_cell = static_cast<int32_t *>(srv->pinned.take(sizeof(int32_t) * std::max<int64_t>(P, 1)));
+        {
+            uint32_t bad = 0;
+            const uint32_t ncell = (uint32_t)nl->num_cells;
+            for (int64_t k = 0; k < P; ++k) {
+                const int32_t c = nl->pin_cell[k];
+                r->pin_cell[k] = c;
+                bad |= (uint32_t)c >= ncell;  // negative ids wrap above num_cells
+            }
+            GIFT_REQUIRE(!bad, "gift_serve_submit: pin cell out of range");
+        }
+        r->is_fixed = static_cast<uint8_t *>(srv->pinned.take((size_t)nl->num_cells));
+        if (nl->is_fixed) std::memcpy(r->is_fixed, nl->is_fixed, (size_t)nl->num_cells);
+        else std::memset(r->is_fixed, 0, (size_t)nl->num_cells);
         const size_t count = (size_t)nl->num_cells * 2 * S;
-        for (size_t i = 0; i < count; ++i) GIFT_REQUIRE(std::isfinite(g_in[i]), "gift_serve_submit: g_in must be finite");
-        r->pool = &srv->pinned;
         r->sig_bytes = sizeof(float) * count;
         r->g_in = static_cast<float *>(srv->pinned.take(r->sig_bytes));
-        std::memcpy(r->g_in, g_in, r->sig_bytes);
+        {
+            uint32_t bad = 0;
+            const uint32_t *src = reinterpret_cast<const uint32_t *>(g_in);
+            uint32_t *dst = reinterpret_cast<uint32_t *>(r->g_in);
+            for (size_t i = 0; i < count; ++i) {
+                const uint32_t v = src[i];
+                dst[i] = v;
+                bad |= (v & 0x7f800000u) == 0x7f800000u;  // exponent all ones: infinity or NaN
+            }
+            GIFT_REQUIRE(!bad, "gift_serve_submit: g_in must be finite");
+        }
         r->footprint = footprint_bytes(nl->num_cells, nl->num_nets, P, R, S, wd, srv->chains);
         GIFT_REQUIRE(r->footprint <= srv->opts.hbm_budget_bytes,
                      "gift_serve_submit: the request's footprint exceeds the server's HBM budget");
@@ -466,6 +661,9 @@ gift_status gift_serve_stats_get(gift_server *srv, gift_serve_stats *out) {
         out->peak_footprint_bytes = srv->peak_in_use;
         out->max_slots = srv->opts.max_slots;
         out->peak_running = srv->peak_running;
+        out->batches = srv->batches;
+        out->batched_requests = srv->batched_requests;
+        out->peak_batch = srv->peak_batch;
     });
 }
 
@@ -479,9 +677,15 @@ void gift_serve_destroy(gift_server *srv) {
     }
     srv->cv_work.notify_all();
     srv->cv_done.notify_all();
-    for (auto &t : srv->workers) t.join();
+    for (auto &t : srv->workers) t.join();  // running requests finish, including their filter batches
     cudaSetDevice(srv->opts.device);
+    if (srv->bstream) cudaStreamSynchronize(srv->bstream);
     for (auto s : srv->streams) cudaStreamDestroy(s);
+    for (auto e : srv->ev_ready) cudaEventDestroy(e);
+    for (auto e : srv->ev_done) cudaEventDestroy(e);
+    if (srv->bstream) cudaStreamDestroy(srv->bstream);
+    if (srv->prev) cudaEventDestroy(srv->prev);
+    if (srv->staging) cudaFreeHost(srv->staging);
     gift_ctx_destroy(srv->ctx);
     delete srv;
 }

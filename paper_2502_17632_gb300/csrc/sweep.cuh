@@ -70,6 +70,7 @@ struct SweepArgs {
     int64_t n_slots;      // slots in order
     int32_t slot_csr;     // 1: row_ptr / col / val hold the rows in slot order (row_ptr[slot]);
                           // 0: they are indexed by row
+    int32_t weight_dtype; // GIFT_WEIGHT_* of val (read at run time by the multi-graph sweep)
     ImplicitArgs imp;
 };
 

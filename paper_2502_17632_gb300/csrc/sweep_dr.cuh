@@ -16,6 +16,8 @@
 // about half of the lane-steps of a warp are idle.
 #pragma once
 
+#include <type_traits>
+
 #include "sweep_mp.cuh"
 
 namespace gift {
@@ -46,6 +48,21 @@ struct DrIdx {
     float w[U];
 };
 
+// Weight type chosen at run time from a.weight_dtype (the multi-graph sweep,
+// whose graphs may store different types).
+struct WeightRuntime {};
+
+template <typename WT>
+__device__ __forceinline__ float dr_weight(const SweepArgs &a, int64_t k) {
+    if constexpr (std::is_same<WT, WeightRuntime>::value) {
+        if (a.weight_dtype == GIFT_WEIGHT_BF16) return ld_weight_plain<__nv_bfloat16>(a.val, k);
+        if (a.weight_dtype == GIFT_WEIGHT_F16) return ld_weight_plain<__half>(a.val, k);
+        return ld_weight_plain<float>(a.val, k);
+    } else {
+        return ld_weight_plain<WT>(a.val, k);
+    }
+}
+
 template <typename WT, int U>
 __device__ __forceinline__ DrIdx<U> dr_load_idx(const SweepArgs &a, int64_t k0, int64_t ke, int ns) {
     DrIdx<U> r;
@@ -54,7 +71,7 @@ __device__ __forceinline__ DrIdx<U> dr_load_idx(const SweepArgs &a, int64_t k0, 
         const int64_t k = k0 + (int64_t)u * ns;
         const bool in = k < ke;
         r.j[u] = in ? __ldg(a.col + k) : 0;
-        r.w[u] = in ? ld_weight_plain<WT>(a.val, k) : 0.f;
+        r.w[u] = in ? dr_weight<WT>(a, k) : 0.f;
     }
     return r;
 }
@@ -67,20 +84,116 @@ __device__ __forceinline__ void comp_add(float &s, float &e, float x) {
     s = t;
 }
 
+// One row of a direct row-group sweep, for the lanes that own it (the whole
+// warp with WR); row < 0: no row (the lanes still take part in the warp's
+// shuffles), ci: the row's index into a.row_ptr (its slot in the sorted copy).
 // FIRST: the first sweep, whose input is the unscaled g (row j of chain c is
 // multiplied by pre_c[j]); NX = 1 there, and NC otherwise.
 // WR: a whole warp per row -- NS = 32 / CW groups of CW lanes, group ns taking
 // the row's nonzeros ns, ns + NS, ... (U at a time), then a fixed xor tree
 // over the groups; for rows of hundreds to thousands of nonzeros.
 // COMP (with WR): compensated FP32 sums (Neumaier) per lane and in the tree.
+template <typename WT, int VEC, int CW, int U, int NC, bool FIRST, bool WR, bool COMP>
+__device__ __forceinline__ void dr_row(const SweepArgs &a, int64_t row, int64_t ci, int ns, int col) {
+    constexpr int NX = FIRST ? 1 : NC;
+    constexpr int G = WR ? 32 : CW;  // lanes per row
+    constexpr int NS = G / CW;       // nonzero groups per row
+    const float *x0 = a.ch[0].x + col;
+    const float *x1 = a.ch[NX - 1].x + col;
+    const float2 *gp2 = FIRST && NC == 2 ? a.gpre2 : nullptr;
+    const float *gp0 = FIRST ? a.ch[0].gpre : nullptr;
+    const float *gp1 = FIRST ? a.ch[NC - 1].gpre : nullptr;
+    const int ldx0 = a.ch[0].ldx, ldx1 = a.ch[NX - 1].ldx;
+    float acc[NC][VEC], err[NC][VEC];
+#pragma unroll
+    for (int c = 0; c < NC; ++c)
+#pragma unroll
+        for (int v = 0; v < VEC; ++v) acc[c][v] = err[c][v] = 0.f;
+    int64_t kb = 0, ke = 0;
+    if (row >= 0) {
+        kb = __ldg(a.row_ptr + ci);
+        ke = __ldg(a.row_ptr + ci + 1);
+    }
+    // Warp rows (rows of hundreds to thousands of nonzeros): the next
+    // step's (col, val) are loaded while this step's rows are gathered,
+    // so the CSR stream's DRAM latency overlaps the gathers.
+    DrIdx<U> nx;
+    if (WR) nx = dr_load_idx<WT, U>(a, kb + ns, ke, NS);
+    for (int64_t k0 = kb + ns; k0 < ke; k0 += (int64_t)NS * U) {
+        const DrIdx<U> cur = WR ? nx : dr_load_idx<WT, U>(a, k0, ke, NS);
+        if (WR) nx = dr_load_idx<WT, U>(a, k0 + (int64_t)NS * U, ke, NS);
+        const int32_t(&j)[U] = cur.j;
+        const float(&w)[U] = cur.w;
+        float xv[U][NX][VEC];
+#pragma unroll
+        for (int u = 0; u < U; ++u) {
+            if (k0 + (int64_t)u * NS < ke) {
+                ldv<VEC>(x0 + (int64_t)j[u] * ldx0, xv[u][0]);
+                if (NX == 2) ldv<VEC>(x1 + (int64_t)j[u] * ldx1, xv[u][NX - 1]);
+            }
+        }
+        float wc[U][NC];
+#pragma unroll
+        for (int u = 0; u < U; ++u) {
+            if (!FIRST) {
+#pragma unroll
+                for (int c = 0; c < NC; ++c) wc[u][c] = w[u];
+            } else if (k0 + (int64_t)u * NS < ke) {
+                if (gp2) {
+                    const float2 s = __ldg(gp2 + j[u]);
+                    wc[u][0] = w[u] * s.x;
+                    wc[u][NC - 1] = w[u] * s.y;
+                } else {
+                    wc[u][0] = gp0 ? w[u] * __ldg(gp0 + j[u]) : w[u];
+                    if (NC == 2) wc[u][NC - 1] = gp1 ? w[u] * __ldg(gp1 + j[u]) : w[u];
+                }
+            }
+        }
+#pragma unroll
+        for (int u = 0; u < U; ++u) {
+            if (k0 + (int64_t)u * NS < ke) {
+#pragma unroll
+                for (int c = 0; c < NC; ++c)
+#pragma unroll
+                    for (int v = 0; v < VEC; ++v) {
+                        if (COMP) comp_add(acc[c][v], err[c][v], wc[u][c] * xv[u][NX == 2 ? c : 0][v]);
+                        else acc[c][v] = fmaf(wc[u][c], xv[u][NX == 2 ? c : 0][v], acc[c][v]);
+                    }
+            }
+        }
+    }
+    if (WR) {  // fixed tree over the nonzero groups of the row
+#pragma unroll
+        for (int o = CW; o < 32; o <<= 1)
+#pragma unroll
+            for (int c = 0; c < NC; ++c)
+#pragma unroll
+                for (int v = 0; v < VEC; ++v) {
+                    const float b = __shfl_xor_sync(0xffffffffu, acc[c][v], o);
+                    if (COMP) {
+                        const float eb = __shfl_xor_sync(0xffffffffu, err[c][v], o);
+                        err[c][v] += eb;
+                        comp_add(acc[c][v], err[c][v], b);
+                    } else {
+                        acc[c][v] += b;
+                    }
+                }
+    }
+    if (COMP) {
+#pragma unroll
+        for (int c = 0; c < NC; ++c)
+#pragma unroll
+            for (int v = 0; v < VEC; ++v) acc[c][v] += err[c][v];
+    }
+    if (row >= 0 && ns == 0) mp_finish<VEC, NC>(a, row, col, acc);
+}
+
 template <typename WT, int VEC, int CW, int U, int NC, bool FIRST, bool WR = false, bool COMP = false>
 __global__ void __launch_bounds__(kSweepThreads, dr_min_blocks(VEC, U, (COMP ? 2 : 1) * NC, FIRST ? 1 : NC, FIRST, WR))
 k_sweep_dr(const SweepArgs a) {
     static_assert(CW >= 1 && CW <= 32 && 32 % CW == 0, "lanes per row divide the warp");
     static_assert(WR || !COMP, "compensated sums come with warp rows");
-    constexpr int NX = FIRST ? 1 : NC;
     constexpr int G = WR ? 32 : CW;  // lanes per row
-    constexpr int NS = G / CW;       // nonzero groups per row
     constexpr int RPW = 32 / G;
     const int lane = threadIdx.x & 31;
     const int gi = lane / G, gl = lane % G;
@@ -88,102 +201,68 @@ k_sweep_dr(const SweepArgs a) {
     const int col = a.c0 + q * VEC;
     const int64_t warp = (blockIdx.x * (int64_t)blockDim.x + threadIdx.x) >> 5;
     const int64_t nwarps = ((int64_t)gridDim.x * blockDim.x) >> 5;
-    const float *x0 = a.ch[0].x + col;
-    const float *x1 = a.ch[NX - 1].x + col;
-    const float2 *gp2 = FIRST && NC == 2 ? a.gpre2 : nullptr;
-    const float *gp0 = FIRST ? a.ch[0].gpre : nullptr;
-    const float *gp1 = FIRST ? a.ch[NC - 1].gpre : nullptr;
-
     const int64_t nslots = a.order ? a.n_slots : a.n_rows;
-    const int ldx0 = a.ch[0].ldx, ldx1 = a.ch[NX - 1].ldx;
     for (int64_t slot = warp * RPW + gi; slot - gi < nslots; slot += nwarps * RPW) {
         const int64_t row = slot < nslots ? (a.order ? (int64_t)__ldg(a.order + slot) : slot) : -1;
-        float acc[NC][VEC], err[NC][VEC];
-#pragma unroll
-        for (int c = 0; c < NC; ++c)
-#pragma unroll
-            for (int v = 0; v < VEC; ++v) acc[c][v] = err[c][v] = 0.f;
-        int64_t kb = 0, ke = 0;
-        if (row >= 0) {
-            // the sorted copy of the CSR holds the rows in slot order
-            const int64_t ci = a.slot_csr ? slot : row;
-            kb = __ldg(a.row_ptr + ci);
-            ke = __ldg(a.row_ptr + ci + 1);
-        }
-        // Warp rows (rows of hundreds to thousands of nonzeros): the next
-        // step's (col, val) are loaded while this step's rows are gathered,
-        // so the CSR stream's DRAM latency overlaps the gathers.
-        DrIdx<U> nx;
-        if (WR) nx = dr_load_idx<WT, U>(a, kb + ns, ke, NS);
-        for (int64_t k0 = kb + ns; k0 < ke; k0 += (int64_t)NS * U) {
-            const DrIdx<U> cur = WR ? nx : dr_load_idx<WT, U>(a, k0, ke, NS);
-            if (WR) nx = dr_load_idx<WT, U>(a, k0 + (int64_t)NS * U, ke, NS);
-            const int32_t(&j)[U] = cur.j;
-            const float(&w)[U] = cur.w;
-            float xv[U][NX][VEC];
-#pragma unroll
-            for (int u = 0; u < U; ++u) {
-                if (k0 + (int64_t)u * NS < ke) {
-                    ldv<VEC>(x0 + (int64_t)j[u] * ldx0, xv[u][0]);
-                    if (NX == 2) ldv<VEC>(x1 + (int64_t)j[u] * ldx1, xv[u][NX - 1]);
-                }
-            }
-            float wc[U][NC];
-#pragma unroll
-            for (int u = 0; u < U; ++u) {
-                if (!FIRST) {
-#pragma unroll
-                    for (int c = 0; c < NC; ++c) wc[u][c] = w[u];
-                } else if (k0 + (int64_t)u * NS < ke) {
-                    if (gp2) {
-                        const float2 s = __ldg(gp2 + j[u]);
-                        wc[u][0] = w[u] * s.x;
-                        wc[u][NC - 1] = w[u] * s.y;
-                    } else {
-                        wc[u][0] = gp0 ? w[u] * __ldg(gp0 + j[u]) : w[u];
-                        if (NC == 2) wc[u][NC - 1] = gp1 ? w[u] * __ldg(gp1 + j[u]) : w[u];
-                    }
-                }
-            }
-#pragma unroll
-            for (int u = 0; u < U; ++u) {
-                if (k0 + (int64_t)u * NS < ke) {
-#pragma unroll
-                    for (int c = 0; c < NC; ++c)
-#pragma unroll
-                        for (int v = 0; v < VEC; ++v) {
-                            if (COMP) comp_add(acc[c][v], err[c][v], wc[u][c] * xv[u][NX == 2 ? c : 0][v]);
-                            else acc[c][v] = fmaf(wc[u][c], xv[u][NX == 2 ? c : 0][v], acc[c][v]);
-                        }
-                }
-            }
-        }
-        if (WR) {  // fixed tree over the nonzero groups of the row
-#pragma unroll
-            for (int o = CW; o < 32; o <<= 1)
-#pragma unroll
-                for (int c = 0; c < NC; ++c)
-#pragma unroll
-                    for (int v = 0; v < VEC; ++v) {
-                        const float b = __shfl_xor_sync(0xffffffffu, acc[c][v], o);
-                        if (COMP) {
-                            const float eb = __shfl_xor_sync(0xffffffffu, err[c][v], o);
-                            err[c][v] += eb;
-                            comp_add(acc[c][v], err[c][v], b);
-                        } else {
-                            acc[c][v] += b;
-                        }
-                    }
-        }
-        if (COMP) {
-#pragma unroll
-            for (int c = 0; c < NC; ++c)
-#pragma unroll
-                for (int v = 0; v < VEC; ++v) acc[c][v] += err[c][v];
-        }
-        if (row >= 0 && ns == 0) mp_finish<VEC, NC>(a, row, col, acc);
+        // the sorted copy of the CSR holds the rows in slot order
+        dr_row<WT, VEC, CW, U, NC, FIRST, WR, COMP>(a, row, a.slot_csr ? slot : row, ns, col);
     }
 }
+
+// ---- several graphs in one launch (the request loop's shared sweeps).
+// The launch's rows are the graphs' rows one after another: graph r owns
+// rows [begin[r], begin[r + 1]) of the launch, each graph with its own
+// arguments (CSR, signals, scales, outputs, weight type).  Every row is
+// computed exactly as k_sweep_dr computes it for its graph alone (same lane
+// mapping, same order of additions), so a graph's result does not depend on
+// the other graphs of the launch.  Rows in natural order, no warp rows; at
+// most kMaxMulti graphs.
+
+struct MultiArgs {
+    const SweepArgs *args;  // [ng] (device)
+    const int64_t *begin;   // [ng + 1] (device)
+    int32_t ng;             // 1 .. kMaxMulti
+};
+
+// (one block per SM fewer than k_sweep_dr: the graphs' arguments come from
+// shared memory and need a few more registers)
+constexpr int multi_min_blocks(int vec, int u, int nc, bool first) {
+    return dr_min_blocks(vec, u, nc, first ? 1 : nc, first, false) > 3 ? dr_min_blocks(vec, u, nc, first ? 1 : nc, first, false) - 1
+                                                                       : 3;
+}
+
+template <int VEC, int CW, int U, int NC, bool FIRST>
+__global__ void __launch_bounds__(kSweepThreads, multi_min_blocks(VEC, U, NC, FIRST))
+k_sweep_multi(const MultiArgs m) {
+    static_assert(CW >= 1 && CW <= 32 && 32 % CW == 0, "lanes per row divide the warp");
+    __shared__ SweepArgs sa[kMaxMulti];
+    __shared__ int64_t sb[kMaxMulti + 1];
+    {
+        const int words = m.ng * (int)(sizeof(SweepArgs) / sizeof(int));
+        const int *src = reinterpret_cast<const int *>(m.args);
+        int *dst = reinterpret_cast<int *>(sa);
+        for (int t = threadIdx.x; t < words; t += blockDim.x) dst[t] = src[t];
+        for (int t = threadIdx.x; t <= m.ng; t += blockDim.x) sb[t] = m.begin[t];
+    }
+    __syncthreads();
+    constexpr int RPW = 32 / CW;
+    const int lane = threadIdx.x & 31;
+    const int gi = lane / CW, q = lane % CW;
+    const int64_t warp = (blockIdx.x * (int64_t)blockDim.x + threadIdx.x) >> 5;
+    const int64_t nwarps = ((int64_t)gridDim.x * blockDim.x) >> 5;
+    const int64_t total = sb[m.ng];
+    for (int64_t slot = warp * RPW + gi; slot - gi < total; slot += nwarps * RPW) {
+        int r = 0;
+        if (slot < total)
+            while (sb[r + 1] <= slot) ++r;
+        const SweepArgs &a = sa[r];
+        const int64_t row = slot < total ? slot - sb[r] : -1;
+        dr_row<WeightRuntime, VEC, CW, U, NC, FIRST, false, false>(a, row, row, 0, a.c0 + q * VEC);
+    }
+}
+
+// Multi-graph kernel for a configuration; nullptr if not instantiated.
+const void *sweep_multi_kernel(int vec, int cw, int u, int nc, bool first);
 
 // Kernel for a configuration; nullptr if not instantiated (u = 8 exists for
 // one chain with float2 lanes in row groups only; warp rows have u = 4).

@@ -71,7 +71,8 @@ class gift_kernel_stat(C.Structure):
 class gift_serve_opts(C.Structure):
     _fields_ = [("device", C.c_int32), ("max_slots", C.c_int32), ("hbm_budget_bytes", C.c_int64),
                 ("weight_dtype", C.c_int32), ("compute_hpwl", C.c_int32), ("spec", gift_filter_spec),
-                ("implicit_min_pins", C.c_int32), ("reserved", C.c_int32 * 7)]
+                ("implicit_min_pins", C.c_int32), ("separate_filters", C.c_int32),
+                ("batch_window_us", C.c_int32), ("reserved", C.c_int32 * 5)]
 
 
 class gift_req_stats(C.Structure):
@@ -85,7 +86,9 @@ class gift_serve_stats(C.Structure):
                 ("waiting", C.c_int64), ("running", C.c_int64), ("p50_ms", C.c_double), ("p99_ms", C.c_double),
                 ("mean_ms", C.c_double), ("max_ms", C.c_double), ("uptime_s", C.c_double),
                 ("requests_per_s", C.c_double), ("edge_updates_per_s", C.c_double), ("budget_bytes", C.c_int64),
-                ("peak_footprint_bytes", C.c_int64), ("max_slots", C.c_int32), ("peak_running", C.c_int32)]
+                ("peak_footprint_bytes", C.c_int64), ("max_slots", C.c_int32), ("peak_running", C.c_int32),
+                ("batches", C.c_int64), ("batched_requests", C.c_int64), ("peak_batch", C.c_int32),
+                ("reserved0", C.c_int32)]
 
 
 _lib = None

@@ -120,10 +120,12 @@ def test_serve_structs_match_header():
 #include <stddef.h>
 #include "gift.h"
 int main(void) {
-  printf("%zu %zu %zu %zu\n", sizeof(gift_serve_opts), offsetof(gift_serve_opts, spec),
+  printf("%zu %zu %zu %zu %zu %zu\n", sizeof(gift_serve_opts), offsetof(gift_serve_opts, spec),
+         offsetof(gift_serve_opts, separate_filters), offsetof(gift_serve_opts, batch_window_us),
          offsetof(gift_serve_opts, reserved), sizeof(gift_req_stats));
-  printf("%zu %zu %zu\n", sizeof(gift_serve_stats), offsetof(gift_serve_stats, budget_bytes),
-         offsetof(gift_serve_stats, peak_running));
+  printf("%zu %zu %zu %zu %zu\n", sizeof(gift_serve_stats), offsetof(gift_serve_stats, budget_bytes),
+         offsetof(gift_serve_stats, peak_running), offsetof(gift_serve_stats, batched_requests),
+         offsetof(gift_serve_stats, peak_batch));
   return 0;
 }
 """
@@ -134,7 +136,10 @@ int main(void) {
             f.write(src)
         subprocess.run([cc, "-I", f"{root}/include", f"{d}/t.c", "-o", f"{d}/t"], check=True)
         out = subprocess.run([f"{d}/t"], check=True, capture_output=True, text=True).stdout.split()
-    want = [C.sizeof(gift.gift_serve_opts), gift.gift_serve_opts.spec.offset, gift.gift_serve_opts.reserved.offset,
+    want = [C.sizeof(gift.gift_serve_opts), gift.gift_serve_opts.spec.offset,
+            gift.gift_serve_opts.separate_filters.offset, gift.gift_serve_opts.batch_window_us.offset,
+            gift.gift_serve_opts.reserved.offset,
             C.sizeof(gift.gift_req_stats), C.sizeof(gift.gift_serve_stats),
-            gift.gift_serve_stats.budget_bytes.offset, gift.gift_serve_stats.peak_running.offset]
+            gift.gift_serve_stats.budget_bytes.offset, gift.gift_serve_stats.peak_running.offset,
+            gift.gift_serve_stats.batched_requests.offset, gift.gift_serve_stats.peak_batch.offset]
     assert [int(x) for x in out] == want

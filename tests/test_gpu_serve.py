@@ -3,8 +3,9 @@
 Each request's result must be the same alone and in the mix: a request run by
 itself through gift_build_graph + gift_filter + gift_hpwl (same schedule, same
 weight type) and the same request served while others of different sizes
-and weight types overlap on the device give bit-identical outputs (every
-kernel is deterministic per request), and the FP32 requests match the FP64
+and weight types overlap on the device -- their filters sharing sweep
+launches -- give bit-identical outputs (every row is computed as the
+request's own filter computes it), and the FP32 requests match the FP64
 oracle within the 1e-5 bar.
 """
 import time
@@ -187,3 +188,70 @@ def test_implicit_cliques_in_the_mix(requests):
     for (out, hp, _), (out_a, hp_a) in zip(got, ref):
         np.testing.assert_array_equal(out, out_a)
         np.testing.assert_array_equal(hp, hp_a)
+
+
+@pytest.mark.parametrize("separate,window", [(0, 0), (0, 20000), (1, 0)])
+def test_burst_shares_filter_launches(requests, separate, window):
+    """A burst of requests: with shared filters (the default) several
+    requests run per launch -- FP32 and BF16 graphs in the same launch,
+    requests grouped by their number of signals -- and every result is still
+    bit-identical to the request alone (a batch window of 20 ms makes the
+    batches gather); with separate_filters = 1 every request runs its own
+    launches."""
+    reqs = requests * 3  # 36 requests, S in {1, 2, 4}, both weight types
+    ctx = gift.gift_ctx_create(0)
+    try:
+        ref = [alone(ctx, nl, g, wd) for nl, g, wd in requests]
+    finally:
+        gift.gift_ctx_destroy(ctx)
+    srv = gift.gift_serve_create(max_slots=16, separate_filters=separate, batch_window_us=window)
+    try:
+        tickets = submit_all(srv, reqs)
+        got = [gift.gift_serve_wait(srv, t, nl.num_cells, g.shape[1]) for t, (nl, g, _) in zip(tickets, reqs)]
+        st = gift.gift_serve_stats_get(srv)
+    finally:
+        gift.gift_serve_destroy(srv)
+    for k, (out, hp, _) in enumerate(got):
+        np.testing.assert_array_equal(out, ref[k % len(requests)][0])
+        np.testing.assert_array_equal(hp, ref[k % len(requests)][1])
+    assert st.completed == len(reqs) and st.failed == 0
+    if separate:
+        assert st.batches == 0 and st.batched_requests == 0
+    else:
+        assert st.batched_requests == len(reqs) and st.peak_batch <= 16
+        if window:
+            assert st.batches < len(reqs) and st.peak_batch >= 2  # requests shared launches
+
+
+def test_compensated_spec_runs_unbatched(requests):
+    """A server whose spec asks for compensated sums filters each request on
+    its own (warp-row kernels); the results equal the request's own
+    compensated filter."""
+    reqs = requests[:4]
+    spec = gift.make_spec(compensated=True)
+    ctx = gift.gift_ctx_create(0)
+    dev = lambda a: torch.from_numpy(np.ascontiguousarray(a)).cuda()  # noqa: E731
+    ref = []
+    try:
+        for nl, g, wd in reqs:
+            h = gift.gift_build_graph(ctx, nl.num_cells, dev(nl.net_ptr), dev(nl.pin_cell), dev(nl.is_fixed),
+                                      gift.WEIGHT[wd])
+            gi = dev(g)
+            go = torch.empty_like(gi)
+            s2 = gift.make_spec(compensated=True, schedule=SERVE_SCHEDULE)
+            gift.gift_filter(ctx, h, gi, go, s2)
+            torch.cuda.synchronize()
+            ref.append(go.cpu().numpy())
+            gift.gift_graph_free(h)
+    finally:
+        gift.gift_ctx_destroy(ctx)
+    srv = gift.gift_serve_create(max_slots=4, spec=spec)
+    try:
+        tickets = submit_all(srv, reqs)
+        got = [gift.gift_serve_wait(srv, t, nl.num_cells, g.shape[1]) for t, (nl, g, _) in zip(tickets, reqs)]
+        st = gift.gift_serve_stats_get(srv)
+    finally:
+        gift.gift_serve_destroy(srv)
+    for (out, _, _), r in zip(got, ref):
+        np.testing.assert_array_equal(out, r)
+    assert st.batches == 0
