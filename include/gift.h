@@ -110,7 +110,14 @@ typedef struct gift_filter_spec {
     gift_term term[GIFT_MAX_TERMS];
     int32_t norm;                   /* GIFT_NORM_SYM (paper) or GIFT_NORM_RW    */
     int32_t reimpose_fixed;         /* 1: fixed rows of the output := input     */
-    int32_t compensated;            /* 1: compensated FP32 sums on long rows    */
+    int32_t compensated;            /* 0 (default): compensated FP32 sums
+                                       (Neumaier) on the rows of at least 1024
+                                       stored entries, plain FP32 on the others;
+                                       1: on every row; 2: on none.  Rows are
+                                       left to the automatic compensation only
+                                       by direct and row-group schedules
+                                       (merge-path, TMA and sliced-ELL
+                                       schedules sum every row plainly)    */
     int32_t schedule;               /* 0: autotuned; else a fixed kernel choice */
 } gift_filter_spec;
 /* Schedule codes (every launch kind uses the one shape):

@@ -79,6 +79,12 @@ def lib():
         L.oracle_filter.argtypes = [C.c_int32, C.c_int32, P, P, P, P, C.c_int32, P, P, P,
                                     C.c_int32, C.c_int32, P, P, P]
         L.oracle_hpwl.argtypes = [C.c_int32, P, P, C.c_int32, P, P]
+        L.oracle_apply_cut.restype = C.c_int
+        L.oracle_apply_cut.argtypes = [C.c_int32, C.c_int32, P, P, P, P, C.c_double, C.c_int32, C.c_int32, P, P,
+                                       C.c_int64, P, P]
+        L.oracle_filter_cut.restype = C.c_int
+        L.oracle_filter_cut.argtypes = [C.c_int32, C.c_int32, P, P, P, P, C.c_int32, P, P, P, C.c_int32, C.c_int32,
+                                        P, C.c_int32, P, P, C.c_int64, P, P]
         _lib = L
     return _lib
 
@@ -272,9 +278,37 @@ def apply(g: Graph, d: np.ndarray, sigma: float, x: np.ndarray, norm: str = "sym
     return y
 
 
+def _netlist_args(net_ptr, pin_cell):
+    net_ptr = np.ascontiguousarray(net_ptr, dtype=np.int64)
+    pin_cell = np.ascontiguousarray(pin_cell, dtype=np.int32)
+    if pin_cell.size == 0:
+        pin_cell = np.zeros(1, dtype=np.int32)
+    return net_ptr, pin_cell
+
+
+def apply_cut(g: Graph, d: np.ndarray, sigma: float, x: np.ndarray, net_ptr: np.ndarray, pin_cell: np.ndarray,
+              cut: int, norm: str = "sym") -> np.ndarray:
+    """One product y = A~_sigma x with the cliques of the nets of at least
+    `cut` pins applied from the netlist (g holds the other nets, from
+    build_graph(..., cut); d the degrees of the whole expansion)."""
+    x = np.ascontiguousarray(x, dtype=np.float64)
+    K = 1 if x.ndim == 1 else int(np.prod(x.shape[1:]))
+    y = np.zeros_like(x)
+    rp, col, val = _csr_args(g)
+    npt, pc = _netlist_args(net_ptr, pin_cell)
+    rc = lib().oracle_apply_cut(g.n, K, _p(rp), _p(col), _p(val), _p(np.ascontiguousarray(d, dtype=np.float64)),
+                                float(sigma), 0 if norm == "sym" else 1, int(npt.size - 1), _p(npt), _p(pc), int(cut),
+                                _p(x), _p(y))
+    if rc != 0:
+        raise MemoryError("oracle_apply_cut: out of memory")
+    return y
+
+
 def gift(g: Graph, d: np.ndarray, sig: np.ndarray, is_fixed: np.ndarray | None,
-         terms=DEFAULT_TERMS, norm: str = "sym", reimpose: bool = True) -> np.ndarray:
-    """GiFt (Eq. 15): sum_t alpha_t A~_{sigma_t}^{k_t} g, fixed rows reimposed."""
+         terms=DEFAULT_TERMS, norm: str = "sym", reimpose: bool = True, implicit=None) -> np.ndarray:
+    """GiFt (Eq. 15): sum_t alpha_t A~_{sigma_t}^{k_t} g, fixed rows reimposed.
+    implicit = (net_ptr, pin_cell, cut): g holds the nets of fewer than cut
+    pins and the larger nets' cliques are applied from the netlist."""
     x = np.ascontiguousarray(sig, dtype=np.float64)
     K = 1 if x.ndim == 1 else int(np.prod(x.shape[1:]))
     out = np.zeros_like(x)
@@ -283,9 +317,15 @@ def gift(g: Graph, d: np.ndarray, sig: np.ndarray, is_fixed: np.ndarray | None,
     al = np.array([t[2] for t in terms], dtype=np.float64)
     fx = np.ascontiguousarray(is_fixed if is_fixed is not None else np.zeros(g.n), dtype=np.uint8)
     rp, col, val = _csr_args(g)
-    rc = lib().oracle_filter(g.n, K, _p(rp), _p(col), _p(val), _p(np.ascontiguousarray(d, dtype=np.float64)),
-                             len(terms), _p(sg), _p(pw), _p(al), 0 if norm == "sym" else 1,
-                             1 if reimpose else 0, _p(fx), _p(x), _p(out))
+    dd = np.ascontiguousarray(d, dtype=np.float64)
+    if implicit is not None and implicit[2] > 0:
+        npt, pc = _netlist_args(implicit[0], implicit[1])
+        rc = lib().oracle_filter_cut(g.n, K, _p(rp), _p(col), _p(val), _p(dd), len(terms), _p(sg), _p(pw), _p(al),
+                                     0 if norm == "sym" else 1, 1 if reimpose else 0, _p(fx), int(npt.size - 1),
+                                     _p(npt), _p(pc), int(implicit[2]), _p(x), _p(out))
+    else:
+        rc = lib().oracle_filter(g.n, K, _p(rp), _p(col), _p(val), _p(dd), len(terms), _p(sg), _p(pw), _p(al),
+                                 0 if norm == "sym" else 1, 1 if reimpose else 0, _p(fx), _p(x), _p(out))
     if rc != 0:
         raise MemoryError("oracle_filter: out of memory")
     return out
@@ -305,16 +345,23 @@ def hpwl(net_ptr: np.ndarray, pin_cell: np.ndarray, xy: np.ndarray) -> np.ndarra
 
 
 def run(nl, sig: np.ndarray, fmt: str = "f64", terms=DEFAULT_TERMS, norm: str = "sym",
-        reimpose: bool = True):
+        reimpose: bool = True, cut: int = 0):
     """Whole path for a netlist: (graph, degrees, filtered signal).
 
     ``fmt`` rounds the weights as the storage format would before the degrees
-    are taken (degrees always over the stored weights)."""
-    g = build_graph(nl.num_cells, nl.net_ptr, nl.pin_cell)
+    are taken (degrees always over the stored weights).  ``cut`` > 0 applies
+    the cliques of the nets of at least cut pins from the netlist (the same
+    operator; for netlists whose full expansion is too large to form): the
+    graph then holds the other nets, their weights rounded, and the degrees
+    add the large nets' cliques exactly."""
+    g = build_graph(nl.num_cells, nl.net_ptr, nl.pin_cell, cut=cut)
     if fmt != "f64":
         g = stored(g, fmt)
     d = degrees(g)
-    out = gift(g, d, sig, nl.is_fixed, terms, norm, reimpose)
+    if cut > 0:
+        d = implicit_degrees(d, nl.net_ptr, nl.pin_cell, cut)
+    out = gift(g, d, sig, nl.is_fixed, terms, norm, reimpose,
+               implicit=(nl.net_ptr, nl.pin_cell, cut) if cut > 0 else None)
     return g, d, out
 
 

@@ -235,12 +235,87 @@ void oracle_apply(int32_t n, int32_t K, const int64_t *row_ptr, const int32_t *c
     }
 }
 
+/* Step 3 with the cliques of the nets of at least `cut` pins applied from the
+ * netlist instead of the CSR (which holds the other nets, oracle_build_cut):
+ * same operator as oracle_apply on the full expansion.  In the clique model
+ * each pin slot p of such a net e (M pins, weight w = 2/M) on cell i pairs
+ * with every slot q on another cell and adds w * xh_cell(q) to row i, where xh
+ * is the scaled signal (s x, or x in the random-walk form).  Summed over the
+ * slots q first, a slot of cell i adds w * (S_e - k xh_i), with S_e the sum of
+ * xh over all M slots and k the slots of e on cell i; cell i's k slots add k
+ * times that.  Rows take the CSR part (column order), then the nets in
+ * increasing order, then the self-loop.  Returns 0, or -1 on allocation
+ * failure. */
+int oracle_apply_cut(int32_t n, int32_t K, const int64_t *row_ptr, const int32_t *col, const double *val,
+                     const double *d, double sigma, int32_t norm, int32_t num_nets, const int64_t *net_ptr,
+                     const int32_t *pin_cell, int64_t cut, const double *x, double *y) {
+    size_t len = (size_t)n * (size_t)K;
+    double *xh = (double *)malloc((len > 0 ? len : 1) * sizeof(double));
+    double *acc = (double *)calloc(len > 0 ? len : 1, sizeof(double));
+    double *S = (double *)malloc((size_t)(K > 0 ? K : 1) * sizeof(double));
+    if (!xh || !acc || !S) {
+        free(xh);
+        free(acc);
+        free(S);
+        return -1;
+    }
+    for (int32_t j = 0; j < n; ++j) {
+        double sj = norm == 0 ? 1.0 / sqrt(d[j] + sigma) : 1.0;
+        for (int32_t c = 0; c < K; ++c) xh[(int64_t)j * K + c] = sj * x[(int64_t)j * K + c];
+    }
+    for (int32_t i = 0; i < n; ++i)
+        for (int64_t k = row_ptr[i]; k < row_ptr[i + 1]; ++k)
+            for (int32_t c = 0; c < K; ++c) acc[(int64_t)i * K + c] += val[k] * xh[(int64_t)col[k] * K + c];
+    for (int32_t e = 0; cut > 0 && e < num_nets; ++e) {
+        int64_t b = net_ptr[e], m = net_ptr[e + 1] - net_ptr[e];
+        if (m < 2 || m < cut) continue;
+        double w = 2.0 / (double)m;
+        for (int32_t c = 0; c < K; ++c) {
+            double t = 0.0;
+            for (int64_t p = 0; p < m; ++p) t += xh[(int64_t)pin_cell[b + p] * K + c];
+            S[c] = t;
+        }
+        int32_t *cells = (int32_t *)malloc((size_t)m * sizeof(int32_t));
+        if (!cells) {
+            free(xh);
+            free(acc);
+            free(S);
+            return -1;
+        }
+        memcpy(cells, pin_cell + b, (size_t)m * sizeof(int32_t));
+        qsort(cells, (size_t)m, sizeof(int32_t), cmp_i32);
+        for (int64_t r = 0; r < m;) {
+            int64_t k = 1;
+            while (r + k < m && cells[r + k] == cells[r]) ++k;
+            int64_t i = cells[r];
+            for (int32_t c = 0; c < K; ++c)
+                acc[i * K + c] += (double)k * w * (S[c] - (double)k * xh[i * K + c]);
+            r += k;
+        }
+        free(cells);
+    }
+    for (int32_t i = 0; i < n; ++i) {
+        double si = norm == 0 ? 1.0 / sqrt(d[i] + sigma) : 1.0;
+        for (int32_t c = 0; c < K; ++c) {
+            double a = acc[(int64_t)i * K + c] + sigma * xh[(int64_t)i * K + c];
+            y[(int64_t)i * K + c] = norm == 0 ? si * a : a / (d[i] + sigma);
+        }
+    }
+    free(xh);
+    free(acc);
+    free(S);
+    return 0;
+}
+
 /* Steps 4-5: out = sum_t alpha_t A~_{sigma_t}^{power_t} g, then fixed rows := g.
- * Each term starts again from g (no sharing between terms). */
-int oracle_filter(int32_t n, int32_t K, const int64_t *row_ptr, const int32_t *col, const double *val,
-                  const double *d, int32_t num_terms, const double *sigma, const int32_t *power,
-                  const double *alpha, int32_t norm, int32_t reimpose, const uint8_t *is_fixed,
-                  const double *g, double *out) {
+ * Each term starts again from g (no sharing between terms).  cut > 0: the
+ * cliques of the nets of at least cut pins come from the netlist
+ * (oracle_apply_cut), the rest from the CSR. */
+static int filter_terms(int32_t n, int32_t K, const int64_t *row_ptr, const int32_t *col, const double *val,
+                        const double *d, int32_t num_terms, const double *sigma, const int32_t *power,
+                        const double *alpha, int32_t norm, int32_t reimpose, const uint8_t *is_fixed,
+                        int32_t num_nets, const int64_t *net_ptr, const int32_t *pin_cell, int64_t cut,
+                        const double *g, double *out) {
     size_t len = (size_t)n * (size_t)K;
     double *v = (double *)malloc(len * sizeof(double));
     double *t = (double *)malloc(len * sizeof(double));
@@ -253,7 +328,16 @@ int oracle_filter(int32_t n, int32_t K, const int64_t *row_ptr, const int32_t *c
     for (int32_t term = 0; term < num_terms; ++term) {
         memcpy(v, g, len * sizeof(double));
         for (int32_t p = 0; p < power[term]; ++p) {
-            oracle_apply(n, K, row_ptr, col, val, d, sigma[term], norm, v, t);
+            if (cut > 0) {
+                if (oracle_apply_cut(n, K, row_ptr, col, val, d, sigma[term], norm, num_nets, net_ptr, pin_cell, cut,
+                                     v, t) != 0) {
+                    free(v);
+                    free(t);
+                    return -1;
+                }
+            } else {
+                oracle_apply(n, K, row_ptr, col, val, d, sigma[term], norm, v, t);
+            }
             double *sw = v;
             v = t;
             t = sw;
@@ -268,6 +352,23 @@ int oracle_filter(int32_t n, int32_t K, const int64_t *row_ptr, const int32_t *c
     free(v);
     free(t);
     return 0;
+}
+
+int oracle_filter(int32_t n, int32_t K, const int64_t *row_ptr, const int32_t *col, const double *val,
+                  const double *d, int32_t num_terms, const double *sigma, const int32_t *power,
+                  const double *alpha, int32_t norm, int32_t reimpose, const uint8_t *is_fixed,
+                  const double *g, double *out) {
+    return filter_terms(n, K, row_ptr, col, val, d, num_terms, sigma, power, alpha, norm, reimpose, is_fixed, 0, NULL,
+                        NULL, 0, g, out);
+}
+
+int oracle_filter_cut(int32_t n, int32_t K, const int64_t *row_ptr, const int32_t *col, const double *val,
+                      const double *d, int32_t num_terms, const double *sigma, const int32_t *power,
+                      const double *alpha, int32_t norm, int32_t reimpose, const uint8_t *is_fixed,
+                      int32_t num_nets, const int64_t *net_ptr, const int32_t *pin_cell, int64_t cut,
+                      const double *g, double *out) {
+    return filter_terms(n, K, row_ptr, col, val, d, num_terms, sigma, power, alpha, norm, reimpose, is_fixed,
+                        num_nets, net_ptr, pin_cell, cut, g, out);
 }
 
 /* Step 6: HPWL of each of S signals; xy is [N][S][2]. */

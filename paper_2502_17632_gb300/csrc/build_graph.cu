@@ -1242,6 +1242,9 @@ void build_graph_impl(gift_ctx *ctx, const gift_netlist *nl, const gift_build_op
         check_launch("k_copy_rows");
     }
     g->device_bytes += (int64_t)(sizeof(int64_t) * (N + 1) + (4 + wsz) * g->stored + 16 * N + 8 * (E + 1) + 4 * P + N);
+    // rows long enough for compensated sums: the length order finds them
+    // (a stored row holds at most max_row_nnz entries plus padding)
+    if ((int64_t)g->max_row_nnz + (g->stored - g->nnz) >= kCompRows) ensure_sorted(ctx, g, false, st, true);
     *out = g;
     owner.g = nullptr;
 }

@@ -375,6 +375,11 @@ struct Plan {
     // compensated sums: every launch uses warp-row direct kernels with
     // Neumaier summation (the shapes' lane counts are kept)
     bool comp = false;
+    // only the rows of at least kCompRows entries get compensated sums: the
+    // direct and row-group launches leave them out and a warp-row launch
+    // with Neumaier sums over those rows (g->n_long slots of the length
+    // order) follows each
+    bool comp_long = false;
     // implicit cliques: net sums of the current chain group, [nets][2][K]
     float *S = nullptr;
 };
@@ -794,6 +799,9 @@ int run_sweeps(gift_ctx *ctx, const Plan &p, ShapeSet ss, cudaStream_t st, std::
                         1, std::min<int64_t>(want, (int64_t)ctx->num_sms * occupancy_blocks(fn, threads)));
                     params = {&a};
                 }
+                // long rows with compensated sums: left out of this launch, summed by the next
+                const bool split_long = p.comp_long && (shape.family == 0 || shape.family == 4) && !p.comp;
+                if (split_long) a.skip_above = kCompRows;
                 LaunchTimer lt(ctx, st, "filter.sweep", bytes);
                 TimedLaunch tl{gr.planned, nullptr, nullptr};
                 if (timed) {
@@ -802,6 +810,25 @@ int run_sweeps(gift_ctx *ctx, const Plan &p, ShapeSet ss, cudaStream_t st, std::
                     GIFT_CUDA(cudaEventRecord(tl.e0, st));
                 }
                 GIFT_CUDA(cudaLaunchKernel(fn, dim3(grid), dim3(threads), params.data(), smem, st));
+                if (split_long) {
+                    SweepArgs b = a;
+                    b.skip_above = 0;
+                    b.row_ptr = g->row_ptr;
+                    b.col = g->col;
+                    b.val = g->val;
+                    b.slot_csr = 0;
+                    b.order = g->srt.perm;
+                    b.n_slots = g->n_long;
+                    const int lcw = shape.family == 4 ? cw : std::min(cw, 8);
+                    const int lvec = shape.family == 4 ? sv : p.vec;
+                    const void *lf = sweep_dr_kernel(g->weight_dtype, lvec, lcw, 4, nc, first, true, true);
+                    GIFT_REQUIRE(lf != nullptr, "gift_filter: no compensated warp-row kernel for this shape");
+                    const int lgrid = (int)std::max<int64_t>(
+                        1, std::min<int64_t>(ceil_div(g->n_long, kSweepThreads / 32),
+                                             (int64_t)ctx->num_sms * occupancy_blocks(lf, kSweepThreads)));
+                    void *lparams[] = {&b};
+                    GIFT_CUDA(cudaLaunchKernel(lf, dim3(lgrid), dim3(kSweepThreads), lparams, 0, st));
+                }
                 if (timed) {
                     GIFT_CUDA(cudaEventRecord(tl.e1, st));
                     timed->push_back(tl);
@@ -1085,7 +1112,7 @@ void filter_impl(gift_ctx *ctx, const gift_graph *cg, const gift_filter_spec *sp
     GIFT_REQUIRE(spec->num_terms >= 1 && spec->num_terms <= GIFT_MAX_TERMS, "gift_filter: num_terms out of range");
     GIFT_REQUIRE(spec->norm == GIFT_NORM_SYM || spec->norm == GIFT_NORM_RW, "gift_filter: unknown norm");
     GIFT_REQUIRE(spec->reimpose_fixed == 0 || spec->reimpose_fixed == 1, "gift_filter: reimpose_fixed is 0 or 1");
-    GIFT_REQUIRE(spec->compensated == 0 || spec->compensated == 1, "gift_filter: compensated is 0 or 1");
+    GIFT_REQUIRE(spec->compensated >= 0 && spec->compensated <= 2, "gift_filter: compensated is 0, 1 or 2");
     const bool split_sched = spec->schedule >= 10000;
     const int sched = split_sched ? spec->schedule - 10000 : spec->schedule;
     GIFT_REQUIRE(spec->schedule == 0 || (sched >= 4 && valid_shape(shape_from_schedule(sched))),
@@ -1101,6 +1128,7 @@ void filter_impl(gift_ctx *ctx, const gift_graph *cg, const gift_filter_spec *sp
     p.K = K;
     p.reimpose = spec->reimpose_fixed;
     p.comp = spec->compensated == 1;
+    p.comp_long = spec->compensated == 0 && g->n_long > 0;
     plan_chains(spec, p, "gift_filter");
 
     // ---- signal buffers
@@ -1241,7 +1269,8 @@ void filter_on_scratch(gift_ctx *ctx, const gift_graph *g, const gift_filter_spe
     GIFT_REQUIRE(spec->norm == GIFT_NORM_SYM || spec->norm == GIFT_NORM_RW, "gift_filter_noalloc: unknown norm");
     GIFT_REQUIRE(spec->reimpose_fixed == 0 || spec->reimpose_fixed == 1,
                  "gift_filter_noalloc: reimpose_fixed is 0 or 1");
-    GIFT_REQUIRE(spec->compensated == 0 || spec->compensated == 1, "gift_filter_noalloc: compensated is 0 or 1");
+    GIFT_REQUIRE(spec->compensated >= 0 && spec->compensated <= 2,
+                 "gift_filter_noalloc: compensated is 0, 1 or 2");
     const int64_t N = g->n;
     const int32_t K = 2 * S;
     const size_t sig_bytes = sizeof(float) * (size_t)N * K;
@@ -1251,6 +1280,7 @@ void filter_on_scratch(gift_ctx *ctx, const gift_graph *g, const gift_filter_spe
     p.K = K;
     p.reimpose = spec->reimpose_fixed;
     p.comp = spec->compensated == 1;
+    p.comp_long = spec->compensated == 0 && g->n_long > 0;
     plan_chains(spec, p, "gift_filter_noalloc");
     GIFT_REQUIRE(filter_scratch_bytes(g, spec, S) <= scratch_bytes,
                  "gift_filter_noalloc: graph and signal need more scratch than the fixed no-alloc area");
@@ -1358,7 +1388,7 @@ void filter_batch(gift_ctx *ctx, const std::vector<BatchItem> &items, const gift
     GIFT_REQUIRE(S >= 1, "filter_batch: num_signals must be >= 1");
     GIFT_REQUIRE(spec->num_terms >= 1 && spec->num_terms <= GIFT_MAX_TERMS, "filter_batch: num_terms out of range");
     GIFT_REQUIRE(spec->norm == GIFT_NORM_SYM || spec->norm == GIFT_NORM_RW, "filter_batch: unknown norm");
-    GIFT_REQUIRE(spec->compensated == 0, "filter_batch: compensated sums are not batched");
+    GIFT_REQUIRE(spec->compensated == 0 || spec->compensated == 2, "filter_batch: compensated sums are not batched");
     GIFT_REQUIRE(batchable_shape(schedule), "filter_batch: the shape must be direct row groups in natural order");
     const Shape shape = shape_from_schedule(schedule);
     const int K = 2 * S;
@@ -1368,6 +1398,8 @@ void filter_batch(gift_ctx *ctx, const std::vector<BatchItem> &items, const gift
     for (const BatchItem &it : items) {
         GIFT_REQUIRE(it.g && it.din && it.dout, "filter_batch: NULL graph or signal");
         GIFT_REQUIRE(it.g->imp_nets == 0, "filter_batch: graphs with implicit cliques are not batched");
+        GIFT_REQUIRE(it.g->n_long == 0 || spec->compensated == 2,
+                     "filter_batch: graphs with rows for compensated sums are not batched");
         al16 = al16 && reinterpret_cast<uintptr_t>(it.din) % 16 == 0 && reinterpret_cast<uintptr_t>(it.dout) % 16 == 0;
     }
     for (size_t i = 0; i < items.size(); ++i) {

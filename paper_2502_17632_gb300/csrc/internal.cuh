@@ -200,6 +200,11 @@ __device__ __forceinline__ float scale_value(double d, double sigma, int norm) {
 
 constexpr int kWeightTable = 4096;  // 2/M from a table for M <= this
 
+// Rows of at least this many stored entries are summed with compensated FP32
+// sums (Neumaier) by default: the worst-case error of a plain FP32 sum of n
+// terms grows with n u, and such rows are the hubs of high-fanout nets.
+constexpr int64_t kCompRows = 1024;
+
 }  // namespace gift
 
 // ---------------------------------------------------------------- graph
@@ -255,6 +260,9 @@ struct gift_graph {
         int32_t *col = nullptr;
         void *val = nullptr;
     } srt;
+    // rows of at least kCompRows stored entries: the first n_long slots of
+    // srt.perm (the build makes the order when there are any; 0: none)
+    int64_t n_long = 0;
     // sliced-ELL execution format (built on first use by a sliced-ELL schedule)
     struct Sell {
         int rps = 0;              // rows per slice (0: not built)
@@ -281,8 +289,9 @@ void ensure_row_order(gift_ctx *ctx, gift_graph *g, cudaStream_t st);
 void build_sell(gift_ctx *ctx, gift_graph *g, int rps, cudaStream_t st);
 void release_sell(gift_graph *g, cudaStream_t st);
 // builds g->srt's row order (and, with copy, the CSR copy in that order) if
-// absent (caller holds g->mu)
-void ensure_sorted(gift_ctx *ctx, gift_graph *g, bool copy, cudaStream_t st);
+// absent (caller holds g->mu); want_long: also count the rows of at least
+// kCompRows entries into g->n_long (a host wait)
+void ensure_sorted(gift_ctx *ctx, gift_graph *g, bool copy, cudaStream_t st, bool want_long = false);
 void release_sorted(gift_graph *g, cudaStream_t st);
 // filter.cu
 // mirror (optional): the last sweep also stores the output there -- mapped

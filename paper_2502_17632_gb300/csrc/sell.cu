@@ -104,6 +104,9 @@ __global__ void k_sell_fill(int64_t nslices, int rps, const int64_t *__restrict_
 // whatever slot it takes.
 constexpr int kSortKeys = 256;
 constexpr int kSortChunk = 4096;
+// keys 0 .. kLongKeys - 1 hold exactly the rows of at least kCompRows entries
+constexpr int kLongKeys = kSortKeys - (192 + (int)((kCompRows - 192) >> 6));
+static_assert((kCompRows - 192) % 64 == 0 && kCompRows >= 192, "kCompRows on a bucket boundary");
 
 __device__ __forceinline__ int len_key(int64_t len) {
     const int64_t over = len < 192 ? 0 : (len - 192) >> 6;
@@ -200,7 +203,7 @@ __global__ void k_copy_sorted(int64_t n, const int64_t *__restrict__ row_ptr, co
 
 }  // namespace
 
-void ensure_sorted(gift_ctx *ctx, gift_graph *g, bool copy, cudaStream_t st) {
+void ensure_sorted(gift_ctx *ctx, gift_graph *g, bool copy, cudaStream_t st, bool want_long) {
     const int64_t N = g->n;
     const size_t wsz = g->weight_dtype == GIFT_WEIGHT_F32 ? 4 : 2;
     if (!g->srt.perm) {
@@ -215,10 +218,15 @@ void ensure_sorted(gift_ctx *ctx, gift_graph *g, bool copy, cudaStream_t st) {
             k_sort_count<<<(unsigned)nblocks, 256, 0, st>>>(N, g->row_ptr, nblocks, counts.as<int32_t>());
             check_launch("k_sort_count");
             exclusive_scan(ctx, counts.as<int32_t>(), offs.as<int64_t>(), kSortKeys * nblocks, st);
+            if (want_long) {  // rows in the keys of the long rows
+                GIFT_CUDA(cudaMemcpyAsync(&g->n_long, offs.as<int64_t>() + (int64_t)kLongKeys * nblocks,
+                                          sizeof(int64_t), cudaMemcpyDeviceToHost, st));
+            }
             k_sort_place<<<(unsigned)nblocks, 256, 0, st>>>(N, g->row_ptr, nblocks, offs.as<int64_t>(),
                                                             perm.as<int32_t>(), len.as<int64_t>());
             check_launch("k_sort_place");
             exclusive_scan(ctx, len.as<int64_t>(), rp.as<int64_t>(), N, st);
+            if (want_long) GIFT_CUDA(cudaStreamSynchronize(st));
         }
         g->srt.perm = perm.as<int32_t>();
         g->srt.rp = rp.as<int64_t>();

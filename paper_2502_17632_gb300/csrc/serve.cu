@@ -230,7 +230,7 @@ void gift_server::run(Request &r, int w) {
     spec.schedule = schedule;
     r.g_out = static_cast<float *>(pinned.take(sig_bytes));
     float *mirror = host_mirror(r.g_out, sig_bytes);  // the last sweep stores the result into it
-    if (batching && g->imp_nets == 0) {
+    if (batching && g->imp_nets == 0 && (g->n_long == 0 || spec.compensated == 2)) {
         // join the next shared filter batch and wait for it
         FilterJob job;
         job.g = g;
@@ -441,7 +441,7 @@ gift_status gift_serve_create(const gift_serve_opts *opts, gift_server **out) {
             srv->opts.hbm_budget_bytes = (int64_t)(fr / 2);
         }
         srv->schedule = o.spec.schedule != 0 ? o.spec.schedule : kServeSchedule;
-        srv->batching = o.separate_filters == 0 && o.spec.compensated == 0 && batchable_shape(srv->schedule);
+        srv->batching = o.separate_filters == 0 && o.spec.compensated != 1 && batchable_shape(srv->schedule);
         srv->t_create = Clock::now();
         try {
             for (int w = 0; w < o.max_slots; ++w) {

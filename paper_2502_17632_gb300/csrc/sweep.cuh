@@ -71,6 +71,8 @@ struct SweepArgs {
     int32_t slot_csr;     // 1: row_ptr / col / val hold the rows in slot order (row_ptr[slot]);
                           // 0: they are indexed by row
     int32_t weight_dtype; // GIFT_WEIGHT_* of val (read at run time by the multi-graph sweep)
+    int64_t skip_above;   // > 0: rows of at least this many entries are left out (another
+                          // launch sums them with compensation); 0: every row
     ImplicitArgs imp;
 };
 
@@ -236,6 +238,8 @@ __global__ void __launch_bounds__(kSweepThreads) k_sweep(const SweepArgs a) {
             kb = __ldg(a.row_ptr + row);
             ke = __ldg(a.row_ptr + row + 1);
         }
+        const bool skip = active && a.skip_above > 0 && ke - kb >= a.skip_above;
+        if (skip) kb = ke = 0;  // another launch sums this long row
         for (int64_t c0 = kb; c0 < ke; c0 += G) {
             const int64_t k = c0 + gl;
             int32_t jl = 0;
@@ -287,7 +291,7 @@ __global__ void __launch_bounds__(kSweepThreads) k_sweep(const SweepArgs a) {
 #pragma unroll
                 for (int v = 0; v < VEC; ++v) acc[c][v] += __shfl_xor_sync(0xffffffffu, acc[c][v], o, G);
 
-        if (!active || ns != 0) continue;
+        if (!active || skip || ns != 0) continue;
         const int64_t off = row * a.K + colo;
         float out[VEC];
 #pragma unroll

@@ -113,6 +113,10 @@ __device__ __forceinline__ void dr_row(const SweepArgs &a, int64_t row, int64_t 
     if (row >= 0) {
         kb = __ldg(a.row_ptr + ci);
         ke = __ldg(a.row_ptr + ci + 1);
+        if (a.skip_above > 0 && ke - kb >= a.skip_above) {  // another launch sums this long row
+            row = -1;
+            kb = ke = 0;
+        }
     }
     // Warp rows (rows of hundreds to thousands of nonzeros): the next
     // step's (col, val) are loaded while this step's rows are gathered,

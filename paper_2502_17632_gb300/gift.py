@@ -249,7 +249,8 @@ def gift_filter_spec_default() -> gift_filter_spec:
 
 
 def make_spec(terms=None, norm: int = GIFT_NORM_SYM, reimpose: bool = True, schedule: int = 0,
-              compensated: bool = False) -> gift_filter_spec:
+              compensated: int = 0) -> gift_filter_spec:
+    """compensated: 0 (or False) long rows only, 1 (or True) every row, 2 none."""
     s = gift_filter_spec_default()
     if terms is not None:
         s.num_terms = len(terms)
@@ -258,7 +259,7 @@ def make_spec(terms=None, norm: int = GIFT_NORM_SYM, reimpose: bool = True, sche
     s.norm = norm
     s.reimpose_fixed = 1 if reimpose else 0
     s.schedule = schedule
-    s.compensated = 1 if compensated else 0
+    s.compensated = int(compensated)
     return s
 
 

@@ -1,15 +1,14 @@
 """The high-fanout workload at full size (1.3M cells, Zipf(2.2) pin counts
 capped at 2,000: 828M expanded nonzeros, rows of up to 10,600), expanded and
-with implicit cliques, against values computed from the netlist alone.
+with implicit cliques, against the FP64 oracle.
 
-The FP64 oracle cannot expand this netlist in test time, so:
-- one sweep (A~_2 x) is checked on sampled rows -- the longest rows and a
-  seeded random sample -- each computed by its definition in FP64 on the
-  CPU (row i sums, over its pins' nets e, (2/M_e) s_q x_q over the net's pins
-  q on other cells, s = (d + sigma)^-1/2 with the exact degrees of the
-  netlist);
-- the filter's fixed point: A~_4^4 (d + 4)^1/2 = (d + 4)^1/2 (Theorem 1);
-- the filter operator without reimposed cells is symmetric.
+The oracle applies the cliques of the nets of 8 or more pins from the netlist
+(oracle.run with cut = 8: the same operator as the full expansion, whose 828M
+FP64 pairs it could not sort in test time) and expands the rest; it filters
+signal 0 of the GPU run, every cell, and the GPU's whole filter output (all
+three terms, fixed cells) is compared element by element at the FP32 bar.
+Also checked: the filter's fixed point A~_4^4 (d + 4)^1/2 = (d + 4)^1/2
+(Theorem 1) and the symmetry of the filter operator without reimposed cells.
 """
 import numpy as np
 import pytest
@@ -27,18 +26,17 @@ def dev(a):
     return torch.from_numpy(np.ascontiguousarray(a)).cuda()
 
 
+ORACLE_CUT = 8  # nets of at least this many pins: cliques applied from the netlist by the oracle
+
+
 @pytest.fixture(scope="module")
 def fanout():
-    nl, _ = synth.workload("fanout-1.3m")
+    nl, g = synth.workload("fanout-1.3m")
     # exact degrees of the full expansion: every net's clique, from the netlist
     d = oracle.implicit_degrees(np.zeros(nl.num_cells), nl.net_ptr, nl.pin_cell, cut=2)
-    order = np.argsort(nl.pin_cell, kind="stable")
-    pin_net = np.repeat(np.arange(nl.num_nets, dtype=np.int64), np.diff(nl.net_ptr))
-    inc_ptr = np.concatenate([[0], np.cumsum(np.bincount(nl.pin_cell, minlength=nl.num_cells))]).astype(np.int64)
-    inc_net = pin_net[order]
-    u = synth.uniform(2024, synth.T_MISC, np.arange(200, dtype=np.uint64))
-    rows = np.unique(np.concatenate([np.argsort(-d)[:40], (u * nl.num_cells).astype(np.int64)]))
-    return nl, d, inc_ptr, inc_net, rows
+    # the FP64 filter of signal 0 (x and y of every cell)
+    _, _, ref = oracle.run(nl, np.ascontiguousarray(g[:, 0, :]), cut=ORACLE_CUT)
+    return nl, d, g, ref
 
 
 @pytest.fixture(scope="module")
@@ -46,20 +44,6 @@ def ctx():
     c = gift.gift_ctx_create(0)
     yield c
     gift.gift_ctx_destroy(c)
-
-
-def rows_by_definition(nl, d, inc_ptr, inc_net, sigma, x, rows):
-    s = 1.0 / np.sqrt(d + sigma)
-    out = np.empty((len(rows), x.shape[1]))
-    for r, i in enumerate(rows):
-        acc = np.zeros(x.shape[1])
-        for e in inc_net[inc_ptr[i]:inc_ptr[i + 1]]:  # once per pin of cell i in net e
-            pins = nl.pin_cell[nl.net_ptr[e]:nl.net_ptr[e + 1]]
-            q = pins[pins != i]
-            acc += (2.0 / len(pins)) * (s[q, None] * x[q]).sum(axis=0)
-        acc += sigma * s[i] * x[i]
-        out[r] = s[i] * acc
-    return out
 
 
 def run(ctx, nl, cut, g, spec):
@@ -79,17 +63,53 @@ def run(ctx, nl, cut, g, spec):
 CASES = [(0, False), (0, True), (8, False), (64, True)]  # (implicit_min_pins, compensated)
 
 
-@pytest.mark.parametrize("cut,comp", CASES)
-def test_one_sweep_on_sampled_rows(ctx, fanout, cut, comp):
-    nl, d, inc_ptr, inc_net, rows = fanout
-    g = synth.make_signals(nl, 2, 5)
-    spec = gift.make_spec(terms=((2.0, 1, 1.0),), reimpose=False, compensated=comp)
-    got = run(ctx, nl, cut, g, spec).reshape(nl.num_cells, -1)
-    x = g.reshape(nl.num_cells, -1).astype(np.float64)
-    ref = rows_by_definition(nl, d, inc_ptr, inc_net, 2.0, x, rows)
-    floor = 1e-3 * np.abs(x).max()
-    err = np.abs(got[rows] - ref) / np.maximum(np.abs(ref), floor)
+@pytest.mark.parametrize("cut,comp", CASES + [(2, False)])
+def test_whole_filter_against_oracle(ctx, fanout, cut, comp):
+    """The paper's filter on all 4 signals, expanded or with implicit
+    cliques, plain or compensated sums: signal 0 of every cell against the
+    FP64 oracle, fixed cells bit-exact."""
+    nl, _, g, ref = fanout
+    got = run(ctx, nl, cut, g, gift.make_spec(compensated=comp))
+    x0 = g[:, 0, :].astype(np.float64)
+    floor = 1e-3 * np.abs(x0).max()
+    err = np.abs(got[:, 0, :].astype(np.float64) - ref) / np.maximum(np.abs(ref), floor)
     assert err.max() <= RTOL
+    fx = nl.is_fixed.astype(bool)
+    np.testing.assert_array_equal(got[fx], g[fx])
+
+
+@pytest.fixture(scope="module")
+def fanout_bf16(fanout):
+    """The oracle with the expanded nets' weights rounded to bfloat16 (the
+    implicit cliques keep 2/M), degrees over those weights."""
+    nl, _, g, _ = fanout
+    return oracle.run(nl, np.ascontiguousarray(g[:, 0, :]), fmt="bf16", cut=ORACLE_CUT)[2]
+
+
+@pytest.mark.parametrize("cut", [0, ORACLE_CUT])
+def test_bf16_weights_against_oracle(ctx, fanout, fanout_bf16, cut):
+    """BF16 weights: with the oracle's cut the GPU computes the same rounded
+    operator (FP32 bar); fully expanded, every weight is rounded, and the
+    result stays within the derived bound 8u + the FP32 bar of the exact
+    filter (u = 2^-8)."""
+    nl, _, g, ref = fanout
+    h = gift.gift_build_graph(ctx, nl.num_cells, dev(nl.net_ptr), dev(nl.pin_cell), dev(nl.is_fixed),
+                              gift.GIFT_WEIGHT_BF16, implicit_min_pins=cut)
+    try:
+        gi = dev(g)
+        go = torch.empty_like(gi)
+        gift.gift_filter(ctx, h, gi, go)
+        torch.cuda.synchronize()
+        got = go.cpu().numpy()[:, 0, :].astype(np.float64)
+    finally:
+        gift.gift_graph_free(h)
+    floor = 1e-3 * np.abs(g[:, 0, :]).max()
+    if cut == ORACLE_CUT:
+        err = np.abs(got - fanout_bf16) / np.maximum(np.abs(fanout_bf16), floor)
+        assert err.max() <= RTOL
+    else:
+        err = np.abs(got - ref) / np.maximum(np.abs(ref), floor)
+        assert err.max() <= 8 * 2.0 ** -8 + RTOL
 
 
 @pytest.mark.parametrize("cut,comp", CASES)

@@ -271,6 +271,30 @@ def test_row_order_does_not_change_sums(ctx, name, S):
     assert rel_err(pre, ref.reshape(g.shape), g).max() <= RTOL
 
 
+@pytest.mark.parametrize("S", [2, 8])
+@pytest.mark.parametrize("schedule", [4244, 4844, 5044, 4224, 408, 14244])
+def test_long_rows_compensated_by_default(ctx, S, schedule):
+    """The default spec sums the rows of at least 1024 entries (the hub row of
+    17,600 here) with Neumaier compensation and every other row plainly: on
+    one product, the hub row equals the all-rows compensated result and the
+    other rows the plain result, bit for bit; and the default filter meets
+    the FP32 bar against the oracle."""
+    nl = NETLISTS["global-tier-row"]
+    g = synth.make_signals(nl, S, 31)
+    one = ((2.0, 1, 1.0),)
+    auto = run_filter(ctx, nl, g, spec=gift.make_spec(terms=one, schedule=schedule, compensated=0))
+    comp = run_filter(ctx, nl, g, spec=gift.make_spec(terms=one, schedule=schedule, compensated=1))
+    plain = run_filter(ctx, nl, g, spec=gift.make_spec(terms=one, schedule=schedule, compensated=2))
+    rp = oracle.build_graph(nl.num_cells, nl.net_ptr, nl.pin_cell).row_ptr
+    long_rows = np.diff(rp) >= 1024
+    assert long_rows.sum() == 1 and long_rows[0]
+    np.testing.assert_array_equal(auto[long_rows], comp[long_rows])
+    np.testing.assert_array_equal(auto[~long_rows], plain[~long_rows])
+    got = run_filter(ctx, nl, g, spec=gift.make_spec(schedule=schedule))
+    _, _, ref = oracle.run(nl, g.reshape(nl.num_cells, -1))
+    assert rel_err(got, ref.reshape(g.shape), g).max() <= RTOL
+
+
 @pytest.mark.parametrize("name", sorted(NETLISTS))
 @pytest.mark.parametrize("schedule", [0, 4644, 4424, 408])
 def test_compensated_sums(ctx, name, schedule):
@@ -363,10 +387,11 @@ def test_invalid_filter_args(ctx):
             with pytest.raises(gift.GiftError) as e:
                 gift.gift_filter(ctx, h, g, out, gift.make_spec(terms=terms))
             assert e.value.status == gift.GIFT_ERR_INVALID
-        spec = gift.make_spec()
-        spec.compensated = 2
-        with pytest.raises(gift.GiftError):
-            gift.gift_filter(ctx, h, g, out, spec)
+        for bad in (3, -1):
+            spec = gift.make_spec()
+            spec.compensated = bad
+            with pytest.raises(gift.GiftError):
+                gift.gift_filter(ctx, h, g, out, spec)
         spec = gift.make_spec()
         spec.num_terms = 9
         with pytest.raises(gift.GiftError):

@@ -41,6 +41,15 @@ C_MUTANTS = {
     "implicit_ignores_repeats": [("d[cells[r]] += ((double)k * w) * (double)(m - k);",
                                   "d[cells[r]] += ((double)k * w) * (double)(m - 1);", 0)],
     "implicit_cut_off_by_one": [("if (m < 2 || m < cut) continue;", "if (m < 2 || m <= cut) continue;", 0)],
+    # cliques applied from the netlist (same operator as the expansion)
+    "implicit_apply_weight": [("double w = 2.0 / (double)m;", "double w = 1.0 / (double)(m - 1);", 2)],
+    "implicit_apply_ignores_repeats": [("(S[c] - (double)k * xh[i * K + c])", "(S[c] - xh[i * K + c])", 0)],
+    "implicit_apply_once_per_cell": [("acc[i * K + c] += (double)k * w *", "acc[i * K + c] += w *", 0)],
+    "implicit_apply_unscaled": [("double sj = norm == 0 ? 1.0 / sqrt(d[j] + sigma) : 1.0;", "double sj = 1.0;", 0)],
+    "implicit_apply_cut_off_by_one": [("if (m < 2 || m < cut) continue;", "if (m < 2 || m <= cut) continue;", 1)],
+    "implicit_apply_self_loop_dropped": [("double a = acc[(int64_t)i * K + c] + sigma * xh[(int64_t)i * K + c];",
+                                         "double a = acc[(int64_t)i * K + c];", 0)],
+    "implicit_apply_last_pin_dropped": [("for (int64_t p = 0; p < m; ++p) t += xh", "for (int64_t p = 0; p < m - 1; ++p) t += xh", 0)],
     # degrees (Sec. 2.1)
     "degree_drops_first_entry": [("for (int64_t k = row_ptr[i]; k < row_ptr[i + 1]; ++k) s += val[k];",
                                   "for (int64_t k = row_ptr[i] + 1; k < row_ptr[i + 1]; ++k) s += val[k];", 0)],
@@ -91,16 +100,24 @@ PY_MUTANTS = {
     "density_overflow_whole_bin": [("acc += c - tq", "acc += c")],
     "density_overflow_unclamped": [("if c > tq:\n                acc += c - tq", "if True:\n                acc += c - tq")],
     # storage format applied after the degrees
-    "degrees_before_rounding": [("    g = build_graph(nl.num_cells, nl.net_ptr, nl.pin_cell)\n    if fmt != \"f64\":\n"
+    "degrees_before_rounding": [("    g = build_graph(nl.num_cells, nl.net_ptr, nl.pin_cell, cut=cut)\n    if fmt != \"f64\":\n"
                                  "        g = stored(g, fmt)\n    d = degrees(g)",
-                                 "    g = build_graph(nl.num_cells, nl.net_ptr, nl.pin_cell)\n    d = degrees(g)\n"
+                                 "    g = build_graph(nl.num_cells, nl.net_ptr, nl.pin_cell, cut=cut)\n    d = degrees(g)\n"
                                  "    if fmt != \"f64\":\n        g = stored(g, fmt)")],
     "implicit_drops_expanded_part": [("out = np.array(d, dtype=np.float64, copy=True)",
                                       "out = np.zeros(np.shape(d), dtype=np.float64)")],
+    "run_cut_degrees_of_small_nets_only": [("        d = implicit_degrees(d, nl.net_ptr, nl.pin_cell, cut)\n",
+                                            "        d = d\n")],
+    "run_cut_ignores_large_nets": [("implicit=(nl.net_ptr, nl.pin_cell, cut) if cut > 0 else None)", "implicit=None)")],
     # the wrappers' arguments to the C library
     "apply_norm_flag_swapped": [("float(sigma), 0 if norm == \"sym\" else 1, _p(x), _p(y))",
                                  "float(sigma), 1 if norm == \"sym\" else 0, _p(x), _p(y))")],
-    "filter_norm_flag_swapped": [("_p(al), 0 if norm == \"sym\" else 1,", "_p(al), 1 if norm == \"sym\" else 0,")],
+    "filter_norm_flag_swapped": [("0 if norm == \"sym\" else 1, 1 if reimpose else 0, _p(fx), _p(x), _p(out))",
+                                  "1 if norm == \"sym\" else 0, 1 if reimpose else 0, _p(fx), _p(x), _p(out))")],
+    "filter_cut_norm_flag_swapped": [("0 if norm == \"sym\" else 1, 1 if reimpose else 0, _p(fx), int(npt.size - 1),",
+                                      "1 if norm == \"sym\" else 0, 1 if reimpose else 0, _p(fx), int(npt.size - 1),")],
+    "apply_cut_norm_flag_swapped": [("float(sigma), 0 if norm == \"sym\" else 1, int(npt.size - 1)",
+                                     "float(sigma), 1 if norm == \"sym\" else 0, int(npt.size - 1)")],
     "rounding_format_ignored": [("_p(out), FMT[fmt])", "_p(out), FMT[\"f32\"])")],
     "stored_weights_unrounded": [("return Graph(g.n, g.row_ptr, g.col, round_values(g.val, fmt))",
                                   "return Graph(g.n, g.row_ptr, g.col, np.array(g.val, copy=True))")],

@@ -410,6 +410,47 @@ def test_implicit_degree_of_one_net_by_pair_count(M, k):
     assert G.nnz == 0
 
 
+@pytest.mark.parametrize("cut", [2, 3, 5, 50])
+@pytest.mark.parametrize("seed", [1, 2, 3])
+def test_implicit_apply_matches_dense_brute_force(seed, cut):
+    """The product with the large nets' cliques applied from the netlist
+    equals the independent dense construction's product (repeated cells
+    included), in both normalisations and for two sigmas, and so does the
+    whole filter built that way."""
+    nl = synth.random_small(seed + 60, num_cells=30 + seed, num_nets=26 + 4 * seed, max_pins=8, num_fixed=2,
+                            allow_repeat=seed != 2)
+    x = synth.uniform(seed, 9, np.arange(nl.num_cells * 4, dtype=np.uint64)).reshape(nl.num_cells, 4) * 1000
+    A, want = _dense_reference(nl, x)
+    deg = A.sum(axis=1)
+    G = oracle.build_graph(nl.num_cells, nl.net_ptr, nl.pin_cell, cut=cut)
+    d = oracle.implicit_degrees(oracle.degrees(G), nl.net_ptr, nl.pin_cell, cut)
+    for sigma in (2.0, 4.0):
+        S = np.diag(1.0 / np.sqrt(deg + sigma))
+        ref_sym = S @ (A + sigma * np.eye(nl.num_cells)) @ S @ x
+        ref_rw = np.diag(1.0 / (deg + sigma)) @ (A + sigma * np.eye(nl.num_cells)) @ x
+        got_sym = oracle.apply_cut(G, d, sigma, x, nl.net_ptr, nl.pin_cell, cut)
+        got_rw = oracle.apply_cut(G, d, sigma, x, nl.net_ptr, nl.pin_cell, cut, norm="rw")
+        np.testing.assert_allclose(got_sym, ref_sym, rtol=1e-12, atol=1e-9)
+        np.testing.assert_allclose(got_rw, ref_rw, rtol=1e-12, atol=1e-9)
+    _, _, got = oracle.run(nl, x, cut=cut)
+    np.testing.assert_allclose(got, want, rtol=1e-12, atol=1e-9)
+
+
+def test_implicit_single_net_closed_form():
+    """GiFt on K_M with the clique applied from the netlist (every net
+    implicit) equals mean + f_M (g - mean), f_M derived by hand."""
+    fm, _ = _golden_f()
+    for M, f in fm.items():
+        N, rp, pc = _single_net(M)
+        nl = synth.Netlist(N, 1, rp, pc, np.zeros(N, np.uint8), np.zeros((N, 2), np.float32), 1000.0, {})
+        x = synth.uniform(7, 1, np.arange(M * 2, dtype=np.uint64)).reshape(M, 2) * 1000
+        G, d, y = oracle.run(nl, x, cut=2)
+        assert G.nnz == 0
+        np.testing.assert_allclose(d, 2.0 * (M - 1) / M, rtol=1e-13, atol=0)
+        mean = x.mean(axis=0)
+        np.testing.assert_allclose(y, mean + float(f) * (x - mean), rtol=1e-13, atol=1e-11)
+
+
 # ------------------------------------------------------------ Tikhonov smoothing
 @pytest.mark.parametrize("M", [2, 3, 7])
 @pytest.mark.parametrize("sigma,lam", [(2.0, 1.0), (4.0, 0.5), (1.0, 3.0)])
