@@ -105,25 +105,84 @@ def peaks():
 
 # ----------------------------------------------------------------- clocks
 class ClockSampler:
-    """nvidia-smi samples during the timed region."""
+    """SM clock and clock-event (throttle) reasons sampled during the timed
+    region: NVML read through ctypes every few milliseconds (read-only
+    queries), else nvidia-smi every 100 ms."""
+    REASONS = {0x8: "hw_slowdown", 0x40: "hw_thermal_slowdown", 0x20: "sw_thermal_slowdown", 0x4: "sw_power_cap",
+               0x80: "hw_power_brake_slowdown"}
     Q = ("index,clocks.sm,clocks.max.sm,power.draw,clocks_event_reasons.active,"
          "clocks_event_reasons.hw_slowdown,clocks_event_reasons.hw_thermal_slowdown,"
          "clocks_event_reasons.sw_thermal_slowdown,clocks_event_reasons.sw_power_cap")
 
-    def __init__(self, index: int):
+    def __init__(self, index: int, period_s: float = 0.002):
         self.index = index
+        self.period = period_s
+        self.samples = []  # (sm_mhz, max_mhz, reason bits)
         self.proc = None
         self.lines = []
+        self.stop = threading.Event()
+        self.nvml = None
+        self.handle = None
+        self.source = "none"
+
+    def _open_nvml(self):
+        import ctypes as C
+        import torch
+        for name in ("libnvidia-ml.so.1", "libnvidia-ml.so"):
+            try:
+                lib = C.CDLL(name)
+                break
+            except OSError:
+                lib = None
+        if lib is None or lib.nvmlInit_v2() != 0:
+            return False
+        h = C.c_void_p()
+        props = torch.cuda.get_device_properties(self.index)
+        uuid = getattr(props, "uuid", None)
+        ok = False
+        if uuid is not None:
+            text = str(uuid)
+            if not text.startswith("GPU-"):
+                text = "GPU-" + text
+            ok = lib.nvmlDeviceGetHandleByUUID(text.encode(), C.byref(h)) == 0
+        if not ok:
+            bus = getattr(props, "pci_bus_id", None)
+            if bus is not None:
+                text = f"{getattr(props, 'pci_domain_id', 0):08X}:{bus:02X}:{getattr(props, 'pci_device_id', 0):02X}.0"
+                ok = lib.nvmlDeviceGetHandleByPciBusId_v2(text.encode(), C.byref(h)) == 0
+        if not ok:
+            return False
+        self.nvml, self.handle = lib, h
+        return True
+
+    def _poll(self):
+        import ctypes as C
+        sm, mx, rs = C.c_uint(), C.c_uint(), C.c_ulonglong()
+        get_reasons = getattr(self.nvml, "nvmlDeviceGetCurrentClocksEventReasons", None) or \
+            self.nvml.nvmlDeviceGetCurrentClocksThrottleReasons
+        while not self.stop.is_set():
+            if (self.nvml.nvmlDeviceGetClockInfo(self.handle, 1, C.byref(sm)) == 0 and
+                    self.nvml.nvmlDeviceGetMaxClockInfo(self.handle, 1, C.byref(mx)) == 0 and
+                    get_reasons(self.handle, C.byref(rs)) == 0):
+                self.samples.append((sm.value, mx.value, rs.value))
+            time.sleep(self.period)
 
     def __enter__(self):
+        try:
+            if self._open_nvml():
+                self.source = "nvml"
+                self.t = threading.Thread(target=self._poll, daemon=True)
+                self.t.start()
+                return self
+        except Exception:
+            self.nvml = None
         try:
             self.proc = subprocess.Popen(["nvidia-smi", "-i", str(self.index), f"--query-gpu={self.Q}",
                                           "--format=csv,noheader,nounits", "-lms", "100"],
                                          stdout=subprocess.PIPE, stderr=subprocess.DEVNULL, text=True)
+            self.source = "nvidia-smi"
             self.t = threading.Thread(target=self._read, daemon=True)
             self.t.start()
-            # the sampler is running once its first line arrives; keep only
-            # the samples taken from here on (the timed region)
             t0 = time.time()
             while not self.lines and time.time() - t0 < 5.0:
                 time.sleep(0.01)
@@ -137,6 +196,13 @@ class ClockSampler:
             self.lines.append(line.strip())
 
     def __exit__(self, *a):
+        self.stop.set()
+        if self.nvml is not None:
+            self.t.join(timeout=1.0)
+            try:
+                self.nvml.nvmlShutdown()
+            except Exception:
+                pass
         if self.proc:
             self.proc.terminate()
             try:
@@ -146,6 +212,12 @@ class ClockSampler:
 
     def summary(self):
         sm, mx, reasons = [], None, set()
+        for f, m, bits in self.samples:
+            sm.append(float(f))
+            mx = float(m)
+            for bit, name in self.REASONS.items():
+                if bits & bit:
+                    reasons.add(name)
         names = ["hw_slowdown", "hw_thermal_slowdown", "sw_thermal_slowdown", "sw_power_cap"]
         for ln in self.lines:
             f = [x.strip() for x in ln.split(",")]
@@ -160,8 +232,9 @@ class ClockSampler:
                 if v.lower() == "active":
                     reasons.add(n)
         if not sm:
-            return {"sm_mhz": None, "sm_max_mhz": None, "reasons": ["unsampled"], "samples": 0}
-        return {"sm_mhz": statistics.median(sm), "sm_max_mhz": mx, "reasons": sorted(reasons), "samples": len(sm)}
+            return {"sm_mhz": None, "sm_max_mhz": None, "reasons": ["unsampled"], "samples": 0, "source": self.source}
+        return {"sm_mhz": statistics.median(sm), "sm_max_mhz": mx, "reasons": sorted(reasons), "samples": len(sm),
+                "source": self.source}
 
 
 # ----------------------------------------------------------------- traffic record
@@ -233,11 +306,13 @@ def record_traffic(args):
 
 
 # ----------------------------------------------------------------- oracle (CPU)
-def oracle_sample(nl, g, num_signals: int = 1):
+def oracle_sample(nl, g, num_signals: int = 1, threads: bool = False):
     """Oracle build + filter + HPWL on the netlist with the first `num_signals`
-    signals; returns (seconds, edge-updates, output [N][num_signals][2], HPWL)."""
+    signals (threads: the OpenMP build, on all host cores); returns (seconds,
+    edge-updates, output [N][num_signals][2], HPWL, threads used)."""
     import oracle  # CPU baseline leg only
 
+    oracle.use_threads(threads)
     gs = np.ascontiguousarray(g[:, :num_signals, :]).reshape(nl.num_cells, -1)
     t0 = time.perf_counter()
     G = oracle.build_graph(nl.num_cells, nl.net_ptr, nl.pin_cell)
@@ -245,7 +320,9 @@ def oracle_sample(nl, g, num_signals: int = 1):
     out = oracle.gift(G, d, gs, nl.is_fixed).reshape(nl.num_cells, num_signals, 2)
     hp = oracle.hpwl(nl.net_ptr, nl.pin_cell, out)
     dt = time.perf_counter() - t0
-    return dt, 6.0 * G.nnz * num_signals, out, hp
+    nthreads = oracle.threads()
+    oracle.use_threads(False)
+    return dt, 6.0 * G.nnz * num_signals, out, hp, nthreads
 
 
 def precision_report(g0, outs, hps, ref, hp_ref):
@@ -263,19 +340,24 @@ def precision_report(g0, outs, hps, ref, hp_ref):
 
 
 def run_reference(args):
+    """The oracle (OpenMP build, all host cores) on the benchmark's netlist:
+    each step builds the graph of the whole netlist and filters and measures
+    1 of its signals (a bounded sample of the step, on the same
+    edge-updates metric)."""
     rank, world, _ = dist_env()
     if rank != 0:
         return
     import oracle
     oracle.build()
-    scale = 0.05  # about 0.4 s of single-threaded oracle work per step
-    nl, g = synth.workload(args.workload, scale=scale)
-    sample = f"{args.workload} law at {scale:g} scale ({nl.num_cells} cells, {nl.num_nets} nets), 1 of {g.shape[1]} signals; build + filter + HPWL"
+    oracle.build(threads=True)
+    nl, g = synth.workload(args.workload, scale=args.scale)
+    sample = (f"{args.workload}: full netlist ({nl.num_cells} cells, {nl.num_nets} nets), build + filter + HPWL "
+              f"of 1 of {g.shape[1]} signals per step, FP64 C oracle, OpenMP")
     for _ in range(args.warmup):
-        oracle_sample(nl, g)
-    times, units = [], 0.0
+        oracle_sample(nl, g, threads=True)
+    times, units, nth = [], 0.0, 1
     for _ in range(args.steps):
-        dt, u, _, _ = oracle_sample(nl, g)
+        dt, u, _, _, nth = oracle_sample(nl, g, threads=True)
         times.append(dt)
         units += u
     total = sum(times)
@@ -285,7 +367,7 @@ def run_reference(args):
         "warmup": args.warmup, "ms_per_step": 1e3 * total / args.steps, "higher_is_better": True,
         "scaling": "weak", "vs_baseline": None, "dtype": "f64", "data": "synthetic",
         "config": {"workload": args.workload, "sample": sample},
-        "cpu_baseline": {"value": v, "unit": UNIT, "cores": 1, "kind": "oracle", "sample": sample},
+        "cpu_baseline": {"value": v, "unit": UNIT, "cores": nth, "kind": "oracle", "sample": sample},
         "e2e": {"value": v, "unit": UNIT, "h2d_bytes_per_step": 0, "d2h_bytes_per_step": 0},
     }
     print(json.dumps(line), flush=True)
@@ -411,6 +493,20 @@ def run_serving(args, gift):
 
 
 # ----------------------------------------------------------------- batched
+def filter_alg_bytes(n: int, stored: int, wsz: int, K: int) -> float:
+    """Algorithmic bytes of the paper's filter (4 sweeps, chains sigma = 2 and
+    4), counted as the library counts a sweep: the CSR once, each distinct
+    input, scale and next input once, the accumulator read and written once,
+    the fixed flags in the last sweep."""
+    csr = stored * (4.0 + wsz) + 8.0 * (n + 1)
+    sig = 4.0 * n * K
+    s1 = csr + sig + 2 * (4.0 * n + sig)                       # g; both chains go on
+    s2 = csr + 2 * sig + (4.0 * n) + (4.0 * n + sig) + sig     # two inputs; chain 4 goes on; terms written
+    s3 = csr + sig + (4.0 * n + sig)                           # chain 4 alone
+    s4 = csr + sig + 4.0 * n + sig + sig + n                   # accumulator read, result written, fixed flags
+    return s1 + s2 + s3 + s4
+
+
 def run_batched(args, gift, ctx, stream):
     """64 netlists (cells log-uniform in [5k, 300k], nets/cell uniform in
     [1.0, 1.2], 1 % fixed), 4 signals each, BF16 weights: the block-diagonal
@@ -444,6 +540,8 @@ def run_batched(args, gift, ctx, stream):
 
     t_batch = timed(lambda: gift.gift_exec_launch(ex, stream))
     sched_batch = gift.gift_ctx_last_schedule(ctx)
+    info = gift.gift_graph_info(hb)
+    alg = filter_alg_bytes(int(info.num_cells), int(info.stored), 2, 2 * S)
     # one call per graph, each on its own graph (shapes tuned per graph)
     singles = []
     for (nl, g), (n, a, b, c) in zip(batch, nets):
@@ -465,7 +563,10 @@ def run_batched(args, gift, ctx, stream):
             "nnz": nnz, "edge_updates_per_filter": units, "captured_launch_ms": t_batch,
             "captured_edge_updates_per_s": units / (t_batch * 1e-3), "per_graph_calls_ms": t_loop,
             "per_graph_edge_updates_per_s": units / (t_loop * 1e-3), "speedup": t_loop / t_batch,
-            "schedule": sched_batch}
+            "schedule": sched_batch,
+            # the whole captured filter (every kernel of the call) against the measured HBM copy bandwidth
+            "roofline": {"bound": "hbm", "alg_bytes": alg, "achieved": alg / (t_batch * 1e-3) / 1e9,
+                         "peak": peaks()[0], "unit": "GB/s", "frac": alg / (t_batch * 1e-3) / 1e9 / peaks()[0]}}
 
 
 # ----------------------------------------------------------------- implicit cliques
@@ -936,10 +1037,13 @@ def run_ours(args):
     cpu = None
     precision = None
     if rank == 0 and world == 1 and not args.no_cpu_baseline:
-        dt, u, ref0, hp_ref = oracle_sample(nl, g, 1)
-        cpu = {"value": u / dt, "unit": UNIT, "cores": 1, "kind": "oracle",
+        dt1, u, ref0, hp_ref, _ = oracle_sample(nl, g, 1)
+        dtn, un, refn, _, nth = oracle_sample(nl, g, 1, threads=True)
+        assert np.array_equal(refn, ref0), "the OpenMP oracle build must give the single-threaded build's bits"
+        cpu = {"value": un / dtn, "unit": UNIT, "cores": nth, "kind": "oracle",
                "sample": f"{args.workload}: full netlist ({N} cells), build + filter + HPWL of 1 of {S} signals, "
-                         f"FP64 single-threaded C, {dt:.1f} s"}
+                         f"FP64 C oracle, OpenMP on {nth} threads, {dtn:.1f} s",
+               "single_thread": {"value": u / dt1, "unit": UNIT, "cores": 1, "seconds": dt1}}
         precision = precision_report(g[:, 0, :], outs0, hps0, ref0[:, 0, :], hp_ref[0])
         precision["sample"] = (f"signal 0 of {S}, all {N} cells, against the FP64 oracle with exact weights; "
                                "FP32 signal and accumulation")

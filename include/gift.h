@@ -203,6 +203,19 @@ GIFT_API gift_status gift_ctx_device_status(gift_ctx *ctx);
  * next one) fails as if the device were out of memory; 0 disables. */
 GIFT_API void gift_ctx_debug_fail_alloc(gift_ctx *ctx, int32_t n);
 
+/* Test hook for the bounded device waits (the paper has no counterpart): the
+ * TMA sweep pipeline (schedules 2000 + w), with drop_copies = 1, announces
+ * every stage without issuing the stage's copies and gives up each mbarrier
+ * wait after `polls` polls (0: the default, 2^22), so the waits on those
+ * stages run out: the kernel records GIFT_ERR_TIMEOUT in the context's device
+ * error word and returns, with no copy in flight.  The filter's output is
+ * then invalid; gift_ctx_device_status (or the next host-memory call) reports
+ * GIFT_ERR_TIMEOUT once.  drop_copies = 0 restores normal operation and the
+ * default limit (a short limit is never applied while copies are issued: a
+ * wait that gave up while copies were still landing would let the kernel end
+ * under them). */
+GIFT_API void gift_ctx_debug_waits(gift_ctx *ctx, uint32_t polls, int32_t drop_copies);
+
 /* Paper defaults: terms {sigma 2, k 2, 0.1}, {4, 2, 0.7}, {4, 4, 0.2} (Eq. 15
  * with the Sec. 4.1 coefficients), symmetric normalisation, fixed cells kept. */
 GIFT_API void gift_filter_spec_default(gift_filter_spec *spec);

@@ -2,8 +2,10 @@
 
 Only ``tests/``, the smoke check and the CPU-baseline leg of ``bench.py`` may
 import this package.  The product path (the CUDA library and its binding)
-never calls it.  The arithmetic lives in ``gift_oracle.c`` (plain C, FP64,
-single thread); this module compiles it with gcc and marshals numpy arrays.
+never calls it.  The arithmetic lives in ``gift_oracle.c`` (plain C, FP64);
+this module compiles it with gcc -- single-threaded, and with OpenMP for the
+timed CPU baseline (:func:`use_threads`; the same results) -- and marshals
+numpy arrays.
 
 Every function states the paper passage it follows:
 
@@ -38,29 +40,46 @@ _HERE = os.path.dirname(os.path.abspath(__file__))
 _SRC = os.path.join(_HERE, "gift_oracle.c")
 _LIBDIR = os.path.join(_HERE, "lib")
 _LIB = os.path.join(_LIBDIR, "libgift_oracle.so")
+_LIB_OMP = os.path.join(_LIBDIR, "libgift_oracle_omp.so")
 
 DEFAULT_TERMS = ((2.0, 2, 0.1), (4.0, 2, 0.7), (4.0, 4, 0.2))  # Eq. 15 + Sec. 4.1
 FMT = {"f64": 0, "f32": 1, "bf16": 2, "f16": 3}
 
 
-def build() -> str:
-    """Compile the oracle library (gcc, -O2, no fast-math)."""
+def build(threads: bool = False) -> str:
+    """Compile the oracle library (gcc, -O2, no fast-math); threads=True: the
+    OpenMP build (same results, the row loops over the host's cores)."""
     os.makedirs(_LIBDIR, exist_ok=True)
-    if (not os.path.exists(_LIB)) or os.path.getmtime(_LIB) < os.path.getmtime(_SRC):
-        tmp = _LIB + f".tmp{os.getpid()}"
+    lib_path = _LIB_OMP if threads else _LIB
+    if (not os.path.exists(lib_path)) or os.path.getmtime(lib_path) < os.path.getmtime(_SRC):
+        tmp = lib_path + f".tmp{os.getpid()}"
         subprocess.check_call(["gcc", "-O2", "-std=c11", "-fPIC", "-shared", "-fno-fast-math",
-                               "-ffp-contract=off", "-o", tmp, _SRC, "-lm"])
-        os.replace(tmp, _LIB)
-    return _LIB
+                               "-ffp-contract=off", *(["-fopenmp"] if threads else []), "-o", tmp, _SRC, "-lm"])
+        os.replace(tmp, lib_path)
+    return lib_path
 
 
 _lib = None
+_threads = False
+
+
+def use_threads(on: bool) -> None:
+    """Switch between the single-threaded and the OpenMP build."""
+    global _lib, _threads
+    if on != _threads:
+        _threads = on
+        _lib = None
+
+
+def threads() -> int:
+    """Threads the loaded build runs its parallel loops on."""
+    return int(lib().oracle_threads())
 
 
 def lib():
     global _lib
     if _lib is None:
-        L = C.CDLL(build())
+        L = C.CDLL(build(_threads))
         P = C.c_void_p
         L.oracle_build.restype = P
         L.oracle_build.argtypes = [C.c_int32, C.c_int32, P, P]
@@ -79,6 +98,8 @@ def lib():
         L.oracle_filter.argtypes = [C.c_int32, C.c_int32, P, P, P, P, C.c_int32, P, P, P,
                                     C.c_int32, C.c_int32, P, P, P]
         L.oracle_hpwl.argtypes = [C.c_int32, P, P, C.c_int32, P, P]
+        L.oracle_threads.restype = C.c_int
+        L.oracle_threads.argtypes = []
         L.oracle_apply_cut.restype = C.c_int
         L.oracle_apply_cut.argtypes = [C.c_int32, C.c_int32, P, P, P, P, C.c_double, C.c_int32, C.c_int32, P, P,
                                        C.c_int64, P, P]

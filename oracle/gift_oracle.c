@@ -4,6 +4,9 @@
  * TEST INFRASTRUCTURE.  Only the test suite, the smoke check and the CPU
  * baseline leg of the benchmark may load this file's library.  It shares no
  * code, header, table or helper with the CUDA path, and nothing here is tuned.
+ * Built twice: single-threaded, and with OpenMP (the row loops spread over the
+ * host's cores; the same bits, since every output element is still summed by
+ * one thread in the same order).
  *
  * What it computes, step by step in the paper's order:
  *   1. clique net model (Sec. 3.2.3 with Algorithm 1; weight rule after Eq. 4):
@@ -88,7 +91,36 @@ static oracle_graph *build_cut(int32_t num_cells, int32_t num_nets, const int64_
                 ++k;
             }
     }
-    qsort(pairs, (size_t)k, sizeof(oracle_pair), cmp_pair);
+    /* sort by (row, column, net): pairs bucketed by row in generation order,
+     * then each row's bucket sorted by (column, net) */
+    int64_t *bstart = (int64_t *)calloc((size_t)num_cells + 1, sizeof(int64_t));
+    oracle_pair *sorted = (oracle_pair *)malloc((size_t)(k > 0 ? k : 1) * sizeof(oracle_pair));
+    if (!bstart || !sorted) {
+        free(pairs);
+        free(bstart);
+        free(sorted);
+        return NULL;
+    }
+    for (int64_t t = 0; t < k; ++t) bstart[pairs[t].i + 1] += 1;
+    for (int32_t i = 0; i < num_cells; ++i) bstart[i + 1] += bstart[i];
+    {
+        int64_t *fill = (int64_t *)malloc(((size_t)num_cells + 1) * sizeof(int64_t));
+        if (!fill) {
+            free(pairs);
+            free(bstart);
+            free(sorted);
+            return NULL;
+        }
+        memcpy(fill, bstart, ((size_t)num_cells + 1) * sizeof(int64_t));
+        for (int64_t t = 0; t < k; ++t) sorted[fill[pairs[t].i]++] = pairs[t];
+        free(fill);
+    }
+    free(pairs);
+    pairs = sorted;
+#pragma omp parallel for schedule(dynamic, 256)
+    for (int32_t i = 0; i < num_cells; ++i)
+        qsort(pairs + bstart[i], (size_t)(bstart[i + 1] - bstart[i]), sizeof(oracle_pair), cmp_pair);
+    free(bstart);
 
     oracle_graph *g = (oracle_graph *)calloc(1, sizeof(oracle_graph));
     g->n = num_cells;
@@ -201,6 +233,7 @@ void oracle_round(int64_t n, const double *in, double *out, int32_t fmt) {
 
 /* Step 2: d_i = sum_j A_ij (Sec. 2.1), summed in column order. */
 void oracle_degrees(int32_t n, const int64_t *row_ptr, const double *val, double *d) {
+#pragma omp parallel for schedule(static)
     for (int32_t i = 0; i < n; ++i) {
         double s = 0.0;
         for (int64_t k = row_ptr[i]; k < row_ptr[i + 1]; ++k) s += val[k];
@@ -213,6 +246,7 @@ void oracle_degrees(int32_t n, const int64_t *row_ptr, const double *val, double
  *   norm 1 (random walk): y_i = ( sum_j A_ij x_j + sigma x_i ) / (d_i + sigma)          */
 void oracle_apply(int32_t n, int32_t K, const int64_t *row_ptr, const int32_t *col, const double *val,
                   const double *d, double sigma, int32_t norm, const double *x, double *y) {
+#pragma omp parallel for schedule(dynamic, 1024)
     for (int32_t i = 0; i < n; ++i) {
         for (int32_t c = 0; c < K; ++c) {
             double acc = 0.0;
@@ -259,10 +293,12 @@ int oracle_apply_cut(int32_t n, int32_t K, const int64_t *row_ptr, const int32_t
         free(S);
         return -1;
     }
+#pragma omp parallel for schedule(static)
     for (int32_t j = 0; j < n; ++j) {
         double sj = norm == 0 ? 1.0 / sqrt(d[j] + sigma) : 1.0;
         for (int32_t c = 0; c < K; ++c) xh[(int64_t)j * K + c] = sj * x[(int64_t)j * K + c];
     }
+#pragma omp parallel for schedule(dynamic, 1024)
     for (int32_t i = 0; i < n; ++i)
         for (int64_t k = row_ptr[i]; k < row_ptr[i + 1]; ++k)
             for (int32_t c = 0; c < K; ++c) acc[(int64_t)i * K + c] += val[k] * xh[(int64_t)col[k] * K + c];
@@ -294,6 +330,7 @@ int oracle_apply_cut(int32_t n, int32_t K, const int64_t *row_ptr, const int32_t
         }
         free(cells);
     }
+#pragma omp parallel for schedule(static)
     for (int32_t i = 0; i < n; ++i) {
         double si = norm == 0 ? 1.0 / sqrt(d[i] + sigma) : 1.0;
         for (int32_t c = 0; c < K; ++c) {
@@ -342,6 +379,7 @@ static int filter_terms(int32_t n, int32_t K, const int64_t *row_ptr, const int3
             v = t;
             t = sw;
         }
+#pragma omp parallel for schedule(static)
         for (size_t q = 0; q < len; ++q) out[q] += alpha[term] * v[q];
     }
     if (reimpose && is_fixed) {
@@ -370,6 +408,16 @@ int oracle_filter_cut(int32_t n, int32_t K, const int64_t *row_ptr, const int32_
     return filter_terms(n, K, row_ptr, col, val, d, num_terms, sigma, power, alpha, norm, reimpose, is_fixed,
                         num_nets, net_ptr, pin_cell, cut, g, out);
 }
+
+/* Threads the library runs its parallel loops on (1 when built without OpenMP).
+ * Every parallel loop writes each output element from one thread, in the
+ * serial build's order, so both builds give the same bits. */
+#ifdef _OPENMP
+#include <omp.h>
+int oracle_threads(void) { return omp_get_max_threads(); }
+#else
+int oracle_threads(void) { return 1; }
+#endif
 
 /* Step 6: HPWL of each of S signals; xy is [N][S][2]. */
 void oracle_hpwl(int32_t num_nets, const int64_t *net_ptr, const int32_t *pin_cell, int32_t S,

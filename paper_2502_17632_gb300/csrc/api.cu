@@ -232,6 +232,14 @@ void gift_ctx_debug_fail_alloc(gift_ctx *ctx, int32_t n) {
     if (ctx) ctx->fail_alloc_in = n > 0 ? n : 0;
 }
 
+void gift_ctx_debug_waits(gift_ctx *ctx, uint32_t polls, int32_t drop_copies) {
+    if (!ctx) return;
+    // a short limit only without copies: a wait that gave up while copies were
+    // still landing would let the kernel end under them
+    ctx->dbg_spin_limit = drop_copies ? polls : 0;
+    ctx->dbg_drop_copies = drop_copies ? 1 : 0;
+}
+
 void gift_filter_spec_default(gift_filter_spec *spec) {
     if (!spec) return;
     std::memset(spec, 0, sizeof(*spec));

@@ -746,6 +746,9 @@ int run_sweeps(gift_ctx *ctx, const Plan &p, ShapeSet ss, cudaStream_t st, std::
                     t.stage_bytes = stage_bytes;
                     t.tile_counter = p.counters + tma_launch++;
                     t.error = ctx->dev_error;
+                    const uint32_t lim = ctx->dbg_spin_limit.load();
+                    t.spin_limit = lim ? lim : kSpinLimit;
+                    t.drop_copies = ctx->dbg_drop_copies.load();
                     params = {&a, &m0, &m1, &t};
                     grid = ctx->num_sms;
                     threads = 32 + kTmaRows * (W / 4);

@@ -115,6 +115,10 @@ struct gift_ctx {
     int last_schedules[4] = {0, 0, 0, 0};  // guarded by tune_mu (filter calls may run on several threads)
     // device word set by kernels whose bounded waits ran out (0 = fine)
     int32_t *dev_error = nullptr;
+    // test hooks of the bounded waits (gift_ctx_debug_waits): polls per wait
+    // (0: the default) and a producer that issues no copies
+    std::atomic<uint32_t> dbg_spin_limit{0};
+    std::atomic<int32_t> dbg_drop_copies{0};
     // wtab[m] = 2/m in FP64 for m in [2, kWeightTable] (0 below), filled on the host
     double *wtab = nullptr;
     // side stream for uploads that overlap work on the caller's stream (gift_run)

@@ -35,6 +35,9 @@ struct TmaArgs {
     int32_t stage_bytes;
     int32_t *tile_counter;  // zeroed before the launch
     int32_t *error;         // set to a nonzero code on a wait that ran out
+    uint32_t spin_limit;    // try_wait rounds before a wait gives up
+    int32_t drop_copies;    // test hook: 1 = the producer announces its stages but issues no copy,
+                            // so every wait on them runs out (no copy is ever in flight)
 };
 
 struct __align__(16) StageMeta {
@@ -57,8 +60,8 @@ __device__ __forceinline__ void mbar_arrive_tx(uint64_t *bar, uint32_t bytes) {
     asm volatile("mbarrier.arrive.expect_tx.shared::cta.b64 _, [%0], %1;" ::"r"(smem_addr(bar)), "r"(bytes) : "memory");
 }
 // Bounded wait for the phase of the given parity; false if it ran out.
-__device__ __forceinline__ bool mbar_wait(uint64_t *bar, uint32_t parity) {
-    for (uint32_t i = 0; i < kSpinLimit; ++i) {
+__device__ __forceinline__ bool mbar_wait(uint64_t *bar, uint32_t parity, uint32_t limit) {
+    for (uint32_t i = 0; i < limit; ++i) {
         uint32_t done;
         asm volatile(
             "{ .reg .pred p; mbarrier.try_wait.parity.shared::cta.b64 p, [%1], %2; selp.u32 %0, 1, 0, p; }"
@@ -136,7 +139,7 @@ k_sweep_tma(const SweepArgs a, const __grid_constant__ CUtensorMap map0, const _
             while (true) {
                 const int s = (int)(n % NS);
                 const int64_t use = n / NS;
-                if (use >= 1 && !mbar_wait(&empty[s], (uint32_t)((use - 1) & 1))) {
+                if (use >= 1 && !mbar_wait(&empty[s], (uint32_t)((use - 1) & 1), t.spin_limit)) {
                     if (lane == 0) atomicExch(t.error, 1);
                     ok = false;
                     break;
@@ -170,7 +173,7 @@ k_sweep_tma(const SweepArgs a, const __grid_constant__ CUtensorMap map0, const _
                 if (lane == 0) mbar_arrive_tx(&full[s], (uint32_t)(ngroups * 4 * W * 4 * NX));
                 else mbar_arrive(&full[s]);
                 __syncwarp();
-                for (int gi = lane; gi < ngroups; gi += 32) {
+                for (int gi = lane; gi < (t.drop_copies ? 0 : ngroups); gi += 32) {
                     const int b0 = 4 * gi;
                     const int y0 = scol[b0];
                     const int y1 = scol[min(b0 + 1, cnt - 1)];
@@ -189,7 +192,7 @@ k_sweep_tma(const SweepArgs a, const __grid_constant__ CUtensorMap map0, const _
         // drain: wait until every issued stage has landed before leaving
         for (int64_t m = n > NS ? n - NS : 0; m < n; ++m) {
             const int s = (int)(m % NS);
-            if (!mbar_wait(&full[s], (uint32_t)((m / NS) & 1)) && lane == 0) atomicExch(t.error, 2);
+            if (!mbar_wait(&full[s], (uint32_t)((m / NS) & 1), t.spin_limit) && lane == 0) atomicExch(t.error, 2);
         }
         return;
     }
@@ -204,7 +207,7 @@ k_sweep_tma(const SweepArgs a, const __grid_constant__ CUtensorMap map0, const _
         for (int v = 0; v < 4; ++v) acc[c][v] = 0.f;
     for (int64_t n = 0;; ++n) {
         const int s = (int)(n % NS);
-        if (!mbar_wait(&full[s], (uint32_t)((n / NS) & 1))) {
+        if (!mbar_wait(&full[s], (uint32_t)((n / NS) & 1), t.spin_limit)) {
             if ((ct & 31) == 0) atomicExch(t.error, 3);
             return;
         }

@@ -115,6 +115,7 @@ def load(build_if_missing: bool = True):
         "gift_ctx_kernel_stats": (I32, [P, P, I32]),
         "gift_ctx_reset_stats": (None, [P]),
         "gift_ctx_debug_fail_alloc": (None, [P, I32]),
+        "gift_ctx_debug_waits": (None, [P, C.c_uint32, I32]),
         "gift_ctx_last_schedule": (I32, [P, P]),
         "gift_ctx_device_status": (I32, [P]),
         "gift_filter_spec_default": (None, [P]),
@@ -240,6 +241,12 @@ def gift_ctx_device_status(ctx):
 
 def gift_ctx_debug_fail_alloc(ctx, n: int):
     load().gift_ctx_debug_fail_alloc(ctx, n)
+
+
+def gift_ctx_debug_waits(ctx, polls: int, drop_copies: bool = False):
+    """Test hook: bound the TMA pipeline's waits to `polls` polls (0: default)
+    and optionally drop its copies so that the waits run out."""
+    load().gift_ctx_debug_waits(ctx, polls, 1 if drop_copies else 0)
 
 
 def gift_filter_spec_default() -> gift_filter_spec:

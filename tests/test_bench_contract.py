@@ -24,7 +24,7 @@ def _bench(args, env=None, timeout=300):
 
 def test_reference_arm_prints_one_complete_line():
     import bench
-    r = _bench(["--impl", "reference", "--steps", "2", "--warmup", "3"])
+    r = _bench(["--impl", "reference", "--steps", "2", "--warmup", "3", "--scale", "0.05"])
     assert r.returncode == 0, r.stderr[-2000:]
     lines = [ln for ln in r.stdout.splitlines() if ln.strip()]
     assert len(lines) == 1

@@ -19,8 +19,13 @@ import warnings
 
 import pytest
 
-import oracle
-from tests import test_oracle_eigen, test_oracle_pins
+# the OpenMP builds run the tiny pin inputs: a couple of threads each keeps
+# parallel test runs from oversubscribing the host (read when the first
+# OpenMP build is loaded)
+os.environ.setdefault("OMP_NUM_THREADS", "2")
+
+import oracle  # noqa: E402
+from tests import test_oracle_eigen, test_oracle_pins  # noqa: E402
 
 C_SRC = os.path.join(os.path.dirname(oracle.__file__), "gift_oracle.c")
 PY_SRC = os.path.join(os.path.dirname(oracle.__file__), "__init__.py")
@@ -177,12 +182,12 @@ def _patch(src, edits):
     return src
 
 
-def _compile(tmp_path, name, src):
+def _compile(tmp_path, name, src, threads=False):
     c = tmp_path / f"{name}.c"
     so = tmp_path / f"{name}.so"
     c.write_text(src)
     subprocess.check_call(["gcc", "-O1", "-std=c11", "-fPIC", "-shared", "-fno-fast-math", "-ffp-contract=off",
-                           "-o", str(so), str(c), "-lm"])
+                           *(["-fopenmp"] if threads else []), "-o", str(so), str(c), "-lm"])
     return str(so)
 
 
@@ -191,7 +196,7 @@ def _with_c_library(so_path, run):
     saved_lib, saved_build = oracle._lib, oracle.build
     try:
         oracle._lib = None
-        oracle.build = lambda: so_path
+        oracle.build = lambda threads=False: so_path
         oracle.lib()
         return run()
     finally:
@@ -219,16 +224,21 @@ def _with_python_source(src, run):
             setattr(oracle, k, v)
 
 
-def test_unmutated_copies_pass_every_pin(tmp_path):
-    so = _compile(tmp_path, "identity", open(C_SRC).read())
+@pytest.mark.parametrize("threads", [False, True])
+def test_unmutated_copies_pass_every_pin(tmp_path, threads):
+    so = _compile(tmp_path, "identity", open(C_SRC).read(), threads)
     assert _with_c_library(so, _failing_pins) == []
-    assert _with_python_source(open(PY_SRC).read(), _failing_pins) == []
+    if not threads:
+        assert _with_python_source(open(PY_SRC).read(), _failing_pins) == []
     assert len(list(_pin_cases())) >= 60
 
 
+@pytest.mark.parametrize("threads", [False, True])
 @pytest.mark.parametrize("name", sorted(C_MUTANTS))
-def test_c_mutant_is_caught(tmp_path, name):
-    so = _compile(tmp_path, name, _patch(open(C_SRC).read(), C_MUTANTS[name]))
+def test_c_mutant_is_caught(tmp_path, name, threads):
+    """Every planted C mistake fails a pin, in the single-threaded and in the
+    OpenMP build."""
+    so = _compile(tmp_path, name, _patch(open(C_SRC).read(), C_MUTANTS[name]), threads)
     assert _with_c_library(so, _failing_pins), f"planted mistake {name} passed every pin"
 
 
