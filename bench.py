@@ -27,6 +27,10 @@ import time
 
 import numpy as np
 
+# the OpenMP oracle's idle threads sleep instead of spinning, so they do not
+# take host cores from the timed GPU sections that run after it
+os.environ.setdefault("OMP_WAIT_POLICY", "PASSIVE")
+
 ROOT = os.path.dirname(os.path.abspath(__file__))
 sys.path.insert(0, ROOT)
 
@@ -917,7 +921,8 @@ def run_ours(args):
     # one build for sizes
     h = gift.gift_build_graph(ctx, N, d_np, d_pc, d_fx, wd, stream=stream)
     info = gift.gift_graph_info(h)
-    nnz = int(info.nnz)
+    info = type("Info", (), {"nnz": int(info.nnz), "stored": int(info.stored)})()
+    nnz = info.nnz
     gift.gift_graph_free(h)
     units = 6.0 * nnz * S
 
@@ -958,9 +963,17 @@ def run_ours(args):
     per_launch_bytes = trec["alg_bytes"] / max(trec["launches"], 1)
     achieved = per_launch_bytes / (per_launch_ms * 1e-3) / 1e9 if per_launch_ms > 0 else 0.0
     traffic = recorded_traffic(tname, args.workload, args.weights, schedule)
+    # the survey's byte model per sweep (CSR once, the scale vector, the signal read and written once, plus
+    # the second written signal of the two-chain sweeps 1 and 2), for comparison with the library's count
+    wsz = 4 if args.weights == "f32" else 2
+    survey_filter_bytes = 4 * (info.stored * (4.0 + wsz) + 8.0 * (N + 1) + 4.0 * N + 8.0 * N * 2 * S) + \
+        2 * 4.0 * N * 2 * S
     roofline = {"bound": "hbm", "kernel": tname, "achieved": achieved, "peak": peak, "unit": "GB/s",
                 "frac": achieved / peak, "peak_source": f"hbm_gbs, {peak_src}",
                 "alg_bytes_per_launch": per_launch_bytes, "ms_per_launch": per_launch_ms,
+                # one filter per step: the survey's bytes of all steps over the same kernels' time
+                "frac_survey_bytes": (survey_filter_bytes * args.steps / (trec["total_ms"] * 1e-3) / 1e9 / peak
+                                      if tname == "filter.sweep" and trec["total_ms"] > 0 else None),
                 "traffic": traffic,
                 # DRAM bytes the launches really move (recorded traffic) over the live launch time: the
                 # random row gathers fetch about 4.4x the algorithmic bytes on this graph

@@ -1006,8 +1006,10 @@ ShapeSet autotune(gift_ctx *ctx, const Plan &p, cudaStream_t st) {
             double ms[4];
             bool seen[4];
             measure(ss, ms, seen);
+            // a later candidate must be clearly faster: shapes within timing noise of each other
+            // keep the earlier one, so the choice repeats from run to run
             for (int kd = 0; kd < 4; ++kd)
-                if (seen[kd] && ms[kd] < best_ms[kd]) {
+                if (seen[kd] && ms[kd] < best_ms[kd] * 0.98) {
                     best_ms[kd] = ms[kd];
                     best.kind[kd] = s;
                 }
@@ -1037,6 +1039,8 @@ ShapeSet autotune(gift_ctx *ctx, const Plan &p, cudaStream_t st) {
         throw;
     }
     cleanup();
+    // the pre-scaled pair copy only concerns the first sweep of a chain pair
+    for (int kd = 1; kd < 4; ++kd) best.kind[kd].prescale = 0;
     std::lock_guard<std::mutex> lk(ctx->tune_mu);
     TunedSet ts;
     for (int kd = 0; kd < 4; ++kd) ts.kind[kd] = best.kind[kd];
