@@ -11,8 +11,9 @@
 //   scatter  cell -> list of its nets (one entry per pin)
 //   rows     per cell: generate (neighbour, net) keys from its nets, sort them in
 //            shared memory, sum duplicates in FP64 in increasing net order
-//            (warp per row; a block per row for long rows; global-memory keys
-//            for rows beyond the shared-memory capacity)
+//            (a thread per short row, a warp per row up to 512 entries, a
+//            block per longer row with a stable radix sort by neighbour,
+//            global-memory buffers for rows beyond the shared-memory capacity)
 //   scan     unique counts -> row_ptr
 //   compact  round each sum once to the storage type, write col/val, and
 //            d_i = sum_j A_ij in FP64 over the stored weights in column order.
@@ -27,10 +28,15 @@ namespace {
 
 constexpr int kWarpCap = 512;      // keys per warp in the warp tier
 constexpr int kRowsWarps = 8;      // warps per block in the warp tier
-constexpr int kBlockCap = 16384;   // keys in shared memory in the block tier (128 KiB)
-constexpr int kBlockThreads = 512;
 constexpr uint64_t kPadKey = ~0ull;
 constexpr int64_t kPadFraction = 1024;
+
+// Bits needed to write v (0 for v = 0).
+inline int bit_width_u64(uint64_t v) {
+    int b = 0;
+    for (; v; v >>= 1) ++b;
+    return b;
+}
 
 // Sub-buffers of one device allocation, each 256-byte aligned: the build's
 // temporaries come from two such arenas (one allocation, one memset each
@@ -56,8 +62,8 @@ __device__ __forceinline__ int32_t key_net(uint64_t k) { return static_cast<int3
 // decreases, 2: a pin outside [0, N), 4: net_ptr[0] != 0, 8: net_ptr[E] < 0),
 // [1] net_ptr[0], [2] net_ptr[E] = P, [3] incidences, [4] raw pairs, [5] the
 // longest row's raw pairs, [6] the finishing pass's unique entries, [7] its
-// longest row.
-enum { kSumFlags, kSumFirst, kSumPins, kSumInc, kSumRaw, kSumMaxRaw, kSumUnique, kSumMaxRow, kSumSize };
+// longest row, [8] the most raw pairs + incidences of a row.
+enum { kSumFlags, kSumFirst, kSumPins, kSumInc, kSumRaw, kSumMaxRaw, kSumUnique, kSumMaxRow, kSumMaxNeed, kSumSize };
 
 __global__ void k_validate(int32_t E, int32_t N, const int64_t *__restrict__ net_ptr,
                            const int32_t *__restrict__ pin_cell, unsigned long long *__restrict__ summary) {
@@ -136,12 +142,22 @@ __global__ void k_count(int32_t E, int32_t N, const int64_t *__restrict__ net_pt
     });
 }
 
-__global__ void k_max_rawlen(int32_t N, const int64_t *__restrict__ raw_ptr, unsigned long long *__restrict__ mx) {
-    unsigned long long best = 0;
-    for (int64_t i = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; i < N; i += (int64_t)gridDim.x * blockDim.x)
-        best = max(best, (unsigned long long)(raw_ptr[i + 1] - raw_ptr[i]));
-    for (int o = 16; o; o >>= 1) best = max(best, __shfl_xor_sync(0xffffffffu, best, o));
+// The longest row's raw pairs into mx[0], and its raw pairs + incidences
+// (the block tier's slots) into mx[need_at].
+__global__ void k_max_rawlen(int32_t N, const int64_t *__restrict__ raw_ptr, const int64_t *__restrict__ inc_ptr,
+                             unsigned long long *__restrict__ mx, int need_at) {
+    unsigned long long best = 0, need = 0;
+    for (int64_t i = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; i < N; i += (int64_t)gridDim.x * blockDim.x) {
+        const unsigned long long raw = (unsigned long long)(raw_ptr[i + 1] - raw_ptr[i]);
+        best = max(best, raw);
+        need = max(need, raw + (unsigned long long)(inc_ptr[i + 1] - inc_ptr[i]));
+    }
+    for (int o = 16; o; o >>= 1) {
+        best = max(best, __shfl_xor_sync(0xffffffffu, best, o));
+        need = max(need, __shfl_xor_sync(0xffffffffu, need, o));
+    }
     if ((threadIdx.x & 31) == 0 && best) atomicMax(mx, best);
+    if ((threadIdx.x & 31) == 0 && need) atomicMax(mx + need_at, need);
 }
 
 // ------------------------------------------------------------------ scatter
@@ -684,112 +700,320 @@ __device__ __forceinline__ long long sat_add(long long a, long long b) {
     return s < kExactCap ? s : kExactCap;
 }
 
-// Block tiers: one block per long row.  GLOBAL_KEYS: keys live in a per-block
-// global scratch of `gcap` entries (rows beyond the shared-memory capacity);
-// else in dynamic shared memory of `cap` keys followed by `cap` stored
-// weights, and the block takes the rows of the list with lo < raw length <=
-// cap (launched once per size class, so that short rows do not reserve the
-// shared memory of the longest and many blocks share an SM).  The degree is
-// the block's exact fixed-point sum of the stored weights where that equals
-// the column-order FP64 sum (above), else one thread's FP64 sum in column
-// order: a serial FP64 chain of one active lane per entry occupies the SM's
-// narrow FP64 pipe for a full warp instruction per step.
-template <typename WT, bool GLOBAL_KEYS>
-__global__ void __launch_bounds__(kBlockThreads)
+// Block tiers: one block of NW warps per long row, every step block-wide and
+// in a fixed order:
+//   1. the row's incidences in increasing net order (a register sort in one
+//      warp for up to 32, else the radix sort below on the net ids);
+//   2. their pin offsets (a block scan of the nets' pin counts), and their
+//      nets' weights 2/M staged in shared memory when there are few;
+//   3. one entry per pin of those nets, in that order: (cell, incidence
+//      index), the row's own cell replaced by N so that it sorts last;
+//   4. a stable LSD radix sort of the entries by cell (kRadixBits a pass),
+//      so that each cell's entries stay in increasing net order;
+//   5. each run of equal cells summed in FP64 in that order and rounded once;
+//      unique indices from per-warp counts of run heads.
+// A row takes raw entries + incidences ("slots"): the shared-memory classes
+// take the rows with lo < slots <= cap; GLOBAL puts the same buffers in a
+// per-block slice of global scratch for longer rows.  The degree is the
+// block's exact fixed-point sum of the stored weights where that equals the
+// column-order FP64 sum (above), else one thread's FP64 sum in column order.
+constexpr int kRadixBits = 8;
+constexpr int kHistStride = (1 << kRadixBits) + 1;  // a warp's digit counts, padded against bank conflicts
+constexpr int kIncW = 64;                           // incidences whose net weights are staged
+constexpr int64_t kBlockTop = 15360;                // slots of the largest shared-memory class
+// Shared-memory classes (caps in slots, the last one clamped to the largest
+// the device allows) and the warps per block: kNarrowWarps up to kNarrowCap
+// slots, kWideWarps above.
+constexpr int64_t kBlockClasses[] = {1024, 1536, 2048, 3072, 4096, 6144, 8192, 12288, kBlockTop};
+constexpr int64_t kNarrowCap = 3072;
+constexpr int kNarrowWarps = 4, kWideWarps = 8;
+
+// Bytes of a block's buffers for C slots (C a multiple of 512) with payload
+// type KT: cells and payloads twice (the sort's two sides), then the sorted
+// incidences' nets (at most C / 2: every incidence has >= 2 pins).  While the
+// entries are generated, the second side holds the incidences' pin offsets
+// (C / 2 x 4 bytes) and pin bases (C / 2 x 8 bytes).
+template <typename KT>
+__host__ __device__ constexpr int64_t block_bytes(int64_t C) {
+    return C * (4 + (int64_t)sizeof(KT)) * 2 + C / 2 * 4;
+}
+static_assert(kBlockTop % 512 == 0, "block classes are multiples of 512 slots");
+
+__device__ __forceinline__ uint32_t warp_incl_scan(uint32_t v, int lane) {
+#pragma unroll
+    for (int o = 1; o < 32; o <<= 1) {
+        const uint32_t t = __shfl_up_sync(0xffffffffu, v, o);
+        if (lane >= o) v += t;
+    }
+    return v;
+}
+
+// Exclusive scan in place over total values, the p-th at at(p), by a block of
+// NW warps (each thread a contiguous run); s_part holds NW partial sums.
+// Ends without a barrier: the caller syncs before the values are read.
+template <int NW, class At>
+__device__ __forceinline__ void block_scan_excl(int total, At at, uint32_t *s_part) {
+    const int tid = threadIdx.x, lane = tid & 31, wid = tid >> 5;
+    const int per = (total + NW * 32 - 1) / (NW * 32);
+    const int p0 = min(tid * per, total), p1 = min(p0 + per, total);
+    uint32_t sum = 0;
+    for (int p = p0; p < p1; ++p) sum += at(p);
+    const uint32_t incl = warp_incl_scan(sum, lane);
+    if (lane == 31) s_part[wid] = incl;
+    __syncthreads();
+    if (wid == 0) {
+        const uint32_t v = lane < NW ? s_part[lane] : 0u;
+        const uint32_t inc = warp_incl_scan(v, lane);
+        if (lane < NW) s_part[lane] = inc - v;
+    }
+    __syncthreads();
+    uint32_t run = s_part[wid] + incl - sum;
+    for (int p = p0; p < p1; ++p) {
+        uint32_t &h = at(p);
+        const uint32_t c = h;
+        h = run;
+        run += c;
+    }
+}
+
+// Stable LSD radix sort of n cells (and their payloads, if k0 is not null)
+// by their low nbits bits, between (c0, k0) and (c1, k1), by a block of NW
+// warps.  Each warp owns a contiguous segment: it counts its digits (shared
+// atomics into its own row of cnt), then works out its own offsets (entries
+// of lower digits in all warps, then of the same digit in lower warps) into
+// its row of off, and walks its segment 32 entries at a time, each entry's
+// rank being its digit's offset plus the lanes of lower index with the same
+// digit.  Returns the number of passes: odd leaves the result in (c1, k1).
+template <typename KT, int NW>
+__device__ int block_radix_sort(uint32_t *c0, KT *k0, uint32_t *c1, KT *k1, int n, int nbits, uint32_t *cnt,
+                                uint32_t *off) {
+    const unsigned full = 0xffffffffu;
+    const int lane = threadIdx.x & 31, wid = threadIdx.x >> 5;
+    const int seg = ((n + NW - 1) / NW + 31) & ~31;
+    const int beg = min(wid * seg, n), end = min(beg + seg, n);
+    uint32_t *h = cnt + wid * kHistStride;
+    uint32_t *o = off + wid * kHistStride;
+    int passes = 0;
+    for (int s = 0; s < nbits; s += kRadixBits, ++passes) {
+        const int R = 1 << min(kRadixBits, nbits - s);
+        const uint32_t mask = (uint32_t)R - 1u;
+        for (int d = lane; d < R; d += 32) h[d] = 0u;
+        __syncwarp();
+        for (int i = beg + lane; i < end; i += 32) atomicAdd(&h[(c0[i] >> s) & mask], 1u);
+        __syncthreads();
+        uint32_t carry = 0u;
+        for (int d0 = 0; d0 < R; d0 += 32) {  // lane owns digit d0 + lane
+            const int d = d0 + lane;
+            uint32_t all = 0u, before = 0u;
+            if (d < R) {
+#pragma unroll
+                for (int w = 0; w < NW; ++w) {
+                    const uint32_t c = cnt[w * kHistStride + d];
+                    all += c;
+                    before += w < wid ? c : 0u;
+                }
+            }
+            const uint32_t incl = warp_incl_scan(all, lane);
+            if (d < R) o[d] = carry + incl - all + before;
+            carry += __shfl_sync(full, incl, 31);
+        }
+        __syncwarp();
+        for (int b = beg; b < end; b += 32) {
+            const int i = b + lane;
+            uint32_t c = 0u, base = 0u;
+            KT k = 0;
+            if (i < end) {
+                c = c0[i];
+                if (k0) k = k0[i];
+            }
+            const uint32_t d = i < end ? (c >> s) & mask : full;
+            const unsigned peers = __match_any_sync(full, d);
+            if (i < end) {
+                base = o[d];
+                const uint32_t pos = base + __popc(peers & ((1u << lane) - 1u));
+                c1[pos] = c;
+                if (k0) k1[pos] = k;
+            }
+            __syncwarp();
+            if (i < end && lane == __ffs(peers) - 1) o[d] = base + __popc(peers);
+            __syncwarp();
+        }
+        __syncthreads();
+        uint32_t *tc = c0;
+        c0 = c1;
+        c1 = tc;
+        KT *tk = k0;
+        k0 = k1;
+        k1 = tk;
+    }
+    return passes;
+}
+
+template <typename WT, typename KT, bool GLOBAL, int NW>
+__global__ void __launch_bounds__(NW * 32, 32 / NW)
 k_rows_block(const int64_t *__restrict__ inc_ptr, const int32_t *__restrict__ inc_net,
              const int64_t *__restrict__ net_ptr, const int32_t *__restrict__ pin_cell,
              const double *__restrict__ wnet, const int64_t *__restrict__ raw_ptr, int32_t *__restrict__ out_col,
              WT *__restrict__ out_val, int32_t *__restrict__ ucount, double *__restrict__ degree,
-             const int32_t *__restrict__ big_rows, const int32_t *__restrict__ big_count,
-             uint64_t *__restrict__ gkeys, int64_t gcap, int64_t lo, int64_t cap) {
-    extern __shared__ uint64_t smem_keys[];
-    __shared__ int s_cnt;
-    __shared__ int s_warp[kBlockThreads / 32];
-    __shared__ int s_uniq;
-    __shared__ long long s_q[kBlockThreads / 32];
-    __shared__ int s_ex[kBlockThreads / 32];
-    uint64_t *keys = GLOBAL_KEYS ? gkeys + blockIdx.x * gcap : smem_keys;
-    WT *svals = GLOBAL_KEYS ? nullptr : reinterpret_cast<WT *>(smem_keys + cap);
+             const int32_t *__restrict__ big_rows, const int32_t *__restrict__ big_count, char *__restrict__ gscratch,
+             int64_t lo, int64_t cap, int32_t N, int cell_bits, int net_bits) {
+    constexpr int T = NW * 32;
+    extern __shared__ __align__(16) char smem_dyn[];
+    __shared__ uint32_t cnt[NW * kHistStride];
+    __shared__ uint32_t off[NW * kHistStride];
+    __shared__ double inc_w[kIncW];
+    __shared__ uint32_t s_part[NW];
+    __shared__ long long s_q[NW];
+    __shared__ int s_ex[NW];
+    __shared__ int s_self;
+    const unsigned full = 0xffffffffu;
     const int tid = threadIdx.x, lane = tid & 31, wid = tid >> 5;
+    const int C = (int)cap;
+    char *buf = GLOBAL ? gscratch + (size_t)blockIdx.x * (size_t)block_bytes<KT>(cap) : smem_dyn;
+    uint32_t *ca = reinterpret_cast<uint32_t *>(buf);
+    KT *ka = reinterpret_cast<KT *>(ca + C);
+    uint32_t *cb = reinterpret_cast<uint32_t *>(ka + C);
+    KT *kb = reinterpret_cast<KT *>(cb + C);
+    int32_t *inc_e = reinterpret_cast<int32_t *>(kb + C);
+    uint32_t *ofs = cb;                                        // while generating
+    int64_t *pbase = reinterpret_cast<int64_t *>(cb + C / 2);  // while generating
     const int nrows = *big_count;
     for (int r = blockIdx.x; r < nrows; r += gridDim.x) {
         const int32_t row = big_rows[r];
         const int64_t rbase = raw_ptr[row];
-        const int64_t rawlen = raw_ptr[row + 1] - rbase;
-        if (GLOBAL_KEYS ? rawlen <= kBlockCap : (rawlen <= lo || rawlen > cap)) continue;
-        if (tid == 0) {
-            s_cnt = 0;
-            s_uniq = 0;
-        }
-        __syncthreads();
-        const int64_t ib = inc_ptr[row], ie = inc_ptr[row + 1];
-        for (int64_t k = ib; k < ie; ++k) {
-            int32_t e = inc_net[k];
-            int64_t nb = net_ptr[e], m = net_ptr[e + 1] - nb;
-            for (int64_t t = tid; t < m; t += blockDim.x) {
-                int32_t q = pin_cell[nb + t];
-                if (q != row) keys[atomicAdd(&s_cnt, 1)] = make_key(q, e);
-            }
-        }
-        __syncthreads();
-        const int n = s_cnt;
-        int64_t p2 = 2;
-        while (p2 < n) p2 <<= 1;
-        for (int64_t t = n + tid; t < p2; t += blockDim.x) keys[t] = kPadKey;
-        __syncthreads();
-        for (int64_t size = 2; size <= p2; size <<= 1) {
-            for (int64_t stride = size >> 1; stride > 0; stride >>= 1) {
-                for (int64_t t = tid; t < (p2 >> 1); t += blockDim.x) {
-                    int64_t i = 2 * t - (t & (stride - 1));
-                    int64_t j = i + stride;
-                    bool up = (i & size) == 0;
-                    uint64_t a = keys[i], b = keys[j];
-                    if ((a > b) == up) {
-                        keys[i] = b;
-                        keys[j] = a;
+        const int64_t ib = inc_ptr[row];
+        const int64_t ninc64 = inc_ptr[row + 1] - ib;
+        const int64_t need = raw_ptr[row + 1] - rbase + ninc64;
+        if (need <= lo || need > cap) continue;
+        const int ninc = (int)ninc64, n = (int)need;
+        const bool staged = ninc <= kIncW;
+
+        // 1. incidences in increasing net order
+        if (ninc <= 32) {
+            if (wid == 0) {
+                int32_t v = lane < ninc ? inc_net[ib + lane] : INT32_MAX;
+#pragma unroll
+                for (int k = 2; k <= 32; k <<= 1)
+#pragma unroll
+                    for (int j = k >> 1; j > 0; j >>= 1) {
+                        const int32_t o = __shfl_xor_sync(full, v, j);
+                        v = (((lane & j) == 0) == ((lane & k) == 0)) ? min(v, o) : max(v, o);
                     }
-                }
-                __syncthreads();
+                if (lane < ninc) inc_e[lane] = v;
             }
+        } else {
+            for (int i = tid; i < ninc; i += T) ca[i] = (uint32_t)inc_net[ib + i];
+            __syncthreads();
+            const int p = block_radix_sort<KT, NW>(ca, nullptr, cb, nullptr, ninc, net_bits, cnt, off);
+            const uint32_t *srt = (p & 1) ? cb : ca;
+            for (int i = tid; i < ninc; i += T) inc_e[i] = (int32_t)srt[i];
+        }
+        if (tid == 0) s_self = 0;
+        __syncthreads();
+
+        // 2. pin offsets of the sorted incidences; pbase[k] + f is the pin of entry f
+        for (int i = tid; i < ninc; i += T) {
+            const int32_t e = inc_e[i];
+            const int64_t nb = net_ptr[e];
+            ofs[i] = (uint32_t)(net_ptr[e + 1] - nb);
+            pbase[i] = nb;
+            if (staged) inc_w[i] = wnet[e];
+        }
+        __syncthreads();
+        block_scan_excl<NW>(ninc, [&](int p) -> uint32_t & { return ofs[p]; }, s_part);
+        __syncthreads();
+        for (int i = tid; i < ninc; i += T) pbase[i] -= (int64_t)ofs[i];
+        __syncthreads();
+
+        // 3. entries, one per pin, incidences in order (four gathers in flight)
+        int self = 0;
+        for (int f0 = tid; f0 < n; f0 += 4 * T) {
+            int a[4];
+            int32_t q[4];
+#pragma unroll
+            for (int u = 0; u < 4; ++u) {
+                const int f = f0 + u * T;
+                int x = 0, y = ninc - 1;  // the last incidence whose offset <= f
+                while (x < y) {
+                    const int mid = (x + y + 1) >> 1;
+                    if (ofs[mid] <= (uint32_t)f) x = mid;
+                    else y = mid - 1;
+                }
+                a[u] = x;
+            }
+#pragma unroll
+            for (int u = 0; u < 4; ++u) {
+                const int f = f0 + u * T;
+                q[u] = f < n ? pin_cell[pbase[a[u]] + f] : 0;
+            }
+#pragma unroll
+            for (int u = 0; u < 4; ++u) {
+                const int f = f0 + u * T;
+                if (f < n) {
+                    self += q[u] == row;
+                    ca[f] = q[u] == row ? (uint32_t)N : (uint32_t)q[u];
+                    ka[f] = (KT)a[u];
+                }
+            }
+        }
+#pragma unroll
+        for (int o = 16; o > 0; o >>= 1) self += __shfl_xor_sync(full, self, o);
+        if (lane == 0 && self) atomicAdd(&s_self, self);
+        __syncthreads();
+
+        // 4. stable sort by cell
+        const int p = block_radix_sort<KT, NW>(ca, ka, cb, kb, n, cell_bits, cnt, off);
+        const uint32_t *cs = (p & 1) ? cb : ca;
+        const KT *ks = (p & 1) ? kb : ka;
+        WT *svals = reinterpret_cast<WT *>((p & 1) ? ca : cb);  // the free side
+        const int nv = n - s_self;
+
+        // 5. run heads: per-warp counts, then unique indices and run sums
+        const int seg = ((nv + NW - 1) / NW + 31) & ~31;
+        const int beg = min(wid * seg, nv), end = min(beg + seg, nv);
+        int heads = 0;
+        for (int b = beg; b < end; b += 32) {
+            const int t = b + lane;
+            const bool head = t < end && (t == 0 || cs[t - 1] != cs[t]);
+            heads += __popc(__ballot_sync(full, head));
+        }
+        if (lane == 0) s_part[wid] = (uint32_t)heads;
+        __syncthreads();
+        int u0 = 0, uniq = 0;
+#pragma unroll
+        for (int w = 0; w < NW; ++w) {
+            const int c = (int)s_part[w];
+            u0 += w < wid ? c : 0;
+            uniq += c;
         }
         long long qsum = 0;
         bool exact = true;
-        for (int base = 0; base < n; base += blockDim.x) {
-            int t = base + tid;
+        for (int b = beg; b < end; b += 32) {
+            const int t = b + lane;
+            uint32_t c = 0u;
             bool head = false;
-            int32_t c = 0;
-            if (t < n) {
-                c = key_cell(keys[t]);
-                head = (t == 0) || key_cell(keys[t - 1]) != c;
+            if (t < end) {
+                c = cs[t];
+                head = t == 0 || cs[t - 1] != c;
             }
-            unsigned hm = __ballot_sync(0xffffffffu, head);
-            if (lane == 0) s_warp[wid] = __popc(hm);
-            __syncthreads();
-            int before = s_uniq;
-            for (int q = 0; q < wid; ++q) before += s_warp[q];
+            const unsigned hm = __ballot_sync(full, head);
             if (head) {
-                int u = before + __popc(hm & ((1u << lane) - 1));
+                const int u = u0 + __popc(hm & ((1u << lane) - 1u));
                 double sum = 0.0;
-                for (int rr = t; rr < n && key_cell(keys[rr]) == c; ++rr) sum += wnet[key_net(keys[rr])];
+                for (int rr = t; rr < nv && cs[rr] == c; ++rr) sum += staged ? inc_w[ks[rr]] : wnet[inc_e[ks[rr]]];
                 const WT w = Store<WT>::put(sum);
-                out_col[rbase + u] = c;
+                out_col[rbase + u] = (int32_t)c;
                 out_val[rbase + u] = w;
-                if (!GLOBAL_KEYS) svals[u] = w;
+                svals[u] = w;
                 const float wf = Store<WT>::getf(w);
                 if (wf >= 0x1p-11f && wf < 0x1p19f) qsum = sat_add(qsum, (long long)(wf * 0x1p34f));
                 else exact = false;
             }
-            __syncthreads();
-            if (tid == 0) {
-                int add = 0;
-                for (int q = 0; q < (int)(blockDim.x >> 5); ++q) add += s_warp[q];
-                s_uniq += add;
-            }
-            __syncthreads();
+            u0 += __popc(hm);
         }
 #pragma unroll
-        for (int o = 16; o > 0; o >>= 1) qsum = sat_add(qsum, __shfl_xor_sync(0xffffffffu, qsum, o));
-        const int wexact = __all_sync(0xffffffffu, exact);
+        for (int o = 16; o > 0; o >>= 1) qsum = sat_add(qsum, __shfl_xor_sync(full, qsum, o));
+        const int wexact = __all_sync(full, exact);
         if (lane == 0) {
             s_q[wid] = qsum;
             s_ex[wid] = wexact;
@@ -798,20 +1022,17 @@ k_rows_block(const int64_t *__restrict__ inc_ptr, const int32_t *__restrict__ in
         if (tid == 0) {
             long long q = 0;
             bool ex = true;
-            for (int k = 0; k < (int)(blockDim.x >> 5); ++k) {
+            for (int k = 0; k < NW; ++k) {
                 q = sat_add(q, s_q[k]);
                 ex = ex && s_ex[k] != 0;
             }
             double d = 0.0;
             if (ex && q < kExactCap) {
                 d = (double)q * 0x1p-34;
-            } else {  // column order, from shared memory where it fits
-                if (GLOBAL_KEYS)
-                    for (int u = 0; u < s_uniq; ++u) d += Store<WT>::get(out_val[rbase + u]);
-                else
-                    for (int u = 0; u < s_uniq; ++u) d += Store<WT>::get(svals[u]);
+            } else {  // column order
+                for (int u = 0; u < uniq; ++u) d += Store<WT>::get(svals[u]);
             }
-            ucount[row] = s_uniq;
+            ucount[row] = uniq;
             degree[row] = d;
         }
         __syncthreads();
@@ -1026,8 +1247,9 @@ void build_graph_impl(gift_ctx *ctx, const gift_netlist *nl, const gift_build_op
         exclusive_scan(ctx, reinterpret_cast<int64_t *>(rawlen_p), raw_ptr.as<int64_t>(), N, st);
     }
     {
-        LaunchTimer lt(ctx, st, "build.maxraw", 8.0 * (N + 1));
-        k_max_rawlen<<<grid_for(ctx, N, 256), 256, 0, st>>>(N, raw_ptr.as<int64_t>(), sum_d + kSumMaxRaw);
+        LaunchTimer lt(ctx, st, "build.maxraw", 16.0 * (N + 1));
+        k_max_rawlen<<<grid_for(ctx, N, 256), 256, 0, st>>>(N, raw_ptr.as<int64_t>(), inc_ptr_p, sum_d + kSumMaxRaw,
+                                                             kSumMaxNeed - kSumMaxRaw);
         check_launch("k_max_rawlen");
     }
     GIFT_CUDA(cudaMemcpyAsync(sum_d + kSumInc, inc_ptr_p + N, sizeof(int64_t), cudaMemcpyDeviceToDevice,
@@ -1041,7 +1263,8 @@ void build_graph_impl(gift_ctx *ctx, const gift_netlist *nl, const gift_build_op
     GIFT_REQUIRE(!(hs[kSumFlags] & 8), "gift_build_graph: net_ptr[E] must be >= 0");
     GIFT_REQUIRE(!(hs[kSumFlags] & 1), "gift_build_graph: net_ptr decreases");
     GIFT_REQUIRE(!(hs[kSumFlags] & 2), "gift_build_graph: pin_cell id out of [0, num_cells)");
-    const int64_t ninc = (int64_t)hs[kSumInc], nraw = (int64_t)hs[kSumRaw], maxraw = (int64_t)hs[kSumMaxRaw];
+    const int64_t ninc = (int64_t)hs[kSumInc], nraw = (int64_t)hs[kSumRaw], maxraw = (int64_t)hs[kSumMaxRaw],
+                  maxneed = (int64_t)hs[kSumMaxNeed];
     g->raw_pairs = nraw;
 
     // ---- temporaries once the totals are known: the fill counters and the
@@ -1077,12 +1300,30 @@ void build_graph_impl(gift_ctx *ctx, const gift_netlist *nl, const gift_build_op
     DevBuf out_col(ctx, sizeof(int32_t) * std::max<int64_t>(nraw, 1), st);  // may become the graph's col
     DevBuf out_val(ctx, wsz * std::max<int64_t>(nraw, 1), st);             // and val
     g->degree = (double *)dev_alloc(ctx, sizeof(double) * N, st);
-    DevBuf gkeys;
+    // block tiers: shared-memory classes of slots (raw pairs + incidences of
+    // a row), the largest one as big as the device allows next to the
+    // kernel's static shared memory; longer rows take global scratch
+    const int cell_bits = bit_width_u64((uint64_t)N);  // the pad value N sorts last
+    const int net_bits = bit_width_u64((uint64_t)std::max(E - 1, 1));
+    int64_t top = 0;
+    GIFT_REQUIRE(maxneed < ((int64_t)1 << 31) - 512, "gift_build_graph: a row has too many pins");
+    if (maxraw > kWarpCap) {
+        int optin = 0;
+        GIFT_CUDA(cudaDeviceGetAttribute(&optin, cudaDevAttrMaxSharedMemoryPerBlockOptin, ctx->device));
+        cudaFuncAttributes fa{};
+        GIFT_CUDA(cudaFuncGetAttributes(&fa, (const void *)k_rows_block<float, uint16_t, false, kWideWarps>));
+        const int64_t room = (int64_t)optin - (int64_t)fa.sharedSizeBytes;
+        top = std::min<int64_t>(kBlockTop, room / block_bytes<uint16_t>(512) * 512);
+        GIFT_REQUIRE(top >= 1024, "gift_build_graph: too little shared memory for the block tier");
+    }
+    DevBuf gscratch;
     int64_t gcap = 0;
-    if (maxraw > kBlockCap) {
-        gcap = 2;
-        while (gcap < maxraw) gcap <<= 1;
-        gkeys = DevBuf(ctx, sizeof(uint64_t) * gcap * ctx->num_sms, st);
+    int ggrid = 0;
+    if (maxraw > kWarpCap && maxneed > top) {
+        gcap = (maxneed + 511) / 512 * 512;
+        const int64_t per = block_bytes<uint32_t>(gcap);
+        ggrid = (int)std::max<int64_t>(1, std::min<int64_t>(ctx->num_sms, ((int64_t)1 << 30) / per));
+        gscratch = DevBuf(ctx, (size_t)per * ggrid, st);
     }
     auto rows = [&](auto tag) {
         using WT = decltype(tag);
@@ -1118,26 +1359,34 @@ void build_graph_impl(gift_ctx *ctx, const gift_netlist *nl, const gift_build_op
         }
         if (maxraw > kWarpCap) {
             LaunchTimer lt(ctx, st, "build.rows_block", 0.0);
-            const void *fn = (const void *)k_rows_block<WT, false>;
-            GIFT_CUDA(cudaFuncSetAttribute(fn, cudaFuncAttributeMaxDynamicSharedMemorySize,
-                                           (int)((sizeof(uint64_t) + sizeof(WT)) * kBlockCap)));
-            for (int64_t lo = kWarpCap, cap = 1024; lo < std::min<int64_t>(maxraw, kBlockCap); lo = cap, cap <<= 1) {
-                const size_t smem = (sizeof(uint64_t) + sizeof(WT)) * cap;
+            auto launch = [&](auto nw, int64_t lo, int64_t cap) {
+                constexpr int NW = decltype(nw)::value;
+                const void *fn = (const void *)k_rows_block<WT, uint16_t, false, NW>;
+                const size_t smem = (size_t)block_bytes<uint16_t>(cap);
+                GIFT_CUDA(cudaFuncSetAttribute(fn, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem));
                 int per_sm = 0;
-                GIFT_CUDA(cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, fn, kBlockThreads, smem));
-                k_rows_block<WT, false><<<ctx->num_sms * std::max(per_sm, 1), kBlockThreads, smem, st>>>(
+                GIFT_CUDA(cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, fn, NW * 32, smem));
+                k_rows_block<WT, uint16_t, false, NW><<<ctx->num_sms * std::max(per_sm, 1), NW * 32, smem, st>>>(
                     inc_ptr_p, inc_net_p, g->net_ptr, g->pin_cell, wnet_p,
                     raw_ptr.as<int64_t>(), out_col.as<int32_t>(), ov, ucount_p, g->degree,
-                    big_p, bc, nullptr, 0, lo, cap);
+                    big_p, bc, nullptr, lo, cap, N, cell_bits, net_bits);
                 check_launch("k_rows_block");
+            };
+            int64_t lo = kWarpCap;
+            for (const int64_t c : kBlockClasses) {
+                const int64_t cap = std::min(c, top);
+                if (lo >= std::min(maxneed, top)) break;
+                if (cap <= kNarrowCap) launch(std::integral_constant<int, kNarrowWarps>{}, lo, cap);
+                else launch(std::integral_constant<int, kWideWarps>{}, lo, cap);
+                lo = cap;
             }
         }
-        if (maxraw > kBlockCap) {
+        if (gcap > 0) {
             LaunchTimer lt(ctx, st, "build.rows_global", 0.0);
-            k_rows_block<WT, true><<<ctx->num_sms, kBlockThreads, 0, st>>>(
+            k_rows_block<WT, uint32_t, true, kWideWarps><<<ggrid, kWideWarps * 32, 0, st>>>(
                 inc_ptr_p, inc_net_p, g->net_ptr, g->pin_cell, wnet_p,
                 raw_ptr.as<int64_t>(), out_col.as<int32_t>(), ov, ucount_p, g->degree,
-                big_p, bc, gkeys.as<uint64_t>(), gcap, kBlockCap, kBlockCap);
+                big_p, bc, gscratch.as<char>(), top, gcap, N, cell_bits, net_bits);
             check_launch("k_rows_block<global>");
         }
     };
