@@ -728,6 +728,66 @@ constexpr int64_t kBlockClasses[] = {1024, 1536, 2048, 3072, 4096, 6144, 8192, 1
 constexpr int64_t kNarrowCap = 3072;
 constexpr int kNarrowWarps = 4, kWideWarps = 8;
 
+// The long rows binned by class before the class launches, so that each
+// launch walks only its own rows: bin b holds the rows with
+// cap[b - 1] < slots <= cap[b] (cap[-1] = kWarpCap).
+constexpr int kMaxBins = 16;
+struct BlockBins {
+    int64_t cap[kMaxBins];
+    int n;
+};
+
+__device__ __forceinline__ int bin_of(const BlockBins &bins, int64_t slots) {
+    int b = 0;
+    while (b < bins.n - 1 && slots > bins.cap[b]) ++b;
+    return b;
+}
+
+__device__ __forceinline__ int64_t row_slots(const int64_t *__restrict__ raw_ptr, const int64_t *__restrict__ inc_ptr,
+                                             int32_t row) {
+    return raw_ptr[row + 1] - raw_ptr[row] + inc_ptr[row + 1] - inc_ptr[row];
+}
+
+__global__ void k_bin_count(const int32_t *__restrict__ big_rows, const int32_t *__restrict__ big_count,
+                            const int64_t *__restrict__ raw_ptr, const int64_t *__restrict__ inc_ptr, BlockBins bins,
+                            int32_t *__restrict__ bin_cnt) {
+    __shared__ int32_t s[kMaxBins];
+    if (threadIdx.x < kMaxBins) s[threadIdx.x] = 0;
+    __syncthreads();
+    const int n = *big_count;
+    for (int i = blockIdx.x * blockDim.x + threadIdx.x; i < n; i += gridDim.x * blockDim.x)
+        atomicAdd(&s[bin_of(bins, row_slots(raw_ptr, inc_ptr, big_rows[i]))], 1);
+    __syncthreads();
+    if (threadIdx.x < bins.n && s[threadIdx.x]) atomicAdd(&bin_cnt[threadIdx.x], s[threadIdx.x]);
+}
+
+// bin_off[b] = rows of the bins before b (bin_off[n] = all); the rows placed
+// at bin_off[b] + a running count (the order within a bin does not matter:
+// each row's result depends on that row alone).
+__global__ void k_bin_place(const int32_t *__restrict__ big_rows, const int32_t *__restrict__ big_count,
+                            const int64_t *__restrict__ raw_ptr, const int64_t *__restrict__ inc_ptr, BlockBins bins,
+                            const int32_t *__restrict__ bin_cnt, int32_t *__restrict__ bin_fill,
+                            int32_t *__restrict__ bin_off, int32_t *__restrict__ binned) {
+    __shared__ int32_t s_off[kMaxBins + 1];
+    if (threadIdx.x == 0) {
+        int32_t o = 0;
+        for (int b = 0; b < bins.n; ++b) {
+            s_off[b] = o;
+            o += bin_cnt[b];
+        }
+        s_off[bins.n] = o;
+        if (blockIdx.x == 0)
+            for (int b = 0; b <= bins.n; ++b) bin_off[b] = s_off[b];
+    }
+    __syncthreads();
+    const int n = *big_count;
+    for (int i = blockIdx.x * blockDim.x + threadIdx.x; i < n; i += gridDim.x * blockDim.x) {
+        const int32_t row = big_rows[i];
+        const int b = bin_of(bins, row_slots(raw_ptr, inc_ptr, row));
+        binned[s_off[b] + atomicAdd(&bin_fill[b], 1)] = row;
+    }
+}
+
 // Bytes of a block's buffers for C slots (C a multiple of 512) with payload
 // type KT: cells and payloads twice (the sort's two sides), then the sorted
 // incidences' nets (at most C / 2: every incidence has >= 2 pins).  While the
@@ -855,8 +915,8 @@ k_rows_block(const int64_t *__restrict__ inc_ptr, const int32_t *__restrict__ in
              const int64_t *__restrict__ net_ptr, const int32_t *__restrict__ pin_cell,
              const double *__restrict__ wnet, const int64_t *__restrict__ raw_ptr, int32_t *__restrict__ out_col,
              WT *__restrict__ out_val, int32_t *__restrict__ ucount, double *__restrict__ degree,
-             const int32_t *__restrict__ big_rows, const int32_t *__restrict__ big_count, char *__restrict__ gscratch,
-             int64_t lo, int64_t cap, int32_t N, int cell_bits, int net_bits) {
+             const int32_t *__restrict__ binned, const int32_t *__restrict__ bin_off, int bin,
+             char *__restrict__ gscratch, int64_t cap, int32_t N, int cell_bits, int net_bits) {
     constexpr int T = NW * 32;
     extern __shared__ __align__(16) char smem_dyn[];
     __shared__ uint32_t cnt[NW * kHistStride];
@@ -877,14 +937,14 @@ k_rows_block(const int64_t *__restrict__ inc_ptr, const int32_t *__restrict__ in
     int32_t *inc_e = reinterpret_cast<int32_t *>(kb + C);
     uint32_t *ofs = cb;                                        // while generating
     int64_t *pbase = reinterpret_cast<int64_t *>(cb + C / 2);  // while generating
-    const int nrows = *big_count;
-    for (int r = blockIdx.x; r < nrows; r += gridDim.x) {
-        const int32_t row = big_rows[r];
+    const int rows_end = bin_off[bin + 1];
+    for (int r = bin_off[bin] + blockIdx.x; r < rows_end; r += gridDim.x) {
+        const int32_t row = binned[r];
         const int64_t rbase = raw_ptr[row];
         const int64_t ib = inc_ptr[row];
         const int64_t ninc64 = inc_ptr[row + 1] - ib;
         const int64_t need = raw_ptr[row + 1] - rbase + ninc64;
-        if (need <= lo || need > cap) continue;
+        if (need > cap) continue;  // (the binning puts no such row here)
         const int ninc = (int)ninc64, n = (int)need;
         const bool staged = ninc <= kIncW;
 
@@ -1272,15 +1332,19 @@ void build_graph_impl(gift_ctx *ctx, const gift_netlist *nl, const gift_build_op
     // counts and the per-net stored weights
     const size_t wsz = g->weight_dtype == GIFT_WEIGHT_F32 ? 4 : 2;
     Carve cb;
-    const size_t o_fill = cb.take(sizeof(int32_t) * N), o_counts = cb.take(sizeof(int32_t) * 2);
+    const size_t o_fill = cb.take(sizeof(int32_t) * N), o_counts = cb.take(sizeof(int32_t) * (3 + 3 * kMaxBins));
     const size_t zeroed_b = cb.off;
     const size_t o_incnet = cb.take(sizeof(int32_t) * std::max<int64_t>(ninc, 1)),
                  o_ucount = cb.take(sizeof(int32_t) * N), o_wlist = cb.take(sizeof(int32_t) * N),
-                 o_big = cb.take(sizeof(int32_t) * N), o_wst = cb.take(wsz * std::max(E, 1));
+                 o_big = cb.take(sizeof(int32_t) * N), o_wst = cb.take(wsz * std::max(E, 1)),
+                 o_binned = cb.take(sizeof(int32_t) * (maxraw > kWarpCap ? N : 1));
     DevBuf arena_b(ctx, cb.off, st);
     char *B = static_cast<char *>(arena_b.p);
     int32_t *fill_p = reinterpret_cast<int32_t *>(B + o_fill);
-    int32_t *counts_p = reinterpret_cast<int32_t *>(B + o_counts);  // [0] warp-tier rows, [1] block-tier rows
+    // [0] warp-tier rows, [1] block-tier rows, then per bin: rows, placed rows, offsets
+    int32_t *counts_p = reinterpret_cast<int32_t *>(B + o_counts);
+    int32_t *bin_cnt = counts_p + 2, *bin_fill = bin_cnt + kMaxBins, *bin_off = bin_fill + kMaxBins;
+    int32_t *binned_p = reinterpret_cast<int32_t *>(B + o_binned);
     int32_t *inc_net_p = reinterpret_cast<int32_t *>(B + o_incnet);
     int32_t *ucount_p = reinterpret_cast<int32_t *>(B + o_ucount);
     int32_t *wlist_p = reinterpret_cast<int32_t *>(B + o_wlist);
@@ -1357,9 +1421,21 @@ void build_graph_impl(gift_ctx *ctx, const gift_netlist *nl, const gift_build_op
                 ucount_p, g->degree, big_p, bc);
             check_launch("k_rows_warp");
         }
+        // the classes: caps clamped to the device's largest, then global scratch
+        BlockBins bins{};
+        for (const int64_t c : kBlockClasses) {
+            const int64_t cap = std::min(c, top);
+            if (bins.n == 0 || cap > bins.cap[bins.n - 1]) bins.cap[bins.n++] = cap;
+        }
+        bins.cap[bins.n++] = INT64_MAX;
         if (maxraw > kWarpCap) {
             LaunchTimer lt(ctx, st, "build.rows_block", 0.0);
-            auto launch = [&](auto nw, int64_t lo, int64_t cap) {
+            const int bgrid = ctx->num_sms * 2;
+            k_bin_count<<<bgrid, 256, 0, st>>>(big_p, bc, raw_ptr.as<int64_t>(), inc_ptr_p, bins, bin_cnt);
+            k_bin_place<<<bgrid, 256, 0, st>>>(big_p, bc, raw_ptr.as<int64_t>(), inc_ptr_p, bins, bin_cnt, bin_fill,
+                                                 bin_off, binned_p);
+            check_launch("k_bin_place");
+            auto launch = [&](auto nw, int bin, int64_t cap) {
                 constexpr int NW = decltype(nw)::value;
                 const void *fn = (const void *)k_rows_block<WT, uint16_t, false, NW>;
                 const size_t smem = (size_t)block_bytes<uint16_t>(cap);
@@ -1369,16 +1445,12 @@ void build_graph_impl(gift_ctx *ctx, const gift_netlist *nl, const gift_build_op
                 k_rows_block<WT, uint16_t, false, NW><<<ctx->num_sms * std::max(per_sm, 1), NW * 32, smem, st>>>(
                     inc_ptr_p, inc_net_p, g->net_ptr, g->pin_cell, wnet_p,
                     raw_ptr.as<int64_t>(), out_col.as<int32_t>(), ov, ucount_p, g->degree,
-                    big_p, bc, nullptr, lo, cap, N, cell_bits, net_bits);
+                    binned_p, bin_off, bin, nullptr, cap, N, cell_bits, net_bits);
                 check_launch("k_rows_block");
             };
-            int64_t lo = kWarpCap;
-            for (const int64_t c : kBlockClasses) {
-                const int64_t cap = std::min(c, top);
-                if (lo >= std::min(maxneed, top)) break;
-                if (cap <= kNarrowCap) launch(std::integral_constant<int, kNarrowWarps>{}, lo, cap);
-                else launch(std::integral_constant<int, kWideWarps>{}, lo, cap);
-                lo = cap;
+            for (int b = 0, lo = (int)kWarpCap; b + 1 < bins.n && lo < std::min(maxneed, top); lo = (int)bins.cap[b++]) {
+                if (bins.cap[b] <= kNarrowCap) launch(std::integral_constant<int, kNarrowWarps>{}, b, bins.cap[b]);
+                else launch(std::integral_constant<int, kWideWarps>{}, b, bins.cap[b]);
             }
         }
         if (gcap > 0) {
@@ -1386,7 +1458,7 @@ void build_graph_impl(gift_ctx *ctx, const gift_netlist *nl, const gift_build_op
             k_rows_block<WT, uint32_t, true, kWideWarps><<<ggrid, kWideWarps * 32, 0, st>>>(
                 inc_ptr_p, inc_net_p, g->net_ptr, g->pin_cell, wnet_p,
                 raw_ptr.as<int64_t>(), out_col.as<int32_t>(), ov, ucount_p, g->degree,
-                big_p, bc, gscratch.as<char>(), top, gcap, N, cell_bits, net_bits);
+                binned_p, bin_off, bins.n - 1, gscratch.as<char>(), gcap, N, cell_bits, net_bits);
             check_launch("k_rows_block<global>");
         }
     };
