@@ -258,16 +258,18 @@ def sweep_source_hash() -> str:
 
 
 def recorded_traffic(kernel: str, workload: str, weights: str, schedule):
-    """DRAM bytes per launch from a committed ncu summary, if it was taken on
-    the current kernel source with the same tuned schedule."""
+    """DRAM bytes per launch from a committed ncu summary, if one was taken on
+    the current kernel source with the same tuned schedule (the tuner may pick
+    either of two near-equal shapes, so a workload keeps one record per
+    schedule captured)."""
     path = os.path.join(ROOT, "profiles", "traffic.json")
     try:
         with open(path) as f:
             rec = json.load(f)
-        r = rec[kernel][f"{workload}/{weights}"]
-        if r.get("source_hash") != sweep_source_hash() or list(r.get("sweep_schedule", [])) != list(schedule):
-            return None
-        return r["dram_bytes_per_launch"]
+        for r in rec[kernel][f"{workload}/{weights}"]:
+            if r.get("source_hash") == sweep_source_hash() and list(r.get("sweep_schedule", [])) == list(schedule):
+                return r["dram_bytes_per_launch"]
+        return None
     except Exception:
         return None
 
@@ -295,7 +297,7 @@ def record_traffic(args):
     if os.path.exists(path):
         with open(path) as f:
             rec = json.load(f)
-    rec.setdefault("filter.sweep", {})[f"{args.workload}/{args.weights}"] = {
+    entry = {
         "dram_bytes_per_launch": sum(p["dram_read"] + p["dram_write"] for p in per) / max(len(per), 1),
         "per_launch": per, "source_hash": sweep_source_hash(),
         "sweep_schedule": [int(x) for x in args.schedule.split(",")] if args.schedule else [],
@@ -303,10 +305,15 @@ def record_traffic(args):
                    "--clock-control none --nvtx --nvtx-include capture/ -k regex:k_sweep --csv --log-file "
                    "traffic_full.csv python bench.py --capture",
         "note": "all sweep launches of one tuned filter call on the full workload (1 pass per launch)"}
+    # one record per (source, schedule): a new capture replaces its own and drops records of older sources
+    old = rec.setdefault("filter.sweep", {}).get(f"{args.workload}/{args.weights}", [])
+    keep = [r for r in old if r.get("source_hash") == entry["source_hash"]
+            and r.get("sweep_schedule") != entry["sweep_schedule"]]
+    rec["filter.sweep"][f"{args.workload}/{args.weights}"] = keep + [entry]
     with open(path, "w") as f:
         json.dump(rec, f, indent=1)
         f.write("\n")
-    print(json.dumps(rec["filter.sweep"][f"{args.workload}/{args.weights}"]["dram_bytes_per_launch"]))
+    print(json.dumps(entry["dram_bytes_per_launch"]))
 
 
 # ----------------------------------------------------------------- oracle (CPU)

@@ -972,31 +972,38 @@ ShapeSet autotune(gift_ctx *ctx, const Plan &p, cudaStream_t st) {
     auto cleanup = [&] {
         for (auto e : pool) cudaEventDestroy(e);
     };
-    // one warm run and one timed run of the whole filter; per planned kind ms
+    // one warm run, then the least of kTuneRuns timed runs of the whole
+    // filter; per planned kind ms
+    constexpr int kTuneRuns = 3;
     auto measure = [&](const ShapeSet &ss, double (&ms)[4], bool (&seen)[4]) {
         GIFT_CUDA(cudaMemsetAsync(p.counters, 0, sizeof(int32_t) * p.ncounters, st));
         run_sweeps(ctx, p, ss, st);
-        GIFT_CUDA(cudaMemsetAsync(p.counters, 0, sizeof(int32_t) * p.ncounters, st));
-        std::vector<TimedLaunch> timed;
-        std::vector<cudaEvent_t> avail = pool;
-        const size_t need = 2 * (size_t)(p.Lmax * (p.chains.size() + 1) * (p.K / 2 + 1));
-        while (avail.size() < need) {
-            cudaEvent_t e;
-            GIFT_CUDA(cudaEventCreate(&e));
-            pool.push_back(e);
-            avail.push_back(e);
-        }
-        run_sweeps(ctx, p, ss, st, &timed, &avail);
-        GIFT_CUDA(cudaStreamSynchronize(st));
         for (int kd = 0; kd < 4; ++kd) {
-            ms[kd] = 0.0;
+            ms[kd] = 1e30;
             seen[kd] = false;
         }
-        for (const TimedLaunch &t : timed) {
-            float m = 0.f;
-            GIFT_CUDA(cudaEventElapsedTime(&m, t.e0, t.e1));
-            ms[t.kind] += m;
-            seen[t.kind] = true;
+        for (int run = 0; run < kTuneRuns; ++run) {
+            GIFT_CUDA(cudaMemsetAsync(p.counters, 0, sizeof(int32_t) * p.ncounters, st));
+            std::vector<TimedLaunch> timed;
+            std::vector<cudaEvent_t> avail = pool;
+            const size_t need = 2 * (size_t)(p.Lmax * (p.chains.size() + 1) * (p.K / 2 + 1));
+            while (avail.size() < need) {
+                cudaEvent_t e;
+                GIFT_CUDA(cudaEventCreate(&e));
+                pool.push_back(e);
+                avail.push_back(e);
+            }
+            run_sweeps(ctx, p, ss, st, &timed, &avail);
+            GIFT_CUDA(cudaStreamSynchronize(st));
+            double sum[4] = {0.0, 0.0, 0.0, 0.0};
+            for (const TimedLaunch &t : timed) {
+                float m = 0.f;
+                GIFT_CUDA(cudaEventElapsedTime(&m, t.e0, t.e1));
+                sum[t.kind] += m;
+                seen[t.kind] = true;
+            }
+            for (int kd = 0; kd < 4; ++kd)
+                if (seen[kd]) ms[kd] = std::min(ms[kd], sum[kd]);
         }
     };
     try {

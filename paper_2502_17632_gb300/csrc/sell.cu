@@ -169,11 +169,14 @@ __global__ void __launch_bounds__(256) k_sort_place(int64_t n, const int64_t *__
 
 // A warp per 32 consecutive slots: their entries are one contiguous range of
 // the copy, written lane by lane (coalesced); lane l finds the slot of its
-// entry by a binary search over the 32 slot starts held one per lane.
+// entry by a binary search over the 32 slot starts held one per lane.  Four
+// rounds of 32 entries are read before any is written, so that a lane has
+// up to eight loads in flight.
 template <typename WT>
 __global__ void k_copy_sorted(int64_t n, const int64_t *__restrict__ row_ptr, const int32_t *__restrict__ col,
                               const WT *__restrict__ val, const int32_t *__restrict__ perm,
                               const int64_t *__restrict__ rp2, int32_t *__restrict__ col2, WT *__restrict__ val2) {
+    constexpr int R = 4;
     const int lane = threadIdx.x & 31;
     const int64_t warp = (blockIdx.x * (int64_t)blockDim.x + threadIdx.x) >> 5;
     const int64_t nwarps = ((int64_t)gridDim.x * blockDim.x) >> 5;
@@ -183,20 +186,35 @@ __global__ void k_copy_sorted(int64_t n, const int64_t *__restrict__ row_ptr, co
         const int64_t src = s < n ? row_ptr[perm[s]] : 0;            // the row's first entry in the CSR
         const int64_t b = __shfl_sync(0xffffffffu, start, 0);
         const int64_t e = rp2[s0 + 32 < n ? s0 + 32 : n];
-        for (int64_t p0 = b; p0 < e; p0 += 32) {  // same trip count on every lane
-            const int64_t p = p0 + lane;
-            int lo = 0;  // last slot i of the 32 with start_i <= p
+        for (int64_t p0 = b; p0 < e; p0 += 32 * R) {  // same trip count on every lane
+            int64_t at[R];
 #pragma unroll
-            for (int step = 16; step >= 1; step >>= 1) {
-                const int64_t v = __shfl_sync(0xffffffffu, start, lo + step);
-                if (v <= p) lo += step;
+            for (int r = 0; r < R; ++r) {
+                const int64_t p = p0 + 32 * r + lane;
+                int lo = 0;  // last slot i of the 32 with start_i <= p
+#pragma unroll
+                for (int step = 16; step >= 1; step >>= 1) {
+                    const int64_t v = __shfl_sync(0xffffffffu, start, lo + step);
+                    if (v <= p) lo += step;
+                }
+                const int64_t si = __shfl_sync(0xffffffffu, start, lo);
+                const int64_t sr = __shfl_sync(0xffffffffu, src, lo);
+                at[r] = p < e ? sr + (p - si) : -1;
             }
-            const int64_t si = __shfl_sync(0xffffffffu, start, lo);
-            const int64_t sr = __shfl_sync(0xffffffffu, src, lo);
-            if (p < e) {
-                col2[p] = col[sr + (p - si)];
-                val2[p] = val[sr + (p - si)];
-            }
+            int32_t c[R];
+            WT w[R];
+#pragma unroll
+            for (int r = 0; r < R; ++r)
+                if (at[r] >= 0) {
+                    c[r] = col[at[r]];
+                    w[r] = val[at[r]];
+                }
+#pragma unroll
+            for (int r = 0; r < R; ++r)
+                if (at[r] >= 0) {
+                    col2[p0 + 32 * r + lane] = c[r];
+                    val2[p0 + 32 * r + lane] = w[r];
+                }
         }
     }
 }

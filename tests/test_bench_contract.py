@@ -56,15 +56,20 @@ def test_recorded_traffic_is_tied_to_source_and_schedule(monkeypatch):
         rec = json.load(f)["filter.sweep"]
     key = next(iter(rec))
     workload, weights = key.split("/")
-    entry = rec[key]
-    sched = entry["sweep_schedule"]
-    want = entry["dram_bytes_per_launch"]
-    # the per-launch mean is the mean of the recorded launches
-    per = entry["per_launch"]
-    assert want == pytest.approx(sum(p["dram_read"] + p["dram_write"] for p in per) / len(per))
-    monkeypatch.setattr(bench, "sweep_source_hash", lambda: entry["source_hash"])
-    assert bench.recorded_traffic("filter.sweep", workload, weights, sched) == want
-    assert bench.recorded_traffic("filter.sweep", workload, weights, list(reversed(sched))) is None
-    assert bench.recorded_traffic("filter.sweep", workload, "bf16" if weights != "bf16" else "f32", sched) is None
-    monkeypatch.setattr(bench, "sweep_source_hash", lambda: "0" * 16)
-    assert bench.recorded_traffic("filter.sweep", workload, weights, sched) is None
+    entries = rec[key]
+    scheds = [e["sweep_schedule"] for e in entries]
+    assert len({tuple(s) for s in scheds}) == len(scheds)  # one record per schedule
+    for entry in entries:
+        sched = entry["sweep_schedule"]
+        want = entry["dram_bytes_per_launch"]
+        # the per-launch mean is the mean of the recorded launches
+        per = entry["per_launch"]
+        assert want == pytest.approx(sum(p["dram_read"] + p["dram_write"] for p in per) / len(per))
+        monkeypatch.setattr(bench, "sweep_source_hash", lambda: entry["source_hash"])
+        assert bench.recorded_traffic("filter.sweep", workload, weights, sched) == want
+        if list(reversed(sched)) not in scheds:
+            assert bench.recorded_traffic("filter.sweep", workload, weights, list(reversed(sched))) is None
+        assert bench.recorded_traffic("filter.sweep", workload, "bf16" if weights != "bf16" else "f32",
+                                      sched) is None
+        monkeypatch.setattr(bench, "sweep_source_hash", lambda: "0" * 16)
+        assert bench.recorded_traffic("filter.sweep", workload, weights, sched) is None
