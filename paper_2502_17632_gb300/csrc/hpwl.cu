@@ -129,6 +129,15 @@ k_hpwl(int32_t E, int32_t S, const int64_t *__restrict__ net_ptr, const int32_t 
     }
 }
 
+// A piece of a pin's location row; a miss fetches only the 64 bytes around
+// it (the rows are gathered at random: a 128-byte fill per miss was half
+// another cell's row).
+__device__ __forceinline__ float4 ld_row(const float4 *p) {
+    float4 v;
+    asm("ld.global.nc.L2::64B.v4.f32 {%0,%1,%2,%3}, [%4];" : "=f"(v.x), "=f"(v.y), "=f"(v.z), "=f"(v.w) : "l"(p));
+    return v;
+}
+
 // Even S, 16-byte aligned locations: a group of GH lanes per net, lane q of a
 // group covering signals s0 + 2q, s0 + 2q + 1 with one float4 per pin, so a
 // group reads a pin's whole row piece in one access; 4 pins in flight per
@@ -167,7 +176,7 @@ k_hpwl_groups(int32_t E, int32_t S, const int64_t *__restrict__ net_ptr, const i
                 float4 v[4];
 #pragma unroll
                 for (int u = 0; u < 4; ++u)
-                    v[u] = (c[u] >= 0 && on) ? __ldg(xy4 + (int64_t)c[u] * half + qq) : make_float4(0.f, 0.f, 0.f, 0.f);
+                    v[u] = (c[u] >= 0 && on) ? ld_row(xy4 + (int64_t)c[u] * half + qq) : make_float4(0.f, 0.f, 0.f, 0.f);
 #pragma unroll
                 for (int u = 0; u < 4; ++u)
                     if (c[u] >= 0) {

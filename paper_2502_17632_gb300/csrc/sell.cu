@@ -167,6 +167,29 @@ __global__ void __launch_bounds__(256) k_sort_place(int64_t n, const int64_t *__
     }
 }
 
+// Read-only loads whose misses fetch only the 64 bytes around the request
+// (the rows copied here are short runs at random places: a 128-byte fill
+// per miss was mostly bytes of other rows).
+__device__ __forceinline__ int32_t ld64b(const int32_t *p) {
+    int32_t v;
+    asm("ld.global.nc.L2::64B.b32 %0, [%1];" : "=r"(v) : "l"(p));
+    return v;
+}
+__device__ __forceinline__ float ld64b(const float *p) {
+    float v;
+    asm("ld.global.nc.L2::64B.f32 %0, [%1];" : "=f"(v) : "l"(p));
+    return v;
+}
+template <typename T>
+__device__ __forceinline__ T ld64b(const T *p) {  // 16-bit weights
+    static_assert(sizeof(T) == 2, "16-bit weight types");
+    unsigned short v;
+    asm("ld.global.nc.L2::64B.b16 %0, [%1];" : "=h"(v) : "l"(p));
+    T t;
+    memcpy(&t, &v, 2);
+    return t;
+}
+
 // A warp per 32 consecutive slots: their entries are one contiguous range of
 // the copy, written lane by lane (coalesced); lane l finds the slot of its
 // entry by a binary search over the 32 slot starts held one per lane.  Four
@@ -206,8 +229,8 @@ __global__ void k_copy_sorted(int64_t n, const int64_t *__restrict__ row_ptr, co
 #pragma unroll
             for (int r = 0; r < R; ++r)
                 if (at[r] >= 0) {
-                    c[r] = col[at[r]];
-                    w[r] = val[at[r]];
+                    c[r] = ld64b(col + at[r]);
+                    w[r] = ld64b(val + at[r]);
                 }
 #pragma unroll
             for (int r = 0; r < R; ++r)
