@@ -301,10 +301,12 @@ __global__ void k_net_stored(int32_t E, const double *__restrict__ wnet, WT *__r
 constexpr int kLaneCap = 32;  // raw entries of a row in the lane tier
 constexpr int kLaneThreads = 128;
 
-// Batcher's odd-even merge sort, ascending, on R registers (R a power of two).
-// The comparator list is generated at compile time and expanded into
-// straight-line code, so the array stays in registers and each comparator is
-// a min and a max.
+// Batcher's odd-even merge sort, ascending, on R registers (R a power of two),
+// or on the first N of them: padded with the largest key, positions N and
+// up hold padding throughout (a comparator only moves the larger key up), so
+// every comparator that reaches past N is dropped.  The comparator list is
+// generated at compile time and expanded into straight-line code, so the
+// array stays in registers and each comparator is a min and a max.
 template <typename K>
 __device__ __forceinline__ void cmp_swap(K &a, K &b) {
     const K lo = a < b ? a : b, hi = a < b ? b : a;
@@ -316,7 +318,7 @@ struct CmpPair {
     int a, b;
 };
 
-template <int R>
+template <int R, int N = R>
 struct OddEvenNet {
     template <class F>
     static constexpr void visit(F &&f) {
@@ -324,7 +326,7 @@ struct OddEvenNet {
             for (int s = p; s >= 1; s /= 2)
                 for (int j = s % p; j + s < R; j += 2 * s)
                     for (int i = 0; i < s && i + j + s < R; ++i)
-                        if ((i + j) / (2 * p) == (i + j + s) / (2 * p)) f(i + j, i + j + s);
+                        if ((i + j) / (2 * p) == (i + j + s) / (2 * p) && i + j + s < N) f(i + j, i + j + s);
     }
     static constexpr int count() {
         int c = 0;
@@ -344,19 +346,19 @@ struct OddEvenNet {
     static constexpr Table kTable = table();
 };
 
-template <int A, int B, int R, typename K>
-__device__ __forceinline__ void cmp_swap_at(K (&k)[R]) {
+template <int A, int B, int N, typename K>
+__device__ __forceinline__ void cmp_swap_at(K (&k)[N]) {
     cmp_swap(k[A], k[B]);
 }
 
-template <int R, typename K, int... Is>
-__device__ __forceinline__ void apply_net(K (&k)[R], std::integer_sequence<int, Is...>) {
-    (cmp_swap_at<OddEvenNet<R>::kTable.v[Is].a, OddEvenNet<R>::kTable.v[Is].b>(k), ...);
+template <int R, int N, typename K, int... Is>
+__device__ __forceinline__ void apply_net(K (&k)[N], std::integer_sequence<int, Is...>) {
+    (cmp_swap_at<OddEvenNet<R, N>::kTable.v[Is].a, OddEvenNet<R, N>::kTable.v[Is].b>(k), ...);
 }
 
-template <int R, typename K>
-__device__ __forceinline__ void oddeven_merge_sort(K (&k)[R]) {
-    apply_net<R>(k, std::make_integer_sequence<int, OddEvenNet<R>::kCount>{});
+template <int R, int N = R, typename K>
+__device__ __forceinline__ void oddeven_merge_sort(K (&k)[N]) {
+    apply_net<R, N>(k, std::make_integer_sequence<int, OddEvenNet<R, N>::kCount>{});
 }
 
 // The row's incidences (net ids) in increasing order, into sinc[.][tid].
@@ -372,15 +374,16 @@ __device__ __forceinline__ void lane_sort_incidences(const int32_t *__restrict__
         if (i < ninc) sinc[i][tid] = e[i];
 }
 
-// The row's n keys (neighbour << 5 | incidence), sorted in place in skey[.][tid].
-template <int R, typename K, int T>
+// The row's n <= N keys (neighbour << 5 | incidence), sorted in place in
+// skey[.][tid] by the R-input network cut to N.
+template <int R, int N, typename K, int T>
 __device__ __forceinline__ void lane_sort_keys(int n, K (*skey)[T], int tid) {
-    K k[R];
+    K k[N];
 #pragma unroll
-    for (int i = 0; i < R; ++i) k[i] = i < n ? skey[i][tid] : ~K(0);
-    oddeven_merge_sort<R>(k);
+    for (int i = 0; i < N; ++i) k[i] = i < n ? skey[i][tid] : ~K(0);
+    oddeven_merge_sort<R, N>(k);
 #pragma unroll
-    for (int i = 0; i < R; ++i)
+    for (int i = 0; i < N; ++i)
         if (i < n) skey[i][tid] = k[i];
 }
 
@@ -500,9 +503,15 @@ k_rows_lane(int32_t N, const int64_t *__restrict__ inc_ptr, const int32_t *__res
             }
         }
         const int max_n = (int)__reduce_max_sync(full, (unsigned)n);
-        if (max_n <= 8) lane_sort_keys<8>(n, skey, tid);
-        else if (max_n <= 16) lane_sort_keys<16>(n, skey, tid);
-        else lane_sort_keys<32>(n, skey, tid);
+        // the smallest network for the warp's longest row (comparator counts
+        // 19, 55, 63, 103, 132, 162, 191)
+        if (max_n <= 8) lane_sort_keys<8, 8>(n, skey, tid);
+        else if (max_n <= 12) lane_sort_keys<16, 12>(n, skey, tid);
+        else if (max_n <= 16) lane_sort_keys<16, 16>(n, skey, tid);
+        else if (max_n <= 20) lane_sort_keys<32, 20>(n, skey, tid);
+        else if (max_n <= 24) lane_sort_keys<32, 24>(n, skey, tid);
+        else if (max_n <= 28) lane_sort_keys<32, 28>(n, skey, tid);
+        else lane_sort_keys<32, 32>(n, skey, tid);
         if (!lane_row) continue;
 
         int u = 0;
