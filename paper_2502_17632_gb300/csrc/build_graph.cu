@@ -1448,7 +1448,9 @@ void build_graph_impl(gift_ctx *ctx, const gift_netlist *nl, const gift_build_op
                 constexpr int NW = decltype(nw)::value;
                 const void *fn = (const void *)k_rows_block<WT, uint16_t, false, NW>;
                 const size_t smem = (size_t)block_bytes<uint16_t>(cap);
-                GIFT_CUDA(cudaFuncSetAttribute(fn, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem));
+                // always the largest class's size: builds on other host threads set the same value
+                GIFT_CUDA(cudaFuncSetAttribute(fn, cudaFuncAttributeMaxDynamicSharedMemorySize,
+                                               (int)block_bytes<uint16_t>(top)));
                 int per_sm = 0;
                 GIFT_CUDA(cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, fn, NW * 32, smem));
                 k_rows_block<WT, uint16_t, false, NW><<<ctx->num_sms * std::max(per_sm, 1), NW * 32, smem, st>>>(
