@@ -721,9 +721,10 @@ __device__ __forceinline__ long long sat_add(long long a, long long b) {
 //      so that each cell's entries stay in increasing net order;
 //   5. each run of equal cells summed in FP64 in that order and rounded once;
 //      unique indices from per-warp counts of run heads.
-// A row takes raw entries + incidences ("slots"): the shared-memory classes
-// take the rows with lo < slots <= cap; GLOBAL puts the same buffers in a
-// per-block slice of global scratch for longer rows.  The degree is the
+// A row takes raw entries + incidences ("slots"): a shared-memory class
+// launch takes the rows of its bin (slots up to its cap, above the previous
+// class's); GLOBAL puts the same buffers in a per-block slice of global
+// scratch for the rows beyond the largest class.  The degree is the
 // block's exact fixed-point sum of the stored weights where that equals the
 // column-order FP64 sum (above), else one thread's FP64 sum in column order.
 constexpr int kRadixBits = 8;
