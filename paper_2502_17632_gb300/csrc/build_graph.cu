@@ -299,6 +299,7 @@ __global__ void k_net_stored(int32_t E, const double *__restrict__ wnet, WT *__r
 // over the stored weights in column order (Sec. 2.1).
 
 constexpr int kLaneCap = 32;  // raw entries of a row in the lane tier
+constexpr int kLaneInc = 16;  // incidences of a row in the lane tier
 constexpr int kLaneThreads = 128;
 
 // Batcher's odd-even merge sort, ascending, on R registers (R a power of two),
@@ -407,15 +408,21 @@ __device__ __forceinline__ unsigned long long units34(float w) {
 // 2^19 make each partial FP64 sum a multiple of 2^-34 below 2^53 units, so
 // the integer sum of units equals the column-order FP64 sum; otherwise the
 // row adds its stored weights in FP64 in column order.  Rows with more raw
-// entries go to `wlist` for the warp tier.  K is uint32 for at most 2^27
-// cells, else uint64 (with half the threads per block).
+// entries or more than kLaneInc incidences go to `wlist` for the warp tier
+// (few rows have that many nets within 32 raw entries, and the smaller
+// incidence array lets eight blocks share an SM).  K is uint32 for at most
+// 2^27 cells, else uint64 (with half the threads per block).
 template <typename K>
 __host__ __device__ constexpr int lane_threads() {
     return sizeof(K) == 4 ? kLaneThreads : kLaneThreads / 2;
 }
+template <typename K>
+__host__ __device__ constexpr int lane_blocks() {  // per SM
+    return sizeof(K) == 4 ? 8 : 10;
+}
 
 template <typename WT, typename K>
-__global__ void __launch_bounds__(lane_threads<K>(), 6)
+__global__ void __launch_bounds__(lane_threads<K>(), lane_blocks<K>())
 k_rows_lane(int32_t N, const int64_t *__restrict__ inc_ptr, const int32_t *__restrict__ inc_net,
             const int64_t *__restrict__ net_ptr, const int32_t *__restrict__ pin_cell,
             const double *__restrict__ wtab, const int64_t *__restrict__ raw_ptr, int32_t *__restrict__ out_col,
@@ -424,7 +431,7 @@ k_rows_lane(int32_t N, const int64_t *__restrict__ inc_ptr, const int32_t *__res
     constexpr int kMaxM = kLaneCap + 1;
     constexpr int T = lane_threads<K>();
     __shared__ K skey[kLaneCap][T];
-    __shared__ int32_t sinc[kLaneCap][T];  // net id, then the net's pin count M
+    __shared__ int32_t sinc[kLaneInc][T];  // net id, then the net's pin count M
     __shared__ double dtab[kMaxM + 1];                // 2/M in FP64 (weight rule after Eq. 4)
     __shared__ WT stab[kMaxM + 1];                    // 2/M as stored
     const unsigned full = 0xffffffffu;
@@ -445,8 +452,8 @@ k_rows_lane(int32_t N, const int64_t *__restrict__ inc_ptr, const int32_t *__res
             ib = inc_ptr[row];
             ninc = (int)(inc_ptr[row + 1] - ib);
         }
-        const bool lane_row = row < N && raw > 0 && raw <= kLaneCap;
-        const bool longer = row < N && raw > kLaneCap;
+        const bool lane_row = row < N && raw > 0 && raw <= kLaneCap && ninc <= kLaneInc;
+        const bool longer = row < N && raw > 0 && !lane_row;
         const unsigned lm = __ballot_sync(full, longer);
         if (lm) {
             const int leader = __ffs(lm) - 1;
@@ -463,8 +470,7 @@ k_rows_lane(int32_t N, const int64_t *__restrict__ inc_ptr, const int32_t *__res
         const int max_inc = (int)__reduce_max_sync(full, (unsigned)ninc);
         if (max_inc == 0) continue;
         if (max_inc <= 8) lane_sort_incidences<8>(inc_net + ib, ninc, sinc, tid);
-        else if (max_inc <= 16) lane_sort_incidences<16>(inc_net + ib, ninc, sinc, tid);
-        else lane_sort_incidences<32>(inc_net + ib, ninc, sinc, tid);
+        else lane_sort_incidences<kLaneInc>(inc_net + ib, ninc, sinc, tid);
 
         int n = 0;
         const int32_t self = (int32_t)row;
@@ -1410,20 +1416,20 @@ void build_graph_impl(gift_ctx *ctx, const gift_netlist *nl, const gift_build_op
             if (E > 0)
                 k_net_stored<WT><<<grid_for(ctx, E, 256), 256, 0, st>>>(E, wnet_p, wst);
             if (N <= (1 << 27))
-                k_rows_lane<WT, uint32_t><<<grid_for(ctx, N, lane_threads<uint32_t>(), 6),
+                k_rows_lane<WT, uint32_t><<<grid_for(ctx, N, lane_threads<uint32_t>(), lane_blocks<uint32_t>()),
                                             lane_threads<uint32_t>(), 0, st>>>(
                     N, inc_ptr_p, inc_net_p, g->net_ptr, g->pin_cell, ctx->wtab,
                     raw_ptr.as<int64_t>(), out_col.as<int32_t>(), ov, ucount_p, g->degree,
                     wlist_p, wc);
             else
-                k_rows_lane<WT, uint64_t><<<grid_for(ctx, N, lane_threads<uint64_t>(), 12),
+                k_rows_lane<WT, uint64_t><<<grid_for(ctx, N, lane_threads<uint64_t>(), lane_blocks<uint64_t>()),
                                             lane_threads<uint64_t>(), 0, st>>>(
                     N, inc_ptr_p, inc_net_p, g->net_ptr, g->pin_cell, ctx->wtab,
                     raw_ptr.as<int64_t>(), out_col.as<int32_t>(), ov, ucount_p, g->degree,
                     wlist_p, wc);
             check_launch("k_rows_lane");
         }
-        if (maxraw > kLaneCap) {
+        if (maxraw > kLaneInc) {  // rows of more raw entries or more incidences than the lane tier takes
             LaunchTimer lt(ctx, st, "build.rows_warp", 0.0);
             k_rows_warp<WT><<<ctx->num_sms * 6, kRowsWarps * 32, 0, st>>>(
                 wlist_p, wc, inc_ptr_p, inc_net_p, g->net_ptr, g->pin_cell,

@@ -440,28 +440,35 @@ def test_injected_oom_leaves_library_usable(ctx):
 
 
 def lane_tier_netlist(seed):
-    """Rows that drive every width of the lane tier's sorting networks (8,
-    16 and 32 incidences, 8 / 16 / 32 keys): cell 0 in 32 two-pin nets (32
-    raw entries, the tier's cap), cell 1 in 20, cell 2 in 12; cells 3..5 share
-    the same cell pairs through several nets (runs of 2, 3 and 5 nets, summed
-    in FP64 in net order), cell 6 holds a net twice (a repeated pin); the rest
-    random small nets with repeats on cells 100..699."""
+    """Rows that drive every width of the lane tier's sorting networks, one
+    such row per warp (cells 0, 32, 64, ...), and the rows just past its
+    caps: cell 0 in 32 two-pin nets and cell 32 in 20 (more than the 16
+    incidences the lane tier takes: the warp tier), cell 64 in 16 (the
+    incidence cap, 16 keys), cell 96 in 12; cell 128 in one net of 33 pins
+    (32 keys, the raw-entry cap), cell 160 in two nets of 15 pins (28 keys),
+    cell 192 in three of 9 (24), cell 224 in four of 6 (20); cells 256..258
+    share a cell pair through runs of 2, 3 and 5 nets (summed in FP64 in net
+    order), cell 288 holds a net twice (a repeated pin); the rest random
+    small nets with repeats on cells 320..899."""
     nets = []
-    for c, k in ((0, 32), (1, 20), (2, 12)):
+    for c, k in ((0, 32), (32, 20), (64, 16), (96, 12)):
         for t in range(k):
-            nets.append([c, 100 + (7 * t + 13 * c) % 600])
-    for c, run in ((3, 2), (4, 3), (5, 5)):
+            nets.append([c, 320 + (7 * t + 13 * c) % 580])
+    for c, count, pins in ((128, 1, 33), (160, 2, 15), (192, 3, 9), (224, 4, 6)):
+        for t in range(count):
+            nets.append([c] + [320 + (37 * t + 11 * q + c) % 580 for q in range(pins - 1)])
+    for c, run in ((256, 2), (257, 3), (258, 5)):
         for r in range(run):
-            nets.append([c, 50, 51 + r])  # cell pair (c, 50) in `run` nets of 3 pins
-    nets.append([6, 60, 6, 61])  # cell 6 twice in one net
-    small = synth.random_small(seed, 700, 900, 7, allow_repeat=True, min_pins=2)
-    for e in range(small.num_nets):  # on cells 100..699, away from the rows above
-        nets.append([100 + int(c) % 600 for c in small.pin_cell[small.net_ptr[e]:small.net_ptr[e + 1]]])
+            nets.append([c, 330, 331 + r])  # cell pair (c, 330) in `run` nets of 3 pins
+    nets.append([288, 340, 288, 341])  # cell 288 twice in one net
+    small = synth.random_small(seed, 580, 900, 7, allow_repeat=True, min_pins=2)
+    for e in range(small.num_nets):  # on cells 320..899, away from the rows above
+        nets.append([320 + int(c) for c in small.pin_cell[small.net_ptr[e]:small.net_ptr[e + 1]]])
     order = synth.u64(seed, 91, np.arange(len(nets), dtype=np.uint64)).argsort(kind="stable")  # shuffle the net ids
     nets = [nets[i] for i in order]
     net_ptr = np.concatenate([[0], np.cumsum([len(n) for n in nets])]).astype(np.int64)
     pin_cell = np.array([c for n in nets for c in n], dtype=np.int32)
-    return synth.Netlist(700, len(nets), net_ptr, pin_cell, np.zeros(700, np.uint8), np.zeros((700, 2), np.float32))
+    return synth.Netlist(900, len(nets), net_ptr, pin_cell, np.zeros(900, np.uint8), np.zeros((900, 2), np.float32))
 
 
 @pytest.mark.parametrize("wd", ["f32", "bf16", "f16"])
@@ -469,11 +476,18 @@ def lane_tier_netlist(seed):
 def test_lane_tier_network_widths(ctx, wd, seed):
     nl = lane_tier_netlist(seed)
     raw = np.zeros(nl.num_cells, dtype=np.int64)
+    inc = np.zeros(nl.num_cells, dtype=np.int64)
     for e in range(nl.num_nets):
         cells = nl.pin_cell[nl.net_ptr[e]:nl.net_ptr[e + 1]]
         for c in cells:
             raw[c] += len(cells) - 1
-    assert raw[0] == 32 and raw[1] == 20 and raw[2] == 12  # cap, and the 32- and 16-wide incidence networks
+            inc[c] += 1
+    # incidences past the lane tier's 16, at its cap, and below it
+    assert (inc[0], inc[32], inc[64], inc[96]) == (32, 20, 16, 12)
+    # keys: the raw-entry cap and the 28-, 24- and 20-key networks with few incidences
+    assert (raw[128], raw[160], raw[192], raw[224]) == (32, 28, 24, 20)
+    assert inc[128] == 1 and inc[160] == 2 and inc[192] == 3 and inc[224] == 4
+    assert raw[320:].max() <= 512
     h = build(ctx, nl, wd)
     try:
         rp, col, val, deg = gift.gift_graph_export(h)
