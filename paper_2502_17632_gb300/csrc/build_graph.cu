@@ -18,6 +18,7 @@
 //   compact  round each sum once to the storage type, write col/val, and
 //            d_i = sum_j A_ij in FP64 over the stored weights in column order.
 #include <algorithm>
+#include <type_traits>
 #include <utility>
 
 #include "internal.cuh"
@@ -62,8 +63,12 @@ __device__ __forceinline__ int32_t key_net(uint64_t k) { return static_cast<int3
 // decreases, 2: a pin outside [0, N), 4: net_ptr[0] != 0, 8: net_ptr[E] < 0),
 // [1] net_ptr[0], [2] net_ptr[E] = P, [3] incidences, [4] raw pairs, [5] the
 // longest row's raw pairs, [6] the finishing pass's unique entries, [7] its
-// longest row, [8] the most raw pairs + incidences of a row.
-enum { kSumFlags, kSumFirst, kSumPins, kSumInc, kSumRaw, kSumMaxRaw, kSumUnique, kSumMaxRow, kSumMaxNeed, kSumSize };
+// longest row, [8] the most raw pairs + incidences of a row, [9] the most
+// incidences of a row of more than kWarpCap raw pairs.
+enum {
+    kSumFlags, kSumFirst, kSumPins, kSumInc, kSumRaw, kSumMaxRaw, kSumUnique, kSumMaxRow, kSumMaxNeed, kSumMaxLongInc,
+    kSumSize
+};
 
 __global__ void k_validate(int32_t E, int32_t N, const int64_t *__restrict__ net_ptr,
                            const int32_t *__restrict__ pin_cell, unsigned long long *__restrict__ summary) {
@@ -142,22 +147,29 @@ __global__ void k_count(int32_t E, int32_t N, const int64_t *__restrict__ net_pt
     });
 }
 
-// The longest row's raw pairs into mx[0], and its raw pairs + incidences
-// (the block tier's slots) into mx[need_at].
+// Into the summary: the longest row's raw pairs, the most raw pairs +
+// incidences of a row (the block tier's slots), and the most incidences of a
+// row of more than kWarpCap raw pairs.
 __global__ void k_max_rawlen(int32_t N, const int64_t *__restrict__ raw_ptr, const int64_t *__restrict__ inc_ptr,
-                             unsigned long long *__restrict__ mx, int need_at) {
-    unsigned long long best = 0, need = 0;
+                             unsigned long long *__restrict__ sum) {
+    unsigned long long best = 0, need = 0, linc = 0;
     for (int64_t i = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; i < N; i += (int64_t)gridDim.x * blockDim.x) {
         const unsigned long long raw = (unsigned long long)(raw_ptr[i + 1] - raw_ptr[i]);
+        const unsigned long long inc = (unsigned long long)(inc_ptr[i + 1] - inc_ptr[i]);
         best = max(best, raw);
-        need = max(need, raw + (unsigned long long)(inc_ptr[i + 1] - inc_ptr[i]));
+        need = max(need, raw + inc);
+        if (raw > (unsigned long long)kWarpCap) linc = max(linc, inc);
     }
     for (int o = 16; o; o >>= 1) {
         best = max(best, __shfl_xor_sync(0xffffffffu, best, o));
         need = max(need, __shfl_xor_sync(0xffffffffu, need, o));
+        linc = max(linc, __shfl_xor_sync(0xffffffffu, linc, o));
     }
-    if ((threadIdx.x & 31) == 0 && best) atomicMax(mx, best);
-    if ((threadIdx.x & 31) == 0 && need) atomicMax(mx + need_at, need);
+    if ((threadIdx.x & 31) == 0) {
+        if (best) atomicMax(sum + kSumMaxRaw, best);
+        if (need) atomicMax(sum + kSumMaxNeed, need);
+        if (linc) atomicMax(sum + kSumMaxLongInc, linc);
+    }
 }
 
 // ------------------------------------------------------------------ scatter
@@ -855,20 +867,21 @@ __device__ __forceinline__ void block_scan_excl(int total, At at, uint32_t *s_pa
 // Stable LSD radix sort of n cells (and their payloads, if k0 is not null)
 // by their low nbits bits, between (c0, k0) and (c1, k1), by a block of NW
 // warps.  Each warp owns a contiguous segment: it counts its digits (shared
-// atomics into its own row of cnt), then works out its own offsets (entries
-// of lower digits in all warps, then of the same digit in lower warps) into
-// its row of off, and walks its segment 32 entries at a time, each entry's
-// rank being its digit's offset plus the lanes of lower index with the same
-// digit.  Returns the number of passes: odd leaves the result in (c1, k1).
+// atomics into its own row of cnt), works out its own offsets (entries of
+// lower digits in all warps, then of the same digit in lower warps) in
+// registers, and once every warp has read the counts puts them in its row,
+// then walks its segment 32 entries at a time, each entry's rank being its
+// digit's offset plus the lanes of lower index with the same digit.
+// Returns the number of passes: odd leaves the result in (c1, k1).
 template <typename KT, int NW>
-__device__ int block_radix_sort(uint32_t *c0, KT *k0, uint32_t *c1, KT *k1, int n, int nbits, uint32_t *cnt,
-                                uint32_t *off) {
+__device__ int block_radix_sort(uint32_t *c0, KT *k0, uint32_t *c1, KT *k1, int n, int nbits, uint32_t *cnt) {
+    constexpr int kDigitsPerLane = (1 << kRadixBits) / 32;
     const unsigned full = 0xffffffffu;
     const int lane = threadIdx.x & 31, wid = threadIdx.x >> 5;
     const int seg = ((n + NW - 1) / NW + 31) & ~31;
     const int beg = min(wid * seg, n), end = min(beg + seg, n);
     uint32_t *h = cnt + wid * kHistStride;
-    uint32_t *o = off + wid * kHistStride;
+    uint32_t *o = h;  // the offsets replace the counts
     int passes = 0;
     for (int s = 0; s < nbits; s += kRadixBits, ++passes) {
         const int R = 1 << min(kRadixBits, nbits - s);
@@ -877,9 +890,11 @@ __device__ int block_radix_sort(uint32_t *c0, KT *k0, uint32_t *c1, KT *k1, int 
         __syncwarp();
         for (int i = beg + lane; i < end; i += 32) atomicAdd(&h[(c0[i] >> s) & mask], 1u);
         __syncthreads();
+        uint32_t mine[kDigitsPerLane];  // this warp's offset of digit 32 j + lane
         uint32_t carry = 0u;
-        for (int d0 = 0; d0 < R; d0 += 32) {  // lane owns digit d0 + lane
-            const int d = d0 + lane;
+#pragma unroll
+        for (int j = 0; j < kDigitsPerLane; ++j) {
+            const int d = 32 * j + lane;
             uint32_t all = 0u, before = 0u;
             if (d < R) {
 #pragma unroll
@@ -890,9 +905,13 @@ __device__ int block_radix_sort(uint32_t *c0, KT *k0, uint32_t *c1, KT *k1, int 
                 }
             }
             const uint32_t incl = warp_incl_scan(all, lane);
-            if (d < R) o[d] = carry + incl - all + before;
+            mine[j] = carry + incl - all + before;
             carry += __shfl_sync(full, incl, 31);
         }
+        __syncthreads();  // every warp has read every warp's counts
+#pragma unroll
+        for (int j = 0; j < kDigitsPerLane; ++j)
+            if (32 * j + lane < R) o[32 * j + lane] = mine[j];
         __syncwarp();
         for (int b = beg; b < end; b += 32) {
             const int i = b + lane;
@@ -936,7 +955,6 @@ k_rows_block(const int64_t *__restrict__ inc_ptr, const int32_t *__restrict__ in
     constexpr int T = NW * 32;
     extern __shared__ __align__(16) char smem_dyn[];
     __shared__ uint32_t cnt[NW * kHistStride];
-    __shared__ uint32_t off[NW * kHistStride];
     __shared__ double inc_w[kIncW];
     __shared__ uint32_t s_part[NW];
     __shared__ long long s_q[NW];
@@ -951,8 +969,12 @@ k_rows_block(const int64_t *__restrict__ inc_ptr, const int32_t *__restrict__ in
     uint32_t *cb = reinterpret_cast<uint32_t *>(ka + C);
     KT *kb = reinterpret_cast<KT *>(cb + C);
     int32_t *inc_e = reinterpret_cast<int32_t *>(kb + C);
-    uint32_t *ofs = cb;                                        // while generating
-    int64_t *pbase = reinterpret_cast<int64_t *>(cb + C / 2);  // while generating
+    // While generating: the incidences' pin offsets and pin bases, 32-bit
+    // bases with one-byte payloads (the host takes those only for fewer than
+    // 2^32 pins), so that they fit the smaller second side.
+    using PB = std::conditional_t<sizeof(KT) == 1, uint32_t, int64_t>;
+    uint32_t *ofs = cb;
+    PB *pbase = reinterpret_cast<PB *>(cb + C / 2);
     const int rows_end = bin_off[bin + 1];
     for (int r = bin_off[bin] + blockIdx.x; r < rows_end; r += gridDim.x) {
         const int32_t row = binned[r];
@@ -980,7 +1002,7 @@ k_rows_block(const int64_t *__restrict__ inc_ptr, const int32_t *__restrict__ in
         } else {
             for (int i = tid; i < ninc; i += T) ca[i] = (uint32_t)inc_net[ib + i];
             __syncthreads();
-            const int p = block_radix_sort<KT, NW>(ca, nullptr, cb, nullptr, ninc, net_bits, cnt, off);
+            const int p = block_radix_sort<KT, NW>(ca, nullptr, cb, nullptr, ninc, net_bits, cnt);
             const uint32_t *srt = (p & 1) ? cb : ca;
             for (int i = tid; i < ninc; i += T) inc_e[i] = (int32_t)srt[i];
         }
@@ -992,13 +1014,13 @@ k_rows_block(const int64_t *__restrict__ inc_ptr, const int32_t *__restrict__ in
             const int32_t e = inc_e[i];
             const int64_t nb = net_ptr[e];
             ofs[i] = (uint32_t)(net_ptr[e + 1] - nb);
-            pbase[i] = nb;
+            pbase[i] = (PB)nb;
             if (staged) inc_w[i] = wnet[e];
         }
         __syncthreads();
         block_scan_excl<NW>(ninc, [&](int p) -> uint32_t & { return ofs[p]; }, s_part);
         __syncthreads();
-        for (int i = tid; i < ninc; i += T) pbase[i] -= (int64_t)ofs[i];
+        for (int i = tid; i < ninc; i += T) pbase[i] -= (PB)ofs[i];  // modulo 2^32 for PB = uint32
         __syncthreads();
 
         // 3. entries, one per pin, incidences in order (four gathers in flight)
@@ -1020,7 +1042,7 @@ k_rows_block(const int64_t *__restrict__ inc_ptr, const int32_t *__restrict__ in
 #pragma unroll
             for (int u = 0; u < 4; ++u) {
                 const int f = f0 + u * T;
-                q[u] = f < n ? pin_cell[pbase[a[u]] + f] : 0;
+                q[u] = f < n ? pin_cell[(int64_t)(PB)(pbase[a[u]] + (PB)f)] : 0;
             }
 #pragma unroll
             for (int u = 0; u < 4; ++u) {
@@ -1038,7 +1060,7 @@ k_rows_block(const int64_t *__restrict__ inc_ptr, const int32_t *__restrict__ in
         __syncthreads();
 
         // 4. stable sort by cell
-        const int p = block_radix_sort<KT, NW>(ca, ka, cb, kb, n, cell_bits, cnt, off);
+        const int p = block_radix_sort<KT, NW>(ca, ka, cb, kb, n, cell_bits, cnt);
         const uint32_t *cs = (p & 1) ? cb : ca;
         const KT *ks = (p & 1) ? kb : ka;
         WT *svals = reinterpret_cast<WT *>((p & 1) ? ca : cb);  // the free side
@@ -1324,8 +1346,7 @@ void build_graph_impl(gift_ctx *ctx, const gift_netlist *nl, const gift_build_op
     }
     {
         LaunchTimer lt(ctx, st, "build.maxraw", 16.0 * (N + 1));
-        k_max_rawlen<<<grid_for(ctx, N, 256), 256, 0, st>>>(N, raw_ptr.as<int64_t>(), inc_ptr_p, sum_d + kSumMaxRaw,
-                                                             kSumMaxNeed - kSumMaxRaw);
+        k_max_rawlen<<<grid_for(ctx, N, 256), 256, 0, st>>>(N, raw_ptr.as<int64_t>(), inc_ptr_p, sum_d);
         check_launch("k_max_rawlen");
     }
     GIFT_CUDA(cudaMemcpyAsync(sum_d + kSumInc, inc_ptr_p + N, sizeof(int64_t), cudaMemcpyDeviceToDevice,
@@ -1340,7 +1361,7 @@ void build_graph_impl(gift_ctx *ctx, const gift_netlist *nl, const gift_build_op
     GIFT_REQUIRE(!(hs[kSumFlags] & 1), "gift_build_graph: net_ptr decreases");
     GIFT_REQUIRE(!(hs[kSumFlags] & 2), "gift_build_graph: pin_cell id out of [0, num_cells)");
     const int64_t ninc = (int64_t)hs[kSumInc], nraw = (int64_t)hs[kSumRaw], maxraw = (int64_t)hs[kSumMaxRaw],
-                  maxneed = (int64_t)hs[kSumMaxNeed];
+                  maxneed = (int64_t)hs[kSumMaxNeed], maxlonginc = (int64_t)hs[kSumMaxLongInc];
     g->raw_pairs = nraw;
 
     // ---- temporaries once the totals are known: the fill counters and the
@@ -1390,10 +1411,10 @@ void build_graph_impl(gift_ctx *ctx, const gift_netlist *nl, const gift_build_op
     if (maxraw > kWarpCap) {
         int optin = 0;
         GIFT_CUDA(cudaDeviceGetAttribute(&optin, cudaDevAttrMaxSharedMemoryPerBlockOptin, ctx->device));
-        cudaFuncAttributes fa{};
+        cudaFuncAttributes fa{};  // static shared memory: the same for every payload and weight type
         GIFT_CUDA(cudaFuncGetAttributes(&fa, (const void *)k_rows_block<float, uint16_t, false, kWideWarps>));
         const int64_t room = (int64_t)optin - (int64_t)fa.sharedSizeBytes;
-        top = std::min<int64_t>(kBlockTop, room / block_bytes<uint16_t>(512) * 512);
+        top = std::min<int64_t>(kBlockTop, room / block_bytes<uint16_t>(512) * 512);  // fits both payloads
         GIFT_REQUIRE(top >= 1024, "gift_build_graph: too little shared memory for the block tier");
     }
     DevBuf gscratch;
@@ -1451,24 +1472,32 @@ void build_graph_impl(gift_ctx *ctx, const gift_netlist *nl, const gift_build_op
             k_bin_place<<<bgrid, 256, 0, st>>>(big_p, bc, raw_ptr.as<int64_t>(), inc_ptr_p, bins, bin_cnt, bin_fill,
                                                  bin_off, binned_p);
             check_launch("k_bin_place");
-            auto launch = [&](auto nw, int bin, int64_t cap) {
+            // one-byte incidence indices (12 bytes a slot instead of 14: more
+            // blocks per SM) when no long row has more than 256 incidences
+            const bool narrow_payload = maxlonginc <= 256 && P < ((int64_t)1 << 32);
+            auto launch = [&](auto nw, auto kt, int bin, int64_t cap) {
                 constexpr int NW = decltype(nw)::value;
-                const void *fn = (const void *)k_rows_block<WT, uint16_t, false, NW>;
-                const size_t smem = (size_t)block_bytes<uint16_t>(cap);
+                using KT = decltype(kt);
+                const void *fn = (const void *)k_rows_block<WT, KT, false, NW>;
+                const size_t smem = (size_t)block_bytes<KT>(cap);
                 // always the largest class's size: builds on other host threads set the same value
                 GIFT_CUDA(cudaFuncSetAttribute(fn, cudaFuncAttributeMaxDynamicSharedMemorySize,
-                                               (int)block_bytes<uint16_t>(top)));
+                                               (int)block_bytes<KT>(top)));
                 int per_sm = 0;
                 GIFT_CUDA(cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, fn, NW * 32, smem));
-                k_rows_block<WT, uint16_t, false, NW><<<ctx->num_sms * std::max(per_sm, 1), NW * 32, smem, st>>>(
+                k_rows_block<WT, KT, false, NW><<<ctx->num_sms * std::max(per_sm, 1), NW * 32, smem, st>>>(
                     inc_ptr_p, inc_net_p, g->net_ptr, g->pin_cell, wnet_p,
                     raw_ptr.as<int64_t>(), out_col.as<int32_t>(), ov, ucount_p, g->degree,
                     binned_p, bin_off, bin, nullptr, cap, N, cell_bits, net_bits);
                 check_launch("k_rows_block");
             };
+            auto launch_class = [&](auto kt, int b) {
+                if (bins.cap[b] <= kNarrowCap) launch(std::integral_constant<int, kNarrowWarps>{}, kt, b, bins.cap[b]);
+                else launch(std::integral_constant<int, kWideWarps>{}, kt, b, bins.cap[b]);
+            };
             for (int b = 0, lo = (int)kWarpCap; b + 1 < bins.n && lo < std::min(maxneed, top); lo = (int)bins.cap[b++]) {
-                if (bins.cap[b] <= kNarrowCap) launch(std::integral_constant<int, kNarrowWarps>{}, b, bins.cap[b]);
-                else launch(std::integral_constant<int, kWideWarps>{}, b, bins.cap[b]);
+                if (narrow_payload) launch_class(uint8_t{}, b);
+                else launch_class(uint16_t{}, b);
             }
         }
         if (gcap > 0) {

@@ -5,7 +5,9 @@ oracle: structure, stored weights and degrees.
 A row's slots are its raw entries plus its incidences (every pin of every
 net of the row, its own included).  The cases: a row of exactly 1,024 slots
 (the smallest class, full); a row of exactly 15,360 slots (the largest
-shared-memory class on this device, full); more than 32 incidences (the
+shared-memory class on this device, full) with 256 incidences (the most
+that one-byte incidence indices allow); a row of 300 incidences in a
+shared-memory class (two-byte indices); more than 32 incidences (the
 incidences sorted block-wide rather than in one warp) with more than 2^16
 cells and nets (three radix passes on each, the result on the other side of
 the buffers); cells repeated inside long nets, the long row's cell twice in
@@ -109,6 +111,11 @@ def case_repeats():
     return from_nets(N, nets), hub, None
 
 
+def case_many_incidences():
+    nets = hub_nets(41, 5000, 9, 300, 3) + [n for n in small_nets(42, 5000, 3000) if 9 not in n]
+    return from_nets(5000, nets), 9, 900
+
+
 def case_global_wide_ids():
     N = 70000
     nets = hub_nets(39, N, 2, 400, 45) + [n for n in small_nets(40, N, 3000) if 2 not in n]
@@ -116,7 +123,8 @@ def case_global_wide_ids():
 
 
 CASES = {"need-1024": case_need_1024, "top-class": case_top_class, "wide-ids": case_wide_ids,
-         "repeats": case_repeats, "global-wide-ids": case_global_wide_ids}
+         "repeats": case_repeats, "many-incidences": case_many_incidences,
+         "global-wide-ids": case_global_wide_ids}
 _BUILT = {}
 
 
@@ -139,8 +147,12 @@ def test_block_tier_bit_exact(ctx, name, wd):
         assert need > 15360
     if name in ("wide-ids", "global-wide-ids"):
         assert nl.num_cells > 1 << 16 and (name == "global-wide-ids" or nl.num_nets > 1 << 16)
-    if name in ("wide-ids", "repeats", "global-wide-ids"):
+    if name in ("wide-ids", "repeats", "many-incidences", "global-wide-ids"):
         assert int((nl.pin_cell == hub).sum()) > 32
+    if name == "top-class":  # the most incidences a row may have for one-byte indices
+        assert int((nl.pin_cell == hub).sum()) == 256
+    if name == "many-incidences":  # more: two-byte indices, in a shared-memory class
+        assert int((nl.pin_cell == hub).sum()) == 300
     h = gift.gift_build_graph(ctx, nl.num_cells, dev(nl.net_ptr), dev(nl.pin_cell), dev(nl.is_fixed),
                               gift.WEIGHT[wd])
     try:
