@@ -983,7 +983,7 @@ def run_ours(args):
                                       if tname == "filter.sweep" and trec["total_ms"] > 0 else None),
                 "traffic": traffic,
                 # DRAM bytes the launches really move (recorded traffic) over the live launch time: the
-                # random row gathers fetch about 4.4x the algorithmic bytes on this graph
+                # random row gathers fetch about 3.3x the algorithmic bytes on this graph
                 "dram_frac": (traffic / (per_launch_ms * 1e-3) / 1e9 / peak) if traffic and per_launch_ms > 0 else None}
     breakdown = {k: {"ms_per_step": v["total_ms"] / args.steps, "kernels_per_step": v["kernels"] / args.steps,
                      "alg_GBps": (v["alg_bytes"] / (v["total_ms"] * 1e-3) / 1e9) if v["total_ms"] > 0 else None}
