@@ -73,3 +73,54 @@ def test_recorded_traffic_is_tied_to_source_and_schedule(monkeypatch):
                                       sched) is None
         monkeypatch.setattr(bench, "sweep_source_hash", lambda: "0" * 16)
         assert bench.recorded_traffic("filter.sweep", workload, weights, sched) is None
+
+
+def _traffic_csv(path, reads):
+    """An ncu launch-list CSV with one k_sweep launch per entry of reads."""
+    head = ["ID", "Kernel Name", "Metric Name", "Metric Unit", "Metric Value", "Extra"]
+    rows = [head]
+    for i, rd in enumerate(reads):
+        name = f"void k_sweep_dr<float, 4, 4, 2, 2, {i % 2}, 0, 0>(gift::SweepArgs)"
+        rows += [[str(i), name, "dram__bytes_read.sum", "byte", f"{rd:,}", ""],
+                 [str(i), name, "dram__bytes_write.sum", "byte", "1,000", ""],
+                 [str(i), name, "gpu__time_duration.sum", "ns", "100", ""]]
+    with open(path, "w", newline="") as f:
+        import csv
+        csv.writer(f).writerows(rows)
+
+
+def test_record_traffic_keeps_one_record_per_schedule(tmp_path, monkeypatch):
+    """A capture replaces the record of its own schedule, keeps the records of
+    other schedules taken on the same kernel source, and drops records of an
+    older source."""
+    import argparse
+    import shutil
+    import bench
+    root = tmp_path / "repo"
+    (root / "profiles").mkdir(parents=True)
+    shutil.copytree(os.path.join(ROOT, "paper_2502_17632_gb300", "csrc"), root / "paper_2502_17632_gb300" / "csrc")
+    monkeypatch.setattr(bench, "ROOT", str(root))
+    cur = bench.sweep_source_hash()
+    stale = {"dram_bytes_per_launch": 1.0, "per_launch": [], "source_hash": "0" * 16, "sweep_schedule": [1, 2, 3, 4]}
+    with open(root / "profiles" / "traffic.json", "w") as f:
+        json.dump({"filter.sweep": {"large-2.2m/f32": [stale]}}, f)
+
+    def record(reads, sched):
+        csv_path = tmp_path / "t.csv"
+        _traffic_csv(csv_path, reads)
+        args = argparse.Namespace(record_traffic=str(csv_path), schedule=sched, workload="large-2.2m",
+                                  weights="f32")
+        bench.record_traffic(args)
+        with open(root / "profiles" / "traffic.json") as f:
+            return json.load(f)["filter.sweep"]["large-2.2m/f32"]
+
+    recs = record([100, 200, 300, 400], "4842,4842,0,4844")
+    assert [r["sweep_schedule"] for r in recs] == [[4842, 4842, 0, 4844]]  # the stale record is gone
+    assert recs[0]["source_hash"] == cur and recs[0]["dram_bytes_per_launch"] == pytest.approx(1250.0)
+    recs = record([500, 600, 700, 800], "4844,4842,0,4844")
+    assert sorted(tuple(r["sweep_schedule"]) for r in recs) == [(4842, 4842, 0, 4844), (4844, 4842, 0, 4844)]
+    recs = record([1000, 1000, 1000, 1000], "4842,4842,0,4844")  # replaces its own schedule's record
+    by = {tuple(r["sweep_schedule"]): r["dram_bytes_per_launch"] for r in recs}
+    assert by == {(4842, 4842, 0, 4844): pytest.approx(2000.0), (4844, 4842, 0, 4844): pytest.approx(1650.0)}
+    assert bench.recorded_traffic("filter.sweep", "large-2.2m", "f32", [4844, 4842, 0, 4844]) == pytest.approx(1650.0)
+    assert bench.recorded_traffic("filter.sweep", "large-2.2m", "f32", [4842, 4842, 0, 4842]) is None
