@@ -169,6 +169,7 @@ void gift_ctx_destroy(gift_ctx *ctx) {
     collect_timings(ctx, true);
     for (auto e : ctx->event_pool) cudaEventDestroy(e);
     if (ctx->side) cudaStreamDestroy(ctx->side);
+    if (ctx->order_side) cudaStreamDestroy(ctx->order_side);
     if (ctx->dev_error) cudaFree(ctx->dev_error);
     if (ctx->wtab) cudaFree(ctx->wtab);
     if (ctx->pool) cudaMemPoolDestroy(ctx->pool);

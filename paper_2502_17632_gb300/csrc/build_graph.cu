@@ -18,6 +18,7 @@
 //   compact  round each sum once to the storage type, write col/val, and
 //            d_i = sum_j A_ij in FP64 over the stored weights in column order.
 #include <algorithm>
+#include <mutex>
 #include <type_traits>
 #include <utility>
 
@@ -31,6 +32,7 @@ constexpr int kWarpCap = 512;      // keys per warp in the warp tier
 constexpr int kRowsWarps = 8;      // warps per block in the warp tier
 constexpr uint64_t kPadKey = ~0ull;
 constexpr int64_t kPadFraction = 1024;
+constexpr int64_t kEarlyOrderRows = 1 << 16;  // graphs from this many rows order them beside the row kernels
 
 // Bits needed to write v (0 for v = 0).
 inline int bit_width_u64(uint64_t v) {
@@ -64,10 +66,11 @@ __device__ __forceinline__ int32_t key_net(uint64_t k) { return static_cast<int3
 // [1] net_ptr[0], [2] net_ptr[E] = P, [3] incidences, [4] raw pairs, [5] the
 // longest row's raw pairs, [6] the finishing pass's unique entries, [7] its
 // longest row, [8] the most raw pairs + incidences of a row, [9] the most
-// incidences of a row of more than kWarpCap raw pairs.
+// incidences of a row of more than kWarpCap raw pairs, [10] the rows of at
+// least kCompRows raw pairs (from the length order worked out beside the rows).
 enum {
     kSumFlags, kSumFirst, kSumPins, kSumInc, kSumRaw, kSumMaxRaw, kSumUnique, kSumMaxRow, kSumMaxNeed, kSumMaxLongInc,
-    kSumSize
+    kSumLong, kSumSize
 };
 
 __global__ void k_validate(int32_t E, int32_t N, const int64_t *__restrict__ net_ptr,
@@ -1397,6 +1400,41 @@ void build_graph_impl(gift_ctx *ctx, const gift_netlist *nl, const gift_build_op
         check_launch("k_scatter");
     }
 
+    // ---- rows in length order over the raw layout (large graphs), worked
+    // out on a stream of its own while the row kernels run: when the raw
+    // layout becomes the CSR (below) it is the sweeps' length order
+    DevBuf early_perm, early_rp;
+    cudaEvent_t order_done = nullptr;
+    struct OrderWait {  // on every way out, st waits for the order's kernels (they read raw_ptr)
+        cudaStream_t st;
+        cudaEvent_t &ev;
+        ~OrderWait() {
+            if (ev) {
+                cudaStreamWaitEvent(st, ev, 0);
+                cudaEventDestroy(ev);
+            }
+        }
+    };
+    if (N >= kEarlyOrderRows) {
+        cudaStream_t os;
+        {
+            std::lock_guard<std::mutex> lk(ctx->side_mu);
+            if (!ctx->order_side) GIFT_CUDA(cudaStreamCreateWithFlags(&ctx->order_side, cudaStreamNonBlocking));
+            os = ctx->order_side;
+        }
+        // raw_ptr is complete: the summary read above waited for st
+        early_perm = DevBuf(ctx, sizeof(int32_t) * N, os);
+        early_rp = DevBuf(ctx, sizeof(int64_t) * (N + 1), os);
+        {
+            LaunchTimer lt(ctx, os, "build.sorted", 36.0 * N, 8);
+            length_order(ctx, raw_ptr.as<int64_t>(), N, early_perm.as<int32_t>(), early_rp.as<int64_t>(),
+                         reinterpret_cast<int64_t *>(sum_d + kSumLong), os);
+        }
+        GIFT_CUDA(cudaEventCreateWithFlags(&order_done, cudaEventDisableTiming));
+        GIFT_CUDA(cudaEventRecord(order_done, os));
+    }
+    OrderWait order_wait{st, order_done};
+
     // ---- per-row expansion, sort, duplicate sums, rounding, degrees
     DevBuf out_col(ctx, sizeof(int32_t) * std::max<int64_t>(nraw, 1), st);  // may become the graph's col
     DevBuf out_val(ctx, wsz * std::max<int64_t>(nraw, 1), st);             // and val
@@ -1574,7 +1612,8 @@ void build_graph_impl(gift_ctx *ctx, const gift_netlist *nl, const gift_build_op
                                                            out_col.as<int32_t>(), out_val.as<__half>(), s2, s4, agg);
         check_launch("k_finish_rows");
     }
-    unsigned long long hagg[2] = {0, 0};
+    if (order_done) GIFT_CUDA(cudaStreamWaitEvent(st, order_done, 0));
+    unsigned long long hagg[kSumSize - kSumUnique] = {};
     GIFT_CUDA(cudaMemcpyAsync(hagg, agg, sizeof(hagg), cudaMemcpyDeviceToHost, st));
     GIFT_CUDA(cudaStreamSynchronize(st));
     const int64_t nnz = (int64_t)hagg[0];
@@ -1586,6 +1625,12 @@ void build_graph_impl(gift_ctx *ctx, const gift_netlist *nl, const gift_build_op
         g->col = static_cast<int32_t *>(out_col.release());
         g->val = out_val.release();
         g->stored = nraw;
+        if (early_perm.p) {  // the raw lengths are the stored lengths: the order is the graph's length order
+            g->n_long = (int64_t)hagg[kSumLong - kSumUnique];
+            g->srt.perm = static_cast<int32_t *>(early_perm.release());
+            g->srt.rp = static_cast<int64_t *>(early_rp.release());
+            g->device_bytes += (int64_t)(4 * N + 8 * (N + 1));
+        }
     } else {
         g->row_ptr = (int64_t *)dev_alloc(ctx, sizeof(int64_t) * (N + 1), st);
         {

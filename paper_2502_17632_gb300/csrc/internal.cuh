@@ -124,6 +124,9 @@ struct gift_ctx {
     // side stream for uploads that overlap work on the caller's stream (gift_run)
     std::mutex side_mu;
     cudaStream_t side = nullptr;
+    // stream on which a build works out the rows' length order while its
+    // row kernels run on the caller's stream (created on first use, under side_mu)
+    cudaStream_t order_side = nullptr;
 };
 
 namespace gift {
@@ -296,6 +299,11 @@ void release_sell(gift_graph *g, cudaStream_t st);
 // absent (caller holds g->mu); want_long: also count the rows of at least
 // kCompRows entries into g->n_long (a host wait)
 void ensure_sorted(gift_ctx *ctx, gift_graph *g, bool copy, cudaStream_t st, bool want_long = false);
+// The N rows of row_ptr in length order, longest first (perm[slot] = row),
+// and the offsets of their entries in that order (rp, N + 1 values); with
+// n_long (device memory) the number of rows of at least kCompRows entries.
+void length_order(gift_ctx *ctx, const int64_t *row_ptr, int64_t N, int32_t *perm, int64_t *rp, int64_t *n_long,
+                  cudaStream_t st);
 void release_sorted(gift_graph *g, cudaStream_t st);
 // filter.cu
 // mirror (optional): the last sweep also stores the output there -- mapped

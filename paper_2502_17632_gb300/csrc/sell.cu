@@ -244,30 +244,39 @@ __global__ void k_copy_sorted(int64_t n, const int64_t *__restrict__ row_ptr, co
 
 }  // namespace
 
+void length_order(gift_ctx *ctx, const int64_t *row_ptr, int64_t N, int32_t *perm, int64_t *rp, int64_t *n_long,
+                  cudaStream_t st) {
+    const int64_t nblocks = std::max<int64_t>(1, ceil_div(N, kSortChunk));
+    DevBuf counts(ctx, sizeof(int32_t) * kSortKeys * nblocks, st);
+    DevBuf offs(ctx, sizeof(int64_t) * (kSortKeys * nblocks + 1), st);
+    DevBuf len(ctx, sizeof(int64_t) * std::max<int64_t>(N, 1), st);
+    k_sort_count<<<(unsigned)nblocks, 256, 0, st>>>(N, row_ptr, nblocks, counts.as<int32_t>());
+    check_launch("k_sort_count");
+    exclusive_scan(ctx, counts.as<int32_t>(), offs.as<int64_t>(), kSortKeys * nblocks, st);
+    if (n_long)  // rows in the keys of the long rows
+        GIFT_CUDA(cudaMemcpyAsync(n_long, offs.as<int64_t>() + (int64_t)kLongKeys * nblocks, sizeof(int64_t),
+                                  cudaMemcpyDeviceToDevice, st));
+    k_sort_place<<<(unsigned)nblocks, 256, 0, st>>>(N, row_ptr, nblocks, offs.as<int64_t>(), perm,
+                                                    len.as<int64_t>());
+    check_launch("k_sort_place");
+    exclusive_scan(ctx, len.as<int64_t>(), rp, N, st);
+}
+
 void ensure_sorted(gift_ctx *ctx, gift_graph *g, bool copy, cudaStream_t st, bool want_long) {
     const int64_t N = g->n;
     const size_t wsz = g->weight_dtype == GIFT_WEIGHT_F32 ? 4 : 2;
     if (!g->srt.perm) {
-        const int64_t nblocks = std::max<int64_t>(1, ceil_div(N, kSortChunk));
-        DevBuf counts(ctx, sizeof(int32_t) * kSortKeys * nblocks, st);
-        DevBuf offs(ctx, sizeof(int64_t) * (kSortKeys * nblocks + 1), st);
         DevBuf perm(ctx, sizeof(int32_t) * std::max<int64_t>(N, 1), st);
-        DevBuf len(ctx, sizeof(int64_t) * std::max<int64_t>(N, 1), st);
         DevBuf rp(ctx, sizeof(int64_t) * (N + 1), st);
         {
             LaunchTimer lt(ctx, st, "build.sorted", 36.0 * N, 8);
-            k_sort_count<<<(unsigned)nblocks, 256, 0, st>>>(N, g->row_ptr, nblocks, counts.as<int32_t>());
-            check_launch("k_sort_count");
-            exclusive_scan(ctx, counts.as<int32_t>(), offs.as<int64_t>(), kSortKeys * nblocks, st);
-            if (want_long) {  // rows in the keys of the long rows
-                GIFT_CUDA(cudaMemcpyAsync(&g->n_long, offs.as<int64_t>() + (int64_t)kLongKeys * nblocks,
-                                          sizeof(int64_t), cudaMemcpyDeviceToHost, st));
+            DevBuf nl;
+            if (want_long) nl = DevBuf(ctx, sizeof(int64_t), st);
+            length_order(ctx, g->row_ptr, N, perm.as<int32_t>(), rp.as<int64_t>(), nl.as<int64_t>(), st);
+            if (want_long) {
+                GIFT_CUDA(cudaMemcpyAsync(&g->n_long, nl.p, sizeof(int64_t), cudaMemcpyDeviceToHost, st));
+                GIFT_CUDA(cudaStreamSynchronize(st));
             }
-            k_sort_place<<<(unsigned)nblocks, 256, 0, st>>>(N, g->row_ptr, nblocks, offs.as<int64_t>(),
-                                                            perm.as<int32_t>(), len.as<int64_t>());
-            check_launch("k_sort_place");
-            exclusive_scan(ctx, len.as<int64_t>(), rp.as<int64_t>(), N, st);
-            if (want_long) GIFT_CUDA(cudaStreamSynchronize(st));
         }
         g->srt.perm = perm.as<int32_t>();
         g->srt.rp = rp.as<int64_t>();
