@@ -970,16 +970,16 @@ def run_ours(args):
     per_launch_bytes = trec["alg_bytes"] / max(trec["launches"], 1)
     achieved = per_launch_bytes / (per_launch_ms * 1e-3) / 1e9 if per_launch_ms > 0 else 0.0
     traffic = recorded_traffic(tname, args.workload, args.weights, schedule)
-    # the survey's byte model per sweep (CSR once, the scale vector, the signal read and written once, plus
+    # a coarser byte model per sweep (CSR once, the scale vector, the signal read and written once, plus
     # the second written signal of the two-chain sweeps 1 and 2), for comparison with the library's count
     wsz = 4 if args.weights == "f32" else 2
-    survey_filter_bytes = 4 * (info.stored * (4.0 + wsz) + 8.0 * (N + 1) + 4.0 * N + 8.0 * N * 2 * S) + \
+    coarse_filter_bytes = 4 * (info.stored * (4.0 + wsz) + 8.0 * (N + 1) + 4.0 * N + 8.0 * N * 2 * S) + \
         2 * 4.0 * N * 2 * S
     roofline = {"bound": "hbm", "kernel": tname, "achieved": achieved, "peak": peak, "unit": "GB/s",
                 "frac": achieved / peak, "peak_source": f"hbm_gbs, {peak_src}",
                 "alg_bytes_per_launch": per_launch_bytes, "ms_per_launch": per_launch_ms,
-                # one filter per step: the survey's bytes of all steps over the same kernels' time
-                "frac_survey_bytes": (survey_filter_bytes * args.steps / (trec["total_ms"] * 1e-3) / 1e9 / peak
+                # one filter per step: the coarser model's bytes of all steps over the same kernels' time
+                "frac_coarse_bytes": (coarse_filter_bytes * args.steps / (trec["total_ms"] * 1e-3) / 1e9 / peak
                                       if tname == "filter.sweep" and trec["total_ms"] > 0 else None),
                 "traffic": traffic,
                 # DRAM bytes the launches really move (recorded traffic) over the live launch time: the
